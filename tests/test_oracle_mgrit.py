@@ -1,0 +1,153 @@
+"""Pins of the oracle's MGRIT (Section 2.2, Tables 2, 3, 4 and 6)."""
+import numpy as np
+import pytest
+
+import workloads
+from conftest import golden
+from oracle import mgrit, psi, schemes, stepping
+
+
+def _two_level(fam, p, c, nx, nt, m, coarse):
+    st = stepping.FineStep(fam, p, c, nx)
+    return st, mgrit.make_levels(st, m, [coarse])
+
+
+def test_converges_to_sequential_stepping():
+    nx, nt, m = 64, 512, 8
+    c = schemes.cfl_number("ERK", 3)
+    ops = psi.build_hierarchy("ERK", 3, c, nx, nt, m, 3, rule="auto")
+    st = stepping.FineStep("ERK", 3, c, nx)
+    lev = mgrit.make_levels(st, m, [o.diag for o in ops])
+    u0 = workloads.fourier_field(nx)
+    U = mgrit.zero_iterate(u0, nt)
+    it, rel = mgrit.solve(lev, U, tol=1e-13)
+    ref = stepping.sequential(st, u0, nt)
+    assert rel <= 1e-13
+    assert np.linalg.norm(U - ref) / np.linalg.norm(ref) < 1e-11
+
+
+def test_ideal_coarse_operator_converges_in_one_iteration():
+    """Section 2.2: Psi = Phi^m makes the coarse problem the exact Schur
+    complement, so one iteration solves the system."""
+    nx, nt, m = 32, 256, 4
+    c = schemes.cfl_number("ERK", 2)
+    st = stepping.FineStep("ERK", 2, c, nx)
+    ideal = psi.build_hierarchy("ERK", 2, c, nx, nt, m, 2, rule="ideal")[0].diag
+    lev = mgrit.make_levels(st, m, [ideal])
+    U = workloads.random_iterate(nt, nx, workloads.sin4(nx), 7)
+    it, rel = mgrit.solve(lev, U, tol=1e-12)
+    assert it == 1 and rel < 1e-12
+
+
+@pytest.mark.parametrize("coarse", ["zero", "random"])
+def test_exactness_and_finite_termination(coarse):
+    """Whatever Psi is, after k FCF iterations C-points 0..2k equal the
+    sequential solution, and the solve ends after ceil((N_c - 1)/2) = n_t/(2m)
+    iterations (the exact-arithmetic count of Table 2's right-hand side)."""
+    nx, m, nc = 16, 4, 16
+    nt = m * nc
+    st = stepping.FineStep("ERK", 1, 0.85, nx)
+    rng = np.random.default_rng(3)
+    diag = {0: 0.0} if coarse == "zero" else {i: float(rng.standard_normal()) * 0.3 for i in range(-3, 2)}
+    lev = mgrit.make_levels(st, m, [diag])
+    u0 = workloads.sin4(nx)
+    ref = stepping.sequential(st, u0, nt)
+    U = workloads.random_iterate(nt, nx, u0, 11)
+    G = np.zeros_like(U)
+    for k in range(1, nc):
+        mgrit.f_relax(U, G, st, m); mgrit.c_relax(U, G, st, m); mgrit.f_relax(U, G, st, m)
+        r = mgrit.c_residual(U, G, st, m)
+        E = np.zeros_like(r)
+        mgrit.vcycle(lev, 1, E, r)
+        U[m::m] += E[1:]
+        mgrit.f_relax(U, G, st, m)
+        upto = min(2 * k, nc) * m
+        err = np.max(np.abs(U[: upto + 1] - ref[: upto + 1]))
+        assert err < 1e-12, (k, err)
+    U = workloads.random_iterate(nt, nx, u0, 11)
+    it, rel = mgrit.solve(lev, U, tol=1e-12, max_iter=50)
+    assert it == nt // (2 * m)
+
+
+def _table6():
+    out = {}
+    for r in golden("table6_threshold.txt"):
+        p, nx, nt = int(r[0]), int(r[1]), int(r[2])
+        for m, v in zip((2, 4, 8, 16, 32, 64), r[3:]):
+            out[(p, nx, nt, m)] = int(v)
+    return out
+
+
+# entries whose final residual ratio is not within a factor 2 of the
+# tolerance (robust to the random initial iterate); see the slow test for all
+TABLE6_ROBUST = [(1, 1024, 1024, 8), (2, 1024, 1024, 8), (3, 1024, 1024, 4), (3, 1024, 1024, 16),
+                 (4, 1024, 1024, 8)]
+
+
+@pytest.mark.parametrize("key", TABLE6_ROBUST)
+def test_table6_threshold_iterations_exact(key):
+    p, nx, nt, m = key
+    ops = psi.build_hierarchy("SDIRK", p, 4.0, nx, nt, m, 2, rule="threshold")
+    st, lev = _two_level("SDIRK", p, 4.0, nx, nt, m, ops[0].diag)
+    U = workloads.random_iterate(nt, nx, workloads.sin4(nx), 1)
+    it, rel = mgrit.solve(lev, U)
+    assert it == _table6()[key]
+
+
+def test_table2_rediscretized_sdirk1_m2():
+    """Table 2: SDIRK1+U1, 2^10 x 2^10, m = 2, Psi = Phi(m dt): 18 iterations."""
+    nx = nt = 1024
+    st = stepping.FineStep("SDIRK", 1, 4.0, nx)
+    lev = mgrit.make_levels(st, 2, [stepping.FineStep("SDIRK", 1, 8.0, nx)])
+    U = workloads.random_iterate(nt, nx, workloads.sin4(nx), 1)
+    it, rel = mgrit.solve(lev, U)
+    row = [r for r in golden("table2_rediscretized.txt") if r[0] == "1" and r[3] == "2"][0]
+    assert it == int(row[4])
+
+
+def test_table3_erk_soft():
+    """Table 3 right-hand side, soft (the paper's hand-tuned patterns are not
+    printed): the width rule must be no worse than the paper by more than 2
+    iterations (it is sometimes wider and then faster).  m = 2 is skipped: for
+    ERK1 the 3-point window already holds all of Phi^2."""
+    for r in golden("table3_erk_phim.txt"):
+        p, nx, nt = int(r[0]), int(r[1]), int(r[2])
+        c = schemes.cfl_number("ERK", p)
+        for m, v in zip((4, 8, 16, 32, 64), r[4:]):
+            ops = psi.build_hierarchy("ERK", p, c, nx, nt, m, 2, rule="auto")
+            st, lev = _two_level("ERK", p, c, nx, nt, m, ops[0].diag)
+            U = workloads.random_iterate(nt, nx, workloads.sin4(nx), 1)
+            it, rel = mgrit.solve(lev, U)
+            assert 2 <= it <= int(v) + 2, (p, m, it, v)
+
+
+def test_table4_multilevel_soft():
+    """Table 4: V-cycles with m = 4; iterations within 1, OC within 0.05."""
+    rows = golden("table4_multilevel.txt")
+    iters = {int(r[1]): (int(r[2]), int(r[3]), [int(v) for v in r[4:]]) for r in rows if r[0] == "iters"}
+    ocs = {int(r[1]): [float(v) for v in r[2:]] for r in rows if r[0] == "oc"}
+    for p, (nx, nt, counts) in iters.items():
+        c = schemes.cfl_number("ERK", p)
+        st = stepping.FineStep("ERK", p, c, nx)
+        nnz1 = len(psi.phi_m_column_nonzeros(st, nx))
+        for L, v in zip(range(2, 2 + len(counts)), counts):
+            ops = psi.build_hierarchy("ERK", p, c, nx, nt, 4, L, rule="auto")
+            lev = mgrit.make_levels(st, 4, [o.diag for o in ops])
+            U = workloads.random_iterate(nt, nx, workloads.sin4(nx), 1)
+            it, rel = mgrit.solve(lev, U)
+            assert abs(it - v) <= 1, (p, L, it, v)
+            oc = psi.operator_complexity([nnz1] + [o.nnz for o in ops], 4)
+            assert abs(oc - ocs[p][L - 2]) <= 0.05, (p, L, oc)
+
+
+@pytest.mark.slow
+def test_table6_all_within_one():
+    for key, v in _table6().items():
+        p, nx, nt, m = key
+        if nx > 1024:
+            continue
+        ops = psi.build_hierarchy("SDIRK", p, 4.0, nx, nt, m, 2, rule="threshold")
+        st, lev = _two_level("SDIRK", p, 4.0, nx, nt, m, ops[0].diag)
+        U = workloads.random_iterate(nt, nx, workloads.sin4(nx), 1)
+        it, rel = mgrit.solve(lev, U)
+        assert abs(it - v) <= 1, (key, it, v)
