@@ -1,0 +1,228 @@
+/*
+ * mgrit.h -- C ABI of the GB300 MGRIT/Parareal library for periodic linear
+ * advection with least-squares optimised coarse-grid operators.
+ *
+ * Method: De Sterck, Falgout, Friedhoff, Krzysik, MacLachlan, "Optimizing
+ * multigrid reduction-in-time (MGRIT) and Parareal coarse-grid operators for
+ * linear advection", Numer. Linear Algebra Appl. (2021).
+ *
+ *   PDE        u_t + alpha u_x = 0 on periodic [-1, 1)            (Eq. 1)
+ *   space      nx points x_i = -1 + i dx, dx = 2/nx; U_p upwind    (Section 2.1)
+ *   time       nt steps of ERKp or SDIRKp, u^{n+1} = Phi u^n      (Eq. 3, App. A)
+ *   CFL        c = alpha dt / dx                                  (Eq. 3')
+ *   solver     FCF-relaxation, C-point residual, injection, coarse
+ *              system e_j = Psi e_{j-1} + r_j                      (Section 2.2, Eq. 5)
+ *   Psi        sparse circulant fitted by weighted least squares   (Eq. 6, Section 4)
+ *
+ * Conventions for every entry point
+ *   - Plain C types only.  Arrays are row-major doubles with x contiguous:
+ *     time level n of a solution occupies [n*nx, (n+1)*nx).
+ *   - Pointers marked "host or device" may point to either; the library
+ *     detects which with cudaPointerGetAttributes and copies accordingly.
+ *   - Caller buffers stay owned by the caller and are only read/written for
+ *     the duration of the call.  Library objects (handles, servers) are owned
+ *     by the library and released with the matching destroy call.
+ *   - No entry point aborts or throws.  Each returns an mgrit_status; on an
+ *     error, mgrit_last_error() returns a message for the calling thread.
+ *   - Every call that touches the GPU runs on the CUDA stream given at
+ *     creation (NULL = the legacy default stream) and returns after that
+ *     stream has finished the call's work.
+ */
+#ifndef MGRIT_GB300_H
+#define MGRIT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MGRIT_ABI_VERSION 1
+#define MGRIT_MAX_LEVELS 8
+#define MGRIT_MAX_HISTORY 128
+#define MGRIT_MAX_TAPS 256
+
+typedef enum mgrit_status {
+  MGRIT_OK = 0,
+  MGRIT_PENDING = 1,              /* mgrit_poll: request not finished yet          */
+  MGRIT_ERR_INVALID = -1,         /* bad argument or unsupported combination       */
+  MGRIT_ERR_UNSTABLE = -2,        /* ERK CFL number above the limit (Table 1)      */
+  MGRIT_ERR_PSI_ILLCOND = -3,     /* fit rejected: |Im psi| > 1e-8 (Section 4.1)   */
+  MGRIT_ERR_NOT_CONVERGED = -4,   /* max_iter reached above tol                    */
+  MGRIT_ERR_DIVERGED = -5,        /* residual not finite or grew by > 1e6          */
+  MGRIT_ERR_OVER_BUDGET = -6,     /* server: request larger than the HBM budget    */
+  MGRIT_ERR_OOM = -7,             /* device allocation failed                      */
+  MGRIT_ERR_TIMEOUT = -8,         /* a bounded device wait ran out                 */
+  MGRIT_ERR_CUDA = -9,            /* CUDA runtime error                            */
+  MGRIT_ERR_UNSUPPORTED = -10,    /* valid request this build does not implement   */
+  MGRIT_ERR_UNKNOWN_TICKET = -11  /* mgrit_poll: ticket never issued or released   */
+} mgrit_status;
+
+enum { MGRIT_ERK = 0, MGRIT_SDIRK = 1 };
+
+/* Arithmetic of the relaxation (Section 2.2 reading, see the library notes):
+ *  FP64   every step in FP64.
+ *  MIXED  the C-point update and its residual rho_j = Phi^m c_{j-1} - c_j in
+ *         FP64; the second F-relaxation, which only acts on the correction
+ *         rho, in FP32; coarse solve and convergence test in FP64.
+ *  MIXED_DF  as MIXED, with the FP64 pass evaluated in float-float (pairs of
+ *         FP32, about 44 significant bits) on the FP32 pipes. */
+enum { MGRIT_PREC_FP64 = 0, MGRIT_PREC_MIXED = 1, MGRIT_PREC_MIXED_DF = 2 };
+
+/* Coarse-operator sparsity rule (Sections 4.2-4.4, 4.6). */
+enum {
+  MGRIT_PSI_AUTO = 0,       /* ERK: widest-mass contiguous window grown until the
+                               fit is acceptable and Eq. 4's bound <= psi_rho;
+                               SDIRK: threshold with the paper's eta_tol(p, m)  */
+  MGRIT_PSI_HALFWIDTH = 1,  /* 2h+1 offsets centred on argmax |phi~^m_i|      */
+  MGRIT_PSI_THRESHOLD = 2,  /* |phi~^m_i| >= psi_eta * max |phi~^m|            */
+  MGRIT_PSI_USER = 3,       /* caller supplies offsets and coefficients        */
+  MGRIT_PSI_IDEAL = 4       /* Psi = Phi^m exactly (ERK, two levels)           */
+};
+
+enum { MGRIT_OUT_FINAL = 0, MGRIT_OUT_CPOINTS = 1, MGRIT_OUT_FULL = 2 };
+
+typedef struct mgrit_problem {
+  int32_t nx;            /* spatial points (periodic), >= 8                       */
+  int32_t nt;            /* time steps; divisible by m^(levels-1)                  */
+  int32_t family;        /* MGRIT_ERK or MGRIT_SDIRK                               */
+  int32_t rk_order;      /* ERK 1..5, SDIRK 1..4 (Appendix A)                      */
+  int32_t upwind_order;  /* U1..U5 (Section 2.1)                                   */
+  int32_t reserved;
+  double cfl;            /* c = alpha dt / dx (> 0)                                */
+} mgrit_problem;
+
+typedef struct mgrit_opts {
+  int32_t m;             /* coarsening factor >= 2                                 */
+  int32_t levels;        /* 2 = two-level (Parareal-like), up to MGRIT_MAX_LEVELS  */
+  int32_t max_iter;      /* cap on coarse corrections                              */
+  int32_t precision;     /* MGRIT_PREC_*                                           */
+  int32_t psi_rule;      /* MGRIT_PSI_*                                            */
+  int32_t psi_halfwidth; /* for MGRIT_PSI_HALFWIDTH                                */
+  int32_t output;        /* MGRIT_OUT_*                                            */
+  int32_t min_coarse;    /* smallest admissible number of coarsest-level steps     */
+  double tol;            /* stop when ||r|| <= tol ||r^(0)|| (Section 2.2)         */
+  double psi_eta;        /* threshold eta_tol; <= 0 = paper's table (Section 4.6)  */
+  double psi_rho;        /* bound target of MGRIT_PSI_AUTO (default 0.15)          */
+  /* MGRIT_PSI_USER: coarse level l = 2..levels has psi_user_nnz[l-2] taps; the
+   * offsets (diagonal index i: (Psi v)_r = sum_i psi_i v_{r+i}) and
+   * coefficients of all levels are concatenated in level order. */
+  const int32_t* psi_user_nnz;
+  const int32_t* psi_user_offsets;
+  const double* psi_user_coeffs;
+} mgrit_opts;
+
+typedef struct mgrit_result {
+  int32_t iterations;    /* coarse-grid corrections applied before the test passed */
+  int32_t n_levels;
+  int32_t converged;     /* 1 if rel_residual <= tol                               */
+  int32_t n_history;     /* entries of history[] used                              */
+  double rel_residual;   /* ||r|| / ||r^(0)|| after the final FCF-relaxation       */
+  double r0_norm;        /* ||r^(0)||, zero initial iterate: ||Phi u0||            */
+  double setup_s;        /* host setup of this handle (Psi fit, allocation)         */
+  double solve_s;        /* wall time of the solve call                             */
+  double dof_per_s;      /* nx * nt / solve_s                                       */
+  double op_complexity;  /* Eq. 5 (ERK; 0 for SDIRK, whose Phi is dense)            */
+  double history[MGRIT_MAX_HISTORY]; /* relative residual after each FCF            */
+} mgrit_result;
+
+typedef struct mgrit_handle mgrit_handle;
+typedef struct mgrit_server mgrit_server;
+
+/* Fill *o with the defaults: m 8, levels 2, max_iter 100, FP64, PSI_AUTO,
+ * halfwidth 3, OUT_CPOINTS, min_coarse 2, tol 1e-10, eta <= 0, rho 0.15. */
+void mgrit_opts_default(mgrit_opts* o);
+
+/* Optional device allocator used for all later allocations (NULL, NULL
+ * restores cudaMallocAsync/cudaFreeAsync on the handle's stream).  The
+ * callbacks receive the byte count / pointer, the CUDA stream and ctx. */
+typedef void* (*mgrit_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*mgrit_free_fn)(void* ptr, void* stream, void* ctx);
+void mgrit_set_allocator(mgrit_alloc_fn alloc, mgrit_free_fn release, void* ctx);
+
+/* ---------------------------------------------------------------- host only */
+
+/* Taps of the fine propagator Phi as one circulant stencil (Corollary 1):
+ * (Phi v)_r = sum_k coeffs[k] v_{r + offsets[k]}.  ERK only (SDIRK's Phi is
+ * dense).  cap = capacity of the arrays.  No GPU is touched. */
+mgrit_status mgrit_phi_taps(const mgrit_problem* prob, int32_t cap, int32_t* ntaps,
+                            int32_t* offsets, double* coeffs);
+
+/* Coarse operators Psi_2..Psi_L that mgrit_setup would build (Eq. 6 on the
+ * rule's pattern, recursively per level, Section 4.4).  nnz[levels-1];
+ * offsets/coeffs concatenated (capacity cap); diag[3*(levels-1)] receives per
+ * level {max |Im psi| of the complex fit, max_k Eq. 4 bound, max_k |mu_k|}.
+ * No GPU is touched. */
+mgrit_status mgrit_psi_plan(const mgrit_problem* prob, const mgrit_opts* opts, int32_t cap,
+                            int32_t* nnz, int32_t* offsets, double* coeffs, double* diag);
+
+/* ------------------------------------------------------------ single solves */
+
+/* Validate, fit Psi on the host (FP64), allocate device state, and upload the
+ * stencils.  stream: a cudaStream_t (NULL = default stream). */
+mgrit_status mgrit_setup(const mgrit_problem* prob, const mgrit_opts* opts, void* stream,
+                         mgrit_handle** out);
+
+/* Solve from u0 (nx values, host or device) with a zero initial iterate at
+ * t > 0.  out (host or device) receives, per opts.output: FINAL the nx
+ * values at t = T; CPOINTS (nt/m + 1) * nx C-point values; FULL (nt + 1) * nx
+ * values (F-points recomputed by a final F-relaxation, ideal interpolation).
+ * out may be NULL.  res may be NULL. */
+mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* out, mgrit_result* res);
+
+/* Plain sequential time stepping u^{n+1} = Phi u^n on the GPU (FP64), the
+ * baseline of Section 5; out as for mgrit_solve.  seconds may be NULL. */
+mgrit_status mgrit_sequential(mgrit_handle* h, const double* u0, double* out, double* seconds);
+
+/* Apply Phi_level^k to `count` vectors: in and out are count * nx doubles
+ * (device).  level 1 = fine Phi, level l >= 2 = Psi_l.  Used to check single
+ * fine steps against the definition. */
+mgrit_status mgrit_propagate(mgrit_handle* h, int32_t level, int32_t k, int32_t count,
+                             const double* in, double* out);
+
+/* Copy back the coarse operator of level l (2..levels) as built on the
+ * handle: nnz, offsets, coeffs (capacity cap). */
+mgrit_status mgrit_psi_info(mgrit_handle* h, int32_t level, int32_t cap, int32_t* nnz,
+                            int32_t* offsets, double* coeffs);
+
+/* Bytes of device memory this handle holds. */
+size_t mgrit_device_bytes(const mgrit_handle* h);
+
+void mgrit_destroy(mgrit_handle* h);
+
+/* --------------------------------------------------------------- serving */
+
+typedef struct mgrit_server_opts {
+  double hbm_budget_bytes;   /* admission budget for resident solve state       */
+  int32_t max_active;        /* most solves advanced together (0 = 4096)         */
+  int32_t reserved;
+} mgrit_server_opts;
+
+/* Continuous-batching server: a host thread admits submitted solves while
+ * their state fits in the budget, advances every admitted solve by one MGRIT
+ * cycle per batched launch, retires converged solves and frees their slots. */
+mgrit_status mgrit_server_create(const mgrit_server_opts* sopts, void* stream, mgrit_server** out);
+
+/* Queue a solve (u0 host or device, copied before return).  *ticket
+ * identifies it.  MGRIT_ERR_OVER_BUDGET if it could never fit the budget. */
+mgrit_status mgrit_submit(mgrit_server* s, const mgrit_problem* prob, const mgrit_opts* opts,
+                          const double* u0, uint64_t* ticket);
+
+/* MGRIT_PENDING until the solve has finished; then copies the output (layout
+ * as mgrit_solve, host or device; may be NULL) and the result, releases the
+ * request, and returns its final status.  A released ticket gives
+ * MGRIT_ERR_UNKNOWN_TICKET. */
+mgrit_status mgrit_poll(mgrit_server* s, uint64_t ticket, double* out, mgrit_result* res);
+
+void mgrit_server_destroy(mgrit_server* s);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* mgrit_last_error(void);
+
+int32_t mgrit_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGRIT_GB300_H */

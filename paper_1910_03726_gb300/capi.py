@@ -1,0 +1,302 @@
+"""Thin ctypes binding of ``include/mgrit.h``: argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Arrays may
+be numpy arrays (host) or torch tensors (host or CUDA); the library detects
+device pointers itself.  PyTorch supplies the CUDA stream and, through
+``use_torch_allocator``, the device memory of the library's state.
+
+There is no fallback: if ``libmgrit_gb300.so`` is missing the import fails
+and says how to build it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmgrit_gb300.so")
+
+MGRIT_OK, MGRIT_PENDING = 0, 1
+STATUS = {0: "OK", 1: "PENDING", -1: "ERR_INVALID", -2: "ERR_UNSTABLE", -3: "ERR_PSI_ILLCOND",
+          -4: "ERR_NOT_CONVERGED", -5: "ERR_DIVERGED", -6: "ERR_OVER_BUDGET", -7: "ERR_OOM",
+          -8: "ERR_TIMEOUT", -9: "ERR_CUDA", -10: "ERR_UNSUPPORTED", -11: "ERR_UNKNOWN_TICKET"}
+ERK, SDIRK = 0, 1
+PREC_FP64, PREC_MIXED, PREC_MIXED_DF = 0, 1, 2
+PSI_AUTO, PSI_HALFWIDTH, PSI_THRESHOLD, PSI_USER, PSI_IDEAL = 0, 1, 2, 3, 4
+OUT_FINAL, OUT_CPOINTS, OUT_FULL = 0, 1, 2
+MAX_HISTORY = 128
+MAX_LEVELS = 8
+
+EXPORTED = ["mgrit_opts_default", "mgrit_set_allocator", "mgrit_phi_taps", "mgrit_psi_plan",
+            "mgrit_setup", "mgrit_solve", "mgrit_sequential", "mgrit_propagate", "mgrit_psi_info",
+            "mgrit_device_bytes", "mgrit_destroy", "mgrit_server_create", "mgrit_submit",
+            "mgrit_poll", "mgrit_server_destroy", "mgrit_last_error", "mgrit_abi_version"]
+
+
+class MgritProblem(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("nt", C.c_int32), ("family", C.c_int32), ("rk_order", C.c_int32),
+                ("upwind_order", C.c_int32), ("reserved", C.c_int32), ("cfl", C.c_double)]
+
+
+class MgritOpts(C.Structure):
+    _fields_ = [("m", C.c_int32), ("levels", C.c_int32), ("max_iter", C.c_int32), ("precision", C.c_int32),
+                ("psi_rule", C.c_int32), ("psi_halfwidth", C.c_int32), ("output", C.c_int32),
+                ("min_coarse", C.c_int32), ("tol", C.c_double), ("psi_eta", C.c_double),
+                ("psi_rho", C.c_double), ("psi_user_nnz", C.POINTER(C.c_int32)),
+                ("psi_user_offsets", C.POINTER(C.c_int32)), ("psi_user_coeffs", C.POINTER(C.c_double))]
+
+
+class MgritResult(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("n_levels", C.c_int32), ("converged", C.c_int32),
+                ("n_history", C.c_int32), ("rel_residual", C.c_double), ("r0_norm", C.c_double),
+                ("setup_s", C.c_double), ("solve_s", C.c_double), ("dof_per_s", C.c_double),
+                ("op_complexity", C.c_double), ("history", C.c_double * MAX_HISTORY)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "history"}
+        d["history"] = list(self.history[: self.n_history])
+        return d
+
+
+class MgritServerOpts(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_double), ("max_active", C.c_int32), ("reserved", C.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing; build it with `python -m paper_1910_03726_gb300.build` "
+                          "(needs nvcc); there is no CPU fallback")
+    return C.CDLL(LIB_PATH)
+
+
+_lib = _load()
+_vp, _i32, _f64 = C.c_void_p, C.c_int32, C.c_double
+_P = C.POINTER
+
+
+def _sig(name, res, *args):
+    f = getattr(_lib, name, None)
+    if f is not None:
+        f.restype = res
+        f.argtypes = list(args)
+    return f
+
+
+_sig("mgrit_opts_default", None, _P(MgritOpts))
+ALLOC_FN = C.CFUNCTYPE(_vp, C.c_size_t, _vp, _vp)
+FREE_FN = C.CFUNCTYPE(None, _vp, _vp, _vp)
+_sig("mgrit_set_allocator", None, ALLOC_FN, FREE_FN, _vp)
+_sig("mgrit_phi_taps", _i32, _P(MgritProblem), _i32, _P(_i32), _P(_i32), _P(_f64))
+_sig("mgrit_psi_plan", _i32, _P(MgritProblem), _P(MgritOpts), _i32, _P(_i32), _P(_i32), _P(_f64), _P(_f64))
+_sig("mgrit_setup", _i32, _P(MgritProblem), _P(MgritOpts), _vp, _P(_vp))
+_sig("mgrit_solve", _i32, _vp, _vp, _vp, _P(MgritResult))
+_sig("mgrit_sequential", _i32, _vp, _vp, _vp, _P(_f64))
+_sig("mgrit_propagate", _i32, _vp, _i32, _i32, _i32, _vp, _vp)
+_sig("mgrit_psi_info", _i32, _vp, _i32, _i32, _P(_i32), _P(_i32), _P(_f64))
+_sig("mgrit_device_bytes", C.c_size_t, _vp)
+_sig("mgrit_destroy", None, _vp)
+_sig("mgrit_server_create", _i32, _P(MgritServerOpts), _vp, _P(_vp))
+_sig("mgrit_submit", _i32, _vp, _P(MgritProblem), _P(MgritOpts), _vp, _P(C.c_uint64))
+_sig("mgrit_poll", _i32, _vp, C.c_uint64, _vp, _P(MgritResult))
+_sig("mgrit_server_destroy", None, _vp)
+_sig("mgrit_last_error", C.c_char_p)
+_sig("mgrit_abi_version", _i32)
+
+
+class MgritError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status, allow=(MGRIT_OK,)):
+    if status not in allow:
+        raise MgritError(status, mgrit_last_error())
+    return status
+
+
+def _ptr(x):
+    """Raw pointer of a numpy array or torch tensor (contiguous float64)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise TypeError("arrays must be C-contiguous float64")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        return x.data_ptr()
+    raise TypeError(type(x))
+
+
+# ------------------------------------------------------------------ helpers
+
+def problem(nx, nt, family="ERK", rk_order=1, upwind_order=None, cfl=0.85):
+    fam = ERK if family in ("ERK", ERK) else SDIRK
+    return MgritProblem(nx, nt, fam, rk_order, upwind_order or rk_order, 0, float(cfl))
+
+
+def mgrit_opts_default(**overrides):
+    o = MgritOpts()
+    _lib.mgrit_opts_default(C.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def user_psi(opts, ops):
+    """Attach caller-supplied coarse operators (list of (offsets, coeffs)) to
+    opts; returns the ctypes arrays, which must stay alive with opts."""
+    nnz = (C.c_int32 * len(ops))(*[len(o[0]) for o in ops])
+    offs = [int(i) for o in ops for i in o[0]]
+    cfs = [float(c) for o in ops for c in o[1]]
+    off_arr = (C.c_int32 * max(1, len(offs)))(*offs)
+    cf_arr = (C.c_double * max(1, len(cfs)))(*cfs)
+    opts.psi_rule = PSI_USER
+    opts.psi_user_nnz = C.cast(nnz, _P(C.c_int32))
+    opts.psi_user_offsets = C.cast(off_arr, _P(C.c_int32))
+    opts.psi_user_coeffs = C.cast(cf_arr, _P(C.c_double))
+    return (nnz, off_arr, cf_arr)
+
+
+# ----------------------------------------------------------- entry points
+
+def mgrit_last_error():
+    s = _lib.mgrit_last_error()
+    return s.decode() if s else ""
+
+
+def mgrit_abi_version():
+    return int(_lib.mgrit_abi_version())
+
+
+def mgrit_phi_taps(prob, cap=1024):
+    n = C.c_int32()
+    offs = (C.c_int32 * cap)()
+    cfs = (C.c_double * cap)()
+    _check(_lib.mgrit_phi_taps(C.byref(prob), cap, C.byref(n), offs, cfs))
+    return list(offs[: n.value]), list(cfs[: n.value])
+
+
+def mgrit_psi_plan(prob, opts, cap=1 << 16):
+    L = opts.levels - 1
+    nnz = (C.c_int32 * L)()
+    offs = (C.c_int32 * cap)()
+    cfs = (C.c_double * cap)()
+    diag = (C.c_double * (3 * L))()
+    st = _lib.mgrit_psi_plan(C.byref(prob), C.byref(opts), cap, nnz, offs, cfs, diag)
+    _check(st)
+    out, pos = [], 0
+    for l in range(L):
+        n = nnz[l]
+        out.append((list(offs[pos:pos + n]), list(cfs[pos:pos + n])))
+        pos += n
+    return out, [tuple(diag[3 * l:3 * l + 3]) for l in range(L)]
+
+
+def _stream_ptr(stream):
+    if stream is not None:
+        return int(stream)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # noqa: BLE001
+        pass
+    return None
+
+
+def mgrit_setup(prob, opts, stream=None):
+    h = C.c_void_p()
+    _check(_lib.mgrit_setup(C.byref(prob), C.byref(opts), _stream_ptr(stream), C.byref(h)))
+    return h
+
+
+def mgrit_solve(h, u0, out=None, allow_not_converged=False):
+    r = MgritResult()
+    allow = (MGRIT_OK, -4) if allow_not_converged else (MGRIT_OK,)
+    st = _check(_lib.mgrit_solve(h, _ptr(u0), _ptr(out), C.byref(r)), allow)
+    return r, st
+
+
+def mgrit_sequential(h, u0, out=None):
+    t = C.c_double()
+    _check(_lib.mgrit_sequential(h, _ptr(u0), _ptr(out), C.byref(t)))
+    return t.value
+
+
+def mgrit_propagate(h, level, k, count, inp, out):
+    _check(_lib.mgrit_propagate(h, level, k, count, _ptr(inp), _ptr(out)))
+
+
+def mgrit_psi_info(h, level, cap=4096):
+    n = C.c_int32()
+    offs = (C.c_int32 * cap)()
+    cfs = (C.c_double * cap)()
+    _check(_lib.mgrit_psi_info(h, level, cap, C.byref(n), offs, cfs))
+    return list(offs[: n.value]), list(cfs[: n.value])
+
+
+def mgrit_device_bytes(h):
+    return int(_lib.mgrit_device_bytes(h))
+
+
+def mgrit_destroy(h):
+    _lib.mgrit_destroy(h)
+
+
+def mgrit_server_create(budget_bytes, max_active=0, stream=None):
+    so = MgritServerOpts(float(budget_bytes), int(max_active), 0)
+    s = C.c_void_p()
+    _check(_lib.mgrit_server_create(C.byref(so), _stream_ptr(stream), C.byref(s)))
+    return s
+
+
+def mgrit_submit(s, prob, opts, u0):
+    t = C.c_uint64()
+    _check(_lib.mgrit_submit(s, C.byref(prob), C.byref(opts), _ptr(u0), C.byref(t)))
+    return t.value
+
+
+def mgrit_poll(s, ticket, out=None):
+    """Returns (status, result); status PENDING (1) while running."""
+    r = MgritResult()
+    st = _lib.mgrit_poll(s, C.c_uint64(ticket), _ptr(out), C.byref(r))
+    return st, r
+
+
+def mgrit_server_destroy(s):
+    _lib.mgrit_server_destroy(s)
+
+
+# ------------------------------------------------------------ torch memory
+
+_KEEP = []
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching
+    allocator on the caller's stream."""
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0)))
+        except Exception:  # noqa: BLE001  (the C side reports OOM)
+            return None
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+    _KEEP[:] = [a, f]
+    _lib.mgrit_set_allocator(a, f, None)
+
+
+def use_default_allocator():
+    _lib.mgrit_set_allocator(ALLOC_FN(), FREE_FN(), None)
+    _KEEP[:] = []

@@ -1,0 +1,69 @@
+// Kernel argument blocks shared by the host driver and the CUDA kernels.
+// Internal interface (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace mg {
+
+constexpr int kMaxDevTaps = 256;
+
+// A circulant stencil passed by value in the kernel parameter space:
+// (T v)_r = sum_t c[t] v_{r + off[t]}.  lo <= 0 <= hi bound the offsets.
+struct DevTaps {
+  int n, lo, hi, pad;
+  int off[kMaxDevTaps];
+  double c64[kMaxDevTaps];
+  float c32[kMaxDevTaps];
+};
+
+// FCF-relaxation of one level with the fused C-point residual.
+// Interval j = 1..N starts at C-point j-1.  For every j the kernel computes
+//   v_j   = m steps of u <- T u + g from u_old[C(j-1)]   (F- then C-relaxation)
+//   rho_j = v_j - u_old[C(j)];  c_new[j] = v_j
+//   r_{j+1} = T^m rho_j  (j < N)  = residual at C-point j+1 after the second
+//   F-relaxation, and partial[j] = ||r_{j+1}||^2.
+struct FcfArgs {
+  const double* u_old;     // C-point j at u_old + j*cstride (unused if zero_old)
+  long long cstride;
+  double* c_new;           // c_new + j*nx
+  const double* g;         // right-hand side, point n at g + n*nx (nullptr: none)
+  double* r;               // r + j*nx, j = 2..N written
+  double* partial;         // partial[j], j = 1..N-1 (nullptr: skip)
+  int nx, m, N, zero_old;  // zero_old: u_old is identically zero
+};
+
+// Sequential march u_n = T u_{n-1} + g_n, n = 1..P-1, on one thread-block
+// cluster whose CTAs split x; halos move through distributed shared memory.
+struct MarchArgs {
+  const double* init;      // u_0 (nullptr: zero)
+  const double* g;         // point n at g + n*nx (nullptr: none)
+  double* u_out;           // store u_n at u_out + (n/store_every)*nx when n % store_every == 0
+  int store_every;
+  double* c_add;           // c_add + n*nx += u_n for n >= 1 (nullptr: none)
+  int nx, P;
+};
+
+// Correction and F-relaxation (ideal interpolation) of one level:
+// u[(j-1)m] = c_new[j-1] + e[j-1], then m-1 steps with g; interval N also
+// writes u[Nm] = c_new[N] + e[N].  e == nullptr reads as zero (final
+// interpolation of the fine level's F-points from its C-points).
+struct CorrectArgs {
+  const double* c_new;     // c_new + j*nx
+  const double* e;         // e + j*nx (next level's solution)
+  const double* g;         // point n at g + n*nx (nullptr: none)
+  double* u;               // all points of the level, point n at u + n*nx
+  int nx, m, N;
+};
+
+cudaError_t launch_fcf(const FcfArgs& a, const DevTaps& t, int precision, int threads,
+                       cudaStream_t s);
+cudaError_t launch_march(const MarchArgs& a, const DevTaps& t, int cluster, int threads,
+                         cudaStream_t s);
+cudaError_t launch_correct(const CorrectArgs& a, const DevTaps& t, int threads, cudaStream_t s);
+cudaError_t launch_norm(const double* partial, int n, double* out, cudaStream_t s);
+cudaError_t launch_add(double* c, const double* e, long long count, cudaStream_t s);
+cudaError_t launch_propagate(const double* in, double* out, int count, int nx, int k,
+                             const DevTaps& t, double* partial, int threads, cudaStream_t s);
+int march_max_cluster();
+
+}  // namespace mg

@@ -1,0 +1,670 @@
+// C ABI of the GB300 MGRIT library: validation, device state, the cycle
+// loop (FCF-relaxation, residual test, coarse solve or V-cycle, correction),
+// sequential stepping, and the host-only planning entry points.
+// Section 2.2 defines the cycle; Eq. 5 the coarse system; Section 4 the Psi fit.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mgrit.h"
+#include "device.h"
+#include "setup.h"
+
+using namespace mg;
+
+// --------------------------------------------------------------- error text
+
+static thread_local std::string g_err;
+
+static mgrit_status fail(mgrit_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (expr);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(e_ == cudaErrorMemoryAllocation ? MGRIT_ERR_OOM : MGRIT_ERR_CUDA, \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));              \
+  } while (0)
+
+// ---------------------------------------------------------------- allocator
+
+static mgrit_alloc_fn g_alloc = nullptr;
+static mgrit_free_fn g_free = nullptr;
+static void* g_alloc_ctx = nullptr;
+
+extern "C" void mgrit_set_allocator(mgrit_alloc_fn a, mgrit_free_fn f, void* ctx) {
+  g_alloc = a;
+  g_free = f;
+  g_alloc_ctx = ctx;
+}
+
+struct DevBuf {
+  double* p = nullptr;
+  size_t n = 0;
+  mgrit_free_fn freefn = nullptr;
+  void* ctx = nullptr;
+};
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// ------------------------------------------------------------------- handle
+
+struct mgrit_handle {
+  mgrit_problem prob;
+  mgrit_opts opts;
+  cudaStream_t stream = nullptr;
+  int nx = 0, nt = 0, m = 0, L = 0;
+  std::vector<int> Nl;            // Nl[l] intervals of level l (l = 1..L-1)
+  Taps phi;                       // fine propagator (ERK, collapsed)
+  std::vector<CoarseOp> ops;      // ops[l-2] = Psi_l, l = 2..L
+  DevTaps dphi;
+  std::vector<DevTaps> dpsi;      // dpsi[l-2]
+  std::vector<DevBuf> bufs;       // everything allocated, for release
+  double* c[2] = {nullptr, nullptr};
+  std::vector<double*> r, u, cnew;  // indexed by level (size L+1)
+  double* partial = nullptr;
+  double* scratch = nullptr;      // 2*nx + 1 doubles
+  double* norm_host = nullptr;    // pinned
+  int fcf_threads = 512, march_cluster = 1, march_threads = 256;
+  double setup_s = 0.0, op_complexity = 0.0;
+  size_t bytes = 0;
+};
+
+static mgrit_status dalloc(mgrit_handle* h, size_t count, double** out) {
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(double);
+  void* p = nullptr;
+  DevBuf b;
+  if (g_alloc) {
+    p = g_alloc(bytes, (void*)h->stream, g_alloc_ctx);
+    if (!p) return fail(MGRIT_ERR_OOM, "allocator callback returned NULL");
+    b.freefn = g_free;
+    b.ctx = g_alloc_ctx;
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, bytes, h->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(e == cudaErrorMemoryAllocation ? MGRIT_ERR_OOM : MGRIT_ERR_CUDA,
+                  std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+    }
+  }
+  b.p = (double*)p;
+  b.n = count;
+  h->bufs.push_back(b);
+  h->bytes += bytes;
+  *out = (double*)p;
+  return MGRIT_OK;
+}
+
+static void release(mgrit_handle* h) {
+  for (auto& b : h->bufs) {
+    if (!b.p) continue;
+    if (b.freefn) b.freefn(b.p, (void*)h->stream, b.ctx);
+    else cudaFreeAsync(b.p, h->stream);
+  }
+  h->bufs.clear();
+  if (h->norm_host) cudaFreeHost(h->norm_host);
+  h->norm_host = nullptr;
+  cudaStreamSynchronize(h->stream);
+}
+
+static DevTaps to_dev(const Taps& t) {
+  DevTaps d;
+  std::memset(&d, 0, sizeof(d));
+  d.n = t.size();
+  d.lo = t.lo();
+  d.hi = t.hi();
+  for (int k = 0; k < d.n; ++k) {
+    d.off[k] = t.off[k];
+    d.c64[k] = t.coef[k];
+    d.c32[k] = (float)t.coef[k];
+  }
+  return d;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static cudaMemcpyKind kind_to_dev(const void* src) {
+  return is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+static cudaMemcpyKind kind_from_dev(const void* dst) {
+  return is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+// ------------------------------------------------------------- validation
+
+extern "C" void mgrit_opts_default(mgrit_opts* o) {
+  std::memset(o, 0, sizeof(*o));
+  o->m = 8;
+  o->levels = 2;
+  o->max_iter = 100;
+  o->precision = MGRIT_PREC_FP64;
+  o->psi_rule = MGRIT_PSI_AUTO;
+  o->psi_halfwidth = 3;
+  o->output = MGRIT_OUT_CPOINTS;
+  o->min_coarse = 2;
+  o->tol = 1e-10;
+  o->psi_eta = 0.0;
+  o->psi_rho = 0.15;
+}
+
+extern "C" int32_t mgrit_abi_version(void) { return MGRIT_ABI_VERSION; }
+
+extern "C" const char* mgrit_last_error(void) { return g_err.c_str(); }
+
+static mgrit_status validate_problem(const mgrit_problem* p) {
+  if (!p) return fail(MGRIT_ERR_INVALID, "problem is NULL");
+  if (p->nx < 8) return fail(MGRIT_ERR_INVALID, "nx must be >= 8");
+  if (p->nt < 1) return fail(MGRIT_ERR_INVALID, "nt must be >= 1");
+  if (p->family != MGRIT_ERK && p->family != MGRIT_SDIRK) return fail(MGRIT_ERR_INVALID, "family must be ERK or SDIRK");
+  if (p->family == MGRIT_ERK && (p->rk_order < 1 || p->rk_order > 5))
+    return fail(MGRIT_ERR_INVALID, "ERK order must be 1..5");
+  if (p->family == MGRIT_SDIRK && (p->rk_order < 1 || p->rk_order > 4))
+    return fail(MGRIT_ERR_INVALID, "SDIRK order must be 1..4");
+  if (p->upwind_order < 1 || p->upwind_order > 5) return fail(MGRIT_ERR_INVALID, "upwind order must be 1..5");
+  if (!(p->cfl > 0.0) || !std::isfinite(p->cfl)) return fail(MGRIT_ERR_INVALID, "cfl must be > 0");
+  if (p->family == MGRIT_ERK && p->rk_order == p->upwind_order) {
+    // Table 1 limits as printed (last digit rounded up)
+    static const double cmax[6] = {0, 1.0, 0.5, 1.62590, 1.04450, 1.96584};
+    if (p->cfl > cmax[p->rk_order])
+      return fail(MGRIT_ERR_UNSTABLE, "ERK CFL number above the stability limit of Table 1");
+  } else if (p->family == MGRIT_ERK) {
+    if (p->cfl > erk_cfl_limit(p->rk_order, p->upwind_order))
+      return fail(MGRIT_ERR_UNSTABLE, "ERK CFL number above the stability limit");
+  }
+  return MGRIT_OK;
+}
+
+static mgrit_status validate_opts(const mgrit_problem* p, const mgrit_opts* o) {
+  if (!o) return fail(MGRIT_ERR_INVALID, "opts is NULL");
+  if (o->m < 2) return fail(MGRIT_ERR_INVALID, "m must be >= 2");
+  if (o->levels < 2 || o->levels > MGRIT_MAX_LEVELS) return fail(MGRIT_ERR_INVALID, "levels must be 2..8");
+  long long div = 1;
+  for (int l = 1; l < o->levels; ++l) {
+    div *= o->m;
+    if (p->nt % div != 0) return fail(MGRIT_ERR_INVALID, "nt must be divisible by m^(levels-1)");
+  }
+  if (p->nt / div < std::max(1, o->min_coarse))
+    return fail(MGRIT_ERR_INVALID, "coarsest level has fewer than min_coarse steps");
+  if (!(o->tol > 0.0)) return fail(MGRIT_ERR_INVALID, "tol must be > 0");
+  if (o->max_iter < 0) return fail(MGRIT_ERR_INVALID, "max_iter must be >= 0");
+  if (o->precision < 0 || o->precision > 2) return fail(MGRIT_ERR_INVALID, "unknown precision");
+  if (o->output < 0 || o->output > 2) return fail(MGRIT_ERR_INVALID, "unknown output");
+  if (o->psi_rule == MGRIT_PSI_IDEAL && (p->family != MGRIT_ERK || o->levels != 2))
+    return fail(MGRIT_ERR_INVALID, "PSI_IDEAL needs ERK and two levels");
+  if (o->psi_rule == MGRIT_PSI_HALFWIDTH && o->psi_halfwidth < 0)
+    return fail(MGRIT_ERR_INVALID, "psi_halfwidth must be >= 0");
+  return MGRIT_OK;
+}
+
+static PlanRequest make_request(const mgrit_problem* p, const mgrit_opts* o) {
+  PlanRequest rq;
+  rq.nx = p->nx; rq.nt = p->nt; rq.family = p->family; rq.rk_order = p->rk_order;
+  rq.upwind_order = p->upwind_order; rq.cfl = p->cfl;
+  rq.m = o->m; rq.levels = o->levels; rq.rule = o->psi_rule; rq.halfwidth = o->psi_halfwidth;
+  rq.eta = o->psi_eta; rq.rho = o->psi_rho > 0.0 ? o->psi_rho : 0.15;
+  rq.user_nnz = o->psi_user_nnz; rq.user_off = o->psi_user_offsets; rq.user_coef = o->psi_user_coeffs;
+  return rq;
+}
+
+static mgrit_status plan(const mgrit_problem* p, const mgrit_opts* o, std::vector<CoarseOp>* ops) {
+  std::string err;
+  if (!build_hierarchy(make_request(p, o), ops, &err)) return fail(MGRIT_ERR_INVALID, err);
+  for (size_t l = 0; l < ops->size(); ++l) {
+    if ((*ops)[l].imag > 1e-8)
+      return fail(MGRIT_ERR_PSI_ILLCOND, "least-squares Psi has an imaginary part above 1e-8 (level " +
+                                             std::to_string(l + 2) + ")");
+  }
+  return MGRIT_OK;
+}
+
+// ----------------------------------------------------------- host-only ABI
+
+extern "C" mgrit_status mgrit_phi_taps(const mgrit_problem* prob, int32_t cap, int32_t* ntaps, int32_t* offsets,
+                                       double* coeffs) {
+  mgrit_status st = validate_problem(prob);
+  if (st != MGRIT_OK) return st;
+  if (prob->family != MGRIT_ERK) return fail(MGRIT_ERR_INVALID, "Phi is a single stencil only for ERK");
+  Taps t = erk_phi_taps(prob->rk_order, prob->upwind_order, prob->cfl);
+  if (ntaps) *ntaps = t.size();
+  if (t.size() > cap) return fail(MGRIT_ERR_INVALID, "capacity too small");
+  for (int k = 0; k < t.size(); ++k) {
+    if (offsets) offsets[k] = t.off[k];
+    if (coeffs) coeffs[k] = t.coef[k];
+  }
+  return MGRIT_OK;
+}
+
+extern "C" mgrit_status mgrit_psi_plan(const mgrit_problem* prob, const mgrit_opts* opts, int32_t cap, int32_t* nnz,
+                                       int32_t* offsets, double* coeffs, double* diag) {
+  mgrit_status st = validate_problem(prob);
+  if (st == MGRIT_OK) st = validate_opts(prob, opts);
+  if (st != MGRIT_OK) return st;
+  std::vector<CoarseOp> ops;
+  std::string err;
+  if (!build_hierarchy(make_request(prob, opts), &ops, &err)) return fail(MGRIT_ERR_INVALID, err);
+  int pos = 0;
+  for (size_t l = 0; l < ops.size(); ++l) {
+    const Taps& t = ops[l].taps;
+    if (nnz) nnz[l] = t.size();
+    if (diag) {
+      diag[3 * l] = ops[l].imag;
+      diag[3 * l + 1] = ops[l].bound;
+      diag[3 * l + 2] = ops[l].mumax;
+    }
+    if (pos + t.size() > cap) return fail(MGRIT_ERR_INVALID, "capacity too small");
+    for (int k = 0; k < t.size(); ++k) {
+      if (offsets) offsets[pos + k] = t.off[k];
+      if (coeffs) coeffs[pos + k] = t.coef[k];
+    }
+    pos += t.size();
+  }
+  for (size_t l = 0; l < ops.size(); ++l)
+    if (ops[l].imag > 1e-8) return fail(MGRIT_ERR_PSI_ILLCOND, "imaginary part above 1e-8");
+  return MGRIT_OK;
+}
+
+// ------------------------------------------------------------------- setup
+
+static int pick_cluster(int nx, const Taps& t) {
+  int reach = std::max(-t.lo(), t.hi());
+  for (int cs = march_max_cluster(); cs > 1; cs >>= 1)
+    if (nx % cs == 0 && nx / cs >= std::max(64, reach)) return cs;
+  return 1;
+}
+
+extern "C" mgrit_status mgrit_setup(const mgrit_problem* prob, const mgrit_opts* opts, void* stream,
+                                    mgrit_handle** out) {
+  if (!out) return fail(MGRIT_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  const double t0 = now_s();
+  mgrit_status st = validate_problem(prob);
+  if (st == MGRIT_OK) st = validate_opts(prob, opts);
+  if (st != MGRIT_OK) return st;
+  if (prob->family == MGRIT_SDIRK) return fail(MGRIT_ERR_UNSUPPORTED, "SDIRK relaxation not built yet");
+  if (opts->precision == MGRIT_PREC_MIXED_DF) return fail(MGRIT_ERR_UNSUPPORTED, "float-float mode not built yet");
+  if (2.0 * prob->nx * sizeof(double) > 227.0 * 1024.0)
+    return fail(MGRIT_ERR_UNSUPPORTED, "nx too large for one shared-memory slab (max 14528)");
+  mgrit_handle* h = new mgrit_handle();
+  h->prob = *prob;
+  h->opts = *opts;
+  h->opts.psi_user_nnz = nullptr;
+  h->opts.psi_user_offsets = nullptr;
+  h->opts.psi_user_coeffs = nullptr;
+  h->stream = (cudaStream_t)stream;
+  h->nx = prob->nx;
+  h->nt = prob->nt;
+  h->m = opts->m;
+  h->L = opts->levels;
+  st = plan(prob, opts, &h->ops);
+  if (st != MGRIT_OK) {
+    delete h;
+    return st;
+  }
+  h->phi = erk_phi_taps(prob->rk_order, prob->upwind_order, prob->cfl);
+  if (h->phi.size() > kMaxDevTaps) {
+    delete h;
+    return fail(MGRIT_ERR_UNSUPPORTED, "fine stencil too wide");
+  }
+  for (auto& op : h->ops)
+    if (op.taps.size() > kMaxDevTaps) {
+      delete h;
+      return fail(MGRIT_ERR_UNSUPPORTED, "coarse stencil wider than 256 taps");
+    }
+  h->dphi = to_dev(h->phi);
+  for (auto& op : h->ops) h->dpsi.push_back(to_dev(op.taps));
+  // operator complexity, Eq. 5 (ERK)
+  {
+    double s = h->phi.size();
+    double f = 1.0;
+    for (auto& op : h->ops) {
+      f /= h->m;
+      s += f * op.taps.size();
+    }
+    h->op_complexity = s / h->phi.size();
+  }
+  const int nx = h->nx, L = h->L, m = h->m;
+  h->Nl.assign(L + 1, 0);
+  h->Nl[1] = h->nt / m;
+  for (int l = 2; l < L; ++l) h->Nl[l] = h->Nl[l - 1] / m;
+  h->r.assign(L + 1, nullptr);
+  h->u.assign(L + 1, nullptr);
+  h->cnew.assign(L + 1, nullptr);
+  const size_t N1 = h->Nl[1];
+  auto A = [&](size_t count, double** p) { return dalloc(h, count, p); };
+  if ((st = A((N1 + 1) * nx, &h->c[0])) != MGRIT_OK || (st = A((N1 + 1) * nx, &h->c[1])) != MGRIT_OK ||
+      (st = A((N1 + 1) * nx, &h->r[1])) != MGRIT_OK || (st = A(N1 + 1, &h->partial)) != MGRIT_OK ||
+      (st = A(2 * (size_t)nx + 8, &h->scratch)) != MGRIT_OK) {
+    release(h);
+    delete h;
+    return st;
+  }
+  cudaMemsetAsync(h->r[1], 0, (N1 + 1) * nx * sizeof(double), h->stream);
+  cudaMemsetAsync(h->partial, 0, (N1 + 1) * sizeof(double), h->stream);
+  for (int l = 2; l <= L; ++l) {
+    const size_t P = (size_t)h->Nl[l - 1] + 1;  // points of level l
+    if (l < L || L > 2) {
+      if ((st = A(P * nx, &h->u[l])) != MGRIT_OK) break;
+      cudaMemsetAsync(h->u[l], 0, P * nx * sizeof(double), h->stream);
+    }
+    if (l < L) {
+      const size_t Nc = (size_t)h->Nl[l] + 1;
+      if ((st = A(Nc * nx, &h->cnew[l])) != MGRIT_OK || (st = A(Nc * nx, &h->r[l])) != MGRIT_OK) break;
+      cudaMemsetAsync(h->cnew[l], 0, Nc * nx * sizeof(double), h->stream);
+      cudaMemsetAsync(h->r[l], 0, Nc * nx * sizeof(double), h->stream);
+    }
+  }
+  if (st != MGRIT_OK) {
+    release(h);
+    delete h;
+    return st;
+  }
+  if (cudaMallocHost(&h->norm_host, 8 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    release(h);
+    delete h;
+    return fail(MGRIT_ERR_OOM, "pinned host buffer");
+  }
+  h->fcf_threads = nx >= 2048 ? 512 : (nx >= 512 ? 256 : 128);
+  const Taps& coarsest = h->ops.back().taps;
+  h->march_cluster = pick_cluster(nx, coarsest);
+  h->march_threads = std::min(256, nx / h->march_cluster);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    release(h);
+    delete h;
+    return fail(MGRIT_ERR_CUDA, cudaGetErrorString(e));
+  }
+  h->setup_s = now_s() - t0;
+  *out = h;
+  return MGRIT_OK;
+}
+
+extern "C" void mgrit_destroy(mgrit_handle* h) {
+  if (!h) return;
+  release(h);
+  delete h;
+}
+
+extern "C" size_t mgrit_device_bytes(const mgrit_handle* h) { return h ? h->bytes : 0; }
+
+extern "C" mgrit_status mgrit_psi_info(mgrit_handle* h, int32_t level, int32_t cap, int32_t* nnz, int32_t* offsets,
+                                       double* coeffs) {
+  if (!h) return fail(MGRIT_ERR_INVALID, "handle is NULL");
+  if (level < 2 || level > h->L) return fail(MGRIT_ERR_INVALID, "level must be 2..levels");
+  const Taps& t = h->ops[level - 2].taps;
+  if (nnz) *nnz = t.size();
+  if (t.size() > cap) return fail(MGRIT_ERR_INVALID, "capacity too small");
+  for (int k = 0; k < t.size(); ++k) {
+    if (offsets) offsets[k] = t.off[k];
+    if (coeffs) coeffs[k] = t.coef[k];
+  }
+  return MGRIT_OK;
+}
+
+// ------------------------------------------------------------------- solve
+
+static mgrit_status launch_ok(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) return fail(MGRIT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return MGRIT_OK;
+}
+
+// Launch a march, shrinking the cluster if the device refuses the size.
+static mgrit_status run_march(mgrit_handle* h, const MarchArgs& a, const DevTaps& t) {
+  for (;;) {
+    int threads = std::min(256, a.nx / h->march_cluster);
+    cudaError_t e = launch_march(a, t, h->march_cluster, threads, h->stream);
+    if (e == cudaSuccess) return MGRIT_OK;
+    cudaGetLastError();
+    if (h->march_cluster == 1) return launch_ok(e, "march_kernel");
+    h->march_cluster >>= 1;
+  }
+}
+
+// ||Phi u0||: residual of the zero initial iterate (only time level 1 is nonzero).
+static mgrit_status initial_residual(mgrit_handle* h, const double* u0dev, double* r0) {
+  mgrit_status st;
+  double* out = h->scratch;
+  double* part = h->scratch + h->nx;
+  if ((st = launch_ok(launch_propagate(u0dev, out, 1, h->nx, 1, h->dphi, part, h->fcf_threads, h->stream),
+                      "propagate")) != MGRIT_OK)
+    return st;
+  CUDA_TRY(cudaMemcpyAsync(h->norm_host, part, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  *r0 = std::sqrt(h->norm_host[0]);
+  return MGRIT_OK;
+}
+
+// One V-cycle below level 1: levels 2..L-1 relax, level L marches, corrections
+// come back up; finally c_new += e on level 1 (or fused into the march, L = 2).
+static mgrit_status coarse_cycle(mgrit_handle* h, double* c_new) {
+  const int L = h->L, m = h->m, nx = h->nx;
+  const int prec = h->opts.precision == MGRIT_PREC_FP64 ? 0 : 1;
+  mgrit_status st;
+  if (L == 2) {
+    MarchArgs a = {};
+    a.init = nullptr;
+    a.g = h->r[1];
+    a.c_add = c_new;
+    a.nx = nx;
+    a.P = h->Nl[1] + 1;
+    a.store_every = 1;
+    return run_march(h, a, h->dpsi[0]);
+  }
+  for (int l = 2; l < L; ++l) {
+    FcfArgs f = {};
+    f.u_old = h->u[l];
+    f.cstride = (long long)m * nx;
+    f.c_new = h->cnew[l];
+    f.g = h->r[l - 1];
+    f.r = h->r[l];
+    f.partial = nullptr;
+    f.nx = nx;
+    f.m = m;
+    f.N = h->Nl[l];
+    f.zero_old = 1;
+    if ((st = launch_ok(launch_fcf(f, h->dpsi[l - 2], prec, h->fcf_threads, h->stream), "fcf(coarse)")) != MGRIT_OK)
+      return st;
+  }
+  MarchArgs a = {};
+  a.g = h->r[L - 1];
+  a.u_out = h->u[L];
+  a.store_every = 1;
+  a.nx = nx;
+  a.P = h->Nl[L - 1] + 1;
+  if ((st = run_march(h, a, h->dpsi[L - 2])) != MGRIT_OK) return st;
+  for (int l = L - 1; l >= 2; --l) {
+    CorrectArgs c = {};
+    c.c_new = h->cnew[l];
+    c.e = h->u[l + 1];
+    c.g = h->r[l - 1];
+    c.u = h->u[l];
+    c.nx = nx;
+    c.m = m;
+    c.N = h->Nl[l];
+    if ((st = launch_ok(launch_correct(c, h->dpsi[l - 2], h->fcf_threads, h->stream), "correct")) != MGRIT_OK)
+      return st;
+  }
+  return launch_ok(launch_add(c_new + nx, h->u[2] + nx, (long long)h->Nl[1] * nx, h->stream), "add");
+}
+
+extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* out, mgrit_result* res) {
+  if (!h) return fail(MGRIT_ERR_INVALID, "handle is NULL");
+  if (!u0) return fail(MGRIT_ERR_INVALID, "u0 is NULL");
+  const double t0 = now_s();
+  const int nx = h->nx, m = h->m;
+  const size_t N1 = h->Nl[1];
+  const size_t slab = (size_t)nx * sizeof(double);
+  mgrit_result R;
+  std::memset(&R, 0, sizeof(R));
+  R.n_levels = h->L;
+  R.setup_s = h->setup_s;
+  R.op_complexity = h->op_complexity;
+  int cur = 0;
+  CUDA_TRY(cudaMemcpyAsync(h->c[0], u0, slab, kind_to_dev(u0), h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->c[1], h->c[0], slab, cudaMemcpyDeviceToDevice, h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->c[0] + nx, 0, N1 * slab, h->stream));
+  double r0 = 0.0;
+  mgrit_status st = initial_residual(h, h->c[0], &r0);
+  if (st != MGRIT_OK) return st;
+  R.r0_norm = r0;
+  const int prec = h->opts.precision == MGRIT_PREC_FP64 ? 0 : 1;
+  mgrit_status final_status = MGRIT_OK;
+  int it = 0;
+  for (;;) {
+    FcfArgs f = {};
+    f.u_old = h->c[cur];
+    f.cstride = nx;
+    f.c_new = h->c[1 - cur];
+    f.g = nullptr;
+    f.r = h->r[1];
+    f.partial = h->partial;
+    f.nx = nx;
+    f.m = m;
+    f.N = (int)N1;
+    f.zero_old = 0;
+    if ((st = launch_ok(launch_fcf(f, h->dphi, prec, h->fcf_threads, h->stream), "fcf")) != MGRIT_OK) return st;
+    if ((st = launch_ok(launch_norm(h->partial, (int)N1, h->scratch + 2 * nx, h->stream), "norm")) != MGRIT_OK)
+      return st;
+    CUDA_TRY(cudaMemcpyAsync(h->norm_host, h->scratch + 2 * nx, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    const double rel = r0 > 0.0 ? std::sqrt(h->norm_host[0]) / r0 : 0.0;
+    if (R.n_history < MGRIT_MAX_HISTORY) R.history[R.n_history++] = rel;
+    R.rel_residual = rel;
+    if (!std::isfinite(rel) || rel > 1e6) {
+      final_status = fail(MGRIT_ERR_DIVERGED, "residual not finite or grew above 1e6 x initial");
+      break;
+    }
+    if (rel <= h->opts.tol) {
+      R.converged = 1;
+      break;
+    }
+    if (it >= h->opts.max_iter) {
+      final_status = fail(MGRIT_ERR_NOT_CONVERGED, "max_iter reached");
+      break;
+    }
+    if ((st = coarse_cycle(h, h->c[1 - cur])) != MGRIT_OK) return st;
+    cur = 1 - cur;
+    ++it;
+  }
+  R.iterations = it;
+  // result: C-points after the final FCF-relaxation live in c[1-cur]
+  const double* cres = h->c[1 - cur];
+  if (out) {
+    if (h->opts.output == MGRIT_OUT_FINAL) {
+      CUDA_TRY(cudaMemcpyAsync(out, cres + N1 * nx, slab, kind_from_dev(out), h->stream));
+    } else if (h->opts.output == MGRIT_OUT_CPOINTS) {
+      CUDA_TRY(cudaMemcpyAsync(out, cres, (N1 + 1) * slab, kind_from_dev(out), h->stream));
+    } else {
+      // F-points by one F-relaxation from the C-points (ideal interpolation)
+      double* full = nullptr;
+      const bool dev = is_device_ptr(out);
+      if (dev) full = out;
+      else if ((st = dalloc(h, (size_t)(h->nt + 1) * nx, &full)) != MGRIT_OK) return st;
+      CorrectArgs c = {};
+      c.c_new = cres;
+      c.e = nullptr;
+      c.g = nullptr;
+      c.u = full;
+      c.nx = nx;
+      c.m = m;
+      c.N = (int)N1;
+      if ((st = launch_ok(launch_correct(c, h->dphi, h->fcf_threads, h->stream), "interp")) != MGRIT_OK)
+        return st;
+      if (!dev) {
+        CUDA_TRY(cudaMemcpyAsync(out, full, (size_t)(h->nt + 1) * slab, cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        DevBuf b = h->bufs.back();
+        h->bufs.pop_back();
+        h->bytes -= std::max<size_t>(b.n, 1) * sizeof(double);
+        if (b.freefn) b.freefn(b.p, (void*)h->stream, b.ctx);
+        else cudaFreeAsync(b.p, h->stream);
+      }
+    }
+  }
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  R.solve_s = now_s() - t0;
+  R.dof_per_s = R.solve_s > 0 ? (double)nx * h->nt / R.solve_s : 0.0;
+  if (res) *res = R;
+  return final_status;
+}
+
+extern "C" mgrit_status mgrit_sequential(mgrit_handle* h, const double* u0, double* out, double* seconds) {
+  if (!h) return fail(MGRIT_ERR_INVALID, "handle is NULL");
+  if (!u0) return fail(MGRIT_ERR_INVALID, "u0 is NULL");
+  const double t0 = now_s();
+  const int nx = h->nx;
+  const size_t slab = (size_t)nx * sizeof(double);
+  const int every = h->opts.output == MGRIT_OUT_FULL ? 1 : (h->opts.output == MGRIT_OUT_CPOINTS ? h->m : h->nt);
+  const size_t nstore = (size_t)h->nt / every + 1;
+  double* dst = nullptr;
+  mgrit_status st;
+  const bool final_only = h->opts.output == MGRIT_OUT_FINAL;
+  const bool dev = out && is_device_ptr(out) && !final_only;
+  bool temp = false;
+  if (dev) dst = out;
+  else {
+    if ((st = dalloc(h, nstore * nx, &dst)) != MGRIT_OK) return st;
+    temp = true;
+  }
+  double* init = h->scratch;
+  CUDA_TRY(cudaMemcpyAsync(init, u0, slab, kind_to_dev(u0), h->stream));
+  CUDA_TRY(cudaMemcpyAsync(dst, init, slab, cudaMemcpyDeviceToDevice, h->stream));
+  MarchArgs a = {};
+  a.init = init;
+  a.u_out = dst;
+  a.store_every = every;
+  a.nx = nx;
+  a.P = h->nt + 1;
+  int saved = h->march_cluster;
+  h->march_cluster = pick_cluster(nx, h->phi);
+  st = run_march(h, a, h->dphi);
+  h->march_cluster = saved;
+  if (st != MGRIT_OK) return st;
+  if (out && !dev) {
+    if (final_only)
+      CUDA_TRY(cudaMemcpyAsync(out, dst + (nstore - 1) * nx, slab, kind_from_dev(out), h->stream));
+    else
+      CUDA_TRY(cudaMemcpyAsync(out, dst, nstore * slab, cudaMemcpyDeviceToHost, h->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (temp) {
+    DevBuf b = h->bufs.back();
+    h->bufs.pop_back();
+    h->bytes -= std::max<size_t>(b.n, 1) * sizeof(double);
+    if (b.freefn) b.freefn(b.p, (void*)h->stream, b.ctx);
+    else cudaFreeAsync(b.p, h->stream);
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+  }
+  if (seconds) *seconds = now_s() - t0;
+  return MGRIT_OK;
+}
+
+extern "C" mgrit_status mgrit_propagate(mgrit_handle* h, int32_t level, int32_t k, int32_t count, const double* in,
+                                        double* out) {
+  if (!h) return fail(MGRIT_ERR_INVALID, "handle is NULL");
+  if (level < 1 || level > h->L) return fail(MGRIT_ERR_INVALID, "level must be 1..levels");
+  if (k < 0 || count < 0 || !in || !out) return fail(MGRIT_ERR_INVALID, "bad arguments");
+  const DevTaps& t = level == 1 ? h->dphi : h->dpsi[level - 2];
+  mgrit_status st = launch_ok(launch_propagate(in, out, count, h->nx, k, t, nullptr, h->fcf_threads, h->stream),
+                              "propagate");
+  if (st != MGRIT_OK) return st;
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  return MGRIT_OK;
+}

@@ -1,0 +1,172 @@
+"""GPU vs. oracle parity through the C ABI (FP64 relative L2 <= 1e-12 and the
+same iteration count; Section 2.2's MGRIT, Eq. 3's sequential stepping)."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import mgrit as omg
+from oracle import psi as opsi
+from oracle import schemes, stepping
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def capi():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1910_03726_gb300 import build
+    build.build()
+    from paper_1910_03726_gb300 import capi as c
+    return c
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+RULE = {"halfwidth": 1, "auto": 0, "threshold": 2, "ideal": 4}
+
+
+def oracle_run(fam, p, c, nx, nt, m, L, rule, u0, tol=1e-10, psi_ops=None):
+    st = stepping.FineStep(fam, p, c, nx)
+    if psi_ops is None:
+        ops = [o.diag for o in opsi.build_hierarchy(fam, p, c, nx, nt, m, L, rule=rule, halfwidth=3)]
+    else:
+        ops = [dict(zip(o, v)) for o, v in psi_ops]
+    lev = omg.make_levels(st, m, ops)
+    U = omg.zero_iterate(u0, nt)
+    hist = []
+    it, r = omg.solve(lev, U, tol=tol, history=hist)
+    return it, r, U, hist
+
+
+def gpu_run(capi, fam, p, c, nx, nt, m, L, rule, u0, precision=0, output=1, tol=1e-10, user=None):
+    opts = capi.mgrit_opts_default(m=m, levels=L, psi_rule=RULE[rule], psi_halfwidth=3, precision=precision,
+                                   output=output, tol=tol)
+    keep = capi.user_psi(opts, user) if user is not None else None
+    h = capi.mgrit_setup(capi.problem(nx, nt, fam, p, p, c), opts)
+    try:
+        nrow = {0: 1, 1: nt // m + 1, 2: nt + 1}[output]
+        out = np.zeros((nrow, nx))
+        res, st = capi.mgrit_solve(h, np.ascontiguousarray(u0), out)
+        ops = [capi.mgrit_psi_info(h, l) for l in range(2, L + 1)]
+    finally:
+        capi.mgrit_destroy(h)
+    del keep
+    return res, out, ops
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_fine_step_matches_stage_form(capi, p):
+    """A1: the collapsed ERK stencil applied k times equals k stage-wise steps."""
+    import torch
+    nx, k, count = 200, 3, 7           # nx not a power of two: ragged tiles
+    c = schemes.cfl_number("ERK", p)
+    h = capi.mgrit_setup(capi.problem(nx, 8, "ERK", p, p, c), capi.mgrit_opts_default(m=2, levels=2))
+    try:
+        x = np.random.default_rng(p).standard_normal((count, nx))
+        xin = torch.tensor(x, device="cuda")
+        yout = torch.zeros_like(xin)
+        capi.mgrit_propagate(h, 1, k, count, xin, yout)
+    finally:
+        capi.mgrit_destroy(h)
+    st = stepping.FineStep("ERK", p, c, nx)
+    ref = x.copy()
+    for _ in range(k):
+        ref = st(ref)
+    assert rel(yout.cpu().numpy(), ref) <= TOL
+
+
+def test_config1_two_level_parity(capi):
+    """ERK1+U1, nx=64, nt=1024, m=8, Psi half-width 3, sin^4, zero guess."""
+    nx, nt, m = 64, 1024, 8
+    u0 = workloads.sin4(nx)
+    it, r, U, hist = oracle_run("ERK", 1, 0.85, nx, nt, m, 2, "halfwidth", u0)
+    res, out, ops = gpu_run(capi, "ERK", 1, 0.85, nx, nt, m, 2, "halfwidth", u0)
+    assert res.iterations == it
+    assert res.converged == 1
+    assert rel(out, U[::m]) <= TOL
+    np.testing.assert_allclose(res.history[: res.n_history], hist, rtol=1e-6)
+
+
+@pytest.mark.parametrize("case", [
+    ("ERK", 3, 256, 2048, 4, 2), ("ERK", 3, 256, 2048, 8, 3), ("ERK", 3, 256, 2048, 4, 4),
+    ("ERK", 5, 128, 1024, 4, 3), ("ERK", 2, 96, 768, 4, 3), ("ERK", 4, 128, 512, 16, 2),
+])
+def test_mgrit_parity_fp64(capi, case):
+    """Two-level and V-cycle MGRIT, own Psi on each side (same pattern; fitted
+    coefficients agree to ~1e-10, which the iteration damps)."""
+    fam, p, nx, nt, m, L = case
+    c = schemes.cfl_number(fam, p)
+    u0 = workloads.fourier_field(nx)
+    it, r, U, _ = oracle_run(fam, p, c, nx, nt, m, L, "auto", u0)
+    res, out, _ = gpu_run(capi, fam, p, c, nx, nt, m, L, "auto", u0)
+    assert res.iterations == it
+    assert rel(out, U[::m]) <= TOL
+
+
+def test_mgrit_parity_shared_psi_full_output(capi):
+    """Same Psi on both sides (oracle's fit passed through PSI_USER); FULL
+    output = C-points plus F-points by ideal interpolation."""
+    fam, p, nx, nt, m, L = "ERK", 3, 128, 512, 4, 3
+    c = schemes.cfl_number(fam, p)
+    ops = opsi.build_hierarchy(fam, p, c, nx, nt, m, L, rule="auto")
+    user = [(o.offsets, [o.diag[i] for i in o.offsets]) for o in ops]
+    u0 = workloads.sin4(nx)
+    it, r, U, _ = oracle_run(fam, p, c, nx, nt, m, L, "auto", u0, psi_ops=user)
+    res, out, got_ops = gpu_run(capi, fam, p, c, nx, nt, m, L, "auto", u0, output=2, user=user)
+    assert [o for o, _ in got_ops] == [o for o, _ in user]
+    assert res.iterations == it
+    assert rel(out, U) <= TOL
+
+
+def test_mixed_precision_reaches_the_fp64_fixed_point(capi):
+    """MIXED: FP32 second F-relaxation; the FP64 residual drives the iteration
+    to the same discrete solution; iterations equal FP64's (within 1)."""
+    fam, p, nx, nt, m, L = "ERK", 3, 256, 2048, 8, 2
+    c = schemes.cfl_number(fam, p)
+    u0 = workloads.fourier_field(nx)
+    it, r, U, _ = oracle_run(fam, p, c, nx, nt, m, L, "auto", u0)
+    ref = stepping.sequential(stepping.FineStep(fam, p, c, nx), u0, nt)
+    res, out, _ = gpu_run(capi, fam, p, c, nx, nt, m, L, "auto", u0, precision=1)
+    assert abs(res.iterations - it) <= 1
+    assert res.rel_residual <= 1e-10
+    assert rel(out, ref[::m]) <= 1e-9
+
+
+@pytest.mark.parametrize("output", [0, 1, 2])
+def test_sequential_stepping_matches_oracle(capi, output):
+    nx, nt, m = 96, 240, 8
+    c = schemes.cfl_number("ERK", 3)
+    u0 = workloads.fourier_field(nx)
+    ref = stepping.sequential(stepping.FineStep("ERK", 3, c, nx), u0, nt)
+    h = capi.mgrit_setup(capi.problem(nx, nt, "ERK", 3, 3, c), capi.mgrit_opts_default(m=m, output=output))
+    try:
+        rows = {0: 1, 1: nt // m + 1, 2: nt + 1}[output]
+        out = np.zeros((rows, nx))
+        capi.mgrit_sequential(h, u0, out)
+    finally:
+        capi.mgrit_destroy(h)
+    want = {0: ref[-1:], 1: ref[::m], 2: ref}[output]
+    assert rel(out, want) <= TOL
+
+
+def test_edge_cases_small_and_ragged(capi):
+    """Smallest grids (nx = 8), m = 2 with two intervals, non-power-of-two nx,
+    and max_iter = 0 (returns NOT_CONVERGED with the relaxed iterate)."""
+    for (nx, nt, m, L) in [(8, 4, 2, 2), (24, 48, 2, 3), (40, 64, 4, 2)]:
+        u0 = workloads.sin4(nx)
+        it, r, U, _ = oracle_run("ERK", 1, 0.85, nx, nt, m, L, "auto", u0)
+        res, out, _ = gpu_run(capi, "ERK", 1, 0.85, nx, nt, m, L, "auto", u0)
+        assert res.iterations == it, (nx, nt, m, L)
+        assert rel(out, U[::m]) <= TOL
+    opts = capi.mgrit_opts_default(m=8, levels=2, max_iter=0)
+    h = capi.mgrit_setup(capi.problem(64, 256, "ERK", 1, 1, 0.85), opts)
+    try:
+        res, st = capi.mgrit_solve(h, workloads.sin4(64), None, allow_not_converged=True)
+        assert st == -4 and res.iterations == 0 and res.converged == 0
+    finally:
+        capi.mgrit_destroy(h)
