@@ -1,0 +1,325 @@
+#!/usr/bin/env python3
+"""Benchmark: space-time DOF/s of MGRIT at a 1e-10 relative residual.
+
+Workload (one "step" = one complete solve to tol 1e-10): ERK3+U3 on periodic
+[-1, 1), nx = 4096, nt = 16384, c = 0.85 * 1.62589 (85% of Table 1's limit),
+u0 = random Fourier field (modes 1..64, N(0,1)/k^2, seed 2), zero initial
+iterate, V-cycle with 4 levels and m = 8, least-squares Psi on every level,
+FP32 second F-relaxation with FP64 residual / coarse solve / test.  Also timed
+on the same GPU: the FP64 variant, two-level m = 8, and plain FP64
+sequential time stepping.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas
+(the solve has no data-parallel exchange on one box): value = total DOF of all
+ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+NX, NT, P, M, LEVELS = 4096, 16384, 3, 8, 4
+CMAX3 = 1.62589
+CFL = 0.85 * CMAX3
+TOL = 1e-10
+METRIC = "space-time DOF/s at 1e-10 rel. residual vs GPU seq. stepping; p50/p99 latency"
+# FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.070 GHz
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+WORKLOAD = ("ERK3+U3 nx=4096 nt=16384 c=0.85*1.62589, Fourier-field u0 (seed 2), zero initial iterate, "
+            "V-cycle L=4 m=8, LSQ Psi (auto width), FP32 F-relax + FP64 residual/coarse/test, tol 1e-10")
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# --------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (median SM clock, reasons)."""
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, dev):
+        self.dev, self.samples, self.proc = dev, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# --------------------------------------------------------- oracle (CPU)
+
+def oracle_sample(nt_sample):
+    """Oracle FCF-MGRIT on the same scheme/CFL/u0/hierarchy shape, first
+    nt_sample steps of the horizon; returns (DOF/s, seconds, iterations)."""
+    from oracle import mgrit as omg
+    from oracle import psi as opsi
+    from oracle import stepping
+    u0 = workloads.fourier_field(NX)
+    st = stepping.FineStep("ERK", P, CFL, NX)
+    ops = opsi.build_hierarchy("ERK", P, CFL, NX, nt_sample, M, LEVELS, rule="auto")
+    lev = omg.make_levels(st, M, [o.diag for o in ops])
+    U = omg.zero_iterate(u0, nt_sample)
+    t0 = time.perf_counter()
+    it, rel = omg.solve(lev, U, tol=TOL)
+    dt = time.perf_counter() - t0
+    return NX * nt_sample / dt, dt, it
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    nt_sample = 512
+    for _ in range(args.warmup):
+        oracle_sample(nt_sample)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, s, it = oracle_sample(nt_sample)
+        vals.append(v)
+        secs.append(s)
+    value = NX * nt_sample * len(secs) / sum(secs)
+    sample = (f"oracle (numpy, 1 thread) V-cycle L=4 m=8 FCF-MGRIT on nx=4096, nt={nt_sample} (first "
+              f"{nt_sample}/16384 of the horizon), same scheme, CFL, u0 and tol; Psi setup excluded")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU arm
+
+def fcf_traffic_from_profile():
+    """Per-launch DRAM bytes of the level-1 FCF kernel from the committed ncu
+    summary, if it was taken on the current kernels source; else None."""
+    path = os.path.join(ROOT, "profiles", "fcf_kernel_erk3u3_4096.md")
+    src = os.path.join(ROOT, "paper_1910_03726_gb300", "csrc", "kernels.cu")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    m1 = re.search(r"kernels\.cu sha256\[:16\]:\s*([0-9a-f]{16})", text)
+    m2 = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    if not (m1 and m2) or m1.group(1) != h:
+        return None
+    return float(m2.group(1))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    rank, world, local = dist_env()
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1910_03726_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1910_03726_gb300 import capi
+
+    stream = torch.cuda.current_stream()
+    sp = int(stream.cuda_stream)
+    u0_np = workloads.fourier_field(NX)
+    u0 = torch.tensor(u0_np, device="cuda")
+    N1 = NT // M
+    out = torch.empty((N1 + 1, NX), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
+    prob = capi.problem(NX, NT, "ERK", P, P, CFL)
+
+    def make(levels, m, precision, flags=0):
+        o = capi.mgrit_opts_default(m=m, levels=levels, precision=precision, tol=TOL, output=capi.OUT_CPOINTS,
+                                    flags=flags, max_iter=50)
+        return capi.mgrit_setup(prob, o, stream=sp)
+
+    def timed_solves(h, K, W, collect=False):
+        for _ in range(W):
+            capi.mgrit_solve(h, u0, out)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        lat, results = [], []
+        e0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        e1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        for k in range(K):
+            flush.zero_()                       # evict L2 between steps
+            e0[k].record(stream)
+            r, _ = capi.mgrit_solve(h, u0, out)
+            e1[k].record(stream)
+            results.append(r)
+        torch.cuda.synchronize()
+        lat = [a.elapsed_time(b) for a, b in zip(e0, e1)]
+        total = sum(lat)
+        if world > 1:
+            t = torch.tensor([total], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        return lat, total, results
+
+    clocks = ClockSampler(local)
+    # ---- headline: V-cycle L=4, m=8, mixed precision, per-kernel events on
+    h = make(LEVELS, M, capi.PREC_MIXED, flags=capi.FLAG_TIME_KERNELS)
+    clocks.start()
+    lat, total, results = timed_solves(h, args.steps, args.warmup)
+    clk = clocks.stop()
+    res0 = results[-1]
+    value = world * NX * NT * args.steps / (total * 1e-3)
+    fcf_ms = sum(r.kernel_ms[0] for r in results)
+    fcf_n = sum(r.kernel_count[0] for r in results)
+    launches = sum(r.launches for r in results)
+    nnz_phi = len(capi.mgrit_phi_taps(prob)[0])
+    flops64 = N1 * M * NX * 2 * nnz_phi          # FP64 pass of one level-1 FCF launch
+    fcf_avg_s = fcf_ms / max(1, fcf_n) * 1e-3
+    achieved = flops64 / fcf_avg_s / 1e12 if fcf_avg_s > 0 else None
+    kernel_share = {capi.KERNEL_KINDS[i]: round(sum(r.kernel_ms[i] for r in results) /
+                                                max(1e-9, sum(sum(r.kernel_ms) for r in results)), 4)
+                    for i in range(capi.K_KINDS)}
+    # ---- e2e through the C ABI with host buffers (u0 in, C-points out)
+    u0_host = np.ascontiguousarray(u0_np)
+    out_host = np.empty((N1 + 1, NX))
+    capi.mgrit_solve(h, u0_host, out_host)
+    torch.cuda.synchronize()
+    e2e_t = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        capi.mgrit_solve(h, u0_host, out_host)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_value = world * NX * NT * len(e2e_t) / sum(e2e_t)
+    capi.mgrit_destroy(h)
+
+    extra = {}
+    if not args.no_variants:
+        ks = max(3, args.steps // 2)
+        for name, (lv, m, prec) in {"fp64_vcycle_L4_m8": (4, 8, capi.PREC_FP64),
+                                    "mixed_two_level_m8": (2, 8, capi.PREC_MIXED),
+                                    "fp64_two_level_m8": (2, 8, capi.PREC_FP64)}.items():
+            hv = make(lv, m, prec)
+            lv_lat, lv_total, lv_res = timed_solves(hv, ks, 1)
+            extra[name] = {"dof_per_s": NX * NT * ks / (lv_total * 1e-3), "ms": lv_total / ks,
+                           "iterations": lv_res[-1].iterations, "rel_residual": lv_res[-1].rel_residual}
+            capi.mgrit_destroy(hv)
+        # plain FP64 sequential stepping on the GPU (one thread-block cluster)
+        hs = make(2, M, capi.PREC_FP64)
+        fin = torch.empty((N1 + 1, NX), dtype=torch.float64, device="cuda")
+        capi.mgrit_sequential(hs, u0, fin)
+        torch.cuda.synchronize()
+        sl = []
+        for _ in range(3):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            capi.mgrit_sequential(hs, u0, fin)
+            b.record(stream)
+            torch.cuda.synchronize()
+            sl.append(a.elapsed_time(b))
+        seq_ms = statistics.median(sl)
+        extra["gpu_sequential_fp64"] = {"dof_per_s": NX * NT / (seq_ms * 1e-3), "ms": seq_ms}
+        extra["speedup_vs_gpu_sequential"] = (seq_ms / statistics.median(lat))
+        # accuracy of the headline result against FP64 sequential stepping (C-points)
+        err = float(torch.linalg.norm(out - fin) / torch.linalg.norm(fin))
+        extra["rel_l2_vs_fp64_sequential"] = err
+        capi.mgrit_destroy(hs)
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu and world == 1:
+            v, s, it = oracle_sample(4096)
+            cpu = {"value": v, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+                   "sample": f"oracle (numpy, 1 thread) V-cycle L=4 m=8 FCF-MGRIT, nx=4096, nt=4096 (first "
+                             f"1/4 of the horizon), same scheme/CFL/u0/tol, {s:.1f} s, {it} iterations"}
+        lat_sorted = sorted(lat)
+        line = {
+            "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp64+fp32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": NX, "nt": NT, "levels": LEVELS, "m": M,
+                       "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MiB write)"},
+            "latency_ms": {"p50": float(np.percentile(lat_sorted, 50)), "p99": float(np.percentile(lat_sorted, 99))},
+            "iterations": res0.iterations, "rel_residual": res0.rel_residual,
+            "e2e": {"value": e2e_value, "unit": "DOF/s", "h2d_bytes_per_step": NX * 8,
+                    "d2h_bytes_per_step": (N1 + 1) * NX * 8},
+            "gpu_launches": launches,
+            "roofline": {"bound": "alu", "kernel": "fcf_kernel<mixed> (level-1 FCF + fused residual)",
+                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                         "traffic": fcf_traffic_from_profile(),
+                         "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (FP64 FMA pipe)",
+                         "flops_per_launch_fp64": flops64, "launch_ms": fcf_avg_s * 1e3},
+            "kernel_time_share": kernel_share,
+            "clocks": clk, "cpu_baseline": cpu, "variants": extra,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

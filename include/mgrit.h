@@ -83,6 +83,24 @@ enum {
 
 enum { MGRIT_OUT_FINAL = 0, MGRIT_OUT_CPOINTS = 1, MGRIT_OUT_FULL = 2 };
 
+/* MGRIT_FLAG_TIME_KERNELS: bracket every kernel launch of a solve with CUDA
+ * events on the handle's stream and report per-kind device time in
+ * mgrit_result.kernel_ms (adds two event records per launch). */
+enum { MGRIT_FLAG_TIME_KERNELS = 1 };
+
+/* Kernel kinds reported in mgrit_result.kernel_ms / kernel_count. */
+enum {
+  MGRIT_K_FCF = 0,         /* level-1 FCF-relaxation + fused residual            */
+  MGRIT_K_FCF_COARSE = 1,  /* FCF-relaxation on levels 2..L-1                    */
+  MGRIT_K_MARCH = 2,       /* sequential coarsest-level march (cluster)          */
+  MGRIT_K_CORRECT = 3,     /* coarse-level correction + F-relaxation             */
+  MGRIT_K_NORM = 4,        /* residual norm reduction                            */
+  MGRIT_K_ADD = 5,         /* level-1 correction c += e                          */
+  MGRIT_K_PROPAGATE = 6,   /* initial residual / propagate                       */
+  MGRIT_K_OTHER = 7,
+  MGRIT_K_KINDS = 8
+};
+
 typedef struct mgrit_problem {
   int32_t nx;            /* spatial points (periodic), >= 8                       */
   int32_t nt;            /* time steps; divisible by m^(levels-1)                  */
@@ -102,6 +120,8 @@ typedef struct mgrit_opts {
   int32_t psi_halfwidth; /* for MGRIT_PSI_HALFWIDTH                                */
   int32_t output;        /* MGRIT_OUT_*                                            */
   int32_t min_coarse;    /* smallest admissible number of coarsest-level steps     */
+  int32_t flags;         /* MGRIT_FLAG_* bits                                      */
+  int32_t reserved;
   double tol;            /* stop when ||r|| <= tol ||r^(0)|| (Section 2.2)         */
   double psi_eta;        /* threshold eta_tol; <= 0 = paper's table (Section 4.6)  */
   double psi_rho;        /* bound target of MGRIT_PSI_AUTO (default 0.15)          */
@@ -125,13 +145,18 @@ typedef struct mgrit_result {
   double dof_per_s;      /* nx * nt / solve_s                                       */
   double op_complexity;  /* Eq. 5 (ERK; 0 for SDIRK, whose Phi is dense)            */
   double history[MGRIT_MAX_HISTORY]; /* relative residual after each FCF            */
+  int32_t launches;      /* kernels this call launched                              */
+  int32_t reserved;
+  int32_t kernel_count[MGRIT_K_KINDS];  /* launches per kind                         */
+  double kernel_ms[MGRIT_K_KINDS];      /* device time per kind (FLAG_TIME_KERNELS)  */
 } mgrit_result;
 
 typedef struct mgrit_handle mgrit_handle;
 typedef struct mgrit_server mgrit_server;
 
 /* Fill *o with the defaults: m 8, levels 2, max_iter 100, FP64, PSI_AUTO,
- * halfwidth 3, OUT_CPOINTS, min_coarse 2, tol 1e-10, eta <= 0, rho 0.15. */
+ * halfwidth 3, OUT_CPOINTS, min_coarse 2, flags 0, tol 1e-10, eta <= 0,
+ * rho 0.15. */
 void mgrit_opts_default(mgrit_opts* o);
 
 /* Optional device allocator used for all later allocations (NULL, NULL

@@ -28,6 +28,9 @@ PSI_AUTO, PSI_HALFWIDTH, PSI_THRESHOLD, PSI_USER, PSI_IDEAL = 0, 1, 2, 3, 4
 OUT_FINAL, OUT_CPOINTS, OUT_FULL = 0, 1, 2
 MAX_HISTORY = 128
 MAX_LEVELS = 8
+FLAG_TIME_KERNELS = 1
+KERNEL_KINDS = ["fcf", "fcf_coarse", "march", "correct", "norm", "add", "propagate", "other"]
+K_KINDS = len(KERNEL_KINDS)
 
 EXPORTED = ["mgrit_opts_default", "mgrit_set_allocator", "mgrit_phi_taps", "mgrit_psi_plan",
             "mgrit_setup", "mgrit_solve", "mgrit_sequential", "mgrit_propagate", "mgrit_psi_info",
@@ -43,7 +46,7 @@ class MgritProblem(C.Structure):
 class MgritOpts(C.Structure):
     _fields_ = [("m", C.c_int32), ("levels", C.c_int32), ("max_iter", C.c_int32), ("precision", C.c_int32),
                 ("psi_rule", C.c_int32), ("psi_halfwidth", C.c_int32), ("output", C.c_int32),
-                ("min_coarse", C.c_int32), ("tol", C.c_double), ("psi_eta", C.c_double),
+                ("min_coarse", C.c_int32), ("flags", C.c_int32), ("reserved", C.c_int32), ("tol", C.c_double), ("psi_eta", C.c_double),
                 ("psi_rho", C.c_double), ("psi_user_nnz", C.POINTER(C.c_int32)),
                 ("psi_user_offsets", C.POINTER(C.c_int32)), ("psi_user_coeffs", C.POINTER(C.c_double))]
 
@@ -52,11 +55,15 @@ class MgritResult(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("n_levels", C.c_int32), ("converged", C.c_int32),
                 ("n_history", C.c_int32), ("rel_residual", C.c_double), ("r0_norm", C.c_double),
                 ("setup_s", C.c_double), ("solve_s", C.c_double), ("dof_per_s", C.c_double),
-                ("op_complexity", C.c_double), ("history", C.c_double * MAX_HISTORY)]
+                ("op_complexity", C.c_double), ("history", C.c_double * MAX_HISTORY),
+                ("launches", C.c_int32), ("reserved", C.c_int32), ("kernel_count", C.c_int32 * K_KINDS),
+                ("kernel_ms", C.c_double * K_KINDS)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "history"}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("history", "kernel_count", "kernel_ms")}
         d["history"] = list(self.history[: self.n_history])
+        d["kernel_count"] = {KERNEL_KINDS[i]: self.kernel_count[i] for i in range(K_KINDS)}
+        d["kernel_ms"] = {KERNEL_KINDS[i]: self.kernel_ms[i] for i in range(K_KINDS)}
         return d
 
 

@@ -76,6 +76,11 @@ struct mgrit_handle {
   double* scratch = nullptr;      // 2*nx + 1 doubles
   double* norm_host = nullptr;    // pinned
   int fcf_threads = 512, march_cluster = 1, march_threads = 256;
+  // per-solve launch accounting (and CUDA-event timing with MGRIT_FLAG_TIME_KERNELS)
+  int kcount[MGRIT_K_KINDS] = {0};
+  std::vector<cudaEvent_t> evpool;
+  std::vector<int> evkind;      // kind of each recorded (start, stop) pair
+  size_t evused = 0;
   double setup_s = 0.0, op_complexity = 0.0;
   size_t bytes = 0;
 };
@@ -114,6 +119,8 @@ static void release(mgrit_handle* h) {
   h->bufs.clear();
   if (h->norm_host) cudaFreeHost(h->norm_host);
   h->norm_host = nullptr;
+  for (auto ev : h->evpool) cudaEventDestroy(ev);
+  h->evpool.clear();
   cudaStreamSynchronize(h->stream);
 }
 
@@ -159,6 +166,7 @@ extern "C" void mgrit_opts_default(mgrit_opts* o) {
   o->psi_halfwidth = 3;
   o->output = MGRIT_OUT_CPOINTS;
   o->min_coarse = 2;
+  o->flags = 0;
   o->tol = 1e-10;
   o->psi_eta = 0.0;
   o->psi_rho = 0.15;
@@ -425,16 +433,76 @@ static mgrit_status launch_ok(cudaError_t e, const char* what) {
   return MGRIT_OK;
 }
 
+static void reset_stats(mgrit_handle* h) {
+  for (int k = 0; k < MGRIT_K_KINDS; ++k) h->kcount[k] = 0;
+  h->evkind.clear();
+  h->evused = 0;
+}
+
+static cudaEvent_t next_event(mgrit_handle* h) {
+  if (h->evused == h->evpool.size()) {
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    h->evpool.push_back(ev);
+  }
+  return h->evpool[h->evused++];
+}
+
+// Launch one kernel of `kind` through fn(); counts it and, when asked,
+// brackets it with CUDA events on the handle's stream.
+template <typename F>
+static mgrit_status klaunch(mgrit_handle* h, int kind, const char* what, F&& fn) {
+  const bool timed = (h->opts.flags & MGRIT_FLAG_TIME_KERNELS) != 0;
+  cudaEvent_t e0 = timed ? next_event(h) : nullptr;
+  if (e0) cudaEventRecord(e0, h->stream);
+  mgrit_status st = fn();
+  if (st != MGRIT_OK) return st;
+  if (e0) {
+    cudaEvent_t e1 = next_event(h);
+    if (e1) {
+      cudaEventRecord(e1, h->stream);
+      h->evkind.push_back(kind);
+    } else {
+      h->evused--;
+    }
+  }
+  h->kcount[kind]++;
+  (void)what;
+  return MGRIT_OK;
+}
+
+static void collect_stats(mgrit_handle* h, mgrit_result* R) {
+  int total = 0;
+  for (int k = 0; k < MGRIT_K_KINDS; ++k) {
+    R->kernel_count[k] = h->kcount[k];
+    R->kernel_ms[k] = 0.0;
+    total += h->kcount[k];
+  }
+  R->launches = total;
+  for (size_t p = 0; p < h->evkind.size(); ++p) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, h->evpool[2 * p], h->evpool[2 * p + 1]) == cudaSuccess)
+      R->kernel_ms[h->evkind[p]] += ms;
+    else
+      cudaGetLastError();
+  }
+}
+
 // Launch a march, shrinking the cluster if the device refuses the size.
 static mgrit_status run_march(mgrit_handle* h, const MarchArgs& a, const DevTaps& t) {
-  for (;;) {
-    int threads = std::min(256, a.nx / h->march_cluster);
-    cudaError_t e = launch_march(a, t, h->march_cluster, threads, h->stream);
-    if (e == cudaSuccess) return MGRIT_OK;
-    cudaGetLastError();
-    if (h->march_cluster == 1) return launch_ok(e, "march_kernel");
-    h->march_cluster >>= 1;
-  }
+  return klaunch(h, MGRIT_K_MARCH, "march", [&]() -> mgrit_status {
+    for (;;) {
+      int threads = std::min(256, a.nx / h->march_cluster);
+      cudaError_t e = launch_march(a, t, h->march_cluster, threads, h->stream);
+      if (e == cudaSuccess) return MGRIT_OK;
+      cudaGetLastError();
+      if (h->march_cluster == 1) return launch_ok(e, "march_kernel");
+      h->march_cluster >>= 1;
+    }
+  });
 }
 
 // ||Phi u0||: residual of the zero initial iterate (only time level 1 is nonzero).
@@ -442,8 +510,10 @@ static mgrit_status initial_residual(mgrit_handle* h, const double* u0dev, doubl
   mgrit_status st;
   double* out = h->scratch;
   double* part = h->scratch + h->nx;
-  if ((st = launch_ok(launch_propagate(u0dev, out, 1, h->nx, 1, h->dphi, part, h->fcf_threads, h->stream),
-                      "propagate")) != MGRIT_OK)
+  if ((st = klaunch(h, MGRIT_K_PROPAGATE, "propagate", [&] {
+         return launch_ok(launch_propagate(u0dev, out, 1, h->nx, 1, h->dphi, part, h->fcf_threads, h->stream),
+                          "propagate");
+       })) != MGRIT_OK)
     return st;
   CUDA_TRY(cudaMemcpyAsync(h->norm_host, part, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -479,7 +549,9 @@ static mgrit_status coarse_cycle(mgrit_handle* h, double* c_new) {
     f.m = m;
     f.N = h->Nl[l];
     f.zero_old = 1;
-    if ((st = launch_ok(launch_fcf(f, h->dpsi[l - 2], prec, h->fcf_threads, h->stream), "fcf(coarse)")) != MGRIT_OK)
+    if ((st = klaunch(h, MGRIT_K_FCF_COARSE, "fcf", [&] {
+           return launch_ok(launch_fcf(f, h->dpsi[l - 2], prec, h->fcf_threads, h->stream), "fcf(coarse)");
+         })) != MGRIT_OK)
       return st;
   }
   MarchArgs a = {};
@@ -498,10 +570,14 @@ static mgrit_status coarse_cycle(mgrit_handle* h, double* c_new) {
     c.nx = nx;
     c.m = m;
     c.N = h->Nl[l];
-    if ((st = launch_ok(launch_correct(c, h->dpsi[l - 2], h->fcf_threads, h->stream), "correct")) != MGRIT_OK)
+    if ((st = klaunch(h, MGRIT_K_CORRECT, "correct", [&] {
+           return launch_ok(launch_correct(c, h->dpsi[l - 2], h->fcf_threads, h->stream), "correct");
+         })) != MGRIT_OK)
       return st;
   }
-  return launch_ok(launch_add(c_new + nx, h->u[2] + nx, (long long)h->Nl[1] * nx, h->stream), "add");
+  return klaunch(h, MGRIT_K_ADD, "add", [&] {
+    return launch_ok(launch_add(c_new + nx, h->u[2] + nx, (long long)h->Nl[1] * nx, h->stream), "add");
+  });
 }
 
 extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* out, mgrit_result* res) {
@@ -516,6 +592,7 @@ extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* o
   R.n_levels = h->L;
   R.setup_s = h->setup_s;
   R.op_complexity = h->op_complexity;
+  reset_stats(h);
   int cur = 0;
   CUDA_TRY(cudaMemcpyAsync(h->c[0], u0, slab, kind_to_dev(u0), h->stream));
   CUDA_TRY(cudaMemcpyAsync(h->c[1], h->c[0], slab, cudaMemcpyDeviceToDevice, h->stream));
@@ -539,8 +616,13 @@ extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* o
     f.m = m;
     f.N = (int)N1;
     f.zero_old = 0;
-    if ((st = launch_ok(launch_fcf(f, h->dphi, prec, h->fcf_threads, h->stream), "fcf")) != MGRIT_OK) return st;
-    if ((st = launch_ok(launch_norm(h->partial, (int)N1, h->scratch + 2 * nx, h->stream), "norm")) != MGRIT_OK)
+    if ((st = klaunch(h, MGRIT_K_FCF, "fcf", [&] {
+           return launch_ok(launch_fcf(f, h->dphi, prec, h->fcf_threads, h->stream), "fcf");
+         })) != MGRIT_OK)
+      return st;
+    if ((st = klaunch(h, MGRIT_K_NORM, "norm", [&] {
+           return launch_ok(launch_norm(h->partial, (int)N1, h->scratch + 2 * nx, h->stream), "norm");
+         })) != MGRIT_OK)
       return st;
     CUDA_TRY(cudaMemcpyAsync(h->norm_host, h->scratch + 2 * nx, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -585,7 +667,9 @@ extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* o
       c.nx = nx;
       c.m = m;
       c.N = (int)N1;
-      if ((st = launch_ok(launch_correct(c, h->dphi, h->fcf_threads, h->stream), "interp")) != MGRIT_OK)
+      if ((st = klaunch(h, MGRIT_K_OTHER, "interp", [&] {
+             return launch_ok(launch_correct(c, h->dphi, h->fcf_threads, h->stream), "interp");
+           })) != MGRIT_OK)
         return st;
       if (!dev) {
         CUDA_TRY(cudaMemcpyAsync(out, full, (size_t)(h->nt + 1) * slab, cudaMemcpyDeviceToHost, h->stream));
@@ -600,6 +684,7 @@ extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* o
   }
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   R.solve_s = now_s() - t0;
+  collect_stats(h, &R);
   R.dof_per_s = R.solve_s > 0 ? (double)nx * h->nt / R.solve_s : 0.0;
   if (res) *res = R;
   return final_status;
@@ -632,6 +717,7 @@ extern "C" mgrit_status mgrit_sequential(mgrit_handle* h, const double* u0, doub
   a.store_every = every;
   a.nx = nx;
   a.P = h->nt + 1;
+  reset_stats(h);
   int saved = h->march_cluster;
   h->march_cluster = pick_cluster(nx, h->phi);
   st = run_march(h, a, h->dphi);
@@ -662,8 +748,10 @@ extern "C" mgrit_status mgrit_propagate(mgrit_handle* h, int32_t level, int32_t 
   if (level < 1 || level > h->L) return fail(MGRIT_ERR_INVALID, "level must be 1..levels");
   if (k < 0 || count < 0 || !in || !out) return fail(MGRIT_ERR_INVALID, "bad arguments");
   const DevTaps& t = level == 1 ? h->dphi : h->dpsi[level - 2];
-  mgrit_status st = launch_ok(launch_propagate(in, out, count, h->nx, k, t, nullptr, h->fcf_threads, h->stream),
-                              "propagate");
+  reset_stats(h);
+  mgrit_status st = klaunch(h, MGRIT_K_PROPAGATE, "propagate", [&] {
+    return launch_ok(launch_propagate(in, out, count, h->nx, k, t, nullptr, h->fcf_threads, h->stream), "propagate");
+  });
   if (st != MGRIT_OK) return st;
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   return MGRIT_OK;
