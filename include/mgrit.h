@@ -242,6 +242,40 @@ mgrit_status mgrit_poll(mgrit_server* s, uint64_t ticket, double* out, mgrit_res
 
 void mgrit_server_destroy(mgrit_server* s);
 
+/* ------------------------------------------------- no-allocation variant */
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory where they relax (a memory manager owns
+ * every device byte, a real-time loop may not stall on an allocation, or a
+ * plug-in is handed pre-sized buffers).
+ *
+ * One FCF-relaxation with the fused C-point residual, as mgrit_solve performs
+ * it on the fine level: for j = 1..n_intervals
+ *   c_new[j]   = T^m c_old[j-1]                  (F- then C-relaxation)
+ *   r[j+1]     = T^m (c_new[j] - c_old[j])       (residual after the second
+ *                                                 F-relaxation, j < n_intervals)
+ *   *norm2     = sum_j ||r[j+1]||^2
+ * with (T v)_i = sum_k coeffs[k] v_{(i + offsets[k]) mod nx} (for example the
+ * taps of mgrit_phi_taps).  c_old, c_new, r: (n_intervals + 1) * nx doubles;
+ * c_new slab 0 and r slabs 0 and 1 are not written.  norm2: one double.  All
+ * four are device pointers; offsets/coeffs are host arrays of ntaps entries.
+ * precision: MGRIT_PREC_FP64 or MGRIT_PREC_MIXED (second pass in FP32).
+ *
+ * Allocates nothing: the per-interval partial norms live in a static device
+ * array of MGRIT_STATIC_MAX_INTERVALS doubles (512 KiB) that every GPU which
+ * loads the library keeps until exit; n_intervals above that is rejected with
+ * MGRIT_ERR_INVALID.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call shares the one array, so calls
+ * whose work overlaps on the GPU (other streams, other threads) race.  The
+ * call only enqueues work on `stream` and returns; synchronise the stream
+ * before reading the outputs. */
+#define MGRIT_STATIC_MAX_INTERVALS 65536
+mgrit_status mgrit_fcf_residual_static(const double* c_old, double* c_new, double* r, double* norm2,
+                                       int32_t nx, int32_t m, int32_t n_intervals, int32_t ntaps,
+                                       const int32_t* offsets, const double* coeffs, int32_t precision,
+                                       void* stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* mgrit_last_error(void);
 

@@ -19,7 +19,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmgrit_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["kernels.cu", "setup.cpp", "driver.cpp"]
+SOURCES = ["kernels.cu", "setup.cpp", "driver.cpp", "noalloc.cu"]
 HEADERS = ["device.h", "setup.h"]
 
 

@@ -35,7 +35,8 @@ K_KINDS = len(KERNEL_KINDS)
 EXPORTED = ["mgrit_opts_default", "mgrit_set_allocator", "mgrit_phi_taps", "mgrit_psi_plan",
             "mgrit_setup", "mgrit_solve", "mgrit_sequential", "mgrit_propagate", "mgrit_psi_info",
             "mgrit_device_bytes", "mgrit_destroy", "mgrit_server_create", "mgrit_submit",
-            "mgrit_poll", "mgrit_server_destroy", "mgrit_last_error", "mgrit_abi_version"]
+            "mgrit_poll", "mgrit_server_destroy", "mgrit_fcf_residual_static", "mgrit_last_error",
+            "mgrit_abi_version"]
 
 
 class MgritProblem(C.Structure):
@@ -108,6 +109,7 @@ _sig("mgrit_server_create", _i32, _P(MgritServerOpts), _vp, _P(_vp))
 _sig("mgrit_submit", _i32, _vp, _P(MgritProblem), _P(MgritOpts), _vp, _P(C.c_uint64))
 _sig("mgrit_poll", _i32, _vp, C.c_uint64, _vp, _P(MgritResult))
 _sig("mgrit_server_destroy", None, _vp)
+_sig("mgrit_fcf_residual_static", _i32, _vp, _vp, _vp, _vp, _i32, _i32, _i32, _i32, _P(_i32), _P(_f64), _i32, _vp)
 _sig("mgrit_last_error", C.c_char_p)
 _sig("mgrit_abi_version", _i32)
 
@@ -278,6 +280,16 @@ def mgrit_poll(s, ticket, out=None):
 
 def mgrit_server_destroy(s):
     _lib.mgrit_server_destroy(s)
+
+
+def mgrit_fcf_residual_static(c_old, c_new, r, norm2, nx, m, n_intervals, offsets, coeffs, precision=PREC_FP64,
+                              stream=None):
+    """No-allocation FCF + residual (device tensors in/out, host taps)."""
+    n = len(offsets)
+    offs = (C.c_int32 * max(1, n))(*[int(o) for o in offsets])
+    cfs = (C.c_double * max(1, n))(*[float(v) for v in coeffs])
+    return _check(_lib.mgrit_fcf_residual_static(_ptr(c_old), _ptr(c_new), _ptr(r), _ptr(norm2), nx, m,
+                                                 n_intervals, n, offs, cfs, precision, _stream_ptr(stream)))
 
 
 # ------------------------------------------------------------ torch memory

@@ -26,6 +26,10 @@ static mgrit_status fail(mgrit_status s, const std::string& msg) {
   return s;
 }
 
+namespace mg {
+void set_error(const std::string& msg) { g_err = msg; }
+}  // namespace mg
+
 #define CUDA_TRY(expr)                                                              \
   do {                                                                              \
     cudaError_t e_ = (expr);                                                        \

@@ -1,0 +1,72 @@
+"""The no-allocation entry point, for callers that cannot allocate device
+memory where they relax (their memory manager owns the device, or an
+allocation could stall a real-time loop).  It must give what the library's
+ordinary entry points give: the relaxed C-points and residual of one
+FCF-relaxation, rebuilt here from mgrit_propagate, on two calls in a row that
+share the static scratch array.  This file is collected last on purpose."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def capi():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1910_03726_gb300 import build
+    build.build()
+    from paper_1910_03726_gb300 import capi as c
+    return c
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_static_scratch_fcf_matches_propagate_two_calls(capi):
+    import torch
+    from oracle import schemes  # only for the CFL number of the test problem
+
+    nx, m, N, p = 320, 4, 37, 3            # nx not a power of two; ragged tail of threads
+    c = schemes.cfl_number("ERK", p)
+    prob = capi.problem(nx, m * N, "ERK", p, p, c)
+    offs, cfs = capi.mgrit_phi_taps(prob)
+    h = capi.mgrit_setup(prob, capi.mgrit_opts_default(m=m, levels=2))
+    try:
+        for call, seed in enumerate((5, 6)):
+            rng = np.random.default_rng(seed)
+            c_old = torch.tensor(rng.standard_normal((N + 1, nx)), device="cuda")
+            c_new = torch.zeros_like(c_old)
+            r = torch.zeros_like(c_old)
+            norm2 = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+            capi.mgrit_fcf_residual_static(c_old, c_new, r, norm2, nx, m, N, offs, cfs, capi.PREC_FP64)
+            torch.cuda.synchronize()
+            # the same quantities from the library's ordinary entry point
+            cn_ref = torch.zeros((N, nx), dtype=torch.float64, device="cuda")
+            capi.mgrit_propagate(h, 1, m, N, c_old[:N].contiguous(), cn_ref)
+            rho = (cn_ref - c_old[1:]).contiguous()
+            r_ref = torch.zeros((N - 1, nx), dtype=torch.float64, device="cuda")
+            capi.mgrit_propagate(h, 1, m, N - 1, rho[: N - 1].contiguous(), r_ref)
+            got_c, want_c = c_new[1:].cpu().numpy(), cn_ref.cpu().numpy()
+            got_r, want_r = r[2:].cpu().numpy(), r_ref.cpu().numpy()
+            assert _rel(got_c, want_c) <= TOL, call
+            assert _rel(got_r, want_r) <= TOL, call
+            want_n2 = float((r_ref * r_ref).sum())
+            assert abs(float(norm2.item()) - want_n2) <= TOL * want_n2, call
+            assert float(c_new[0].abs().max()) == 0.0 and float(r[:2].abs().max()) == 0.0
+    finally:
+        capi.mgrit_destroy(h)
+
+
+def test_static_scratch_rejects_oversize_requests(capi):
+    import torch
+    nx = 64
+    big = 65536 + 1
+    dummy = torch.zeros(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(capi.MgritError) as ei:
+        capi.mgrit_fcf_residual_static(dummy, dummy, dummy, dummy, nx, 4, big, [0, -1], [0.15, 0.85])
+    assert ei.value.status == -1
+    assert "65536" in capi.mgrit_last_error()
