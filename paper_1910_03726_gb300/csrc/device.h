@@ -6,15 +6,26 @@
 namespace mg {
 
 constexpr int kMaxDevTaps = 256;
+constexpr int kMaxSpan = 256;
 
-// A circulant stencil passed by value in the kernel parameter space:
+// A circulant stencil passed by value in the kernel parameter space (or
+// copied into shared memory by the batched kernels):
 // (T v)_r = sum_t c[t] v_{r + off[t]}.  lo <= 0 <= hi bound the offsets.
+// The dense form d64/d32 holds the coefficients of offsets lo..hi (zeros for
+// absent offsets) when span = hi - lo + 1 <= kMaxSpan (else span = 0).
+// shift (sigma) is the moving-frame shift used by the sequential march.
 struct DevTaps {
-  int n, lo, hi, pad;
+  int n, lo, hi, span;
+  int shift, pad0, pad1, pad2;
   int off[kMaxDevTaps];
   double c64[kMaxDevTaps];
   float c32[kMaxDevTaps];
+  double d64[kMaxSpan];
+  float d32[kMaxSpan];
 };
+
+// Fill a DevTaps from n (offset, coefficient) pairs; false if n > kMaxDevTaps.
+bool make_dev_taps(const int* off, const double* coef, int n, DevTaps* out);
 
 // FCF-relaxation of one level with the fused C-point residual.
 // Interval j = 1..N starts at C-point j-1.  For every j the kernel computes
@@ -57,6 +68,28 @@ struct CorrectArgs {
 
 cudaError_t launch_fcf(const FcfArgs& a, const DevTaps& t, int precision, int threads,
                        cudaStream_t s);
+
+// Shared-memory slab length for nx points in the padded layout (one pad
+// element per 8 so that per-thread chunks of 8 are bank-conflict free).
+__host__ __device__ inline int padded_len(int nx) { return nx + (nx >> 3) + 1; }
+
+// ------------------------------------------------------------ batched solves
+// One entry per active solve of a batched launch (server).
+struct BatchSolve {
+  FcfArgs fcf;         // level-1 FCF arguments (host updates u_old/c_new per cycle)
+  int prec;            // 0 FP64, 1 mixed
+  int taps;            // index of the fine stencil in the taps array
+  int psi;             // index of the coarse stencil (two-level march)
+  int cluster;         // CTAs per march cluster
+};
+struct BatchItem {
+  int solve, j;        // solve index, interval j (1..N)
+};
+cudaError_t launch_fcf_batched(const BatchSolve* S, const BatchItem* items, int nitems, const DevTaps* taps,
+                               int max_nx, int threads, cudaStream_t s);
+cudaError_t launch_norm_batched(const BatchSolve* S, const int* ids, int count, double* out, cudaStream_t s);
+cudaError_t launch_march_batched(const BatchSolve* S, const int* ids, int count, const DevTaps* taps, int cluster,
+                                 int max_w, int max_halo, cudaStream_t s);
 cudaError_t launch_march(const MarchArgs& a, const DevTaps& t, int cluster, int threads,
                          cudaStream_t s);
 cudaError_t launch_correct(const CorrectArgs& a, const DevTaps& t, int threads, cudaStream_t s);
@@ -65,5 +98,7 @@ cudaError_t launch_add(double* c, const double* e, long long count, cudaStream_t
 cudaError_t launch_propagate(const double* in, double* out, int count, int nx, int k,
                              const DevTaps& t, double* partial, int threads, cudaStream_t s);
 int march_max_cluster();
+void set_tile(int r);   // register tile of the stencil kernels: 8, 4 or 0
+int get_tile();
 
 }  // namespace mg

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -130,15 +131,7 @@ static void release(mgrit_handle* h) {
 
 static DevTaps to_dev(const Taps& t) {
   DevTaps d;
-  std::memset(&d, 0, sizeof(d));
-  d.n = t.size();
-  d.lo = t.lo();
-  d.hi = t.hi();
-  for (int k = 0; k < d.n; ++k) {
-    d.off[k] = t.off[k];
-    d.c64[k] = t.coef[k];
-    d.c32[k] = (float)t.coef[k];
-  }
+  make_dev_taps(t.off.data(), t.coef.data(), t.size(), &d);
   return d;
 }
 
@@ -294,10 +287,13 @@ extern "C" mgrit_status mgrit_psi_plan(const mgrit_problem* prob, const mgrit_op
 
 // ------------------------------------------------------------------- setup
 
+// Cluster size of the march: the largest power of two <= 16 dividing nx with
+// at least 64 points per CTA and a CTA at least as wide as the stencil (the
+// march runs in the stencil's moving frame, so only the width matters).
 static int pick_cluster(int nx, const Taps& t) {
-  int reach = std::max(-t.lo(), t.hi());
+  const int width = t.hi() - t.lo();
   for (int cs = march_max_cluster(); cs > 1; cs >>= 1)
-    if (nx % cs == 0 && nx / cs >= std::max(64, reach)) return cs;
+    if (nx % cs == 0 && nx / cs >= std::max(64, width)) return cs;
   return 1;
 }
 
@@ -393,7 +389,8 @@ extern "C" mgrit_status mgrit_setup(const mgrit_problem* prob, const mgrit_opts*
     delete h;
     return fail(MGRIT_ERR_OOM, "pinned host buffer");
   }
-  h->fcf_threads = nx >= 2048 ? 512 : (nx >= 512 ? 256 : 128);
+  h->fcf_threads = 0;  // chosen per launch from nx and the register tile
+  if (const char* tile = std::getenv("MGRIT_TILE")) set_tile(std::atoi(tile));
   const Taps& coarsest = h->ops.back().taps;
   h->march_cluster = pick_cluster(nx, coarsest);
   h->march_threads = std::min(256, nx / h->march_cluster);

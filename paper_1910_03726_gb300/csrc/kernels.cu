@@ -1,12 +1,16 @@
 // CUDA kernels (sm_103a) of the MGRIT hot path for periodic advection:
-//   fcf_kernel      FCF-relaxation + fused C-point residual (Section 2.2)
-//   march_kernel    sequential march u_n = T u_{n-1} + g_n on a thread-block
-//                   cluster (coarse solve, Eq. 5; sequential stepping, Eq. 3)
-//   correct_kernel  coarse-level correction + F-relaxation (ideal interpolation)
-//   norm_kernel     deterministic residual 2-norm (Section 2.2 stopping test)
-//   propagate_kernel  T^k applied to a batch of vectors
+//   fcf_kernel / fcf_batched_kernel   FCF-relaxation + fused C-point residual
+//                                     (Section 2.2), one CTA per coarse interval
+//   march_kernel / march_batched_kernel  sequential march u_n = T u_{n-1} + g_n on
+//                                     a thread-block cluster (coarse solve, Eq. 5;
+//                                     sequential stepping, Eq. 3)
+//   correct_kernel                    correction + F-relaxation (ideal interpolation)
+//   norm_kernel / norm_batched_kernel deterministic residual 2-norm (stopping test)
+//   propagate_kernel                  T^k applied to a batch of vectors
 // Every stencil is a circulant (Corollary 1): periodic indices wrap modulo nx.
 #include <cooperative_groups.h>
+
+#include <cstring>
 
 #include "device.h"
 
@@ -14,27 +18,97 @@ namespace cg = cooperative_groups;
 
 namespace mg {
 
+bool make_dev_taps(const int* off, const double* coef, int n, DevTaps* d) {
+  if (n < 1 || n > kMaxDevTaps) return false;
+  std::memset(d, 0, sizeof(*d));
+  d->n = n;
+  int lo = off[0], hi = off[0];
+  for (int k = 0; k < n; ++k) {
+    d->off[k] = off[k];
+    d->c64[k] = coef[k];
+    d->c32[k] = (float)coef[k];
+    lo = off[k] < lo ? off[k] : lo;
+    hi = off[k] > hi ? off[k] : hi;
+  }
+  d->lo = lo;
+  d->hi = hi;
+  d->span = hi - lo + 1 <= kMaxSpan ? hi - lo + 1 : 0;
+  if (d->span)
+    for (int k = 0; k < n; ++k) d->d64[off[k] - lo] += coef[k];
+  for (int k = 0; k < d->span; ++k) d->d32[k] = (float)d->d64[k];
+  // frame shift for the march: centre of the offsets (floor)
+  d->shift = (lo + hi) >= 0 ? (lo + hi) / 2 : -((-(lo + hi) + 1) / 2);
+  return true;
+}
+
 __device__ __forceinline__ int wrapi(int k, int nx) {
   k = (k < 0) ? k + nx : k;
   return (k >= nx) ? k - nx : k;
 }
 
-template <typename T>
-__device__ __forceinline__ T tap_coef(const DevTaps& t, int k);
-template <>
-__device__ __forceinline__ double tap_coef<double>(const DevTaps& t, int k) { return t.c64[k]; }
-template <>
-__device__ __forceinline__ float tap_coef<float>(const DevTaps& t, int k) { return t.c32[k]; }
+// Padded shared-memory index: one pad element after every 8, so that threads
+// owning consecutive chunks of 8 elements hit distinct banks.
+__device__ __forceinline__ int pidx(int e) { return e + (e >> 3); }
 
-// dst[i] = g[i] + sum_t c_t src[(i + off_t) mod nx] over the whole slab.
 template <typename T>
-__device__ __forceinline__ void slab_step(const DevTaps& t, const T* __restrict__ src, T* __restrict__ dst,
-                                          const double* __restrict__ g, int nx) {
+__device__ __forceinline__ T sparse_coef(const DevTaps& t, int k);
+template <>
+__device__ __forceinline__ double sparse_coef<double>(const DevTaps& t, int k) { return t.c64[k]; }
+template <>
+__device__ __forceinline__ float sparse_coef<float>(const DevTaps& t, int k) { return t.c32[k]; }
+template <typename T>
+__device__ __forceinline__ T dense_coef(const DevTaps& t, int k);
+template <>
+__device__ __forceinline__ double dense_coef<double>(const DevTaps& t, int k) { return t.d64[k]; }
+template <>
+__device__ __forceinline__ float dense_coef<float>(const DevTaps& t, int k) { return t.d32[k]; }
+
+// dst = T src (+ g): one tap at a time, any offsets (padded layout).
+template <typename T>
+__device__ __forceinline__ void step_sparse(const DevTaps& t, const T* __restrict__ src, T* __restrict__ dst,
+                                           const double* __restrict__ g, int nx) {
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     T acc = g ? (T)__ldg(g + i) : (T)0;
-    for (int k = 0; k < t.n; ++k) acc = fma(tap_coef<T>(t, k), src[wrapi(i + t.off[k], nx)], acc);
-    dst[i] = acc;
+    for (int k = 0; k < t.n; ++k) acc = fma(sparse_coef<T>(t, k), src[pidx(wrapi(i + t.off[k], nx))], acc);
+    dst[pidx(i)] = acc;
   }
+}
+
+// dst = T src (+ g), register-tiled: each thread produces R consecutive
+// outputs from a sliding window of R inputs that advances one offset per tap,
+// so each tap costs one shared load and R FMAs.  Needs the dense form and
+// nx >= 64 (so that every index below wraps at most once).
+template <typename T, int R>
+__device__ __forceinline__ void step_tiled(const DevTaps& t, const T* __restrict__ src, T* __restrict__ dst,
+                                           const double* __restrict__ g, int nx) {
+  const int lo = t.lo, span = t.span;
+  for (int i0 = threadIdx.x * R; i0 < nx; i0 += blockDim.x * R) {
+    T acc[R], w[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      acc[r] = (g && i0 + r < nx) ? (T)__ldg(g + i0 + r) : (T)0;
+      w[r] = src[pidx(wrapi(i0 + lo + r, nx))];
+    }
+    for (int k = 0; k < span; ++k) {
+      const T c = dense_coef<T>(t, k);
+      if (c != (T)0) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = fma(c, w[r], acc[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < R - 1; ++r) w[r] = w[r + 1];
+      w[R - 1] = src[pidx(wrapi(i0 + lo + k + R, nx))];
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (i0 + r < nx) dst[pidx(i0 + r)] = acc[r];
+  }
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void slab_step(const DevTaps& t, const T* src, T* dst, const double* g, int nx) {
+  if constexpr (R > 0) step_tiled<T, R>(t, src, dst, g, nx);
+  else step_sparse<T>(t, src, dst, g, nx);
 }
 
 // Sum over the block in a fixed order (deterministic); result valid in thread 0.
@@ -53,24 +127,22 @@ __device__ double block_sum(double v) {
 }
 
 // ----------------------------------------------------------------------------
-// FCF-relaxation with the fused residual.  One CTA per coarse interval; the
-// interval's slab lives in shared memory for all 2m fine steps, so each C-point
-// crosses HBM once per cycle.  PREC 0: both passes FP64.  PREC 1: the second
-// pass (acting on the correction rho) in FP32.
+// FCF-relaxation with the fused residual for interval j.  The interval's slab
+// lives in shared memory for all 2m fine steps, so each C-point crosses HBM
+// once per cycle.  PREC 0: both passes FP64.  PREC 1: the second pass (acting
+// on the correction rho) in FP32.
 // ----------------------------------------------------------------------------
-template <int PREC>
-__global__ void __launch_bounds__(1024) fcf_kernel(const FcfArgs a, const DevTaps t) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int nx = a.nx, m = a.m;
-  const int j = blockIdx.x + 1;
+template <int PREC, int R>
+__device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const DevTaps& t, unsigned char* smraw) {
+  const int nx = a.nx, m = a.m, plen = padded_len(nx);
   double* b0 = reinterpret_cast<double*>(smraw);
-  double* b1 = b0 + nx;
+  double* b1 = b0 + plen;
   const double* start = a.u_old + (long long)(j - 1) * a.cstride;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) b0[i] = a.zero_old ? 0.0 : start[i];
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) b0[pidx(i)] = a.zero_old ? 0.0 : start[i];
   __syncthreads();
   for (int s = 1; s <= m; ++s) {
     const double* g = a.g ? a.g + ((long long)(j - 1) * m + s) * nx : nullptr;
-    slab_step<double>(t, b0, b1, g, nx);
+    slab_step<double, R>(t, b0, b1, g, nx);
     __syncthreads();
     double* tmp = b0; b0 = b1; b1 = tmp;
   }
@@ -80,43 +152,43 @@ __global__ void __launch_bounds__(1024) fcf_kernel(const FcfArgs a, const DevTap
   double ss = 0.0;
   if (PREC == 0) {
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const double v = b0[i];
+      const double v = b0[pidx(i)];
       cn[i] = v;
-      b1[i] = v - (a.zero_old ? 0.0 : oldj[i]);
+      b1[pidx(i)] = v - (a.zero_old ? 0.0 : oldj[i]);
     }
     __syncthreads();
     if (!more) return;
     double* x0 = b1;
     double* x1 = b0;
     for (int s = 1; s <= m; ++s) {
-      slab_step<double>(t, x0, x1, nullptr, nx);
+      slab_step<double, R>(t, x0, x1, nullptr, nx);
       __syncthreads();
       double* tmp = x0; x0 = x1; x1 = tmp;
     }
     double* rr = a.r + (long long)(j + 1) * nx;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const double v = x0[i];
+      const double v = x0[pidx(i)];
       rr[i] = v;
       ss = fma(v, v, ss);
     }
   } else {
     float* f0 = reinterpret_cast<float*>(b1);
-    float* f1 = f0 + nx;
+    float* f1 = f0 + plen;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const double v = b0[i];
+      const double v = b0[pidx(i)];
       cn[i] = v;
-      f0[i] = (float)(v - (a.zero_old ? 0.0 : oldj[i]));
+      f0[pidx(i)] = (float)(v - (a.zero_old ? 0.0 : oldj[i]));
     }
     __syncthreads();
     if (!more) return;
     for (int s = 1; s <= m; ++s) {
-      slab_step<float>(t, f0, f1, nullptr, nx);
+      slab_step<float, R>(t, f0, f1, nullptr, nx);
       __syncthreads();
       float* tmp = f0; f0 = f1; f1 = tmp;
     }
     double* rr = a.r + (long long)(j + 1) * nx;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const double v = (double)f0[i];
+      const double v = (double)f0[pidx(i)];
       rr[i] = v;
       ss = fma(v, v, ss);
     }
@@ -127,101 +199,172 @@ __global__ void __launch_bounds__(1024) fcf_kernel(const FcfArgs a, const DevTap
   }
 }
 
+template <int PREC, int R>
+__global__ void __launch_bounds__(R == 8 ? 512 : 1024) fcf_kernel(const FcfArgs a, const DevTaps t) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  fcf_body<PREC, R>(a, blockIdx.x + 1, t, smraw);
+}
+
+// Batched: one CTA per (solve, interval) item across all admitted solves; the
+// solve's stencil is copied into shared memory first.
+template <int R>
+__global__ void __launch_bounds__(R == 8 ? 512 : 1024) fcf_batched_kernel(const BatchSolve* __restrict__ S,
+                                                            const BatchItem* __restrict__ items,
+                                                            const DevTaps* __restrict__ taps) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ __align__(16) DevTaps st;
+  const BatchItem it = items[blockIdx.x];
+  const BatchSolve* s = S + it.solve;
+  const int* src = reinterpret_cast<const int*>(taps + s->taps);
+  int* dst = reinterpret_cast<int*>(&st);
+  for (int k = threadIdx.x; k < (int)(sizeof(DevTaps) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
+  __syncthreads();
+  const FcfArgs a = s->fcf;
+  if (s->prec == 0) fcf_body<0, R>(a, it.j, st, smraw);
+  else fcf_body<1, R>(a, it.j, st, smraw);
+}
+
 // ----------------------------------------------------------------------------
-// Sequential march on one thread-block cluster.  CTA `rank` owns x in
-// [rank*w, (rank+1)*w); its shared buffer holds [left halo | own | right halo].
-// Per step: compute own points, cluster barrier, pull halos from the owning
-// CTAs' shared memory (DSMEM), block barrier.  Two buffers alternate so a
-// neighbour's reads of step n never meet its writes of step n+1.
+// Sequential march on one thread-block cluster, in a frame that moves with the
+// stencil: the shared buffers hold B_n[x] = u_n[(x + S_n) mod nx] with
+// S_n = -n*sigma, sigma the centre of the stencil's offsets, so that
+// B_n[x] = sum_k c_k B_{n-1}[x + off_k - sigma] + g_n[x + S_n] needs halos of
+// the stencil's width only, not of its (characteristic) shift.  CTA `rank`
+// owns frame positions [rank*w, (rank+1)*w); its buffer holds
+// [left halo | own | right halo].  Per step: compute, cluster barrier, pull
+// halos from the owners' shared memory (DSMEM), block barrier.  Two buffers
+// alternate so a neighbour's reads of step n never meet its writes of n+1.
 // The next step's g and c_add values are loaded one step ahead.
 // ----------------------------------------------------------------------------
+__device__ __forceinline__ int modnx(long long v, int nx) {
+  long long r = v % nx;
+  return (int)(r < 0 ? r + nx : r);
+}
+
 template <int PPT>
-__global__ void __launch_bounds__(256) march_kernel(const MarchArgs a, const DevTaps t) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  cg::cluster_group cl = cg::this_cluster();
+__device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t, unsigned char* smraw,
+                                           cg::cluster_group& cl) {
   const int cs = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const int nx = a.nx, w = nx / cs, base = rank * w;
-  const int L = -t.lo, R = t.hi, W = L + w + R;
+  const int sigma = t.shift;
+  const int L = sigma - t.lo, R = t.hi - sigma, W = L + w + R;
   double* B0 = reinterpret_cast<double*>(smraw);
   double* B1 = B0 + W;
   const int tid = threadIdx.x, bs = blockDim.x;
   for (int k = tid; k < W; k += bs) {
-    const int gi = wrapi(base - L + k, nx);
+    const int gi = modnx((long long)base - L + k, nx);
     B0[k] = a.init ? a.init[gi] : 0.0;
   }
   __syncthreads();
   double gq[PPT], cq[PPT];
 #pragma unroll
   for (int p = 0; p < PPT; ++p) { gq[p] = 0.0; cq[p] = 0.0; }
-  auto prefetch = [&](int n) {
+  auto prefetch = [&](int n, int Sn) {
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
       const int i = tid + p * bs;
       if (i < w) {
-        const long long o = (long long)n * nx + base + i;
+        const long long o = (long long)n * nx + wrapi(base + i + Sn, nx);
         if (a.g) gq[p] = __ldcg(a.g + o);
         if (a.c_add) cq[p] = __ldcg(a.c_add + o);
       }
     }
   };
-  if (a.P > 1) prefetch(1);
+  int S = modnx(-(long long)sigma, nx);  // S_1
+  if (a.P > 1) prefetch(1, S);
   for (int n = 1; n < a.P; ++n) {
     double* cur = (n & 1) ? B0 : B1;
     double* nxt = (n & 1) ? B1 : B0;
     double gc[PPT], cc[PPT];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) { gc[p] = gq[p]; cc[p] = cq[p]; }
-    if (n + 1 < a.P) prefetch(n + 1);
+    const int Snext = modnx((long long)S - sigma, nx);
+    if (n + 1 < a.P) prefetch(n + 1, Snext);
     const bool store = a.u_out && (n % a.store_every) == 0;
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
       const int i = tid + p * bs;
       if (i < w) {
         double acc = gc[p];
-        const double* c = cur + L + i;
+        const double* c = cur + L + i - sigma;
         for (int k = 0; k < t.n; ++k) acc = fma(t.c64[k], c[t.off[k]], acc);
         nxt[L + i] = acc;
-        const long long o = (long long)n * nx + base + i;
-        if (a.c_add) a.c_add[o] = cc[p] + acc;
-        if (store) a.u_out[(long long)(n / a.store_every) * nx + base + i] = acc;
+        const int gi = wrapi(base + i + S, nx);
+        if (a.c_add) a.c_add[(long long)n * nx + gi] = cc[p] + acc;
+        if (store) a.u_out[(long long)(n / a.store_every) * nx + gi] = acc;
       }
     }
     cl.sync();
     for (int k = tid; k < L + R; k += bs) {
-      int dst, gi;
-      if (k < L) { dst = k; gi = base - L + k; }
-      else { dst = w + k; gi = base + w + (k - L); }
-      gi = wrapi(gi, nx);
-      const int owner = gi / w, loc = gi - owner * w;
+      int dst, fi;
+      if (k < L) { dst = k; fi = base - L + k; }
+      else { dst = w + k; fi = base + w + (k - L); }
+      fi = modnx(fi, nx);
+      const int owner = fi / w, loc = fi - owner * w;
       const double* rem = cl.map_shared_rank(nxt, owner);
       nxt[dst] = rem[L + loc];
     }
     __syncthreads();
+    S = Snext;
   }
   cl.sync();  // no CTA leaves while a neighbour may still read its shared memory
 }
 
-// ----------------------------------------------------------------------------
-// Correction + F-relaxation of a coarse level (ideal interpolation).
-// ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) correct_kernel(const CorrectArgs a, const DevTaps t) {
+template <int PPT>
+__global__ void __launch_bounds__(256) march_kernel(const MarchArgs a, const DevTaps t) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int nx = a.nx, m = a.m, j = blockIdx.x + 1;
+  cg::cluster_group cl = cg::this_cluster();
+  march_body<PPT>(a, t, smraw, cl);
+}
+
+// Batched two-level coarse solve: cluster c marches solve ids[c] with its
+// coarse stencil and adds e_j into its new C-points.
+template <int PPT>
+__global__ void __launch_bounds__(256) march_batched_kernel(const BatchSolve* __restrict__ S,
+                                                             const int* __restrict__ ids,
+                                                             const DevTaps* __restrict__ taps) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ __align__(16) DevTaps st;
+  cg::cluster_group cl = cg::this_cluster();
+  const int c = blockIdx.x / (int)cl.num_blocks();
+  const BatchSolve* s = S + ids[c];
+  const int* src = reinterpret_cast<const int*>(taps + s->psi);
+  int* dst = reinterpret_cast<int*>(&st);
+  for (int k = threadIdx.x; k < (int)(sizeof(DevTaps) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
+  __syncthreads();
+  MarchArgs a = {};
+  a.init = nullptr;
+  a.g = s->fcf.r;
+  a.u_out = nullptr;
+  a.store_every = 1;
+  a.c_add = s->fcf.c_new;
+  a.nx = s->fcf.nx;
+  a.P = s->fcf.N + 1;
+  march_body<PPT>(a, st, smraw, cl);
+}
+
+// ----------------------------------------------------------------------------
+// Correction + F-relaxation of a level (ideal interpolation).
+// ----------------------------------------------------------------------------
+template <int R>
+__global__ void __launch_bounds__(R == 8 ? 512 : 1024) correct_kernel(const CorrectArgs a, const DevTaps t) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int nx = a.nx, m = a.m, j = blockIdx.x + 1, plen = padded_len(nx);
   double* b0 = reinterpret_cast<double*>(smraw);
-  double* b1 = b0 + nx;
+  double* b1 = b0 + plen;
   const long long p0 = (long long)(j - 1) * m;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     const double v = a.c_new[(long long)(j - 1) * nx + i] + (a.e ? a.e[(long long)(j - 1) * nx + i] : 0.0);
-    b0[i] = v;
+    b0[pidx(i)] = v;
     a.u[p0 * nx + i] = v;
   }
   __syncthreads();
   for (int s = 1; s < m; ++s) {
     const double* g = a.g ? a.g + (p0 + s) * nx : nullptr;
-    slab_step<double>(t, b0, b1, g, nx);
+    slab_step<double, R>(t, b0, b1, g, nx);
     __syncthreads();
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) a.u[(p0 + s) * nx + i] = b1[i];
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) a.u[(p0 + s) * nx + i] = b1[pidx(i)];
     double* tmp = b0; b0 = b1; b1 = tmp;
   }
   if (j == a.N)
@@ -236,29 +379,42 @@ __global__ void __launch_bounds__(1024) norm_kernel(const double* __restrict__ p
   if (threadIdx.x == 0) out[0] = v;
 }
 
+__global__ void __launch_bounds__(1024) norm_batched_kernel(const BatchSolve* __restrict__ S,
+                                                            const int* __restrict__ ids, double* out) {
+  const BatchSolve* s = S + ids[blockIdx.x];
+  const double* partial = s->fcf.partial;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < s->fcf.N; i += blockDim.x) v += partial[i];
+  v = block_sum(v);
+  if (threadIdx.x == 0) out[blockIdx.x] = v;
+}
+
 __global__ void add_kernel(double* __restrict__ c, const double* __restrict__ e, long long count) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x)
     c[i] += e[i];
 }
 
-__global__ void __launch_bounds__(1024) propagate_kernel(const double* in, double* out, int nx, int k,
+template <int R>
+__global__ void __launch_bounds__(R == 8 ? 512 : 1024) propagate_kernel(const double* in, double* out, int nx, int k,
                                                          const DevTaps t, double* partial) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  const int plen = padded_len(nx);
   double* b0 = reinterpret_cast<double*>(smraw);
-  double* b1 = b0 + nx;
+  double* b1 = b0 + plen;
   const long long v = blockIdx.x;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) b0[i] = in[v * nx + i];
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) b0[pidx(i)] = in[v * nx + i];
   __syncthreads();
   for (int s = 0; s < k; ++s) {
-    slab_step<double>(t, b0, b1, nullptr, nx);
+    slab_step<double, R>(t, b0, b1, nullptr, nx);
     __syncthreads();
     double* tmp = b0; b0 = b1; b1 = tmp;
   }
   double ss = 0.0;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    out[v * nx + i] = b0[i];
-    ss = fma(b0[i], b0[i], ss);
+    const double x = b0[pidx(i)];
+    out[v * nx + i] = x;
+    ss = fma(x, x, ss);
   }
   if (partial) {
     ss = block_sum(ss);
@@ -268,39 +424,81 @@ __global__ void __launch_bounds__(1024) propagate_kernel(const double* in, doubl
 
 // ------------------------------------------------------------------ launches
 
+static int g_tile = 8;  // register tile of the stencil (0 = one tap at a time)
+
+void set_tile(int r) { g_tile = (r == 4 || r == 8) ? r : 0; }
+int get_tile() { return g_tile; }
+
+static int tile_for(const DevTaps& t, int nx) { return (t.span > 0 && nx >= 64) ? g_tile : 0; }
+
+static int threads_for(int nx, int R, int hint) {
+  const int cap = 512;
+  if (hint > 0) return hint < cap ? hint : cap;
+  const int per = R > 0 ? R : 4;
+  int th = (nx + per - 1) / per;
+  th = ((th + 31) / 32) * 32;
+  return th < 32 ? 32 : (th > cap ? cap : th);
+}
+
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
   if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   return cudaSuccess;
 }
 
-cudaError_t launch_fcf(const FcfArgs& a, const DevTaps& t, int precision, int threads, cudaStream_t s) {
-  if (a.N < 1) return cudaSuccess;
-  const size_t smem = 2 * (size_t)a.nx * sizeof(double);
-  cudaError_t e;
-  if (precision == 0) {
-    if ((e = set_smem(fcf_kernel<0>, smem)) != cudaSuccess) return e;
-    fcf_kernel<0><<<a.N, threads, smem, s>>>(a, t);
-  } else {
-    if ((e = set_smem(fcf_kernel<1>, smem)) != cudaSuccess) return e;
-    fcf_kernel<1><<<a.N, threads, smem, s>>>(a, t);
-  }
+template <int PREC, int R>
+static cudaError_t launch_fcf_t(const FcfArgs& a, const DevTaps& t, int threads, cudaStream_t s) {
+  const size_t smem = 2 * (size_t)padded_len(a.nx) * sizeof(double);
+  cudaError_t e = set_smem(fcf_kernel<PREC, R>, smem);
+  if (e != cudaSuccess) return e;
+  fcf_kernel<PREC, R><<<a.N, threads_for(a.nx, R, threads), smem, s>>>(a, t);
   return cudaGetLastError();
 }
 
-template <int PPT>
-static cudaError_t launch_march_t(const MarchArgs& a, const DevTaps& t, int cluster, int threads,
-                                  cudaStream_t s) {
-  const int w = a.nx / cluster;
-  const size_t smem = 2 * (size_t)(w - t.lo + t.hi) * sizeof(double);
-  cudaError_t e = set_smem(march_kernel<PPT>, smem);
+cudaError_t launch_fcf(const FcfArgs& a, const DevTaps& t, int precision, int threads, cudaStream_t s) {
+  if (a.N < 1) return cudaSuccess;
+  const int R = tile_for(t, a.nx);
+  if (precision == 0) {
+    if (R == 8) return launch_fcf_t<0, 8>(a, t, threads, s);
+    if (R == 4) return launch_fcf_t<0, 4>(a, t, threads, s);
+    return launch_fcf_t<0, 0>(a, t, threads, s);
+  }
+  if (R == 8) return launch_fcf_t<1, 8>(a, t, threads, s);
+  if (R == 4) return launch_fcf_t<1, 4>(a, t, threads, s);
+  return launch_fcf_t<1, 0>(a, t, threads, s);
+}
+
+template <int R>
+static cudaError_t launch_fcf_batched_t(const BatchSolve* S, const BatchItem* items, int nitems, const DevTaps* taps,
+                                        int max_nx, int threads, cudaStream_t s) {
+  const size_t smem = 2 * (size_t)padded_len(max_nx) * sizeof(double);
+  cudaError_t e = set_smem(fcf_batched_kernel<R>, smem);
+  if (e != cudaSuccess) return e;
+  fcf_batched_kernel<R><<<nitems, threads, smem, s>>>(S, items, taps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fcf_batched(const BatchSolve* S, const BatchItem* items, int nitems, const DevTaps* taps,
+                               int max_nx, int threads, cudaStream_t s) {
+  if (nitems < 1) return cudaSuccess;
+  // threads < 0 selects the one-tap-at-a-time path (batches whose stencils
+  // have no dense form or whose nx < 64)
+  if (threads > 0 && g_tile == 8) return launch_fcf_batched_t<8>(S, items, nitems, taps, max_nx, threads, s);
+  if (threads > 0 && g_tile == 4) return launch_fcf_batched_t<4>(S, items, nitems, taps, max_nx, threads, s);
+  return launch_fcf_batched_t<0>(S, items, nitems, taps, max_nx, threads > 0 ? threads : -threads, s);
+}
+
+template <typename K>
+static cudaError_t launch_cluster(K kernel, int grid, int cluster, int threads, size_t smem, cudaStream_t s,
+                                  void** args) {
+  cudaError_t e = set_smem(kernel, smem);
   if (e != cudaSuccess) return e;
   if (cluster > 8) {
-    e = cudaFuncSetAttribute(march_kernel<PPT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(cluster);
+  cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
@@ -311,7 +509,17 @@ static cudaError_t launch_march_t(const MarchArgs& a, const DevTaps& t, int clus
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, march_kernel<PPT>, a, t);
+  return cudaLaunchKernelExC(&cfg, (const void*)kernel, args);
+}
+
+template <int PPT>
+static cudaError_t launch_march_t(const MarchArgs& a, const DevTaps& t, int cluster, int threads, cudaStream_t s) {
+  const int w = a.nx / cluster;
+  const size_t smem = 2 * (size_t)(w + t.hi - t.lo) * sizeof(double);
+  MarchArgs aa = a;
+  DevTaps tt = t;
+  void* args[] = {&aa, &tt};
+  return launch_cluster(march_kernel<PPT>, cluster, cluster, threads, smem, s, args);
 }
 
 cudaError_t launch_march(const MarchArgs& a, const DevTaps& t, int cluster, int threads, cudaStream_t s) {
@@ -329,19 +537,61 @@ cudaError_t launch_march(const MarchArgs& a, const DevTaps& t, int cluster, int 
   }
 }
 
+template <int PPT>
+static cudaError_t launch_march_batched_t(const BatchSolve* S, const int* ids, int count, const DevTaps* taps,
+                                          int cluster, int max_w, int max_halo, cudaStream_t s) {
+  const size_t smem = 2 * (size_t)(max_w + max_halo) * sizeof(double);
+  const BatchSolve* SS = S;
+  const int* ii = ids;
+  const DevTaps* tt = taps;
+  void* args[] = {&SS, &ii, &tt};
+  const int threads = max_w < 256 ? ((max_w + 31) / 32) * 32 : 256;
+  return launch_cluster(march_batched_kernel<PPT>, count * cluster, cluster, threads, smem, s, args);
+}
+
+cudaError_t launch_march_batched(const BatchSolve* S, const int* ids, int count, const DevTaps* taps, int cluster,
+                                 int max_w, int max_halo, cudaStream_t s) {
+  if (count < 1) return cudaSuccess;
+  const int threads = max_w < 256 ? ((max_w + 31) / 32) * 32 : 256;
+  const int ppt = (max_w + threads - 1) / threads;
+  switch (ppt) {
+    case 1: return launch_march_batched_t<1>(S, ids, count, taps, cluster, max_w, max_halo, s);
+    case 2: return launch_march_batched_t<2>(S, ids, count, taps, cluster, max_w, max_halo, s);
+    case 3: case 4: return launch_march_batched_t<4>(S, ids, count, taps, cluster, max_w, max_halo, s);
+    case 5: case 6: case 7: case 8: return launch_march_batched_t<8>(S, ids, count, taps, cluster, max_w, max_halo, s);
+    default:
+      if (ppt <= 16) return launch_march_batched_t<16>(S, ids, count, taps, cluster, max_w, max_halo, s);
+      return cudaErrorInvalidConfiguration;
+  }
+}
+
 int march_max_cluster() { return 16; }
+
+template <int R>
+static cudaError_t launch_correct_t(const CorrectArgs& a, const DevTaps& t, int threads, cudaStream_t s) {
+  const size_t smem = 2 * (size_t)padded_len(a.nx) * sizeof(double);
+  cudaError_t e = set_smem(correct_kernel<R>, smem);
+  if (e != cudaSuccess) return e;
+  correct_kernel<R><<<a.N, threads_for(a.nx, R, threads), smem, s>>>(a, t);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_correct(const CorrectArgs& a, const DevTaps& t, int threads, cudaStream_t s) {
   if (a.N < 1) return cudaSuccess;
-  const size_t smem = 2 * (size_t)a.nx * sizeof(double);
-  cudaError_t e = set_smem(correct_kernel, smem);
-  if (e != cudaSuccess) return e;
-  correct_kernel<<<a.N, threads, smem, s>>>(a, t);
-  return cudaGetLastError();
+  const int R = tile_for(t, a.nx);
+  if (R == 8) return launch_correct_t<8>(a, t, threads, s);
+  if (R == 4) return launch_correct_t<4>(a, t, threads, s);
+  return launch_correct_t<0>(a, t, threads, s);
 }
 
 cudaError_t launch_norm(const double* partial, int n, double* out, cudaStream_t s) {
   norm_kernel<<<1, 1024, 0, s>>>(partial, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm_batched(const BatchSolve* S, const int* ids, int count, double* out, cudaStream_t s) {
+  if (count < 1) return cudaSuccess;
+  norm_batched_kernel<<<count, 256, 0, s>>>(S, ids, out);
   return cudaGetLastError();
 }
 
@@ -353,14 +603,23 @@ cudaError_t launch_add(double* c, const double* e, long long count, cudaStream_t
   return cudaGetLastError();
 }
 
+template <int R>
+static cudaError_t launch_propagate_t(const double* in, double* out, int count, int nx, int k, const DevTaps& t,
+                                      double* partial, int threads, cudaStream_t s) {
+  const size_t smem = 2 * (size_t)padded_len(nx) * sizeof(double);
+  cudaError_t e = set_smem(propagate_kernel<R>, smem);
+  if (e != cudaSuccess) return e;
+  propagate_kernel<R><<<count, threads_for(nx, R, threads), smem, s>>>(in, out, nx, k, t, partial);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_propagate(const double* in, double* out, int count, int nx, int k, const DevTaps& t,
                              double* partial, int threads, cudaStream_t s) {
   if (count < 1) return cudaSuccess;
-  const size_t smem = 2 * (size_t)nx * sizeof(double);
-  cudaError_t e = set_smem(propagate_kernel, smem);
-  if (e != cudaSuccess) return e;
-  propagate_kernel<<<count, threads, smem, s>>>(in, out, nx, k, t, partial);
-  return cudaGetLastError();
+  const int R = tile_for(t, nx);
+  if (R == 8) return launch_propagate_t<8>(in, out, count, nx, k, t, partial, threads, s);
+  if (R == 4) return launch_propagate_t<4>(in, out, count, nx, k, t, partial, threads, s);
+  return launch_propagate_t<0>(in, out, count, nx, k, t, partial, threads, s);
 }
 
 }  // namespace mg
