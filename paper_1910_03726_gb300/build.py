@@ -19,8 +19,8 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmgrit_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["kernels.cu", "setup.cpp", "driver.cpp", "noalloc.cu"]
-HEADERS = ["device.h", "setup.h"]
+SOURCES = ["kernels.cu", "setup.cpp", "driver.cpp", "server.cpp", "noalloc.cu"]
+HEADERS = ["device.h", "setup.h", "handle.h"]
 
 
 def nvcc() -> str:

@@ -14,6 +14,7 @@
 
 #include "../../include/mgrit.h"
 #include "device.h"
+#include "handle.h"
 #include "setup.h"
 
 using namespace mg;
@@ -22,7 +23,7 @@ using namespace mg;
 
 static thread_local std::string g_err;
 
-static mgrit_status fail(mgrit_status s, const std::string& msg) {
+mgrit_status fail(mgrit_status s, const std::string& msg) {
   g_err = msg;
   return s;
 }
@@ -51,46 +52,13 @@ extern "C" void mgrit_set_allocator(mgrit_alloc_fn a, mgrit_free_fn f, void* ctx
   g_alloc_ctx = ctx;
 }
 
-struct DevBuf {
-  double* p = nullptr;
-  size_t n = 0;
-  mgrit_free_fn freefn = nullptr;
-  void* ctx = nullptr;
-};
-
-static double now_s() {
+double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
 // ------------------------------------------------------------------- handle
 
-struct mgrit_handle {
-  mgrit_problem prob;
-  mgrit_opts opts;
-  cudaStream_t stream = nullptr;
-  int nx = 0, nt = 0, m = 0, L = 0;
-  std::vector<int> Nl;            // Nl[l] intervals of level l (l = 1..L-1)
-  Taps phi;                       // fine propagator (ERK, collapsed)
-  std::vector<CoarseOp> ops;      // ops[l-2] = Psi_l, l = 2..L
-  DevTaps dphi;
-  std::vector<DevTaps> dpsi;      // dpsi[l-2]
-  std::vector<DevBuf> bufs;       // everything allocated, for release
-  double* c[2] = {nullptr, nullptr};
-  std::vector<double*> r, u, cnew;  // indexed by level (size L+1)
-  double* partial = nullptr;
-  double* scratch = nullptr;      // 2*nx + 1 doubles
-  double* norm_host = nullptr;    // pinned
-  int fcf_threads = 512, march_cluster = 1, march_threads = 256;
-  // per-solve launch accounting (and CUDA-event timing with MGRIT_FLAG_TIME_KERNELS)
-  int kcount[MGRIT_K_KINDS] = {0};
-  std::vector<cudaEvent_t> evpool;
-  std::vector<int> evkind;      // kind of each recorded (start, stop) pair
-  size_t evused = 0;
-  double setup_s = 0.0, op_complexity = 0.0;
-  size_t bytes = 0;
-};
-
-static mgrit_status dalloc(mgrit_handle* h, size_t count, double** out) {
+mgrit_status dalloc(mgrit_handle* h, size_t count, double** out) {
   const size_t bytes = std::max<size_t>(count, 1) * sizeof(double);
   void* p = nullptr;
   DevBuf b;
@@ -115,7 +83,7 @@ static mgrit_status dalloc(mgrit_handle* h, size_t count, double** out) {
   return MGRIT_OK;
 }
 
-static void release(mgrit_handle* h) {
+void release(mgrit_handle* h) {
   for (auto& b : h->bufs) {
     if (!b.p) continue;
     if (b.freefn) b.freefn(b.p, (void*)h->stream, b.ctx);
@@ -129,13 +97,13 @@ static void release(mgrit_handle* h) {
   cudaStreamSynchronize(h->stream);
 }
 
-static DevTaps to_dev(const Taps& t) {
+DevTaps to_dev(const Taps& t) {
   DevTaps d;
   make_dev_taps(t.off.data(), t.coef.data(), t.size(), &d);
   return d;
 }
 
-static bool is_device_ptr(const void* p) {
+bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
@@ -144,10 +112,10 @@ static bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-static cudaMemcpyKind kind_to_dev(const void* src) {
+cudaMemcpyKind kind_to_dev(const void* src) {
   return is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
 }
-static cudaMemcpyKind kind_from_dev(const void* dst) {
+cudaMemcpyKind kind_from_dev(const void* dst) {
   return is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
 }
 
@@ -173,7 +141,7 @@ extern "C" int32_t mgrit_abi_version(void) { return MGRIT_ABI_VERSION; }
 
 extern "C" const char* mgrit_last_error(void) { return g_err.c_str(); }
 
-static mgrit_status validate_problem(const mgrit_problem* p) {
+mgrit_status validate_problem(const mgrit_problem* p) {
   if (!p) return fail(MGRIT_ERR_INVALID, "problem is NULL");
   if (p->nx < 8) return fail(MGRIT_ERR_INVALID, "nx must be >= 8");
   if (p->nt < 1) return fail(MGRIT_ERR_INVALID, "nt must be >= 1");
@@ -196,7 +164,7 @@ static mgrit_status validate_problem(const mgrit_problem* p) {
   return MGRIT_OK;
 }
 
-static mgrit_status validate_opts(const mgrit_problem* p, const mgrit_opts* o) {
+mgrit_status validate_opts(const mgrit_problem* p, const mgrit_opts* o) {
   if (!o) return fail(MGRIT_ERR_INVALID, "opts is NULL");
   if (o->m < 2) return fail(MGRIT_ERR_INVALID, "m must be >= 2");
   if (o->levels < 2 || o->levels > MGRIT_MAX_LEVELS) return fail(MGRIT_ERR_INVALID, "levels must be 2..8");
@@ -228,7 +196,7 @@ static PlanRequest make_request(const mgrit_problem* p, const mgrit_opts* o) {
   return rq;
 }
 
-static mgrit_status plan(const mgrit_problem* p, const mgrit_opts* o, std::vector<CoarseOp>* ops) {
+mgrit_status plan(const mgrit_problem* p, const mgrit_opts* o, std::vector<CoarseOp>* ops) {
   std::string err;
   if (!build_hierarchy(make_request(p, o), ops, &err)) return fail(MGRIT_ERR_INVALID, err);
   for (size_t l = 0; l < ops->size(); ++l) {
@@ -290,16 +258,29 @@ extern "C" mgrit_status mgrit_psi_plan(const mgrit_problem* prob, const mgrit_op
 // Cluster size of the march: the largest power of two <= 16 dividing nx with
 // at least 64 points per CTA and a CTA at least as wide as the stencil (the
 // march runs in the stencil's moving frame, so only the width matters).
-static int pick_cluster(int nx, const Taps& t) {
+int pick_cluster(int nx, const Taps& t) {
   const int width = t.hi() - t.lo();
   for (int cs = march_max_cluster(); cs > 1; cs >>= 1)
     if (nx % cs == 0 && nx / cs >= std::max(64, width)) return cs;
   return 1;
 }
 
-extern "C" mgrit_status mgrit_setup(const mgrit_problem* prob, const mgrit_opts* opts, void* stream,
-                                    mgrit_handle** out) {
-  if (!out) return fail(MGRIT_ERR_INVALID, "out is NULL");
+size_t handle_bytes(const mgrit_problem* prob, const mgrit_opts* opts) {
+  const size_t nx = prob->nx, m = opts->m, L = opts->levels;
+  std::vector<size_t> N(L + 1, 0);
+  N[1] = prob->nt / m;
+  for (size_t l = 2; l < L; ++l) N[l] = N[l - 1] / m;
+  size_t d = 3 * (N[1] + 1) * nx + (N[1] + 1) + 2 * nx + 8;
+  for (size_t l = 2; l <= L; ++l) {
+    const size_t P = N[l - 1] + 1;
+    if (l < L || L > 2) d += P * nx;
+    if (l < L) d += 2 * (N[l] + 1) * nx;
+  }
+  return d * sizeof(double);
+}
+
+mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cudaStream_t stream,
+                           const std::vector<CoarseOp>* ops, mgrit_handle** out) {
   *out = nullptr;
   const double t0 = now_s();
   mgrit_status st = validate_problem(prob);
@@ -315,12 +296,13 @@ extern "C" mgrit_status mgrit_setup(const mgrit_problem* prob, const mgrit_opts*
   h->opts.psi_user_nnz = nullptr;
   h->opts.psi_user_offsets = nullptr;
   h->opts.psi_user_coeffs = nullptr;
-  h->stream = (cudaStream_t)stream;
+  h->stream = stream;
   h->nx = prob->nx;
   h->nt = prob->nt;
   h->m = opts->m;
   h->L = opts->levels;
-  st = plan(prob, opts, &h->ops);
+  if (ops) h->ops = *ops;
+  else st = plan(prob, opts, &h->ops);
   if (st != MGRIT_OK) {
     delete h;
     return st;
@@ -405,6 +387,12 @@ extern "C" mgrit_status mgrit_setup(const mgrit_problem* prob, const mgrit_opts*
   return MGRIT_OK;
 }
 
+extern "C" mgrit_status mgrit_setup(const mgrit_problem* prob, const mgrit_opts* opts, void* stream,
+                                    mgrit_handle** out) {
+  if (!out) return fail(MGRIT_ERR_INVALID, "out is NULL");
+  return handle_create(prob, opts, (cudaStream_t)stream, nullptr, out);
+}
+
 extern "C" void mgrit_destroy(mgrit_handle* h) {
   if (!h) return;
   release(h);
@@ -429,18 +417,18 @@ extern "C" mgrit_status mgrit_psi_info(mgrit_handle* h, int32_t level, int32_t c
 
 // ------------------------------------------------------------------- solve
 
-static mgrit_status launch_ok(cudaError_t e, const char* what) {
+mgrit_status launch_ok(cudaError_t e, const char* what) {
   if (e != cudaSuccess) return fail(MGRIT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
   return MGRIT_OK;
 }
 
-static void reset_stats(mgrit_handle* h) {
+void reset_stats(mgrit_handle* h) {
   for (int k = 0; k < MGRIT_K_KINDS; ++k) h->kcount[k] = 0;
   h->evkind.clear();
   h->evused = 0;
 }
 
-static cudaEvent_t next_event(mgrit_handle* h) {
+cudaEvent_t next_event(mgrit_handle* h) {
   if (h->evused == h->evpool.size()) {
     cudaEvent_t ev;
     if (cudaEventCreate(&ev) != cudaSuccess) {
@@ -452,30 +440,7 @@ static cudaEvent_t next_event(mgrit_handle* h) {
   return h->evpool[h->evused++];
 }
 
-// Launch one kernel of `kind` through fn(); counts it and, when asked,
-// brackets it with CUDA events on the handle's stream.
-template <typename F>
-static mgrit_status klaunch(mgrit_handle* h, int kind, const char* what, F&& fn) {
-  const bool timed = (h->opts.flags & MGRIT_FLAG_TIME_KERNELS) != 0;
-  cudaEvent_t e0 = timed ? next_event(h) : nullptr;
-  if (e0) cudaEventRecord(e0, h->stream);
-  mgrit_status st = fn();
-  if (st != MGRIT_OK) return st;
-  if (e0) {
-    cudaEvent_t e1 = next_event(h);
-    if (e1) {
-      cudaEventRecord(e1, h->stream);
-      h->evkind.push_back(kind);
-    } else {
-      h->evused--;
-    }
-  }
-  h->kcount[kind]++;
-  (void)what;
-  return MGRIT_OK;
-}
-
-static void collect_stats(mgrit_handle* h, mgrit_result* R) {
+void collect_stats(mgrit_handle* h, mgrit_result* R) {
   int total = 0;
   for (int k = 0; k < MGRIT_K_KINDS; ++k) {
     R->kernel_count[k] = h->kcount[k];
@@ -493,7 +458,7 @@ static void collect_stats(mgrit_handle* h, mgrit_result* R) {
 }
 
 // Launch a march, shrinking the cluster if the device refuses the size.
-static mgrit_status run_march(mgrit_handle* h, const MarchArgs& a, const DevTaps& t) {
+mgrit_status run_march(mgrit_handle* h, const MarchArgs& a, const DevTaps& t) {
   return klaunch(h, MGRIT_K_MARCH, "march", [&]() -> mgrit_status {
     for (;;) {
       int threads = std::min(256, a.nx / h->march_cluster);
@@ -507,7 +472,7 @@ static mgrit_status run_march(mgrit_handle* h, const MarchArgs& a, const DevTaps
 }
 
 // ||Phi u0||: residual of the zero initial iterate (only time level 1 is nonzero).
-static mgrit_status initial_residual(mgrit_handle* h, const double* u0dev, double* r0) {
+mgrit_status initial_residual(mgrit_handle* h, const double* u0dev, double* r0) {
   mgrit_status st;
   double* out = h->scratch;
   double* part = h->scratch + h->nx;
@@ -524,7 +489,7 @@ static mgrit_status initial_residual(mgrit_handle* h, const double* u0dev, doubl
 
 // One V-cycle below level 1: levels 2..L-1 relax, level L marches, corrections
 // come back up; finally c_new += e on level 1 (or fused into the march, L = 2).
-static mgrit_status coarse_cycle(mgrit_handle* h, double* c_new) {
+mgrit_status coarse_cycle(mgrit_handle* h, double* c_new) {
   const int L = h->L, m = h->m, nx = h->nx;
   const int prec = h->opts.precision == MGRIT_PREC_FP64 ? 0 : 1;
   mgrit_status st;
@@ -581,6 +546,46 @@ static mgrit_status coarse_cycle(mgrit_handle* h, double* c_new) {
   });
 }
 
+mgrit_status write_output(mgrit_handle* h, const double* cres, double* out) {
+  const int nx = h->nx, m = h->m;
+  const size_t N1 = h->Nl[1];
+  const size_t slab = (size_t)nx * sizeof(double);
+  mgrit_status st;
+  if (h->opts.output == MGRIT_OUT_FINAL) {
+    CUDA_TRY(cudaMemcpyAsync(out, cres + N1 * nx, slab, kind_from_dev(out), h->stream));
+  } else if (h->opts.output == MGRIT_OUT_CPOINTS) {
+    CUDA_TRY(cudaMemcpyAsync(out, cres, (N1 + 1) * slab, kind_from_dev(out), h->stream));
+  } else {
+    // F-points by one F-relaxation from the C-points (ideal interpolation)
+    double* full = nullptr;
+    const bool dev = is_device_ptr(out);
+    if (dev) full = out;
+    else if ((st = dalloc(h, (size_t)(h->nt + 1) * nx, &full)) != MGRIT_OK) return st;
+    CorrectArgs c = {};
+    c.c_new = cres;
+    c.e = nullptr;
+    c.g = nullptr;
+    c.u = full;
+    c.nx = nx;
+    c.m = m;
+    c.N = (int)N1;
+    if ((st = klaunch(h, MGRIT_K_OTHER, "interp", [&] {
+           return launch_ok(launch_correct(c, h->dphi, h->fcf_threads, h->stream), "interp");
+         })) != MGRIT_OK)
+      return st;
+    if (!dev) {
+      CUDA_TRY(cudaMemcpyAsync(out, full, (size_t)(h->nt + 1) * slab, cudaMemcpyDeviceToHost, h->stream));
+      CUDA_TRY(cudaStreamSynchronize(h->stream));
+      DevBuf b = h->bufs.back();
+      h->bufs.pop_back();
+      h->bytes -= std::max<size_t>(b.n, 1) * sizeof(double);
+      if (b.freefn) b.freefn(b.p, (void*)h->stream, b.ctx);
+      else cudaFreeAsync(b.p, h->stream);
+    }
+  }
+  return MGRIT_OK;
+}
+
 extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* out, mgrit_result* res) {
   if (!h) return fail(MGRIT_ERR_INVALID, "handle is NULL");
   if (!u0) return fail(MGRIT_ERR_INVALID, "u0 is NULL");
@@ -627,7 +632,7 @@ extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* o
       return st;
     CUDA_TRY(cudaMemcpyAsync(h->norm_host, h->scratch + 2 * nx, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
-    const double rel = r0 > 0.0 ? std::sqrt(h->norm_host[0]) / r0 : 0.0;
+    const double rel = !std::isfinite(r0) ? r0 : (r0 > 0.0 ? std::sqrt(h->norm_host[0]) / r0 : 0.0);
     if (R.n_history < MGRIT_MAX_HISTORY) R.history[R.n_history++] = rel;
     R.rel_residual = rel;
     if (!std::isfinite(rel) || rel > 1e6) {
@@ -648,41 +653,7 @@ extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* o
   }
   R.iterations = it;
   // result: C-points after the final FCF-relaxation live in c[1-cur]
-  const double* cres = h->c[1 - cur];
-  if (out) {
-    if (h->opts.output == MGRIT_OUT_FINAL) {
-      CUDA_TRY(cudaMemcpyAsync(out, cres + N1 * nx, slab, kind_from_dev(out), h->stream));
-    } else if (h->opts.output == MGRIT_OUT_CPOINTS) {
-      CUDA_TRY(cudaMemcpyAsync(out, cres, (N1 + 1) * slab, kind_from_dev(out), h->stream));
-    } else {
-      // F-points by one F-relaxation from the C-points (ideal interpolation)
-      double* full = nullptr;
-      const bool dev = is_device_ptr(out);
-      if (dev) full = out;
-      else if ((st = dalloc(h, (size_t)(h->nt + 1) * nx, &full)) != MGRIT_OK) return st;
-      CorrectArgs c = {};
-      c.c_new = cres;
-      c.e = nullptr;
-      c.g = nullptr;
-      c.u = full;
-      c.nx = nx;
-      c.m = m;
-      c.N = (int)N1;
-      if ((st = klaunch(h, MGRIT_K_OTHER, "interp", [&] {
-             return launch_ok(launch_correct(c, h->dphi, h->fcf_threads, h->stream), "interp");
-           })) != MGRIT_OK)
-        return st;
-      if (!dev) {
-        CUDA_TRY(cudaMemcpyAsync(out, full, (size_t)(h->nt + 1) * slab, cudaMemcpyDeviceToHost, h->stream));
-        CUDA_TRY(cudaStreamSynchronize(h->stream));
-        DevBuf b = h->bufs.back();
-        h->bufs.pop_back();
-        h->bytes -= std::max<size_t>(b.n, 1) * sizeof(double);
-        if (b.freefn) b.freefn(b.p, (void*)h->stream, b.ctx);
-        else cudaFreeAsync(b.p, h->stream);
-      }
-    }
-  }
+  if (out && (st = write_output(h, h->c[1 - cur], out)) != MGRIT_OK) return st;
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   R.solve_s = now_s() - t0;
   collect_stats(h, &R);

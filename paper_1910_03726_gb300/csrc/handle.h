@@ -1,0 +1,97 @@
+// Internal interface shared by the C ABI's translation units (driver.cpp,
+// server.cpp): the handle of one solve and the helpers that build, run and
+// release it.  Not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mgrit.h"
+#include "device.h"
+#include "setup.h"
+
+struct DevBuf {
+  double* p = nullptr;
+  size_t n = 0;
+  mgrit_free_fn freefn = nullptr;
+  void* ctx = nullptr;
+};
+
+struct mgrit_handle {
+  mgrit_problem prob;
+  mgrit_opts opts;
+  cudaStream_t stream = nullptr;
+  int nx = 0, nt = 0, m = 0, L = 0;
+  std::vector<int> Nl;            // Nl[l] intervals of level l (l = 1..L-1)
+  mg::Taps phi;                       // fine propagator (ERK, collapsed)
+  std::vector<mg::CoarseOp> ops;      // ops[l-2] = Psi_l, l = 2..L
+  mg::DevTaps dphi;
+  std::vector<mg::DevTaps> dpsi;      // dpsi[l-2]
+  std::vector<DevBuf> bufs;       // everything allocated, for release
+  double* c[2] = {nullptr, nullptr};
+  std::vector<double*> r, u, cnew;  // indexed by level (size L+1)
+  double* partial = nullptr;
+  double* scratch = nullptr;      // 2*nx + 1 doubles
+  double* norm_host = nullptr;    // pinned
+  int fcf_threads = 512, march_cluster = 1, march_threads = 256;
+  // per-solve launch accounting (and CUDA-event timing with MGRIT_FLAG_TIME_KERNELS)
+  int kcount[MGRIT_K_KINDS] = {0};
+  std::vector<cudaEvent_t> evpool;
+  std::vector<int> evkind;      // kind of each recorded (start, stop) pair
+  size_t evused = 0;
+  double setup_s = 0.0, op_complexity = 0.0;
+  size_t bytes = 0;
+};
+
+
+mgrit_status fail(mgrit_status s, const std::string& msg);
+double now_s();
+mgrit_status dalloc(mgrit_handle* h, size_t count, double** out);
+void release(mgrit_handle* h);
+mg::DevTaps to_dev(const mg::Taps& t);
+bool is_device_ptr(const void* p);
+cudaMemcpyKind kind_to_dev(const void* src);
+cudaMemcpyKind kind_from_dev(const void* dst);
+mgrit_status validate_problem(const mgrit_problem* p);
+mgrit_status validate_opts(const mgrit_problem* p, const mgrit_opts* o);
+mgrit_status plan(const mgrit_problem* p, const mgrit_opts* o, std::vector<mg::CoarseOp>* ops);
+int pick_cluster(int nx, const mg::Taps& t);
+mgrit_status launch_ok(cudaError_t e, const char* what);
+void reset_stats(mgrit_handle* h);
+cudaEvent_t next_event(mgrit_handle* h);
+void collect_stats(mgrit_handle* h, mgrit_result* R);
+mgrit_status run_march(mgrit_handle* h, const mg::MarchArgs& a, const mg::DevTaps& t);
+mgrit_status initial_residual(mgrit_handle* h, const double* u0dev, double* r0);
+mgrit_status coarse_cycle(mgrit_handle* h, double* c_new);
+// Build a handle; ops != nullptr supplies an already fitted hierarchy.
+mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cudaStream_t stream,
+                           const std::vector<mg::CoarseOp>* ops, mgrit_handle** out);
+// Device bytes a handle for this request will allocate (admission control).
+size_t handle_bytes(const mgrit_problem* prob, const mgrit_opts* opts);
+// Copy the converged C-points cres out per opts.output (FULL interpolates).
+mgrit_status write_output(mgrit_handle* h, const double* cres, double* out);
+
+// Launch one kernel of `kind` through fn(); counts it and, when asked,
+// brackets it with CUDA events on the handle's stream.
+template <typename F>
+inline mgrit_status klaunch(mgrit_handle* h, int kind, const char* what, F&& fn) {
+  const bool timed = (h->opts.flags & MGRIT_FLAG_TIME_KERNELS) != 0;
+  cudaEvent_t e0 = timed ? next_event(h) : nullptr;
+  if (e0) cudaEventRecord(e0, h->stream);
+  mgrit_status st = fn();
+  if (st != MGRIT_OK) return st;
+  if (e0) {
+    cudaEvent_t e1 = next_event(h);
+    if (e1) {
+      cudaEventRecord(e1, h->stream);
+      h->evkind.push_back(kind);
+    } else {
+      h->evused--;
+    }
+  }
+  h->kcount[kind]++;
+  (void)what;
+  return MGRIT_OK;
+}
+

@@ -1,0 +1,502 @@
+// Continuous-batching MGRIT server (mgrit_server_create / mgrit_submit /
+// mgrit_poll / mgrit_server_destroy).
+//
+// A host worker thread owns one CUDA stream.  Each turn it
+//   1. admits queued requests, first come first served, while their device
+//      state fits in the HBM budget and fewer than max_active are running
+//      (fitted coarse operators are cached per problem/options);
+//   2. advances every admitted solve by one MGRIT cycle: one batched
+//      FCF-relaxation launch per nx over all intervals of all solves, one
+//      batched norm launch, one read-back of all norms, then the coarse solves
+//      (one batched cluster march per cluster size for two-level solves, the
+//      V-cycle kernels per handle for multilevel ones);
+//   3. retires converged (or failed) solves: copies their output to host
+//      memory, frees their device state, and wakes pollers.
+// Requests that arrive while others run join at the next turn, so their work
+// overlaps on the device with the solves already in flight.  Per-solve
+// arithmetic is the single-solve path's (same kernels, same block shapes),
+// so a result is the same alone and in the mix.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/mgrit.h"
+#include "device.h"
+#include "handle.h"
+#include "setup.h"
+
+using namespace mg;
+
+namespace {
+
+struct Request {
+  uint64_t ticket = 0;
+  mgrit_problem prob{};
+  mgrit_opts opts{};
+  std::vector<double> u0;
+  int state = 0;  // 0 queued, 1 active, 2 done
+  mgrit_status status = MGRIT_OK;
+  std::string error;
+  mgrit_result res{};
+  std::vector<double> out;
+  mgrit_handle* h = nullptr;
+  int cur = 0, it = 0;
+  double r0 = 0.0, t_submit = 0.0;
+  size_t bytes = 0;
+};
+
+struct PlanKey {
+  int nx, nt, family, p, q, m, levels, rule, halfwidth;
+  double cfl, eta, rho;
+  bool operator<(const PlanKey& o) const {
+    return std::memcmp(this, &o, sizeof(PlanKey)) < 0;
+  }
+};
+
+// Device copy of an array that grows as needed.
+template <typename T>
+struct DevArray {
+  T* p = nullptr;
+  size_t cap = 0;
+  bool reserve(size_t n) {
+    if (n <= cap) return true;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = std::max<size_t>(n, 2 * cap);
+    if (cudaMalloc(&p, cap * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      cap = 0;
+      return false;
+    }
+    return true;
+  }
+  void free() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+}  // namespace
+
+struct mgrit_server {
+  mgrit_server_opts o{};
+  cudaStream_t stream = nullptr;
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Request*> queue;
+  std::vector<Request*> active;
+  std::unordered_map<uint64_t, Request*> reqs;
+  bool stop = false;
+  uint64_t next_ticket = 1;
+  size_t resident = 0;
+  std::map<PlanKey, std::vector<CoarseOp>> plans;
+  DevArray<BatchSolve> dS;
+  DevArray<BatchItem> dItems;
+  DevArray<DevTaps> dTaps;
+  DevArray<int> dIds;
+  DevArray<double> dNorm;
+  double* hNorm = nullptr;
+  size_t hNormCap = 0;
+  std::string fatal;
+};
+
+static PlanKey key_of(const mgrit_problem& p, const mgrit_opts& o) {
+  PlanKey k;
+  std::memset(&k, 0, sizeof(k));
+  k.nx = p.nx; k.nt = p.nt; k.family = p.family; k.p = p.rk_order; k.q = p.upwind_order;
+  k.m = o.m; k.levels = o.levels; k.rule = o.psi_rule; k.halfwidth = o.psi_halfwidth;
+  k.cfl = p.cfl; k.eta = o.psi_eta; k.rho = o.psi_rho;
+  return k;
+}
+
+static void finish(mgrit_server* S, Request* r, mgrit_status st, const std::string& msg) {
+  r->status = st;
+  r->error = msg;
+  if (r->h) {
+    mgrit_destroy(r->h);
+    r->h = nullptr;
+    S->resident -= std::min(S->resident, r->bytes);
+  }
+  r->res.solve_s = now_s() - r->t_submit;
+  r->res.dof_per_s = r->res.solve_s > 0 ? (double)r->prob.nx * r->prob.nt / r->res.solve_s : 0.0;
+  r->state = 2;
+}
+
+// Admit queued requests that fit (called with the lock held; releases it
+// around the host setup).  Returns the newly admitted requests.
+static std::vector<Request*> admit(mgrit_server* S, std::unique_lock<std::mutex>& lk) {
+  std::vector<Request*> fresh;
+  const size_t max_active = S->o.max_active > 0 ? (size_t)S->o.max_active : 4096;
+  while (!S->queue.empty() && S->active.size() + fresh.size() < max_active) {
+    Request* r = S->queue.front();
+    if ((double)(S->resident + r->bytes) > S->o.hbm_budget_bytes && !(S->active.empty() && fresh.empty())) break;
+    S->queue.pop_front();
+    S->resident += r->bytes;
+    lk.unlock();
+    const PlanKey key = key_of(r->prob, r->opts);
+    const std::vector<CoarseOp>* cached = nullptr;
+    {
+      auto itp = S->plans.find(key);
+      if (itp != S->plans.end()) cached = &itp->second;
+    }
+    mgrit_status st = MGRIT_OK;
+    std::vector<CoarseOp> ops;
+    if (!cached && r->opts.psi_rule != MGRIT_PSI_USER) {
+      st = plan(&r->prob, &r->opts, &ops);
+      if (st == MGRIT_OK) {
+        S->plans[key] = ops;
+        cached = &S->plans[key];
+      }
+    }
+    if (st == MGRIT_OK) st = handle_create(&r->prob, &r->opts, S->stream, cached, &r->h);
+    std::string msg = st == MGRIT_OK ? "" : mgrit_last_error();
+    if (st == MGRIT_OK) {
+      mgrit_handle* h = r->h;
+      const size_t slab = (size_t)h->nx * sizeof(double);
+      cudaMemcpyAsync(h->c[0], r->u0.data(), slab, cudaMemcpyHostToDevice, S->stream);
+      cudaMemcpyAsync(h->c[1], h->c[0], slab, cudaMemcpyDeviceToDevice, S->stream);
+      cudaMemsetAsync(h->c[0] + h->nx, 0, (size_t)h->Nl[1] * slab, S->stream);
+      reset_stats(h);
+      std::memset(&r->res, 0, sizeof(r->res));
+      r->res.n_levels = h->L;
+      r->res.setup_s = h->setup_s;
+      r->res.op_complexity = h->op_complexity;
+      st = initial_residual(h, h->c[0], &r->r0);
+      if (st != MGRIT_OK) msg = mgrit_last_error();
+      r->res.r0_norm = r->r0;
+    }
+    lk.lock();
+    if (st != MGRIT_OK) {
+      S->resident -= std::min(S->resident, r->bytes);
+      r->bytes = 0;
+      finish(S, r, st, msg);
+      S->cv.notify_all();
+      continue;
+    }
+    S->resident = S->resident - std::min(S->resident, r->bytes) + r->h->bytes;
+    r->bytes = r->h->bytes;
+    r->state = 1;
+    fresh.push_back(r);
+  }
+  return fresh;
+}
+
+// One MGRIT cycle for every active solve.  Called without the lock.
+static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std::vector<char>* done) {
+  const int n = (int)act.size();
+  std::vector<BatchSolve> hs(n);
+  std::vector<DevTaps> taps(2 * n);
+  for (int k = 0; k < n; ++k) {
+    mgrit_handle* h = act[k]->h;
+    BatchSolve& b = hs[k];
+    std::memset(&b, 0, sizeof(b));
+    b.fcf.u_old = h->c[act[k]->cur];
+    b.fcf.cstride = h->nx;
+    b.fcf.c_new = h->c[1 - act[k]->cur];
+    b.fcf.g = nullptr;
+    b.fcf.r = h->r[1];
+    b.fcf.partial = h->partial;
+    b.fcf.nx = h->nx;
+    b.fcf.m = h->m;
+    b.fcf.N = h->Nl[1];
+    b.fcf.zero_old = 0;
+    b.prec = h->opts.precision == MGRIT_PREC_FP64 ? 0 : 1;
+    b.taps = 2 * k;
+    b.psi = 2 * k + 1;
+    b.cluster = h->march_cluster;
+    taps[2 * k] = h->dphi;
+    taps[2 * k + 1] = h->dpsi.back();
+  }
+  if (!S->dS.reserve(n) || !S->dTaps.reserve(2 * n) || !S->dIds.reserve(n) || !S->dNorm.reserve(n))
+    return fail(MGRIT_ERR_OOM, "server batch descriptors");
+  cudaMemcpyAsync(S->dS.p, hs.data(), n * sizeof(BatchSolve), cudaMemcpyHostToDevice, S->stream);
+  cudaMemcpyAsync(S->dTaps.p, taps.data(), 2 * n * sizeof(DevTaps), cudaMemcpyHostToDevice, S->stream);
+  // ---- batched FCF, one launch per (nx, register-tile eligibility)
+  std::map<std::pair<int, int>, std::vector<int>> groups;
+  const int tile = get_tile();
+  for (int k = 0; k < n; ++k) {
+    const mgrit_handle* h = act[k]->h;
+    const int tiled = (h->dphi.span > 0 && h->nx >= 64 && tile > 0) ? 1 : 0;
+    groups[{h->nx, tiled}].push_back(k);
+  }
+  std::vector<BatchItem> items;
+  std::vector<std::pair<size_t, size_t>> ranges;
+  for (auto& g : groups) {
+    const size_t b0 = items.size();
+    for (int k : g.second)
+      for (int j = 1; j <= hs[k].fcf.N; ++j) items.push_back({k, j});
+    ranges.push_back({b0, items.size()});
+  }
+  if (!S->dItems.reserve(items.size())) return fail(MGRIT_ERR_OOM, "server batch items");
+  cudaMemcpyAsync(S->dItems.p, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, S->stream);
+  size_t gi = 0;
+  for (auto& g : groups) {
+    const int nx = g.first.first, tiled = g.first.second;
+    const int per = tiled ? tile : 4;
+    int th = ((nx + per - 1) / per + 31) / 32 * 32;
+    th = std::max(32, std::min(512, th));
+    const auto rg = ranges[gi++];
+    cudaError_t e = launch_fcf_batched(S->dS.p, S->dItems.p + rg.first, (int)(rg.second - rg.first), S->dTaps.p, nx,
+                                       tiled ? th : -th, S->stream);
+    if (e != cudaSuccess) return launch_ok(e, "fcf_batched");
+    for (int k : g.second) act[k]->h->kcount[MGRIT_K_FCF]++;
+  }
+  // ---- norms of all solves, one read-back
+  std::vector<int> ids(n);
+  for (int k = 0; k < n; ++k) ids[k] = k;
+  cudaMemcpyAsync(S->dIds.p, ids.data(), n * sizeof(int), cudaMemcpyHostToDevice, S->stream);
+  cudaError_t e = launch_norm_batched(S->dS.p, S->dIds.p, n, S->dNorm.p, S->stream);
+  if (e != cudaSuccess) return launch_ok(e, "norm_batched");
+  if ((size_t)n > S->hNormCap) {
+    if (S->hNorm) cudaFreeHost(S->hNorm);
+    S->hNormCap = std::max<size_t>(n, 2 * S->hNormCap);
+    if (cudaMallocHost(&S->hNorm, S->hNormCap * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      S->hNorm = nullptr;
+      S->hNormCap = 0;
+      return fail(MGRIT_ERR_OOM, "pinned norms");
+    }
+  }
+  cudaMemcpyAsync(S->hNorm, S->dNorm.p, n * sizeof(double), cudaMemcpyDeviceToHost, S->stream);
+  e = cudaStreamSynchronize(S->stream);
+  if (e != cudaSuccess) return launch_ok(e, "server cycle");
+  // ---- convergence decisions (Section 2.2 stopping test, per solve)
+  std::vector<int> two_level;
+  std::map<int, std::vector<int>> by_cluster;
+  for (int k = 0; k < n; ++k) {
+    Request* r = act[k];
+    r->h->kcount[MGRIT_K_NORM]++;
+    const double rel =
+        !std::isfinite(r->r0) ? r->r0 : (r->r0 > 0.0 ? std::sqrt(S->hNorm[k]) / r->r0 : 0.0);
+    if (r->res.n_history < MGRIT_MAX_HISTORY) r->res.history[r->res.n_history++] = rel;
+    r->res.rel_residual = rel;
+    r->res.iterations = r->it;
+    if (!std::isfinite(rel) || rel > 1e6) {
+      r->status = MGRIT_ERR_DIVERGED;
+      r->error = "residual not finite or grew above 1e6 x initial";
+      (*done)[k] = 1;
+    } else if (rel <= r->opts.tol) {
+      r->res.converged = 1;
+      (*done)[k] = 1;
+    } else if (r->it >= r->opts.max_iter) {
+      r->status = MGRIT_ERR_NOT_CONVERGED;
+      r->error = "max_iter reached";
+      (*done)[k] = 1;
+    } else if (r->h->L == 2) {
+      by_cluster[r->h->march_cluster].push_back(k);
+    }
+  }
+  // ---- coarse solves: batched cluster marches (two-level), V-cycles (multilevel)
+  for (auto& g : by_cluster) {
+    int max_w = 0, max_halo = 0;
+    for (int k : g.second) {
+      const mgrit_handle* h = act[k]->h;
+      max_w = std::max(max_w, h->nx / g.first);
+      max_halo = std::max(max_halo, h->dpsi.back().hi - h->dpsi.back().lo);
+    }
+    cudaMemcpyAsync(S->dIds.p, g.second.data(), g.second.size() * sizeof(int), cudaMemcpyHostToDevice, S->stream);
+    e = launch_march_batched(S->dS.p, S->dIds.p, (int)g.second.size(), S->dTaps.p, g.first, max_w, max_halo,
+                             S->stream);
+    if (e != cudaSuccess) return launch_ok(e, "march_batched");
+    for (int k : g.second) act[k]->h->kcount[MGRIT_K_MARCH]++;
+    // the ids buffer is reused by the next group: keep launches ordered
+    e = cudaStreamSynchronize(S->stream);
+    if (e != cudaSuccess) return launch_ok(e, "march_batched");
+  }
+  for (int k = 0; k < n; ++k) {
+    Request* r = act[k];
+    if ((*done)[k]) continue;
+    if (r->h->L > 2) {
+      mgrit_status st = coarse_cycle(r->h, r->h->c[1 - r->cur]);
+      if (st != MGRIT_OK) {
+        r->status = st;
+        r->error = mgrit_last_error();
+        (*done)[k] = 1;
+        continue;
+      }
+    }
+    r->cur = 1 - r->cur;
+    r->it++;
+  }
+  return MGRIT_OK;
+}
+
+static void retire(mgrit_server* S, Request* r) {
+  mgrit_handle* h = r->h;
+  if (r->status == MGRIT_OK || r->status == MGRIT_ERR_NOT_CONVERGED) {
+    const size_t rows = r->opts.output == MGRIT_OUT_FINAL ? 1
+                        : r->opts.output == MGRIT_OUT_CPOINTS ? (size_t)h->Nl[1] + 1
+                                                              : (size_t)h->nt + 1;
+    r->out.assign(rows * h->nx, 0.0);
+    mgrit_status st = write_output(h, h->c[1 - r->cur], r->out.data());
+    if (st == MGRIT_OK && cudaStreamSynchronize(S->stream) != cudaSuccess) st = MGRIT_ERR_CUDA;
+    if (st != MGRIT_OK) {
+      r->status = st;
+      r->error = mgrit_last_error();
+    }
+  }
+  collect_stats(h, &r->res);
+  finish(S, r, r->status, r->error);
+}
+
+static void worker_main(mgrit_server* S) {
+  std::unique_lock<std::mutex> lk(S->mu);
+  if (!S->stream) {
+    if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      S->fatal = "cudaStreamCreate failed";
+    }
+  }
+  while (!S->stop) {
+    if (!S->fatal.empty()) {
+      for (Request* r : S->queue) finish(S, r, MGRIT_ERR_CUDA, S->fatal);
+      S->queue.clear();
+      S->cv.notify_all();
+      S->cv.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+      continue;
+    }
+    std::vector<Request*> fresh = admit(S, lk);
+    for (Request* r : fresh) S->active.push_back(r);
+    if (S->active.empty()) {
+      S->cv.notify_all();
+      S->cv.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+      continue;
+    }
+    std::vector<Request*> act = S->active;
+    lk.unlock();
+    std::vector<char> done(act.size(), 0);
+    mgrit_status st = cycle(S, act, &done);
+    std::string msg = st == MGRIT_OK ? "" : mgrit_last_error();
+    if (st != MGRIT_OK)
+      for (size_t k = 0; k < act.size(); ++k) {
+        done[k] = 1;
+        act[k]->status = st;
+        act[k]->error = msg;
+      }
+    for (size_t k = 0; k < act.size(); ++k)
+      if (done[k]) retire(S, act[k]);
+    lk.lock();
+    std::vector<Request*> keep;
+    for (size_t k = 0; k < act.size(); ++k)
+      if (!done[k]) keep.push_back(act[k]);
+    S->active.swap(keep);
+    S->cv.notify_all();
+  }
+  // drain: everything still queued or active fails with TIMEOUT-free cancellation
+  for (Request* r : S->active) finish(S, r, MGRIT_ERR_CUDA, "server destroyed");
+  for (Request* r : S->queue) finish(S, r, MGRIT_ERR_CUDA, "server destroyed");
+  S->active.clear();
+  S->queue.clear();
+  S->cv.notify_all();
+}
+
+extern "C" mgrit_status mgrit_server_create(const mgrit_server_opts* sopts, void* stream, mgrit_server** out) {
+  if (!out) return fail(MGRIT_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!sopts || !(sopts->hbm_budget_bytes > 0.0) || sopts->max_active < 0)
+    return fail(MGRIT_ERR_INVALID, "server options need hbm_budget_bytes > 0 and max_active >= 0");
+  mgrit_server* S = new mgrit_server();
+  S->o = *sopts;
+  S->stream = (cudaStream_t)stream;
+  S->worker = std::thread(worker_main, S);
+  *out = S;
+  return MGRIT_OK;
+}
+
+extern "C" mgrit_status mgrit_submit(mgrit_server* S, const mgrit_problem* prob, const mgrit_opts* opts,
+                                     const double* u0, uint64_t* ticket) {
+  if (!S || !ticket || !u0) return fail(MGRIT_ERR_INVALID, "server, u0 and ticket must be non-NULL");
+  mgrit_status st = validate_problem(prob);
+  if (st == MGRIT_OK) st = validate_opts(prob, opts);
+  if (st != MGRIT_OK) return st;
+  if (opts->psi_rule == MGRIT_PSI_USER) return fail(MGRIT_ERR_UNSUPPORTED, "the server fits Psi itself");
+  Request* r = new Request();
+  r->prob = *prob;
+  r->opts = *opts;
+  r->opts.psi_user_nnz = nullptr;
+  r->opts.psi_user_offsets = nullptr;
+  r->opts.psi_user_coeffs = nullptr;
+  r->bytes = handle_bytes(prob, opts);
+  if ((double)r->bytes > S->o.hbm_budget_bytes) {
+    delete r;
+    return fail(MGRIT_ERR_OVER_BUDGET, "request needs more device memory than the server budget");
+  }
+  r->u0.resize(prob->nx);
+  if (is_device_ptr(u0)) {
+    if (cudaMemcpy(r->u0.data(), u0, prob->nx * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      delete r;
+      return fail(MGRIT_ERR_CUDA, "copying u0 from the device");
+    }
+  } else {
+    std::memcpy(r->u0.data(), u0, prob->nx * sizeof(double));
+  }
+  r->t_submit = now_s();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->ticket = S->next_ticket++;
+    S->reqs[r->ticket] = r;
+    S->queue.push_back(r);
+    *ticket = r->ticket;
+  }
+  S->cv.notify_all();
+  return MGRIT_OK;
+}
+
+extern "C" mgrit_status mgrit_poll(mgrit_server* S, uint64_t ticket, double* out, mgrit_result* res) {
+  if (!S) return fail(MGRIT_ERR_INVALID, "server is NULL");
+  Request* r = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return fail(MGRIT_ERR_UNKNOWN_TICKET, "ticket unknown or already released");
+    r = it->second;
+    if (r->state != 2) return MGRIT_PENDING;
+    S->reqs.erase(it);
+  }
+  if (out && !r->out.empty()) {
+    if (is_device_ptr(out)) {
+      if (cudaMemcpy(out, r->out.data(), r->out.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaGetLastError();
+    } else {
+      std::memcpy(out, r->out.data(), r->out.size() * sizeof(double));
+    }
+  }
+  if (res) *res = r->res;
+  const mgrit_status st = r->status;
+  if (st != MGRIT_OK) fail(st, r->error);
+  delete r;
+  return st;
+}
+
+extern "C" void mgrit_server_destroy(mgrit_server* S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  for (auto& kv : S->reqs) delete kv.second;
+  S->reqs.clear();
+  S->dS.free();
+  S->dItems.free();
+  S->dTaps.free();
+  S->dIds.free();
+  S->dNorm.free();
+  if (S->hNorm) cudaFreeHost(S->hNorm);
+  delete S;
+}

@@ -91,3 +91,24 @@ def test_setup_rejects_invalid_requests_before_touching_the_gpu(capi):
             capi.mgrit_setup(prob, o)
         assert ei.value.status == code
         assert capi.mgrit_last_error()
+
+
+def test_server_host_side_without_gpu(capi):
+    """Admission control and ticket bookkeeping run on the host: an oversize
+    request is refused at submit, an unknown ticket is reported, and the server
+    shuts down cleanly (no GPU work is needed for any of this)."""
+    import workloads
+    srv = capi.mgrit_server_create(1e6)
+    try:
+        prob = capi.problem(1024, 4096, "ERK", 1, 1, 0.85)
+        with pytest.raises(capi.MgritError) as ei:
+            capi.mgrit_submit(srv, prob, capi.mgrit_opts_default(m=4), workloads.sin4(1024))
+        assert ei.value.status == -6
+        st, _ = capi.mgrit_poll(srv, 12345)
+        assert st == -11
+        with pytest.raises(capi.MgritError) as ei:
+            capi.mgrit_submit(srv, capi.problem(64, 1020, "ERK", 1, 1, 0.85), capi.mgrit_opts_default(m=8),
+                              workloads.sin4(64))
+        assert ei.value.status == -1
+    finally:
+        capi.mgrit_server_destroy(srv)

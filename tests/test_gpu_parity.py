@@ -170,3 +170,15 @@ def test_edge_cases_small_and_ragged(capi):
         assert st == -4 and res.iterations == 0 and res.converged == 0
     finally:
         capi.mgrit_destroy(h)
+
+
+def test_nonfinite_initial_condition_reports_divergence(capi):
+    u0 = workloads.sin4(64)
+    u0[3] = np.inf
+    h = capi.mgrit_setup(capi.problem(64, 256, "ERK", 1, 1, 0.85), capi.mgrit_opts_default(m=8))
+    try:
+        with pytest.raises(capi.MgritError) as ei:
+            capi.mgrit_solve(h, u0, None)
+        assert ei.value.status == -5
+    finally:
+        capi.mgrit_destroy(h)

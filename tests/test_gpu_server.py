@@ -1,0 +1,123 @@
+"""Continuous-batching server through the C ABI: every result equals the same
+solve run alone (same iterations, C-points identical to 1e-14), requests that
+arrive while others run are admitted as memory frees up, and failures are
+reported per request."""
+import time
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import schemes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1910_03726_gb300 import build
+    build.build()
+    from paper_1910_03726_gb300 import capi as c
+    return c
+
+
+MIX = [  # (p, nx, nt, m, levels, precision)
+    (1, 64, 512, 8, 2, 0), (3, 128, 1024, 4, 2, 1), (2, 96, 768, 4, 3, 0), (5, 128, 512, 4, 2, 1),
+    (3, 256, 2048, 8, 2, 0), (4, 128, 1024, 16, 2, 1), (1, 256, 1024, 4, 3, 1), (3, 64, 256, 4, 2, 0),
+    (2, 128, 2048, 8, 2, 1), (5, 256, 1024, 8, 3, 0), (3, 128, 512, 8, 2, 1), (1, 128, 4096, 16, 2, 0),
+]
+
+
+def _spec(capi, p, nx, nt, m, levels, prec):
+    c = schemes.cfl_number("ERK", p)
+    prob = capi.problem(nx, nt, "ERK", p, p, c)
+    opts = capi.mgrit_opts_default(m=m, levels=levels, precision=prec, output=capi.OUT_CPOINTS)
+    u0 = workloads.fourier_field(nx, seed=100 + p * 7 + nx)
+    return prob, opts, u0
+
+
+def _alone(capi, prob, opts, u0):
+    h = capi.mgrit_setup(prob, opts)
+    try:
+        out = np.zeros((prob.nt // opts.m + 1, prob.nx))
+        res, _ = capi.mgrit_solve(h, u0, out)
+    finally:
+        capi.mgrit_destroy(h)
+    return res, out
+
+
+def _wait(capi, srv, ticket, rows, nx, timeout=120.0):
+    out = np.zeros((rows, nx))
+    t0 = time.time()
+    while True:
+        st, res = capi.mgrit_poll(srv, ticket, out)
+        if st != capi.MGRIT_PENDING:
+            return st, res, out
+        assert time.time() - t0 < timeout, "request did not finish"
+        time.sleep(0.002)
+
+
+@pytest.mark.parametrize("budget_solves", [100, 3])
+def test_batch_results_equal_alone(capi, budget_solves):
+    specs = [_spec(capi, *s) for s in MIX]
+    alone = [_alone(capi, *sp) for sp in specs]
+    from paper_1910_03726_gb300.capi import _lib  # noqa: F401
+    max_bytes = max(sp[0].nx * (sp[0].nt // sp[1].m + 1) * 8 * 6 for sp in specs)
+    srv = capi.mgrit_server_create(budget_solves * max_bytes)
+    try:
+        tickets = [capi.mgrit_submit(srv, *sp) for sp in specs]
+        for (prob, opts, u0), t, (ares, aout) in zip(specs, tickets, alone):
+            st, res, out = _wait(capi, srv, t, prob.nt // opts.m + 1, prob.nx)
+            assert st == 0, capi.mgrit_last_error()
+            assert res.iterations == ares.iterations
+            assert res.converged == 1
+            err = float(np.max(np.abs(out - aout)) / np.max(np.abs(aout)))
+            assert err <= 1e-14, err
+        # a released ticket is gone
+        st, _ = capi.mgrit_poll(srv, tickets[0])
+        assert st == -11
+    finally:
+        capi.mgrit_server_destroy(srv)
+
+
+def test_requests_join_while_others_run(capi):
+    specs = [_spec(capi, *s) for s in MIX[:6]]
+    srv = capi.mgrit_server_create(8e9, max_active=2)
+    try:
+        first = [capi.mgrit_submit(srv, *sp) for sp in specs[:3]]
+        time.sleep(0.01)
+        later = [capi.mgrit_submit(srv, *sp) for sp in specs[3:]]
+        for (prob, opts, u0), t in zip(specs, first + later):
+            st, res, out = _wait(capi, srv, t, prob.nt // opts.m + 1, prob.nx)
+            assert st == 0 and res.converged == 1
+    finally:
+        capi.mgrit_server_destroy(srv)
+
+
+def test_failures_are_per_request(capi):
+    """Over-budget requests are refused at submit; a NaN initial condition
+    diverges without disturbing its neighbours; max_iter = 0 reports
+    NOT_CONVERGED with the relaxed iterate."""
+    good = _spec(capi, 3, 128, 512, 4, 2, 0)
+    srv = capi.mgrit_server_create(1e8)
+    try:
+        big = capi.problem(4096, 16384, "ERK", 3, 3, schemes.cfl_number("ERK", 3))
+        with pytest.raises(capi.MgritError) as ei:
+            capi.mgrit_submit(srv, big, capi.mgrit_opts_default(m=2), workloads.sin4(4096))
+        assert ei.value.status == -6
+        bad_u0 = workloads.sin4(128)
+        bad_u0[5] = np.nan
+        t_bad = capi.mgrit_submit(srv, good[0], good[1], bad_u0)
+        t_good = capi.mgrit_submit(srv, *good)
+        o0 = capi.mgrit_opts_default(m=4, levels=2, max_iter=0)
+        t_cap = capi.mgrit_submit(srv, good[0], o0, good[2])
+        st, res, _ = _wait(capi, srv, t_bad, 129, 128)
+        assert st == -5
+        st, res, _ = _wait(capi, srv, t_good, 129, 128)
+        assert st == 0 and res.converged == 1
+        st, res, _ = _wait(capi, srv, t_cap, 129, 128)
+        assert st == -4 and res.iterations == 0
+    finally:
+        capi.mgrit_server_destroy(srv)
