@@ -37,10 +37,11 @@ def apply_taps(v: np.ndarray, taps: dict) -> np.ndarray:
 class FineStep:
     """u -> Phi u for a family/order pair at CFL number c on nx points."""
 
-    def __init__(self, family: str, p: int, c: float, nx: int):
+    def __init__(self, family: str, p: int, c: float, nx: int, q: int | None = None):
+        """q: order of the upwind stencil (default p, the paper's pairing)."""
         self.family, self.p, self.c, self.nx = family, p, c, nx
         self.A, self.b = schemes.tableau(family, p)
-        self.taps = schemes.dtL_taps(p, c)
+        self.taps = schemes.dtL_taps(q or p, c)
         if family == "SDIRK":
             sym = schemes.stencil_symbol(self.taps, schemes.thetas(nx))
             # one divisor per distinct diagonal entry (all equal for SDIRK)

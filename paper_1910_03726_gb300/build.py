@@ -19,7 +19,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmgrit_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["kernels.cu", "setup.cpp", "driver.cpp", "server.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "sdirk.cu", "setup.cpp", "driver.cpp", "server.cpp", "noalloc.cu"]
 HEADERS = ["device.h", "setup.h", "handle.h"]
 
 
@@ -40,7 +40,7 @@ def _compile(src: str, verbose: bool) -> str:
     path = os.path.join(CSRC, src)
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(path), _newest_dep()):
         return obj
-    cmd = [nvcc(), *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
+    cmd = [nvcc(), *ARCH, "-O3", "-std=c++20", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
            "-I", os.path.join(ROOT, "include"), "-c", path, "-o", obj]
     if src.endswith(".cu"):
         cmd[1:1] = ["-Xptxas", "-O3"]

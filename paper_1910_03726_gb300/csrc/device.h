@@ -73,6 +73,44 @@ cudaError_t launch_fcf(const FcfArgs& a, const DevTaps& t, int precision, int th
 // element per 8 so that per-thread chunks of 8 are bank-conflict free).
 __host__ __device__ inline int padded_len(int nx) { return nx + (nx >> 3) + 1; }
 
+// ------------------------------------------------------------- SDIRK steps
+// One SDIRK step (stage form, Appendix A tableaux):
+//   K_i = M^{-1} dtL (u + sum_{j<i} a_ij K_j),  M = I - gamma dtL,
+//   u_new = u + sum_i b_i K_i  (stiffly accurate: b = last row of A).
+// M = E^{-ql} p_d prod_r (E - z_r), E the forward shift: each linear factor is
+// a periodic first-order recurrence solved by a chunked parallel scan in its
+// stable direction (forward if |z_r| < 1, backward otherwise) closed by an
+// exact rank-one periodic wrap.
+constexpr int kMaxStages = 5;
+constexpr int kMaxFactors = 5;
+struct SdirkPlan {
+  int s;                        // stages
+  int nL;                       // taps of dt L
+  int ql;                       // input shift of the solve
+  int nf;                       // linear factors of M
+  int offL[6];
+  double cL[6];
+  float cL32[6];
+  double a[kMaxStages][kMaxStages];
+  float a32[kMaxStages][kMaxStages];
+  double gamma;
+  float gamma32;
+  int dir[kMaxFactors];         // +1: forward recurrence x_i = m x_{i-1} + b_i; -1: backward
+  double mre[kMaxFactors], mim[kMaxFactors];   // recurrence multiplier m (|m| < 1)
+  double bscale_re[kMaxFactors], bscale_im[kMaxFactors];  // input scale of the factor
+  double inv_pd;                // 1 / leading coefficient
+};
+int sdirk_slots(const SdirkPlan& p);                      // shared slabs a step needs
+size_t sdirk_smem(const SdirkPlan& p, int nx, int prec);  // bytes of an FCF CTA
+int sdirk_threads(int nx);                                // CTA size (0: nx unsupported)
+cudaError_t launch_fcf_sdirk(const FcfArgs& a, const SdirkPlan& p, int precision, cudaStream_t s);
+cudaError_t launch_propagate_sdirk(const double* in, double* out, int count, int nx, int k, const SdirkPlan& p,
+                                   double* partial, cudaStream_t s);
+cudaError_t launch_interp_sdirk(const double* c, double* u, int nx, int m, int N, const SdirkPlan& p,
+                                cudaStream_t s);
+cudaError_t launch_seq_sdirk(const double* u0, double* out, int nx, int P, int store_every, const SdirkPlan& p,
+                             cudaStream_t s);
+
 // ------------------------------------------------------------ batched solves
 // One entry per active solve of a batched launch (server).
 struct BatchSolve {

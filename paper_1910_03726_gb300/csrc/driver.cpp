@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <complex>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -265,6 +266,118 @@ int pick_cluster(int nx, const Taps& t) {
   return 1;
 }
 
+// Host reference of the factored solve (used to check the plan): applies
+// E^{shift}, every factor's periodic recurrence, and the scale, in FP64.
+static void host_sdirk_solve(const SdirkPlan& P, std::vector<double>& y) {
+  const int n = (int)y.size();
+  std::vector<double> x(n);
+  for (int i = 0; i < n; ++i) x[i] = y[((i + P.ql) % n + n) % n];
+  for (int f = 0; f < P.nf; ++f) {
+    const std::complex<double> m(P.mre[f], P.mim[f]);
+    std::vector<std::complex<double>> z(n);
+    for (int i = 0; i < n; ++i) z[i] = x[i];
+    const bool back = P.dir[f] < 0;
+    // zero-carry pass, wrap value, carried pass
+    std::complex<double> c = 0.0;
+    std::vector<std::complex<double>> w(n);
+    for (int k = 0; k < n; ++k) {
+      const int i = back ? n - 1 - k : k;
+      c = m * c + z[i];
+      w[i] = c;
+    }
+    std::complex<double> mn = std::pow(m, n);
+    std::complex<double> carry = c / (1.0 - mn);
+    for (int k = 0; k < n; ++k) {
+      const int i = back ? n - 1 - k : k;
+      carry = m * carry + z[i];
+      w[i] = carry;
+    }
+    if (P.mim[f] == 0.0)
+      for (int i = 0; i < n; ++i) x[i] = w[i].real();
+    else
+      for (int i = 0; i < n; ++i) x[i] = (m * w[i]).imag() / P.mim[f];
+  }
+  for (int i = 0; i < n; ++i) y[i] = x[i] * P.inv_pd;
+}
+
+mgrit_status make_sdirk_plan(const mgrit_problem* prob, SdirkPlan* out) {
+  SdirkPlan P;
+  std::memset(&P, 0, sizeof(P));
+  Tableau tb = sdirk_tableau(prob->rk_order);
+  Taps L = dtL_taps(prob->upwind_order, prob->cfl);
+  if (tb.s < 1 || tb.s > kMaxStages || L.size() > 6) return fail(MGRIT_ERR_INVALID, "unsupported SDIRK scheme");
+  P.s = tb.s;
+  for (int i = 0; i < tb.s; ++i)
+    for (int j = 0; j < tb.s; ++j) {
+      P.a[i][j] = tb.a(i, j);
+      P.a32[i][j] = (float)tb.a(i, j);
+    }
+  P.gamma = tb.a(0, 0);
+  P.gamma32 = (float)P.gamma;
+  P.nL = L.size();
+  for (int k = 0; k < L.size(); ++k) {
+    P.offL[k] = L.off[k];
+    P.cL[k] = L.coef[k];
+    P.cL32[k] = (float)L.coef[k];
+  }
+  // M = I - gamma dtL = E^{lo} sum_k m_k E^{k-lo}: polynomial of degree hi-lo
+  const int lo = L.lo(), hi = L.hi(), d = hi - lo;
+  std::vector<double> poly(d + 1, 0.0);
+  for (int k = 0; k < L.size(); ++k) poly[L.off[k] - lo] += -P.gamma * L.coef[k];
+  poly[-lo] += 1.0;
+  std::vector<std::complex<double>> roots = poly_roots(poly);
+  double scale = 1.0 / poly[d];
+  int nfwd = 0, nf = 0, npos = 0, nneg = 0;
+  for (auto z : roots) {
+    if (std::fabs(std::abs(z) - 1.0) < 1e-8) return fail(MGRIT_ERR_INVALID, "stage matrix has a root on |z| = 1");
+    const bool real = std::fabs(z.imag()) <= 1e-10 * std::max(1.0, std::abs(z));
+    if (!real && z.imag() < 0) {
+      ++nneg;
+      continue;
+    }
+    if (!real) ++npos;
+    if (nf >= kMaxFactors) return fail(MGRIT_ERR_INVALID, "too many stage-matrix factors");
+    if (std::abs(z) < 1.0) {
+      P.dir[nf] = 1;
+      P.mre[nf] = z.real();
+      P.mim[nf] = real ? 0.0 : z.imag();
+      nfwd += real ? 1 : 2;
+    } else {
+      const std::complex<double> w = real ? std::complex<double>(1.0 / z.real(), 0.0) : 1.0 / z;
+      P.dir[nf] = -1;
+      P.mre[nf] = w.real();
+      P.mim[nf] = real ? 0.0 : w.imag();
+      scale *= real ? 1.0 / (-z.real()) : 1.0 / std::norm(z);
+    }
+    ++nf;
+  }
+  if (npos != nneg) return fail(MGRIT_ERR_INVALID, "unpaired complex roots of the stage matrix");
+  P.nf = nf;
+  P.ql = -lo - nfwd;
+  P.inv_pd = scale;
+  // check: M (M^{-1} y) = y on a test vector
+  const int n = 64;
+  std::vector<double> y(n), x(n);
+  for (int i = 0; i < n; ++i) y[i] = std::sin(0.37 * i) + 0.25 * std::cos(1.9 * i * i);
+  x = y;
+  host_sdirk_solve(P, x);
+  double err = 0.0, ref = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double mx = x[i];
+    for (int k = 0; k < L.size(); ++k) mx -= P.gamma * L.coef[k] * x[((i + L.off[k]) % n + n) % n];
+    err = std::max(err, std::fabs(mx - y[i]));
+    ref = std::max(ref, std::fabs(y[i]));
+  }
+  if (!(err <= 1e-12 * ref)) return fail(MGRIT_ERR_INVALID, "stage-matrix factorisation check failed");
+  *out = P;
+  return MGRIT_OK;
+}
+
+cudaError_t launch_fine_fcf(mgrit_handle* h, const FcfArgs& f, int prec) {
+  if (h->sdirk) return launch_fcf_sdirk(f, h->splan, prec, h->stream);
+  return launch_fcf(f, h->dphi, prec, h->fcf_threads, h->stream);
+}
+
 size_t handle_bytes(const mgrit_problem* prob, const mgrit_opts* opts) {
   const size_t nx = prob->nx, m = opts->m, L = opts->levels;
   std::vector<size_t> N(L + 1, 0);
@@ -286,7 +399,6 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
   mgrit_status st = validate_problem(prob);
   if (st == MGRIT_OK) st = validate_opts(prob, opts);
   if (st != MGRIT_OK) return st;
-  if (prob->family == MGRIT_SDIRK) return fail(MGRIT_ERR_UNSUPPORTED, "SDIRK relaxation not built yet");
   if (opts->precision == MGRIT_PREC_MIXED_DF) return fail(MGRIT_ERR_UNSUPPORTED, "float-float mode not built yet");
   if (2.0 * prob->nx * sizeof(double) > 227.0 * 1024.0)
     return fail(MGRIT_ERR_UNSUPPORTED, "nx too large for one shared-memory slab (max 14528)");
@@ -307,7 +419,26 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
     delete h;
     return st;
   }
-  h->phi = erk_phi_taps(prob->rk_order, prob->upwind_order, prob->cfl);
+  if (prob->family == MGRIT_SDIRK) {
+    h->sdirk = true;
+    if (!sdirk_threads(prob->nx)) {
+      delete h;
+      return fail(MGRIT_ERR_UNSUPPORTED, "SDIRK needs nx = threads * C, threads a multiple of 32 <= 512, C <= 16");
+    }
+    if ((st = make_sdirk_plan(prob, &h->splan)) != MGRIT_OK) {
+      delete h;
+      return st;
+    }
+    if (sdirk_smem(h->splan, prob->nx, 0) > 227 * 1024) {
+      delete h;
+      return fail(MGRIT_ERR_UNSUPPORTED, "nx too large for the SDIRK stage slabs in shared memory");
+    }
+    // Phi is dense for SDIRK; only its order-1 stencil placeholder is kept
+    h->phi.off = {0};
+    h->phi.coef = {1.0};
+  } else {
+    h->phi = erk_phi_taps(prob->rk_order, prob->upwind_order, prob->cfl);
+  }
   if (h->phi.size() > kMaxDevTaps) {
     delete h;
     return fail(MGRIT_ERR_UNSUPPORTED, "fine stencil too wide");
@@ -327,7 +458,7 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
       f /= h->m;
       s += f * op.taps.size();
     }
-    h->op_complexity = s / h->phi.size();
+    h->op_complexity = h->sdirk ? 0.0 : s / h->phi.size();
   }
   const int nx = h->nx, L = h->L, m = h->m;
   h->Nl.assign(L + 1, 0);
@@ -477,6 +608,8 @@ mgrit_status initial_residual(mgrit_handle* h, const double* u0dev, double* r0) 
   double* out = h->scratch;
   double* part = h->scratch + h->nx;
   if ((st = klaunch(h, MGRIT_K_PROPAGATE, "propagate", [&] {
+         if (h->sdirk) return launch_ok(launch_propagate_sdirk(u0dev, out, 1, h->nx, 1, h->splan, part, h->stream),
+                                        "propagate");
          return launch_ok(launch_propagate(u0dev, out, 1, h->nx, 1, h->dphi, part, h->fcf_threads, h->stream),
                           "propagate");
        })) != MGRIT_OK)
@@ -570,6 +703,8 @@ mgrit_status write_output(mgrit_handle* h, const double* cres, double* out) {
     c.m = m;
     c.N = (int)N1;
     if ((st = klaunch(h, MGRIT_K_OTHER, "interp", [&] {
+           if (h->sdirk)
+             return launch_ok(launch_interp_sdirk(cres, full, nx, m, (int)N1, h->splan, h->stream), "interp");
            return launch_ok(launch_correct(c, h->dphi, h->fcf_threads, h->stream), "interp");
          })) != MGRIT_OK)
       return st;
@@ -623,7 +758,7 @@ extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* o
     f.N = (int)N1;
     f.zero_old = 0;
     if ((st = klaunch(h, MGRIT_K_FCF, "fcf", [&] {
-           return launch_ok(launch_fcf(f, h->dphi, prec, h->fcf_threads, h->stream), "fcf");
+           return launch_ok(launch_fine_fcf(h, f, prec), "fcf");
          })) != MGRIT_OK)
       return st;
     if ((st = klaunch(h, MGRIT_K_NORM, "norm", [&] {
@@ -690,10 +825,16 @@ extern "C" mgrit_status mgrit_sequential(mgrit_handle* h, const double* u0, doub
   a.nx = nx;
   a.P = h->nt + 1;
   reset_stats(h);
-  int saved = h->march_cluster;
-  h->march_cluster = pick_cluster(nx, h->phi);
-  st = run_march(h, a, h->dphi);
-  h->march_cluster = saved;
+  if (h->sdirk) {
+    st = klaunch(h, MGRIT_K_MARCH, "seq", [&] {
+      return launch_ok(launch_seq_sdirk(init, dst, nx, h->nt + 1, every, h->splan, h->stream), "seq_sdirk");
+    });
+  } else {
+    int saved = h->march_cluster;
+    h->march_cluster = pick_cluster(nx, h->phi);
+    st = run_march(h, a, h->dphi);
+    h->march_cluster = saved;
+  }
   if (st != MGRIT_OK) return st;
   if (out && !dev) {
     if (final_only)
@@ -722,6 +863,8 @@ extern "C" mgrit_status mgrit_propagate(mgrit_handle* h, int32_t level, int32_t 
   const DevTaps& t = level == 1 ? h->dphi : h->dpsi[level - 2];
   reset_stats(h);
   mgrit_status st = klaunch(h, MGRIT_K_PROPAGATE, "propagate", [&] {
+    if (level == 1 && h->sdirk)
+      return launch_ok(launch_propagate_sdirk(in, out, count, h->nx, k, h->splan, nullptr, h->stream), "propagate");
     return launch_ok(launch_propagate(in, out, count, h->nx, k, t, nullptr, h->fcf_threads, h->stream), "propagate");
   });
   if (st != MGRIT_OK) return st;

@@ -27,6 +27,8 @@ struct mgrit_handle {
   mg::Taps phi;                       // fine propagator (ERK, collapsed)
   std::vector<mg::CoarseOp> ops;      // ops[l-2] = Psi_l, l = 2..L
   mg::DevTaps dphi;
+  bool sdirk = false;             // fine level is SDIRK (stage solves)
+  mg::SdirkPlan splan;
   std::vector<mg::DevTaps> dpsi;      // dpsi[l-2]
   std::vector<DevBuf> bufs;       // everything allocated, for release
   double* c[2] = {nullptr, nullptr};
@@ -69,6 +71,11 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
                            const std::vector<mg::CoarseOp>* ops, mgrit_handle** out);
 // Device bytes a handle for this request will allocate (admission control).
 size_t handle_bytes(const mgrit_problem* prob, const mgrit_opts* opts);
+// SDIRK stage-solve plan for the problem (factored stage matrix), checked on
+// the host against the stage matrix itself.
+mgrit_status make_sdirk_plan(const mgrit_problem* prob, mg::SdirkPlan* out);
+// Launch the fine-level FCF (ERK stencil or SDIRK) of a handle.
+cudaError_t launch_fine_fcf(mgrit_handle* h, const mg::FcfArgs& f, int prec);
 // Copy the converged C-points cres out per opts.output (FULL interpolates).
 mgrit_status write_output(mgrit_handle* h, const double* cres, double* out);
 

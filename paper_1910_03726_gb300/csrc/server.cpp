@@ -228,7 +228,13 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
   std::map<std::pair<int, int>, std::vector<int>> groups;
   const int tile = get_tile();
   for (int k = 0; k < n; ++k) {
-    const mgrit_handle* h = act[k]->h;
+    mgrit_handle* h = act[k]->h;
+    if (h->sdirk) {  // SDIRK fine levels relax through their own launch
+      cudaError_t e = launch_fine_fcf(h, hs[k].fcf, hs[k].prec);
+      if (e != cudaSuccess) return launch_ok(e, "fcf_sdirk");
+      h->kcount[MGRIT_K_FCF]++;
+      continue;
+    }
     const int tiled = (h->dphi.span > 0 && h->nx >= 64 && tile > 0) ? 1 : 0;
     groups[{h->nx, tiled}].push_back(k);
   }
