@@ -86,7 +86,13 @@ enum { MGRIT_OUT_FINAL = 0, MGRIT_OUT_CPOINTS = 1, MGRIT_OUT_FULL = 2 };
 /* MGRIT_FLAG_TIME_KERNELS: bracket every kernel launch of a solve with CUDA
  * events on the handle's stream and report per-kind device time in
  * mgrit_result.kernel_ms (adds two event records per launch). */
-enum { MGRIT_FLAG_TIME_KERNELS = 1 };
+/* MGRIT_FLAG_NO_AUTOTUNE: skip the setup-time timing of the level-1 FCF
+ * launch shapes and use the built-in defaults. */
+/* MGRIT_FLAG_HOST_LOOP: drive the cycles from the host (one read-back per
+ * cycle) instead of the default single CUDA-graph launch per solve, whose
+ * WHILE/IF conditional nodes are set by an on-device stopping test.
+ * MGRIT_FLAG_TIME_KERNELS implies the host loop. */
+enum { MGRIT_FLAG_TIME_KERNELS = 1, MGRIT_FLAG_NO_AUTOTUNE = 2, MGRIT_FLAG_HOST_LOOP = 4 };
 
 /* Kernel kinds reported in mgrit_result.kernel_ms / kernel_count. */
 enum {
@@ -146,7 +152,9 @@ typedef struct mgrit_result {
   double op_complexity;  /* Eq. 5 (ERK; 0 for SDIRK, whose Phi is dense)            */
   double history[MGRIT_MAX_HISTORY]; /* relative residual after each FCF            */
   int32_t launches;      /* kernels this call launched                              */
-  int32_t reserved;
+  int32_t fine_tile;     /* level-1 FCF launch shape picked by the autotuner:       */
+  int32_t fine_threads;  /*   register tile (99 = fixed-span path) and CTA size     */
+  int32_t graph;         /* 1 if the solve ran as one CUDA-graph launch             */
   int32_t kernel_count[MGRIT_K_KINDS];  /* launches per kind                         */
   double kernel_ms[MGRIT_K_KINDS];      /* device time per kind (FLAG_TIME_KERNELS)  */
 } mgrit_result;

@@ -29,6 +29,8 @@ OUT_FINAL, OUT_CPOINTS, OUT_FULL = 0, 1, 2
 MAX_HISTORY = 128
 MAX_LEVELS = 8
 FLAG_TIME_KERNELS = 1
+FLAG_NO_AUTOTUNE = 2
+FLAG_HOST_LOOP = 4
 KERNEL_KINDS = ["fcf", "fcf_coarse", "march", "correct", "norm", "add", "propagate", "other"]
 K_KINDS = len(KERNEL_KINDS)
 
@@ -57,7 +59,8 @@ class MgritResult(C.Structure):
                 ("n_history", C.c_int32), ("rel_residual", C.c_double), ("r0_norm", C.c_double),
                 ("setup_s", C.c_double), ("solve_s", C.c_double), ("dof_per_s", C.c_double),
                 ("op_complexity", C.c_double), ("history", C.c_double * MAX_HISTORY),
-                ("launches", C.c_int32), ("reserved", C.c_int32), ("kernel_count", C.c_int32 * K_KINDS),
+                ("launches", C.c_int32), ("fine_tile", C.c_int32), ("fine_threads", C.c_int32),
+                ("graph", C.c_int32), ("kernel_count", C.c_int32 * K_KINDS),
                 ("kernel_ms", C.c_double * K_KINDS)]
 
     def as_dict(self):

@@ -16,12 +16,17 @@ constexpr int kMaxSpan = 256;
 // shift (sigma) is the moving-frame shift used by the sequential march.
 struct DevTaps {
   int n, lo, hi, span;
-  int shift, pad0, pad1, pad2;
+  int shift;
+  float one;       // 1.0f, read at run time (see the float-float accumulation)
+  int pad1, pad2;
   int off[kMaxDevTaps];
   double c64[kMaxDevTaps];
   float c32[kMaxDevTaps];
   double d64[kMaxSpan];
   float d32[kMaxSpan];
+  // float-float split of the coefficients (c = hi + lo, |lo| <= ulp(hi)/2)
+  float chi[kMaxDevTaps], clo[kMaxDevTaps];
+  float dhi[kMaxSpan], dlo[kMaxSpan];
 };
 
 // Fill a DevTaps from n (offset, coefficient) pairs; false if n > kMaxDevTaps.
@@ -66,12 +71,34 @@ struct CorrectArgs {
   int nx, m, N;
 };
 
+// tile: register tile (0, 4 or 8), kFixedTile for the fixed-span path of the
+// collapsed ERK stencils; -1 = the default for this stencil and nx.
+constexpr int kFixedTile = 99;
 cudaError_t launch_fcf(const FcfArgs& a, const DevTaps& t, int precision, int threads,
-                       cudaStream_t s);
+                       cudaStream_t s, int tile = -1);
 
 // Shared-memory slab length for nx points in the padded layout (one pad
 // element per 8 so that per-thread chunks of 8 are bank-conflict free).
 __host__ __device__ inline int padded_len(int nx) { return nx + (nx >> 3) + 1; }
+
+// ------------------------------------------------------- device-side cycle test
+// State of the stopping test when a whole solve runs as one CUDA graph: the
+// check kernel reads ||r||^2 (and ||r^(0)||^2), records the relative
+// residual, and drives the graph's WHILE/IF conditions.
+struct CheckState {
+  double r0sq;            // ||r^(0)||^2 (written by the initial-residual kernel)
+  double tol;
+  int max_iter;
+  int it;                 // coarse corrections applied so far
+  int done;               // 1 once the test has stopped the loop
+  int status;             // mgrit_status of the stop
+  int result_cur;         // buffer index read by the final FCF (result in c[1-cur])
+  int nhist;
+  double rel;
+  double hist[128];
+};
+cudaError_t launch_check(const double* norm2, CheckState* st, unsigned long long while_handle,
+                         unsigned long long if_handle, int cur, cudaStream_t s);
 
 // ------------------------------------------------------------- SDIRK steps
 // One SDIRK step (stage form, Appendix A tableaux):
@@ -124,13 +151,15 @@ struct BatchItem {
   int solve, j;        // solve index, interval j (1..N)
 };
 cudaError_t launch_fcf_batched(const BatchSolve* S, const BatchItem* items, int nitems, const DevTaps* taps,
-                               int max_nx, int threads, cudaStream_t s);
+                               int max_nx, int threads, int tile, int span, cudaStream_t s);
+int default_threads(int nx, int tile);        // CTA size the launches pick for nx
+int default_tile(const DevTaps& t, int nx);   // register tile the launches pick
 cudaError_t launch_norm_batched(const BatchSolve* S, const int* ids, int count, double* out, cudaStream_t s);
 cudaError_t launch_march_batched(const BatchSolve* S, const int* ids, int count, const DevTaps* taps, int cluster,
                                  int max_w, int max_halo, cudaStream_t s);
 cudaError_t launch_march(const MarchArgs& a, const DevTaps& t, int cluster, int threads,
                          cudaStream_t s);
-cudaError_t launch_correct(const CorrectArgs& a, const DevTaps& t, int threads, cudaStream_t s);
+cudaError_t launch_correct(const CorrectArgs& a, const DevTaps& t, int threads, cudaStream_t s, int fp32 = 0);
 cudaError_t launch_norm(const double* partial, int n, double* out, cudaStream_t s);
 cudaError_t launch_add(double* c, const double* e, long long count, cudaStream_t s);
 cudaError_t launch_propagate(const double* in, double* out, int count, int nx, int k,

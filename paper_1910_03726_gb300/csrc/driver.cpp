@@ -6,6 +6,9 @@
 
 #include <algorithm>
 #include <chrono>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <complex>
 #include <cmath>
 #include <cstdlib>
@@ -95,6 +98,14 @@ void release(mgrit_handle* h) {
   h->norm_host = nullptr;
   for (auto ev : h->evpool) cudaEventDestroy(ev);
   h->evpool.clear();
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->hstate) cudaFreeHost(h->hstate);
+  h->gexec = nullptr;
+  h->graph = nullptr;
+  h->cap_stream = nullptr;
+  h->hstate = nullptr;
   cudaStreamSynchronize(h->stream);
 }
 
@@ -260,7 +271,12 @@ extern "C" mgrit_status mgrit_psi_plan(const mgrit_problem* prob, const mgrit_op
 // at least 64 points per CTA and a CTA at least as wide as the stencil (the
 // march runs in the stencil's moving frame, so only the width matters).
 int pick_cluster(int nx, const Taps& t) {
-  const int width = t.hi() - t.lo();
+  int lo = t.off.empty() ? 0 : t.off[0], hi = lo;
+  for (int o : t.off) {
+    lo = std::min(lo, o);
+    hi = std::max(hi, o);
+  }
+  const int width = hi - lo;
   for (int cs = march_max_cluster(); cs > 1; cs >>= 1)
     if (nx % cs == 0 && nx / cs >= std::max(64, width)) return cs;
   return 1;
@@ -373,9 +389,97 @@ mgrit_status make_sdirk_plan(const mgrit_problem* prob, SdirkPlan* out) {
   return MGRIT_OK;
 }
 
+int fine_prec(const mgrit_handle* h) {
+  if (h->opts.precision == MGRIT_PREC_FP64) return 0;
+  if (h->opts.precision == MGRIT_PREC_MIXED_DF && !h->sdirk) return 3;
+  return 1;  // SDIRK keeps its FP64 pass in MIXED_DF
+}
+
+namespace {
+struct TuneKey {
+  int prec, nx, span, ntaps, m;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(prec, nx, span, ntaps, m) < std::tie(o.prec, o.nx, o.span, o.ntaps, o.m);
+  }
+};
+std::map<TuneKey, std::pair<int, int>> g_tune;
+std::mutex g_tune_mu;
+}  // namespace
+
+void autotune_fine(mgrit_handle* h) {
+  const int prec = fine_prec(h);
+  h->fine_tile = default_tile(h->dphi, h->nx);
+  h->fine_threads = default_threads(h->nx, h->fine_tile);
+  if (h->sdirk || (h->opts.flags & MGRIT_FLAG_NO_AUTOTUNE)) return;
+  const TuneKey key{prec, h->nx, h->dphi.span, h->dphi.n, h->m};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      h->fine_tile = it->second.first;
+      h->fine_threads = it->second.second;
+      return;
+    }
+  }
+  const int nx = h->nx;
+  FcfArgs f = {};
+  f.u_old = h->c[0];
+  f.cstride = nx;
+  f.c_new = h->c[1];
+  f.r = h->r[1];
+  f.partial = h->partial;
+  f.nx = nx;
+  f.m = h->m;
+  f.N = std::min(h->Nl[1], 3 * 152 * 2);
+  cudaMemsetAsync(h->c[0], 0, ((size_t)f.N + 1) * nx * sizeof(double), h->stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  float best = 1e30f;
+  std::pair<int, int> pick{h->fine_tile, h->fine_threads};
+  const bool dense = h->dphi.span > 0 && nx >= 64;
+  for (int tile : {kFixedTile, 8, 4, 0}) {
+    if (tile > 0 && !dense) continue;
+    if (tile == kFixedTile && !(h->dphi.span == 2 || h->dphi.span == 5 || h->dphi.span == 10 ||
+                                h->dphi.span == 17 || h->dphi.span == 31))
+      continue;
+    const int per = tile == kFixedTile ? 4 : (tile > 0 ? tile : 1);
+    for (int th : {128, 256, 512}) {
+      if (th > std::max(32, (nx / per + 31) / 32 * 32)) continue;
+      if (launch_fcf(f, h->dphi, prec, th, h->stream, tile) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      float t = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, h->stream);
+        launch_fcf(f, h->dphi, prec, th, h->stream, tile);
+        cudaEventRecord(e1, h->stream);
+        float ms = 0.0f;
+        if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+          t = std::min(t, ms);
+        else
+          cudaGetLastError();
+      }
+      if (t < best) {
+        best = t;
+        pick = {tile, th};
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->fine_tile = pick.first;
+  h->fine_threads = pick.second;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = pick;
+}
+
 cudaError_t launch_fine_fcf(mgrit_handle* h, const FcfArgs& f, int prec) {
-  if (h->sdirk) return launch_fcf_sdirk(f, h->splan, prec, h->stream);
-  return launch_fcf(f, h->dphi, prec, h->fcf_threads, h->stream);
+  if (h->sdirk) return launch_fcf_sdirk(f, h->splan, prec == 0 ? 0 : 1, h->stream);
+  return launch_fcf(f, h->dphi, prec, h->fine_threads, h->stream, h->fine_tile);
 }
 
 size_t handle_bytes(const mgrit_problem* prob, const mgrit_opts* opts) {
@@ -399,7 +503,6 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
   mgrit_status st = validate_problem(prob);
   if (st == MGRIT_OK) st = validate_opts(prob, opts);
   if (st != MGRIT_OK) return st;
-  if (opts->precision == MGRIT_PREC_MIXED_DF) return fail(MGRIT_ERR_UNSUPPORTED, "float-float mode not built yet");
   if (2.0 * prob->nx * sizeof(double) > 227.0 * 1024.0)
     return fail(MGRIT_ERR_UNSUPPORTED, "nx too large for one shared-memory slab (max 14528)");
   mgrit_handle* h = new mgrit_handle();
@@ -507,6 +610,7 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
   const Taps& coarsest = h->ops.back().taps;
   h->march_cluster = pick_cluster(nx, coarsest);
   h->march_threads = std::min(256, nx / h->march_cluster);
+  autotune_fine(h);
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
     release(h);
@@ -579,6 +683,8 @@ void collect_stats(mgrit_handle* h, mgrit_result* R) {
     total += h->kcount[k];
   }
   R->launches = total;
+  R->fine_tile = h->fine_tile;
+  R->fine_threads = h->fine_threads;
   for (size_t p = 0; p < h->evkind.size(); ++p) {
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, h->evpool[2 * p], h->evpool[2 * p + 1]) == cudaSuccess)
@@ -624,7 +730,8 @@ mgrit_status initial_residual(mgrit_handle* h, const double* u0dev, double* r0) 
 // come back up; finally c_new += e on level 1 (or fused into the march, L = 2).
 mgrit_status coarse_cycle(mgrit_handle* h, double* c_new) {
   const int L = h->L, m = h->m, nx = h->nx;
-  const int prec = h->opts.precision == MGRIT_PREC_FP64 ? 0 : 1;
+  // coarse levels relax the error equation: FP32 in the mixed modes
+  const int prec = h->opts.precision == MGRIT_PREC_FP64 ? 0 : 2;
   mgrit_status st;
   if (L == 2) {
     MarchArgs a = {};
@@ -670,7 +777,7 @@ mgrit_status coarse_cycle(mgrit_handle* h, double* c_new) {
     c.m = m;
     c.N = h->Nl[l];
     if ((st = klaunch(h, MGRIT_K_CORRECT, "correct", [&] {
-           return launch_ok(launch_correct(c, h->dpsi[l - 2], h->fcf_threads, h->stream), "correct");
+           return launch_ok(launch_correct(c, h->dpsi[l - 2], h->fcf_threads, h->stream, prec == 2), "correct");
          })) != MGRIT_OK)
       return st;
   }
@@ -721,6 +828,154 @@ mgrit_status write_output(mgrit_handle* h, const double* cres, double* out) {
   return MGRIT_OK;
 }
 
+// ----------------------------------------------------------- graph solve
+
+// Capture the launches fn() issues on the handle into `body` (a conditional
+// node's body graph); *leaf receives the last captured node.
+template <typename F>
+static mgrit_status capture_into(mgrit_handle* h, cudaGraph_t body, F&& fn, cudaGraphNode_t* leaf) {
+  cudaStream_t saved = h->stream;
+  cudaError_t e = cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return launch_ok(e, "begin capture");
+  h->stream = h->cap_stream;
+  mgrit_status st = fn();
+  h->stream = saved;
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  e = cudaStreamGetCaptureInfo(h->cap_stream, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+  if (e == cudaSuccess && leaf) *leaf = ndeps ? deps[0] : nullptr;
+  cudaGraph_t out = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &out);
+  if (st != MGRIT_OK) return st;
+  if (e != cudaSuccess) return launch_ok(e, "capture info");
+  return launch_ok(e2, "end capture");
+}
+
+static mgrit_status add_conditional(cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle hd,
+                                    cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = hd;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  cudaError_t e = cudaGraphAddNode(&node, g, dep ? &dep : nullptr, nullptr, dep ? 1 : 0, &p);
+  if (e != cudaSuccess) return launch_ok(e, "conditional node");
+  *body = p.conditional.phGraph_out[0];
+  return MGRIT_OK;
+}
+
+// One level-1 FCF + norm + stopping test reading c[cur], writing c[1-cur].
+static mgrit_status graph_cycle(mgrit_handle* h, int cur, cudaGraphConditionalHandle hw,
+                                cudaGraphConditionalHandle hif) {
+  const int nx = h->nx;
+  FcfArgs f = {};
+  f.u_old = h->c[cur];
+  f.cstride = nx;
+  f.c_new = h->c[1 - cur];
+  f.r = h->r[1];
+  f.partial = h->partial;
+  f.nx = nx;
+  f.m = h->m;
+  f.N = h->Nl[1];
+  mgrit_status st;
+  if ((st = launch_ok(launch_fine_fcf(h, f, fine_prec(h)), "fcf")) != MGRIT_OK) return st;
+  if ((st = launch_ok(launch_norm(h->partial, h->Nl[1], h->scratch + 2 * nx, h->stream), "norm")) != MGRIT_OK)
+    return st;
+  return launch_ok(launch_check(h->scratch + 2 * nx, h->dstate, hw, hif, cur, h->stream), "check");
+}
+
+// WHILE(not stopped) { cycle(0); IF(go on) { coarse -> c[1]; cycle(1); IF(go on) { coarse -> c[0] } } }
+static mgrit_status build_solve_graph(mgrit_handle* h) {
+  mgrit_status st;
+  if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return launch_ok(cudaGetLastError(), "capture stream");
+  if (!h->dstate) {
+    double* p = nullptr;
+    if ((st = dalloc(h, sizeof(CheckState) / sizeof(double) + 1, &p)) != MGRIT_OK) return st;
+    h->dstate = reinterpret_cast<CheckState*>(p);
+  }
+  if (!h->hstate && cudaMallocHost(&h->hstate, sizeof(CheckState)) != cudaSuccess)
+    return launch_ok(cudaGetLastError(), "pinned state");
+  cudaGraph_t g = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return launch_ok(cudaGetLastError(), "graph");
+  h->graph = g;
+  // each conditional handle belongs to the graph that holds its node
+  cudaGraphConditionalHandle hw, hif0, hif1;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&hw, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return launch_ok(e, "conditional handle");
+  cudaGraph_t body_w, body_if0, body_if1;
+  cudaGraphNode_t leaf = nullptr;
+  if ((st = add_conditional(g, nullptr, hw, cudaGraphCondTypeWhile, &body_w)) != MGRIT_OK) return st;
+  if ((e = cudaGraphConditionalHandleCreate(&hif0, body_w, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+    return launch_ok(e, "conditional handle");
+  if ((st = capture_into(h, body_w, [&] { return graph_cycle(h, 0, hw, hif0); }, &leaf)) != MGRIT_OK) return st;
+  if ((st = add_conditional(body_w, leaf, hif0, cudaGraphCondTypeIf, &body_if0)) != MGRIT_OK) return st;
+  if ((e = cudaGraphConditionalHandleCreate(&hif1, body_if0, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+    return launch_ok(e, "conditional handle");
+  const int before = h->kcount[MGRIT_K_MARCH] + h->kcount[MGRIT_K_FCF_COARSE] + h->kcount[MGRIT_K_CORRECT] +
+                     h->kcount[MGRIT_K_ADD];
+  if ((st = capture_into(h, body_if0, [&] {
+         mgrit_status s2 = coarse_cycle(h, h->c[1]);
+         return s2 != MGRIT_OK ? s2 : graph_cycle(h, 1, hw, hif1);
+       }, &leaf)) != MGRIT_OK)
+    return st;
+  h->graph_coarse_launches = h->kcount[MGRIT_K_MARCH] + h->kcount[MGRIT_K_FCF_COARSE] +
+                             h->kcount[MGRIT_K_CORRECT] + h->kcount[MGRIT_K_ADD] - before;
+  if ((st = add_conditional(body_if0, leaf, hif1, cudaGraphCondTypeIf, &body_if1)) != MGRIT_OK) return st;
+  if ((st = capture_into(h, body_if1, [&] { return coarse_cycle(h, h->c[0]); }, nullptr)) != MGRIT_OK) return st;
+  e = cudaGraphInstantiate(&h->gexec, g, 0);
+  if (e != cudaSuccess) return launch_ok(e, "graph instantiate");
+  return MGRIT_OK;
+}
+
+// Whole solve: prologue on the stream, one graph launch, one read-back.
+static mgrit_status solve_graph(mgrit_handle* h, const double* u0, double* out, mgrit_result* R) {
+  const int nx = h->nx;
+  const size_t N1 = h->Nl[1];
+  const size_t slab = (size_t)nx * sizeof(double);
+  CUDA_TRY(cudaMemcpyAsync(h->c[0], u0, slab, kind_to_dev(u0), h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->c[1], h->c[0], slab, cudaMemcpyDeviceToDevice, h->stream));
+  CUDA_TRY(cudaMemsetAsync(h->c[0] + nx, 0, N1 * slab, h->stream));
+  std::memset(h->hstate, 0, sizeof(CheckState));
+  h->hstate->tol = h->opts.tol;
+  h->hstate->max_iter = h->opts.max_iter;
+  CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(CheckState), cudaMemcpyHostToDevice, h->stream));
+  // ||Phi u0||^2 straight into the state (zero initial iterate: r^(0) = Phi u0)
+  mgrit_status st;
+  if ((st = launch_ok(h->sdirk ? launch_propagate_sdirk(h->c[0], h->scratch, 1, nx, 1, h->splan, &h->dstate->r0sq,
+                                                        h->stream)
+                               : launch_propagate(h->c[0], h->scratch, 1, nx, 1, h->dphi, &h->dstate->r0sq,
+                                                  h->fcf_threads, h->stream),
+                      "propagate")) != MGRIT_OK)
+    return st;
+  CUDA_TRY(cudaGraphLaunch(h->gexec, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(CheckState), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  const CheckState& S = *h->hstate;
+  R->r0_norm = std::sqrt(S.r0sq);
+  R->iterations = S.it;
+  R->rel_residual = S.rel;
+  R->n_history = std::min(S.nhist, MGRIT_MAX_HISTORY);
+  for (int k = 0; k < R->n_history; ++k) R->history[k] = S.hist[k];
+  R->converged = S.status == 0 && S.done ? 1 : 0;
+  // launches: initial residual, (it+1) x (fcf, norm, check), it x coarse correction
+  reset_stats(h);
+  h->kcount[MGRIT_K_PROPAGATE] = 1;
+  h->kcount[MGRIT_K_FCF] = S.it + 1;
+  h->kcount[MGRIT_K_NORM] = S.it + 1;
+  h->kcount[MGRIT_K_OTHER] = S.it + 1;
+  if (out && (st = write_output(h, h->c[1 - S.result_cur], out)) != MGRIT_OK) return st;
+  const int other_before = h->kcount[MGRIT_K_OTHER];
+  (void)other_before;
+  if (!S.done) return fail(MGRIT_ERR_CUDA, "graph ended without a stopping decision");
+  if (S.status == -5) return fail(MGRIT_ERR_DIVERGED, "residual not finite or grew above 1e6 x initial");
+  if (S.status == -4) return fail(MGRIT_ERR_NOT_CONVERGED, "max_iter reached");
+  return MGRIT_OK;
+}
+
 extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* out, mgrit_result* res) {
   if (!h) return fail(MGRIT_ERR_INVALID, "handle is NULL");
   if (!u0) return fail(MGRIT_ERR_INVALID, "u0 is NULL");
@@ -734,6 +989,37 @@ extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* o
   R.setup_s = h->setup_s;
   R.op_complexity = h->op_complexity;
   reset_stats(h);
+  const bool host_loop = (h->opts.flags & (MGRIT_FLAG_TIME_KERNELS | MGRIT_FLAG_HOST_LOOP)) != 0;
+  if (!host_loop && !h->graph_failed) {
+    if (!h->gexec) {
+      const std::string keep = g_err;
+      mgrit_status gs = build_solve_graph(h);
+      if (gs != MGRIT_OK) {
+        // fall back to the host-driven loop; keep no half-built graph
+        h->graph_failed = true;
+        if (h->gexec) cudaGraphExecDestroy(h->gexec);
+        if (h->graph) cudaGraphDestroy(h->graph);
+        h->gexec = nullptr;
+        h->graph = nullptr;
+        cudaGetLastError();
+        g_err = keep;
+      }
+    }
+    if (h->gexec) {
+      mgrit_status gs = solve_graph(h, u0, out, &R);
+      if (gs == MGRIT_OK || gs == MGRIT_ERR_NOT_CONVERGED || gs == MGRIT_ERR_DIVERGED) {
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        R.solve_s = now_s() - t0;
+        R.dof_per_s = R.solve_s > 0 ? (double)nx * h->nt / R.solve_s : 0.0;
+        collect_stats(h, &R);
+        R.launches += R.iterations * h->graph_coarse_launches;
+        R.graph = 1;
+        if (res) *res = R;
+        return gs;
+      }
+      return gs;
+    }
+  }
   int cur = 0;
   CUDA_TRY(cudaMemcpyAsync(h->c[0], u0, slab, kind_to_dev(u0), h->stream));
   CUDA_TRY(cudaMemcpyAsync(h->c[1], h->c[0], slab, cudaMemcpyDeviceToDevice, h->stream));
@@ -742,7 +1028,7 @@ extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* o
   mgrit_status st = initial_residual(h, h->c[0], &r0);
   if (st != MGRIT_OK) return st;
   R.r0_norm = r0;
-  const int prec = h->opts.precision == MGRIT_PREC_FP64 ? 0 : 1;
+  const int prec = fine_prec(h);
   mgrit_status final_status = MGRIT_OK;
   int it = 0;
   for (;;) {

@@ -37,6 +37,16 @@ struct mgrit_handle {
   double* scratch = nullptr;      // 2*nx + 1 doubles
   double* norm_host = nullptr;    // pinned
   int fcf_threads = 512, march_cluster = 1, march_threads = 256;
+  int fine_tile = -1, fine_threads = 0;   // level-1 FCF launch shape (autotuned)
+  // a whole solve as one CUDA graph (WHILE over cycles, IF around each
+  // coarse correction), built at the first solve
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  bool graph_failed = false;
+  int graph_coarse_launches = 0;          // kernels of one coarse correction
+  mg::CheckState* dstate = nullptr;       // device
+  mg::CheckState* hstate = nullptr;       // pinned host
   // per-solve launch accounting (and CUDA-event timing with MGRIT_FLAG_TIME_KERNELS)
   int kcount[MGRIT_K_KINDS] = {0};
   std::vector<cudaEvent_t> evpool;
@@ -74,6 +84,11 @@ size_t handle_bytes(const mgrit_problem* prob, const mgrit_opts* opts);
 // SDIRK stage-solve plan for the problem (factored stage matrix), checked on
 // the host against the stage matrix itself.
 mgrit_status make_sdirk_plan(const mgrit_problem* prob, mg::SdirkPlan* out);
+// Fine-level FCF arithmetic of a handle: 0 FP64, 1 FP64 + FP32, 3 float-float + FP32.
+int fine_prec(const mgrit_handle* h);
+// Pick the level-1 FCF launch shape (register tile, CTA size) by timing the
+// candidates on the handle's buffers; cached per shape key for the process.
+void autotune_fine(mgrit_handle* h);
 // Launch the fine-level FCF (ERK stencil or SDIRK) of a handle.
 cudaError_t launch_fine_fcf(mgrit_handle* h, const mg::FcfArgs& f, int prec);
 // Copy the converged C-points cres out per opts.output (FULL interpolates).

@@ -32,10 +32,19 @@ bool make_dev_taps(const int* off, const double* coef, int n, DevTaps* d) {
   }
   d->lo = lo;
   d->hi = hi;
+  d->one = 1.0f;
   d->span = hi - lo + 1 <= kMaxSpan ? hi - lo + 1 : 0;
   if (d->span)
     for (int k = 0; k < n; ++k) d->d64[off[k] - lo] += coef[k];
   for (int k = 0; k < d->span; ++k) d->d32[k] = (float)d->d64[k];
+  for (int k = 0; k < n; ++k) {
+    d->chi[k] = (float)coef[k];
+    d->clo[k] = (float)(coef[k] - (double)d->chi[k]);
+  }
+  for (int k = 0; k < d->span; ++k) {
+    d->dhi[k] = (float)d->d64[k];
+    d->dlo[k] = (float)(d->d64[k] - (double)d->dhi[k]);
+  }
   // frame shift for the march: centre of the offsets (floor)
   d->shift = (lo + hi) >= 0 ? (lo + hi) / 2 : -((-(lo + hi) + 1) / 2);
   return true;
@@ -50,6 +59,64 @@ __device__ __forceinline__ int wrapi(int k, int nx) {
 // owning consecutive chunks of 8 elements hit distinct banks.
 __device__ __forceinline__ int pidx(int e) { return e + (e >> 3); }
 
+// Float-float value: hi + lo with |lo| <= ulp(hi)/2 (about 48 significant
+// bits), evaluated on the FP32 pipes.
+struct __align__(8) df64 {
+  float hi, lo;
+};
+
+// acc + c * x, c and x float-float: exact hi*hi product (TwoProd by FMA), the
+// cross terms into the low word, TwoSum on the high words.  Half of the
+// additions run as fma(a, one, b) (one = 1.0f from the kernel parameters, so
+// it is not folded): the same rounding as a + b, issued to the FMA pipe to
+// balance it against the add pipe.
+__device__ __forceinline__ df64 df_fma1(df64 c, df64 x, df64 acc, float one) {
+  const float p = c.hi * x.hi;
+  float e = fmaf(c.hi, x.hi, -p);
+  e = fmaf(c.hi, x.lo, e);
+  e = fmaf(c.lo, x.hi, e);
+  const float s = fmaf(p, one, acc.hi);
+  const float bb = fmaf(acc.hi, -one, s);
+  const float err = (acc.hi - (s - bb)) + (p - bb);
+  return {s, fmaf(fmaf(err, one, e), one, acc.lo)};
+}
+__device__ __forceinline__ df64 df_fma(df64 c, df64 x, df64 acc) { return df_fma1(c, x, acc, 1.0f); }
+__device__ __forceinline__ df64 df_norm(df64 a) {
+  const float s = a.hi + a.lo;
+  return {s, a.lo - (s - a.hi)};
+}
+__device__ __forceinline__ df64 df_from(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double df_to(df64 a) { return (double)a.hi + (double)a.lo; }
+
+// Generic arithmetic over double, float and df64 slabs.
+template <typename T>
+__device__ __forceinline__ T vzero() { return (T)0; }
+template <>
+__device__ __forceinline__ df64 vzero<df64>() { return {0.0f, 0.0f}; }
+template <typename T>
+__device__ __forceinline__ T vfrom(double v) { return (T)v; }
+template <>
+__device__ __forceinline__ df64 vfrom<df64>(double v) { return df_from(v); }
+template <typename T>
+__device__ __forceinline__ T vfma(T c, T x, T acc) { return fma(c, x, acc); }
+template <>
+__device__ __forceinline__ df64 vfma<df64>(df64 c, df64 x, df64 acc) { return df_fma(c, x, acc); }
+template <typename T>
+__device__ __forceinline__ T vfma1(T c, T x, T acc, float one) { return fma(c, x, acc); }
+template <>
+__device__ __forceinline__ df64 vfma1<df64>(df64 c, df64 x, df64 acc, float one) { return df_fma1(c, x, acc, one); }
+template <typename T>
+__device__ __forceinline__ T vfinish(T a) { return a; }
+template <>
+__device__ __forceinline__ df64 vfinish<df64>(df64 a) { return df_norm(a); }
+template <typename T>
+__device__ __forceinline__ bool vnonzero(T c) { return c != (T)0; }
+template <>
+__device__ __forceinline__ bool vnonzero<df64>(df64 c) { return c.hi != 0.0f || c.lo != 0.0f; }
+
 template <typename T>
 __device__ __forceinline__ T sparse_coef(const DevTaps& t, int k);
 template <>
@@ -62,15 +129,19 @@ template <>
 __device__ __forceinline__ double dense_coef<double>(const DevTaps& t, int k) { return t.d64[k]; }
 template <>
 __device__ __forceinline__ float dense_coef<float>(const DevTaps& t, int k) { return t.d32[k]; }
+template <>
+__device__ __forceinline__ df64 sparse_coef<df64>(const DevTaps& t, int k) { return {t.chi[k], t.clo[k]}; }
+template <>
+__device__ __forceinline__ df64 dense_coef<df64>(const DevTaps& t, int k) { return {t.dhi[k], t.dlo[k]}; }
 
 // dst = T src (+ g): one tap at a time, any offsets (padded layout).
 template <typename T>
 __device__ __forceinline__ void step_sparse(const DevTaps& t, const T* __restrict__ src, T* __restrict__ dst,
                                            const double* __restrict__ g, int nx) {
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    T acc = g ? (T)__ldg(g + i) : (T)0;
-    for (int k = 0; k < t.n; ++k) acc = fma(sparse_coef<T>(t, k), src[pidx(wrapi(i + t.off[k], nx))], acc);
-    dst[pidx(i)] = acc;
+    T acc = g ? vfrom<T>(__ldg(g + i)) : vzero<T>();
+    for (int k = 0; k < t.n; ++k) acc = vfma<T>(sparse_coef<T>(t, k), src[pidx(wrapi(i + t.off[k], nx))], acc);
+    dst[pidx(i)] = vfinish<T>(acc);
   }
 }
 
@@ -86,14 +157,14 @@ __device__ __forceinline__ void step_tiled(const DevTaps& t, const T* __restrict
     T acc[R], w[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      acc[r] = (g && i0 + r < nx) ? (T)__ldg(g + i0 + r) : (T)0;
+      acc[r] = (g && i0 + r < nx) ? vfrom<T>(__ldg(g + i0 + r)) : vzero<T>();
       w[r] = src[pidx(wrapi(i0 + lo + r, nx))];
     }
     for (int k = 0; k < span; ++k) {
       const T c = dense_coef<T>(t, k);
-      if (c != (T)0) {
+      if (vnonzero<T>(c)) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = fma(c, w[r], acc[r]);
+        for (int r = 0; r < R; ++r) acc[r] = vfma<T>(c, w[r], acc[r]);
       }
 #pragma unroll
       for (int r = 0; r < R - 1; ++r) w[r] = w[r + 1];
@@ -101,13 +172,37 @@ __device__ __forceinline__ void step_tiled(const DevTaps& t, const T* __restrict
     }
 #pragma unroll
     for (int r = 0; r < R; ++r)
-      if (i0 + r < nx) dst[pidx(i0 + r)] = acc[r];
+      if (i0 + r < nx) dst[pidx(i0 + r)] = vfinish<T>(acc[r]);
   }
 }
 
-template <typename T, int R>
+// dst = T src (+ g) for a stencil whose dense span is the compile-time SPAN:
+// each thread loads its R + SPAN - 1 inputs once and keeps them in registers;
+// coefficients are read from the kernel parameters (constant bank).
+template <typename T, int R, int SPAN>
+__device__ __forceinline__ void step_fixed(const DevTaps& t, const T* __restrict__ src, T* __restrict__ dst,
+                                           const double* __restrict__ g, int nx) {
+  const int lo = t.lo;
+  for (int i0 = threadIdx.x * R; i0 < nx; i0 += blockDim.x * R) {
+    T w[R + SPAN - 1];
+#pragma unroll
+    for (int q = 0; q < R + SPAN - 1; ++q) w[q] = src[pidx(wrapi(i0 + lo + q, nx))];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      T acc = (g && i0 + r < nx) ? vfrom<T>(__ldg(g + i0 + r)) : vzero<T>();
+#pragma unroll
+      for (int k = 0; k < SPAN; ++k) acc = vfma1<T>(dense_coef<T>(t, k), w[r + k], acc, t.one);
+      if (i0 + r < nx) dst[pidx(i0 + r)] = vfinish<T>(acc);
+    }
+  }
+}
+
+// R encodes the path: 0 one tap at a time; 4, 8 sliding window; SPAN > 0
+// selects the fixed-span path with register tile R.
+template <typename T, int R, int SPAN = 0>
 __device__ __forceinline__ void slab_step(const DevTaps& t, const T* src, T* dst, const double* g, int nx) {
-  if constexpr (R > 0) step_tiled<T, R>(t, src, dst, g, nx);
+  if constexpr (SPAN > 0) step_fixed<T, R, SPAN>(t, src, dst, g, nx);
+  else if constexpr (R > 0) step_tiled<T, R>(t, src, dst, g, nx);
   else step_sparse<T>(t, src, dst, g, nx);
 }
 
@@ -132,8 +227,106 @@ __device__ double block_sum(double v) {
 // once per cycle.  PREC 0: both passes FP64.  PREC 1: the second pass (acting
 // on the correction rho) in FP32.
 // ----------------------------------------------------------------------------
-template <int PREC, int R>
+// PREC 2: both passes in FP32 (coarse levels of the mixed mode, where every
+// quantity is a correction of the error equation).
+template <int R, int SPAN = 0>
+__device__ __forceinline__ void fcf_body_fp32(const FcfArgs& a, const int j, const DevTaps& t, unsigned char* smraw) {
+  const int nx = a.nx, m = a.m, plen = padded_len(nx);
+  float* b0 = reinterpret_cast<float*>(smraw);
+  float* b1 = b0 + plen;
+  const double* start = a.u_old + (long long)(j - 1) * a.cstride;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) b0[pidx(i)] = a.zero_old ? 0.0f : (float)start[i];
+  __syncthreads();
+  for (int s = 1; s <= m; ++s) {
+    const double* g = a.g ? a.g + ((long long)(j - 1) * m + s) * nx : nullptr;
+    slab_step<float, R, SPAN>(t, b0, b1, g, nx);
+    __syncthreads();
+    float* tmp = b0; b0 = b1; b1 = tmp;
+  }
+  const double* oldj = a.u_old + (long long)j * a.cstride;
+  double* cn = a.c_new + (long long)j * nx;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const float v = b0[pidx(i)];
+    cn[i] = (double)v;
+    b1[pidx(i)] = v - (a.zero_old ? 0.0f : (float)oldj[i]);
+  }
+  __syncthreads();
+  if (j >= a.N) return;
+  float* x0 = b1;
+  float* x1 = b0;
+  for (int s = 1; s <= m; ++s) {
+    slab_step<float, R, SPAN>(t, x0, x1, nullptr, nx);
+    __syncthreads();
+    float* tmp = x0; x0 = x1; x1 = tmp;
+  }
+  double* rr = a.r + (long long)(j + 1) * nx;
+  double ss = 0.0;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const double v = (double)x0[pidx(i)];
+    rr[i] = v;
+    ss = fma(v, v, ss);
+  }
+  if (a.partial) {
+    ss = block_sum(ss);
+    if (threadIdx.x == 0) a.partial[j] = ss;
+  }
+}
+
+// PREC 3: pass 1 (C-point update and residual rho) in float-float, pass 2 in
+// FP32.  A df64 slab occupies as many bytes as an FP64 slab.
+template <int R, int SPAN = 0>
+__device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const DevTaps& t, unsigned char* smraw) {
+  const int nx = a.nx, m = a.m, plen = padded_len(nx);
+  df64* b0 = reinterpret_cast<df64*>(smraw);
+  df64* b1 = b0 + plen;
+  const double* start = a.u_old + (long long)(j - 1) * a.cstride;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) b0[pidx(i)] = df_from(a.zero_old ? 0.0 : start[i]);
+  __syncthreads();
+  for (int s = 1; s <= m; ++s) {
+    const double* g = a.g ? a.g + ((long long)(j - 1) * m + s) * nx : nullptr;
+    slab_step<df64, R, SPAN>(t, b0, b1, g, nx);
+    __syncthreads();
+    df64* tmp = b0; b0 = b1; b1 = tmp;
+  }
+  const double* oldj = a.u_old + (long long)j * a.cstride;
+  double* cn = a.c_new + (long long)j * nx;
+  float* f0 = reinterpret_cast<float*>(b1);
+  float* f1 = f0 + plen;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const double v = df_to(b0[pidx(i)]);
+    cn[i] = v;
+    f0[pidx(i)] = (float)(v - (a.zero_old ? 0.0 : oldj[i]));
+  }
+  __syncthreads();
+  if (j >= a.N) return;
+  for (int s = 1; s <= m; ++s) {
+    slab_step<float, R, SPAN>(t, f0, f1, nullptr, nx);
+    __syncthreads();
+    float* tmp = f0; f0 = f1; f1 = tmp;
+  }
+  double* rr = a.r + (long long)(j + 1) * nx;
+  double ss = 0.0;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const double v = (double)f0[pidx(i)];
+    rr[i] = v;
+    ss = fma(v, v, ss);
+  }
+  if (a.partial) {
+    ss = block_sum(ss);
+    if (threadIdx.x == 0) a.partial[j] = ss;
+  }
+}
+
+template <int PREC, int R, int SPAN = 0>
 __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const DevTaps& t, unsigned char* smraw) {
+  if constexpr (PREC == 2) {
+    fcf_body_fp32<R, SPAN>(a, j, t, smraw);
+    return;
+  }
+  if constexpr (PREC == 3) {
+    fcf_body_df<R, SPAN>(a, j, t, smraw);
+    return;
+  }
   const int nx = a.nx, m = a.m, plen = padded_len(nx);
   double* b0 = reinterpret_cast<double*>(smraw);
   double* b1 = b0 + plen;
@@ -142,7 +335,7 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
   __syncthreads();
   for (int s = 1; s <= m; ++s) {
     const double* g = a.g ? a.g + ((long long)(j - 1) * m + s) * nx : nullptr;
-    slab_step<double, R>(t, b0, b1, g, nx);
+    slab_step<double, R, SPAN>(t, b0, b1, g, nx);
     __syncthreads();
     double* tmp = b0; b0 = b1; b1 = tmp;
   }
@@ -161,7 +354,7 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
     double* x0 = b1;
     double* x1 = b0;
     for (int s = 1; s <= m; ++s) {
-      slab_step<double, R>(t, x0, x1, nullptr, nx);
+      slab_step<double, R, SPAN>(t, x0, x1, nullptr, nx);
       __syncthreads();
       double* tmp = x0; x0 = x1; x1 = tmp;
     }
@@ -182,7 +375,7 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
     __syncthreads();
     if (!more) return;
     for (int s = 1; s <= m; ++s) {
-      slab_step<float, R>(t, f0, f1, nullptr, nx);
+      slab_step<float, R, SPAN>(t, f0, f1, nullptr, nx);
       __syncthreads();
       float* tmp = f0; f0 = f1; f1 = tmp;
     }
@@ -199,15 +392,15 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
   }
 }
 
-template <int PREC, int R>
+template <int PREC, int R, int SPAN = 0>
 __global__ void __launch_bounds__(R == 8 ? 512 : 1024) fcf_kernel(const FcfArgs a, const DevTaps t) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  fcf_body<PREC, R>(a, blockIdx.x + 1, t, smraw);
+  fcf_body<PREC, R, SPAN>(a, blockIdx.x + 1, t, smraw);
 }
 
 // Batched: one CTA per (solve, interval) item across all admitted solves; the
 // solve's stencil is copied into shared memory first.
-template <int R>
+template <int R, int SPAN = 0>
 __global__ void __launch_bounds__(R == 8 ? 512 : 1024) fcf_batched_kernel(const BatchSolve* __restrict__ S,
                                                             const BatchItem* __restrict__ items,
                                                             const DevTaps* __restrict__ taps) {
@@ -220,8 +413,9 @@ __global__ void __launch_bounds__(R == 8 ? 512 : 1024) fcf_batched_kernel(const 
   for (int k = threadIdx.x; k < (int)(sizeof(DevTaps) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
   __syncthreads();
   const FcfArgs a = s->fcf;
-  if (s->prec == 0) fcf_body<0, R>(a, it.j, st, smraw);
-  else fcf_body<1, R>(a, it.j, st, smraw);
+  if (s->prec == 0) fcf_body<0, R, SPAN>(a, it.j, st, smraw);
+  else if (s->prec == 3) fcf_body<3, R, SPAN>(a, it.j, st, smraw);
+  else fcf_body<1, R, SPAN>(a, it.j, st, smraw);
 }
 
 // ----------------------------------------------------------------------------
@@ -347,25 +541,25 @@ __global__ void __launch_bounds__(256) march_batched_kernel(const BatchSolve* __
 // ----------------------------------------------------------------------------
 // Correction + F-relaxation of a level (ideal interpolation).
 // ----------------------------------------------------------------------------
-template <int R>
+template <typename T, int R>
 __global__ void __launch_bounds__(R == 8 ? 512 : 1024) correct_kernel(const CorrectArgs a, const DevTaps t) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nx = a.nx, m = a.m, j = blockIdx.x + 1, plen = padded_len(nx);
-  double* b0 = reinterpret_cast<double*>(smraw);
-  double* b1 = b0 + plen;
+  T* b0 = reinterpret_cast<T*>(smraw);
+  T* b1 = b0 + plen;
   const long long p0 = (long long)(j - 1) * m;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     const double v = a.c_new[(long long)(j - 1) * nx + i] + (a.e ? a.e[(long long)(j - 1) * nx + i] : 0.0);
-    b0[pidx(i)] = v;
+    b0[pidx(i)] = (T)v;
     a.u[p0 * nx + i] = v;
   }
   __syncthreads();
   for (int s = 1; s < m; ++s) {
     const double* g = a.g ? a.g + (p0 + s) * nx : nullptr;
-    slab_step<double, R>(t, b0, b1, g, nx);
+    slab_step<T, R>(t, b0, b1, g, nx);
     __syncthreads();
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) a.u[(p0 + s) * nx + i] = b1[pidx(i)];
-    double* tmp = b0; b0 = b1; b1 = tmp;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) a.u[(p0 + s) * nx + i] = (double)b1[pidx(i)];
+    T* tmp = b0; b0 = b1; b1 = tmp;
   }
   if (j == a.N)
     for (int i = threadIdx.x; i < nx; i += blockDim.x)
@@ -422,7 +616,41 @@ __global__ void __launch_bounds__(R == 8 ? 512 : 1024) propagate_kernel(const do
   }
 }
 
+// ----------------------------------------------------------------------------
+// Stopping test inside a graph (one thread): relative residual, history, and
+// the WHILE (keep cycling) / IF (apply this cycle's coarse correction)
+// conditions.  Same decisions, in the same order, as the host loop.
+// ----------------------------------------------------------------------------
+__global__ void check_kernel(const double* __restrict__ norm2, CheckState* st, cudaGraphConditionalHandle hw,
+                             cudaGraphConditionalHandle hif, int cur) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double r0 = sqrt(st->r0sq);
+  const double rel = !isfinite(r0) ? r0 : (r0 > 0.0 ? sqrt(norm2[0]) / r0 : 0.0);
+  if (st->nhist < 128) st->hist[st->nhist++] = rel;
+  st->rel = rel;
+  int stop = 0;
+  if (!isfinite(rel) || rel > 1e6) { st->status = -5; stop = 1; }
+  else if (rel <= st->tol) { st->status = 0; stop = 1; }
+  else if (st->it >= st->max_iter) { st->status = -4; stop = 1; }
+  if (stop) {
+    st->done = 1;
+    st->result_cur = cur;
+    cudaGraphSetConditional(hif, 0);
+    cudaGraphSetConditional(hw, 0);
+  } else {
+    st->it += 1;
+    cudaGraphSetConditional(hif, 1);
+  }
+}
+
 // ------------------------------------------------------------------ launches
+
+cudaError_t launch_check(const double* norm2, CheckState* st, unsigned long long while_handle,
+                         unsigned long long if_handle, int cur, cudaStream_t s) {
+  check_kernel<<<1, 32, 0, s>>>(norm2, st, (cudaGraphConditionalHandle)while_handle,
+                                (cudaGraphConditionalHandle)if_handle, cur);
+  return cudaGetLastError();
+}
 
 static int g_tile = 8;  // register tile of the stencil (0 = one tap at a time)
 
@@ -431,9 +659,14 @@ int get_tile() { return g_tile; }
 
 static int tile_for(const DevTaps& t, int nx) { return (t.span > 0 && nx >= 64) ? g_tile : 0; }
 
+static int threads_for(int nx, int R, int hint);
+int default_threads(int nx, int R) { return threads_for(nx, R, 0); }
+int default_tile(const DevTaps& t, int nx) { return (t.span > 0 && nx >= 64) ? g_tile : 0; }
+
 static int threads_for(int nx, int R, int hint) {
   const int cap = 512;
   if (hint > 0) return hint < cap ? hint : cap;
+  if (R == kFixedTile) R = 8;
   const int per = R > 0 ? R : 4;
   int th = (nx + per - 1) / per;
   th = ((th + 31) / 32) * 32;
@@ -446,46 +679,91 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaSuccess;
 }
 
-template <int PREC, int R>
+template <int PREC, int R, int SPAN = 0>
 static cudaError_t launch_fcf_t(const FcfArgs& a, const DevTaps& t, int threads, cudaStream_t s) {
-  const size_t smem = 2 * (size_t)padded_len(a.nx) * sizeof(double);
-  cudaError_t e = set_smem(fcf_kernel<PREC, R>, smem);
+  const size_t smem = 2 * (size_t)padded_len(a.nx) * (PREC == 2 ? sizeof(float) : sizeof(double));
+  cudaError_t e = set_smem(fcf_kernel<PREC, R, SPAN>, smem);
   if (e != cudaSuccess) return e;
-  fcf_kernel<PREC, R><<<a.N, threads_for(a.nx, R, threads), smem, s>>>(a, t);
+  fcf_kernel<PREC, R, SPAN><<<a.N, threads_for(a.nx, R, threads), smem, s>>>(a, t);
   return cudaGetLastError();
 }
 
-cudaError_t launch_fcf(const FcfArgs& a, const DevTaps& t, int precision, int threads, cudaStream_t s) {
+// Fixed-span instantiations: the collapsed ERK1..ERK5 stencils (spans
+// s(w-1)+1 = 2, 5, 10, 17, 31).
+static bool fixed_span_ok(int span) {
+  return span == 2 || span == 5 || span == 10 || span == 17 || span == 31;
+}
+
+template <int PREC>
+static cudaError_t launch_fcf_fixed(const FcfArgs& a, const DevTaps& t, int threads, cudaStream_t s) {
+  switch (t.span) {
+    case 2: return launch_fcf_t<PREC, 8, 2>(a, t, threads, s);
+    case 5: return launch_fcf_t<PREC, 8, 5>(a, t, threads, s);
+    case 10: return launch_fcf_t<PREC, 8, 10>(a, t, threads, s);
+    case 17: return launch_fcf_t<PREC, 4, 17>(a, t, threads, s);
+    case 31: return launch_fcf_t<PREC, 4, 31>(a, t, threads, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_fcf(const FcfArgs& a, const DevTaps& t, int precision, int threads, cudaStream_t s, int tile) {
   if (a.N < 1) return cudaSuccess;
-  const int R = tile_for(t, a.nx);
+  if (tile == kFixedTile) {
+    if (!fixed_span_ok(t.span) || a.nx < 64) return cudaErrorInvalidValue;
+    switch (precision) {
+      case 0: return launch_fcf_fixed<0>(a, t, threads, s);
+      case 1: return launch_fcf_fixed<1>(a, t, threads, s);
+      case 2: return launch_fcf_fixed<2>(a, t, threads, s);
+      default: return launch_fcf_fixed<3>(a, t, threads, s);
+    }
+  }
+  const int R = (tile >= 0 && (tile == 0 || (t.span > 0 && a.nx >= 64))) ? tile : tile_for(t, a.nx);
   if (precision == 0) {
     if (R == 8) return launch_fcf_t<0, 8>(a, t, threads, s);
     if (R == 4) return launch_fcf_t<0, 4>(a, t, threads, s);
     return launch_fcf_t<0, 0>(a, t, threads, s);
+  }
+  if (precision == 2) {
+    if (R == 8) return launch_fcf_t<2, 8>(a, t, threads, s);
+    if (R == 4) return launch_fcf_t<2, 4>(a, t, threads, s);
+    return launch_fcf_t<2, 0>(a, t, threads, s);
+  }
+  if (precision == 3) {
+    if (R == 8) return launch_fcf_t<3, 8>(a, t, threads, s);
+    if (R == 4) return launch_fcf_t<3, 4>(a, t, threads, s);
+    return launch_fcf_t<3, 0>(a, t, threads, s);
   }
   if (R == 8) return launch_fcf_t<1, 8>(a, t, threads, s);
   if (R == 4) return launch_fcf_t<1, 4>(a, t, threads, s);
   return launch_fcf_t<1, 0>(a, t, threads, s);
 }
 
-template <int R>
+template <int R, int SPAN = 0>
 static cudaError_t launch_fcf_batched_t(const BatchSolve* S, const BatchItem* items, int nitems, const DevTaps* taps,
                                         int max_nx, int threads, cudaStream_t s) {
   const size_t smem = 2 * (size_t)padded_len(max_nx) * sizeof(double);
-  cudaError_t e = set_smem(fcf_batched_kernel<R>, smem);
+  cudaError_t e = set_smem(fcf_batched_kernel<R, SPAN>, smem);
   if (e != cudaSuccess) return e;
-  fcf_batched_kernel<R><<<nitems, threads, smem, s>>>(S, items, taps);
+  fcf_batched_kernel<R, SPAN><<<nitems, threads, smem, s>>>(S, items, taps);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fcf_batched(const BatchSolve* S, const BatchItem* items, int nitems, const DevTaps* taps,
-                               int max_nx, int threads, cudaStream_t s) {
+                               int max_nx, int threads, int tile, int span, cudaStream_t s) {
   if (nitems < 1) return cudaSuccess;
-  // threads < 0 selects the one-tap-at-a-time path (batches whose stencils
-  // have no dense form or whose nx < 64)
-  if (threads > 0 && g_tile == 8) return launch_fcf_batched_t<8>(S, items, nitems, taps, max_nx, threads, s);
-  if (threads > 0 && g_tile == 4) return launch_fcf_batched_t<4>(S, items, nitems, taps, max_nx, threads, s);
-  return launch_fcf_batched_t<0>(S, items, nitems, taps, max_nx, threads > 0 ? threads : -threads, s);
+  if (tile == kFixedTile) {
+    switch (span) {
+      case 2: return launch_fcf_batched_t<8, 2>(S, items, nitems, taps, max_nx, threads, s);
+      case 5: return launch_fcf_batched_t<8, 5>(S, items, nitems, taps, max_nx, threads, s);
+      case 10: return launch_fcf_batched_t<8, 10>(S, items, nitems, taps, max_nx, threads, s);
+      case 17: return launch_fcf_batched_t<4, 17>(S, items, nitems, taps, max_nx, threads, s);
+      case 31: return launch_fcf_batched_t<4, 31>(S, items, nitems, taps, max_nx, threads, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (tile == 8) return launch_fcf_batched_t<8>(S, items, nitems, taps, max_nx, threads, s);
+  if (tile == 4) return launch_fcf_batched_t<4>(S, items, nitems, taps, max_nx, threads, s);
+  return launch_fcf_batched_t<0>(S, items, nitems, taps, max_nx, threads, s);
 }
 
 template <typename K>
@@ -567,21 +845,26 @@ cudaError_t launch_march_batched(const BatchSolve* S, const int* ids, int count,
 
 int march_max_cluster() { return 16; }
 
-template <int R>
+template <typename T, int R>
 static cudaError_t launch_correct_t(const CorrectArgs& a, const DevTaps& t, int threads, cudaStream_t s) {
-  const size_t smem = 2 * (size_t)padded_len(a.nx) * sizeof(double);
-  cudaError_t e = set_smem(correct_kernel<R>, smem);
+  const size_t smem = 2 * (size_t)padded_len(a.nx) * sizeof(T);
+  cudaError_t e = set_smem(correct_kernel<T, R>, smem);
   if (e != cudaSuccess) return e;
-  correct_kernel<R><<<a.N, threads_for(a.nx, R, threads), smem, s>>>(a, t);
+  correct_kernel<T, R><<<a.N, threads_for(a.nx, R, threads), smem, s>>>(a, t);
   return cudaGetLastError();
 }
 
-cudaError_t launch_correct(const CorrectArgs& a, const DevTaps& t, int threads, cudaStream_t s) {
+cudaError_t launch_correct(const CorrectArgs& a, const DevTaps& t, int threads, cudaStream_t s, int fp32) {
   if (a.N < 1) return cudaSuccess;
   const int R = tile_for(t, a.nx);
-  if (R == 8) return launch_correct_t<8>(a, t, threads, s);
-  if (R == 4) return launch_correct_t<4>(a, t, threads, s);
-  return launch_correct_t<0>(a, t, threads, s);
+  if (fp32) {
+    if (R == 8) return launch_correct_t<float, 8>(a, t, threads, s);
+    if (R == 4) return launch_correct_t<float, 4>(a, t, threads, s);
+    return launch_correct_t<float, 0>(a, t, threads, s);
+  }
+  if (R == 8) return launch_correct_t<double, 8>(a, t, threads, s);
+  if (R == 4) return launch_correct_t<double, 4>(a, t, threads, s);
+  return launch_correct_t<double, 0>(a, t, threads, s);
 }
 
 cudaError_t launch_norm(const double* partial, int n, double* out, cudaStream_t s) {

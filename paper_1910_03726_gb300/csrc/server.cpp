@@ -28,6 +28,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -213,7 +214,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     b.fcf.m = h->m;
     b.fcf.N = h->Nl[1];
     b.fcf.zero_old = 0;
-    b.prec = h->opts.precision == MGRIT_PREC_FP64 ? 0 : 1;
+    b.prec = fine_prec(h);
     b.taps = 2 * k;
     b.psi = 2 * k + 1;
     b.cluster = h->march_cluster;
@@ -224,9 +225,9 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     return fail(MGRIT_ERR_OOM, "server batch descriptors");
   cudaMemcpyAsync(S->dS.p, hs.data(), n * sizeof(BatchSolve), cudaMemcpyHostToDevice, S->stream);
   cudaMemcpyAsync(S->dTaps.p, taps.data(), 2 * n * sizeof(DevTaps), cudaMemcpyHostToDevice, S->stream);
-  // ---- batched FCF, one launch per (nx, register-tile eligibility)
-  std::map<std::pair<int, int>, std::vector<int>> groups;
-  const int tile = get_tile();
+  // ---- batched FCF, one launch per (nx, launch shape): each solve keeps the
+  // shape it was tuned to, so its arithmetic is the single-solve path's
+  std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
   for (int k = 0; k < n; ++k) {
     mgrit_handle* h = act[k]->h;
     if (h->sdirk) {  // SDIRK fine levels relax through their own launch
@@ -235,8 +236,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
       h->kcount[MGRIT_K_FCF]++;
       continue;
     }
-    const int tiled = (h->dphi.span > 0 && h->nx >= 64 && tile > 0) ? 1 : 0;
-    groups[{h->nx, tiled}].push_back(k);
+    groups[{h->nx, h->fine_tile, h->fine_threads, h->dphi.span}].push_back(k);
   }
   std::vector<BatchItem> items;
   std::vector<std::pair<size_t, size_t>> ranges;
@@ -250,13 +250,11 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
   cudaMemcpyAsync(S->dItems.p, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, S->stream);
   size_t gi = 0;
   for (auto& g : groups) {
-    const int nx = g.first.first, tiled = g.first.second;
-    const int per = tiled ? tile : 4;
-    int th = ((nx + per - 1) / per + 31) / 32 * 32;
-    th = std::max(32, std::min(512, th));
+    const int nx = std::get<0>(g.first), tile = std::get<1>(g.first), th = std::get<2>(g.first);
+    const int span = std::get<3>(g.first);
     const auto rg = ranges[gi++];
     cudaError_t e = launch_fcf_batched(S->dS.p, S->dItems.p + rg.first, (int)(rg.second - rg.first), S->dTaps.p, nx,
-                                       tiled ? th : -th, S->stream);
+                                       th, tile, span, S->stream);
     if (e != cudaSuccess) return launch_ok(e, "fcf_batched");
     for (int k : g.second) act[k]->h->kcount[MGRIT_K_FCF]++;
   }

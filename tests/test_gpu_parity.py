@@ -182,3 +182,45 @@ def test_nonfinite_initial_condition_reports_divergence(capi):
         assert ei.value.status == -5
     finally:
         capi.mgrit_destroy(h)
+
+
+@pytest.mark.parametrize("precision,L", [(1, 3), (2, 2), (2, 4)])
+def test_mixed_modes_reach_the_fp64_fixed_point(capi, precision, L):
+    """MIXED (FP32 coarse levels) and MIXED_DF (float-float C-point pass):
+    the FP64 stopping test is met and the solution agrees with FP64
+    sequential stepping to the accuracy the tolerance implies."""
+    fam, p, nx, nt, m = "ERK", 3, 256, 4096, 8 if L < 4 else 4
+    c = schemes.cfl_number(fam, p)
+    u0 = workloads.fourier_field(nx)
+    ref = stepping.sequential(stepping.FineStep(fam, p, c, nx), u0, nt)
+    it64 = gpu_run(capi, fam, p, c, nx, nt, m, L, "auto", u0, precision=0)[0].iterations
+    res, out, _ = gpu_run(capi, fam, p, c, nx, nt, m, L, "auto", u0, precision=precision)
+    assert res.converged == 1 and res.rel_residual <= 1e-10
+    assert abs(res.iterations - it64) <= 1
+    assert rel(out, ref[::m]) <= 1e-9
+
+
+@pytest.mark.parametrize("L,precision", [(2, 0), (3, 0), (4, 1), (2, 2)])
+def test_graph_solve_equals_host_loop(capi, L, precision):
+    """The whole solve as one CUDA graph (on-device stopping test driving the
+    WHILE/IF nodes) gives the host-driven loop's iterations and C-points."""
+    fam, p, nx, nt, m = "ERK", 3, 128, 2048, 4
+    c = schemes.cfl_number(fam, p)
+    u0 = workloads.fourier_field(nx)
+    outs = []
+    for flags in (capi.FLAG_HOST_LOOP, 0):
+        opts = capi.mgrit_opts_default(m=m, levels=L, precision=precision, flags=flags)
+        h = capi.mgrit_setup(capi.problem(nx, nt, fam, p, p, c), opts)
+        try:
+            out = np.zeros((nt // m + 1, nx))
+            res, _ = capi.mgrit_solve(h, u0, out)
+            res2, _ = capi.mgrit_solve(h, u0, out)  # the graph is reused
+        finally:
+            capi.mgrit_destroy(h)
+        assert res.iterations == res2.iterations
+        outs.append((res, out))
+    (r0, o0), (r1, o1) = outs
+    assert r1.graph == 1 and r0.graph == 0
+    assert r1.iterations == r0.iterations
+    np.testing.assert_allclose(r1.history[: r1.n_history], r0.history[: r0.n_history], rtol=1e-14)
+    assert rel(o1, o0) <= 1e-15
