@@ -152,6 +152,136 @@ def fcf_traffic_from_profile():
     return float(m2.group(1))
 
 
+CMAX_TABLE1 = {1: 1.0, 2: 0.5, 3: 1.62589, 4: 1.04449, 5: 1.96583}   # Table 1 CFL limits (ERK_p+U_p)
+
+
+def mix_request(capi, s, tol, precision):
+    """Problem, options and u0 of one solve of the uneven batch / serving mix:
+    ERK at 85% of Table 1's limit with the auto-width Psi, SDIRK at c = 4 with
+    the threshold Psi; two-level, final time level returned."""
+    fam, p = s["family"], s["p"]
+    c = 4.0 if fam == "SDIRK" else 0.85 * CMAX_TABLE1[p]
+    prob = capi.problem(s["nx"], s["nt"], fam, p, p, c)
+    opts = capi.mgrit_opts_default(m=s["m"], levels=2, precision=precision, tol=tol, output=capi.OUT_FINAL,
+                                   max_iter=80, psi_rule=capi.PSI_THRESHOLD if fam == "SDIRK" else capi.PSI_AUTO)
+    return prob, opts, workloads.fourier_field(s["nx"], seed=s["field_seed"])
+
+
+def run_server(capi, reqs, times, budget):
+    """Submit reqs[i] at times[i] seconds (None: all at once), wait for all.
+    Returns wall seconds from the first submission to the last completion,
+    per-request latencies (seconds, measured inside the library from submit to
+    completion) and results."""
+    srv = capi.mgrit_server_create(budget)
+    tickets = []
+    try:
+        t0 = time.perf_counter()
+        for i, (prob, opts, u0) in enumerate(reqs):
+            if times is not None:
+                wait = t0 + times[i] - time.perf_counter()
+                if wait > 0:
+                    time.sleep(wait)
+            tickets.append(capi.mgrit_submit(srv, prob, opts, u0))
+        pending = dict(enumerate(tickets))
+        results = [None] * len(tickets)
+        while pending:
+            for i in list(pending):
+                st, r = capi.mgrit_poll(srv, pending[i])
+                if st != capi.MGRIT_PENDING:
+                    results[i] = (st, r)
+                    del pending[i]
+            if pending:
+                time.sleep(0.001)
+        wall = time.perf_counter() - t0
+    finally:
+        capi.mgrit_server_destroy(srv)
+    lat = [r.solve_s for st, r in results]
+    return wall, lat, results
+
+
+def batch_variant(capi, count, stream):
+    """Uneven batch of independent solves through the continuous-batching
+    server (all submitted at once; FP32 F-relaxation, FP64 residual), against
+    a sample of the same solves run alone in plain FP64 and by sequential
+    stepping on the same GPU."""
+    specs = workloads.batch_specs(count)
+    reqs = [mix_request(capi, s, TOL, capi.PREC_MIXED) for s in specs]
+    dof = sum(s["nx"] * s["nt"] for s in specs)
+    wall, lat, results = run_server(capi, reqs, None, 150e9)
+    ok = sum(1 for st, r in results if st == 0 and r.converged)
+    its = [r.iterations for st, r in results]
+    sample = specs[:32]
+    t_fp64 = t_seq = 0.0
+    dof_s = 0
+    import torch
+    for s in sample:
+        prob, opts, u0 = mix_request(capi, s, TOL, capi.PREC_FP64)
+        h = capi.mgrit_setup(prob, opts, stream=stream)
+        try:
+            capi.mgrit_solve(h, u0, None)
+            r, _ = capi.mgrit_solve(h, u0, None)
+            t_fp64 += r.solve_s
+            fin = torch.empty(s["nx"], dtype=torch.float64, device="cuda")
+            t_seq += capi.mgrit_sequential(h, u0, fin)
+        finally:
+            capi.mgrit_destroy(h)
+        dof_s += s["nx"] * s["nt"]
+    return {"solves": count, "converged": ok, "dof": dof, "wall_s": wall, "dof_per_s": dof / wall,
+            "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99))},
+            "iterations_mean": float(np.mean(its)),
+            "plain_fp64_alone_dof_per_s": dof_s / t_fp64, "gpu_sequential_dof_per_s": dof_s / t_seq,
+            "baseline_sample": f"first {len(sample)} solves of the batch, each alone (solve time only, setup "
+                               f"excluded)", "budget_bytes": 150e9,
+            "mix": "nx 256..4096, nt 1024..16384, p 1..5, ERK or SDIRK, m 4/8/16 (seed 4), two-level, tol 1e-10"}
+
+
+def serving_variant(capi, rates, count):
+    """Poisson arrivals of the batch mix with a 1e-8 or 1e-10 tolerance drawn
+    per request; latency from submission to completion."""
+    out = {}
+    for rate in rates:
+        times, tols = workloads.arrivals(rate, count)
+        specs = workloads.batch_specs(count, seed=workloads.SEED_ARRIVALS * 7 + int(rate))
+        reqs = [mix_request(capi, s, float(t), capi.PREC_MIXED) for s, t in zip(specs, tols)]
+        dof = sum(s["nx"] * s["nt"] for s in specs)
+        wall, lat, results = run_server(capi, reqs, times, 150e9)
+        ok = sum(1 for st, r in results if st == 0 and r.converged)
+        out[f"{rate:g}/s"] = {"requests": count, "converged": ok, "wall_s": wall, "dof_per_s": dof / wall,
+                              "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
+                                             "p99": 1e3 * float(np.percentile(lat, 99))}}
+    return out
+
+
+def sdirk_variant(capi, stream, K):
+    """SDIRK3+U5, nx = 8192, nt = 8192, c = 4, two-level m = 16, threshold
+    Psi, wave-packet u0 (seed 3): MIXED, FP64 and sequential stepping."""
+    import torch
+    nx = nt = 8192
+    u0 = torch.tensor(workloads.wave_packet(nx), device="cuda")
+    prob = capi.problem(nx, nt, "SDIRK", 3, 5, 4.0)
+    res = {}
+    for name, prec in (("mixed", capi.PREC_MIXED), ("fp64", capi.PREC_FP64)):
+        o = capi.mgrit_opts_default(m=16, levels=2, precision=prec, tol=TOL, output=capi.OUT_FINAL,
+                                    psi_rule=capi.PSI_THRESHOLD, max_iter=50)
+        h = capi.mgrit_setup(prob, o, stream=stream)
+        try:
+            capi.mgrit_solve(h, u0, None)
+            ts = []
+            for _ in range(K):
+                r, _ = capi.mgrit_solve(h, u0, None)
+                ts.append(r.solve_s)
+            res[name] = {"dof_per_s": nx * nt / statistics.median(ts), "ms": 1e3 * statistics.median(ts),
+                         "iterations": r.iterations, "rel_residual": r.rel_residual}
+            if name == "fp64":
+                fin = torch.empty(nx, dtype=torch.float64, device="cuda")
+                s = capi.mgrit_sequential(h, u0, fin)
+                res["gpu_sequential_fp64"] = {"dof_per_s": nx * nt / s, "ms": 1e3 * s}
+        finally:
+            capi.mgrit_destroy(h)
+    res["workload"] = "SDIRK3+U5 8192x8192 c=4, two-level m=16, threshold Psi, wave packet u0 (seed 3), tol 1e-10"
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -162,6 +292,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "mixed_df"],
                     help="arithmetic of the headline solve")
+    ap.add_argument("--batch", type=int, default=4096, help="solves in the uneven batch (0: skip)")
+    ap.add_argument("--serve", type=int, default=400, help="requests per arrival rate (0: skip)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = dist_env()
@@ -296,6 +428,11 @@ def main():
         err = float(torch.linalg.norm(out - fin) / torch.linalg.norm(fin))
         extra["rel_l2_vs_fp64_sequential"] = err
         capi.mgrit_destroy(hs)
+        extra["sdirk3_u5_8192"] = sdirk_variant(capi, sp, 3)
+        if args.batch > 0:
+            extra["batch_uneven"] = batch_variant(capi, args.batch, sp)
+        if args.serve > 0:
+            extra["serving_poisson"] = serving_variant(capi, (100, 1000, 3000, 10000), args.serve)
 
     line = None
     if rank == 0:

@@ -101,35 +101,46 @@ cudaError_t launch_check(const double* norm2, CheckState* st, unsigned long long
                          unsigned long long if_handle, int cur, cudaStream_t s);
 
 // ------------------------------------------------------------- SDIRK steps
-// One SDIRK step (stage form, Appendix A tableaux):
-//   K_i = M^{-1} dtL (u + sum_{j<i} a_ij K_j),  M = I - gamma dtL,
-//   u_new = u + sum_i b_i K_i  (stiffly accurate: b = last row of A).
-// M = E^{-ql} p_d prod_r (E - z_r), E the forward shift: each linear factor is
-// a periodic first-order recurrence solved by a chunked parallel scan in its
-// stable direction (forward if |z_r| < 1, backward otherwise) closed by an
-// exact rank-one periodic wrap.
+// One SDIRK step (stage form, Appendix A tableaux, all stiffly accurate):
+//   (I - gamma dtL) K_i = dtL A_i,  A_i = u + sum_{j<i} a_ij K_j,
+//   u_new = A_s + gamma K_s.
+// With M = I - gamma dtL the stage is K_i = (M^{-1} A_i - A_i) / gamma, so a
+// stage is one periodic banded solve and no separate application of dtL.
+// M = p_d E^{lo} prod_r (E - z_r) (E the forward shift) splits into
+//   forward part  prod_{|z|<1} (I - z S),   S = E^{-1}: x_i = sum_q af_q x_{i-q} + y_i
+//   backward part prod_{|z|>1} (I - E/z):             x_i = sum_q ab_q x_{i+q} + y_i
+// (real coefficients: conjugate roots stay on one side), a shift E^{ql} and a
+// scale.  Each periodic recurrence runs as a chunked parallel scan over the
+// slab (C points per thread, warp-shuffle and cross-warp scans of the K-vector
+// states with the powers of the companion matrix, exact periodic closure
+// (I - T^nx)^{-1}); every table is computed on the host in FP64.
 constexpr int kMaxStages = 5;
-constexpr int kMaxFactors = 5;
+constexpr int kMaxRec = 5;       // order of one directional recurrence
+constexpr int kSdirkCMax = 16;   // points per thread
 struct SdirkPlan {
-  int s;                        // stages
-  int nL;                       // taps of dt L
-  int ql;                       // input shift of the solve
-  int nf;                       // linear factors of M
-  int offL[6];
-  double cL[6];
-  float cL32[6];
+  int s;                 // stages
+  int kf, kb;            // orders of the forward / backward recurrences
+  int ql;                // input shift of the solve: x_i = y_{i+ql}
+  int C, threads;        // points per thread and CTA size, nx = threads * C
+  int nx;
+  int tab_len;           // elements of one precision's recurrence tables
   double a[kMaxStages][kMaxStages];
   float a32[kMaxStages][kMaxStages];
-  double gamma;
-  float gamma32;
-  int dir[kMaxFactors];         // +1: forward recurrence x_i = m x_{i-1} + b_i; -1: backward
-  double mre[kMaxFactors], mim[kMaxFactors];   // recurrence multiplier m (|m| < 1)
-  double bscale_re[kMaxFactors], bscale_im[kMaxFactors];  // input scale of the factor
-  double inv_pd;                // 1 / leading coefficient
+  double gamma, inv_gamma, scale;   // scale = 1 / (p_d prod_{|z|>1} (-z))
+  float gamma32, inv_gamma32, scale32;
+  double af[kMaxRec], ab[kMaxRec];  // recurrence coefficients (host copy)
+  const double* tab64;   // device: tables, FP64
+  const float* tab32;    // device: tables, FP32
 };
+// Elements of the tables of one direction of order K with C points per
+// thread: a[K], (A^k)_{k=0..32}, ((A^32)^k)_{k=0..16} (A = T^C, T the
+// companion matrix, K x K row-major), G[C][K] (row 0 of T^{c+1}) and
+// Q = (I - T^nx)^{-1}.
+__host__ __device__ constexpr int sdirk_rec_len(int K, int C) { return K == 0 ? 0 : K + 51 * K * K + C * K; }
 int sdirk_slots(const SdirkPlan& p);                      // shared slabs a step needs
-size_t sdirk_smem(const SdirkPlan& p, int nx, int prec);  // bytes of an FCF CTA
+size_t sdirk_smem(const SdirkPlan& p);                    // bytes of shared memory of a CTA
 int sdirk_threads(int nx);                                // CTA size (0: nx unsupported)
+bool sdirk_orders_supported(int kf, int kb);
 cudaError_t launch_fcf_sdirk(const FcfArgs& a, const SdirkPlan& p, int precision, cudaStream_t s);
 cudaError_t launch_propagate_sdirk(const double* in, double* out, int count, int nx, int k, const SdirkPlan& p,
                                    double* partial, cudaStream_t s);
@@ -146,12 +157,17 @@ struct BatchSolve {
   int taps;            // index of the fine stencil in the taps array
   int psi;             // index of the coarse stencil (two-level march)
   int cluster;         // CTAs per march cluster
+  const SdirkPlan* sd; // device copy of the SDIRK plan (SDIRK fine levels)
 };
 struct BatchItem {
   int solve, j;        // solve index, interval j (1..N)
 };
 cudaError_t launch_fcf_batched(const BatchSolve* S, const BatchItem* items, int nitems, const DevTaps* taps,
                                int max_nx, int threads, int tile, int span, cudaStream_t s);
+// SDIRK fine levels of several solves with the same nx, recurrence orders and
+// precision; smem_bytes = the largest sdirk_smem of the group.
+cudaError_t launch_fcf_sdirk_batched(const BatchSolve* S, const BatchItem* items, int nitems, const SdirkPlan& any,
+                                     size_t smem_bytes, int precision, cudaStream_t s);
 int default_threads(int nx, int tile);        // CTA size the launches pick for nx
 int default_tile(const DevTaps& t, int nx);   // register tile the launches pick
 cudaError_t launch_norm_batched(const BatchSolve* S, const int* ids, int count, double* out, cudaStream_t s);

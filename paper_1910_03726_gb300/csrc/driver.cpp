@@ -282,46 +282,164 @@ int pick_cluster(int nx, const Taps& t) {
   return 1;
 }
 
-// Host reference of the factored solve (used to check the plan): applies
-// E^{shift}, every factor's periodic recurrence, and the scale, in FP64.
+namespace {
+using Mat = std::vector<double>;  // K x K row-major
+
+Mat mat_mul(const Mat& A, const Mat& B, int K) {
+  Mat C(K * K, 0.0);
+  for (int i = 0; i < K; ++i)
+    for (int k = 0; k < K; ++k)
+      for (int j = 0; j < K; ++j) C[i * K + j] += A[i * K + k] * B[k * K + j];
+  return C;
+}
+Mat mat_eye(int K) {
+  Mat I(K * K, 0.0);
+  for (int i = 0; i < K; ++i) I[i * K + i] = 1.0;
+  return I;
+}
+Mat mat_pow(Mat A, long long n, int K) {
+  Mat R = mat_eye(K);
+  while (n > 0) {
+    if (n & 1) R = mat_mul(R, A, K);
+    A = mat_mul(A, A, K);
+    n >>= 1;
+  }
+  return R;
+}
+// Inverse by Gauss-Jordan elimination with partial pivoting (K <= 5).
+bool mat_inv(Mat A, int K, Mat* out) {
+  Mat I = mat_eye(K);
+  for (int c = 0; c < K; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < K; ++r)
+      if (std::fabs(A[r * K + c]) > std::fabs(A[piv * K + c])) piv = r;
+    if (std::fabs(A[piv * K + c]) < 1e-300) return false;
+    for (int j = 0; j < K; ++j) {
+      std::swap(A[c * K + j], A[piv * K + j]);
+      std::swap(I[c * K + j], I[piv * K + j]);
+    }
+    const double d = 1.0 / A[c * K + c];
+    for (int j = 0; j < K; ++j) {
+      A[c * K + j] *= d;
+      I[c * K + j] *= d;
+    }
+    for (int r = 0; r < K; ++r)
+      if (r != c) {
+        const double f = A[r * K + c];
+        for (int j = 0; j < K; ++j) {
+          A[r * K + j] -= f * A[c * K + j];
+          I[r * K + j] -= f * I[c * K + j];
+        }
+      }
+  }
+  *out = I;
+  return true;
+}
+// Companion matrix of x_i = sum_q a_q x_{i-q} + y_i on the state
+// (x_i, x_{i-1}, ..., x_{i-K+1}).
+Mat companion(const double* a, int K) {
+  Mat T(K * K, 0.0);
+  for (int q = 0; q < K; ++q) T[q] = a[q];
+  for (int q = 1; q < K; ++q) T[q * K + q - 1] = 1.0;
+  return T;
+}
+// Tables of one direction (layout of sdirk_rec_len): a, A^k (k <= 32),
+// (A^32)^k (k <= 16), G[c] = row 0 of T^{c+1}, Q = (I - T^nx)^{-1}.
+bool rec_tables(const double* a, int K, int C, int nx, std::vector<double>* out) {
+  if (K == 0) return true;
+  const Mat T = companion(a, K);
+  const Mat A = mat_pow(T, C, K);
+  const Mat A32 = mat_pow(A, 32, K);
+  for (int q = 0; q < K; ++q) out->push_back(a[q]);
+  Mat P = mat_eye(K);
+  for (int k = 0; k <= 32; ++k) {
+    out->insert(out->end(), P.begin(), P.end());
+    P = mat_mul(P, A, K);
+  }
+  P = mat_eye(K);
+  for (int k = 0; k <= 16; ++k) {
+    out->insert(out->end(), P.begin(), P.end());
+    P = mat_mul(P, A32, K);
+  }
+  P = T;
+  for (int c = 0; c < C; ++c) {
+    for (int q = 0; q < K; ++q) out->push_back(P[q]);
+    P = mat_mul(P, T, K);
+  }
+  Mat M = mat_pow(T, nx, K), Q;
+  for (int i = 0; i < K * K; ++i) M[i] = (i % (K + 1) == 0 ? 1.0 : 0.0) - M[i];
+  if (!mat_inv(M, K, &Q)) return false;
+  out->insert(out->end(), Q.begin(), Q.end());
+  return true;
+}
+// One periodic recurrence over y (forward, or backward over reversed order),
+// sequentially: a zero-state pass, the closure s_{-1} = (I - T^n)^{-1} s_{n-1},
+// and the pass from s_{-1}.
+void host_rec(const double* a, int K, bool backward, std::vector<double>& y) {
+  if (K == 0) return;
+  const int n = (int)y.size();
+  auto at = [&](int k) -> double& { return y[backward ? n - 1 - k : k]; };
+  std::vector<double> w(n);
+  std::vector<double> st(K, 0.0);
+  for (int k = 0; k < n; ++k) {
+    double v = at(k);
+    for (int q = 0; q < K; ++q) v += a[q] * st[q];
+    for (int q = K - 1; q > 0; --q) st[q] = st[q - 1];
+    st[0] = v;
+  }
+  Mat M = mat_pow(companion(a, K), n, K), Q;
+  for (int i = 0; i < K * K; ++i) M[i] = (i % (K + 1) == 0 ? 1.0 : 0.0) - M[i];
+  if (!mat_inv(M, K, &Q)) return;
+  std::vector<double> s0(K, 0.0);
+  for (int r = 0; r < K; ++r)
+    for (int q = 0; q < K; ++q) s0[r] += Q[r * K + q] * st[q];
+  st = s0;
+  for (int k = 0; k < n; ++k) {
+    double v = at(k);
+    for (int q = 0; q < K; ++q) v += a[q] * st[q];
+    for (int q = K - 1; q > 0; --q) st[q] = st[q - 1];
+    st[0] = v;
+    w[k] = v;
+  }
+  for (int k = 0; k < n; ++k) at(k) = w[k];
+}
+}  // namespace
+
+// Host reference of the stage solve M^{-1} y (checks the plan).
 static void host_sdirk_solve(const SdirkPlan& P, std::vector<double>& y) {
   const int n = (int)y.size();
   std::vector<double> x(n);
   for (int i = 0; i < n; ++i) x[i] = y[((i + P.ql) % n + n) % n];
-  for (int f = 0; f < P.nf; ++f) {
-    const std::complex<double> m(P.mre[f], P.mim[f]);
-    std::vector<std::complex<double>> z(n);
-    for (int i = 0; i < n; ++i) z[i] = x[i];
-    const bool back = P.dir[f] < 0;
-    // zero-carry pass, wrap value, carried pass
-    std::complex<double> c = 0.0;
-    std::vector<std::complex<double>> w(n);
-    for (int k = 0; k < n; ++k) {
-      const int i = back ? n - 1 - k : k;
-      c = m * c + z[i];
-      w[i] = c;
-    }
-    std::complex<double> mn = std::pow(m, n);
-    std::complex<double> carry = c / (1.0 - mn);
-    for (int k = 0; k < n; ++k) {
-      const int i = back ? n - 1 - k : k;
-      carry = m * carry + z[i];
-      w[i] = carry;
-    }
-    if (P.mim[f] == 0.0)
-      for (int i = 0; i < n; ++i) x[i] = w[i].real();
-    else
-      for (int i = 0; i < n; ++i) x[i] = (m * w[i]).imag() / P.mim[f];
-  }
-  for (int i = 0; i < n; ++i) y[i] = x[i] * P.inv_pd;
+  host_rec(P.af, P.kf, false, x);
+  host_rec(P.ab, P.kb, true, x);
+  for (int i = 0; i < n; ++i) y[i] = x[i] * P.scale;
 }
 
-mgrit_status make_sdirk_plan(const mgrit_problem* prob, SdirkPlan* out) {
+// Expand prod_r (1 - w_r t) = 1 - sum_q a_q t^q; returns a_1..a_K.
+static std::vector<double> rec_coeffs(const std::vector<std::complex<double>>& w) {
+  std::vector<std::complex<double>> c(1, 1.0);
+  for (auto z : w) {
+    std::vector<std::complex<double>> n(c.size() + 1, 0.0);
+    for (size_t k = 0; k < c.size(); ++k) {
+      n[k] += c[k];
+      n[k + 1] -= z * c[k];
+    }
+    c = n;
+  }
+  std::vector<double> a;
+  for (size_t q = 1; q < c.size(); ++q) a.push_back(-c[q].real());
+  return a;
+}
+
+mgrit_status make_sdirk_plan(const mgrit_problem* prob, SdirkPlan* out, std::vector<double>* tables) {
   SdirkPlan P;
   std::memset(&P, 0, sizeof(P));
   Tableau tb = sdirk_tableau(prob->rk_order);
   Taps L = dtL_taps(prob->upwind_order, prob->cfl);
   if (tb.s < 1 || tb.s > kMaxStages || L.size() > 6) return fail(MGRIT_ERR_INVALID, "unsupported SDIRK scheme");
+  for (int j = 0; j < tb.s; ++j)
+    if (std::fabs(tb.b[j] - tb.a(tb.s - 1, j)) > 1e-15)
+      return fail(MGRIT_ERR_UNSUPPORTED, "SDIRK tableau is not stiffly accurate");
   P.s = tb.s;
   for (int i = 0; i < tb.s; ++i)
     for (int j = 0; j < tb.s; ++j) {
@@ -329,50 +447,48 @@ mgrit_status make_sdirk_plan(const mgrit_problem* prob, SdirkPlan* out) {
       P.a32[i][j] = (float)tb.a(i, j);
     }
   P.gamma = tb.a(0, 0);
+  P.inv_gamma = 1.0 / P.gamma;
   P.gamma32 = (float)P.gamma;
-  P.nL = L.size();
-  for (int k = 0; k < L.size(); ++k) {
-    P.offL[k] = L.off[k];
-    P.cL[k] = L.coef[k];
-    P.cL32[k] = (float)L.coef[k];
-  }
+  P.inv_gamma32 = (float)P.inv_gamma;
   // M = I - gamma dtL = E^{lo} sum_k m_k E^{k-lo}: polynomial of degree hi-lo
   const int lo = L.lo(), hi = L.hi(), d = hi - lo;
   std::vector<double> poly(d + 1, 0.0);
   for (int k = 0; k < L.size(); ++k) poly[L.off[k] - lo] += -P.gamma * L.coef[k];
   poly[-lo] += 1.0;
   std::vector<std::complex<double>> roots = poly_roots(poly);
-  double scale = 1.0 / poly[d];
-  int nfwd = 0, nf = 0, npos = 0, nneg = 0;
+  std::vector<std::complex<double>> fwd, bwd;
+  std::complex<double> scale = 1.0 / poly[d];
   for (auto z : roots) {
     if (std::fabs(std::abs(z) - 1.0) < 1e-8) return fail(MGRIT_ERR_INVALID, "stage matrix has a root on |z| = 1");
-    const bool real = std::fabs(z.imag()) <= 1e-10 * std::max(1.0, std::abs(z));
-    if (!real && z.imag() < 0) {
-      ++nneg;
-      continue;
-    }
-    if (!real) ++npos;
-    if (nf >= kMaxFactors) return fail(MGRIT_ERR_INVALID, "too many stage-matrix factors");
     if (std::abs(z) < 1.0) {
-      P.dir[nf] = 1;
-      P.mre[nf] = z.real();
-      P.mim[nf] = real ? 0.0 : z.imag();
-      nfwd += real ? 1 : 2;
+      fwd.push_back(z);
     } else {
-      const std::complex<double> w = real ? std::complex<double>(1.0 / z.real(), 0.0) : 1.0 / z;
-      P.dir[nf] = -1;
-      P.mre[nf] = w.real();
-      P.mim[nf] = real ? 0.0 : w.imag();
-      scale *= real ? 1.0 / (-z.real()) : 1.0 / std::norm(z);
+      bwd.push_back(1.0 / z);
+      scale /= -z;
     }
-    ++nf;
   }
-  if (npos != nneg) return fail(MGRIT_ERR_INVALID, "unpaired complex roots of the stage matrix");
-  P.nf = nf;
-  P.ql = -lo - nfwd;
-  P.inv_pd = scale;
-  // check: M (M^{-1} y) = y on a test vector
-  const int n = 64;
+  P.kf = (int)fwd.size();
+  P.kb = (int)bwd.size();
+  if (!sdirk_orders_supported(P.kf, P.kb))
+    return fail(MGRIT_ERR_UNSUPPORTED, "stage matrix splits into unsupported recurrence orders");
+  const std::vector<double> af = rec_coeffs(fwd), ab = rec_coeffs(bwd);
+  for (int q = 0; q < P.kf; ++q) P.af[q] = af[q];
+  for (int q = 0; q < P.kb; ++q) P.ab[q] = ab[q];
+  P.ql = -lo - P.kf;
+  P.scale = scale.real();
+  P.scale32 = (float)P.scale;
+  P.nx = prob->nx;
+  P.threads = sdirk_threads(prob->nx);
+  if (!P.threads) return fail(MGRIT_ERR_UNSUPPORTED, "SDIRK needs nx = threads * C, threads a multiple of 32 <= 512");
+  P.C = prob->nx / P.threads;
+  tables->clear();
+  if (!rec_tables(P.af, P.kf, P.C, P.nx, tables) || !rec_tables(P.ab, P.kb, P.C, P.nx, tables))
+    return fail(MGRIT_ERR_INVALID, "periodic closure of the stage recurrences is singular");
+  P.tab_len = (int)tables->size();
+  if (P.tab_len != sdirk_rec_len(P.kf, P.C) + sdirk_rec_len(P.kb, P.C))
+    return fail(MGRIT_ERR_INVALID, "SDIRK table layout mismatch");
+  // check: M (M^{-1} y) = y on a test vector of the solve's size
+  const int n = prob->nx;
   std::vector<double> y(n), x(n);
   for (int i = 0; i < n; ++i) y[i] = std::sin(0.37 * i) + 0.25 * std::cos(1.9 * i * i);
   x = y;
@@ -493,6 +609,7 @@ size_t handle_bytes(const mgrit_problem* prob, const mgrit_opts* opts) {
     if (l < L || L > 2) d += P * nx;
     if (l < L) d += 2 * (N[l] + 1) * nx;
   }
+  if (prob->family == MGRIT_SDIRK) d += 4096;  // recurrence tables and the device plan
   return d * sizeof(double);
 }
 
@@ -522,17 +639,14 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
     delete h;
     return st;
   }
+  std::vector<double> sd_tables;
   if (prob->family == MGRIT_SDIRK) {
     h->sdirk = true;
-    if (!sdirk_threads(prob->nx)) {
-      delete h;
-      return fail(MGRIT_ERR_UNSUPPORTED, "SDIRK needs nx = threads * C, threads a multiple of 32 <= 512, C <= 16");
-    }
-    if ((st = make_sdirk_plan(prob, &h->splan)) != MGRIT_OK) {
+    if ((st = make_sdirk_plan(prob, &h->splan, &sd_tables)) != MGRIT_OK) {
       delete h;
       return st;
     }
-    if (sdirk_smem(h->splan, prob->nx, 0) > 227 * 1024) {
+    if (sdirk_smem(h->splan) > 227 * 1024) {
       delete h;
       return fail(MGRIT_ERR_UNSUPPORTED, "nx too large for the SDIRK stage slabs in shared memory");
     }
@@ -604,6 +718,23 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
     release(h);
     delete h;
     return fail(MGRIT_ERR_OOM, "pinned host buffer");
+  }
+  if (h->sdirk) {  // recurrence tables (FP64 then FP32) and a device copy of the plan
+    const size_t tl = (size_t)h->splan.tab_len;
+    double* tab = nullptr;
+    double* dplan = nullptr;
+    if ((st = A(tl + (tl + 1) / 2, &tab)) != MGRIT_OK || (st = A((sizeof(SdirkPlan) + 7) / 8, &dplan)) != MGRIT_OK) {
+      release(h);
+      delete h;
+      return st;
+    }
+    const std::vector<float> t32(sd_tables.begin(), sd_tables.end());
+    h->splan.tab64 = tab;
+    h->splan.tab32 = reinterpret_cast<float*>(tab + tl);
+    h->dsplan = reinterpret_cast<SdirkPlan*>(dplan);
+    cudaMemcpyAsync(tab, sd_tables.data(), tl * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(tab + tl, t32.data(), tl * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(dplan, &h->splan, sizeof(SdirkPlan), cudaMemcpyHostToDevice, h->stream);
   }
   h->fcf_threads = 0;  // chosen per launch from nx and the register tile
   if (const char* tile = std::getenv("MGRIT_TILE")) set_tile(std::atoi(tile));

@@ -28,7 +28,8 @@ struct mgrit_handle {
   std::vector<mg::CoarseOp> ops;      // ops[l-2] = Psi_l, l = 2..L
   mg::DevTaps dphi;
   bool sdirk = false;             // fine level is SDIRK (stage solves)
-  mg::SdirkPlan splan;
+  mg::SdirkPlan splan;            // host copy (its table pointers are device addresses)
+  mg::SdirkPlan* dsplan = nullptr;  // device copy (batched launches)
   std::vector<mg::DevTaps> dpsi;      // dpsi[l-2]
   std::vector<DevBuf> bufs;       // everything allocated, for release
   double* c[2] = {nullptr, nullptr};
@@ -83,7 +84,7 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
 size_t handle_bytes(const mgrit_problem* prob, const mgrit_opts* opts);
 // SDIRK stage-solve plan for the problem (factored stage matrix), checked on
 // the host against the stage matrix itself.
-mgrit_status make_sdirk_plan(const mgrit_problem* prob, mg::SdirkPlan* out);
+mgrit_status make_sdirk_plan(const mgrit_problem* prob, mg::SdirkPlan* out, std::vector<double>* tables);
 // Fine-level FCF arithmetic of a handle: 0 FP64, 1 FP64 + FP32, 3 float-float + FP32.
 int fine_prec(const mgrit_handle* h);
 // Pick the level-1 FCF launch shape (register tile, CTA size) by timing the

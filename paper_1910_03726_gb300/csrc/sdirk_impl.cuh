@@ -1,0 +1,441 @@
+// SDIRK fine steps (sm_103a), device side: the stage form of Appendix A's
+// stiffly accurate L-stable tableaux with the implicit stage matrix
+// M = I - gamma dt L solved exactly by periodic recurrences (Section 2.1).
+//
+// Stage i of a step:  K_i = (M^{-1} A_i - A_i) / gamma,  A_i = u + sum_{j<i} a_ij K_j,
+// and u_new = A_s + gamma K_s.  M^{-1} = scale * E^{ql} * B^{-1} * F^{-1} with
+//   F: x_i = sum_{q=1..KF} af_q x_{i-q} + y_i   (roots of M inside the unit circle)
+//   B: x_i = sum_{q=1..KB} ab_q x_{i+q} + y_i   (roots outside), both periodic.
+//
+// A periodic recurrence of order K over the slab runs as a chunked scan:
+//   1. each thread owns C consecutive points and runs the recurrence over
+//      them from a zero state (the state is the vector of the last K values);
+//   2. the chunk-end states are combined by an inclusive Kogge-Stone scan
+//      over the warp (state_t += A^d state_{t-d}, A = T^C, T the companion
+//      matrix) and over the warps (with A^32);
+//   3. the periodic closure is exact: the state before point 0 equals the
+//      state after point nx-1, s_{-1} = (I - T^nx)^{-1} P_last;
+//   4. each thread's carry-in state is P_{t-1} + A^t s_{-1}, and point c of
+//      its chunk gets (row 0 of T^{c+1}) . carry.
+// The backward recurrence is the same scan over mirrored thread and point
+// order.  Every table (powers of A, G, the closure matrix Q) comes from the
+// host in FP64 (and its FP32 rounding for the FP32 pass).
+//
+// Template parameters: PREC (0 FP64, 1 FP64 + FP32 second F-relaxation),
+// C (points per thread), KF/KB (recurrence orders: 1/0, 2/0, 2/1, 3/1, 3/2
+// for U1..U5, whose stage matrices keep -lo roots inside the unit circle).
+// Each instantiation file compiles one (KF, KB) pair.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "device.h"
+
+namespace mg {
+namespace sd {
+
+__device__ __forceinline__ int wrapn(int k, int nx) {
+  k = (k < 0) ? k + nx : k;
+  return (k >= nx) ? k - nx : k;
+}
+__device__ __forceinline__ int pix(int e) { return e + (e >> 3); }
+
+template <typename T>
+struct Prec;
+template <>
+struct Prec<double> {
+  static __device__ __forceinline__ double a(const SdirkPlan& p, int i, int j) { return p.a[i][j]; }
+  static __device__ __forceinline__ double gamma(const SdirkPlan& p) { return p.gamma; }
+  static __device__ __forceinline__ double inv_gamma(const SdirkPlan& p) { return p.inv_gamma; }
+  static __device__ __forceinline__ double scale(const SdirkPlan& p) { return p.scale; }
+};
+template <>
+struct Prec<float> {
+  static __device__ __forceinline__ float a(const SdirkPlan& p, int i, int j) { return p.a32[i][j]; }
+  static __device__ __forceinline__ float gamma(const SdirkPlan& p) { return p.gamma32; }
+  static __device__ __forceinline__ float inv_gamma(const SdirkPlan& p) { return p.inv_gamma32; }
+  static __device__ __forceinline__ float scale(const SdirkPlan& p) { return p.scale32; }
+};
+
+template <typename T>
+__device__ __forceinline__ T shfl_prev(T v, int d, bool bwd) {
+  return bwd ? __shfl_down_sync(0xffffffffu, v, d) : __shfl_up_sync(0xffffffffu, v, d);
+}
+
+// y += M x for a K x K row-major matrix M.
+template <typename T, int K>
+__device__ __forceinline__ void matvec_acc(const T* M, const T (&x)[K], T (&y)[K]) {
+#pragma unroll
+  for (int r = 0; r < K; ++r) {
+    T acc = y[r];
+#pragma unroll
+    for (int q = 0; q < K; ++q) acc = fma(M[r * K + q], x[q], acc);
+    y[r] = acc;
+  }
+}
+
+// Periodic recurrence of order K over the slab held in registers (x[c] is
+// point threadIdx.x * C + c).  tb: this direction's tables; smw: 16*K scratch.
+template <typename T, int C, int K, bool BWD>
+__device__ __forceinline__ void rec_scan(T (&x)[C], const T* __restrict__ tb, T* smw) {
+  if constexpr (K > 0) {
+    const T* lanep = tb + K;
+    const T* warpp = lanep + 33 * K * K;
+    const T* G = warpp + 17 * K * K;
+    const T* Q = G + C * K;
+    const int nw = blockDim.x >> 5;
+    const int lane = BWD ? 31 - (int)(threadIdx.x & 31) : (int)(threadIdx.x & 31);
+    const int warp = BWD ? nw - 1 - (int)(threadIdx.x >> 5) : (int)(threadIdx.x >> 5);
+#define MG_XM(cc) x[BWD ? C - 1 - (cc) : (cc)]
+    T aq[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) aq[q] = tb[q];
+    // 1. chunk from a zero state
+#pragma unroll
+    for (int cc = 0; cc < C; ++cc) {
+      T acc = MG_XM(cc);
+#pragma unroll
+      for (int q = 1; q <= K; ++q)
+        if (cc - q >= 0) acc = fma(aq[q - 1], MG_XM(cc - q), acc);
+      MG_XM(cc) = acc;
+    }
+    T S[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) S[q] = (C - 1 - q >= 0) ? MG_XM(C - 1 - q) : (T)0;
+    // 2. scan of chunk-end states over the warp ...
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      T Y[K];
+#pragma unroll
+      for (int q = 0; q < K; ++q) Y[q] = shfl_prev(S[q], d, BWD);
+      if (lane >= d) matvec_acc<T, K>(lanep + d * K * K, Y, S);
+    }
+    if (lane == 31)
+#pragma unroll
+      for (int q = 0; q < K; ++q) smw[warp * K + q] = S[q];
+    __syncthreads();
+    // ... and over the warps (one warp, mirrored warp index = lane)
+    if (threadIdx.x < 32) {
+      const int l = threadIdx.x;
+      T W[K];
+#pragma unroll
+      for (int q = 0; q < K; ++q) W[q] = l < nw ? smw[l * K + q] : (T)0;
+#pragma unroll
+      for (int d = 1; d < 16; d <<= 1) {
+        T Y[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) Y[q] = __shfl_up_sync(0xffffffffu, W[q], d);
+        if (l >= d) matvec_acc<T, K>(warpp + d * K * K, Y, W);
+      }
+      if (l < nw)
+#pragma unroll
+        for (int q = 0; q < K; ++q) smw[l * K + q] = W[q];
+    }
+    __syncthreads();
+    // 3. periodic closure and 4. carry-in state of this chunk
+    T P[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const T v = shfl_prev(S[q], 1, BWD);
+      P[q] = lane > 0 ? v : (T)0;
+    }
+    T last[K], sm1[K], V[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      last[q] = smw[(nw - 1) * K + q];
+      sm1[q] = (T)0;
+      V[q] = warp > 0 ? smw[(warp - 1) * K + q] : (T)0;
+    }
+    matvec_acc<T, K>(Q, last, sm1);
+    matvec_acc<T, K>(warpp + warp * K * K, sm1, V);
+    matvec_acc<T, K>(lanep + lane * K * K, V, P);
+#pragma unroll
+    for (int cc = 0; cc < C; ++cc) {
+      T acc = MG_XM(cc);
+#pragma unroll
+      for (int q = 0; q < K; ++q) acc = fma(G[cc * K + q], P[q], acc);
+      MG_XM(cc) = acc;
+    }
+#undef MG_XM
+    __syncthreads();  // smw is reused by the next scan
+  }
+}
+
+// u <- Phi u.  u in slot 0; slots 1..s-2 hold A_3..A_s (A_2 replaces u in slot 0).
+template <typename T, int C, int KF, int KB>
+__device__ __forceinline__ void sdirk_step(const SdirkPlan& p, T* slab, int plen, int nx, const T* tab, T* smw) {
+  const int s = p.s, base = threadIdx.x * C;
+  const T sc = Prec<T>::scale(p), ig = Prec<T>::inv_gamma(p), g = Prec<T>::gamma(p);
+  const T* tf = tab;
+  const T* tb = tab + sdirk_rec_len(KF, C);
+  for (int st = 1; st <= s; ++st) {
+    T* in = st <= 2 ? slab : slab + (st - 2) * plen;
+    T x[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) x[c] = in[pix(wrapn(base + c + p.ql, nx))];
+    rec_scan<T, C, KF, false>(x, tf, smw);
+    rec_scan<T, C, KB, true>(x, tb, smw);
+    if constexpr (KF == 0 && KB == 0) __syncthreads();
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const int e = pix(base + c);
+      const T A = in[e];
+      const T kv = fma(x[c], sc, -A) * ig;  // K_st = (M^{-1} A_st - A_st) / gamma
+      if (st == 1) {
+        for (int l = 3; l <= s; ++l) slab[(l - 2) * plen + e] = fma(Prec<T>::a(p, l - 1, 0), kv, A);
+        in[e] = fma(s >= 2 ? Prec<T>::a(p, 1, 0) : g, kv, A);
+      } else {
+        for (int l = st + 1; l <= s; ++l) {
+          T* Al = slab + (l - 2) * plen;
+          Al[e] = fma(Prec<T>::a(p, l - 1, st - 1), kv, Al[e]);
+        }
+        if (st == s) slab[e] = fma(g, kv, A);  // u_new = A_s + gamma K_s
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ double block_sum(double ss) {
+  __shared__ double ws[32];
+  for (int o = 16; o; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) ws[wid] = ss;
+  __syncthreads();
+  if (wid == 0) {
+    ss = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+    for (int o = 16; o; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
+  }
+  return ss;
+}
+
+__host__ __device__ constexpr size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Shared memory: FP64 tables, FP32 tables, then the slabs.
+struct Smem {
+  double* t64;
+  float* t32;
+  double* slab;
+};
+__device__ __forceinline__ Smem carve(unsigned char* raw, const SdirkPlan& p) {
+  Smem m;
+  m.t64 = reinterpret_cast<double*>(raw);
+  m.t32 = reinterpret_cast<float*>(raw + round256((size_t)p.tab_len * 8));
+  m.slab = reinterpret_cast<double*>(raw + round256((size_t)p.tab_len * 8) + round256((size_t)p.tab_len * 4));
+  return m;
+}
+__device__ __forceinline__ void load_tables(const SdirkPlan& p, const Smem& m) {
+  for (int i = threadIdx.x; i < p.tab_len; i += blockDim.x) {
+    m.t64[i] = p.tab64[i];
+    m.t32[i] = p.tab32[i];
+  }
+}
+
+// One interval's FCF-relaxation and fused residual (see fcf_kernel): m steps
+// from c_{j-1}, rho_j = v - c_j, then r_{j+1} = Phi^m rho_j.
+template <int PREC, int C, int KF, int KB>
+__device__ __forceinline__ void fcf_body(const FcfArgs& a, const SdirkPlan& p, int j, const Smem& sm,
+                                         double* smw) {
+  const int nx = a.nx, m = a.m, plen = padded_len(nx);
+  double* slab = sm.slab;
+  const double* start = a.u_old + (long long)(j - 1) * a.cstride;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) slab[pix(i)] = a.zero_old ? 0.0 : start[i];
+  __syncthreads();
+  for (int s = 0; s < m; ++s) sdirk_step<double, C, KF, KB>(p, slab, plen, nx, sm.t64, smw);
+  const double* oldj = a.u_old + (long long)j * a.cstride;
+  double* cn = a.c_new + (long long)j * nx;
+  const bool more = j < a.N;
+  double ss = 0.0;
+  if (PREC == 0) {
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const double v = slab[pix(i)];
+      cn[i] = v;
+      slab[pix(i)] = v - (a.zero_old ? 0.0 : oldj[i]);
+    }
+    __syncthreads();
+    if (!more) return;
+    for (int s = 0; s < m; ++s) sdirk_step<double, C, KF, KB>(p, slab, plen, nx, sm.t64, smw);
+    double* rr = a.r + (long long)(j + 1) * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const double v = slab[pix(i)];
+      rr[i] = v;
+      ss = fma(v, v, ss);
+    }
+  } else {
+    // each thread owns points i = tid + k*blockDim (k < C): read all FP64
+    // values before the FP32 slab (same storage) is written
+    float* fs = reinterpret_cast<float*>(slab);
+    double vals[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) vals[k] = slab[pix(threadIdx.x + k * blockDim.x)];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      const int i = threadIdx.x + k * blockDim.x;
+      cn[i] = vals[k];
+      fs[pix(i)] = (float)(vals[k] - (a.zero_old ? 0.0 : oldj[i]));
+    }
+    __syncthreads();
+    if (!more) return;
+    for (int s = 0; s < m; ++s)
+      sdirk_step<float, C, KF, KB>(p, fs, plen, nx, sm.t32, reinterpret_cast<float*>(smw));
+    double* rr = a.r + (long long)(j + 1) * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const double v = (double)fs[pix(i)];
+      rr[i] = v;
+      ss = fma(v, v, ss);
+    }
+  }
+  if (a.partial) {
+    ss = block_sum(ss);
+    if (threadIdx.x == 0) a.partial[j] = ss;
+  }
+}
+
+template <int PREC, int C, int KF, int KB>
+__global__ void __launch_bounds__(512) fcf_sdirk_kernel(const FcfArgs a, const SdirkPlan p) {
+  extern __shared__ __align__(256) unsigned char smraw[];
+  __shared__ __align__(16) double smw[16 * kMaxRec];
+  const Smem sm = carve(smraw, p);
+  load_tables(p, sm);
+  fcf_body<PREC, C, KF, KB>(a, p, blockIdx.x + 1, sm, smw);
+}
+
+// Batched over solves: one CTA per (solve, interval) item.
+template <int PREC, int C, int KF, int KB>
+__global__ void __launch_bounds__(512) fcf_sdirk_batched_kernel(const BatchSolve* __restrict__ S,
+                                                                const BatchItem* __restrict__ items) {
+  extern __shared__ __align__(256) unsigned char smraw[];
+  __shared__ __align__(16) double smw[16 * kMaxRec];
+  __shared__ SdirkPlan p;
+  const BatchItem it = items[blockIdx.x];
+  const BatchSolve& b = S[it.solve];
+  {
+    const int* src = reinterpret_cast<const int*>(b.sd);
+    int* dst = reinterpret_cast<int*>(&p);
+    for (int i = threadIdx.x; i < (int)(sizeof(SdirkPlan) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const Smem sm = carve(smraw, p);
+  load_tables(p, sm);
+  const FcfArgs a = b.fcf;
+  fcf_body<PREC, C, KF, KB>(a, p, it.j, sm, smw);
+}
+
+// Runs `steps` SDIRK steps on each of gridDim.x slabs: CTA v starts from
+// in + v*in_stride and stores to out + v*out_stride row r = n/store_every - 1
+// (+1 and the starting slab as row 0 when store_first) after step n; with
+// partial, the squared norm of its final slab goes to partial[v].  Serves
+// propagation, sequential stepping and the F-point interpolation.
+template <int C, int KF, int KB>
+__global__ void __launch_bounds__(512) steps_sdirk_kernel(const double* in, long long in_stride, double* out,
+                                                          long long out_stride, int nx, int steps, int store_every,
+                                                          int store_first, const SdirkPlan p, double* partial) {
+  extern __shared__ __align__(256) unsigned char smraw[];
+  __shared__ __align__(16) double smw[16 * kMaxRec];
+  const Smem sm = carve(smraw, p);
+  load_tables(p, sm);
+  double* slab = sm.slab;
+  const int plen = padded_len(nx);
+  const long long v = blockIdx.x;
+  const double* src = in + v * in_stride;
+  double* dst = out + v * out_stride;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const double x = src[i];
+    slab[pix(i)] = x;
+    if (store_first) dst[i] = x;
+  }
+  __syncthreads();
+  for (int n = 1; n <= steps; ++n) {
+    sdirk_step<double, C, KF, KB>(p, slab, plen, nx, sm.t64, smw);
+    if (n % store_every == 0) {
+      double* row = dst + (long long)(n / store_every - 1 + store_first) * nx;
+      for (int i = threadIdx.x; i < nx; i += blockDim.x) row[i] = slab[pix(i)];
+    }
+  }
+  if (partial) {
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const double x = slab[pix(i)];
+      ss = fma(x, x, ss);
+    }
+    ss = block_sum(ss);
+    if (threadIdx.x == 0) partial[v] = ss;
+  }
+}
+
+template <typename Kern>
+static cudaError_t smem_attr(Kern kernel, size_t bytes) {
+  if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaSuccess;
+}
+
+// Call f.template operator()<C>() with the plan's compile-time chunk length
+// (C in {1, 4, 16}, see sdirk_threads).
+template <typename F>
+static cudaError_t with_chunk(int C, F&& f) {
+  switch (C) {
+    case 1: return f.template operator()<1>();
+    case 4: return f.template operator()<4>();
+    case 16: return f.template operator()<16>();
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sd
+
+// Launchers for one (KF, KB) pair; instantiated by sdirk_k<KF><KB>.cu.
+template <int KF, int KB>
+cudaError_t sdirk_fcf(const FcfArgs& a, const SdirkPlan& p, int precision, cudaStream_t s) {
+  const size_t smem = sdirk_smem(p);
+  return sd::with_chunk(p.C, [&]<int C>() -> cudaError_t {
+    cudaError_t e;
+    if (precision == 0) {
+      if ((e = sd::smem_attr(sd::fcf_sdirk_kernel<0, C, KF, KB>, smem)) != cudaSuccess) return e;
+      sd::fcf_sdirk_kernel<0, C, KF, KB><<<a.N, p.threads, smem, s>>>(a, p);
+    } else {
+      if ((e = sd::smem_attr(sd::fcf_sdirk_kernel<1, C, KF, KB>, smem)) != cudaSuccess) return e;
+      sd::fcf_sdirk_kernel<1, C, KF, KB><<<a.N, p.threads, smem, s>>>(a, p);
+    }
+    return cudaGetLastError();
+  });
+}
+
+template <int KF, int KB>
+cudaError_t sdirk_fcf_batched(const BatchSolve* S, const BatchItem* items, int nitems, const SdirkPlan& any,
+                              size_t smem, int precision, cudaStream_t s) {
+  return sd::with_chunk(any.C, [&]<int C>() -> cudaError_t {
+    cudaError_t e;
+    if (precision == 0) {
+      if ((e = sd::smem_attr(sd::fcf_sdirk_batched_kernel<0, C, KF, KB>, smem)) != cudaSuccess) return e;
+      sd::fcf_sdirk_batched_kernel<0, C, KF, KB><<<nitems, any.threads, smem, s>>>(S, items);
+    } else {
+      if ((e = sd::smem_attr(sd::fcf_sdirk_batched_kernel<1, C, KF, KB>, smem)) != cudaSuccess) return e;
+      sd::fcf_sdirk_batched_kernel<1, C, KF, KB><<<nitems, any.threads, smem, s>>>(S, items);
+    }
+    return cudaGetLastError();
+  });
+}
+
+template <int KF, int KB>
+cudaError_t sdirk_steps(const double* in, long long in_stride, double* out, long long out_stride, int count, int nx,
+                        int steps, int store_every, int store_first, const SdirkPlan& p, double* partial,
+                        cudaStream_t s) {
+  const size_t smem = sdirk_smem(p);
+  return sd::with_chunk(p.C, [&]<int C>() -> cudaError_t {
+    cudaError_t e = sd::smem_attr(sd::steps_sdirk_kernel<C, KF, KB>, smem);
+    if (e != cudaSuccess) return e;
+    sd::steps_sdirk_kernel<C, KF, KB><<<count, p.threads, smem, s>>>(in, in_stride, out, out_stride, nx, steps,
+                                                                     store_every, store_first, p, partial);
+    return cudaGetLastError();
+  });
+}
+
+#define MG_SDIRK_INSTANTIATE(KF, KB)                                                                             \
+  template cudaError_t sdirk_fcf<KF, KB>(const FcfArgs&, const SdirkPlan&, int, cudaStream_t);                   \
+  template cudaError_t sdirk_fcf_batched<KF, KB>(const BatchSolve*, const BatchItem*, int, const SdirkPlan&,      \
+                                                 size_t, int, cudaStream_t);                                     \
+  template cudaError_t sdirk_steps<KF, KB>(const double*, long long, double*, long long, int, int, int, int, int, \
+                                           const SdirkPlan&, double*, cudaStream_t);
+
+}  // namespace mg

@@ -1,0 +1,6 @@
+// SDIRK kernels for forward/backward recurrence orders (2, 0).
+#include "sdirk_impl.cuh"
+
+namespace mg {
+MG_SDIRK_INSTANTIATE(2, 0)
+}  // namespace mg

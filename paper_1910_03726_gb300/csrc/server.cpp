@@ -218,6 +218,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     b.taps = 2 * k;
     b.psi = 2 * k + 1;
     b.cluster = h->march_cluster;
+    b.sd = h->dsplan;
     taps[2 * k] = h->dphi;
     taps[2 * k + 1] = h->dpsi.back();
   }
@@ -226,26 +227,25 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
   cudaMemcpyAsync(S->dS.p, hs.data(), n * sizeof(BatchSolve), cudaMemcpyHostToDevice, S->stream);
   cudaMemcpyAsync(S->dTaps.p, taps.data(), 2 * n * sizeof(DevTaps), cudaMemcpyHostToDevice, S->stream);
   // ---- batched FCF, one launch per (nx, launch shape): each solve keeps the
-  // shape it was tuned to, so its arithmetic is the single-solve path's
-  std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
+  // shape it was tuned to, so its arithmetic is the single-solve path's.
+  // SDIRK fine levels: one launch per (nx, recurrence orders, precision).
+  std::map<std::tuple<int, int, int, int>, std::vector<int>> groups, sgroups;
   for (int k = 0; k < n; ++k) {
     mgrit_handle* h = act[k]->h;
-    if (h->sdirk) {  // SDIRK fine levels relax through their own launch
-      cudaError_t e = launch_fine_fcf(h, hs[k].fcf, hs[k].prec);
-      if (e != cudaSuccess) return launch_ok(e, "fcf_sdirk");
-      h->kcount[MGRIT_K_FCF]++;
-      continue;
-    }
-    groups[{h->nx, h->fine_tile, h->fine_threads, h->dphi.span}].push_back(k);
+    if (h->sdirk)
+      sgroups[{h->nx, h->splan.kf, h->splan.kb, hs[k].prec == 0 ? 0 : 1}].push_back(k);
+    else
+      groups[{h->nx, h->fine_tile, h->fine_threads, h->dphi.span}].push_back(k);
   }
   std::vector<BatchItem> items;
-  std::vector<std::pair<size_t, size_t>> ranges;
-  for (auto& g : groups) {
-    const size_t b0 = items.size();
-    for (int k : g.second)
-      for (int j = 1; j <= hs[k].fcf.N; ++j) items.push_back({k, j});
-    ranges.push_back({b0, items.size()});
-  }
+  std::vector<std::pair<size_t, size_t>> ranges, sranges;
+  for (auto* G : {&groups, &sgroups})
+    for (auto& g : *G) {
+      const size_t b0 = items.size();
+      for (int k : g.second)
+        for (int j = 1; j <= hs[k].fcf.N; ++j) items.push_back({k, j});
+      (G == &groups ? ranges : sranges).push_back({b0, items.size()});
+    }
   if (!S->dItems.reserve(items.size())) return fail(MGRIT_ERR_OOM, "server batch items");
   cudaMemcpyAsync(S->dItems.p, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, S->stream);
   size_t gi = 0;
@@ -256,6 +256,16 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     cudaError_t e = launch_fcf_batched(S->dS.p, S->dItems.p + rg.first, (int)(rg.second - rg.first), S->dTaps.p, nx,
                                        th, tile, span, S->stream);
     if (e != cudaSuccess) return launch_ok(e, "fcf_batched");
+    for (int k : g.second) act[k]->h->kcount[MGRIT_K_FCF]++;
+  }
+  gi = 0;
+  for (auto& g : sgroups) {
+    const auto rg = sranges[gi++];
+    size_t smem = 0;
+    for (int k : g.second) smem = std::max(smem, sdirk_smem(act[k]->h->splan));
+    cudaError_t e = launch_fcf_sdirk_batched(S->dS.p, S->dItems.p + rg.first, (int)(rg.second - rg.first),
+                                             act[g.second[0]]->h->splan, smem, std::get<3>(g.first), S->stream);
+    if (e != cudaSuccess) return launch_ok(e, "fcf_sdirk_batched");
     for (int k : g.second) act[k]->h->kcount[MGRIT_K_FCF]++;
   }
   // ---- norms of all solves, one read-back
