@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MGRIT_ABI_VERSION 1
+#define MGRIT_ABI_VERSION 2
 #define MGRIT_MAX_LEVELS 8
 #define MGRIT_MAX_HISTORY 128
 #define MGRIT_MAX_TAPS 256
@@ -65,9 +65,12 @@ enum { MGRIT_ERK = 0, MGRIT_SDIRK = 1 };
  *  FP64   every step in FP64.
  *  MIXED  the C-point update and its residual rho_j = Phi^m c_{j-1} - c_j in
  *         FP64; the second F-relaxation, which only acts on the correction
- *         rho, in FP32; coarse solve and convergence test in FP64.
- *  MIXED_DF  as MIXED, with the FP64 pass evaluated in float-float (pairs of
- *         FP32, about 44 significant bits) on the FP32 pipes. */
+ *         rho, in FP32.  Below level 1 the V-cycle relaxes the error
+ *         equation in FP32 on levels 2..L-1; the coarsest-level solve (the
+ *         sequential march) and the convergence test stay FP64.
+ *  MIXED_DF  as MIXED, with the FP64 pass of an ERK fine level evaluated in
+ *         float-float (pairs of FP32, about 44 significant bits) on the FP32
+ *         pipes; SDIRK fine levels keep their FP64 pass. */
 enum { MGRIT_PREC_FP64 = 0, MGRIT_PREC_MIXED = 1, MGRIT_PREC_MIXED_DF = 2 };
 
 /* Coarse-operator sparsity rule (Sections 4.2-4.4, 4.6). */
@@ -155,6 +158,8 @@ typedef struct mgrit_result {
   int32_t fine_tile;     /* level-1 FCF launch shape picked by the autotuner:       */
   int32_t fine_threads;  /*   register tile (99 = fixed-span path) and CTA size     */
   int32_t graph;         /* 1 if the solve ran as one CUDA-graph launch             */
+  int32_t fine_collapsed; /* 1 if each FCF pass applies Phi^m as one stencil        */
+  int32_t reserved;
   int32_t kernel_count[MGRIT_K_KINDS];  /* launches per kind                         */
   double kernel_ms[MGRIT_K_KINDS];      /* device time per kind (FLAG_TIME_KERNELS)  */
 } mgrit_result;

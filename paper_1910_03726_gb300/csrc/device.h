@@ -74,6 +74,9 @@ struct CorrectArgs {
 // tile: register tile (0, 4 or 8), kFixedTile for the fixed-span path of the
 // collapsed ERK stencils; -1 = the default for this stencil and nx.
 constexpr int kFixedTile = 99;
+// kChunkTile: any dense span, taken in chunks of 8 taps whose window of
+// R + 7 inputs is loaded into registers once per chunk (R = 8).
+constexpr int kChunkTile = 98;
 cudaError_t launch_fcf(const FcfArgs& a, const DevTaps& t, int precision, int threads,
                        cudaStream_t s, int tile = -1);
 
@@ -124,6 +127,8 @@ struct SdirkPlan {
   int C, threads;        // points per thread and CTA size, nx = threads * C
   int nx;
   int tab_len;           // elements of one precision's recurrence tables
+  int steps_f, steps_b;  // warp-scan doubling steps that matter per direction
+  int trunc_f, trunc_b;  // 1: A^32 below rounding (previous-warp carry only)
   double a[kMaxStages][kMaxStages];
   float a32[kMaxStages][kMaxStages];
   double gamma, inv_gamma, scale;   // scale = 1 / (p_d prod_{|z|>1} (-z))

@@ -12,6 +12,7 @@
 #include <complex>
 #include <cmath>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -485,6 +486,32 @@ mgrit_status make_sdirk_plan(const mgrit_problem* prob, SdirkPlan* out, std::vec
   if (!rec_tables(P.af, P.kf, P.C, P.nx, tables) || !rec_tables(P.ab, P.kb, P.C, P.nx, tables))
     return fail(MGRIT_ERR_INVALID, "periodic closure of the stage recurrences is singular");
   P.tab_len = (int)tables->size();
+  // truncation of the scans: drop terms whose factor A^d lies below FP64
+  // rounding (max-row-sum norm < 1e-18)
+  for (int dir = 0; dir < 2; ++dir) {
+    const int K = dir == 0 ? P.kf : P.kb;
+    int steps = 5, trunc = 0;
+    if (K > 0) {
+      const Mat A = mat_pow(companion(dir == 0 ? P.af : P.ab, K), P.C, K);
+      auto norm = [&](const Mat& M) {
+        double n = 0.0;
+        for (int i = 0; i < K; ++i) {
+          double r = 0.0;
+          for (int j = 0; j < K; ++j) r += std::fabs(M[i * K + j]);
+          n = std::max(n, r);
+        }
+        return n;
+      };
+      for (int D = 0; D <= 5; ++D)
+        if (norm(mat_pow(A, 1LL << D, K)) < 1e-18) {
+          steps = D;
+          break;
+        }
+      trunc = norm(mat_pow(A, 32, K)) < 1e-18 ? 1 : 0;
+    }
+    (dir == 0 ? P.steps_f : P.steps_b) = steps;
+    (dir == 0 ? P.trunc_f : P.trunc_b) = trunc;
+  }
   if (P.tab_len != sdirk_rec_len(P.kf, P.C) + sdirk_rec_len(P.kb, P.C))
     return fail(MGRIT_ERR_INVALID, "SDIRK table layout mismatch");
   // check: M (M^{-1} y) = y on a test vector of the solve's size
@@ -518,26 +545,57 @@ struct TuneKey {
     return std::tie(prec, nx, span, ntaps, m) < std::tie(o.prec, o.nx, o.span, o.ntaps, o.m);
   }
 };
-std::map<TuneKey, std::pair<int, int>> g_tune;
+struct TunePick {
+  int collapse, tile, threads;
+};
+std::map<TuneKey, TunePick> g_tune;
 std::mutex g_tune_mu;
+
+bool fixed_span(int span) { return span == 2 || span == 5 || span == 10 || span == 17 || span == 31; }
 }  // namespace
 
+// Level-1 FCF launch shape: step by step with Phi (m steps per pass) or one
+// application of the collapsed Phi^m per pass; register tile (fixed-span,
+// sliding window 8 or 4, one tap at a time) and CTA size.  Timed on the
+// handle's own interval count at set-up and cached per problem shape.
 void autotune_fine(mgrit_handle* h) {
   const int prec = fine_prec(h);
+  h->fine_collapse = 0;
   h->fine_tile = default_tile(h->dphi, h->nx);
   h->fine_threads = default_threads(h->nx, h->fine_tile);
   if (h->sdirk || (h->opts.flags & MGRIT_FLAG_NO_AUTOTUNE)) return;
-  const TuneKey key{prec, h->nx, h->dphi.span, h->dphi.n, h->m};
+  const int nx = h->nx;
+  auto valid = [&](int collapse, int tile) {
+    if (collapse && !h->have_phim) return false;
+    const DevTaps& t = collapse ? h->dphim : h->dphi;
+    const bool dense = t.span > 0 && nx >= 64;
+    if (tile == kFixedTile) return !collapse && dense && fixed_span(t.span);
+    if (tile == kChunkTile) return dense && t.span >= 8;
+    if (tile == 8 || tile == 4) return dense;
+    return tile == 0;
+  };
+  // MGRIT_FCF_SHAPE="tile,threads[,collapse]" pins the shape (reproducible profiling)
+  if (const char* shape = std::getenv("MGRIT_FCF_SHAPE")) {
+    int tile = 0, th = 0, col = 0;
+    const int n = std::sscanf(shape, "%d,%d,%d", &tile, &th, &col);
+    if (n >= 2 && (th == 128 || th == 256 || th == 512) && (col == 0 || col == 1) && valid(col, tile)) {
+      h->fine_collapse = col;
+      h->fine_tile = tile;
+      h->fine_threads = th;
+      return;
+    }
+  }
+  const TuneKey key{prec, nx, h->dphi.span, h->dphi.n, h->m};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      h->fine_tile = it->second.first;
-      h->fine_threads = it->second.second;
+      h->fine_collapse = it->second.collapse;
+      h->fine_tile = it->second.tile;
+      h->fine_threads = it->second.threads;
       return;
     }
   }
-  const int nx = h->nx;
   FcfArgs f = {};
   f.u_old = h->c[0];
   f.cstride = nx;
@@ -545,56 +603,62 @@ void autotune_fine(mgrit_handle* h) {
   f.r = h->r[1];
   f.partial = h->partial;
   f.nx = nx;
-  f.m = h->m;
-  f.N = std::min(h->Nl[1], 3 * 152 * 2);
-  cudaMemsetAsync(h->c[0], 0, ((size_t)f.N + 1) * nx * sizeof(double), h->stream);
+  f.N = std::min(h->Nl[1], 4096);  // the real interval count: wave quantisation matters
+  // nonzero trial data (every byte 0x3F: each double is 4.8e-4), so that no
+  // interval takes the zero-slab shortcut while it is timed
+  cudaMemsetAsync(h->c[0], 0x3F, ((size_t)f.N + 1) * nx * sizeof(double), h->stream);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     cudaGetLastError();
     return;
   }
   float best = 1e30f;
-  std::pair<int, int> pick{h->fine_tile, h->fine_threads};
-  const bool dense = h->dphi.span > 0 && nx >= 64;
-  for (int tile : {kFixedTile, 8, 4, 0}) {
-    if (tile > 0 && !dense) continue;
-    if (tile == kFixedTile && !(h->dphi.span == 2 || h->dphi.span == 5 || h->dphi.span == 10 ||
-                                h->dphi.span == 17 || h->dphi.span == 31))
-      continue;
-    const int per = tile == kFixedTile ? 4 : (tile > 0 ? tile : 1);
-    for (int th : {128, 256, 512}) {
-      if (th > std::max(32, (nx / per + 31) / 32 * 32)) continue;
-      if (launch_fcf(f, h->dphi, prec, th, h->stream, tile) != cudaSuccess) {
-        cudaGetLastError();
-        continue;
-      }
-      float t = 1e30f;
-      for (int rep = 0; rep < 3; ++rep) {
-        cudaEventRecord(e0, h->stream);
-        launch_fcf(f, h->dphi, prec, th, h->stream, tile);
-        cudaEventRecord(e1, h->stream);
-        float ms = 0.0f;
-        if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
-          t = std::min(t, ms);
-        else
+  TunePick pick{0, h->fine_tile, h->fine_threads};
+  for (int collapse : {0, 1})
+    for (int tile : {kFixedTile, kChunkTile, 8, 4, 0}) {
+      if (!valid(collapse, tile) || (collapse && tile == 0)) continue;
+      const DevTaps& t = collapse ? h->dphim : h->dphi;
+      f.m = collapse ? 1 : h->m;
+      const int per = tile == kFixedTile ? 4 : (tile == kChunkTile ? 8 : (tile > 0 ? tile : 1));
+      for (int th : {128, 256, 512}) {
+        if (th > std::max(32, (nx / per + 31) / 32 * 32)) continue;
+        if (launch_fcf(f, t, prec, th, h->stream, tile) != cudaSuccess) {
           cudaGetLastError();
-      }
-      if (t < best) {
-        best = t;
-        pick = {tile, th};
+          continue;
+        }
+        float tm = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+          cudaEventRecord(e0, h->stream);
+          launch_fcf(f, t, prec, th, h->stream, tile);
+          cudaEventRecord(e1, h->stream);
+          float ms = 0.0f;
+          if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+            tm = std::min(tm, ms);
+          else
+            cudaGetLastError();
+        }
+        if (tm < best) {
+          best = tm;
+          pick = {collapse, tile, th};
+        }
       }
     }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  h->fine_tile = pick.first;
-  h->fine_threads = pick.second;
+  h->fine_collapse = pick.collapse;
+  h->fine_tile = pick.tile;
+  h->fine_threads = pick.threads;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = pick;
 }
 
 cudaError_t launch_fine_fcf(mgrit_handle* h, const FcfArgs& f, int prec) {
   if (h->sdirk) return launch_fcf_sdirk(f, h->splan, prec == 0 ? 0 : 1, h->stream);
+  if (h->fine_collapse) {  // each pass is one application of Phi^m
+    FcfArgs g = f;
+    g.m = 1;
+    return launch_fcf(g, h->dphim, prec, h->fine_threads, h->stream, h->fine_tile);
+  }
   return launch_fcf(f, h->dphi, prec, h->fine_threads, h->stream, h->fine_tile);
 }
 
@@ -666,6 +730,14 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
       return fail(MGRIT_ERR_UNSUPPORTED, "coarse stencil wider than 256 taps");
     }
   h->dphi = to_dev(h->phi);
+  if (!h->sdirk) {  // Phi^m as one stencil (the m-step propagator of an interval)
+    Taps pm = taps_power(h->phi, h->m);
+    const int reach = std::max(-pm.lo(), pm.hi());
+    if (pm.size() <= kMaxDevTaps && pm.size() + 8 < h->nx && reach + 8 < h->nx) {  // indices wrap at most once
+      h->dphim = to_dev(pm);
+      h->have_phim = true;
+    }
+  }
   for (auto& op : h->ops) h->dpsi.push_back(to_dev(op.taps));
   // operator complexity, Eq. 5 (ERK)
   {
@@ -816,6 +888,7 @@ void collect_stats(mgrit_handle* h, mgrit_result* R) {
   R->launches = total;
   R->fine_tile = h->fine_tile;
   R->fine_threads = h->fine_threads;
+  R->fine_collapsed = h->fine_collapse;
   for (size_t p = 0; p < h->evkind.size(); ++p) {
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, h->evpool[2 * p], h->evpool[2 * p + 1]) == cudaSuccess)

@@ -27,6 +27,8 @@ struct mgrit_handle {
   mg::Taps phi;                       // fine propagator (ERK, collapsed)
   std::vector<mg::CoarseOp> ops;      // ops[l-2] = Psi_l, l = 2..L
   mg::DevTaps dphi;
+  mg::DevTaps dphim;                  // Phi^m as one stencil (ERK, if <= 256 taps)
+  bool have_phim = false;
   bool sdirk = false;             // fine level is SDIRK (stage solves)
   mg::SdirkPlan splan;            // host copy (its table pointers are device addresses)
   mg::SdirkPlan* dsplan = nullptr;  // device copy (batched launches)
@@ -39,6 +41,7 @@ struct mgrit_handle {
   double* norm_host = nullptr;    // pinned
   int fcf_threads = 512, march_cluster = 1, march_threads = 256;
   int fine_tile = -1, fine_threads = 0;   // level-1 FCF launch shape (autotuned)
+  int fine_collapse = 0;                  // 1: each pass applies Phi^m once
   // a whole solve as one CUDA graph (WHILE over cycles, IF around each
   // coarse correction), built at the first solve
   cudaGraph_t graph = nullptr;

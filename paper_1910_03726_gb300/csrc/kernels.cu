@@ -197,11 +197,49 @@ __device__ __forceinline__ void step_fixed(const DevTaps& t, const T* __restrict
   }
 }
 
+// dst = T src (+ g) for any dense span: the span is taken in chunks of CH
+// taps; per chunk each thread loads its R + CH - 1 inputs into registers once
+// and does CH * R FMAs with compile-time indices; the last span % CH taps
+// read their inputs directly.  Suits the wide collapsed stencils of Phi^m.
+constexpr int kChunked = -8;
+template <typename T, int R, int CH>
+__device__ __forceinline__ void step_chunked(const DevTaps& t, const T* __restrict__ src, T* __restrict__ dst,
+                                             const double* __restrict__ g, int nx) {
+  const int lo = t.lo, span = t.span;
+  for (int i0 = threadIdx.x * R; i0 < nx; i0 += blockDim.x * R) {
+    T acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = (g && i0 + r < nx) ? vfrom<T>(__ldg(g + i0 + r)) : vzero<T>();
+    int k = 0;
+    for (; k + CH <= span; k += CH) {
+      T w[R + CH - 1];
+#pragma unroll
+      for (int q = 0; q < R + CH - 1; ++q) w[q] = src[pidx(wrapi(i0 + lo + k + q, nx))];
+#pragma unroll
+      for (int kk = 0; kk < CH; ++kk) {
+        const T c = dense_coef<T>(t, k + kk);
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = vfma1<T>(c, w[r + kk], acc[r], t.one);
+      }
+    }
+    for (; k < span; ++k) {
+      const T c = dense_coef<T>(t, k);
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = vfma1<T>(c, src[pidx(wrapi(i0 + lo + k + r, nx))], acc[r], t.one);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (i0 + r < nx) dst[pidx(i0 + r)] = vfinish<T>(acc[r]);
+  }
+}
+
 // R encodes the path: 0 one tap at a time; 4, 8 sliding window; SPAN > 0
-// selects the fixed-span path with register tile R.
+// selects the fixed-span path with register tile R; SPAN == kChunked the
+// chunked path.
 template <typename T, int R, int SPAN = 0>
 __device__ __forceinline__ void slab_step(const DevTaps& t, const T* src, T* dst, const double* g, int nx) {
-  if constexpr (SPAN > 0) step_fixed<T, R, SPAN>(t, src, dst, g, nx);
+  if constexpr (SPAN == kChunked) step_chunked<T, R, 8>(t, src, dst, g, nx);
+  else if constexpr (SPAN > 0) step_fixed<T, R, SPAN>(t, src, dst, g, nx);
   else if constexpr (R > 0) step_tiled<T, R>(t, src, dst, g, nx);
   else step_sparse<T>(t, src, dst, g, nx);
 }
@@ -280,9 +318,14 @@ __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const
   df64* b0 = reinterpret_cast<df64*>(smraw);
   df64* b1 = b0 + plen;
   const double* start = a.u_old + (long long)(j - 1) * a.cstride;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) b0[pidx(i)] = df_from(a.zero_old ? 0.0 : start[i]);
-  __syncthreads();
-  for (int s = 1; s <= m; ++s) {
+  int nz = 0;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const double v = a.zero_old ? 0.0 : start[i];
+    b0[pidx(i)] = df_from(v);
+    nz |= v != 0.0;
+  }
+  const bool run1 = __syncthreads_or(nz) || a.g;  // zero slab, no rhs: Phi^m 0 = 0
+  for (int s = 1; s <= m && run1; ++s) {
     const double* g = a.g ? a.g + ((long long)(j - 1) * m + s) * nx : nullptr;
     slab_step<df64, R, SPAN>(t, b0, b1, g, nx);
     __syncthreads();
@@ -292,14 +335,17 @@ __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const
   double* cn = a.c_new + (long long)j * nx;
   float* f0 = reinterpret_cast<float*>(b1);
   float* f1 = f0 + plen;
+  nz = 0;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     const double v = df_to(b0[pidx(i)]);
     cn[i] = v;
-    f0[pidx(i)] = (float)(v - (a.zero_old ? 0.0 : oldj[i]));
+    const float rho = (float)(v - (a.zero_old ? 0.0 : oldj[i]));
+    f0[pidx(i)] = rho;
+    nz |= rho != 0.0f;
   }
-  __syncthreads();
+  const bool run2 = __syncthreads_or(nz);
   if (j >= a.N) return;
-  for (int s = 1; s <= m; ++s) {
+  for (int s = 1; s <= m && run2; ++s) {
     slab_step<float, R, SPAN>(t, f0, f1, nullptr, nx);
     __syncthreads();
     float* tmp = f0; f0 = f1; f1 = tmp;
@@ -331,9 +377,16 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
   double* b0 = reinterpret_cast<double*>(smraw);
   double* b1 = b0 + plen;
   const double* start = a.u_old + (long long)(j - 1) * a.cstride;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) b0[pidx(i)] = a.zero_old ? 0.0 : start[i];
-  __syncthreads();
-  for (int s = 1; s <= m; ++s) {
+  int nz = 0;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const double v = a.zero_old ? 0.0 : start[i];
+    b0[pidx(i)] = v;
+    nz |= v != 0.0;
+  }
+  // Phi^m of an identically zero slab is zero (no right-hand side): the
+  // steps are skipped, which leaves the result exactly as computed
+  const bool run1 = __syncthreads_or(nz) || a.g;
+  for (int s = 1; s <= m && run1; ++s) {
     const double* g = a.g ? a.g + ((long long)(j - 1) * m + s) * nx : nullptr;
     slab_step<double, R, SPAN>(t, b0, b1, g, nx);
     __syncthreads();
@@ -344,16 +397,19 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
   const bool more = j < a.N;
   double ss = 0.0;
   if (PREC == 0) {
+    nz = 0;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       const double v = b0[pidx(i)];
       cn[i] = v;
-      b1[pidx(i)] = v - (a.zero_old ? 0.0 : oldj[i]);
+      const double rho = v - (a.zero_old ? 0.0 : oldj[i]);
+      b1[pidx(i)] = rho;
+      nz |= rho != 0.0;
     }
-    __syncthreads();
+    const bool run2 = __syncthreads_or(nz);
     if (!more) return;
     double* x0 = b1;
     double* x1 = b0;
-    for (int s = 1; s <= m; ++s) {
+    for (int s = 1; s <= m && run2; ++s) {
       slab_step<double, R, SPAN>(t, x0, x1, nullptr, nx);
       __syncthreads();
       double* tmp = x0; x0 = x1; x1 = tmp;
@@ -367,14 +423,17 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
   } else {
     float* f0 = reinterpret_cast<float*>(b1);
     float* f1 = f0 + plen;
+    nz = 0;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       const double v = b0[pidx(i)];
       cn[i] = v;
-      f0[pidx(i)] = (float)(v - (a.zero_old ? 0.0 : oldj[i]));
+      const float rho = (float)(v - (a.zero_old ? 0.0 : oldj[i]));
+      f0[pidx(i)] = rho;
+      nz |= rho != 0.0f;
     }
-    __syncthreads();
+    const bool run2 = __syncthreads_or(nz);
     if (!more) return;
-    for (int s = 1; s <= m; ++s) {
+    for (int s = 1; s <= m && run2; ++s) {
       slab_step<float, R, SPAN>(t, f0, f1, nullptr, nx);
       __syncthreads();
       float* tmp = f0; f0 = f1; f1 = tmp;
@@ -666,7 +725,7 @@ int default_tile(const DevTaps& t, int nx) { return (t.span > 0 && nx >= 64) ? g
 static int threads_for(int nx, int R, int hint) {
   const int cap = 512;
   if (hint > 0) return hint < cap ? hint : cap;
-  if (R == kFixedTile) R = 8;
+  if (R == kFixedTile || R == kChunkTile) R = 8;
   const int per = R > 0 ? R : 4;
   int th = (nx + per - 1) / per;
   th = ((th + 31) / 32) * 32;
@@ -708,6 +767,15 @@ static cudaError_t launch_fcf_fixed(const FcfArgs& a, const DevTaps& t, int thre
 
 cudaError_t launch_fcf(const FcfArgs& a, const DevTaps& t, int precision, int threads, cudaStream_t s, int tile) {
   if (a.N < 1) return cudaSuccess;
+  if (tile == kChunkTile) {
+    if (!(t.span > 0) || a.nx < 64) return cudaErrorInvalidValue;
+    switch (precision) {
+      case 0: return launch_fcf_t<0, 8, kChunked>(a, t, threads, s);
+      case 1: return launch_fcf_t<1, 8, kChunked>(a, t, threads, s);
+      case 2: return launch_fcf_t<2, 8, kChunked>(a, t, threads, s);
+      default: return launch_fcf_t<3, 8, kChunked>(a, t, threads, s);
+    }
+  }
   if (tile == kFixedTile) {
     if (!fixed_span_ok(t.span) || a.nx < 64) return cudaErrorInvalidValue;
     switch (precision) {
@@ -751,6 +819,7 @@ static cudaError_t launch_fcf_batched_t(const BatchSolve* S, const BatchItem* it
 cudaError_t launch_fcf_batched(const BatchSolve* S, const BatchItem* items, int nitems, const DevTaps* taps,
                                int max_nx, int threads, int tile, int span, cudaStream_t s) {
   if (nitems < 1) return cudaSuccess;
+  if (tile == kChunkTile) return launch_fcf_batched_t<8, kChunked>(S, items, nitems, taps, max_nx, threads, s);
   if (tile == kFixedTile) {
     switch (span) {
       case 2: return launch_fcf_batched_t<8, 2>(S, items, nitems, taps, max_nx, threads, s);

@@ -74,9 +74,14 @@ __device__ __forceinline__ void matvec_acc(const T* M, const T (&x)[K], T (&y)[K
 }
 
 // Periodic recurrence of order K over the slab held in registers (x[c] is
-// point threadIdx.x * C + c).  tb: this direction's tables; smw: 16*K scratch.
+// point threadIdx.x * C + c).  tb: this direction's tables; smw: 16*K scratch
+// owned by this direction.  steps: warp-scan doubling steps that matter
+// (terms carrying A^(2^steps) or more lie below FP64 rounding); trunc: A^32
+// lies below rounding too, so a chunk only feels the previous warp's total
+// (periodically: warp 0 feels the last warp's) and the closure is the
+// identity.  Both are decided on the host from the norms of the powers.
 template <typename T, int C, int K, bool BWD>
-__device__ __forceinline__ void rec_scan(T (&x)[C], const T* __restrict__ tb, T* smw) {
+__device__ __forceinline__ void rec_scan(T (&x)[C], const T* __restrict__ tb, T* smw, int steps, bool trunc) {
   if constexpr (K > 0) {
     const T* lanep = tb + K;
     const T* warpp = lanep + 33 * K * K;
@@ -103,7 +108,9 @@ __device__ __forceinline__ void rec_scan(T (&x)[C], const T* __restrict__ tb, T*
     for (int q = 0; q < K; ++q) S[q] = (C - 1 - q >= 0) ? MG_XM(C - 1 - q) : (T)0;
     // 2. scan of chunk-end states over the warp ...
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
+    for (int i = 0; i < 5; ++i) {
+      if (i >= steps) break;
+      const int d = 1 << i;
       T Y[K];
 #pragma unroll
       for (int q = 0; q < K; ++q) Y[q] = shfl_prev(S[q], d, BWD);
@@ -113,40 +120,48 @@ __device__ __forceinline__ void rec_scan(T (&x)[C], const T* __restrict__ tb, T*
 #pragma unroll
       for (int q = 0; q < K; ++q) smw[warp * K + q] = S[q];
     __syncthreads();
-    // ... and over the warps (one warp, mirrored warp index = lane)
-    if (threadIdx.x < 32) {
-      const int l = threadIdx.x;
-      T W[K];
-#pragma unroll
-      for (int q = 0; q < K; ++q) W[q] = l < nw ? smw[l * K + q] : (T)0;
-#pragma unroll
-      for (int d = 1; d < 16; d <<= 1) {
-        T Y[K];
-#pragma unroll
-        for (int q = 0; q < K; ++q) Y[q] = __shfl_up_sync(0xffffffffu, W[q], d);
-        if (l >= d) matvec_acc<T, K>(warpp + d * K * K, Y, W);
-      }
-      if (l < nw)
-#pragma unroll
-        for (int q = 0; q < K; ++q) smw[l * K + q] = W[q];
-    }
-    __syncthreads();
-    // 3. periodic closure and 4. carry-in state of this chunk
-    T P[K];
+    T P[K], V[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       const T v = shfl_prev(S[q], 1, BWD);
       P[q] = lane > 0 ? v : (T)0;
     }
-    T last[K], sm1[K], V[K];
+    if (trunc) {
+      // 3'. carry from the previous warp's total (the last warp's for warp 0)
+      const int wp = warp == 0 ? nw - 1 : warp - 1;
 #pragma unroll
-    for (int q = 0; q < K; ++q) {
-      last[q] = smw[(nw - 1) * K + q];
-      sm1[q] = (T)0;
-      V[q] = warp > 0 ? smw[(warp - 1) * K + q] : (T)0;
+      for (int q = 0; q < K; ++q) V[q] = smw[wp * K + q];
+    } else {
+      // ... and over the warps (one warp, mirrored warp index = lane)
+      if (threadIdx.x < 32) {
+        const int l = threadIdx.x;
+        T W[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) W[q] = l < nw ? smw[l * K + q] : (T)0;
+#pragma unroll
+        for (int d = 1; d < 16; d <<= 1) {
+          T Y[K];
+#pragma unroll
+          for (int q = 0; q < K; ++q) Y[q] = __shfl_up_sync(0xffffffffu, W[q], d);
+          if (l >= d) matvec_acc<T, K>(warpp + d * K * K, Y, W);
+        }
+        __syncwarp();
+        if (l < nw)
+#pragma unroll
+          for (int q = 0; q < K; ++q) smw[l * K + q] = W[q];
+      }
+      __syncthreads();
+      // 3. periodic closure and 4. carry-in state of this chunk
+      T last[K], sm1[K];
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        last[q] = smw[(nw - 1) * K + q];
+        sm1[q] = (T)0;
+        V[q] = warp > 0 ? smw[(warp - 1) * K + q] : (T)0;
+      }
+      matvec_acc<T, K>(Q, last, sm1);
+      matvec_acc<T, K>(warpp + warp * K * K, sm1, V);
     }
-    matvec_acc<T, K>(Q, last, sm1);
-    matvec_acc<T, K>(warpp + warp * K * K, sm1, V);
     matvec_acc<T, K>(lanep + lane * K * K, V, P);
 #pragma unroll
     for (int cc = 0; cc < C; ++cc) {
@@ -156,7 +171,7 @@ __device__ __forceinline__ void rec_scan(T (&x)[C], const T* __restrict__ tb, T*
       MG_XM(cc) = acc;
     }
 #undef MG_XM
-    __syncthreads();  // smw is reused by the next scan
+    // smw is written again only after the caller's next __syncthreads
   }
 }
 
@@ -172,8 +187,8 @@ __device__ __forceinline__ void sdirk_step(const SdirkPlan& p, T* slab, int plen
     T x[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) x[c] = in[pix(wrapn(base + c + p.ql, nx))];
-    rec_scan<T, C, KF, false>(x, tf, smw);
-    rec_scan<T, C, KB, true>(x, tb, smw);
+    rec_scan<T, C, KF, false>(x, tf, smw, p.steps_f, p.trunc_f);
+    rec_scan<T, C, KB, true>(x, tb, smw + 16 * kMaxRec, p.steps_b, p.trunc_b);
     if constexpr (KF == 0 && KB == 0) __syncthreads();
 #pragma unroll
     for (int c = 0; c < C; ++c) {
@@ -239,22 +254,31 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const SdirkPlan& p, i
   const int nx = a.nx, m = a.m, plen = padded_len(nx);
   double* slab = sm.slab;
   const double* start = a.u_old + (long long)(j - 1) * a.cstride;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) slab[pix(i)] = a.zero_old ? 0.0 : start[i];
-  __syncthreads();
-  for (int s = 0; s < m; ++s) sdirk_step<double, C, KF, KB>(p, slab, plen, nx, sm.t64, smw);
+  int nz = 0;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const double v = a.zero_old ? 0.0 : start[i];
+    slab[pix(i)] = v;
+    nz |= v != 0.0;
+  }
+  // Phi^m of an identically zero slab is zero: the steps are skipped
+  const bool run1 = __syncthreads_or(nz);
+  for (int s = 0; s < m && run1; ++s) sdirk_step<double, C, KF, KB>(p, slab, plen, nx, sm.t64, smw);
   const double* oldj = a.u_old + (long long)j * a.cstride;
   double* cn = a.c_new + (long long)j * nx;
   const bool more = j < a.N;
   double ss = 0.0;
   if (PREC == 0) {
+    nz = 0;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       const double v = slab[pix(i)];
       cn[i] = v;
-      slab[pix(i)] = v - (a.zero_old ? 0.0 : oldj[i]);
+      const double rho = v - (a.zero_old ? 0.0 : oldj[i]);
+      slab[pix(i)] = rho;
+      nz |= rho != 0.0;
     }
-    __syncthreads();
+    const bool run2 = __syncthreads_or(nz);
     if (!more) return;
-    for (int s = 0; s < m; ++s) sdirk_step<double, C, KF, KB>(p, slab, plen, nx, sm.t64, smw);
+    for (int s = 0; s < m && run2; ++s) sdirk_step<double, C, KF, KB>(p, slab, plen, nx, sm.t64, smw);
     double* rr = a.r + (long long)(j + 1) * nx;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       const double v = slab[pix(i)];
@@ -269,15 +293,18 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const SdirkPlan& p, i
 #pragma unroll
     for (int k = 0; k < C; ++k) vals[k] = slab[pix(threadIdx.x + k * blockDim.x)];
     __syncthreads();
+    nz = 0;
 #pragma unroll
     for (int k = 0; k < C; ++k) {
       const int i = threadIdx.x + k * blockDim.x;
       cn[i] = vals[k];
-      fs[pix(i)] = (float)(vals[k] - (a.zero_old ? 0.0 : oldj[i]));
+      const float rho = (float)(vals[k] - (a.zero_old ? 0.0 : oldj[i]));
+      fs[pix(i)] = rho;
+      nz |= rho != 0.0f;
     }
-    __syncthreads();
+    const bool run2 = __syncthreads_or(nz);
     if (!more) return;
-    for (int s = 0; s < m; ++s)
+    for (int s = 0; s < m && run2; ++s)
       sdirk_step<float, C, KF, KB>(p, fs, plen, nx, sm.t32, reinterpret_cast<float*>(smw));
     double* rr = a.r + (long long)(j + 1) * nx;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
@@ -295,7 +322,7 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const SdirkPlan& p, i
 template <int PREC, int C, int KF, int KB>
 __global__ void __launch_bounds__(512) fcf_sdirk_kernel(const FcfArgs a, const SdirkPlan p) {
   extern __shared__ __align__(256) unsigned char smraw[];
-  __shared__ __align__(16) double smw[16 * kMaxRec];
+  __shared__ __align__(16) double smw[2 * 16 * kMaxRec];
   const Smem sm = carve(smraw, p);
   load_tables(p, sm);
   fcf_body<PREC, C, KF, KB>(a, p, blockIdx.x + 1, sm, smw);
@@ -306,7 +333,7 @@ template <int PREC, int C, int KF, int KB>
 __global__ void __launch_bounds__(512) fcf_sdirk_batched_kernel(const BatchSolve* __restrict__ S,
                                                                 const BatchItem* __restrict__ items) {
   extern __shared__ __align__(256) unsigned char smraw[];
-  __shared__ __align__(16) double smw[16 * kMaxRec];
+  __shared__ __align__(16) double smw[2 * 16 * kMaxRec];
   __shared__ SdirkPlan p;
   const BatchItem it = items[blockIdx.x];
   const BatchSolve& b = S[it.solve];
@@ -332,7 +359,7 @@ __global__ void __launch_bounds__(512) steps_sdirk_kernel(const double* in, long
                                                           long long out_stride, int nx, int steps, int store_every,
                                                           int store_first, const SdirkPlan p, double* partial) {
   extern __shared__ __align__(256) unsigned char smraw[];
-  __shared__ __align__(16) double smw[16 * kMaxRec];
+  __shared__ __align__(16) double smw[2 * 16 * kMaxRec];
   const Smem sm = carve(smraw, p);
   load_tables(p, sm);
   double* slab = sm.slab;

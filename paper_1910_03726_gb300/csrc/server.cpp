@@ -211,7 +211,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     b.fcf.r = h->r[1];
     b.fcf.partial = h->partial;
     b.fcf.nx = h->nx;
-    b.fcf.m = h->m;
+    b.fcf.m = h->fine_collapse ? 1 : h->m;  // collapsed: one application of Phi^m per pass
     b.fcf.N = h->Nl[1];
     b.fcf.zero_old = 0;
     b.prec = fine_prec(h);
@@ -219,7 +219,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     b.psi = 2 * k + 1;
     b.cluster = h->march_cluster;
     b.sd = h->dsplan;
-    taps[2 * k] = h->dphi;
+    taps[2 * k] = h->fine_collapse ? h->dphim : h->dphi;
     taps[2 * k + 1] = h->dpsi.back();
   }
   if (!S->dS.reserve(n) || !S->dTaps.reserve(2 * n) || !S->dIds.reserve(n) || !S->dNorm.reserve(n))
@@ -235,7 +235,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     if (h->sdirk)
       sgroups[{h->nx, h->splan.kf, h->splan.kb, hs[k].prec == 0 ? 0 : 1}].push_back(k);
     else
-      groups[{h->nx, h->fine_tile, h->fine_threads, h->dphi.span}].push_back(k);
+      groups[{h->nx, h->fine_tile, h->fine_threads, taps[2 * k].span}].push_back(k);
   }
   std::vector<BatchItem> items;
   std::vector<std::pair<size_t, size_t>> ranges, sranges;

@@ -229,6 +229,25 @@ Taps erk_phi_taps(int rk_order, int upwind_order, double c) {
   return out;
 }
 
+Taps taps_power(const Taps& t, int k) {
+  Taps out;
+  if (t.size() == 0 || k < 1) return out;
+  const int lo = t.lo(), hi = t.hi();
+  std::vector<long double> base(hi - lo + 1, 0.0L), acc(1, 1.0L);
+  for (int j = 0; j < t.size(); ++j) base[t.off[j] - lo] += t.coef[j];
+  for (int step = 0; step < k; ++step) {  // acc <- acc * base (offsets add)
+    std::vector<long double> nxt(acc.size() + base.size() - 1, 0.0L);
+    for (size_t a = 0; a < acc.size(); ++a)
+      for (size_t b = 0; b < base.size(); ++b) nxt[a + b] += acc[a] * base[b];
+    acc.swap(nxt);
+  }
+  for (size_t a = 0; a < acc.size(); ++a) {
+    out.off.push_back(k * lo + (int)a);
+    out.coef.push_back((double)acc[a]);
+  }
+  return out;
+}
+
 // Periodic application of taps to a length-nx vector.
 static std::vector<double> apply_periodic(const Taps& t, const std::vector<double>& v) {
   int nx = (int)v.size();

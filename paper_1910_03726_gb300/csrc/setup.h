@@ -43,6 +43,10 @@ void dft(std::vector<cplx>& a, bool inverse);
 // One ERK step as a single stencil (Corollary 1), from the stage form.
 Taps erk_phi_taps(int rk_order, int upwind_order, double c);
 
+// T^k as one stencil (repeated convolution of the taps, contiguous offsets
+// k*lo .. k*hi), accumulated in long double.
+Taps taps_power(const Taps& t, int k);
+
 // A fitted coarse operator and its diagnostics.
 struct CoarseOp {
   Taps taps;

@@ -224,3 +224,21 @@ def test_graph_solve_equals_host_loop(capi, L, precision):
     assert r1.iterations == r0.iterations
     np.testing.assert_allclose(r1.history[: r1.n_history], r0.history[: r0.n_history], rtol=1e-14)
     assert rel(o1, o0) <= 1e-15
+
+
+@pytest.mark.parametrize("shape", ["99,256,0", "8,256,1", "4,512,1", "0,128,0", "8,128,0", "98,256,1", "98,512,0"])
+def test_every_fine_launch_shape_matches_oracle(capi, shape, monkeypatch):
+    """Each level-1 FCF launch shape the autotuner may pick (step by step with
+    Phi or one application of the collapsed Phi^m per pass; fixed-span,
+    sliding-window or one-tap-at-a-time stencil) gives the oracle's
+    iterations and C-points."""
+    monkeypatch.setenv("MGRIT_FCF_SHAPE", shape)
+    fam, p, nx, nt, m, L = "ERK", 3, 256, 2048, 8, 3
+    c = schemes.cfl_number(fam, p)
+    u0 = workloads.fourier_field(nx)
+    it, r, U, _ = oracle_run(fam, p, c, nx, nt, m, L, "auto", u0)
+    res, out, _ = gpu_run(capi, fam, p, c, nx, nt, m, L, "auto", u0)
+    tile, th, col = (int(v) for v in shape.split(","))
+    assert (res.fine_tile, res.fine_threads, res.fine_collapsed) == (tile, th, col)
+    assert res.iterations == it
+    assert rel(out, U[::m]) <= TOL
