@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MGRIT_ABI_VERSION 2
+#define MGRIT_ABI_VERSION 3
 #define MGRIT_MAX_LEVELS 8
 #define MGRIT_MAX_HISTORY 128
 #define MGRIT_MAX_TAPS 256
@@ -86,6 +86,16 @@ enum {
 
 enum { MGRIT_OUT_FINAL = 0, MGRIT_OUT_CPOINTS = 1, MGRIT_OUT_FULL = 2 };
 
+/* Cycle below level 1 (Section 4.4, Section 5): V-cycle, or F-cycle (the
+ * coarse error equation of each level is solved by an F-cycle from zero
+ * followed by a V-cycle from its result; one exact solve on the level above
+ * the coarsest). */
+enum { MGRIT_CYCLE_V = 0, MGRIT_CYCLE_F = 1 };
+
+/* Relaxation on level 1 (Section 2.2): FCF (the paper's choice) or F only
+ * (with two levels: Parareal).  Coarse levels always use FCF. */
+enum { MGRIT_RELAX_FCF = 0, MGRIT_RELAX_F = 1 };
+
 /* MGRIT_FLAG_TIME_KERNELS: bracket every kernel launch of a solve with CUDA
  * events on the handle's stream and report per-kind device time in
  * mgrit_result.kernel_ms (adds two event records per launch). */
@@ -130,6 +140,8 @@ typedef struct mgrit_opts {
   int32_t output;        /* MGRIT_OUT_*                                            */
   int32_t min_coarse;    /* smallest admissible number of coarsest-level steps     */
   int32_t flags;         /* MGRIT_FLAG_* bits                                      */
+  int32_t cycle;         /* MGRIT_CYCLE_*                                          */
+  int32_t relax;         /* MGRIT_RELAX_*                                          */
   int32_t reserved;
   double tol;            /* stop when ||r|| <= tol ||r^(0)|| (Section 2.2)         */
   double psi_eta;        /* threshold eta_tol; <= 0 = paper's table (Section 4.6)  */
@@ -168,7 +180,8 @@ typedef struct mgrit_handle mgrit_handle;
 typedef struct mgrit_server mgrit_server;
 
 /* Fill *o with the defaults: m 8, levels 2, max_iter 100, FP64, PSI_AUTO,
- * halfwidth 3, OUT_CPOINTS, min_coarse 2, flags 0, tol 1e-10, eta <= 0,
+ * halfwidth 3, OUT_CPOINTS, min_coarse 2, flags 0, V-cycle, FCF-relaxation,
+ * tol 1e-10, eta <= 0,
  * rho 0.15. */
 void mgrit_opts_default(mgrit_opts* o);
 

@@ -1,5 +1,5 @@
-"""Two-level and multilevel FCF-MGRIT with full space-time storage (oracle;
-test infrastructure only).
+"""Two-level and multilevel MGRIT (FCF- or F-relaxation, V- or F-cycles) with
+full space-time storage (oracle; test infrastructure only).
 
 Follows Section 2.2.  On level l the time grid has N_l + 1 points; every
 m-th point is a C-point.  With operator Phi_l and right-hand side g:
@@ -81,7 +81,8 @@ def sequential_solve(U, G, step):
 
 def vcycle(levels, l, U, G):
     """One V-cycle on level l >= 1 of the error/residual equation (l >= 1 here
-    means a coarse level of the recursion; level 0 is driven by `solve`)."""
+    means a coarse level of the recursion; level 0 is driven by `solve`).
+    U is the level's current iterate (zero on the first visit)."""
     lev = levels[l]
     if lev.m is None:
         sequential_solve(U, G, lev.step)
@@ -97,9 +98,35 @@ def vcycle(levels, l, U, G):
     f_relax(U, G, lev.step, m)
 
 
-def solve(levels, U, tol=1e-10, max_iter=200, history=None, r0_norm=None):
-    """FCF-MGRIT on level 0 (g = 0, U[0] = initial condition).
+def fcycle(levels, l, U, G):
+    """One F-cycle on level l >= 1 (multigrid F-cycle, the cycle Section 4.4 and
+    Section 5 compare with V-cycles): relax, then solve the coarse error
+    equation by an F-cycle from zero followed by a V-cycle from that result
+    (one exact solve when the coarse level is the coarsest), correct, and
+    F-relax."""
+    lev = levels[l]
+    if lev.m is None:
+        sequential_solve(U, G, lev.step)
+        return
+    m = lev.m
+    f_relax(U, G, lev.step, m)
+    c_relax(U, G, lev.step, m)
+    f_relax(U, G, lev.step, m)
+    r = c_residual(U, G, lev.step, m)
+    E = np.zeros_like(r)
+    fcycle(levels, l + 1, E, r)
+    if levels[l + 1].m is not None:
+        vcycle(levels, l + 1, E, r)
+    U[m::m] += E[1:]
+    f_relax(U, G, lev.step, m)
 
+
+def solve(levels, U, tol=1e-10, max_iter=200, history=None, r0_norm=None, cycle="V", relax="FCF"):
+    """MGRIT on level 0 (g = 0, U[0] = initial condition).
+
+    cycle: "V" or "F" (the coarse error equation is solved by a V-cycle or by
+    an F-cycle, see fcycle).  relax: "FCF" (the paper's choice) or "F"
+    (F-relaxation only; with two levels this is Parareal, Section 2.2).
     U: (nt+1, nx) initial space-time iterate, modified in place.
     Returns (iterations, final relative residual).
     """
@@ -108,11 +135,13 @@ def solve(levels, U, tol=1e-10, max_iter=200, history=None, r0_norm=None):
     G = np.zeros_like(U)
     if r0_norm is None:
         r0_norm = float(np.linalg.norm(spacetime_residual(U, G, lev.step)))
+    coarse = fcycle if cycle == "F" else vcycle
     it = 0
     while True:
         f_relax(U, G, lev.step, m)
-        c_relax(U, G, lev.step, m)
-        f_relax(U, G, lev.step, m)
+        if relax == "FCF":
+            c_relax(U, G, lev.step, m)
+            f_relax(U, G, lev.step, m)
         r = c_residual(U, G, lev.step, m)
         rel = float(np.linalg.norm(r)) / r0_norm if r0_norm > 0 else 0.0
         if history is not None:
@@ -120,7 +149,7 @@ def solve(levels, U, tol=1e-10, max_iter=200, history=None, r0_norm=None):
         if rel <= tol or it >= max_iter:
             return it, rel
         E = np.zeros_like(r)
-        vcycle(levels, 1, E, r)
+        coarse(levels, 1, E, r)
         U[m::m] += E[1:]
         f_relax(U, G, lev.step, m)
         it += 1

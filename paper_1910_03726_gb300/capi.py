@@ -26,6 +26,8 @@ ERK, SDIRK = 0, 1
 PREC_FP64, PREC_MIXED, PREC_MIXED_DF = 0, 1, 2
 PSI_AUTO, PSI_HALFWIDTH, PSI_THRESHOLD, PSI_USER, PSI_IDEAL = 0, 1, 2, 3, 4
 OUT_FINAL, OUT_CPOINTS, OUT_FULL = 0, 1, 2
+CYCLE_V, CYCLE_F = 0, 1
+RELAX_FCF, RELAX_F = 0, 1
 MAX_HISTORY = 128
 MAX_LEVELS = 8
 FLAG_TIME_KERNELS = 1
@@ -49,7 +51,8 @@ class MgritProblem(C.Structure):
 class MgritOpts(C.Structure):
     _fields_ = [("m", C.c_int32), ("levels", C.c_int32), ("max_iter", C.c_int32), ("precision", C.c_int32),
                 ("psi_rule", C.c_int32), ("psi_halfwidth", C.c_int32), ("output", C.c_int32),
-                ("min_coarse", C.c_int32), ("flags", C.c_int32), ("reserved", C.c_int32), ("tol", C.c_double), ("psi_eta", C.c_double),
+                ("min_coarse", C.c_int32), ("flags", C.c_int32), ("cycle", C.c_int32), ("relax", C.c_int32),
+                ("reserved", C.c_int32), ("tol", C.c_double), ("psi_eta", C.c_double),
                 ("psi_rho", C.c_double), ("psi_user_nnz", C.POINTER(C.c_int32)),
                 ("psi_user_offsets", C.POINTER(C.c_int32)), ("psi_user_coeffs", C.POINTER(C.c_double))]
 

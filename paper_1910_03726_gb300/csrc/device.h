@@ -46,6 +46,7 @@ struct FcfArgs {
   double* r;               // r + j*nx, j = 2..N written
   double* partial;         // partial[j], j = 1..N-1 (nullptr: skip)
   int nx, m, N, zero_old;  // zero_old: u_old is identically zero
+  int relax_f;             // F-relaxation only: c_new = u_old, r_j = Phi^m c_{j-1} - c_j (j = 1..N)
 };
 
 // Sequential march u_n = T u_{n-1} + g_n, n = 1..P-1, on one thread-block

@@ -145,6 +145,8 @@ extern "C" void mgrit_opts_default(mgrit_opts* o) {
   o->output = MGRIT_OUT_CPOINTS;
   o->min_coarse = 2;
   o->flags = 0;
+  o->cycle = MGRIT_CYCLE_V;
+  o->relax = MGRIT_RELAX_FCF;
   o->tol = 1e-10;
   o->psi_eta = 0.0;
   o->psi_rho = 0.15;
@@ -196,6 +198,8 @@ mgrit_status validate_opts(const mgrit_problem* p, const mgrit_opts* o) {
     return fail(MGRIT_ERR_INVALID, "PSI_IDEAL needs ERK and two levels");
   if (o->psi_rule == MGRIT_PSI_HALFWIDTH && o->psi_halfwidth < 0)
     return fail(MGRIT_ERR_INVALID, "psi_halfwidth must be >= 0");
+  if (o->cycle != MGRIT_CYCLE_V && o->cycle != MGRIT_CYCLE_F) return fail(MGRIT_ERR_INVALID, "unknown cycle");
+  if (o->relax != MGRIT_RELAX_FCF && o->relax != MGRIT_RELAX_F) return fail(MGRIT_ERR_INVALID, "unknown relax");
   return MGRIT_OK;
 }
 
@@ -930,12 +934,85 @@ mgrit_status initial_residual(mgrit_handle* h, const double* u0dev, double* r0) 
   return MGRIT_OK;
 }
 
-// One V-cycle below level 1: levels 2..L-1 relax, level L marches, corrections
-// come back up; finally c_new += e on level 1 (or fused into the march, L = 2).
+// Cycles below level 1.  Level l (2..L-1) keeps all its points in u[l], its
+// relaxed C-points in cnew[l] and its C-point residual (level l+1's right-hand
+// side) in r[l]; level l's right-hand side is r[l-1]; the coarsest level L
+// marches into u[L].  Coarse levels relax the error equation: FP32 in the
+// mixed modes.
+namespace {
+int coarse_prec(const mgrit_handle* h) { return h->opts.precision == MGRIT_PREC_FP64 ? 0 : 2; }
+
+// FCF-relaxation of level l from zero (the first visit) or from u[l].
+mgrit_status relax_level(mgrit_handle* h, int l, bool from_zero) {
+  const int nx = h->nx, m = h->m, prec = coarse_prec(h);
+  FcfArgs f = {};
+  f.u_old = h->u[l];
+  f.cstride = (long long)m * nx;
+  f.c_new = h->cnew[l];
+  f.g = h->r[l - 1];
+  f.r = h->r[l];
+  f.partial = nullptr;
+  f.nx = nx;
+  f.m = m;
+  f.N = h->Nl[l];
+  f.zero_old = from_zero ? 1 : 0;
+  return klaunch(h, MGRIT_K_FCF_COARSE, "fcf", [&] {
+    return launch_ok(launch_fcf(f, h->dpsi[l - 2], prec, h->fcf_threads, h->stream), "fcf(coarse)");
+  });
+}
+
+// Exact solve of the coarsest level: u[L] from r[L-1].
+mgrit_status solve_coarsest(mgrit_handle* h) {
+  const int L = h->L;
+  MarchArgs a = {};
+  a.g = h->r[L - 1];
+  a.u_out = h->u[L];
+  a.store_every = 1;
+  a.nx = h->nx;
+  a.P = h->Nl[L - 1] + 1;
+  return run_march(h, a, h->dpsi[L - 2]);
+}
+
+// u[l] = relaxed C-points + u[l+1], then F-relaxation (ideal interpolation).
+mgrit_status correct_level(mgrit_handle* h, int l) {
+  const int prec = coarse_prec(h);
+  CorrectArgs c = {};
+  c.c_new = h->cnew[l];
+  c.e = h->u[l + 1];
+  c.g = h->r[l - 1];
+  c.u = h->u[l];
+  c.nx = h->nx;
+  c.m = h->m;
+  c.N = h->Nl[l];
+  return klaunch(h, MGRIT_K_CORRECT, "correct", [&] {
+    return launch_ok(launch_correct(c, h->dpsi[l - 2], h->fcf_threads, h->stream, prec == 2), "correct");
+  });
+}
+
+mgrit_status vcycle_level(mgrit_handle* h, int l, bool from_zero) {
+  if (l == h->L) return solve_coarsest(h);
+  mgrit_status st;
+  if ((st = relax_level(h, l, from_zero)) != MGRIT_OK) return st;
+  if ((st = vcycle_level(h, l + 1, true)) != MGRIT_OK) return st;
+  return correct_level(h, l);
+}
+
+// F-cycle: the coarse error equation is solved by an F-cycle from zero and
+// then a V-cycle from that result (once, exactly, above the coarsest level).
+mgrit_status fcycle_level(mgrit_handle* h, int l) {
+  if (l == h->L) return solve_coarsest(h);
+  mgrit_status st;
+  if ((st = relax_level(h, l, true)) != MGRIT_OK) return st;
+  if ((st = fcycle_level(h, l + 1)) != MGRIT_OK) return st;
+  if (l + 1 < h->L && (st = vcycle_level(h, l + 1, false)) != MGRIT_OK) return st;
+  return correct_level(h, l);
+}
+}  // namespace
+
+// One coarse-grid correction of level 1: c_new += e (e from the coarse
+// levels; fused into the march when L = 2).
 mgrit_status coarse_cycle(mgrit_handle* h, double* c_new) {
-  const int L = h->L, m = h->m, nx = h->nx;
-  // coarse levels relax the error equation: FP32 in the mixed modes
-  const int prec = h->opts.precision == MGRIT_PREC_FP64 ? 0 : 2;
+  const int L = h->L, nx = h->nx;
   mgrit_status st;
   if (L == 2) {
     MarchArgs a = {};
@@ -947,44 +1024,8 @@ mgrit_status coarse_cycle(mgrit_handle* h, double* c_new) {
     a.store_every = 1;
     return run_march(h, a, h->dpsi[0]);
   }
-  for (int l = 2; l < L; ++l) {
-    FcfArgs f = {};
-    f.u_old = h->u[l];
-    f.cstride = (long long)m * nx;
-    f.c_new = h->cnew[l];
-    f.g = h->r[l - 1];
-    f.r = h->r[l];
-    f.partial = nullptr;
-    f.nx = nx;
-    f.m = m;
-    f.N = h->Nl[l];
-    f.zero_old = 1;
-    if ((st = klaunch(h, MGRIT_K_FCF_COARSE, "fcf", [&] {
-           return launch_ok(launch_fcf(f, h->dpsi[l - 2], prec, h->fcf_threads, h->stream), "fcf(coarse)");
-         })) != MGRIT_OK)
-      return st;
-  }
-  MarchArgs a = {};
-  a.g = h->r[L - 1];
-  a.u_out = h->u[L];
-  a.store_every = 1;
-  a.nx = nx;
-  a.P = h->Nl[L - 1] + 1;
-  if ((st = run_march(h, a, h->dpsi[L - 2])) != MGRIT_OK) return st;
-  for (int l = L - 1; l >= 2; --l) {
-    CorrectArgs c = {};
-    c.c_new = h->cnew[l];
-    c.e = h->u[l + 1];
-    c.g = h->r[l - 1];
-    c.u = h->u[l];
-    c.nx = nx;
-    c.m = m;
-    c.N = h->Nl[l];
-    if ((st = klaunch(h, MGRIT_K_CORRECT, "correct", [&] {
-           return launch_ok(launch_correct(c, h->dpsi[l - 2], h->fcf_threads, h->stream, prec == 2), "correct");
-         })) != MGRIT_OK)
-      return st;
-  }
+  st = h->opts.cycle == MGRIT_CYCLE_F ? fcycle_level(h, 2) : vcycle_level(h, 2, true);
+  if (st != MGRIT_OK) return st;
   return klaunch(h, MGRIT_K_ADD, "add", [&] {
     return launch_ok(launch_add(c_new + nx, h->u[2] + nx, (long long)h->Nl[1] * nx, h->stream), "add");
   });
@@ -1084,9 +1125,11 @@ static mgrit_status graph_cycle(mgrit_handle* h, int cur, cudaGraphConditionalHa
   f.nx = nx;
   f.m = h->m;
   f.N = h->Nl[1];
+  f.relax_f = h->opts.relax == MGRIT_RELAX_F;
   mgrit_status st;
   if ((st = launch_ok(launch_fine_fcf(h, f, fine_prec(h)), "fcf")) != MGRIT_OK) return st;
-  if ((st = launch_ok(launch_norm(h->partial, h->Nl[1], h->scratch + 2 * nx, h->stream), "norm")) != MGRIT_OK)
+  if ((st = launch_ok(launch_norm(h->partial, h->Nl[1] + f.relax_f, h->scratch + 2 * nx, h->stream), "norm")) !=
+      MGRIT_OK)
     return st;
   return launch_ok(launch_check(h->scratch + 2 * nx, h->dstate, hw, hif, cur, h->stream), "check");
 }
@@ -1247,12 +1290,13 @@ extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* o
     f.m = m;
     f.N = (int)N1;
     f.zero_old = 0;
+    f.relax_f = h->opts.relax == MGRIT_RELAX_F;
     if ((st = klaunch(h, MGRIT_K_FCF, "fcf", [&] {
            return launch_ok(launch_fine_fcf(h, f, prec), "fcf");
          })) != MGRIT_OK)
       return st;
     if ((st = klaunch(h, MGRIT_K_NORM, "norm", [&] {
-           return launch_ok(launch_norm(h->partial, (int)N1, h->scratch + 2 * nx, h->stream), "norm");
+           return launch_ok(launch_norm(h->partial, (int)N1 + f.relax_f, h->scratch + 2 * nx, h->stream), "norm");
          })) != MGRIT_OK)
       return st;
     CUDA_TRY(cudaMemcpyAsync(h->norm_host, h->scratch + 2 * nx, sizeof(double), cudaMemcpyDeviceToHost, h->stream));

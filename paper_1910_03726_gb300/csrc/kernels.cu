@@ -333,6 +333,22 @@ __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const
   }
   const double* oldj = a.u_old + (long long)j * a.cstride;
   double* cn = a.c_new + (long long)j * nx;
+  if (a.relax_f) {  // F-relaxation only: the C-point keeps its value, r_j = v - c_j
+    double* rj = a.r + (long long)j * nx;
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const double old = a.zero_old ? 0.0 : oldj[i];
+      const double rho = df_to(b0[pidx(i)]) - old;
+      cn[i] = old;
+      rj[i] = rho;
+      ss = fma(rho, rho, ss);
+    }
+    if (a.partial) {
+      ss = block_sum(ss);
+      if (threadIdx.x == 0) a.partial[j] = ss;
+    }
+    return;
+  }
   float* f0 = reinterpret_cast<float*>(b1);
   float* f1 = f0 + plen;
   nz = 0;
@@ -396,6 +412,21 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
   double* cn = a.c_new + (long long)j * nx;
   const bool more = j < a.N;
   double ss = 0.0;
+  if (a.relax_f) {  // F-relaxation only: the C-point keeps its value, r_j = v - c_j
+    double* rj = a.r + (long long)j * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const double old = a.zero_old ? 0.0 : oldj[i];
+      const double rho = b0[pidx(i)] - old;
+      cn[i] = old;
+      rj[i] = rho;
+      ss = fma(rho, rho, ss);
+    }
+    if (a.partial) {
+      ss = block_sum(ss);
+      if (threadIdx.x == 0) a.partial[j] = ss;
+    }
+    return;
+  }
   if (PREC == 0) {
     nz = 0;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
@@ -637,7 +668,8 @@ __global__ void __launch_bounds__(1024) norm_batched_kernel(const BatchSolve* __
   const BatchSolve* s = S + ids[blockIdx.x];
   const double* partial = s->fcf.partial;
   double v = 0.0;
-  for (int i = threadIdx.x; i < s->fcf.N; i += blockDim.x) v += partial[i];
+  const int n = s->fcf.N + (s->fcf.relax_f ? 1 : 0);  // F-relaxation: residuals 1..N
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += partial[i];
   v = block_sum(v);
   if (threadIdx.x == 0) out[blockIdx.x] = v;
 }

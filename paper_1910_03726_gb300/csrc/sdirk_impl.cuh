@@ -267,6 +267,21 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const SdirkPlan& p, i
   double* cn = a.c_new + (long long)j * nx;
   const bool more = j < a.N;
   double ss = 0.0;
+  if (a.relax_f) {  // F-relaxation only: the C-point keeps its value, r_j = v - c_j
+    double* rj = a.r + (long long)j * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const double old = a.zero_old ? 0.0 : oldj[i];
+      const double rho = slab[pix(i)] - old;
+      cn[i] = old;
+      rj[i] = rho;
+      ss = fma(rho, rho, ss);
+    }
+    if (a.partial) {
+      ss = block_sum(ss);
+      if (threadIdx.x == 0) a.partial[j] = ss;
+    }
+    return;
+  }
   if (PREC == 0) {
     nz = 0;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {

@@ -214,6 +214,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     b.fcf.m = h->fine_collapse ? 1 : h->m;  // collapsed: one application of Phi^m per pass
     b.fcf.N = h->Nl[1];
     b.fcf.zero_old = 0;
+    b.fcf.relax_f = h->opts.relax == MGRIT_RELAX_F;
     b.prec = fine_prec(h);
     b.taps = 2 * k;
     b.psi = 2 * k + 1;

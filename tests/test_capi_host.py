@@ -30,7 +30,7 @@ def test_exports_every_declared_entry_point(capi):
     assert "mgrit_setup" in names and "mgrit_poll" in names
     missing = [n for n in names if not hasattr(capi._lib, n)]
     assert not missing, missing
-    assert capi.mgrit_abi_version() == 2
+    assert capi.mgrit_abi_version() == 3
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4, 5])

@@ -30,7 +30,7 @@ def rel(a, b):
 RULE = {"halfwidth": 1, "auto": 0, "threshold": 2, "ideal": 4}
 
 
-def oracle_run(fam, p, c, nx, nt, m, L, rule, u0, tol=1e-10, psi_ops=None):
+def oracle_run(fam, p, c, nx, nt, m, L, rule, u0, tol=1e-10, psi_ops=None, cycle="V", relax="FCF"):
     st = stepping.FineStep(fam, p, c, nx)
     if psi_ops is None:
         ops = [o.diag for o in opsi.build_hierarchy(fam, p, c, nx, nt, m, L, rule=rule, halfwidth=3)]
@@ -39,13 +39,15 @@ def oracle_run(fam, p, c, nx, nt, m, L, rule, u0, tol=1e-10, psi_ops=None):
     lev = omg.make_levels(st, m, ops)
     U = omg.zero_iterate(u0, nt)
     hist = []
-    it, r = omg.solve(lev, U, tol=tol, history=hist)
+    it, r = omg.solve(lev, U, tol=tol, history=hist, cycle=cycle, relax=relax)
     return it, r, U, hist
 
 
-def gpu_run(capi, fam, p, c, nx, nt, m, L, rule, u0, precision=0, output=1, tol=1e-10, user=None):
+def gpu_run(capi, fam, p, c, nx, nt, m, L, rule, u0, precision=0, output=1, tol=1e-10, user=None, cycle="V",
+            relax="FCF", flags=0):
     opts = capi.mgrit_opts_default(m=m, levels=L, psi_rule=RULE[rule], psi_halfwidth=3, precision=precision,
-                                   output=output, tol=tol)
+                                   output=output, tol=tol, cycle=0 if cycle == "V" else 1,
+                                   relax=0 if relax == "FCF" else 1, flags=flags)
     keep = capi.user_psi(opts, user) if user is not None else None
     h = capi.mgrit_setup(capi.problem(nx, nt, fam, p, p, c), opts)
     try:
@@ -242,3 +244,46 @@ def test_every_fine_launch_shape_matches_oracle(capi, shape, monkeypatch):
     assert (res.fine_tile, res.fine_threads, res.fine_collapsed) == (tile, th, col)
     assert res.iterations == it
     assert rel(out, U[::m]) <= TOL
+
+
+@pytest.mark.parametrize("case", [("ERK", 1, 64, 1024, 2, 6), ("ERK", 3, 128, 2048, 4, 4), ("ERK", 5, 128, 1024, 4, 3)])
+@pytest.mark.parametrize("flags", [0, 4])
+def test_fcycle_parity(capi, case, flags):
+    """F-cycles (graph and host-driven loop): the oracle's iterations and
+    C-points; on ERK1 m = 2, six levels, fewer iterations than V-cycles."""
+    fam, p, nx, nt, m, L = case
+    c = schemes.cfl_number(fam, p)
+    u0 = workloads.fourier_field(nx)
+    it, r, U, _ = oracle_run(fam, p, c, nx, nt, m, L, "auto", u0, cycle="F")
+    res, out, _ = gpu_run(capi, fam, p, c, nx, nt, m, L, "auto", u0, cycle="F", flags=flags)
+    assert res.iterations == it
+    assert rel(out, U[::m]) <= TOL
+    if L == 6:
+        itv = gpu_run(capi, fam, p, c, nx, nt, m, L, "auto", u0, flags=flags)[0].iterations
+        assert res.iterations < itv
+
+
+@pytest.mark.parametrize("case", [("ERK", 3, 256, 2048, 8, 2), ("ERK", 1, 128, 1024, 4, 3), ("ERK", 4, 128, 512, 4, 2)])
+@pytest.mark.parametrize("flags", [0, 4])
+def test_f_relaxation_parity(capi, case, flags):
+    """F-relaxation only on level 1 (two levels: Parareal): the oracle's
+    iterations and C-points."""
+    fam, p, nx, nt, m, L = case
+    c = schemes.cfl_number(fam, p)
+    u0 = workloads.fourier_field(nx)
+    it, r, U, _ = oracle_run(fam, p, c, nx, nt, m, L, "auto", u0, relax="F")
+    res, out, _ = gpu_run(capi, fam, p, c, nx, nt, m, L, "auto", u0, relax="F", flags=flags)
+    assert res.iterations == it
+    assert rel(out, U[::m]) <= TOL
+
+
+def test_f_relaxation_mixed_reaches_the_fp64_fixed_point(capi):
+    fam, p, nx, nt, m, L = "ERK", 3, 256, 2048, 8, 2
+    c = schemes.cfl_number(fam, p)
+    u0 = workloads.fourier_field(nx)
+    ref = stepping.sequential(stepping.FineStep(fam, p, c, nx), u0, nt)
+    it64 = gpu_run(capi, fam, p, c, nx, nt, m, L, "auto", u0, relax="F")[0].iterations
+    for prec in (1, 2):
+        res, out, _ = gpu_run(capi, fam, p, c, nx, nt, m, L, "auto", u0, precision=prec, relax="F")
+        assert res.converged == 1 and abs(res.iterations - it64) <= 1
+        assert rel(out, ref[::m]) <= 1e-9

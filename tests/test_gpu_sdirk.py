@@ -49,12 +49,12 @@ def test_sdirk_steps_match_oracle(capi, p, q, nx):
     assert rel(yout.cpu().numpy(), ref) <= TOL
 
 
-def _oracle(p, nx, nt, m, L, u0):
+def _oracle(p, nx, nt, m, L, u0, cycle="V", relax="FCF"):
     st = stepping.FineStep("SDIRK", p, 4.0, nx)
     ops = opsi.build_hierarchy("SDIRK", p, 4.0, nx, nt, m, L, rule="threshold")
     lev = omg.make_levels(st, m, [o.diag for o in ops])
     U = omg.zero_iterate(u0, nt)
-    it, r = omg.solve(lev, U, tol=1e-10)
+    it, r = omg.solve(lev, U, tol=1e-10, cycle=cycle, relax=relax)
     return it, U
 
 
@@ -123,3 +123,20 @@ def test_sdirk_in_the_server_mix(capi):
             assert float(np.max(np.abs(out - a))) <= 1e-14 * float(np.max(np.abs(a)))
     finally:
         capi.mgrit_server_destroy(srv)
+
+
+@pytest.mark.parametrize("p,nx,nt,m,L,cycle,relax", [(3, 256, 512, 16, 2, "V", "F"), (2, 128, 1024, 4, 3, "F", "FCF"),
+                                                     (1, 128, 512, 4, 3, "F", "F")])
+def test_sdirk_fcycle_and_f_relaxation_parity(capi, p, nx, nt, m, L, cycle, relax):
+    u0 = workloads.wave_packet(nx)
+    it, U = _oracle(p, nx, nt, m, L, u0, cycle, relax)
+    opts = capi.mgrit_opts_default(m=m, levels=L, psi_rule=capi.PSI_THRESHOLD, cycle=0 if cycle == "V" else 1,
+                                   relax=0 if relax == "FCF" else 1)
+    h = capi.mgrit_setup(capi.problem(nx, nt, "SDIRK", p, p, 4.0), opts)
+    try:
+        out = np.zeros((nt // m + 1, nx))
+        res, _ = capi.mgrit_solve(h, u0, out)
+    finally:
+        capi.mgrit_destroy(h)
+    assert res.iterations == it
+    assert rel(out, U[::m]) <= TOL

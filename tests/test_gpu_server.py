@@ -121,3 +121,22 @@ def test_failures_are_per_request(capi):
         assert st == -4 and res.iterations == 0
     finally:
         capi.mgrit_server_destroy(srv)
+
+
+def test_fcycle_and_f_relaxation_requests_equal_alone(capi):
+    specs = []
+    for (p, nx, nt, m, L, prec), cyc, rlx in [((1, 64, 1024, 2, 6, 0), 1, 0), ((3, 256, 2048, 8, 2, 1), 0, 1),
+                                              ((3, 128, 2048, 4, 4, 1), 1, 1)]:
+        prob, opts, u0 = _spec(capi, p, nx, nt, m, L, prec)
+        opts.cycle, opts.relax = cyc, rlx
+        specs.append((prob, opts, u0))
+    alone = [_alone(capi, *sp) for sp in specs]
+    srv = capi.mgrit_server_create(4e9)
+    try:
+        tickets = [capi.mgrit_submit(srv, *sp) for sp in specs]
+        for (prob, opts, u0), t, (ares, aout) in zip(specs, tickets, alone):
+            st, res, out = _wait(capi, srv, t, prob.nt // opts.m + 1, prob.nx)
+            assert st == 0 and res.iterations == ares.iterations
+            assert float(np.max(np.abs(out - aout)) / np.max(np.abs(aout))) <= 1e-14
+    finally:
+        capi.mgrit_server_destroy(srv)

@@ -151,3 +151,137 @@ def test_table6_all_within_one():
         U = workloads.random_iterate(nt, nx, workloads.sin4(nx), 1)
         it, rel = mgrit.solve(lev, U)
         assert abs(it - v) <= 1, (key, it, v)
+
+
+# --------------------------------------------------------------- F-relaxation
+def test_f_relaxation_exactness_and_termination():
+    """F-relaxation only (Parareal with two levels, Section 2.2): whatever Psi
+    is, after k iterations C-points 0..k equal the sequential solution (F-
+    relaxation carries exactness one interval per iteration, FCF two), and
+    the solve ends after N_c iterations."""
+    nx, m, nc = 16, 4, 12
+    nt = m * nc
+    st = stepping.FineStep("ERK", 1, 0.85, nx)
+    rng = np.random.default_rng(5)
+    diag = {i: float(rng.standard_normal()) * 0.3 for i in range(-3, 2)}
+    lev = mgrit.make_levels(st, m, [diag])
+    u0 = workloads.sin4(nx)
+    ref = stepping.sequential(st, u0, nt)
+    U = workloads.random_iterate(nt, nx, u0, 13)
+    G = np.zeros_like(U)
+    for k in range(1, nc + 1):
+        mgrit.f_relax(U, G, st, m)
+        r = mgrit.c_residual(U, G, st, m)
+        E = np.zeros_like(r)
+        mgrit.vcycle(lev, 1, E, r)
+        U[m::m] += E[1:]
+        mgrit.f_relax(U, G, st, m)
+        upto = k * m
+        assert np.max(np.abs(U[: upto + 1] - ref[: upto + 1])) < 1e-12, k
+        if k < nc:  # the next C-point is not exact yet (generic Psi)
+            assert np.max(np.abs(U[upto + m] - ref[upto + m])) > 1e-8, k
+    U = workloads.random_iterate(nt, nx, u0, 13)
+    it, rel = mgrit.solve(lev, U, tol=1e-12, max_iter=50, relax="F")
+    assert it == nc
+
+
+def test_f_relaxation_with_ideal_psi_is_one_iteration_and_fcf_is_faster():
+    nx, nt, m = 32, 256, 4
+    c = schemes.cfl_number("ERK", 3)
+    st = stepping.FineStep("ERK", 3, c, nx)
+    ideal = psi.build_hierarchy("ERK", 3, c, nx, nt, m, 2, rule="ideal")[0].diag
+    U = workloads.random_iterate(nt, nx, workloads.sin4(nx), 7)
+    it, rel = mgrit.solve(mgrit.make_levels(st, m, [ideal]), U, tol=1e-12, relax="F")
+    assert it == 1 and rel < 1e-12
+    ops = psi.build_hierarchy("ERK", 3, c, nx, nt, m, 2, rule="auto")
+    lev = mgrit.make_levels(st, m, [ops[0].diag])
+    its = {}
+    for relax in ("F", "FCF"):
+        U = workloads.random_iterate(nt, nx, workloads.sin4(nx), 7)
+        its[relax], rel = mgrit.solve(lev, U, tol=1e-10, relax=relax)
+        assert rel <= 1e-10
+        ref = stepping.sequential(st, workloads.sin4(nx), nt)
+        assert np.linalg.norm(U - ref) / np.linalg.norm(ref) < 1e-8
+    assert its["FCF"] < its["F"]
+
+
+# -------------------------------------------------------------------- F-cycles
+def test_fcycle_two_levels_is_the_vcycle():
+    nx, nt, m = 32, 256, 8
+    c = schemes.cfl_number("ERK", 3)
+    st = stepping.FineStep("ERK", 3, c, nx)
+    ops = psi.build_hierarchy("ERK", 3, c, nx, nt, m, 2, rule="auto")
+    lev = mgrit.make_levels(st, m, [ops[0].diag])
+    out = []
+    for cyc in ("V", "F"):
+        U = workloads.random_iterate(nt, nx, workloads.sin4(nx), 2)
+        hist = []
+        it, _ = mgrit.solve(lev, U, history=hist, cycle=cyc)
+        out.append((it, hist, U))
+    assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
+    assert np.array_equal(out[0][2], out[1][2])
+
+
+def test_fcycle_with_exact_coarse_operators_is_one_iteration():
+    """Psi_l = (Psi_{l-1})^m on every level (Psi_1 = Phi): every coarse
+    problem is the exact Schur complement, so one F-cycle (or V-cycle)
+    solves the system."""
+    nx, nt, m, L = 24, 128, 2, 4
+    c = schemes.cfl_number("ERK", 2)
+    st = stepping.FineStep("ERK", 2, c, nx)
+    ops, prev = [], st
+    for _ in range(L - 1):
+        def power(v, f=prev, k=m):
+            for _ in range(k):
+                v = f(v)
+            return v
+        ops.append(power)
+        prev = power
+    lev = mgrit.make_levels(st, m, ops)
+    for cyc in ("V", "F"):
+        U = workloads.random_iterate(nt, nx, workloads.sin4(nx), 4)
+        it, rel = mgrit.solve(lev, U, tol=1e-11, cycle=cyc)
+        assert it == 1 and rel < 1e-11, cyc
+
+
+def test_fcycle_keeps_fcf_exactness():
+    """FCF exactness (C-points 0..2k after k iterations) does not depend on the
+    cycle; the F-cycle converges to sequential stepping."""
+    nx, nt, m, L = 64, 1024, 4, 4
+    c = schemes.cfl_number("ERK", 3)
+    st = stepping.FineStep("ERK", 3, c, nx)
+    ops = psi.build_hierarchy("ERK", 3, c, nx, nt, m, L, rule="auto")
+    lev = mgrit.make_levels(st, m, [o.diag for o in ops])
+    u0 = workloads.fourier_field(nx)
+    ref = stepping.sequential(st, u0, nt)
+    U = mgrit.zero_iterate(u0, nt)
+    G = np.zeros_like(U)
+    for k in range(1, 4):
+        mgrit.f_relax(U, G, st, m); mgrit.c_relax(U, G, st, m); mgrit.f_relax(U, G, st, m)
+        r = mgrit.c_residual(U, G, st, m)
+        E = np.zeros_like(r)
+        mgrit.fcycle(lev, 1, E, r)
+        U[m::m] += E[1:]
+        mgrit.f_relax(U, G, st, m)
+        upto = 2 * k * m
+        assert np.max(np.abs(U[: upto + 1] - ref[: upto + 1])) < 1e-12, k
+    U = mgrit.zero_iterate(u0, nt)
+    it, rel = mgrit.solve(lev, U, cycle="F")
+    assert rel <= 1e-10
+    assert np.linalg.norm(U - ref) / np.linalg.norm(ref) < 1e-8
+
+
+def test_fcycle_needs_fewer_iterations_than_vcycle():
+    """Section 5: F-cycles converge in fewer iterations than V-cycles (at more
+    work per iteration).  ERK1+U1, 64 x 1024, m = 2, six levels: 7 against 9."""
+    nx, nt, m, L = 64, 1024, 2, 6
+    c = schemes.cfl_number("ERK", 1)
+    st = stepping.FineStep("ERK", 1, c, nx)
+    ops = psi.build_hierarchy("ERK", 1, c, nx, nt, m, L, rule="auto")
+    lev = mgrit.make_levels(st, m, [o.diag for o in ops])
+    its = {}
+    for cyc in ("V", "F"):
+        U = mgrit.zero_iterate(workloads.fourier_field(nx), nt)
+        its[cyc], rel = mgrit.solve(lev, U, cycle=cyc)
+        assert rel <= 1e-10
+    assert its["F"] < its["V"]
