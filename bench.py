@@ -282,6 +282,45 @@ def sdirk_variant(capi, stream, K, flags=0):
     return res
 
 
+TABLE4_MAX = {1: (16384, 7, (6, 7, 7, 7, 7, 7)), 3: (8192, 6, (6, 7, 7, 8, 8)), 5: (8192, 6, (3, 4, 5, 5, 5))}
+
+
+def paper_parallel_variant(capi, stream):
+    """The paper's parallel runs (Section 5): ERKp+Up, p = 1, 3, 5, on
+    2^12 x (2^14, 2^13, 2^13) with V-cycles, m = 4 and the most levels of
+    Table 4 (7, 6, 6); MIXED and FP64 against GPU sequential stepping (the
+    paper's speed-up metric), iterations beside Table 4's (random initial
+    iterate there, zero here)."""
+    import torch
+    out = {}
+    for p, (nt, L, t4) in TABLE4_MAX.items():
+        nx = 4096
+        prob = capi.problem(nx, nt, "ERK", p, p, 0.85 * CMAX_TABLE1[p])
+        u0 = torch.tensor(workloads.fourier_field(nx), device="cuda")
+        row = {"nx": nx, "nt": nt, "levels": L, "m": 4, "table4_iterations": t4[L - 2]}
+        for name, prec in (("mixed", capi.PREC_MIXED), ("fp64", capi.PREC_FP64)):
+            o = capi.mgrit_opts_default(m=4, levels=L, precision=prec, tol=TOL, output=capi.OUT_FINAL, max_iter=50,
+                                        min_coarse=4)
+            h = capi.mgrit_setup(prob, o, stream=stream)
+            try:
+                capi.mgrit_solve(h, u0, None)
+                ts = []
+                for _ in range(3):
+                    r, _ = capi.mgrit_solve(h, u0, None)
+                    ts.append(r.solve_s)
+                row[name] = {"ms": 1e3 * statistics.median(ts), "dof_per_s": nx * nt / statistics.median(ts),
+                             "iterations": r.iterations, "op_complexity": r.op_complexity}
+                if name == "fp64":
+                    fin = torch.empty(nx, dtype=torch.float64, device="cuda")
+                    sq = capi.mgrit_sequential(h, u0, fin)
+                    row["gpu_sequential_ms"] = 1e3 * sq
+            finally:
+                capi.mgrit_destroy(h)
+        row["speedup_vs_gpu_sequential"] = row["gpu_sequential_ms"] / row["mixed"]["ms"]
+        out[f"ERK{p}+U{p}"] = row
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -334,9 +373,9 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
     prob = capi.problem(NX, NT, "ERK", P, P, CFL)
 
-    def make(levels, m, precision, flags=0):
+    def make(levels, m, precision, flags=0, cycle=0, relax=0):
         o = capi.mgrit_opts_default(m=m, levels=levels, precision=precision, tol=TOL, output=capi.OUT_CPOINTS,
-                                    flags=flags, max_iter=50)
+                                    flags=flags, max_iter=100, cycle=cycle, relax=relax)
         return capi.mgrit_setup(prob, o, stream=sp)
 
     def timed_solves(h, K, W, collect=False):
@@ -416,11 +455,15 @@ def main():
                                              "ms": p_total / args.steps}
     if not args.no_variants:
         ks = max(3, args.steps // 2)
-        for name, (lv, m, prec) in {"mixed_df_vcycle_L4_m8": (4, 8, capi.PREC_MIXED_DF),
-                                    "fp64_vcycle_L4_m8": (4, 8, capi.PREC_FP64),
-                                    "mixed_two_level_m8": (2, 8, capi.PREC_MIXED),
-                                    "fp64_two_level_m8": (2, 8, capi.PREC_FP64)}.items():
-            hv = make(lv, m, prec)
+        for name, (lv, m, prec, cyc, rlx) in {
+                "mixed_df_vcycle_L4_m8": (4, 8, capi.PREC_MIXED_DF, 0, 0),
+                "fp64_vcycle_L4_m8": (4, 8, capi.PREC_FP64, 0, 0),
+                "mixed_fcycle_L4_m8": (4, 8, capi.PREC_MIXED, 1, 0),
+                "mixed_two_level_m8": (2, 8, capi.PREC_MIXED, 0, 0),
+                "fp64_two_level_m8": (2, 8, capi.PREC_FP64, 0, 0),
+                "mixed_parareal_two_level_m8": (2, 8, capi.PREC_MIXED, 0, 1),
+                "mixed_f_relax_vcycle_L4_m8": (4, 8, capi.PREC_MIXED, 0, 1)}.items():
+            hv = make(lv, m, prec, cycle=cyc, relax=rlx)
             lv_lat, lv_total, lv_res = timed_solves(hv, ks, 1)
             extra[name] = {"dof_per_s": NX * NT * ks / (lv_total * 1e-3), "ms": lv_total / ks,
                            "iterations": lv_res[-1].iterations, "rel_residual": lv_res[-1].rel_residual}
@@ -448,6 +491,7 @@ def main():
         extra["rel_l2_vs_fp64_sequential"] = err
         capi.mgrit_destroy(hs)
         extra["sdirk3_u5_8192"] = sdirk_variant(capi, sp, 3)
+        extra["paper_parallel_configs"] = paper_parallel_variant(capi, sp)
         if args.batch > 0:
             extra["batch_uneven"] = batch_variant(capi, args.batch, sp)
         if args.serve > 0:

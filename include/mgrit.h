@@ -222,6 +222,16 @@ mgrit_status mgrit_setup(const mgrit_problem* prob, const mgrit_opts* opts, void
  * out may be NULL.  res may be NULL. */
 mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* out, mgrit_result* res);
 
+/* As mgrit_solve, from a given initial iterate (a warm start, or the
+ * paper's random initial iterate of Section 2.2): c_init holds its C-points,
+ * (nt/m + 1) * nx values (host or device), row 0 = the initial condition.
+ * F-relaxation recomputes the F-points, so only the C-points enter the
+ * iteration.  r0_norm > 0 is the norm the relative tolerance refers to (the
+ * space-time residual norm of the initial iterate, F-points included, which
+ * the caller knows); r0_norm <= 0 uses ||Phi u0||, the zero iterate's. */
+mgrit_status mgrit_solve_from(mgrit_handle* h, const double* c_init, double r0_norm, double* out,
+                              mgrit_result* res);
+
 /* Plain sequential time stepping u^{n+1} = Phi u^n on the GPU (FP64), the
  * baseline of Section 5; out as for mgrit_solve.  seconds may be NULL. */
 mgrit_status mgrit_sequential(mgrit_handle* h, const double* u0, double* out, double* seconds);

@@ -1179,20 +1179,35 @@ static mgrit_status build_solve_graph(mgrit_handle* h) {
 }
 
 // Whole solve: prologue on the stream, one graph launch, one read-back.
-static mgrit_status solve_graph(mgrit_handle* h, const double* u0, double* out, mgrit_result* R) {
+// Initial iterate on the device: C-points from c_init (rows 0..N1) or zero
+// (row 0 = u0).
+static mgrit_status load_iterate(mgrit_handle* h, const double* u0, const double* c_init) {
   const int nx = h->nx;
   const size_t N1 = h->Nl[1];
   const size_t slab = (size_t)nx * sizeof(double);
-  CUDA_TRY(cudaMemcpyAsync(h->c[0], u0, slab, kind_to_dev(u0), h->stream));
+  if (c_init) {
+    CUDA_TRY(cudaMemcpyAsync(h->c[0], c_init, (N1 + 1) * slab, kind_to_dev(c_init), h->stream));
+  } else {
+    CUDA_TRY(cudaMemcpyAsync(h->c[0], u0, slab, kind_to_dev(u0), h->stream));
+    CUDA_TRY(cudaMemsetAsync(h->c[0] + nx, 0, N1 * slab, h->stream));
+  }
   CUDA_TRY(cudaMemcpyAsync(h->c[1], h->c[0], slab, cudaMemcpyDeviceToDevice, h->stream));
-  CUDA_TRY(cudaMemsetAsync(h->c[0] + nx, 0, N1 * slab, h->stream));
+  return MGRIT_OK;
+}
+
+static mgrit_status solve_graph(mgrit_handle* h, const double* u0, const double* c_init, double r0_norm,
+                                double* out, mgrit_result* R) {
+  const int nx = h->nx;
+  mgrit_status st;
+  if ((st = load_iterate(h, u0, c_init)) != MGRIT_OK) return st;
   std::memset(h->hstate, 0, sizeof(CheckState));
   h->hstate->tol = h->opts.tol;
   h->hstate->max_iter = h->opts.max_iter;
+  h->hstate->r0sq = r0_norm > 0.0 ? r0_norm * r0_norm : 0.0;
   CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(CheckState), cudaMemcpyHostToDevice, h->stream));
-  // ||Phi u0||^2 straight into the state (zero initial iterate: r^(0) = Phi u0)
-  mgrit_status st;
-  if ((st = launch_ok(h->sdirk ? launch_propagate_sdirk(h->c[0], h->scratch, 1, nx, 1, h->splan, &h->dstate->r0sq,
+  // otherwise ||Phi u0||^2 straight into the state (zero initial iterate: r^(0) = Phi u0)
+  if (!(r0_norm > 0.0) &&
+      (st = launch_ok(h->sdirk ? launch_propagate_sdirk(h->c[0], h->scratch, 1, nx, 1, h->splan, &h->dstate->r0sq,
                                                         h->stream)
                                : launch_propagate(h->c[0], h->scratch, 1, nx, 1, h->dphi, &h->dstate->r0sq,
                                                   h->fcf_threads, h->stream),
@@ -1210,7 +1225,7 @@ static mgrit_status solve_graph(mgrit_handle* h, const double* u0, double* out, 
   R->converged = S.status == 0 && S.done ? 1 : 0;
   // launches: initial residual, (it+1) x (fcf, norm, check), it x coarse correction
   reset_stats(h);
-  h->kcount[MGRIT_K_PROPAGATE] = 1;
+  h->kcount[MGRIT_K_PROPAGATE] = r0_norm > 0.0 ? 0 : 1;
   h->kcount[MGRIT_K_FCF] = S.it + 1;
   h->kcount[MGRIT_K_NORM] = S.it + 1;
   h->kcount[MGRIT_K_OTHER] = S.it + 1;
@@ -1223,9 +1238,8 @@ static mgrit_status solve_graph(mgrit_handle* h, const double* u0, double* out, 
   return MGRIT_OK;
 }
 
-extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* out, mgrit_result* res) {
-  if (!h) return fail(MGRIT_ERR_INVALID, "handle is NULL");
-  if (!u0) return fail(MGRIT_ERR_INVALID, "u0 is NULL");
+static mgrit_status solve_impl(mgrit_handle* h, const double* u0, const double* c_init, double r0_norm,
+                               double* out, mgrit_result* res) {
   const double t0 = now_s();
   const int nx = h->nx, m = h->m;
   const size_t N1 = h->Nl[1];
@@ -1253,7 +1267,7 @@ extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* o
       }
     }
     if (h->gexec) {
-      mgrit_status gs = solve_graph(h, u0, out, &R);
+      mgrit_status gs = solve_graph(h, u0, c_init, r0_norm, out, &R);
       if (gs == MGRIT_OK || gs == MGRIT_ERR_NOT_CONVERGED || gs == MGRIT_ERR_DIVERGED) {
         CUDA_TRY(cudaStreamSynchronize(h->stream));
         R.solve_s = now_s() - t0;
@@ -1268,12 +1282,10 @@ extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* o
     }
   }
   int cur = 0;
-  CUDA_TRY(cudaMemcpyAsync(h->c[0], u0, slab, kind_to_dev(u0), h->stream));
-  CUDA_TRY(cudaMemcpyAsync(h->c[1], h->c[0], slab, cudaMemcpyDeviceToDevice, h->stream));
-  CUDA_TRY(cudaMemsetAsync(h->c[0] + nx, 0, N1 * slab, h->stream));
-  double r0 = 0.0;
-  mgrit_status st = initial_residual(h, h->c[0], &r0);
+  mgrit_status st = load_iterate(h, u0, c_init);
   if (st != MGRIT_OK) return st;
+  double r0 = r0_norm;
+  if (!(r0_norm > 0.0) && (st = initial_residual(h, h->c[0], &r0)) != MGRIT_OK) return st;
   R.r0_norm = r0;
   const int prec = fine_prec(h);
   mgrit_status final_status = MGRIT_OK;
@@ -1329,6 +1341,20 @@ extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* o
   R.dof_per_s = R.solve_s > 0 ? (double)nx * h->nt / R.solve_s : 0.0;
   if (res) *res = R;
   return final_status;
+}
+
+extern "C" mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* out, mgrit_result* res) {
+  if (!h) return fail(MGRIT_ERR_INVALID, "handle is NULL");
+  if (!u0) return fail(MGRIT_ERR_INVALID, "u0 is NULL");
+  return solve_impl(h, u0, nullptr, 0.0, out, res);
+}
+
+extern "C" mgrit_status mgrit_solve_from(mgrit_handle* h, const double* c_init, double r0_norm, double* out,
+                                         mgrit_result* res) {
+  if (!h) return fail(MGRIT_ERR_INVALID, "handle is NULL");
+  if (!c_init) return fail(MGRIT_ERR_INVALID, "c_init is NULL");
+  if (!std::isfinite(r0_norm)) return fail(MGRIT_ERR_INVALID, "r0_norm must be finite");
+  return solve_impl(h, c_init, c_init, r0_norm, out, res);
 }
 
 extern "C" mgrit_status mgrit_sequential(mgrit_handle* h, const double* u0, double* out, double* seconds) {
