@@ -47,6 +47,12 @@ struct FcfArgs {
   double* partial;         // partial[j], j = 1..N-1 (nullptr: skip)
   int nx, m, N, zero_old;  // zero_old: u_old is identically zero
   int relax_f;             // F-relaxation only: c_new = u_old, r_j = Phi^m c_{j-1} - c_j (j = 1..N)
+  // FP32 storage (mixed modes): r_f replaces r (any precision); on an FP32
+  // coarse level (precision 2) u_old_f, c_new_f, g_f and r_f replace all four.
+  const float* u_old_f;
+  float* c_new_f;
+  const float* g_f;
+  float* r_f;
 };
 
 // Sequential march u_n = T u_{n-1} + g_n, n = 1..P-1, on one thread-block
@@ -58,6 +64,8 @@ struct MarchArgs {
   int store_every;
   double* c_add;           // c_add + n*nx += u_n for n >= 1 (nullptr: none)
   int nx, P;
+  const float* g_f;        // FP32 right-hand side (replaces g when set)
+  float* u_out_f;          // FP32 output (replaces u_out when set)
 };
 
 // Correction and F-relaxation (ideal interpolation) of one level:
@@ -70,6 +78,11 @@ struct CorrectArgs {
   const double* g;         // point n at g + n*nx (nullptr: none)
   double* u;               // all points of the level, point n at u + n*nx
   int nx, m, N;
+  // FP32 storage (an FP32 coarse level): used by the FP32 kernel instead
+  const float* c_new_f;
+  const float* e_f;
+  const float* g_f;
+  float* u_f;
 };
 
 // tile: register tile (0, 4 or 8), kFixedTile for the fixed-span path of the
@@ -184,6 +197,7 @@ cudaError_t launch_march(const MarchArgs& a, const DevTaps& t, int cluster, int 
 cudaError_t launch_correct(const CorrectArgs& a, const DevTaps& t, int threads, cudaStream_t s, int fp32 = 0);
 cudaError_t launch_norm(const double* partial, int n, double* out, cudaStream_t s);
 cudaError_t launch_add(double* c, const double* e, long long count, cudaStream_t s);
+cudaError_t launch_add_f(double* c, const float* e, long long count, cudaStream_t s);
 cudaError_t launch_propagate(const double* in, double* out, int count, int nx, int k,
                              const DevTaps& t, double* partial, int threads, cudaStream_t s);
 int march_max_cluster();

@@ -605,6 +605,7 @@ void autotune_fine(mgrit_handle* h) {
   f.cstride = nx;
   f.c_new = h->c[1];
   f.r = h->r[1];
+  f.r_f = h->rf[1];
   f.partial = h->partial;
   f.nx = nx;
   f.N = std::min(h->Nl[1], 4096);  // the real interval count: wave quantisation matters
@@ -671,11 +672,15 @@ size_t handle_bytes(const mgrit_problem* prob, const mgrit_opts* opts) {
   std::vector<size_t> N(L + 1, 0);
   N[1] = prob->nt / m;
   for (size_t l = 2; l < L; ++l) N[l] = N[l - 1] / m;
-  size_t d = 3 * (N[1] + 1) * nx + (N[1] + 1) + 2 * nx + 8;
+  // doubles: two C-point arrays, partials, scratch; the residual and coarse
+  // arrays take half as many in the mixed modes (FP32)
+  const bool f32 = opts->precision != MGRIT_PREC_FP64;
+  auto arr = [&](size_t count) { return f32 ? (count + 1) / 2 : count; };
+  size_t d = 2 * (N[1] + 1) * nx + arr((N[1] + 1) * nx) + (N[1] + 1) + 2 * nx + 8;
   for (size_t l = 2; l <= L; ++l) {
     const size_t P = N[l - 1] + 1;
-    if (l < L || L > 2) d += P * nx;
-    if (l < L) d += 2 * (N[l] + 1) * nx;
+    if (l < L || L > 2) d += arr(P * nx);
+    if (l < L) d += 2 * arr((N[l] + 1) * nx);
   }
   if (prob->family == MGRIT_SDIRK) d += 4096;  // recurrence tables and the device plan
   return d * sizeof(double);
@@ -760,28 +765,53 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
   h->r.assign(L + 1, nullptr);
   h->u.assign(L + 1, nullptr);
   h->cnew.assign(L + 1, nullptr);
+  h->rf.assign(L + 1, nullptr);
+  h->uf.assign(L + 1, nullptr);
+  h->cnewf.assign(L + 1, nullptr);
+  h->f32c = opts->precision != MGRIT_PREC_FP64;
   const size_t N1 = h->Nl[1];
   auto A = [&](size_t count, double** p) { return dalloc(h, count, p); };
+  // an array of `count` values, FP32 in the mixed modes, zero-filled
+  auto AZ = [&](size_t count, double** pd, float** pf) -> mgrit_status {
+    mgrit_status s2;
+    if (h->f32c) {
+      double* d = nullptr;
+      if ((s2 = dalloc(h, (count + 1) / 2, &d)) != MGRIT_OK) return s2;
+      *pf = reinterpret_cast<float*>(d);
+      cudaMemsetAsync(d, 0, count * sizeof(float), h->stream);
+    } else {
+      if ((s2 = dalloc(h, count, pd)) != MGRIT_OK) return s2;
+      cudaMemsetAsync(*pd, 0, count * sizeof(double), h->stream);
+    }
+    return MGRIT_OK;
+  };
+  // the level-1 residual: FP32 in the mixed modes (the FCF residual comes out
+  // of the FP32 pass), except two-level F-relaxation, whose residual is the
+  // FP64 pass's and feeds the FP64 march directly
+  const bool r1_f32 = h->f32c && !(opts->relax == MGRIT_RELAX_F && L == 2);
+  auto AZ1 = [&](size_t count) -> mgrit_status {
+    if (r1_f32) return AZ(count, &h->r[1], &h->rf[1]);
+    mgrit_status s2 = dalloc(h, count, &h->r[1]);
+    if (s2 == MGRIT_OK) cudaMemsetAsync(h->r[1], 0, count * sizeof(double), h->stream);
+    return s2;
+  };
   if ((st = A((N1 + 1) * nx, &h->c[0])) != MGRIT_OK || (st = A((N1 + 1) * nx, &h->c[1])) != MGRIT_OK ||
-      (st = A((N1 + 1) * nx, &h->r[1])) != MGRIT_OK || (st = A(N1 + 1, &h->partial)) != MGRIT_OK ||
+      (st = AZ1((N1 + 1) * nx)) != MGRIT_OK || (st = A(N1 + 1, &h->partial)) != MGRIT_OK ||
       (st = A(2 * (size_t)nx + 8, &h->scratch)) != MGRIT_OK) {
     release(h);
     delete h;
     return st;
   }
-  cudaMemsetAsync(h->r[1], 0, (N1 + 1) * nx * sizeof(double), h->stream);
   cudaMemsetAsync(h->partial, 0, (N1 + 1) * sizeof(double), h->stream);
   for (int l = 2; l <= L; ++l) {
     const size_t P = (size_t)h->Nl[l - 1] + 1;  // points of level l
-    if (l < L || L > 2) {
-      if ((st = A(P * nx, &h->u[l])) != MGRIT_OK) break;
-      cudaMemsetAsync(h->u[l], 0, P * nx * sizeof(double), h->stream);
-    }
+    if (l < L || L > 2)
+      if ((st = AZ(P * nx, &h->u[l], &h->uf[l])) != MGRIT_OK) break;
     if (l < L) {
       const size_t Nc = (size_t)h->Nl[l] + 1;
-      if ((st = A(Nc * nx, &h->cnew[l])) != MGRIT_OK || (st = A(Nc * nx, &h->r[l])) != MGRIT_OK) break;
-      cudaMemsetAsync(h->cnew[l], 0, Nc * nx * sizeof(double), h->stream);
-      cudaMemsetAsync(h->r[l], 0, Nc * nx * sizeof(double), h->stream);
+      if ((st = AZ(Nc * nx, &h->cnew[l], &h->cnewf[l])) != MGRIT_OK ||
+          (st = AZ(Nc * nx, &h->r[l], &h->rf[l])) != MGRIT_OK)
+        break;
     }
   }
   if (st != MGRIT_OK) {
@@ -951,6 +981,10 @@ mgrit_status relax_level(mgrit_handle* h, int l, bool from_zero) {
   f.c_new = h->cnew[l];
   f.g = h->r[l - 1];
   f.r = h->r[l];
+  f.u_old_f = h->uf[l];
+  f.c_new_f = h->cnewf[l];
+  f.g_f = h->rf[l - 1];
+  f.r_f = h->rf[l];
   f.partial = nullptr;
   f.nx = nx;
   f.m = m;
@@ -966,7 +1000,9 @@ mgrit_status solve_coarsest(mgrit_handle* h) {
   const int L = h->L;
   MarchArgs a = {};
   a.g = h->r[L - 1];
+  a.g_f = h->rf[L - 1];
   a.u_out = h->u[L];
+  a.u_out_f = h->uf[L];
   a.store_every = 1;
   a.nx = h->nx;
   a.P = h->Nl[L - 1] + 1;
@@ -981,6 +1017,10 @@ mgrit_status correct_level(mgrit_handle* h, int l) {
   c.e = h->u[l + 1];
   c.g = h->r[l - 1];
   c.u = h->u[l];
+  c.c_new_f = h->cnewf[l];
+  c.e_f = h->uf[l + 1];
+  c.g_f = h->rf[l - 1];
+  c.u_f = h->uf[l];
   c.nx = h->nx;
   c.m = h->m;
   c.N = h->Nl[l];
@@ -1018,6 +1058,7 @@ mgrit_status coarse_cycle(mgrit_handle* h, double* c_new) {
     MarchArgs a = {};
     a.init = nullptr;
     a.g = h->r[1];
+    a.g_f = h->rf[1];
     a.c_add = c_new;
     a.nx = nx;
     a.P = h->Nl[1] + 1;
@@ -1027,6 +1068,7 @@ mgrit_status coarse_cycle(mgrit_handle* h, double* c_new) {
   st = h->opts.cycle == MGRIT_CYCLE_F ? fcycle_level(h, 2) : vcycle_level(h, 2, true);
   if (st != MGRIT_OK) return st;
   return klaunch(h, MGRIT_K_ADD, "add", [&] {
+    if (h->f32c) return launch_ok(launch_add_f(c_new + nx, h->uf[2] + nx, (long long)h->Nl[1] * nx, h->stream), "add");
     return launch_ok(launch_add(c_new + nx, h->u[2] + nx, (long long)h->Nl[1] * nx, h->stream), "add");
   });
 }
@@ -1121,6 +1163,7 @@ static mgrit_status graph_cycle(mgrit_handle* h, int cur, cudaGraphConditionalHa
   f.cstride = nx;
   f.c_new = h->c[1 - cur];
   f.r = h->r[1];
+  f.r_f = h->rf[1];
   f.partial = h->partial;
   f.nx = nx;
   f.m = h->m;
@@ -1297,6 +1340,7 @@ static mgrit_status solve_impl(mgrit_handle* h, const double* u0, const double* 
     f.c_new = h->c[1 - cur];
     f.g = nullptr;
     f.r = h->r[1];
+    f.r_f = h->rf[1];
     f.partial = h->partial;
     f.nx = nx;
     f.m = m;

@@ -36,6 +36,10 @@ struct mgrit_handle {
   std::vector<DevBuf> bufs;       // everything allocated, for release
   double* c[2] = {nullptr, nullptr};
   std::vector<double*> r, u, cnew;  // indexed by level (size L+1)
+  // Mixed modes keep level 1's residual and every coarse-level array in FP32
+  // (rf, uf, cnewf; the FP64 pointers of those arrays stay null).
+  bool f32c = false;
+  std::vector<float*> rf, uf, cnewf;
   double* partial = nullptr;
   double* scratch = nullptr;      // 2*nx + 1 doubles
   double* norm_host = nullptr;    // pinned

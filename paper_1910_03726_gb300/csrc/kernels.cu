@@ -11,6 +11,7 @@
 #include <cooperative_groups.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "device.h"
 
@@ -117,6 +118,14 @@ __device__ __forceinline__ bool vnonzero(T c) { return c != (T)0; }
 template <>
 __device__ __forceinline__ bool vnonzero<df64>(df64 c) { return c.hi != 0.0f || c.lo != 0.0f; }
 
+// Right-hand-side load: FP64 or FP32 storage into the slab's type.
+template <typename T>
+__device__ __forceinline__ T gload(const double* p) { return vfrom<T>(__ldg(p)); }
+template <typename T>
+__device__ __forceinline__ T gload(const float* p) { return (T)__ldg(p); }
+// A typed "no right-hand side".
+constexpr const double* kNoG = nullptr;
+
 template <typename T>
 __device__ __forceinline__ T sparse_coef(const DevTaps& t, int k);
 template <>
@@ -135,11 +144,11 @@ template <>
 __device__ __forceinline__ df64 dense_coef<df64>(const DevTaps& t, int k) { return {t.dhi[k], t.dlo[k]}; }
 
 // dst = T src (+ g): one tap at a time, any offsets (padded layout).
-template <typename T>
+template <typename T, typename G>
 __device__ __forceinline__ void step_sparse(const DevTaps& t, const T* __restrict__ src, T* __restrict__ dst,
-                                           const double* __restrict__ g, int nx) {
+                                           const G* __restrict__ g, int nx) {
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    T acc = g ? vfrom<T>(__ldg(g + i)) : vzero<T>();
+    T acc = g ? gload<T>(g + i) : vzero<T>();
     for (int k = 0; k < t.n; ++k) acc = vfma<T>(sparse_coef<T>(t, k), src[pidx(wrapi(i + t.off[k], nx))], acc);
     dst[pidx(i)] = vfinish<T>(acc);
   }
@@ -149,15 +158,15 @@ __device__ __forceinline__ void step_sparse(const DevTaps& t, const T* __restric
 // outputs from a sliding window of R inputs that advances one offset per tap,
 // so each tap costs one shared load and R FMAs.  Needs the dense form and
 // nx >= 64 (so that every index below wraps at most once).
-template <typename T, int R>
+template <typename T, int R, typename G>
 __device__ __forceinline__ void step_tiled(const DevTaps& t, const T* __restrict__ src, T* __restrict__ dst,
-                                           const double* __restrict__ g, int nx) {
+                                           const G* __restrict__ g, int nx) {
   const int lo = t.lo, span = t.span;
   for (int i0 = threadIdx.x * R; i0 < nx; i0 += blockDim.x * R) {
     T acc[R], w[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      acc[r] = (g && i0 + r < nx) ? vfrom<T>(__ldg(g + i0 + r)) : vzero<T>();
+      acc[r] = (g && i0 + r < nx) ? gload<T>(g + i0 + r) : vzero<T>();
       w[r] = src[pidx(wrapi(i0 + lo + r, nx))];
     }
     for (int k = 0; k < span; ++k) {
@@ -179,9 +188,9 @@ __device__ __forceinline__ void step_tiled(const DevTaps& t, const T* __restrict
 // dst = T src (+ g) for a stencil whose dense span is the compile-time SPAN:
 // each thread loads its R + SPAN - 1 inputs once and keeps them in registers;
 // coefficients are read from the kernel parameters (constant bank).
-template <typename T, int R, int SPAN>
+template <typename T, int R, int SPAN, typename G>
 __device__ __forceinline__ void step_fixed(const DevTaps& t, const T* __restrict__ src, T* __restrict__ dst,
-                                           const double* __restrict__ g, int nx) {
+                                           const G* __restrict__ g, int nx) {
   const int lo = t.lo;
   for (int i0 = threadIdx.x * R; i0 < nx; i0 += blockDim.x * R) {
     T w[R + SPAN - 1];
@@ -189,7 +198,7 @@ __device__ __forceinline__ void step_fixed(const DevTaps& t, const T* __restrict
     for (int q = 0; q < R + SPAN - 1; ++q) w[q] = src[pidx(wrapi(i0 + lo + q, nx))];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      T acc = (g && i0 + r < nx) ? vfrom<T>(__ldg(g + i0 + r)) : vzero<T>();
+      T acc = (g && i0 + r < nx) ? gload<T>(g + i0 + r) : vzero<T>();
 #pragma unroll
       for (int k = 0; k < SPAN; ++k) acc = vfma1<T>(dense_coef<T>(t, k), w[r + k], acc, t.one);
       if (i0 + r < nx) dst[pidx(i0 + r)] = vfinish<T>(acc);
@@ -202,14 +211,14 @@ __device__ __forceinline__ void step_fixed(const DevTaps& t, const T* __restrict
 // and does CH * R FMAs with compile-time indices; the last span % CH taps
 // read their inputs directly.  Suits the wide collapsed stencils of Phi^m.
 constexpr int kChunked = -8;
-template <typename T, int R, int CH>
+template <typename T, int R, int CH, typename G>
 __device__ __forceinline__ void step_chunked(const DevTaps& t, const T* __restrict__ src, T* __restrict__ dst,
-                                             const double* __restrict__ g, int nx) {
+                                             const G* __restrict__ g, int nx) {
   const int lo = t.lo, span = t.span;
   for (int i0 = threadIdx.x * R; i0 < nx; i0 += blockDim.x * R) {
     T acc[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = (g && i0 + r < nx) ? vfrom<T>(__ldg(g + i0 + r)) : vzero<T>();
+    for (int r = 0; r < R; ++r) acc[r] = (g && i0 + r < nx) ? gload<T>(g + i0 + r) : vzero<T>();
     int k = 0;
     for (; k + CH <= span; k += CH) {
       T w[R + CH - 1];
@@ -236,12 +245,12 @@ __device__ __forceinline__ void step_chunked(const DevTaps& t, const T* __restri
 // R encodes the path: 0 one tap at a time; 4, 8 sliding window; SPAN > 0
 // selects the fixed-span path with register tile R; SPAN == kChunked the
 // chunked path.
-template <typename T, int R, int SPAN = 0>
-__device__ __forceinline__ void slab_step(const DevTaps& t, const T* src, T* dst, const double* g, int nx) {
-  if constexpr (SPAN == kChunked) step_chunked<T, R, 8>(t, src, dst, g, nx);
-  else if constexpr (SPAN > 0) step_fixed<T, R, SPAN>(t, src, dst, g, nx);
-  else if constexpr (R > 0) step_tiled<T, R>(t, src, dst, g, nx);
-  else step_sparse<T>(t, src, dst, g, nx);
+template <typename T, int R, int SPAN = 0, typename G = double>
+__device__ __forceinline__ void slab_step(const DevTaps& t, const T* src, T* dst, const G* g, int nx) {
+  if constexpr (SPAN == kChunked) step_chunked<T, R, 8, G>(t, src, dst, g, nx);
+  else if constexpr (SPAN > 0) step_fixed<T, R, SPAN, G>(t, src, dst, g, nx);
+  else if constexpr (R > 0) step_tiled<T, R, G>(t, src, dst, g, nx);
+  else step_sparse<T, G>(t, src, dst, g, nx);
 }
 
 // Sum over the block in a fixed order (deterministic); result valid in thread 0.
@@ -265,44 +274,104 @@ __device__ double block_sum(double v) {
 // once per cycle.  PREC 0: both passes FP64.  PREC 1: the second pass (acting
 // on the correction rho) in FP32.
 // ----------------------------------------------------------------------------
-// PREC 2: both passes in FP32 (coarse levels of the mixed mode, where every
-// quantity is a correction of the error equation).
+// PREC 2: both passes in FP32 with FP32 storage (coarse levels of the mixed
+// modes, where every quantity is a correction of the error equation): reads
+// u_old_f and g_f, writes c_new_f and r_f.
 template <int R, int SPAN = 0>
 __device__ __forceinline__ void fcf_body_fp32(const FcfArgs& a, const int j, const DevTaps& t, unsigned char* smraw) {
   const int nx = a.nx, m = a.m, plen = padded_len(nx);
   float* b0 = reinterpret_cast<float*>(smraw);
   float* b1 = b0 + plen;
-  const double* start = a.u_old + (long long)(j - 1) * a.cstride;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) b0[pidx(i)] = a.zero_old ? 0.0f : (float)start[i];
-  __syncthreads();
-  for (int s = 1; s <= m; ++s) {
-    const double* g = a.g ? a.g + ((long long)(j - 1) * m + s) * nx : nullptr;
+  const float* start = a.u_old_f + (long long)(j - 1) * a.cstride;
+  int nz = 0;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const float v = a.zero_old ? 0.0f : start[i];
+    b0[pidx(i)] = v;
+    nz |= v != 0.0f;
+  }
+  const bool run1 = __syncthreads_or(nz) || a.g_f;  // zero slab, no rhs: Phi^m 0 = 0
+  for (int s = 1; s <= m && run1; ++s) {
+    const float* g = a.g_f ? a.g_f + ((long long)(j - 1) * m + s) * nx : nullptr;
     slab_step<float, R, SPAN>(t, b0, b1, g, nx);
     __syncthreads();
     float* tmp = b0; b0 = b1; b1 = tmp;
   }
-  const double* oldj = a.u_old + (long long)j * a.cstride;
-  double* cn = a.c_new + (long long)j * nx;
+  const float* oldj = a.u_old_f + (long long)j * a.cstride;
+  float* cn = a.c_new_f + (long long)j * nx;
+  nz = 0;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     const float v = b0[pidx(i)];
-    cn[i] = (double)v;
-    b1[pidx(i)] = v - (a.zero_old ? 0.0f : (float)oldj[i]);
+    cn[i] = v;
+    const float rho = v - (a.zero_old ? 0.0f : oldj[i]);
+    b1[pidx(i)] = rho;
+    nz |= rho != 0.0f;
   }
-  __syncthreads();
+  const bool run2 = __syncthreads_or(nz);
   if (j >= a.N) return;
   float* x0 = b1;
   float* x1 = b0;
-  for (int s = 1; s <= m; ++s) {
-    slab_step<float, R, SPAN>(t, x0, x1, nullptr, nx);
+  for (int s = 1; s <= m && run2; ++s) {
+    slab_step<float, R, SPAN>(t, x0, x1, kNoG, nx);
     __syncthreads();
     float* tmp = x0; x0 = x1; x1 = tmp;
   }
-  double* rr = a.r + (long long)(j + 1) * nx;
+  float* rr = a.r_f + (long long)(j + 1) * nx;
+  float ss = 0.0f;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const float v = x0[pidx(i)];
+    rr[i] = v;
+    ss = fmaf(v, v, ss);
+  }
+  if (a.partial) {
+    const double tot = block_sum((double)ss);
+    if (threadIdx.x == 0) a.partial[j] = tot;
+  }
+}
+
+// Residual epilogue of an FP32 second pass: r_{j+1} (FP32 storage if r_f,
+// else FP64) and the interval's squared norm (per-thread FP32 sums).
+__device__ __forceinline__ void store_residual_f32(const FcfArgs& a, int j, const float* x) {
+  const int nx = a.nx;
+  float ss = 0.0f;
+  if (a.r_f) {
+    float* rr = a.r_f + (long long)(j + 1) * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const float v = x[pidx(i)];
+      rr[i] = v;
+      ss = fmaf(v, v, ss);
+    }
+  } else {
+    double* rr = a.r + (long long)(j + 1) * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const float v = x[pidx(i)];
+      rr[i] = (double)v;
+      ss = fmaf(v, v, ss);
+    }
+  }
+  if (a.partial) {
+    const double tot = block_sum((double)ss);
+    if (threadIdx.x == 0) a.partial[j] = tot;
+  }
+}
+
+// F-relaxation epilogue: the C-point keeps its value, r_j = v - c_j in FP64
+// (stored FP32 if r_f), squared norm from the FP64 values.
+template <typename V>
+__device__ __forceinline__ void store_f_relaxation(const FcfArgs& a, int j, const V* b0) {
+  const int nx = a.nx;
+  const double* oldj = a.u_old + (long long)j * a.cstride;
+  double* cn = a.c_new + (long long)j * nx;
   double ss = 0.0;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    const double v = (double)x0[pidx(i)];
-    rr[i] = v;
-    ss = fma(v, v, ss);
+    const double old = a.zero_old ? 0.0 : oldj[i];
+    double v;
+    if constexpr (std::is_same<V, df64>::value) v = df_to(b0[pidx(i)]);
+    else v = b0[pidx(i)];
+    const double rho = v - old;
+    cn[i] = old;
+    if (a.r_f) a.r_f[(long long)j * nx + i] = (float)rho;
+    else a.r[(long long)j * nx + i] = rho;
+    ss = fma(rho, rho, ss);
   }
   if (a.partial) {
     ss = block_sum(ss);
@@ -333,20 +402,8 @@ __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const
   }
   const double* oldj = a.u_old + (long long)j * a.cstride;
   double* cn = a.c_new + (long long)j * nx;
-  if (a.relax_f) {  // F-relaxation only: the C-point keeps its value, r_j = v - c_j
-    double* rj = a.r + (long long)j * nx;
-    double ss = 0.0;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const double old = a.zero_old ? 0.0 : oldj[i];
-      const double rho = df_to(b0[pidx(i)]) - old;
-      cn[i] = old;
-      rj[i] = rho;
-      ss = fma(rho, rho, ss);
-    }
-    if (a.partial) {
-      ss = block_sum(ss);
-      if (threadIdx.x == 0) a.partial[j] = ss;
-    }
+  if (a.relax_f) {
+    store_f_relaxation(a, j, b0);
     return;
   }
   float* f0 = reinterpret_cast<float*>(b1);
@@ -362,21 +419,11 @@ __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const
   const bool run2 = __syncthreads_or(nz);
   if (j >= a.N) return;
   for (int s = 1; s <= m && run2; ++s) {
-    slab_step<float, R, SPAN>(t, f0, f1, nullptr, nx);
+    slab_step<float, R, SPAN>(t, f0, f1, kNoG, nx);
     __syncthreads();
     float* tmp = f0; f0 = f1; f1 = tmp;
   }
-  double* rr = a.r + (long long)(j + 1) * nx;
-  double ss = 0.0;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    const double v = (double)f0[pidx(i)];
-    rr[i] = v;
-    ss = fma(v, v, ss);
-  }
-  if (a.partial) {
-    ss = block_sum(ss);
-    if (threadIdx.x == 0) a.partial[j] = ss;
-  }
+  store_residual_f32(a, j, f0);
 }
 
 template <int PREC, int R, int SPAN = 0>
@@ -412,19 +459,8 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
   double* cn = a.c_new + (long long)j * nx;
   const bool more = j < a.N;
   double ss = 0.0;
-  if (a.relax_f) {  // F-relaxation only: the C-point keeps its value, r_j = v - c_j
-    double* rj = a.r + (long long)j * nx;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const double old = a.zero_old ? 0.0 : oldj[i];
-      const double rho = b0[pidx(i)] - old;
-      cn[i] = old;
-      rj[i] = rho;
-      ss = fma(rho, rho, ss);
-    }
-    if (a.partial) {
-      ss = block_sum(ss);
-      if (threadIdx.x == 0) a.partial[j] = ss;
-    }
+  if (a.relax_f) {
+    store_f_relaxation(a, j, b0);
     return;
   }
   if (PREC == 0) {
@@ -441,7 +477,7 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
     double* x0 = b1;
     double* x1 = b0;
     for (int s = 1; s <= m && run2; ++s) {
-      slab_step<double, R, SPAN>(t, x0, x1, nullptr, nx);
+      slab_step<double, R, SPAN>(t, x0, x1, kNoG, nx);
       __syncthreads();
       double* tmp = x0; x0 = x1; x1 = tmp;
     }
@@ -465,16 +501,12 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
     const bool run2 = __syncthreads_or(nz);
     if (!more) return;
     for (int s = 1; s <= m && run2; ++s) {
-      slab_step<float, R, SPAN>(t, f0, f1, nullptr, nx);
+      slab_step<float, R, SPAN>(t, f0, f1, kNoG, nx);
       __syncthreads();
       float* tmp = f0; f0 = f1; f1 = tmp;
     }
-    double* rr = a.r + (long long)(j + 1) * nx;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const double v = (double)f0[pidx(i)];
-      rr[i] = v;
-      ss = fma(v, v, ss);
-    }
+    store_residual_f32(a, j, f0);
+    return;
   }
   if (a.partial) {
     ss = block_sum(ss);
@@ -541,16 +573,20 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
     B0[k] = a.init ? a.init[gi] : 0.0;
   }
   __syncthreads();
+  // next step's right-hand side and C-points, loaded one step ahead (an FP32
+  // right-hand side stays FP32 until it is used, so the load is not waited on)
   double gq[PPT], cq[PPT];
+  float gqf[PPT];
 #pragma unroll
-  for (int p = 0; p < PPT; ++p) { gq[p] = 0.0; cq[p] = 0.0; }
+  for (int p = 0; p < PPT; ++p) { gq[p] = 0.0; cq[p] = 0.0; gqf[p] = 0.0f; }
   auto prefetch = [&](int n, int Sn) {
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
       const int i = tid + p * bs;
       if (i < w) {
         const long long o = (long long)n * nx + wrapi(base + i + Sn, nx);
-        if (a.g) gq[p] = __ldcg(a.g + o);
+        if (a.g_f) gqf[p] = __ldcg(a.g_f + o);
+        else if (a.g) gq[p] = __ldcg(a.g + o);
         if (a.c_add) cq[p] = __ldcg(a.c_add + o);
       }
     }
@@ -562,10 +598,10 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
     double* nxt = (n & 1) ? B1 : B0;
     double gc[PPT], cc[PPT];
 #pragma unroll
-    for (int p = 0; p < PPT; ++p) { gc[p] = gq[p]; cc[p] = cq[p]; }
+    for (int p = 0; p < PPT; ++p) { gc[p] = a.g_f ? (double)gqf[p] : gq[p]; cc[p] = cq[p]; }
     const int Snext = modnx((long long)S - sigma, nx);
     if (n + 1 < a.P) prefetch(n + 1, Snext);
-    const bool store = a.u_out && (n % a.store_every) == 0;
+    const bool store = (a.u_out || a.u_out_f) && (n % a.store_every) == 0;
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
       const int i = tid + p * bs;
@@ -576,7 +612,11 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
         nxt[L + i] = acc;
         const int gi = wrapi(base + i + S, nx);
         if (a.c_add) a.c_add[(long long)n * nx + gi] = cc[p] + acc;
-        if (store) a.u_out[(long long)(n / a.store_every) * nx + gi] = acc;
+        if (store) {
+          const long long o = (long long)(n / a.store_every) * nx + gi;
+          if (a.u_out_f) a.u_out_f[o] = (float)acc;
+          else a.u_out[o] = acc;
+        }
       }
     }
     cl.sync();
@@ -620,6 +660,7 @@ __global__ void __launch_bounds__(256) march_batched_kernel(const BatchSolve* __
   MarchArgs a = {};
   a.init = nullptr;
   a.g = s->fcf.r;
+  a.g_f = s->fcf.r_f;
   a.u_out = nullptr;
   a.store_every = 1;
   a.c_add = s->fcf.c_new;
@@ -631,29 +672,46 @@ __global__ void __launch_bounds__(256) march_batched_kernel(const BatchSolve* __
 // ----------------------------------------------------------------------------
 // Correction + F-relaxation of a level (ideal interpolation).
 // ----------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ const T* pick(const double* d, const float* f) {
+  if constexpr (std::is_same<T, float>::value) return f;
+  else return d;
+}
+template <typename T>
+__device__ __forceinline__ T* pick(double* d, float* f) {
+  if constexpr (std::is_same<T, float>::value) return f;
+  else return d;
+}
+
+// Storage of the level in T: FP64 fields for T = double, FP32 fields for
+// T = float (FP32 coarse levels).
 template <typename T, int R>
 __global__ void __launch_bounds__(R == 8 ? 512 : 1024) correct_kernel(const CorrectArgs a, const DevTaps t) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nx = a.nx, m = a.m, j = blockIdx.x + 1, plen = padded_len(nx);
+  const T* cnew = pick<T>(a.c_new, a.c_new_f);
+  const T* e = pick<T>(a.e, a.e_f);
+  const T* gg = pick<T>(a.g, a.g_f);
+  T* u = pick<T>(a.u, a.u_f);
   T* b0 = reinterpret_cast<T*>(smraw);
   T* b1 = b0 + plen;
   const long long p0 = (long long)(j - 1) * m;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    const double v = a.c_new[(long long)(j - 1) * nx + i] + (a.e ? a.e[(long long)(j - 1) * nx + i] : 0.0);
-    b0[pidx(i)] = (T)v;
-    a.u[p0 * nx + i] = v;
+    const T v = cnew[(long long)(j - 1) * nx + i] + (e ? e[(long long)(j - 1) * nx + i] : (T)0);
+    b0[pidx(i)] = v;
+    u[p0 * nx + i] = v;
   }
   __syncthreads();
   for (int s = 1; s < m; ++s) {
-    const double* g = a.g ? a.g + (p0 + s) * nx : nullptr;
+    const T* g = gg ? gg + (p0 + s) * nx : nullptr;
     slab_step<T, R>(t, b0, b1, g, nx);
     __syncthreads();
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) a.u[(p0 + s) * nx + i] = (double)b1[pidx(i)];
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) u[(p0 + s) * nx + i] = b1[pidx(i)];
     T* tmp = b0; b0 = b1; b1 = tmp;
   }
   if (j == a.N)
     for (int i = threadIdx.x; i < nx; i += blockDim.x)
-      a.u[(long long)a.N * m * nx + i] = a.c_new[(long long)a.N * nx + i] + (a.e ? a.e[(long long)a.N * nx + i] : 0.0);
+      u[(long long)a.N * m * nx + i] = cnew[(long long)a.N * nx + i] + (e ? e[(long long)a.N * nx + i] : (T)0);
 }
 
 __global__ void __launch_bounds__(1024) norm_kernel(const double* __restrict__ partial, int n, double* out) {
@@ -680,6 +738,12 @@ __global__ void add_kernel(double* __restrict__ c, const double* __restrict__ e,
     c[i] += e[i];
 }
 
+__global__ void add_f_kernel(double* __restrict__ c, const float* __restrict__ e, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    c[i] += (double)e[i];
+}
+
 template <int R>
 __global__ void __launch_bounds__(R == 8 ? 512 : 1024) propagate_kernel(const double* in, double* out, int nx, int k,
                                                          const DevTaps t, double* partial) {
@@ -691,7 +755,7 @@ __global__ void __launch_bounds__(R == 8 ? 512 : 1024) propagate_kernel(const do
   for (int i = threadIdx.x; i < nx; i += blockDim.x) b0[pidx(i)] = in[v * nx + i];
   __syncthreads();
   for (int s = 0; s < k; ++s) {
-    slab_step<double, R>(t, b0, b1, nullptr, nx);
+    slab_step<double, R>(t, b0, b1, kNoG, nx);
     __syncthreads();
     double* tmp = b0; b0 = b1; b1 = tmp;
   }
@@ -984,6 +1048,14 @@ cudaError_t launch_add(double* c, const double* e, long long count, cudaStream_t
   long long blocks = (count + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   add_kernel<<<(int)blocks, 256, 0, s>>>(c, e, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_f(double* c, const float* e, long long count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  long long blocks = (count + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  add_f_kernel<<<(int)blocks, 256, 0, s>>>(c, e, count);
   return cudaGetLastError();
 }
 

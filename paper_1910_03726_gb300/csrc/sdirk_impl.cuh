@@ -268,12 +268,12 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const SdirkPlan& p, i
   const bool more = j < a.N;
   double ss = 0.0;
   if (a.relax_f) {  // F-relaxation only: the C-point keeps its value, r_j = v - c_j
-    double* rj = a.r + (long long)j * nx;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       const double old = a.zero_old ? 0.0 : oldj[i];
       const double rho = slab[pix(i)] - old;
       cn[i] = old;
-      rj[i] = rho;
+      if (a.r_f) a.r_f[(long long)j * nx + i] = (float)rho;
+      else a.r[(long long)j * nx + i] = rho;
       ss = fma(rho, rho, ss);
     }
     if (a.partial) {
@@ -321,12 +321,14 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const SdirkPlan& p, i
     if (!more) return;
     for (int s = 0; s < m && run2; ++s)
       sdirk_step<float, C, KF, KB>(p, fs, plen, nx, sm.t32, reinterpret_cast<float*>(smw));
-    double* rr = a.r + (long long)(j + 1) * nx;
+    float ssf = 0.0f;  // FP32 residual (FP32 storage if r_f), per-thread FP32 sums
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const double v = (double)fs[pix(i)];
-      rr[i] = v;
-      ss = fma(v, v, ss);
+      const float v = fs[pix(i)];
+      if (a.r_f) a.r_f[(long long)(j + 1) * nx + i] = v;
+      else a.r[(long long)(j + 1) * nx + i] = (double)v;
+      ssf = fmaf(v, v, ssf);
     }
+    ss = (double)ssf;
   }
   if (a.partial) {
     ss = block_sum(ss);

@@ -209,6 +209,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     b.fcf.c_new = h->c[1 - act[k]->cur];
     b.fcf.g = nullptr;
     b.fcf.r = h->r[1];
+    b.fcf.r_f = h->rf[1];
     b.fcf.partial = h->partial;
     b.fcf.nx = h->nx;
     b.fcf.m = h->fine_collapse ? 1 : h->m;  // collapsed: one application of Phi^m per pass
