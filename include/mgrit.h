@@ -50,7 +50,7 @@ typedef enum mgrit_status {
   MGRIT_ERR_UNSTABLE = -2,        /* ERK CFL number above the limit (Table 1)      */
   MGRIT_ERR_PSI_ILLCOND = -3,     /* fit rejected: |Im psi| > 1e-8 (Section 4.1)   */
   MGRIT_ERR_NOT_CONVERGED = -4,   /* max_iter reached above tol                    */
-  MGRIT_ERR_DIVERGED = -5,        /* residual not finite or grew by > 1e6          */
+  MGRIT_ERR_DIVERGED = -5,        /* residual not finite or grew by > 1e6 (flags)  */
   MGRIT_ERR_OVER_BUDGET = -6,     /* server: request larger than the HBM budget    */
   MGRIT_ERR_OOM = -7,             /* device allocation failed                      */
   MGRIT_ERR_TIMEOUT = -8,         /* a bounded device wait ran out                 */
@@ -81,7 +81,10 @@ enum {
   MGRIT_PSI_HALFWIDTH = 1,  /* 2h+1 offsets centred on argmax |phi~^m_i|      */
   MGRIT_PSI_THRESHOLD = 2,  /* |phi~^m_i| >= psi_eta * max |phi~^m|            */
   MGRIT_PSI_USER = 3,       /* caller supplies offsets and coefficients        */
-  MGRIT_PSI_IDEAL = 4       /* Psi = Phi^m exactly (ERK, two levels)           */
+  MGRIT_PSI_IDEAL = 4,      /* Psi = Phi^m exactly (ERK, two levels)           */
+  MGRIT_PSI_REDISC = 5      /* Psi = the fine scheme rediscretised with time
+                               step m dt (Section 2.3, Table 2): SDIRK, two
+                               levels; an implicit coarse step, no stencil  */
 };
 
 enum { MGRIT_OUT_FINAL = 0, MGRIT_OUT_CPOINTS = 1, MGRIT_OUT_FULL = 2 };
@@ -105,7 +108,12 @@ enum { MGRIT_RELAX_FCF = 0, MGRIT_RELAX_F = 1 };
  * cycle) instead of the default single CUDA-graph launch per solve, whose
  * WHILE/IF conditional nodes are set by an on-device stopping test.
  * MGRIT_FLAG_TIME_KERNELS implies the host loop. */
-enum { MGRIT_FLAG_TIME_KERNELS = 1, MGRIT_FLAG_NO_AUTOTUNE = 2, MGRIT_FLAG_HOST_LOOP = 4 };
+/* MGRIT_FLAG_NO_DIVERGENCE_STOP: stop as diverged only on a non-finite
+ * residual, not when it grows above 1e6 x the initial one (the paper's
+ * divergent configurations, Table 2, converge by finite termination after
+ * large transient growth). */
+enum { MGRIT_FLAG_TIME_KERNELS = 1, MGRIT_FLAG_NO_AUTOTUNE = 2, MGRIT_FLAG_HOST_LOOP = 4,
+       MGRIT_FLAG_NO_DIVERGENCE_STOP = 8 };
 
 /* Kernel kinds reported in mgrit_result.kernel_ms / kernel_count. */
 enum {

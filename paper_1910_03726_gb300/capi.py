@@ -24,7 +24,7 @@ STATUS = {0: "OK", 1: "PENDING", -1: "ERR_INVALID", -2: "ERR_UNSTABLE", -3: "ERR
           -8: "ERR_TIMEOUT", -9: "ERR_CUDA", -10: "ERR_UNSUPPORTED", -11: "ERR_UNKNOWN_TICKET"}
 ERK, SDIRK = 0, 1
 PREC_FP64, PREC_MIXED, PREC_MIXED_DF = 0, 1, 2
-PSI_AUTO, PSI_HALFWIDTH, PSI_THRESHOLD, PSI_USER, PSI_IDEAL = 0, 1, 2, 3, 4
+PSI_AUTO, PSI_HALFWIDTH, PSI_THRESHOLD, PSI_USER, PSI_IDEAL, PSI_REDISC = 0, 1, 2, 3, 4, 5
 OUT_FINAL, OUT_CPOINTS, OUT_FULL = 0, 1, 2
 CYCLE_V, CYCLE_F = 0, 1
 RELAX_FCF, RELAX_F = 0, 1
@@ -33,6 +33,7 @@ MAX_LEVELS = 8
 FLAG_TIME_KERNELS = 1
 FLAG_NO_AUTOTUNE = 2
 FLAG_HOST_LOOP = 4
+FLAG_NO_DIVERGENCE_STOP = 8
 KERNEL_KINDS = ["fcf", "fcf_coarse", "march", "correct", "norm", "add", "propagate", "other"]
 K_KINDS = len(KERNEL_KINDS)
 

@@ -47,6 +47,11 @@ struct FcfArgs {
   double* partial;         // partial[j], j = 1..N-1 (nullptr: skip)
   int nx, m, N, zero_old;  // zero_old: u_old is identically zero
   int relax_f;             // F-relaxation only: c_new = u_old, r_j = Phi^m c_{j-1} - c_j (j = 1..N)
+  // Value-form residual (FP64, level 1): the second pass propagates c_new_j
+  // itself and stores Phi^m c_new_j in r row j+1; residual_value then forms
+  // r_{j+1} = Phi^m c_new_j - c_new_{j+1} (the oracle's form, whose
+  // cancellation keeps exact C-points bitwise exact) and the norms.
+  int value_residual;
   // FP32 storage (mixed modes): r_f replaces r (any precision); on an FP32
   // coarse level (precision 2) u_old_f, c_new_f, g_f and r_f replace all four.
   const float* u_old_f;
@@ -113,6 +118,7 @@ struct CheckState {
   int nhist;
   double rel;
   double hist[128];
+  double diverge;         // stop as diverged above this ratio (<= 0: only when not finite)
 };
 cudaError_t launch_check(const double* norm2, CheckState* st, unsigned long long while_handle,
                          unsigned long long if_handle, int cur, cudaStream_t s);
@@ -167,6 +173,11 @@ cudaError_t launch_interp_sdirk(const double* c, double* u, int nx, int m, int N
                                 cudaStream_t s);
 cudaError_t launch_seq_sdirk(const double* u0, double* out, int nx, int P, int store_every, const SdirkPlan& p,
                              cudaStream_t s);
+// Two-level coarse solve with the rediscretised SDIRK step (one CTA):
+// e_0 = 0, e_n = Phi_c e_{n-1} + g_n, c_add[n] += e_n for n = 1..P-1; g is
+// FP64 (g) or FP32 (g_f, used when set).
+cudaError_t launch_coarse_march_sdirk(const double* g, const float* g_f, double* c_add, int nx, int P,
+                                      const SdirkPlan& p, cudaStream_t s);
 
 // ------------------------------------------------------------ batched solves
 // One entry per active solve of a batched launch (server).
@@ -196,6 +207,9 @@ cudaError_t launch_march(const MarchArgs& a, const DevTaps& t, int cluster, int 
                          cudaStream_t s);
 cudaError_t launch_correct(const CorrectArgs& a, const DevTaps& t, int threads, cudaStream_t s, int fp32 = 0);
 cudaError_t launch_norm(const double* partial, int n, double* out, cudaStream_t s);
+// r[j+1] -= c_new[j+1] and partial[j] = ||r[j+1]||^2 for j = 1..N-1.
+cudaError_t launch_residual_value(const double* c_new, double* r, double* partial, int nx, int N, cudaStream_t s);
+cudaError_t launch_residual_value_batched(const BatchSolve* S, const BatchItem* items, int nitems, cudaStream_t s);
 cudaError_t launch_add(double* c, const double* e, long long count, cudaStream_t s);
 cudaError_t launch_add_f(double* c, const float* e, long long count, cudaStream_t s);
 cudaError_t launch_propagate(const double* in, double* out, int count, int nx, int k,

@@ -196,6 +196,9 @@ mgrit_status validate_opts(const mgrit_problem* p, const mgrit_opts* o) {
   if (o->output < 0 || o->output > 2) return fail(MGRIT_ERR_INVALID, "unknown output");
   if (o->psi_rule == MGRIT_PSI_IDEAL && (p->family != MGRIT_ERK || o->levels != 2))
     return fail(MGRIT_ERR_INVALID, "PSI_IDEAL needs ERK and two levels");
+  if (o->psi_rule == MGRIT_PSI_REDISC && (p->family != MGRIT_SDIRK || o->levels != 2))
+    return fail(MGRIT_ERR_INVALID, "PSI_REDISC needs SDIRK and two levels");
+  if (o->psi_rule < MGRIT_PSI_AUTO || o->psi_rule > MGRIT_PSI_REDISC) return fail(MGRIT_ERR_INVALID, "unknown psi_rule");
   if (o->psi_rule == MGRIT_PSI_HALFWIDTH && o->psi_halfwidth < 0)
     return fail(MGRIT_ERR_INVALID, "psi_halfwidth must be >= 0");
   if (o->cycle != MGRIT_CYCLE_V && o->cycle != MGRIT_CYCLE_F) return fail(MGRIT_ERR_INVALID, "unknown cycle");
@@ -215,6 +218,12 @@ static PlanRequest make_request(const mgrit_problem* p, const mgrit_opts* o) {
 
 mgrit_status plan(const mgrit_problem* p, const mgrit_opts* o, std::vector<CoarseOp>* ops) {
   std::string err;
+  if (o->psi_rule == MGRIT_PSI_REDISC) {  // an SDIRK step, not a stencil: placeholder op
+    ops->assign(1, CoarseOp());
+    ops->back().taps.off = {0};
+    ops->back().taps.coef = {1.0};
+    return MGRIT_OK;
+  }
   if (!build_hierarchy(make_request(p, o), ops, &err)) return fail(MGRIT_ERR_INVALID, err);
   for (size_t l = 0; l < ops->size(); ++l) {
     if ((*ops)[l].imag > 1e-8)
@@ -243,6 +252,8 @@ extern "C" mgrit_status mgrit_phi_taps(const mgrit_problem* prob, int32_t cap, i
 
 extern "C" mgrit_status mgrit_psi_plan(const mgrit_problem* prob, const mgrit_opts* opts, int32_t cap, int32_t* nnz,
                                        int32_t* offsets, double* coeffs, double* diag) {
+  if (opts && opts->psi_rule == MGRIT_PSI_REDISC)
+    return fail(MGRIT_ERR_UNSUPPORTED, "the rediscretised Psi is an implicit step, not a stencil");
   mgrit_status st = validate_problem(prob);
   if (st == MGRIT_OK) st = validate_opts(prob, opts);
   if (st != MGRIT_OK) return st;
@@ -712,7 +723,7 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
     delete h;
     return st;
   }
-  std::vector<double> sd_tables;
+  std::vector<double> sd_tables, cd_tables;
   if (prob->family == MGRIT_SDIRK) {
     h->sdirk = true;
     if ((st = make_sdirk_plan(prob, &h->splan, &sd_tables)) != MGRIT_OK) {
@@ -722,6 +733,15 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
     if (sdirk_smem(h->splan) > 227 * 1024) {
       delete h;
       return fail(MGRIT_ERR_UNSUPPORTED, "nx too large for the SDIRK stage slabs in shared memory");
+    }
+    if (opts->psi_rule == MGRIT_PSI_REDISC) {  // coarse step: the same scheme at m dt
+      mgrit_problem pc = *prob;
+      pc.cfl = prob->cfl * opts->m;
+      h->redisc = true;
+      if ((st = make_sdirk_plan(&pc, &h->cplan, &cd_tables)) != MGRIT_OK) {
+        delete h;
+        return st;
+      }
     }
     // Phi is dense for SDIRK; only its order-1 stencil placeholder is kept
     h->phi.off = {0};
@@ -841,6 +861,20 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
     cudaMemcpyAsync(tab, sd_tables.data(), tl * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     cudaMemcpyAsync(tab + tl, t32.data(), tl * sizeof(float), cudaMemcpyHostToDevice, h->stream);
     cudaMemcpyAsync(dplan, &h->splan, sizeof(SdirkPlan), cudaMemcpyHostToDevice, h->stream);
+    if (h->redisc) {
+      const size_t tc = (size_t)h->cplan.tab_len;
+      double* ctab = nullptr;
+      if ((st = A(tc + (tc + 1) / 2, &ctab)) != MGRIT_OK) {
+        release(h);
+        delete h;
+        return st;
+      }
+      const std::vector<float> c32(cd_tables.begin(), cd_tables.end());
+      h->cplan.tab64 = ctab;
+      h->cplan.tab32 = reinterpret_cast<float*>(ctab + tc);
+      cudaMemcpyAsync(ctab, cd_tables.data(), tc * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+      cudaMemcpyAsync(ctab + tc, c32.data(), tc * sizeof(float), cudaMemcpyHostToDevice, h->stream);
+    }
   }
   h->fcf_threads = 0;  // chosen per launch from nx and the register tile
   if (const char* tile = std::getenv("MGRIT_TILE")) set_tile(std::atoi(tile));
@@ -877,6 +911,7 @@ extern "C" mgrit_status mgrit_psi_info(mgrit_handle* h, int32_t level, int32_t c
                                        double* coeffs) {
   if (!h) return fail(MGRIT_ERR_INVALID, "handle is NULL");
   if (level < 2 || level > h->L) return fail(MGRIT_ERR_INVALID, "level must be 2..levels");
+  if (h->redisc) return fail(MGRIT_ERR_UNSUPPORTED, "the rediscretised Psi is an implicit step, not a stencil");
   const Taps& t = h->ops[level - 2].taps;
   if (nnz) *nnz = t.size();
   if (t.size() > cap) return fail(MGRIT_ERR_INVALID, "capacity too small");
@@ -1054,6 +1089,12 @@ mgrit_status fcycle_level(mgrit_handle* h, int l) {
 mgrit_status coarse_cycle(mgrit_handle* h, double* c_new) {
   const int L = h->L, nx = h->nx;
   mgrit_status st;
+  if (L == 2 && h->redisc) {  // e_j = Phi(m dt) e_{j-1} + r_j, c_j += e_j, one CTA
+    return klaunch(h, MGRIT_K_MARCH, "march", [&] {
+      return launch_ok(launch_coarse_march_sdirk(h->r[1], h->rf[1], c_new, nx, h->Nl[1] + 1, h->cplan, h->stream),
+                       "coarse march (SDIRK)");
+    });
+  }
   if (L == 2) {
     MarchArgs a = {};
     a.init = nullptr;
@@ -1169,8 +1210,12 @@ static mgrit_status graph_cycle(mgrit_handle* h, int cur, cudaGraphConditionalHa
   f.m = h->m;
   f.N = h->Nl[1];
   f.relax_f = h->opts.relax == MGRIT_RELAX_F;
+  f.value_residual = fine_prec(h) == 0 && !f.relax_f;
   mgrit_status st;
   if ((st = launch_ok(launch_fine_fcf(h, f, fine_prec(h)), "fcf")) != MGRIT_OK) return st;
+  if (f.value_residual &&
+      (st = launch_ok(launch_residual_value(f.c_new, f.r, f.partial, nx, f.N, h->stream), "residual")) != MGRIT_OK)
+    return st;
   if ((st = launch_ok(launch_norm(h->partial, h->Nl[1] + f.relax_f, h->scratch + 2 * nx, h->stream), "norm")) !=
       MGRIT_OK)
     return st;
@@ -1246,6 +1291,7 @@ static mgrit_status solve_graph(mgrit_handle* h, const double* u0, const double*
   std::memset(h->hstate, 0, sizeof(CheckState));
   h->hstate->tol = h->opts.tol;
   h->hstate->max_iter = h->opts.max_iter;
+  h->hstate->diverge = (h->opts.flags & MGRIT_FLAG_NO_DIVERGENCE_STOP) ? 0.0 : 1e6;
   h->hstate->r0sq = r0_norm > 0.0 ? r0_norm * r0_norm : 0.0;
   CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(CheckState), cudaMemcpyHostToDevice, h->stream));
   // otherwise ||Phi u0||^2 straight into the state (zero initial iterate: r^(0) = Phi u0)
@@ -1270,7 +1316,7 @@ static mgrit_status solve_graph(mgrit_handle* h, const double* u0, const double*
   reset_stats(h);
   h->kcount[MGRIT_K_PROPAGATE] = r0_norm > 0.0 ? 0 : 1;
   h->kcount[MGRIT_K_FCF] = S.it + 1;
-  h->kcount[MGRIT_K_NORM] = S.it + 1;
+  h->kcount[MGRIT_K_NORM] = (fine_prec(h) == 0 && h->opts.relax == MGRIT_RELAX_FCF ? 2 : 1) * (S.it + 1);
   h->kcount[MGRIT_K_OTHER] = S.it + 1;
   if (out && (st = write_output(h, h->c[1 - S.result_cur], out)) != MGRIT_OK) return st;
   const int other_before = h->kcount[MGRIT_K_OTHER];
@@ -1347,9 +1393,15 @@ static mgrit_status solve_impl(mgrit_handle* h, const double* u0, const double* 
     f.N = (int)N1;
     f.zero_old = 0;
     f.relax_f = h->opts.relax == MGRIT_RELAX_F;
+    f.value_residual = prec == 0 && !f.relax_f;
     if ((st = klaunch(h, MGRIT_K_FCF, "fcf", [&] {
            return launch_ok(launch_fine_fcf(h, f, prec), "fcf");
          })) != MGRIT_OK)
+      return st;
+    if (f.value_residual && (st = klaunch(h, MGRIT_K_NORM, "residual", [&] {
+                               return launch_ok(launch_residual_value(f.c_new, f.r, f.partial, nx, f.N, h->stream),
+                                                "residual");
+                             })) != MGRIT_OK)
       return st;
     if ((st = klaunch(h, MGRIT_K_NORM, "norm", [&] {
            return launch_ok(launch_norm(h->partial, (int)N1 + f.relax_f, h->scratch + 2 * nx, h->stream), "norm");
@@ -1360,7 +1412,7 @@ static mgrit_status solve_impl(mgrit_handle* h, const double* u0, const double* 
     const double rel = !std::isfinite(r0) ? r0 : (r0 > 0.0 ? std::sqrt(h->norm_host[0]) / r0 : 0.0);
     if (R.n_history < MGRIT_MAX_HISTORY) R.history[R.n_history++] = rel;
     R.rel_residual = rel;
-    if (!std::isfinite(rel) || rel > 1e6) {
+    if (!std::isfinite(rel) || (rel > 1e6 && !(h->opts.flags & MGRIT_FLAG_NO_DIVERGENCE_STOP))) {
       final_status = fail(MGRIT_ERR_DIVERGED, "residual not finite or grew above 1e6 x initial");
       break;
     }
@@ -1469,6 +1521,8 @@ extern "C" mgrit_status mgrit_propagate(mgrit_handle* h, int32_t level, int32_t 
   mgrit_status st = klaunch(h, MGRIT_K_PROPAGATE, "propagate", [&] {
     if (level == 1 && h->sdirk)
       return launch_ok(launch_propagate_sdirk(in, out, count, h->nx, k, h->splan, nullptr, h->stream), "propagate");
+    if (level == 2 && h->redisc)
+      return launch_ok(launch_propagate_sdirk(in, out, count, h->nx, k, h->cplan, nullptr, h->stream), "propagate");
     return launch_ok(launch_propagate(in, out, count, h->nx, k, t, nullptr, h->fcf_threads, h->stream), "propagate");
   });
   if (st != MGRIT_OK) return st;

@@ -32,6 +32,8 @@ struct mgrit_handle {
   bool sdirk = false;             // fine level is SDIRK (stage solves)
   mg::SdirkPlan splan;            // host copy (its table pointers are device addresses)
   mg::SdirkPlan* dsplan = nullptr;  // device copy (batched launches)
+  bool redisc = false;              // Psi = the SDIRK step at m dt (cplan)
+  mg::SdirkPlan cplan;
   std::vector<mg::DevTaps> dpsi;      // dpsi[l-2]
   std::vector<DevBuf> bufs;       // everything allocated, for release
   double* c[2] = {nullptr, nullptr};

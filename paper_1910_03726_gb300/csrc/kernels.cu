@@ -468,7 +468,7 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       const double v = b0[pidx(i)];
       cn[i] = v;
-      const double rho = v - (a.zero_old ? 0.0 : oldj[i]);
+      const double rho = a.value_residual ? v : v - (a.zero_old ? 0.0 : oldj[i]);
       b1[pidx(i)] = rho;
       nz |= rho != 0.0;
     }
@@ -487,6 +487,7 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
       rr[i] = v;
       ss = fma(v, v, ss);
     }
+    if (a.value_residual) return;  // Phi^m c_new_j stored; residual_value finishes
   } else {
     float* f0 = reinterpret_cast<float*>(b1);
     float* f1 = f0 + plen;
@@ -732,6 +733,34 @@ __global__ void __launch_bounds__(1024) norm_batched_kernel(const BatchSolve* __
   if (threadIdx.x == 0) out[blockIdx.x] = v;
 }
 
+// Value-form residual: r_{j+1} = Phi^m c_new_j - c_new_{j+1} (r row j+1 holds
+// Phi^m c_new_j) and its squared norm into partial[j]; one CTA per row.
+__device__ __forceinline__ void residual_value_row(const double* c_new, double* r, double* partial, int nx, int j) {
+  const double* cn = c_new + (long long)(j + 1) * nx;
+  double* rr = r + (long long)(j + 1) * nx;
+  double ss = 0.0;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const double v = rr[i] - cn[i];
+    rr[i] = v;
+    ss = fma(v, v, ss);
+  }
+  if (partial) {
+    ss = block_sum(ss);
+    if (threadIdx.x == 0) partial[j] = ss;
+  }
+}
+__global__ void __launch_bounds__(512) residual_value_kernel(const double* __restrict__ c_new, double* r,
+                                                             double* partial, int nx) {
+  residual_value_row(c_new, r, partial, nx, blockIdx.x + 1);
+}
+__global__ void __launch_bounds__(512) residual_value_batched_kernel(const BatchSolve* __restrict__ S,
+                                                                     const BatchItem* __restrict__ items) {
+  const BatchItem it = items[blockIdx.x];
+  const FcfArgs& a = S[it.solve].fcf;
+  if (!a.value_residual || it.j >= a.N) return;
+  residual_value_row(a.c_new, a.r, a.partial, a.nx, it.j);
+}
+
 __global__ void add_kernel(double* __restrict__ c, const double* __restrict__ e, long long count) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x)
@@ -784,7 +813,7 @@ __global__ void check_kernel(const double* __restrict__ norm2, CheckState* st, c
   if (st->nhist < 128) st->hist[st->nhist++] = rel;
   st->rel = rel;
   int stop = 0;
-  if (!isfinite(rel) || rel > 1e6) { st->status = -5; stop = 1; }
+  if (!isfinite(rel) || (st->diverge > 0.0 && rel > st->diverge)) { st->status = -5; stop = 1; }
   else if (rel <= st->tol) { st->status = 0; stop = 1; }
   else if (st->it >= st->max_iter) { st->status = -4; stop = 1; }
   if (stop) {
@@ -1030,6 +1059,18 @@ cudaError_t launch_correct(const CorrectArgs& a, const DevTaps& t, int threads, 
   if (R == 8) return launch_correct_t<double, 8>(a, t, threads, s);
   if (R == 4) return launch_correct_t<double, 4>(a, t, threads, s);
   return launch_correct_t<double, 0>(a, t, threads, s);
+}
+
+cudaError_t launch_residual_value(const double* c_new, double* r, double* partial, int nx, int N, cudaStream_t s) {
+  if (N < 2) return cudaSuccess;
+  residual_value_kernel<<<N - 1, nx >= 512 ? 512 : ((nx + 31) / 32) * 32, 0, s>>>(c_new, r, partial, nx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_value_batched(const BatchSolve* S, const BatchItem* items, int nitems, cudaStream_t s) {
+  if (nitems < 1) return cudaSuccess;
+  residual_value_batched_kernel<<<nitems, 256, 0, s>>>(S, items);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_norm(const double* partial, int n, double* out, cudaStream_t s) {

@@ -13,6 +13,9 @@ template <int KF, int KB>
 cudaError_t sdirk_fcf_batched(const BatchSolve* S, const BatchItem* items, int nitems, const SdirkPlan& any,
                               size_t smem, int precision, cudaStream_t s);
 template <int KF, int KB>
+cudaError_t sdirk_coarse_march(const double* g, const float* g_f, double* c_add, int nx, int P, const SdirkPlan& p,
+                               cudaStream_t s);
+template <int KF, int KB>
 cudaError_t sdirk_steps(const double* in, long long in_stride, double* out, long long out_stride, int count, int nx,
                         int steps, int store_every, int store_first, const SdirkPlan& p, double* partial,
                         cudaStream_t s);
@@ -91,6 +94,12 @@ cudaError_t launch_seq_sdirk(const double* u0, double* out, int nx, int P, int s
   return with_orders(p, [&]<int KF, int KB>() {
     return sdirk_steps<KF, KB>(u0, 0, out, 0, 1, nx, P - 1, store_every, 1, p, nullptr, s);
   });
+}
+
+cudaError_t launch_coarse_march_sdirk(const double* g, const float* g_f, double* c_add, int nx, int P,
+                                      const SdirkPlan& p, cudaStream_t s) {
+  if (P < 2) return cudaSuccess;
+  return with_orders(p, [&]<int KF, int KB>() { return sdirk_coarse_march<KF, KB>(g, g_f, c_add, nx, P, p, s); });
 }
 
 }  // namespace mg

@@ -287,7 +287,7 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const SdirkPlan& p, i
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       const double v = slab[pix(i)];
       cn[i] = v;
-      const double rho = v - (a.zero_old ? 0.0 : oldj[i]);
+      const double rho = a.value_residual ? v : v - (a.zero_old ? 0.0 : oldj[i]);
       slab[pix(i)] = rho;
       nz |= rho != 0.0;
     }
@@ -300,6 +300,7 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const SdirkPlan& p, i
       rr[i] = v;
       ss = fma(v, v, ss);
     }
+    if (a.value_residual) return;  // Phi^m c_new_j stored; residual_value finishes
   } else {
     // each thread owns points i = tid + k*blockDim (k < C): read all FP64
     // values before the FP32 slab (same storage) is written
@@ -408,6 +409,31 @@ __global__ void __launch_bounds__(512) steps_sdirk_kernel(const double* in, long
   }
 }
 
+// Two-level coarse solve with an SDIRK step: e_0 = 0, e_n = Phi e_{n-1} + g_n,
+// c_add[n] += e_n (one CTA, sequential in n).
+template <int C, int KF, int KB>
+__global__ void __launch_bounds__(512) coarse_march_sdirk_kernel(const double* g, const float* g_f, double* c_add,
+                                                                 int nx, int P, const SdirkPlan p) {
+  extern __shared__ __align__(256) unsigned char smraw[];
+  __shared__ __align__(16) double smw[2 * 16 * kMaxRec];
+  const Smem sm = carve(smraw, p);
+  load_tables(p, sm);
+  double* slab = sm.slab;
+  const int plen = padded_len(nx);
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) slab[pix(i)] = 0.0;
+  __syncthreads();
+  for (int n = 1; n < P; ++n) {
+    if (n > 1) sdirk_step<double, C, KF, KB>(p, slab, plen, nx, sm.t64, smw);  // Phi 0 = 0
+    const long long o = (long long)n * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const double e = slab[pix(i)] + (g_f ? (double)g_f[o + i] : g[o + i]);
+      slab[pix(i)] = e;
+      c_add[o + i] += e;
+    }
+    __syncthreads();
+  }
+}
+
 template <typename Kern>
 static cudaError_t smem_attr(Kern kernel, size_t bytes) {
   if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -475,11 +501,25 @@ cudaError_t sdirk_steps(const double* in, long long in_stride, double* out, long
   });
 }
 
+template <int KF, int KB>
+cudaError_t sdirk_coarse_march(const double* g, const float* g_f, double* c_add, int nx, int P, const SdirkPlan& p,
+                               cudaStream_t s) {
+  const size_t smem = sdirk_smem(p);
+  return sd::with_chunk(p.C, [&]<int C>() -> cudaError_t {
+    cudaError_t e = sd::smem_attr(sd::coarse_march_sdirk_kernel<C, KF, KB>, smem);
+    if (e != cudaSuccess) return e;
+    sd::coarse_march_sdirk_kernel<C, KF, KB><<<1, p.threads, smem, s>>>(g, g_f, c_add, nx, P, p);
+    return cudaGetLastError();
+  });
+}
+
 #define MG_SDIRK_INSTANTIATE(KF, KB)                                                                             \
   template cudaError_t sdirk_fcf<KF, KB>(const FcfArgs&, const SdirkPlan&, int, cudaStream_t);                   \
   template cudaError_t sdirk_fcf_batched<KF, KB>(const BatchSolve*, const BatchItem*, int, const SdirkPlan&,      \
                                                  size_t, int, cudaStream_t);                                     \
   template cudaError_t sdirk_steps<KF, KB>(const double*, long long, double*, long long, int, int, int, int, int, \
-                                           const SdirkPlan&, double*, cudaStream_t);
+                                           const SdirkPlan&, double*, cudaStream_t);                              \
+  template cudaError_t sdirk_coarse_march<KF, KB>(const double*, const float*, double*, int, int, const SdirkPlan&, \
+                                                  cudaStream_t);
 
 }  // namespace mg

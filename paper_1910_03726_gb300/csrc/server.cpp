@@ -216,6 +216,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     b.fcf.N = h->Nl[1];
     b.fcf.zero_old = 0;
     b.fcf.relax_f = h->opts.relax == MGRIT_RELAX_F;
+    b.fcf.value_residual = fine_prec(h) == 0 && !b.fcf.relax_f;
     b.prec = fine_prec(h);
     b.taps = 2 * k;
     b.psi = 2 * k + 1;
@@ -270,6 +271,11 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     if (e != cudaSuccess) return launch_ok(e, "fcf_sdirk_batched");
     for (int k : g.second) act[k]->h->kcount[MGRIT_K_FCF]++;
   }
+  // ---- value-form residuals of the FP64 solves (no-op for the others)
+  {
+    cudaError_t e = launch_residual_value_batched(S->dS.p, S->dItems.p, (int)items.size(), S->stream);
+    if (e != cudaSuccess) return launch_ok(e, "residual_value_batched");
+  }
   // ---- norms of all solves, one read-back
   std::vector<int> ids(n);
   for (int k = 0; k < n; ++k) ids[k] = k;
@@ -300,7 +306,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     if (r->res.n_history < MGRIT_MAX_HISTORY) r->res.history[r->res.n_history++] = rel;
     r->res.rel_residual = rel;
     r->res.iterations = r->it;
-    if (!std::isfinite(rel) || rel > 1e6) {
+    if (!std::isfinite(rel) || (rel > 1e6 && !(r->opts.flags & MGRIT_FLAG_NO_DIVERGENCE_STOP))) {
       r->status = MGRIT_ERR_DIVERGED;
       r->error = "residual not finite or grew above 1e6 x initial";
       (*done)[k] = 1;
@@ -311,7 +317,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
       r->status = MGRIT_ERR_NOT_CONVERGED;
       r->error = "max_iter reached";
       (*done)[k] = 1;
-    } else if (r->h->L == 2) {
+    } else if (r->h->L == 2 && !r->h->redisc) {
       by_cluster[r->h->march_cluster].push_back(k);
     }
   }
@@ -335,7 +341,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
   for (int k = 0; k < n; ++k) {
     Request* r = act[k];
     if ((*done)[k]) continue;
-    if (r->h->L > 2) {
+    if (r->h->L > 2 || r->h->redisc) {
       mgrit_status st = coarse_cycle(r->h, r->h->c[1 - r->cur]);
       if (st != MGRIT_OK) {
         r->status = st;

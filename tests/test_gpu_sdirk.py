@@ -140,3 +140,25 @@ def test_sdirk_fcycle_and_f_relaxation_parity(capi, p, nx, nt, m, L, cycle, rela
         capi.mgrit_destroy(h)
     assert res.iterations == it
     assert rel(out, U[::m]) <= TOL
+
+
+@pytest.mark.parametrize("p,m", [(1, 2), (2, 4), (3, 2), (4, 4)])
+def test_rediscretised_coarse_step_matches_oracle(capi, p, m):
+    """PSI_REDISC (Table 2): the coarse propagator is one SDIRKp+Up step at
+    m dt, i.e. CFL number m c."""
+    import torch
+    nx, k, count = 256, 2, 3
+    opts = capi.mgrit_opts_default(m=m, levels=2, psi_rule=capi.PSI_REDISC)
+    h = capi.mgrit_setup(capi.problem(nx, 64, "SDIRK", p, p, 4.0), opts)
+    try:
+        x = np.random.default_rng(p + m).standard_normal((count, nx))
+        xin = torch.tensor(x, device="cuda")
+        yout = torch.zeros_like(xin)
+        capi.mgrit_propagate(h, 2, k, count, xin, yout)
+    finally:
+        capi.mgrit_destroy(h)
+    st = stepping.FineStep("SDIRK", p, 4.0 * m, nx)
+    ref = x.copy()
+    for _ in range(k):
+        ref = st(ref)
+    assert rel(yout.cpu().numpy(), ref) <= TOL

@@ -134,3 +134,58 @@ def test_warm_start_from_the_solution_stops_at_once(capi):
         capi.mgrit_destroy(h)
     assert res.iterations == 0 and res.rel_residual <= 1e-12
     assert float(np.max(np.abs(out - cpts))) <= 1e-12 * float(np.max(np.abs(cpts)))
+
+
+@pytest.mark.parametrize("fam,p,c", [("ERK", 1, 0.85), ("SDIRK", 2, 4.0)])
+@pytest.mark.parametrize("scale", [0.3, 0.9])
+def test_finite_termination_with_any_psi(capi, fam, p, c, scale):
+    """Section 1 / Table 2's right-hand side: whatever Psi is, FCF-MGRIT is
+    exact after n_t/(2m) iterations.  With a random Psi the residual first
+    grows by up to 1e80; the FP64 path still stops after exactly n_t/(2m)
+    iterations, as the oracle does (its C-points are bitwise those of
+    sequential stepping once reached)."""
+    nx, nt, m = 64, 512, 4
+    rng = np.random.default_rng(3)
+    offs = list(range(-3, 2))
+    coefs = [float(rng.standard_normal()) * scale for _ in offs]
+    st = stepping.FineStep(fam, p, c, nx)
+    U = workloads.random_iterate(nt, nx, workloads.sin4(nx), 11)
+    r0 = float(np.linalg.norm(omg.spacetime_residual(U, np.zeros_like(U), st)))
+    it, _ = omg.solve(omg.make_levels(st, m, [dict(zip(offs, coefs))]), U.copy(), max_iter=200)
+    assert it == nt // (2 * m)
+    for flags in (capi.FLAG_NO_DIVERGENCE_STOP, capi.FLAG_NO_DIVERGENCE_STOP | capi.FLAG_HOST_LOOP):
+        opts = capi.mgrit_opts_default(m=m, levels=2, psi_rule=capi.PSI_USER, max_iter=200, flags=flags)
+        keep = capi.user_psi(opts, [(offs, coefs)])
+        h = capi.mgrit_setup(capi.problem(nx, nt, fam, p, p, c), opts)
+        try:
+            res, _ = capi.mgrit_solve_from(h, np.ascontiguousarray(U[::m]), r0)
+        finally:
+            capi.mgrit_destroy(h)
+        del keep
+        assert res.iterations == it, (flags, res.iterations, it)
+
+
+def test_table2_rediscretised_sdirk(capi):
+    """Table 2: two-level MGRIT with Psi = the SDIRK step at m dt diverges
+    (iterations near the exact-arithmetic bound n_t/(2m)).  At 2^8 x 2^8 the
+    GPU's counts equal the oracle's on the same random iterate; at 2^10 x 2^10
+    they lie within 2 of the printed ones (SDIRK1+U1, whose counts are far
+    below the bound, within 1)."""
+    flags = capi.FLAG_NO_DIVERGENCE_STOP
+    for p in (1, 2, 3, 4):
+        for m in (2, 4):
+            nx = nt = 256
+            st = stepping.FineStep("SDIRK", p, 4.0, nx)
+            U, cpts, r0 = random_start(st, nt, nx, m)
+            it, _ = omg.solve(omg.make_levels(st, m, [stepping.FineStep("SDIRK", p, 4.0 * m, nx)]), U.copy(),
+                              max_iter=300)
+            opts = capi.mgrit_opts_default(m=m, levels=2, psi_rule=capi.PSI_REDISC, max_iter=300, flags=flags)
+            res = gpu_iterations(capi, capi.problem(nx, nt, "SDIRK", p, p, 4.0), opts, cpts, r0)
+            assert res.iterations == it, (p, m, res.iterations, it)
+    for r in golden("table2_rediscretized.txt"):
+        p, nx, nt, m, v = int(r[0]), int(r[1]), int(r[2]), int(r[3]), int(r[4])
+        st = stepping.FineStep("SDIRK", p, 4.0, nx)
+        U, cpts, r0 = random_start(st, nt, nx, m)
+        opts = capi.mgrit_opts_default(m=m, levels=2, psi_rule=capi.PSI_REDISC, max_iter=400, flags=flags)
+        res = gpu_iterations(capi, capi.problem(nx, nt, "SDIRK", p, p, 4.0), opts, cpts, r0)
+        assert res.converged == 1 and abs(res.iterations - v) <= (1 if p == 1 else 2), (p, m, res.iterations, v)
