@@ -321,6 +321,68 @@ def paper_parallel_variant(capi, stream):
     return out
 
 
+def exact_cpoints(nx, nt, m, c, device):
+    """Exact solution of Eq. 1 (alpha = 1) at the C-points t_j = j m dt for the
+    Fourier-field initial condition: u0(x - t) as a product of the per-time
+    mode amplitudes and the spatial modes (angle addition), on the device."""
+    import torch
+    a, b = workloads.fourier_coefficients()
+    K = len(a)
+    k = torch.arange(1, K + 1, dtype=torch.float64, device=device)
+    x = torch.tensor(workloads.grid(nx), device=device)
+    t = torch.arange(0, nt + 1, m, dtype=torch.float64, device=device) * (c * 2.0 / nx)
+    ak = torch.tensor(a, device=device) / k ** 2
+    bk = torch.tensor(b, device=device) / k ** 2
+    ct, st = torch.cos(torch.pi * t[:, None] * k), torch.sin(torch.pi * t[:, None] * k)
+    A = ak * ct - bk * st                    # coefficient of cos(k pi x) at time t
+    B = ak * st + bk * ct                    # coefficient of sin(k pi x)
+    return A @ torch.cos(torch.pi * k[:, None] * x) + B @ torch.sin(torch.pi * k[:, None] * x)
+
+
+def disc_error_variant(capi, stream):
+    """Time to discretization-error accuracy (Section 5's second stopping
+    criterion): the fewest MGRIT iterations whose C-points are within 1% of
+    sequential stepping's own error against the exact solution, on the
+    paper's parallel configurations (MIXED, V-cycles, m = 4), against GPU
+    sequential stepping."""
+    import torch
+    out = {}
+    for p, (nt, L, _) in TABLE4_MAX.items():
+        nx, m = 4096, 4
+        c = 0.85 * CMAX_TABLE1[p]
+        prob = capi.problem(nx, nt, "ERK", p, p, c)
+        u0 = torch.tensor(workloads.fourier_field(nx), device="cuda")
+        ex = exact_cpoints(nx, nt, m, c, "cuda")
+        nrm = float(torch.linalg.norm(ex))
+        seq = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
+        hs = capi.mgrit_setup(prob, capi.mgrit_opts_default(m=m, levels=L, min_coarse=4), stream=stream)
+        capi.mgrit_sequential(hs, u0, seq)
+        seq_s = capi.mgrit_sequential(hs, u0, seq)
+        capi.mgrit_destroy(hs)
+        e_d = float(torch.linalg.norm(seq - ex)) / nrm
+        row = {"discretization_error_rel": e_d, "gpu_sequential_ms": 1e3 * seq_s}
+        cp = torch.empty_like(seq)
+        for k in range(1, 30):
+            o = capi.mgrit_opts_default(m=m, levels=L, precision=capi.PREC_MIXED, tol=TOL, max_iter=k, min_coarse=4)
+            h = capi.mgrit_setup(prob, o, stream=stream)
+            try:
+                capi.mgrit_solve(h, u0, cp, allow_not_converged=True)
+                err = float(torch.linalg.norm(cp - ex)) / nrm
+                if err <= 1.01 * e_d:
+                    ts = []
+                    for _ in range(3):
+                        r, _ = capi.mgrit_solve(h, u0, None, allow_not_converged=True)
+                        ts.append(r.solve_s)
+                    row.update({"iterations": k, "error_rel": err, "ms": 1e3 * statistics.median(ts),
+                                "dof_per_s": nx * nt / statistics.median(ts),
+                                "speedup_vs_gpu_sequential": seq_s / statistics.median(ts)})
+                    break
+            finally:
+                capi.mgrit_destroy(h)
+        out[f"ERK{p}+U{p}"] = row
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -492,6 +554,7 @@ def main():
         capi.mgrit_destroy(hs)
         extra["sdirk3_u5_8192"] = sdirk_variant(capi, sp, 3)
         extra["paper_parallel_configs"] = paper_parallel_variant(capi, sp)
+        extra["paper_configs_to_discretization_error"] = disc_error_variant(capi, sp)
         if args.batch > 0:
             extra["batch_uneven"] = batch_variant(capi, args.batch, sp)
         if args.serve > 0:

@@ -189,3 +189,47 @@ def test_table2_rediscretised_sdirk(capi):
         opts = capi.mgrit_opts_default(m=m, levels=2, psi_rule=capi.PSI_REDISC, max_iter=400, flags=flags)
         res = gpu_iterations(capi, capi.problem(nx, nt, "SDIRK", p, p, 4.0), opts, cpts, r0)
         assert res.converged == 1 and abs(res.iterations - v) <= (1 if p == 1 else 2), (p, m, res.iterations, v)
+
+
+def _iterations_to_discretization_accuracy(run, exact, e_d, kmax=20):
+    for k in range(1, kmax):
+        if np.linalg.norm(run(k) - exact) / np.linalg.norm(exact) <= 1.01 * e_d:
+            return k
+    return None
+
+
+@pytest.mark.parametrize("p,nx,nt,L", [(1, 256, 1024, 4), (3, 256, 512, 3), (5, 256, 512, 3)])
+def test_iterations_to_discretization_accuracy(capi, p, nx, nt, L):
+    """Section 5's second stopping criterion: the fewest iterations whose
+    C-points are within 1% of sequential stepping's own error against the
+    exact solution u0(x - t) of Eq. 1.  GPU (FP64 and MIXED) and oracle need
+    the same number, no more than for a 1e-10 residual."""
+    m = 4
+    c = schemes.cfl_number("ERK", p)
+    st = stepping.FineStep("ERK", p, c, nx)
+    u0 = workloads.fourier_field(nx)
+    dt = c * 2.0 / nx
+    exact = np.array([workloads.fourier_field(nx, shift=j * m * dt) for j in range(nt // m + 1)])
+    e_d = np.linalg.norm(stepping.sequential(st, u0, nt)[::m] - exact) / np.linalg.norm(exact)
+    ops = opsi.build_hierarchy("ERK", p, c, nx, nt, m, L, rule="auto")
+    lev = omg.make_levels(st, m, [o.diag for o in ops])
+
+    def oracle(k):
+        U = omg.zero_iterate(u0, nt)
+        omg.solve(lev, U, max_iter=k)
+        return U[::m]
+    k_or = _iterations_to_discretization_accuracy(oracle, exact, e_d)
+    for prec in (0, 1):
+        def gpu(k):
+            h = capi.mgrit_setup(capi.problem(nx, nt, "ERK", p, p, c),
+                                 capi.mgrit_opts_default(m=m, levels=L, max_iter=k, min_coarse=4, precision=prec))
+            try:
+                out = np.zeros((nt // m + 1, nx))
+                capi.mgrit_solve(h, u0, out, allow_not_converged=True)
+            finally:
+                capi.mgrit_destroy(h)
+            return out
+        k = _iterations_to_discretization_accuracy(gpu, exact, e_d)
+        assert k is not None and k == k_or, (prec, k, k_or)
+    it10, _ = omg.solve(lev, omg.zero_iterate(u0, nt))
+    assert k_or <= it10

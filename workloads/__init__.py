@@ -31,16 +31,24 @@ def sin4(nx: int) -> np.ndarray:
     return np.sin(np.pi * grid(nx)) ** 4
 
 
-def fourier_field(nx: int, seed: int = SEED_FOURIER_FIELD, modes: int = 64) -> np.ndarray:
-    """Random smooth periodic field: sum over k = 1..modes of
-    (a_k cos(k pi x) + b_k sin(k pi x)) / k^2 with a_k, b_k ~ N(0, 1).
-
-    The period-2 domain makes k*pi the k-th wavenumber.
-    """
+def fourier_coefficients(seed: int = SEED_FOURIER_FIELD, modes: int = 64):
+    """The (a_k, b_k), k = 1..modes, of the random Fourier field."""
     rng = np.random.Generator(np.random.PCG64(seed))
     a = rng.standard_normal(modes)
     b = rng.standard_normal(modes)
-    x = grid(nx)
+    return a, b
+
+
+def fourier_field(nx: int, seed: int = SEED_FOURIER_FIELD, modes: int = 64, shift: float = 0.0) -> np.ndarray:
+    """Random smooth periodic field: sum over k = 1..modes of
+    (a_k cos(k pi x) + b_k sin(k pi x)) / k^2 with a_k, b_k ~ N(0, 1),
+    sampled at x_i - shift (shift = alpha t gives the exact solution of Eq. 1
+    at time t for this initial condition).
+
+    The period-2 domain makes k*pi the k-th wavenumber.
+    """
+    a, b = fourier_coefficients(seed, modes)
+    x = grid(nx) - shift
     u = np.zeros(nx)
     for k in range(1, modes + 1):
         u += (a[k - 1] * np.cos(k * np.pi * x) + b[k - 1] * np.sin(k * np.pi * x)) / (k * k)
