@@ -174,6 +174,7 @@ def run_server(capi, reqs, times, budget):
     completion) and results."""
     srv = capi.mgrit_server_create(budget)
     tickets = []
+    stats = None
     try:
         t0 = time.perf_counter()
         for i, (prob, opts, u0) in enumerate(reqs):
@@ -193,10 +194,11 @@ def run_server(capi, reqs, times, budget):
             if pending:
                 time.sleep(0.001)
         wall = time.perf_counter() - t0
+        stats = capi.mgrit_server_stats(srv)
     finally:
         capi.mgrit_server_destroy(srv)
     lat = [r.solve_s for st, r in results]
-    return wall, lat, results
+    return wall, lat, results, stats
 
 
 def batch_variant(capi, count, stream):
@@ -207,7 +209,7 @@ def batch_variant(capi, count, stream):
     specs = workloads.batch_specs(count)
     reqs = [mix_request(capi, s, TOL, capi.PREC_MIXED) for s in specs]
     dof = sum(s["nx"] * s["nt"] for s in specs)
-    wall, lat, results = run_server(capi, reqs, None, 150e9)
+    wall, lat, results, stats = run_server(capi, reqs, None, 150e9)
     ok = sum(1 for st, r in results if st == 0 and r.converged)
     its = [r.iterations for st, r in results]
     sample = specs[:32]
@@ -232,7 +234,8 @@ def batch_variant(capi, count, stream):
             "plain_fp64_alone_dof_per_s": dof_s / t_fp64, "gpu_sequential_dof_per_s": dof_s / t_seq,
             "baseline_sample": f"first {len(sample)} solves of the batch, each alone (solve time only, setup "
                                f"excluded)", "budget_bytes": 150e9,
-            "mix": "nx 256..4096, nt 1024..16384, p 1..5, ERK or SDIRK, m 4/8/16 (seed 4), two-level, tol 1e-10"}
+            "mix": "nx 256..4096, nt 1024..16384, p 1..5, ERK or SDIRK, m 4/8/16 (seed 4), two-level, tol 1e-10",
+            "server_stats": stats}
 
 
 def serving_variant(capi, rates, count):
@@ -244,11 +247,12 @@ def serving_variant(capi, rates, count):
         specs = workloads.batch_specs(count, seed=workloads.SEED_ARRIVALS * 7 + int(rate))
         reqs = [mix_request(capi, s, float(t), capi.PREC_MIXED) for s, t in zip(specs, tols)]
         dof = sum(s["nx"] * s["nt"] for s in specs)
-        wall, lat, results = run_server(capi, reqs, times, 150e9)
+        wall, lat, results, stats = run_server(capi, reqs, times, 150e9)
         ok = sum(1 for st, r in results if st == 0 and r.converged)
         out[f"{rate:g}/s"] = {"requests": count, "converged": ok, "wall_s": wall, "dof_per_s": dof / wall,
                               "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
-                                             "p99": 1e3 * float(np.percentile(lat, 99))}}
+                                             "p99": 1e3 * float(np.percentile(lat, 99))},
+                              "server_stats": stats}
     return out
 
 

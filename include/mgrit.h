@@ -284,6 +284,20 @@ mgrit_status mgrit_submit(mgrit_server* s, const mgrit_problem* prob, const mgri
  * MGRIT_ERR_UNKNOWN_TICKET. */
 mgrit_status mgrit_poll(mgrit_server* s, uint64_t ticket, double* out, mgrit_result* res);
 
+/* Counters of a server since its creation (observability). */
+typedef struct mgrit_server_counters {
+  uint64_t submitted, completed, failed;  /* requests                          */
+  uint64_t cycles;              /* batched MGRIT cycles run                   */
+  double admit_s;               /* worker time admitting (set-up, uploads)     */
+  double plan_s;                /*   of which fitting coarse operators         */
+  double tune_s;                /*   of which timing launch shapes             */
+  double cycle_s;               /* worker time in cycles                      */
+  double retire_s;              /* worker time retiring (output copies)        */
+  double mean_active;           /* average solves per cycle                    */
+  double peak_resident_bytes;   /* largest device state held at once           */
+} mgrit_server_counters;
+mgrit_status mgrit_server_stats(mgrit_server* s, mgrit_server_counters* out);
+
 void mgrit_server_destroy(mgrit_server* s);
 
 /* ------------------------------------------------- no-allocation variant */

@@ -40,7 +40,7 @@ K_KINDS = len(KERNEL_KINDS)
 EXPORTED = ["mgrit_opts_default", "mgrit_set_allocator", "mgrit_phi_taps", "mgrit_psi_plan",
             "mgrit_setup", "mgrit_solve", "mgrit_solve_from", "mgrit_sequential", "mgrit_propagate", "mgrit_psi_info",
             "mgrit_device_bytes", "mgrit_destroy", "mgrit_server_create", "mgrit_submit",
-            "mgrit_poll", "mgrit_server_destroy", "mgrit_fcf_residual_static", "mgrit_last_error",
+            "mgrit_poll", "mgrit_server_stats", "mgrit_server_destroy", "mgrit_fcf_residual_static", "mgrit_last_error",
             "mgrit_abi_version"]
 
 
@@ -74,6 +74,16 @@ class MgritResult(C.Structure):
         d["kernel_count"] = {KERNEL_KINDS[i]: self.kernel_count[i] for i in range(K_KINDS)}
         d["kernel_ms"] = {KERNEL_KINDS[i]: self.kernel_ms[i] for i in range(K_KINDS)}
         return d
+
+
+class MgritServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("cycles", C.c_uint64), ("admit_s", C.c_double), ("plan_s", C.c_double), ("tune_s", C.c_double),
+                ("cycle_s", C.c_double),
+                ("retire_s", C.c_double), ("mean_active", C.c_double), ("peak_resident_bytes", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class MgritServerOpts(C.Structure):
@@ -117,6 +127,7 @@ _sig("mgrit_destroy", None, _vp)
 _sig("mgrit_server_create", _i32, _P(MgritServerOpts), _vp, _P(_vp))
 _sig("mgrit_submit", _i32, _vp, _P(MgritProblem), _P(MgritOpts), _vp, _P(C.c_uint64))
 _sig("mgrit_poll", _i32, _vp, C.c_uint64, _vp, _P(MgritResult))
+_sig("mgrit_server_stats", _i32, _vp, _P(MgritServerStats))
 _sig("mgrit_server_destroy", None, _vp)
 _sig("mgrit_fcf_residual_static", _i32, _vp, _vp, _vp, _vp, _i32, _i32, _i32, _i32, _P(_i32), _P(_f64), _i32, _vp)
 _sig("mgrit_last_error", C.c_char_p)
@@ -292,6 +303,12 @@ def mgrit_poll(s, ticket, out=None):
     r = MgritResult()
     st = _lib.mgrit_poll(s, C.c_uint64(ticket), _ptr(out), C.byref(r))
     return st, r
+
+
+def mgrit_server_stats(s):
+    st = MgritServerStats()
+    _check(_lib.mgrit_server_stats(s, C.byref(st)))
+    return st.as_dict()
 
 
 def mgrit_server_destroy(s):

@@ -619,7 +619,9 @@ void autotune_fine(mgrit_handle* h) {
   f.r_f = h->rf[1];
   f.partial = h->partial;
   f.nx = nx;
-  f.N = std::min(h->Nl[1], 4096);  // the real interval count: wave quantisation matters
+  // a sample of the handle's intervals, large enough (12 per SM) that the last
+  // wave's share is small for every CTA size
+  f.N = std::min(h->Nl[1], 12 * 152);
   // nonzero trial data (every byte 0x3F: each double is 4.8e-4), so that no
   // interval takes the zero-slab shortcut while it is timed
   cudaMemsetAsync(h->c[0], 0x3F, ((size_t)f.N + 1) * nx * sizeof(double), h->stream);
@@ -628,37 +630,51 @@ void autotune_fine(mgrit_handle* h) {
     cudaGetLastError();
     return;
   }
+  // candidates: the shapes that can win (wide collapsed stencils chunked or
+  // sliding; step by step fixed-span or chunked; one tap at a time only for
+  // stencils without a dense form)
+  struct Cand { int collapse, tile, threads; };
+  std::vector<Cand> cands;
+  for (Cand c : {Cand{1, kChunkTile, 256}, Cand{1, kChunkTile, 512}, Cand{1, 8, 256}, Cand{0, kFixedTile, 256},
+                 Cand{0, kFixedTile, 512}, Cand{0, kChunkTile, 256}, Cand{0, 8, 256}, Cand{0, 0, 128}, Cand{0, 0, 256}})
+    if (valid(c.collapse, c.tile)) cands.push_back(c);
+  bool dense_found = false;
+  for (const Cand& c : cands) dense_found |= c.tile != 0;
   float best = 1e30f;
   TunePick pick{0, h->fine_tile, h->fine_threads};
-  for (int collapse : {0, 1})
-    for (int tile : {kFixedTile, kChunkTile, 8, 4, 0}) {
-      if (!valid(collapse, tile) || (collapse && tile == 0)) continue;
-      const DevTaps& t = collapse ? h->dphim : h->dphi;
-      f.m = collapse ? 1 : h->m;
-      const int per = tile == kFixedTile ? 4 : (tile == kChunkTile ? 8 : (tile > 0 ? tile : 1));
-      for (int th : {128, 256, 512}) {
-        if (th > std::max(32, (nx / per + 31) / 32 * 32)) continue;
-        if (launch_fcf(f, t, prec, th, h->stream, tile) != cudaSuccess) {
-          cudaGetLastError();
-          continue;
-        }
-        float tm = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {
-          cudaEventRecord(e0, h->stream);
-          launch_fcf(f, t, prec, th, h->stream, tile);
-          cudaEventRecord(e1, h->stream);
-          float ms = 0.0f;
-          if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
-            tm = std::min(tm, ms);
-          else
-            cudaGetLastError();
-        }
-        if (tm < best) {
-          best = tm;
-          pick = {collapse, tile, th};
-        }
+  bool warmed = false;
+  for (const Cand& c : cands) {
+    if (c.tile == 0 && dense_found) continue;
+    const DevTaps& t = c.collapse ? h->dphim : h->dphi;
+    f.m = c.collapse ? 1 : h->m;
+    const int per = c.tile == kFixedTile ? 4 : (c.tile == kChunkTile ? 8 : (c.tile > 0 ? c.tile : 1));
+    if (c.threads > std::max(32, (nx / per + 31) / 32 * 32)) continue;
+    if (!warmed) {
+      if (launch_fcf(f, t, prec, c.threads, h->stream, c.tile) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
       }
+      warmed = true;
     }
+    float tm = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, h->stream);
+      if (launch_fcf(f, t, prec, c.threads, h->stream, c.tile) != cudaSuccess) {
+        cudaGetLastError();
+        break;
+      }
+      cudaEventRecord(e1, h->stream);
+      float ms = 0.0f;
+      if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+        tm = std::min(tm, ms);
+      else
+        cudaGetLastError();
+    }
+    if (tm < best) {
+      best = tm;
+      pick = {c.collapse, c.tile, c.threads};
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->fine_collapse = pick.collapse;
@@ -698,7 +714,7 @@ size_t handle_bytes(const mgrit_problem* prob, const mgrit_opts* opts) {
 }
 
 mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cudaStream_t stream,
-                           const std::vector<CoarseOp>* ops, mgrit_handle** out) {
+                           const std::vector<CoarseOp>* ops, mgrit_handle** out, bool sync) {
   *out = nullptr;
   const double t0 = now_s();
   mgrit_status st = validate_problem(prob);
@@ -881,8 +897,10 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
   const Taps& coarsest = h->ops.back().taps;
   h->march_cluster = pick_cluster(nx, coarsest);
   h->march_threads = std::min(256, nx / h->march_cluster);
+  const double tt = now_s();
   autotune_fine(h);
-  cudaError_t e = cudaStreamSynchronize(h->stream);
+  h->tune_s = now_s() - tt;
+  cudaError_t e = sync ? cudaStreamSynchronize(h->stream) : cudaGetLastError();
   if (e != cudaSuccess) {
     release(h);
     delete h;
@@ -983,6 +1001,15 @@ mgrit_status run_march(mgrit_handle* h, const MarchArgs& a, const DevTaps& t) {
 
 // ||Phi u0||: residual of the zero initial iterate (only time level 1 is nonzero).
 mgrit_status initial_residual(mgrit_handle* h, const double* u0dev, double* r0) {
+  mgrit_status st = initial_residual_async(h, u0dev);
+  if (st != MGRIT_OK) return st;
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  *r0 = std::sqrt(h->norm_host[0]);
+  return MGRIT_OK;
+}
+
+// Enqueue ||Phi u0||^2 into h->norm_host[0] (read after a stream sync).
+mgrit_status initial_residual_async(mgrit_handle* h, const double* u0dev) {
   mgrit_status st;
   double* out = h->scratch;
   double* part = h->scratch + h->nx;
@@ -994,8 +1021,6 @@ mgrit_status initial_residual(mgrit_handle* h, const double* u0dev, double* r0) 
        })) != MGRIT_OK)
     return st;
   CUDA_TRY(cudaMemcpyAsync(h->norm_host, part, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  CUDA_TRY(cudaStreamSynchronize(h->stream));
-  *r0 = std::sqrt(h->norm_host[0]);
   return MGRIT_OK;
 }
 

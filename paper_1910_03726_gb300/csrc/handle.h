@@ -63,6 +63,7 @@ struct mgrit_handle {
   std::vector<int> evkind;      // kind of each recorded (start, stop) pair
   size_t evused = 0;
   double setup_s = 0.0, op_complexity = 0.0;
+  double tune_s = 0.0;            // of setup_s: timing launch shapes
   size_t bytes = 0;
 };
 
@@ -85,10 +86,12 @@ cudaEvent_t next_event(mgrit_handle* h);
 void collect_stats(mgrit_handle* h, mgrit_result* R);
 mgrit_status run_march(mgrit_handle* h, const mg::MarchArgs& a, const mg::DevTaps& t);
 mgrit_status initial_residual(mgrit_handle* h, const double* u0dev, double* r0);
+mgrit_status initial_residual_async(mgrit_handle* h, const double* u0dev);
 mgrit_status coarse_cycle(mgrit_handle* h, double* c_new);
 // Build a handle; ops != nullptr supplies an already fitted hierarchy.
 mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cudaStream_t stream,
-                           const std::vector<mg::CoarseOp>* ops, mgrit_handle** out);
+                           const std::vector<mg::CoarseOp>* ops, mgrit_handle** out,
+                           bool sync = true);
 // Device bytes a handle for this request will allocate (admission control).
 size_t handle_bytes(const mgrit_problem* prob, const mgrit_opts* opts);
 // SDIRK stage-solve plan for the problem (factored stage matrix), checked on

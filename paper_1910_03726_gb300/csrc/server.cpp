@@ -103,7 +103,18 @@ struct mgrit_server {
   bool stop = false;
   uint64_t next_ticket = 1;
   size_t resident = 0;
-  std::map<PlanKey, std::vector<CoarseOp>> plans;
+  // Coarse operators per problem shape, fitted by a pool of host threads as
+  // requests arrive (so the worker never fits one while the GPU waits).
+  struct PlanEntry {
+    int state = 0;  // 0 pending, 1 ready, 2 failed
+    std::vector<CoarseOp> ops;
+    mgrit_status st = MGRIT_OK;
+    std::string msg;
+  };
+  std::map<PlanKey, PlanEntry> plans;  // guarded by mu; entries are never erased
+  std::deque<std::tuple<PlanKey, mgrit_problem, mgrit_opts>> plan_jobs;
+  std::vector<std::thread> planners;
+  std::condition_variable plan_cv;
   DevArray<BatchSolve> dS;
   DevArray<BatchItem> dItems;
   DevArray<DevTaps> dTaps;
@@ -112,6 +123,8 @@ struct mgrit_server {
   double* hNorm = nullptr;
   size_t hNormCap = 0;
   std::string fatal;
+  mgrit_server_counters stats{};
+  double active_sum = 0.0;
 };
 
 static PlanKey key_of(const mgrit_problem& p, const mgrit_opts& o) {
@@ -131,6 +144,8 @@ static void finish(mgrit_server* S, Request* r, mgrit_status st, const std::stri
     r->h = nullptr;
     S->resident -= std::min(S->resident, r->bytes);
   }
+  if (st == MGRIT_OK) S->stats.completed++;
+  else S->stats.failed++;
   r->res.solve_s = now_s() - r->t_submit;
   r->res.dof_per_s = r->res.solve_s > 0 ? (double)r->prob.nx * r->prob.nt / r->res.solve_s : 0.0;
   r->state = 2;
@@ -143,26 +158,21 @@ static std::vector<Request*> admit(mgrit_server* S, std::unique_lock<std::mutex>
   const size_t max_active = S->o.max_active > 0 ? (size_t)S->o.max_active : 4096;
   while (!S->queue.empty() && S->active.size() + fresh.size() < max_active) {
     Request* r = S->queue.front();
+    const auto itp = S->plans.find(key_of(r->prob, r->opts));
+    if (itp == S->plans.end() || itp->second.state == 0) break;  // its operators are still being fitted
+    if (itp->second.state == 2) {
+      S->queue.pop_front();
+      finish(S, r, itp->second.st, itp->second.msg);
+      S->cv.notify_all();
+      continue;
+    }
     if ((double)(S->resident + r->bytes) > S->o.hbm_budget_bytes && !(S->active.empty() && fresh.empty())) break;
     S->queue.pop_front();
     S->resident += r->bytes;
+    const std::vector<CoarseOp>* cached = &itp->second.ops;
     lk.unlock();
-    const PlanKey key = key_of(r->prob, r->opts);
-    const std::vector<CoarseOp>* cached = nullptr;
-    {
-      auto itp = S->plans.find(key);
-      if (itp != S->plans.end()) cached = &itp->second;
-    }
-    mgrit_status st = MGRIT_OK;
-    std::vector<CoarseOp> ops;
-    if (!cached && r->opts.psi_rule != MGRIT_PSI_USER) {
-      st = plan(&r->prob, &r->opts, &ops);
-      if (st == MGRIT_OK) {
-        S->plans[key] = ops;
-        cached = &S->plans[key];
-      }
-    }
-    if (st == MGRIT_OK) st = handle_create(&r->prob, &r->opts, S->stream, cached, &r->h);
+    mgrit_status st = handle_create(&r->prob, &r->opts, S->stream, cached, &r->h, false);
+    if (st == MGRIT_OK) S->stats.tune_s += r->h->tune_s;
     std::string msg = st == MGRIT_OK ? "" : mgrit_last_error();
     if (st == MGRIT_OK) {
       mgrit_handle* h = r->h;
@@ -175,9 +185,8 @@ static std::vector<Request*> admit(mgrit_server* S, std::unique_lock<std::mutex>
       r->res.n_levels = h->L;
       r->res.setup_s = h->setup_s;
       r->res.op_complexity = h->op_complexity;
-      st = initial_residual(h, h->c[0], &r->r0);
+      st = initial_residual_async(h, h->c[0]);  // read after the admission batch's one sync
       if (st != MGRIT_OK) msg = mgrit_last_error();
-      r->res.r0_norm = r->r0;
     }
     lk.lock();
     if (st != MGRIT_OK) {
@@ -188,9 +197,23 @@ static std::vector<Request*> admit(mgrit_server* S, std::unique_lock<std::mutex>
       continue;
     }
     S->resident = S->resident - std::min(S->resident, r->bytes) + r->h->bytes;
+    S->stats.peak_resident_bytes = std::max(S->stats.peak_resident_bytes, (double)S->resident);
     r->bytes = r->h->bytes;
     r->state = 1;
     fresh.push_back(r);
+  }
+  if (!fresh.empty()) {  // one sync for the batch: set-up errors and the initial residuals
+    lk.unlock();
+    const cudaError_t e = cudaStreamSynchronize(S->stream);
+    lk.lock();
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      S->fatal = std::string("admission: ") + cudaGetErrorString(e);
+    }
+    for (Request* r : fresh) {
+      r->r0 = std::sqrt(r->h->norm_host[0]);
+      r->res.r0_norm = r->r0;
+    }
   }
   return fresh;
 }
@@ -371,7 +394,49 @@ static void retire(mgrit_server* S, Request* r) {
     }
   }
   collect_stats(h, &r->res);
-  finish(S, r, r->status, r->error);
+  mgrit_destroy(h);  // device state released here, accounted under the lock by the caller
+  r->h = nullptr;
+  r->res.solve_s = now_s() - r->t_submit;
+  r->res.dof_per_s = r->res.solve_s > 0 ? (double)r->prob.nx * r->prob.nt / r->res.solve_s : 0.0;
+}
+
+// Under the lock: a retired request becomes visible to pollers.
+static void publish(mgrit_server* S, Request* r) {
+  S->resident -= std::min(S->resident, r->bytes);
+  if (r->status == MGRIT_OK) S->stats.completed++;
+  else S->stats.failed++;
+  r->state = 2;
+}
+
+// The queue's head can be admitted or failed (its operators are fitted).
+static bool head_ready(mgrit_server* S) {
+  if (S->queue.empty()) return false;
+  const auto it = S->plans.find(key_of(S->queue.front()->prob, S->queue.front()->opts));
+  return it != S->plans.end() && it->second.state != 0;
+}
+
+static void planner_main(mgrit_server* S) {
+  std::unique_lock<std::mutex> lk(S->mu);
+  for (;;) {
+    S->plan_cv.wait(lk, [&] { return S->stop || !S->plan_jobs.empty(); });
+    if (S->stop) return;
+    auto job = S->plan_jobs.front();
+    S->plan_jobs.pop_front();
+    lk.unlock();
+    const double t0 = now_s();
+    std::vector<CoarseOp> ops;
+    const mgrit_status st = plan(&std::get<1>(job), &std::get<2>(job), &ops);
+    const std::string msg = st == MGRIT_OK ? "" : mgrit_last_error();
+    const double dt = now_s() - t0;
+    lk.lock();
+    auto& e = S->plans[std::get<0>(job)];
+    e.ops = std::move(ops);
+    e.st = st;
+    e.msg = msg;
+    e.state = st == MGRIT_OK ? 1 : 2;
+    S->stats.plan_s += dt;
+    S->cv.notify_all();
+  }
 }
 
 static void worker_main(mgrit_server* S) {
@@ -390,17 +455,21 @@ static void worker_main(mgrit_server* S) {
       S->cv.wait(lk, [&] { return S->stop || !S->queue.empty(); });
       continue;
     }
+    const double ta = now_s();
     std::vector<Request*> fresh = admit(S, lk);
+    S->stats.admit_s += now_s() - ta;
     for (Request* r : fresh) S->active.push_back(r);
     if (S->active.empty()) {
       S->cv.notify_all();
-      S->cv.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+      S->cv.wait(lk, [&] { return S->stop || head_ready(S); });
       continue;
     }
     std::vector<Request*> act = S->active;
     lk.unlock();
     std::vector<char> done(act.size(), 0);
+    const double tc = now_s();
     mgrit_status st = cycle(S, act, &done);
+    const double tr = now_s();
     std::string msg = st == MGRIT_OK ? "" : mgrit_last_error();
     if (st != MGRIT_OK)
       for (size_t k = 0; k < act.size(); ++k) {
@@ -410,7 +479,15 @@ static void worker_main(mgrit_server* S) {
       }
     for (size_t k = 0; k < act.size(); ++k)
       if (done[k]) retire(S, act[k]);
+    const double te = now_s();
     lk.lock();
+    for (size_t k = 0; k < act.size(); ++k)
+      if (done[k]) publish(S, act[k]);
+    S->stats.cycles++;
+    S->stats.cycle_s += tr - tc;
+    S->stats.retire_s += te - tr;
+    S->active_sum += (double)act.size();
+    S->stats.mean_active = S->active_sum / (double)S->stats.cycles;
     std::vector<Request*> keep;
     for (size_t k = 0; k < act.size(); ++k)
       if (!done[k]) keep.push_back(act[k]);
@@ -434,6 +511,9 @@ extern "C" mgrit_status mgrit_server_create(const mgrit_server_opts* sopts, void
   S->o = *sopts;
   S->stream = (cudaStream_t)stream;
   S->worker = std::thread(worker_main, S);
+  const unsigned hc = std::thread::hardware_concurrency();
+  const unsigned np = std::max(1u, std::min(8u, hc > 2 ? hc - 2 : 1u));
+  for (unsigned k = 0; k < np; ++k) S->planners.emplace_back(planner_main, S);
   *out = S;
   return MGRIT_OK;
 }
@@ -470,6 +550,13 @@ extern "C" mgrit_status mgrit_submit(mgrit_server* S, const mgrit_problem* prob,
   {
     std::lock_guard<std::mutex> lk(S->mu);
     r->ticket = S->next_ticket++;
+    S->stats.submitted++;
+    const PlanKey key = key_of(r->prob, r->opts);
+    if (S->plans.find(key) == S->plans.end()) {
+      S->plans[key];  // pending
+      S->plan_jobs.emplace_back(key, r->prob, r->opts);
+      S->plan_cv.notify_one();
+    }
     S->reqs[r->ticket] = r;
     S->queue.push_back(r);
     *ticket = r->ticket;
@@ -504,6 +591,13 @@ extern "C" mgrit_status mgrit_poll(mgrit_server* S, uint64_t ticket, double* out
   return st;
 }
 
+extern "C" mgrit_status mgrit_server_stats(mgrit_server* S, mgrit_server_counters* out) {
+  if (!S || !out) return fail(MGRIT_ERR_INVALID, "server and out must be non-NULL");
+  std::lock_guard<std::mutex> lk(S->mu);
+  *out = S->stats;
+  return MGRIT_OK;
+}
+
 extern "C" void mgrit_server_destroy(mgrit_server* S) {
   if (!S) return;
   {
@@ -511,7 +605,10 @@ extern "C" void mgrit_server_destroy(mgrit_server* S) {
     S->stop = true;
   }
   S->cv.notify_all();
+  S->plan_cv.notify_all();
   if (S->worker.joinable()) S->worker.join();
+  for (auto& t : S->planners)
+    if (t.joinable()) t.join();
   for (auto& kv : S->reqs) delete kv.second;
   S->reqs.clear();
   S->dS.free();
