@@ -55,7 +55,7 @@ typedef enum mgrit_status {
   MGRIT_ERR_OOM = -7,             /* device allocation failed                      */
   MGRIT_ERR_TIMEOUT = -8,         /* a bounded device wait ran out                 */
   MGRIT_ERR_CUDA = -9,            /* CUDA runtime error                            */
-  MGRIT_ERR_UNSUPPORTED = -10,    /* valid request this build does not implement   */
+  MGRIT_ERR_UNSUPPORTED = -10,    /* valid request the library does not implement  */
   MGRIT_ERR_UNKNOWN_TICKET = -11  /* mgrit_poll: ticket never issued or released   */
 } mgrit_status;
 
