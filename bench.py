@@ -387,6 +387,24 @@ def disc_error_variant(capi, stream):
     return out
 
 
+def replica_max(total_ms, world, device="cuda"):
+    """Max over ranks of each rank's timed total (ms); one all-reduce when the
+    job runs N > 1 independent replicas (torchrun, NCCL on GPUs, gloo on CPU)."""
+    if world <= 1:
+        return total_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_value(world, dof_per_step, steps, max_total_ms):
+    """Whole-job throughput: the DOF of all ranks' timed steps over the slowest
+    rank's time (weak scaling: each replica solves the full problem)."""
+    return world * dof_per_step * steps / (max_total_ms * 1e-3)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -461,12 +479,11 @@ def main():
             e1[k].record(stream)
             results.append(r)
         torch.cuda.synchronize()
-        lat = [a.elapsed_time(b) for a, b in zip(e0, e1)]
-        total = sum(lat)
         if world > 1:
-            t = torch.tensor([total], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
+            dist.barrier()
+        torch.cuda.synchronize()
+        lat = [a.elapsed_time(b) for a, b in zip(e0, e1)]
+        total = replica_max(sum(lat), world)
         return lat, total, results
 
     clocks = ClockSampler(local)
@@ -478,7 +495,7 @@ def main():
     clk = clocks.stop()
     res0 = results[-1]
     graph_res = res0
-    value = world * NX * NT * args.steps / (total * 1e-3)
+    value = replicas_value(world, NX * NT, args.steps, total)
     launches = sum(r.launches for r in results)
     # ---- e2e through the C ABI with host buffers (u0 in, C-points out)
     u0_host = np.ascontiguousarray(u0_np)
