@@ -325,6 +325,52 @@ def paper_parallel_variant(capi, stream):
     return out
 
 
+# Table 5's largest grids (inflow/outflow, Section 4.5): p -> (nt, most levels, V-cycle counts L = 2..)
+TABLE5_MAX = {1: (16384, 7, (6, 7, 7, 7, 7, 7)), 3: (8192, 6, (6, 7, 7, 7, 7)), 5: (8192, 6, (5, 5, 5, 5, 5))}
+
+
+def inflow_variant(capi, stream):
+    """Inflow/outflow boundaries (Section 4.5, Table 5's 2^12 grids): ERKp+Up,
+    p = 1, 3, 5, V-cycles with m = 4 and the most levels Table 5 lists; MIXED
+    and FP64 solves beside the same configuration with periodic boundaries
+    (the cost of the boundary rows) and GPU sequential stepping of the closed
+    problem; iterations beside Table 5's (random initial iterate there, zero
+    here)."""
+    import torch
+    out = {}
+    for p, (nt, L, t5) in TABLE5_MAX.items():
+        nx = 4096
+        c = 0.85 * CMAX_TABLE1[p]
+        u0 = torch.tensor(workloads.fourier_field(nx), device="cuda")
+        row = {"nx": nx, "nt": nt, "levels": L, "m": 4, "table5_iterations": t5[L - 2]}
+        for bc in ("inflow", "periodic"):
+            prob = capi.problem(nx, nt, "ERK", p, p, c, boundary=bc)
+            for name, prec in (("mixed", capi.PREC_MIXED), ("fp64", capi.PREC_FP64)):
+                if bc == "periodic" and name == "fp64":
+                    continue
+                o = capi.mgrit_opts_default(m=4, levels=L, precision=prec, tol=TOL, output=capi.OUT_FINAL,
+                                            max_iter=50, min_coarse=4)
+                h = capi.mgrit_setup(prob, o, stream=stream)
+                try:
+                    capi.mgrit_solve(h, u0, None)
+                    ts = []
+                    for _ in range(3):
+                        r, _ = capi.mgrit_solve(h, u0, None)
+                        ts.append(r.solve_s)
+                    key = name if bc == "inflow" else f"periodic_{name}"
+                    row[key] = {"ms": 1e3 * statistics.median(ts), "dof_per_s": nx * nt / statistics.median(ts),
+                                "iterations": r.iterations}
+                    if bc == "inflow" and name == "fp64":
+                        fin = torch.empty(nx, dtype=torch.float64, device="cuda")
+                        row["gpu_sequential_ms"] = 1e3 * capi.mgrit_sequential(h, u0, fin)
+                finally:
+                    capi.mgrit_destroy(h)
+        row["speedup_vs_gpu_sequential"] = row["gpu_sequential_ms"] / row["mixed"]["ms"]
+        row["cost_vs_periodic"] = row["mixed"]["ms"] / row["periodic_mixed"]["ms"]
+        out[f"ERK{p}+U{p}"] = row
+    return out
+
+
 def exact_cpoints(nx, nt, m, c, device):
     """Exact solution of Eq. 1 (alpha = 1) at the C-points t_j = j m dt for the
     Fourier-field initial condition: u0(x - t) as a product of the per-time
@@ -417,7 +463,7 @@ def main():
                     help="arithmetic of the headline solve")
     ap.add_argument("--batch", type=int, default=4096, help="solves in the uneven batch (0: skip)")
     ap.add_argument("--serve", type=int, default=400, help="requests per arrival rate (0: skip)")
-    ap.add_argument("--only", choices=["sdirk", "batch", "serve"],
+    ap.add_argument("--only", choices=["sdirk", "batch", "serve", "inflow"],
                     help="run just this variant and print its JSON (no headline line)")
     ap.add_argument("--host-loop", action="store_true",
                     help="with --only sdirk: drive cycles from the host (kernels visible to ncu)")
@@ -447,7 +493,8 @@ def main():
         run = {"sdirk": lambda: sdirk_variant(capi, sp, args.steps,
                                               capi.FLAG_HOST_LOOP if args.host_loop else 0),
                "batch": lambda: batch_variant(capi, args.batch, sp),
-               "serve": lambda: serving_variant(capi, (100, 1000, 3000, 10000), args.serve)}[args.only]
+               "serve": lambda: serving_variant(capi, (100, 1000, 3000, 10000), args.serve),
+               "inflow": lambda: inflow_variant(capi, sp)}[args.only]
         print(json.dumps({args.only: run()}), flush=True)
         return
     u0_np = workloads.fourier_field(NX)
@@ -576,6 +623,7 @@ def main():
         extra["sdirk3_u5_8192"] = sdirk_variant(capi, sp, 3)
         extra["paper_parallel_configs"] = paper_parallel_variant(capi, sp)
         extra["paper_configs_to_discretization_error"] = disc_error_variant(capi, sp)
+        extra["inflow_outflow_table5_configs"] = inflow_variant(capi, sp)
         if args.batch > 0:
             extra["batch_uneven"] = batch_variant(capi, args.batch, sp)
         if args.serve > 0:

@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MGRIT_ABI_VERSION 3
+#define MGRIT_ABI_VERSION 4
 #define MGRIT_MAX_LEVELS 8
 #define MGRIT_MAX_HISTORY 128
 #define MGRIT_MAX_TAPS 256
@@ -60,6 +60,21 @@ typedef enum mgrit_status {
 } mgrit_status;
 
 enum { MGRIT_ERK = 0, MGRIT_SDIRK = 1 };
+
+/* Spatial boundary conditions.
+ *  PERIODIC  Eq. 1 on the periodic interval (every operator a circulant).
+ *  INFLOW    Section 4.5: inflow at x = -1 with zero inflow data (the
+ *            homogeneous problem), no condition at the outflow x = 1; the
+ *            unknowns are x_i = -1 + (i+1) dx, i = 0..nx-1 (the outflow point
+ *            included).  Every Runge-Kutta stage sees zero ghost values left
+ *            of the domain and, right of it, the values of the degree-q
+ *            polynomial (q = upwind_order) through the last q+1 unknowns.
+ *            Psi is the periodic problem's fit truncated at both ends
+ *            (Toeplitz).  ERK only; not with MGRIT_PSI_IDEAL; the two ends'
+ *            closures must stay apart: nx >= 2 s q + q + 2 for s stages and
+ *            nx > the widest Psi's offset range (MGRIT_ERR_UNSUPPORTED
+ *            otherwise).  Iteration counts: Table 5. */
+enum { MGRIT_BC_PERIODIC = 0, MGRIT_BC_INFLOW = 1 };
 
 /* Arithmetic of the relaxation (Section 2.2 reading, see the library notes):
  *  FP64   every step in FP64.
@@ -129,12 +144,12 @@ enum {
 };
 
 typedef struct mgrit_problem {
-  int32_t nx;            /* spatial points (periodic), >= 8                       */
+  int32_t nx;            /* spatial points, >= 8                                   */
   int32_t nt;            /* time steps; divisible by m^(levels-1)                  */
   int32_t family;        /* MGRIT_ERK or MGRIT_SDIRK                               */
   int32_t rk_order;      /* ERK 1..5, SDIRK 1..4 (Appendix A)                      */
   int32_t upwind_order;  /* U1..U5 (Section 2.1)                                   */
-  int32_t reserved;
+  int32_t boundary;      /* MGRIT_BC_* (0 = periodic)                              */
   double cfl;            /* c = alpha dt / dx (> 0)                                */
 } mgrit_problem;
 
@@ -204,9 +219,19 @@ void mgrit_set_allocator(mgrit_alloc_fn alloc, mgrit_free_fn release, void* ctx)
 
 /* Taps of the fine propagator Phi as one circulant stencil (Corollary 1):
  * (Phi v)_r = sum_k coeffs[k] v_{r + offsets[k]}.  ERK only (SDIRK's Phi is
- * dense).  cap = capacity of the arrays.  No GPU is touched. */
+ * dense).  cap = capacity of the arrays.  No GPU is touched.  For
+ * MGRIT_BC_INFLOW these are Phi's interior rows. */
 mgrit_status mgrit_phi_taps(const mgrit_problem* prob, int32_t cap, int32_t* ntaps,
                             int32_t* offsets, double* coeffs);
+
+/* Rows of the fine propagator Phi of an MGRIT_BC_INFLOW problem that differ
+ * from its interior stencil (Section 4.5), as the library builds them: dims
+ * receives {nl, cl, nr, cr}: rows 0..nl-1 over columns 0..cl-1 and rows
+ * nx-nr..nx-1 over columns nx-cr..nx-1; w (capacity cap doubles) receives the
+ * coefficients row-major, the left block first (nl*cl + nr*cr values).  Every
+ * other row r is sum_k coeffs[k] v_{r + offsets[k]} of mgrit_phi_taps.  ERK
+ * only.  No GPU is touched. */
+mgrit_status mgrit_phi_boundary(const mgrit_problem* prob, int32_t cap, int32_t* dims, double* w);
 
 /* Coarse operators Psi_2..Psi_L that mgrit_setup would build (Eq. 6 on the
  * rule's pattern, recursively per level, Section 4.4).  nnz[levels-1];

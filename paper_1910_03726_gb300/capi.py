@@ -23,6 +23,7 @@ STATUS = {0: "OK", 1: "PENDING", -1: "ERR_INVALID", -2: "ERR_UNSTABLE", -3: "ERR
           -4: "ERR_NOT_CONVERGED", -5: "ERR_DIVERGED", -6: "ERR_OVER_BUDGET", -7: "ERR_OOM",
           -8: "ERR_TIMEOUT", -9: "ERR_CUDA", -10: "ERR_UNSUPPORTED", -11: "ERR_UNKNOWN_TICKET"}
 ERK, SDIRK = 0, 1
+BC_PERIODIC, BC_INFLOW = 0, 1
 PREC_FP64, PREC_MIXED, PREC_MIXED_DF = 0, 1, 2
 PSI_AUTO, PSI_HALFWIDTH, PSI_THRESHOLD, PSI_USER, PSI_IDEAL, PSI_REDISC = 0, 1, 2, 3, 4, 5
 OUT_FINAL, OUT_CPOINTS, OUT_FULL = 0, 1, 2
@@ -37,7 +38,7 @@ FLAG_NO_DIVERGENCE_STOP = 8
 KERNEL_KINDS = ["fcf", "fcf_coarse", "march", "correct", "norm", "add", "propagate", "other"]
 K_KINDS = len(KERNEL_KINDS)
 
-EXPORTED = ["mgrit_opts_default", "mgrit_set_allocator", "mgrit_phi_taps", "mgrit_psi_plan",
+EXPORTED = ["mgrit_opts_default", "mgrit_set_allocator", "mgrit_phi_taps", "mgrit_phi_boundary", "mgrit_psi_plan",
             "mgrit_setup", "mgrit_solve", "mgrit_solve_from", "mgrit_sequential", "mgrit_propagate", "mgrit_psi_info",
             "mgrit_device_bytes", "mgrit_destroy", "mgrit_server_create", "mgrit_submit",
             "mgrit_poll", "mgrit_server_stats", "mgrit_server_destroy", "mgrit_fcf_residual_static", "mgrit_last_error",
@@ -46,7 +47,7 @@ EXPORTED = ["mgrit_opts_default", "mgrit_set_allocator", "mgrit_phi_taps", "mgri
 
 class MgritProblem(C.Structure):
     _fields_ = [("nx", C.c_int32), ("nt", C.c_int32), ("family", C.c_int32), ("rk_order", C.c_int32),
-                ("upwind_order", C.c_int32), ("reserved", C.c_int32), ("cfl", C.c_double)]
+                ("upwind_order", C.c_int32), ("boundary", C.c_int32), ("cfl", C.c_double)]
 
 
 class MgritOpts(C.Structure):
@@ -115,6 +116,7 @@ ALLOC_FN = C.CFUNCTYPE(_vp, C.c_size_t, _vp, _vp)
 FREE_FN = C.CFUNCTYPE(None, _vp, _vp, _vp)
 _sig("mgrit_set_allocator", None, ALLOC_FN, FREE_FN, _vp)
 _sig("mgrit_phi_taps", _i32, _P(MgritProblem), _i32, _P(_i32), _P(_i32), _P(_f64))
+_sig("mgrit_phi_boundary", _i32, _P(MgritProblem), _i32, _P(_i32), _P(_f64))
 _sig("mgrit_psi_plan", _i32, _P(MgritProblem), _P(MgritOpts), _i32, _P(_i32), _P(_i32), _P(_f64), _P(_f64))
 _sig("mgrit_setup", _i32, _P(MgritProblem), _P(MgritOpts), _vp, _P(_vp))
 _sig("mgrit_solve", _i32, _vp, _vp, _vp, _P(MgritResult))
@@ -164,9 +166,10 @@ def _ptr(x):
 
 # ------------------------------------------------------------------ helpers
 
-def problem(nx, nt, family="ERK", rk_order=1, upwind_order=None, cfl=0.85):
+def problem(nx, nt, family="ERK", rk_order=1, upwind_order=None, cfl=0.85, boundary=BC_PERIODIC):
     fam = ERK if family in ("ERK", ERK) else SDIRK
-    return MgritProblem(nx, nt, fam, rk_order, upwind_order or rk_order, 0, float(cfl))
+    bc = BC_INFLOW if boundary in ("inflow", BC_INFLOW) else BC_PERIODIC
+    return MgritProblem(nx, nt, fam, rk_order, upwind_order or rk_order, bc, float(cfl))
 
 
 def mgrit_opts_default(**overrides):
@@ -209,6 +212,18 @@ def mgrit_phi_taps(prob, cap=1024):
     cfs = (C.c_double * cap)()
     _check(_lib.mgrit_phi_taps(C.byref(prob), cap, C.byref(n), offs, cfs))
     return list(offs[: n.value]), list(cfs[: n.value])
+
+
+def mgrit_phi_boundary(prob, cap=1 << 14):
+    """Boundary rows of an inflow/outflow problem's Phi: (left block (nl, cl),
+    right block (nr, cr)) as numpy arrays."""
+    import numpy as np
+    dims = (C.c_int32 * 4)()
+    w = (C.c_double * cap)()
+    _check(_lib.mgrit_phi_boundary(C.byref(prob), cap, dims, w))
+    nl, cl, nr, cr = (int(v) for v in dims)
+    a = np.array(w[: nl * cl + nr * cr])
+    return a[: nl * cl].reshape(nl, cl), a[nl * cl:].reshape(nr, cr)
 
 
 def mgrit_psi_plan(prob, opts, cap=1 << 16):

@@ -32,6 +32,18 @@ struct DevTaps {
 // Fill a DevTaps from n (offset, coefficient) pairs; false if n > kMaxDevTaps.
 bool make_dev_taps(const int* off, const double* coef, int n, DevTaps* out);
 
+// Rows of a level's operator that differ from its circulant on the
+// non-periodic domain (Section 4.5): rows 0..nl-1 read columns 0..cl-1, rows
+// nx-nr..nx-1 read columns nx-cr..nx-1; coefficients row-major, left block
+// first, in FP64 (w64) and FP32 (w32), device memory.  The stencil kernels
+// compute every row as the circulant and then overwrite these rows
+// ("fix-up"); nl = nr = 0 (periodic) skips it.
+struct Fixup {
+  int nl, cl, nr, cr;
+  const double* w64;
+  const float* w32;
+};
+
 // FCF-relaxation of one level with the fused C-point residual.
 // Interval j = 1..N starts at C-point j-1.  For every j the kernel computes
 //   v_j   = m steps of u <- T u + g from u_old[C(j-1)]   (F- then C-relaxation)
@@ -58,6 +70,7 @@ struct FcfArgs {
   float* c_new_f;
   const float* g_f;
   float* r_f;
+  Fixup fx;                // boundary rows of T (non-periodic problems)
 };
 
 // Sequential march u_n = T u_{n-1} + g_n, n = 1..P-1, on one thread-block
@@ -71,6 +84,11 @@ struct MarchArgs {
   int nx, P;
   const float* g_f;        // FP32 right-hand side (replaces g when set)
   float* u_out_f;          // FP32 output (replaces u_out when set)
+  // Non-periodic (truncated Toeplitz) T: the march runs on a zero-padded
+  // periodic domain of nxp >= nx + max(-lo, hi) points whose points nx..nxp-1
+  // are held at zero, which truncates every row at both ends exactly.
+  // 0 = periodic (nxp = nx).
+  int nxp;
 };
 
 // Correction and F-relaxation (ideal interpolation) of one level:
@@ -88,6 +106,7 @@ struct CorrectArgs {
   const float* e_f;
   const float* g_f;
   float* u_f;
+  Fixup fx;                // boundary rows of T (non-periodic problems)
 };
 
 // tile: register tile (0, 4 or 8), kFixedTile for the fixed-span path of the
@@ -213,7 +232,13 @@ cudaError_t launch_residual_value_batched(const BatchSolve* S, const BatchItem* 
 cudaError_t launch_add(double* c, const double* e, long long count, cudaStream_t s);
 cudaError_t launch_add_f(double* c, const float* e, long long count, cudaStream_t s);
 cudaError_t launch_propagate(const double* in, double* out, int count, int nx, int k,
-                             const DevTaps& t, double* partial, int threads, cudaStream_t s);
+                             const DevTaps& t, double* partial, int threads, cudaStream_t s,
+                             const Fixup* fx = nullptr);
+// Sequential stepping of a non-periodic level on one CTA (the slab stays in
+// shared memory): u_n = T u_{n-1}, n = 1..P-1, u_n stored at
+// out + (n/store_every)*nx when n % store_every == 0 (u_0 is not written).
+cudaError_t launch_seq_slab(const double* u0, double* out, int nx, int P, int store_every, const DevTaps& t,
+                            const Fixup& fx, int threads, cudaStream_t s);
 int march_max_cluster();
 void set_tile(int r);   // register tile of the stencil kernels: 8, 4 or 0
 int get_tile();

@@ -167,6 +167,10 @@ mgrit_status validate_problem(const mgrit_problem* p) {
     return fail(MGRIT_ERR_INVALID, "SDIRK order must be 1..4");
   if (p->upwind_order < 1 || p->upwind_order > 5) return fail(MGRIT_ERR_INVALID, "upwind order must be 1..5");
   if (!(p->cfl > 0.0) || !std::isfinite(p->cfl)) return fail(MGRIT_ERR_INVALID, "cfl must be > 0");
+  if (p->boundary != MGRIT_BC_PERIODIC && p->boundary != MGRIT_BC_INFLOW)
+    return fail(MGRIT_ERR_INVALID, "unknown boundary");
+  if (p->boundary == MGRIT_BC_INFLOW && p->family != MGRIT_ERK)
+    return fail(MGRIT_ERR_UNSUPPORTED, "inflow/outflow boundaries are implemented for ERK only");
   if (p->family == MGRIT_ERK && p->rk_order == p->upwind_order) {
     // Table 1 limits as printed (last digit rounded up)
     static const double cmax[6] = {0, 1.0, 0.5, 1.62590, 1.04450, 1.96584};
@@ -196,6 +200,8 @@ mgrit_status validate_opts(const mgrit_problem* p, const mgrit_opts* o) {
   if (o->output < 0 || o->output > 2) return fail(MGRIT_ERR_INVALID, "unknown output");
   if (o->psi_rule == MGRIT_PSI_IDEAL && (p->family != MGRIT_ERK || o->levels != 2))
     return fail(MGRIT_ERR_INVALID, "PSI_IDEAL needs ERK and two levels");
+  if (o->psi_rule == MGRIT_PSI_IDEAL && p->boundary == MGRIT_BC_INFLOW)
+    return fail(MGRIT_ERR_UNSUPPORTED, "PSI_IDEAL is the periodic Phi^m; not for inflow/outflow boundaries");
   if (o->psi_rule == MGRIT_PSI_REDISC && (p->family != MGRIT_SDIRK || o->levels != 2))
     return fail(MGRIT_ERR_INVALID, "PSI_REDISC needs SDIRK and two levels");
   if (o->psi_rule < MGRIT_PSI_AUTO || o->psi_rule > MGRIT_PSI_REDISC) return fail(MGRIT_ERR_INVALID, "unknown psi_rule");
@@ -247,6 +253,20 @@ extern "C" mgrit_status mgrit_phi_taps(const mgrit_problem* prob, int32_t cap, i
     if (offsets) offsets[k] = t.off[k];
     if (coeffs) coeffs[k] = t.coef[k];
   }
+  return MGRIT_OK;
+}
+
+extern "C" mgrit_status mgrit_phi_boundary(const mgrit_problem* prob, int32_t cap, int32_t* dims, double* w) {
+  mgrit_status st = validate_problem(prob);
+  if (st != MGRIT_OK) return st;
+  if (prob->boundary != MGRIT_BC_INFLOW) return fail(MGRIT_ERR_INVALID, "the problem is periodic");
+  const BoundaryRows B = inflow_phi_rows(prob->rk_order, prob->upwind_order, prob->cfl, prob->nx);
+  if (B.nl + B.nr == 0) return fail(MGRIT_ERR_UNSUPPORTED, "nx too small for the boundary closures");
+  if (dims) {
+    dims[0] = B.nl; dims[1] = B.cl; dims[2] = B.nr; dims[3] = B.cr;
+  }
+  if ((int)B.w.size() > cap) return fail(MGRIT_ERR_INVALID, "capacity too small");
+  if (w) std::copy(B.w.begin(), B.w.end(), w);
   return MGRIT_OK;
 }
 
@@ -555,9 +575,9 @@ int fine_prec(const mgrit_handle* h) {
 
 namespace {
 struct TuneKey {
-  int prec, nx, span, ntaps, m;
+  int prec, nx, span, ntaps, m, inflow;
   bool operator<(const TuneKey& o) const {
-    return std::tie(prec, nx, span, ntaps, m) < std::tie(o.prec, o.nx, o.span, o.ntaps, o.m);
+    return std::tie(prec, nx, span, ntaps, m, inflow) < std::tie(o.prec, o.nx, o.span, o.ntaps, o.m, o.inflow);
   }
 };
 struct TunePick {
@@ -600,7 +620,7 @@ void autotune_fine(mgrit_handle* h) {
       return;
     }
   }
-  const TuneKey key{prec, nx, h->dphi.span, h->dphi.n, h->m};
+  const TuneKey key{prec, nx, h->dphi.span, h->dphi.n, h->m, h->inflow ? 1 : 0};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
@@ -619,6 +639,7 @@ void autotune_fine(mgrit_handle* h) {
   f.r_f = h->rf[1];
   f.partial = h->partial;
   f.nx = nx;
+  f.fx = h->fx_phi;
   // a sample of the handle's intervals, large enough (12 per SM) that the last
   // wave's share is small for every CTA size
   f.N = std::min(h->Nl[1], 12 * 152);
@@ -686,12 +707,49 @@ void autotune_fine(mgrit_handle* h) {
 
 cudaError_t launch_fine_fcf(mgrit_handle* h, const FcfArgs& f, int prec) {
   if (h->sdirk) return launch_fcf_sdirk(f, h->splan, prec == 0 ? 0 : 1, h->stream);
+  FcfArgs g = f;
+  g.fx = h->fx_phi;  // boundary rows (inflow/outflow; never with the collapsed Phi^m)
   if (h->fine_collapse) {  // each pass is one application of Phi^m
-    FcfArgs g = f;
     g.m = 1;
     return launch_fcf(g, h->dphim, prec, h->fine_threads, h->stream, h->fine_tile);
   }
-  return launch_fcf(f, h->dphi, prec, h->fine_threads, h->stream, h->fine_tile);
+  return launch_fcf(g, h->dphi, prec, h->fine_threads, h->stream, h->fine_tile);
+}
+
+// Boundary rows of Phi (stage-wise closures) and of every truncated Psi_l,
+// FP64 then FP32, in one device table (inflow/outflow problems).
+static mgrit_status upload_boundaries(mgrit_handle* h) {
+  const int nx = h->nx;
+  std::vector<BoundaryRows> rows;
+  rows.push_back(inflow_phi_rows(h->prob.rk_order, h->prob.upwind_order, h->prob.cfl, nx));
+  if (rows[0].nl + rows[0].nr == 0) return fail(MGRIT_ERR_UNSUPPORTED, "nx too small for the boundary closures");
+  for (const CoarseOp& op : h->ops) {
+    if (nx < op.taps.hi() - op.taps.lo() + 1)
+      return fail(MGRIT_ERR_UNSUPPORTED, "a coarse stencil is wider than the domain");
+    rows.push_back(truncated_rows(op.taps, nx));
+  }
+  std::vector<double> w64;
+  for (const BoundaryRows& b : rows) w64.insert(w64.end(), b.w.begin(), b.w.end());
+  const size_t n = std::max<size_t>(w64.size(), 1);
+  double* tab = nullptr;
+  mgrit_status st = dalloc(h, n + (n + 1) / 2, &tab);
+  if (st != MGRIT_OK) return st;
+  float* tab32 = reinterpret_cast<float*>(tab + n);
+  const std::vector<float> w32(w64.begin(), w64.end());
+  if (!w64.empty()) {
+    CUDA_TRY(cudaMemcpyAsync(tab, w64.data(), w64.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    // pageable sources: the copies have staged them when they return
+    CUDA_TRY(cudaMemcpyAsync(tab32, w32.data(), w32.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  }
+  size_t pos = 0;
+  for (size_t k = 0; k < rows.size(); ++k) {
+    const BoundaryRows& b = rows[k];
+    const Fixup f = {b.nl, b.cl, b.nr, b.cr, tab + pos, tab32 + pos};
+    if (k == 0) h->fx_phi = f;
+    else h->fx_psi[k - 1] = f;
+    pos += b.w.size();
+  }
+  return MGRIT_OK;
 }
 
 size_t handle_bytes(const mgrit_problem* prob, const mgrit_opts* opts) {
@@ -775,7 +833,8 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
       return fail(MGRIT_ERR_UNSUPPORTED, "coarse stencil wider than 256 taps");
     }
   h->dphi = to_dev(h->phi);
-  if (!h->sdirk) {  // Phi^m as one stencil (the m-step propagator of an interval)
+  h->inflow = prob->boundary == MGRIT_BC_INFLOW;
+  if (!h->sdirk && !h->inflow) {  // Phi^m as one stencil (the m-step propagator of an interval)
     Taps pm = taps_power(h->phi, h->m);
     const int reach = std::max(-pm.lo(), pm.hi());
     if (pm.size() <= kMaxDevTaps && pm.size() + 8 < h->nx && reach + 8 < h->nx) {  // indices wrap at most once
@@ -855,6 +914,12 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
     delete h;
     return st;
   }
+  h->fx_psi.assign(h->ops.size(), Fixup{});
+  if (h->inflow && (st = upload_boundaries(h)) != MGRIT_OK) {
+    release(h);
+    delete h;
+    return st;
+  }
   if (cudaMallocHost(&h->norm_host, 8 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     release(h);
@@ -895,8 +960,13 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
   h->fcf_threads = 0;  // chosen per launch from nx and the register tile
   if (const char* tile = std::getenv("MGRIT_TILE")) set_tile(std::atoi(tile));
   const Taps& coarsest = h->ops.back().taps;
-  h->march_cluster = pick_cluster(nx, coarsest);
-  h->march_threads = std::min(256, nx / h->march_cluster);
+  if (h->inflow) {  // zero-padded periodic domain: pad >= the stencil's reach, a multiple of 16 in all
+    const int pad = std::max(-coarsest.lo(), coarsest.hi());
+    h->march_nxp = (nx + pad + 15) / 16 * 16;
+  }
+  const int march_np = h->march_nxp ? h->march_nxp : nx;
+  h->march_cluster = pick_cluster(march_np, coarsest);
+  h->march_threads = std::min(256, march_np / h->march_cluster);
   const double tt = now_s();
   autotune_fine(h);
   h->tune_s = now_s() - tt;
@@ -988,8 +1058,9 @@ void collect_stats(mgrit_handle* h, mgrit_result* R) {
 // Launch a march, shrinking the cluster if the device refuses the size.
 mgrit_status run_march(mgrit_handle* h, const MarchArgs& a, const DevTaps& t) {
   return klaunch(h, MGRIT_K_MARCH, "march", [&]() -> mgrit_status {
+    const int np = a.nxp > a.nx ? a.nxp : a.nx;
     for (;;) {
-      int threads = std::min(256, a.nx / h->march_cluster);
+      int threads = std::min(256, np / h->march_cluster);
       cudaError_t e = launch_march(a, t, h->march_cluster, threads, h->stream);
       if (e == cudaSuccess) return MGRIT_OK;
       cudaGetLastError();
@@ -1016,8 +1087,9 @@ mgrit_status initial_residual_async(mgrit_handle* h, const double* u0dev) {
   if ((st = klaunch(h, MGRIT_K_PROPAGATE, "propagate", [&] {
          if (h->sdirk) return launch_ok(launch_propagate_sdirk(u0dev, out, 1, h->nx, 1, h->splan, part, h->stream),
                                         "propagate");
-         return launch_ok(launch_propagate(u0dev, out, 1, h->nx, 1, h->dphi, part, h->fcf_threads, h->stream),
-                          "propagate");
+         return launch_ok(
+             launch_propagate(u0dev, out, 1, h->nx, 1, h->dphi, part, h->fcf_threads, h->stream, &h->fx_phi),
+             "propagate");
        })) != MGRIT_OK)
     return st;
   CUDA_TRY(cudaMemcpyAsync(h->norm_host, part, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -1050,6 +1122,7 @@ mgrit_status relax_level(mgrit_handle* h, int l, bool from_zero) {
   f.m = m;
   f.N = h->Nl[l];
   f.zero_old = from_zero ? 1 : 0;
+  f.fx = h->fx_psi[l - 2];
   return klaunch(h, MGRIT_K_FCF_COARSE, "fcf", [&] {
     return launch_ok(launch_fcf(f, h->dpsi[l - 2], prec, h->fcf_threads, h->stream), "fcf(coarse)");
   });
@@ -1065,6 +1138,7 @@ mgrit_status solve_coarsest(mgrit_handle* h) {
   a.u_out_f = h->uf[L];
   a.store_every = 1;
   a.nx = h->nx;
+  a.nxp = h->march_nxp;
   a.P = h->Nl[L - 1] + 1;
   return run_march(h, a, h->dpsi[L - 2]);
 }
@@ -1084,6 +1158,7 @@ mgrit_status correct_level(mgrit_handle* h, int l) {
   c.nx = h->nx;
   c.m = h->m;
   c.N = h->Nl[l];
+  c.fx = h->fx_psi[l - 2];
   return klaunch(h, MGRIT_K_CORRECT, "correct", [&] {
     return launch_ok(launch_correct(c, h->dpsi[l - 2], h->fcf_threads, h->stream, prec == 2), "correct");
   });
@@ -1127,6 +1202,7 @@ mgrit_status coarse_cycle(mgrit_handle* h, double* c_new) {
     a.g_f = h->rf[1];
     a.c_add = c_new;
     a.nx = nx;
+    a.nxp = h->march_nxp;
     a.P = h->Nl[1] + 1;
     a.store_every = 1;
     return run_march(h, a, h->dpsi[0]);
@@ -1162,6 +1238,7 @@ mgrit_status write_output(mgrit_handle* h, const double* cres, double* out) {
     c.nx = nx;
     c.m = m;
     c.N = (int)N1;
+    c.fx = h->fx_phi;
     if ((st = klaunch(h, MGRIT_K_OTHER, "interp", [&] {
            if (h->sdirk)
              return launch_ok(launch_interp_sdirk(cres, full, nx, m, (int)N1, h->splan, h->stream), "interp");
@@ -1324,7 +1401,7 @@ static mgrit_status solve_graph(mgrit_handle* h, const double* u0, const double*
       (st = launch_ok(h->sdirk ? launch_propagate_sdirk(h->c[0], h->scratch, 1, nx, 1, h->splan, &h->dstate->r0sq,
                                                         h->stream)
                                : launch_propagate(h->c[0], h->scratch, 1, nx, 1, h->dphi, &h->dstate->r0sq,
-                                                  h->fcf_threads, h->stream),
+                                                  h->fcf_threads, h->stream, &h->fx_phi),
                       "propagate")) != MGRIT_OK)
     return st;
   CUDA_TRY(cudaGraphLaunch(h->gexec, h->stream));
@@ -1510,6 +1587,11 @@ extern "C" mgrit_status mgrit_sequential(mgrit_handle* h, const double* u0, doub
     st = klaunch(h, MGRIT_K_MARCH, "seq", [&] {
       return launch_ok(launch_seq_sdirk(init, dst, nx, h->nt + 1, every, h->splan, h->stream), "seq_sdirk");
     });
+  } else if (h->inflow) {  // Phi's boundary rows: one CTA keeps the slab and fixes them up every step
+    st = klaunch(h, MGRIT_K_MARCH, "seq", [&] {
+      return launch_ok(launch_seq_slab(init, dst, nx, h->nt + 1, every, h->dphi, h->fx_phi, 0, h->stream),
+                       "seq_slab");
+    });
   } else {
     int saved = h->march_cluster;
     h->march_cluster = pick_cluster(nx, h->phi);
@@ -1548,7 +1630,9 @@ extern "C" mgrit_status mgrit_propagate(mgrit_handle* h, int32_t level, int32_t 
       return launch_ok(launch_propagate_sdirk(in, out, count, h->nx, k, h->splan, nullptr, h->stream), "propagate");
     if (level == 2 && h->redisc)
       return launch_ok(launch_propagate_sdirk(in, out, count, h->nx, k, h->cplan, nullptr, h->stream), "propagate");
-    return launch_ok(launch_propagate(in, out, count, h->nx, k, t, nullptr, h->fcf_threads, h->stream), "propagate");
+    const Fixup& fx = level == 1 ? h->fx_phi : h->fx_psi[level - 2];
+    return launch_ok(launch_propagate(in, out, count, h->nx, k, t, nullptr, h->fcf_threads, h->stream, &fx),
+                     "propagate");
   });
   if (st != MGRIT_OK) return st;
   CUDA_TRY(cudaStreamSynchronize(h->stream));

@@ -7,7 +7,11 @@
 //   correct_kernel                    correction + F-relaxation (ideal interpolation)
 //   norm_kernel / norm_batched_kernel deterministic residual 2-norm (stopping test)
 //   propagate_kernel                  T^k applied to a batch of vectors
+//   seq_slab_kernel                   sequential stepping of a non-periodic level
 // Every stencil is a circulant (Corollary 1): periodic indices wrap modulo nx.
+// On the inflow/outflow domain (Section 4.5) the rows that reach past either
+// end are recomputed after each step from their own coefficients (Fixup), and
+// the march runs on a zero-padded periodic domain (truncated Toeplitz Psi).
 #include <cooperative_groups.h>
 
 #include <cstring>
@@ -253,6 +257,62 @@ __device__ __forceinline__ void slab_step(const DevTaps& t, const T* src, T* dst
   else step_sparse<T, G>(t, src, dst, g, nx);
 }
 
+// ------------------------------------------------------- boundary rows
+// Non-periodic levels (Section 4.5): after the circulant step, the rows that
+// reach past either end are recomputed from their own coefficients (Fixup).
+// One warp per row: its lanes split the row's columns, a shuffle tree sums.
+template <typename T>
+__device__ __forceinline__ T fx_coef(const Fixup& f, long long k);
+template <>
+__device__ __forceinline__ double fx_coef<double>(const Fixup& f, long long k) { return __ldg(f.w64 + k); }
+template <>
+__device__ __forceinline__ float fx_coef<float>(const Fixup& f, long long k) { return __ldg(f.w32 + k); }
+template <>
+__device__ __forceinline__ df64 fx_coef<df64>(const Fixup& f, long long k) { return df_from(__ldg(f.w64 + k)); }
+
+template <typename T>
+__device__ __forceinline__ T warp_add(T v, float one) {
+  for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+template <>
+__device__ __forceinline__ df64 warp_add<df64>(df64 v, float one) {
+  for (int o = 16; o; o >>= 1) {
+    const df64 u = {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+    v = df_fma1({one, 0.0f}, u, v, one);
+  }
+  return v;
+}
+
+template <typename T, typename G>
+__device__ __forceinline__ void fixup_rows(const Fixup& f, const T* __restrict__ src, T* __restrict__ dst,
+                                           const G* __restrict__ g, int nx, float one) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int q = threadIdx.x >> 5; q < f.nl + f.nr; q += nw) {
+    const bool left = q < f.nl;
+    const int row = left ? q : nx - f.nr + (q - f.nl);
+    const int c0 = left ? 0 : nx - f.cr;
+    const int nc = left ? f.cl : f.cr;
+    const long long w0 = left ? (long long)q * f.cl : (long long)f.nl * f.cl + (long long)(q - f.nl) * f.cr;
+    T acc = (g && lane == 0) ? gload<T>(g + row) : vzero<T>();
+    for (int c = lane; c < nc; c += 32) acc = vfma1<T>(fx_coef<T>(f, w0 + c), src[pidx(c0 + c)], acc, one);
+    acc = warp_add<T>(acc, one);
+    if (lane == 0) dst[pidx(row)] = vfinish<T>(acc);
+  }
+}
+
+// slab_step, then (non-periodic levels) the boundary rows; the caller's
+// barrier after the step covers the fix-up as well.
+template <typename T, int R, int SPAN = 0, typename G = double>
+__device__ __forceinline__ void slab_step_fx(const DevTaps& t, const Fixup& fx, const T* src, T* dst, const G* g,
+                                             int nx) {
+  slab_step<T, R, SPAN, G>(t, src, dst, g, nx);
+  if (fx.nl + fx.nr) {
+    __syncthreads();
+    fixup_rows<T, G>(fx, src, dst, g, nx, t.one);
+  }
+}
+
 // Sum over the block in a fixed order (deterministic); result valid in thread 0.
 __device__ double block_sum(double v) {
   __shared__ double ws[32];
@@ -292,7 +352,7 @@ __device__ __forceinline__ void fcf_body_fp32(const FcfArgs& a, const int j, con
   const bool run1 = __syncthreads_or(nz) || a.g_f;  // zero slab, no rhs: Phi^m 0 = 0
   for (int s = 1; s <= m && run1; ++s) {
     const float* g = a.g_f ? a.g_f + ((long long)(j - 1) * m + s) * nx : nullptr;
-    slab_step<float, R, SPAN>(t, b0, b1, g, nx);
+    slab_step_fx<float, R, SPAN>(t, a.fx, b0, b1, g, nx);
     __syncthreads();
     float* tmp = b0; b0 = b1; b1 = tmp;
   }
@@ -311,7 +371,7 @@ __device__ __forceinline__ void fcf_body_fp32(const FcfArgs& a, const int j, con
   float* x0 = b1;
   float* x1 = b0;
   for (int s = 1; s <= m && run2; ++s) {
-    slab_step<float, R, SPAN>(t, x0, x1, kNoG, nx);
+    slab_step_fx<float, R, SPAN>(t, a.fx, x0, x1, kNoG, nx);
     __syncthreads();
     float* tmp = x0; x0 = x1; x1 = tmp;
   }
@@ -396,7 +456,7 @@ __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const
   const bool run1 = __syncthreads_or(nz) || a.g;  // zero slab, no rhs: Phi^m 0 = 0
   for (int s = 1; s <= m && run1; ++s) {
     const double* g = a.g ? a.g + ((long long)(j - 1) * m + s) * nx : nullptr;
-    slab_step<df64, R, SPAN>(t, b0, b1, g, nx);
+    slab_step_fx<df64, R, SPAN>(t, a.fx, b0, b1, g, nx);
     __syncthreads();
     df64* tmp = b0; b0 = b1; b1 = tmp;
   }
@@ -419,7 +479,7 @@ __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const
   const bool run2 = __syncthreads_or(nz);
   if (j >= a.N) return;
   for (int s = 1; s <= m && run2; ++s) {
-    slab_step<float, R, SPAN>(t, f0, f1, kNoG, nx);
+    slab_step_fx<float, R, SPAN>(t, a.fx, f0, f1, kNoG, nx);
     __syncthreads();
     float* tmp = f0; f0 = f1; f1 = tmp;
   }
@@ -451,7 +511,7 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
   const bool run1 = __syncthreads_or(nz) || a.g;
   for (int s = 1; s <= m && run1; ++s) {
     const double* g = a.g ? a.g + ((long long)(j - 1) * m + s) * nx : nullptr;
-    slab_step<double, R, SPAN>(t, b0, b1, g, nx);
+    slab_step_fx<double, R, SPAN>(t, a.fx, b0, b1, g, nx);
     __syncthreads();
     double* tmp = b0; b0 = b1; b1 = tmp;
   }
@@ -477,7 +537,7 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
     double* x0 = b1;
     double* x1 = b0;
     for (int s = 1; s <= m && run2; ++s) {
-      slab_step<double, R, SPAN>(t, x0, x1, kNoG, nx);
+      slab_step_fx<double, R, SPAN>(t, a.fx, x0, x1, kNoG, nx);
       __syncthreads();
       double* tmp = x0; x0 = x1; x1 = tmp;
     }
@@ -502,7 +562,7 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
     const bool run2 = __syncthreads_or(nz);
     if (!more) return;
     for (int s = 1; s <= m && run2; ++s) {
-      slab_step<float, R, SPAN>(t, f0, f1, kNoG, nx);
+      slab_step_fx<float, R, SPAN>(t, a.fx, f0, f1, kNoG, nx);
       __syncthreads();
       float* tmp = f0; f0 = f1; f1 = tmp;
     }
@@ -558,20 +618,21 @@ __device__ __forceinline__ int modnx(long long v, int nx) {
   return (int)(r < 0 ? r + nx : r);
 }
 
-template <int PPT>
+template <int PPT, bool PAD = false>
 __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t, unsigned char* smraw,
                                            cg::cluster_group& cl) {
   const int cs = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
-  const int nx = a.nx, w = nx / cs, base = rank * w;
+  // np: period of the frame (the zero-padded domain of a non-periodic level)
+  const int nx = a.nx, np = PAD ? a.nxp : nx, w = np / cs, base = rank * w;
   const int sigma = t.shift;
   const int L = sigma - t.lo, R = t.hi - sigma, W = L + w + R;
   double* B0 = reinterpret_cast<double*>(smraw);
   double* B1 = B0 + W;
   const int tid = threadIdx.x, bs = blockDim.x;
   for (int k = tid; k < W; k += bs) {
-    const int gi = modnx((long long)base - L + k, nx);
-    B0[k] = a.init ? a.init[gi] : 0.0;
+    const int gi = modnx((long long)base - L + k, np);
+    B0[k] = (a.init && (!PAD || gi < nx)) ? a.init[gi] : 0.0;
   }
   __syncthreads();
   // next step's right-hand side and C-points, loaded one step ahead (an FP32
@@ -584,15 +645,16 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
       const int i = tid + p * bs;
-      if (i < w) {
-        const long long o = (long long)n * nx + wrapi(base + i + Sn, nx);
+      const int gi = wrapi(base + i + Sn, np);
+      if (i < w && (!PAD || gi < nx)) {
+        const long long o = (long long)n * nx + gi;
         if (a.g_f) gqf[p] = __ldcg(a.g_f + o);
         else if (a.g) gq[p] = __ldcg(a.g + o);
         if (a.c_add) cq[p] = __ldcg(a.c_add + o);
       }
     }
   };
-  int S = modnx(-(long long)sigma, nx);  // S_1
+  int S = modnx(-(long long)sigma, np);  // S_1
   if (a.P > 1) prefetch(1, S);
   for (int n = 1; n < a.P; ++n) {
     double* cur = (n & 1) ? B0 : B1;
@@ -600,7 +662,7 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
     double gc[PPT], cc[PPT];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) { gc[p] = a.g_f ? (double)gqf[p] : gq[p]; cc[p] = cq[p]; }
-    const int Snext = modnx((long long)S - sigma, nx);
+    const int Snext = modnx((long long)S - sigma, np);
     if (n + 1 < a.P) prefetch(n + 1, Snext);
     const bool store = (a.u_out || a.u_out_f) && (n % a.store_every) == 0;
 #pragma unroll
@@ -610,8 +672,12 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
         double acc = gc[p];
         const double* c = cur + L + i - sigma;
         for (int k = 0; k < t.n; ++k) acc = fma(t.c64[k], c[t.off[k]], acc);
+        const int gi = wrapi(base + i + S, np);
+        if (PAD && gi >= nx) {  // the zero padding stays zero
+          nxt[L + i] = 0.0;
+          continue;
+        }
         nxt[L + i] = acc;
-        const int gi = wrapi(base + i + S, nx);
         if (a.c_add) a.c_add[(long long)n * nx + gi] = cc[p] + acc;
         if (store) {
           const long long o = (long long)(n / a.store_every) * nx + gi;
@@ -625,7 +691,7 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
       int dst, fi;
       if (k < L) { dst = k; fi = base - L + k; }
       else { dst = w + k; fi = base + w + (k - L); }
-      fi = modnx(fi, nx);
+      fi = modnx(fi, np);
       const int owner = fi / w, loc = fi - owner * w;
       const double* rem = cl.map_shared_rank(nxt, owner);
       nxt[dst] = rem[L + loc];
@@ -636,11 +702,11 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
   cl.sync();  // no CTA leaves while a neighbour may still read its shared memory
 }
 
-template <int PPT>
+template <int PPT, bool PAD>
 __global__ void __launch_bounds__(256) march_kernel(const MarchArgs a, const DevTaps t) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cg::cluster_group cl = cg::this_cluster();
-  march_body<PPT>(a, t, smraw, cl);
+  march_body<PPT, PAD>(a, t, smraw, cl);
 }
 
 // Batched two-level coarse solve: cluster c marches solve ids[c] with its
@@ -705,7 +771,7 @@ __global__ void __launch_bounds__(R == 8 ? 512 : 1024) correct_kernel(const Corr
   __syncthreads();
   for (int s = 1; s < m; ++s) {
     const T* g = gg ? gg + (p0 + s) * nx : nullptr;
-    slab_step<T, R>(t, b0, b1, g, nx);
+    slab_step_fx<T, R>(t, a.fx, b0, b1, g, nx);
     __syncthreads();
     for (int i = threadIdx.x; i < nx; i += blockDim.x) u[(p0 + s) * nx + i] = b1[pidx(i)];
     T* tmp = b0; b0 = b1; b1 = tmp;
@@ -775,7 +841,7 @@ __global__ void add_f_kernel(double* __restrict__ c, const float* __restrict__ e
 
 template <int R>
 __global__ void __launch_bounds__(R == 8 ? 512 : 1024) propagate_kernel(const double* in, double* out, int nx, int k,
-                                                         const DevTaps t, double* partial) {
+                                                         const DevTaps t, double* partial, const Fixup fx) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int plen = padded_len(nx);
   double* b0 = reinterpret_cast<double*>(smraw);
@@ -784,7 +850,7 @@ __global__ void __launch_bounds__(R == 8 ? 512 : 1024) propagate_kernel(const do
   for (int i = threadIdx.x; i < nx; i += blockDim.x) b0[pidx(i)] = in[v * nx + i];
   __syncthreads();
   for (int s = 0; s < k; ++s) {
-    slab_step<double, R>(t, b0, b1, kNoG, nx);
+    slab_step_fx<double, R>(t, fx, b0, b1, kNoG, nx);
     __syncthreads();
     double* tmp = b0; b0 = b1; b1 = tmp;
   }
@@ -986,16 +1052,19 @@ static cudaError_t launch_cluster(K kernel, int grid, int cluster, int threads, 
 
 template <int PPT>
 static cudaError_t launch_march_t(const MarchArgs& a, const DevTaps& t, int cluster, int threads, cudaStream_t s) {
-  const int w = a.nx / cluster;
+  const bool pad = a.nxp > a.nx;
+  const int w = (pad ? a.nxp : a.nx) / cluster;
   const size_t smem = 2 * (size_t)(w + t.hi - t.lo) * sizeof(double);
   MarchArgs aa = a;
   DevTaps tt = t;
   void* args[] = {&aa, &tt};
-  return launch_cluster(march_kernel<PPT>, cluster, cluster, threads, smem, s, args);
+  if (pad) return launch_cluster(march_kernel<PPT, true>, cluster, cluster, threads, smem, s, args);
+  return launch_cluster(march_kernel<PPT, false>, cluster, cluster, threads, smem, s, args);
 }
 
 cudaError_t launch_march(const MarchArgs& a, const DevTaps& t, int cluster, int threads, cudaStream_t s) {
-  const int w = a.nx / cluster;
+  if (a.nxp > a.nx && (a.nxp < a.nx + (-t.lo > t.hi ? -t.lo : t.hi) || a.nxp % cluster)) return cudaErrorInvalidValue;
+  const int w = (a.nxp > a.nx ? a.nxp : a.nx) / cluster;
   const int ppt = (w + threads - 1) / threads;
   if (a.P < 2) return cudaSuccess;
   switch (ppt) {
@@ -1102,21 +1171,61 @@ cudaError_t launch_add_f(double* c, const float* e, long long count, cudaStream_
 
 template <int R>
 static cudaError_t launch_propagate_t(const double* in, double* out, int count, int nx, int k, const DevTaps& t,
-                                      double* partial, int threads, cudaStream_t s) {
+                                      double* partial, int threads, cudaStream_t s, const Fixup& fx) {
   const size_t smem = 2 * (size_t)padded_len(nx) * sizeof(double);
   cudaError_t e = set_smem(propagate_kernel<R>, smem);
   if (e != cudaSuccess) return e;
-  propagate_kernel<R><<<count, threads_for(nx, R, threads), smem, s>>>(in, out, nx, k, t, partial);
+  propagate_kernel<R><<<count, threads_for(nx, R, threads), smem, s>>>(in, out, nx, k, t, partial, fx);
   return cudaGetLastError();
 }
 
 cudaError_t launch_propagate(const double* in, double* out, int count, int nx, int k, const DevTaps& t,
-                             double* partial, int threads, cudaStream_t s) {
+                             double* partial, int threads, cudaStream_t s, const Fixup* fx) {
   if (count < 1) return cudaSuccess;
+  const Fixup f = fx ? *fx : Fixup{};
   const int R = tile_for(t, nx);
-  if (R == 8) return launch_propagate_t<8>(in, out, count, nx, k, t, partial, threads, s);
-  if (R == 4) return launch_propagate_t<4>(in, out, count, nx, k, t, partial, threads, s);
-  return launch_propagate_t<0>(in, out, count, nx, k, t, partial, threads, s);
+  if (R == 8) return launch_propagate_t<8>(in, out, count, nx, k, t, partial, threads, s, f);
+  if (R == 4) return launch_propagate_t<4>(in, out, count, nx, k, t, partial, threads, s, f);
+  return launch_propagate_t<0>(in, out, count, nx, k, t, partial, threads, s, f);
+}
+
+template <int R>
+__global__ void __launch_bounds__(R == 8 ? 512 : 1024) seq_slab_kernel(const double* __restrict__ u0, double* out,
+                                                                       int nx, int P, int every, const DevTaps t,
+                                                                       const Fixup fx) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int plen = padded_len(nx);
+  double* b0 = reinterpret_cast<double*>(smraw);
+  double* b1 = b0 + plen;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) b0[pidx(i)] = u0[i];
+  __syncthreads();
+  for (int n = 1; n < P; ++n) {
+    slab_step_fx<double, R>(t, fx, b0, b1, kNoG, nx);
+    __syncthreads();
+    if (n % every == 0)
+      for (int i = threadIdx.x; i < nx; i += blockDim.x) out[(long long)(n / every) * nx + i] = b1[pidx(i)];
+    double* tmp = b0; b0 = b1; b1 = tmp;
+  }
+}
+
+template <int R>
+static cudaError_t launch_seq_slab_t(const double* u0, double* out, int nx, int P, int every, const DevTaps& t,
+                                     const Fixup& fx, int threads, cudaStream_t s) {
+  const size_t smem = 2 * (size_t)padded_len(nx) * sizeof(double);
+  cudaError_t e = set_smem(seq_slab_kernel<R>, smem);
+  if (e != cudaSuccess) return e;
+  seq_slab_kernel<R><<<1, threads_for(nx, R, threads), smem, s>>>(u0, out, nx, P, every, t, fx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seq_slab(const double* u0, double* out, int nx, int P, int store_every, const DevTaps& t,
+                            const Fixup& fx, int threads, cudaStream_t s) {
+  if (P < 2) return cudaSuccess;
+  if (store_every < 1) return cudaErrorInvalidValue;
+  const int R = tile_for(t, nx);
+  if (R == 8) return launch_seq_slab_t<8>(u0, out, nx, P, store_every, t, fx, threads, s);
+  if (R == 4) return launch_seq_slab_t<4>(u0, out, nx, P, store_every, t, fx, threads, s);
+  return launch_seq_slab_t<0>(u0, out, nx, P, store_every, t, fx, threads, s);
 }
 
 }  // namespace mg

@@ -8,8 +8,9 @@
 //   2. advances every admitted solve by one MGRIT cycle: one batched
 //      FCF-relaxation launch per nx over all intervals of all solves, one
 //      batched norm launch, one read-back of all norms, then the coarse solves
-//      (one batched cluster march per cluster size for two-level solves, the
-//      V-cycle kernels per handle for multilevel ones);
+//      (one batched cluster march per cluster size for two-level periodic
+//      solves; the handle's own coarse kernels for multilevel, rediscretised
+//      and inflow/outflow ones);
 //   3. retires converged (or failed) solves: copies their output to host
 //      memory, frees their device state, and wakes pollers.
 // Requests that arrive while others run join at the next turn, so their work
@@ -240,6 +241,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     b.fcf.zero_old = 0;
     b.fcf.relax_f = h->opts.relax == MGRIT_RELAX_F;
     b.fcf.value_residual = fine_prec(h) == 0 && !b.fcf.relax_f;
+    b.fcf.fx = h->fx_phi;  // boundary rows (inflow/outflow problems)
     b.prec = fine_prec(h);
     b.taps = 2 * k;
     b.psi = 2 * k + 1;
@@ -340,7 +342,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
       r->status = MGRIT_ERR_NOT_CONVERGED;
       r->error = "max_iter reached";
       (*done)[k] = 1;
-    } else if (r->h->L == 2 && !r->h->redisc) {
+    } else if (r->h->L == 2 && !r->h->redisc && !r->h->inflow) {
       by_cluster[r->h->march_cluster].push_back(k);
     }
   }
@@ -364,7 +366,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
   for (int k = 0; k < n; ++k) {
     Request* r = act[k];
     if ((*done)[k]) continue;
-    if (r->h->L > 2 || r->h->redisc) {
+    if (r->h->L > 2 || r->h->redisc || r->h->inflow) {  // the handle's own coarse solve
       mgrit_status st = coarse_cycle(r->h, r->h->c[1 - r->cur]);
       if (st != MGRIT_OK) {
         r->status = st;

@@ -229,6 +229,107 @@ Taps erk_phi_taps(int rk_order, int upwind_order, double c) {
   return out;
 }
 
+std::vector<double> extrapolation_weights(int q, int j) {
+  std::vector<double> w(q + 1, 1.0);
+  for (int k = 0; k <= q; ++k)
+    for (int r = 0; r <= q; ++r)
+      if (r != k) w[k] *= (double)(j + r) / (double)(r - k);  // nodes -k, -r
+  return w;
+}
+
+// One stage-wise ERK step of the closed problem on np unknowns (inflow
+// ghosts zero, outflow ghosts extrapolated from every stage's input).
+static std::vector<double> inflow_step(const Tableau& tb, const Taps& L, int q, const std::vector<double>& u) {
+  const int np = (int)u.size(), lo = L.lo(), hi = L.hi();
+  std::vector<std::vector<double>> ew;
+  for (int j = 1; j <= hi; ++j) ew.push_back(extrapolation_weights(q, j));
+  auto dtl = [&](const std::vector<double>& y) {
+    std::vector<double> ext(np - lo + hi, 0.0);  // [-lo zeros | y | hi ghosts]
+    for (int i = 0; i < np; ++i) ext[i - lo] = y[i];
+    for (int j = 1; j <= hi; ++j) {
+      double g = 0.0;
+      for (int k = 0; k <= q; ++k) g += ew[j - 1][k] * y[np - 1 - k];
+      ext[np - 1 + j - lo] = g;
+    }
+    std::vector<double> out(np, 0.0);
+    for (int i = 0; i < np; ++i)
+      for (int k = 0; k < L.size(); ++k) out[i] += L.coef[k] * ext[i + L.off[k] - lo];
+    return out;
+  };
+  std::vector<std::vector<double>> K;
+  for (int i = 0; i < tb.s; ++i) {
+    std::vector<double> y = u;
+    for (int j = 0; j < i; ++j)
+      if (tb.a(i, j) != 0.0)
+        for (int x = 0; x < np; ++x) y[x] += tb.a(i, j) * K[j][x];
+    K.push_back(dtl(y));
+  }
+  std::vector<double> r = u;
+  for (int i = 0; i < tb.s; ++i)
+    if (tb.b[i] != 0.0)
+      for (int x = 0; x < np; ++x) r[x] += tb.b[i] * K[i][x];
+  return r;
+}
+
+BoundaryRows inflow_phi_rows(int rk_order, int upwind_order, double c, int nx) {
+  BoundaryRows B;
+  const Tableau tb = erk_tableau(rk_order);
+  const Taps L = dtL_taps(upwind_order, c);
+  if (tb.s == 0 || L.size() == 0) return B;
+  const int s = tb.s, lo = L.lo(), hi = L.hi();
+  const int nl = s * -lo, nr = s * hi;  // rows whose stages reach a ghost value
+  // the two ends stay apart: no row of one block reaches the other end
+  const int need = nl + nr + s * (hi - lo) + upwind_order + 2;
+  if (nx < need) return B;
+  // the blocks do not depend on nx beyond `need`: probe a short domain
+  const int np = std::min(nx, std::max(64, 2 * need));
+  std::vector<double> P((size_t)np * np);  // P[row * np + col]
+  std::vector<double> e(np, 0.0);
+  for (int col = 0; col < np; ++col) {
+    e[col] = 1.0;
+    const std::vector<double> v = inflow_step(tb, L, upwind_order, e);
+    e[col] = 0.0;
+    for (int row = 0; row < np; ++row) P[(size_t)row * np + col] = v[row];
+  }
+  int cl = 0, cmin = np;
+  for (int row = 0; row < nl; ++row)
+    for (int col = 0; col < np; ++col)
+      if (P[(size_t)row * np + col] != 0.0) cl = std::max(cl, col + 1);
+  for (int row = np - nr; row < np; ++row)
+    for (int col = 0; col < np; ++col)
+      if (P[(size_t)row * np + col] != 0.0) cmin = std::min(cmin, col);
+  const int cr = nr ? np - cmin : 0;
+  B.nl = nl; B.cl = cl; B.nr = nr; B.cr = cr;
+  for (int row = 0; row < nl; ++row)
+    for (int col = 0; col < cl; ++col) B.w.push_back(P[(size_t)row * np + col]);
+  for (int row = np - nr; row < np; ++row)
+    for (int col = np - cr; col < np; ++col) B.w.push_back(P[(size_t)row * np + col]);
+  return B;
+}
+
+BoundaryRows truncated_rows(const Taps& t, int nx) {
+  BoundaryRows B;
+  const int lo = t.lo(), hi = t.hi();
+  if (nx < (hi - lo) + 1 || nx < -lo + hi) return B;
+  std::vector<double> d(hi - lo + 1, 0.0);
+  for (int k = 0; k < t.size(); ++k) d[t.off[k] - lo] += t.coef[k];
+  B.nl = -lo; B.cl = -lo ? hi - lo : 0;
+  B.nr = hi;  B.cr = hi ? hi - lo : 0;
+  for (int row = 0; row < B.nl; ++row)
+    for (int col = 0; col < B.cl; ++col) {
+      const int o = col - row;
+      B.w.push_back(o >= lo && o <= hi ? d[o - lo] : 0.0);
+    }
+  for (int r = 0; r < B.nr; ++r) {
+    const int row = nx - B.nr + r;
+    for (int cc = 0; cc < B.cr; ++cc) {
+      const int o = (nx - B.cr + cc) - row;
+      B.w.push_back(o >= lo && o <= hi ? d[o - lo] : 0.0);
+    }
+  }
+  return B;
+}
+
 Taps taps_power(const Taps& t, int k) {
   Taps out;
   if (t.size() == 0 || k < 1) return out;

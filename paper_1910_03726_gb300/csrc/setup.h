@@ -69,6 +69,29 @@ struct PlanRequest {
 // Build Psi_2..Psi_L.  Returns false and sets *err on failure.
 bool build_hierarchy(const PlanRequest& rq, std::vector<CoarseOp>* ops, std::string* err);
 
+// Rows of an operator on the non-periodic domain (Section 4.5) that differ
+// from its circulant: rows 0..nl-1 over columns 0..cl-1 and rows nx-nr..nx-1
+// over columns nx-cr..nx-1, row-major, the left block first.  Every other row
+// is the circulant's and never reaches past either end.
+struct BoundaryRows {
+  int nl = 0, cl = 0, nr = 0, cr = 0;
+  std::vector<double> w;
+};
+
+// Lagrange weights of degree q through the nodes 0, -1, .., -q evaluated at
+// j: the outflow ghost u_{nx-1+j} = sum_k w_k u_{nx-1-k}.
+std::vector<double> extrapolation_weights(int q, int j);
+
+// Phi of ERKp+Uq with a homogeneous inflow condition at x = -1 (zero ghost
+// values left of the domain in every stage) and degree-q extrapolation to
+// the outflow ghosts in every stage; nx unknowns x_i = -1 + (i+1) dx.
+// Empty (nl = nr = 0) if nx is too small for the two ends to stay apart.
+BoundaryRows inflow_phi_rows(int rk_order, int upwind_order, double c, int nx);
+
+// A stencil truncated at both ends (Toeplitz): (T v)_r sums only the taps
+// whose column r + off lies in 0..nx-1.
+BoundaryRows truncated_rows(const Taps& t, int nx);
+
 // Weighted least-squares fit of Eq. 6 on the given offsets; nt_level sets
 // the Eq. 4 bound's horizon.
 CoarseOp lsq_fit(const std::vector<cplx>& lam, const std::vector<double>& col_m,

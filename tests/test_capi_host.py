@@ -30,7 +30,7 @@ def test_exports_every_declared_entry_point(capi):
     assert "mgrit_setup" in names and "mgrit_poll" in names
     missing = [n for n in names if not hasattr(capi._lib, n)]
     assert not missing, missing
-    assert capi.mgrit_abi_version() == 3
+    assert capi.mgrit_abi_version() == 4
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
@@ -112,3 +112,46 @@ def test_server_host_side_without_gpu(capi):
         assert ei.value.status == -1
     finally:
         capi.mgrit_server_destroy(srv)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_phi_boundary_rows_match_oracle(capi, p):
+    """Inflow/outflow Phi (Section 4.5): the library's boundary rows equal the
+    oracle's stage-wise Phi with the same closures, and every other row is the
+    interior stencil of mgrit_phi_taps."""
+    from oracle import boundaries as bd
+    from oracle import schemes
+    nx = 96
+    c = schemes.cfl_number("ERK", p)
+    prob = capi.problem(nx, 64, "ERK", p, p, c, boundary="inflow")
+    left, right = capi.mgrit_phi_boundary(prob)
+    P = bd.dense_phi(bd.InflowStep(p, c, nx))
+    nl, cl = left.shape
+    nr, cr = right.shape
+    assert nl > 0 and (nr > 0) == (max(schemes.dtL_taps(p, c)) > 0)  # outflow ghosts only if the stencil reaches right
+    # same stage-wise arithmetic, other summation orders
+    assert np.max(np.abs(left - P[:nl, :cl])) < 2e-14
+    assert np.all(np.abs(right - P[nx - nr:, nx - cr:]) < 2e-14)
+    # outside the blocks the boundary rows are zero
+    assert np.all(P[:nl, cl:] == 0.0) and np.all(P[nx - nr:, : nx - cr] == 0.0)
+    offs, cfs = capi.mgrit_phi_taps(prob)
+    Q = np.zeros((nx, nx))
+    for r in range(nl, nx - nr):
+        for o, v in zip(offs, cfs):
+            Q[r, r + o] += v
+    assert np.max(np.abs(Q[nl: nx - nr] - P[nl: nx - nr])) < 1e-14
+
+
+def test_inflow_validation(capi):
+    prob = capi.problem(96, 64, "SDIRK", 2, 2, 1.0, boundary="inflow")
+    ok = capi.problem(96, 64, "ERK", 3, 3, 1.0, boundary="inflow")
+    assert capi._lib.mgrit_phi_boundary(capi.C.byref(prob), 0, None, None) == -10  # ERK only
+    small = capi.problem(40, 64, "ERK", 5, 5, 1.5, boundary="inflow")
+    assert capi._lib.mgrit_phi_boundary(capi.C.byref(small), 0, None, None) == -10  # ends too close
+    bad = capi.problem(96, 64, "ERK", 3, 3, 1.0)
+    bad.boundary = 7
+    assert capi._lib.mgrit_phi_boundary(capi.C.byref(bad), 0, None, None) == -1
+    opts = capi.mgrit_opts_default(m=4, levels=2, psi_rule=capi.PSI_IDEAL)
+    L = 1
+    nnz = (capi.C.c_int32 * L)()
+    assert capi._lib.mgrit_psi_plan(capi.C.byref(ok), capi.C.byref(opts), 0, nnz, None, None, None) == -10
