@@ -71,9 +71,8 @@ enum { MGRIT_ERK = 0, MGRIT_SDIRK = 1 };
  *            polynomial (q = upwind_order) through the last q+1 unknowns.
  *            Psi is the periodic problem's fit truncated at both ends
  *            (Toeplitz).  ERK only; not with MGRIT_PSI_IDEAL; the two ends'
- *            closures must stay apart: nx >= 2 s q + q + 2 for s stages and
- *            nx > the widest Psi's offset range (MGRIT_ERR_UNSUPPORTED
- *            otherwise).  Iteration counts: Table 5. */
+ *            closures must stay apart: nx >= 2 s q + q + 2 for s stages
+ *            (MGRIT_ERR_UNSUPPORTED otherwise).  Iteration counts: Table 5. */
 enum { MGRIT_BC_PERIODIC = 0, MGRIT_BC_INFLOW = 1 };
 
 /* Arithmetic of the relaxation (Section 2.2 reading, see the library notes):
@@ -224,14 +223,14 @@ void mgrit_set_allocator(mgrit_alloc_fn alloc, mgrit_free_fn release, void* ctx)
 mgrit_status mgrit_phi_taps(const mgrit_problem* prob, int32_t cap, int32_t* ntaps,
                             int32_t* offsets, double* coeffs);
 
-/* Rows of the fine propagator Phi of an MGRIT_BC_INFLOW problem that differ
- * from its interior stencil (Section 4.5), as the library builds them: dims
- * receives {nl, cl, nr, cr}: rows 0..nl-1 over columns 0..cl-1 and rows
+/* Rows of Phi^m (m >= 1 fine steps) of an MGRIT_BC_INFLOW problem that
+ * differ from its interior stencil (Section 4.5), as the library builds them:
+ * dims receives {nl, cl, nr, cr}: rows 0..nl-1 over columns 0..cl-1 and rows
  * nx-nr..nx-1 over columns nx-cr..nx-1; w (capacity cap doubles) receives the
  * coefficients row-major, the left block first (nl*cl + nr*cr values).  Every
- * other row r is sum_k coeffs[k] v_{r + offsets[k]} of mgrit_phi_taps.  ERK
- * only.  No GPU is touched. */
-mgrit_status mgrit_phi_boundary(const mgrit_problem* prob, int32_t cap, int32_t* dims, double* w);
+ * other row is the circulant one (for m = 1, sum_k coeffs[k] v_{r+offsets[k]}
+ * of mgrit_phi_taps).  ERK only.  No GPU is touched. */
+mgrit_status mgrit_phi_boundary(const mgrit_problem* prob, int32_t m, int32_t cap, int32_t* dims, double* w);
 
 /* Coarse operators Psi_2..Psi_L that mgrit_setup would build (Eq. 6 on the
  * rule's pattern, recursively per level, Section 4.4).  nnz[levels-1];

@@ -116,7 +116,7 @@ ALLOC_FN = C.CFUNCTYPE(_vp, C.c_size_t, _vp, _vp)
 FREE_FN = C.CFUNCTYPE(None, _vp, _vp, _vp)
 _sig("mgrit_set_allocator", None, ALLOC_FN, FREE_FN, _vp)
 _sig("mgrit_phi_taps", _i32, _P(MgritProblem), _i32, _P(_i32), _P(_i32), _P(_f64))
-_sig("mgrit_phi_boundary", _i32, _P(MgritProblem), _i32, _P(_i32), _P(_f64))
+_sig("mgrit_phi_boundary", _i32, _P(MgritProblem), _i32, _i32, _P(_i32), _P(_f64))
 _sig("mgrit_psi_plan", _i32, _P(MgritProblem), _P(MgritOpts), _i32, _P(_i32), _P(_i32), _P(_f64), _P(_f64))
 _sig("mgrit_setup", _i32, _P(MgritProblem), _P(MgritOpts), _vp, _P(_vp))
 _sig("mgrit_solve", _i32, _vp, _vp, _vp, _P(MgritResult))
@@ -214,13 +214,12 @@ def mgrit_phi_taps(prob, cap=1024):
     return list(offs[: n.value]), list(cfs[: n.value])
 
 
-def mgrit_phi_boundary(prob, cap=1 << 14):
-    """Boundary rows of an inflow/outflow problem's Phi: (left block (nl, cl),
-    right block (nr, cr)) as numpy arrays."""
-    import numpy as np
+def mgrit_phi_boundary(prob, m=1, cap=1 << 18):
+    """Boundary rows of an inflow/outflow problem's Phi^m: (left block
+    (nl, cl), right block (nr, cr)) as numpy arrays."""
     dims = (C.c_int32 * 4)()
     w = (C.c_double * cap)()
-    _check(_lib.mgrit_phi_boundary(C.byref(prob), cap, dims, w))
+    _check(_lib.mgrit_phi_boundary(C.byref(prob), m, cap, dims, w))
     nl, cl, nr, cr = (int(v) for v in dims)
     a = np.array(w[: nl * cl + nr * cr])
     return a[: nl * cl].reshape(nl, cl), a[nl * cl:].reshape(nr, cr)

@@ -71,6 +71,7 @@ struct FcfArgs {
   const float* g_f;
   float* r_f;
   Fixup fx;                // boundary rows of T (non-periodic problems)
+  int trunc;               // T truncated at both ends: taps outside 0..nx-1 read zero
 };
 
 // Sequential march u_n = T u_{n-1} + g_n, n = 1..P-1, on one thread-block
@@ -84,11 +85,9 @@ struct MarchArgs {
   int nx, P;
   const float* g_f;        // FP32 right-hand side (replaces g when set)
   float* u_out_f;          // FP32 output (replaces u_out when set)
-  // Non-periodic (truncated Toeplitz) T: the march runs on a zero-padded
-  // periodic domain of nxp >= nx + max(-lo, hi) points whose points nx..nxp-1
-  // are held at zero, which truncates every row at both ends exactly.
-  // 0 = periodic (nxp = nx).
-  int nxp;
+  // T truncated at both ends (Toeplitz, inflow/outflow Psi): a tap whose
+  // column (in the frame that does not move) leaves 0..nx-1 drops out.
+  int trunc;
 };
 
 // Correction and F-relaxation (ideal interpolation) of one level:
@@ -107,6 +106,7 @@ struct CorrectArgs {
   const float* g_f;
   float* u_f;
   Fixup fx;                // boundary rows of T (non-periodic problems)
+  int trunc;               // T truncated at both ends
 };
 
 // tile: register tile (0, 4 or 8), kFixedTile for the fixed-span path of the
@@ -233,7 +233,7 @@ cudaError_t launch_add(double* c, const double* e, long long count, cudaStream_t
 cudaError_t launch_add_f(double* c, const float* e, long long count, cudaStream_t s);
 cudaError_t launch_propagate(const double* in, double* out, int count, int nx, int k,
                              const DevTaps& t, double* partial, int threads, cudaStream_t s,
-                             const Fixup* fx = nullptr);
+                             const Fixup* fx = nullptr, int trunc = 0);
 // Sequential stepping of a non-periodic level on one CTA (the slab stays in
 // shared memory): u_n = T u_{n-1}, n = 1..P-1, u_n stored at
 // out + (n/store_every)*nx when n % store_every == 0 (u_0 is not written).

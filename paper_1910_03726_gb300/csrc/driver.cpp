@@ -256,11 +256,13 @@ extern "C" mgrit_status mgrit_phi_taps(const mgrit_problem* prob, int32_t cap, i
   return MGRIT_OK;
 }
 
-extern "C" mgrit_status mgrit_phi_boundary(const mgrit_problem* prob, int32_t cap, int32_t* dims, double* w) {
+extern "C" mgrit_status mgrit_phi_boundary(const mgrit_problem* prob, int32_t m, int32_t cap, int32_t* dims,
+                                           double* w) {
   mgrit_status st = validate_problem(prob);
   if (st != MGRIT_OK) return st;
   if (prob->boundary != MGRIT_BC_INFLOW) return fail(MGRIT_ERR_INVALID, "the problem is periodic");
-  const BoundaryRows B = inflow_phi_rows(prob->rk_order, prob->upwind_order, prob->cfl, prob->nx);
+  if (m < 1) return fail(MGRIT_ERR_INVALID, "m must be >= 1");
+  const BoundaryRows B = inflow_phi_rows(prob->rk_order, prob->upwind_order, prob->cfl, prob->nx, m);
   if (B.nl + B.nr == 0) return fail(MGRIT_ERR_UNSUPPORTED, "nx too small for the boundary closures");
   if (dims) {
     dims[0] = B.nl; dims[1] = B.cl; dims[2] = B.nr; dims[3] = B.cr;
@@ -668,6 +670,7 @@ void autotune_fine(mgrit_handle* h) {
     if (c.tile == 0 && dense_found) continue;
     const DevTaps& t = c.collapse ? h->dphim : h->dphi;
     f.m = c.collapse ? 1 : h->m;
+    f.fx = c.collapse ? h->fx_phim : h->fx_phi;
     const int per = c.tile == kFixedTile ? 4 : (c.tile == kChunkTile ? 8 : (c.tile > 0 ? c.tile : 1));
     if (c.threads > std::max(32, (nx / per + 31) / 32 * 32)) continue;
     if (!warmed) {
@@ -708,26 +711,27 @@ void autotune_fine(mgrit_handle* h) {
 cudaError_t launch_fine_fcf(mgrit_handle* h, const FcfArgs& f, int prec) {
   if (h->sdirk) return launch_fcf_sdirk(f, h->splan, prec == 0 ? 0 : 1, h->stream);
   FcfArgs g = f;
-  g.fx = h->fx_phi;  // boundary rows (inflow/outflow; never with the collapsed Phi^m)
+  g.fx = h->fx_phi;  // boundary rows (inflow/outflow)
   if (h->fine_collapse) {  // each pass is one application of Phi^m
     g.m = 1;
+    g.fx = h->fx_phim;
     return launch_fcf(g, h->dphim, prec, h->fine_threads, h->stream, h->fine_tile);
   }
   return launch_fcf(g, h->dphi, prec, h->fine_threads, h->stream, h->fine_tile);
 }
 
-// Boundary rows of Phi (stage-wise closures) and of every truncated Psi_l,
-// FP64 then FP32, in one device table (inflow/outflow problems).
+// Boundary rows of Phi and Phi^m (stage-wise closures), FP64 then FP32, in
+// one device table (inflow/outflow problems; Psi_l is truncated by the
+// kernels' loads and needs no table).
 static mgrit_status upload_boundaries(mgrit_handle* h) {
   const int nx = h->nx;
   std::vector<BoundaryRows> rows;
   rows.push_back(inflow_phi_rows(h->prob.rk_order, h->prob.upwind_order, h->prob.cfl, nx));
   if (rows[0].nl + rows[0].nr == 0) return fail(MGRIT_ERR_UNSUPPORTED, "nx too small for the boundary closures");
-  for (const CoarseOp& op : h->ops) {
-    if (nx < op.taps.hi() - op.taps.lo() + 1)
-      return fail(MGRIT_ERR_UNSUPPORTED, "a coarse stencil is wider than the domain");
-    rows.push_back(truncated_rows(op.taps, nx));
-  }
+  // Phi^m's rows for the collapsed path (dropped if its blocks would meet)
+  rows.push_back(h->have_phim ? inflow_phi_rows(h->prob.rk_order, h->prob.upwind_order, h->prob.cfl, nx, h->m)
+                              : BoundaryRows{});
+  if (rows[1].nl + rows[1].nr == 0) h->have_phim = false;
   std::vector<double> w64;
   for (const BoundaryRows& b : rows) w64.insert(w64.end(), b.w.begin(), b.w.end());
   const size_t n = std::max<size_t>(w64.size(), 1);
@@ -746,7 +750,7 @@ static mgrit_status upload_boundaries(mgrit_handle* h) {
     const BoundaryRows& b = rows[k];
     const Fixup f = {b.nl, b.cl, b.nr, b.cr, tab + pos, tab32 + pos};
     if (k == 0) h->fx_phi = f;
-    else h->fx_psi[k - 1] = f;
+    else h->fx_phim = f;
     pos += b.w.size();
   }
   return MGRIT_OK;
@@ -834,7 +838,7 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
     }
   h->dphi = to_dev(h->phi);
   h->inflow = prob->boundary == MGRIT_BC_INFLOW;
-  if (!h->sdirk && !h->inflow) {  // Phi^m as one stencil (the m-step propagator of an interval)
+  if (!h->sdirk) {  // Phi^m as one stencil (the m-step propagator of an interval)
     Taps pm = taps_power(h->phi, h->m);
     const int reach = std::max(-pm.lo(), pm.hi());
     if (pm.size() <= kMaxDevTaps && pm.size() + 8 < h->nx && reach + 8 < h->nx) {  // indices wrap at most once
@@ -914,7 +918,6 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
     delete h;
     return st;
   }
-  h->fx_psi.assign(h->ops.size(), Fixup{});
   if (h->inflow && (st = upload_boundaries(h)) != MGRIT_OK) {
     release(h);
     delete h;
@@ -960,13 +963,8 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
   h->fcf_threads = 0;  // chosen per launch from nx and the register tile
   if (const char* tile = std::getenv("MGRIT_TILE")) set_tile(std::atoi(tile));
   const Taps& coarsest = h->ops.back().taps;
-  if (h->inflow) {  // zero-padded periodic domain: pad >= the stencil's reach, a multiple of 16 in all
-    const int pad = std::max(-coarsest.lo(), coarsest.hi());
-    h->march_nxp = (nx + pad + 15) / 16 * 16;
-  }
-  const int march_np = h->march_nxp ? h->march_nxp : nx;
-  h->march_cluster = pick_cluster(march_np, coarsest);
-  h->march_threads = std::min(256, march_np / h->march_cluster);
+  h->march_cluster = pick_cluster(nx, coarsest);
+  h->march_threads = std::min(256, nx / h->march_cluster);
   const double tt = now_s();
   autotune_fine(h);
   h->tune_s = now_s() - tt;
@@ -1058,9 +1056,8 @@ void collect_stats(mgrit_handle* h, mgrit_result* R) {
 // Launch a march, shrinking the cluster if the device refuses the size.
 mgrit_status run_march(mgrit_handle* h, const MarchArgs& a, const DevTaps& t) {
   return klaunch(h, MGRIT_K_MARCH, "march", [&]() -> mgrit_status {
-    const int np = a.nxp > a.nx ? a.nxp : a.nx;
     for (;;) {
-      int threads = std::min(256, np / h->march_cluster);
+      int threads = std::min(256, a.nx / h->march_cluster);
       cudaError_t e = launch_march(a, t, h->march_cluster, threads, h->stream);
       if (e == cudaSuccess) return MGRIT_OK;
       cudaGetLastError();
@@ -1122,7 +1119,7 @@ mgrit_status relax_level(mgrit_handle* h, int l, bool from_zero) {
   f.m = m;
   f.N = h->Nl[l];
   f.zero_old = from_zero ? 1 : 0;
-  f.fx = h->fx_psi[l - 2];
+  f.trunc = h->inflow;
   return klaunch(h, MGRIT_K_FCF_COARSE, "fcf", [&] {
     return launch_ok(launch_fcf(f, h->dpsi[l - 2], prec, h->fcf_threads, h->stream), "fcf(coarse)");
   });
@@ -1138,7 +1135,7 @@ mgrit_status solve_coarsest(mgrit_handle* h) {
   a.u_out_f = h->uf[L];
   a.store_every = 1;
   a.nx = h->nx;
-  a.nxp = h->march_nxp;
+  a.trunc = h->inflow;
   a.P = h->Nl[L - 1] + 1;
   return run_march(h, a, h->dpsi[L - 2]);
 }
@@ -1158,7 +1155,7 @@ mgrit_status correct_level(mgrit_handle* h, int l) {
   c.nx = h->nx;
   c.m = h->m;
   c.N = h->Nl[l];
-  c.fx = h->fx_psi[l - 2];
+  c.trunc = h->inflow;
   return klaunch(h, MGRIT_K_CORRECT, "correct", [&] {
     return launch_ok(launch_correct(c, h->dpsi[l - 2], h->fcf_threads, h->stream, prec == 2), "correct");
   });
@@ -1202,7 +1199,7 @@ mgrit_status coarse_cycle(mgrit_handle* h, double* c_new) {
     a.g_f = h->rf[1];
     a.c_add = c_new;
     a.nx = nx;
-    a.nxp = h->march_nxp;
+    a.trunc = h->inflow;
     a.P = h->Nl[1] + 1;
     a.store_every = 1;
     return run_march(h, a, h->dpsi[0]);
@@ -1630,9 +1627,12 @@ extern "C" mgrit_status mgrit_propagate(mgrit_handle* h, int32_t level, int32_t 
       return launch_ok(launch_propagate_sdirk(in, out, count, h->nx, k, h->splan, nullptr, h->stream), "propagate");
     if (level == 2 && h->redisc)
       return launch_ok(launch_propagate_sdirk(in, out, count, h->nx, k, h->cplan, nullptr, h->stream), "propagate");
-    const Fixup& fx = level == 1 ? h->fx_phi : h->fx_psi[level - 2];
-    return launch_ok(launch_propagate(in, out, count, h->nx, k, t, nullptr, h->fcf_threads, h->stream, &fx),
-                     "propagate");
+    if (level == 1)
+      return launch_ok(launch_propagate(in, out, count, h->nx, k, t, nullptr, h->fcf_threads, h->stream, &h->fx_phi),
+                       "propagate");
+    return launch_ok(
+        launch_propagate(in, out, count, h->nx, k, t, nullptr, h->fcf_threads, h->stream, nullptr, h->inflow),
+        "propagate");
   });
   if (st != MGRIT_OK) return st;
   CUDA_TRY(cudaStreamSynchronize(h->stream));

@@ -35,13 +35,12 @@ struct mgrit_handle {
   bool redisc = false;              // Psi = the SDIRK step at m dt (cplan)
   mg::SdirkPlan cplan;
   std::vector<mg::DevTaps> dpsi;      // dpsi[l-2]
-  // Inflow/outflow boundaries (Section 4.5): the rows of Phi and of each
-  // truncated Psi_l that differ from the circulant (device tables), and the
-  // period of the zero-padded coarsest-level march (0 = periodic)
+  // Inflow/outflow boundaries (Section 4.5): the rows of Phi and Phi^m that
+  // differ from the circulant (device tables); every Psi_l is truncated at
+  // both ends by the kernels' loads
   bool inflow = false;
   mg::Fixup fx_phi = {};
-  std::vector<mg::Fixup> fx_psi;      // fx_psi[l-2]
-  int march_nxp = 0;
+  mg::Fixup fx_phim = {};             // of Phi^m (the collapsed path)
   std::vector<DevBuf> bufs;       // everything allocated, for release
   double* c[2] = {nullptr, nullptr};
   std::vector<double*> r, u, cnew;  // indexed by level (size L+1)

@@ -9,9 +9,10 @@
 //   propagate_kernel                  T^k applied to a batch of vectors
 //   seq_slab_kernel                   sequential stepping of a non-periodic level
 // Every stencil is a circulant (Corollary 1): periodic indices wrap modulo nx.
-// On the inflow/outflow domain (Section 4.5) the rows that reach past either
-// end are recomputed after each step from their own coefficients (Fixup), and
-// the march runs on a zero-padded periodic domain (truncated Toeplitz Psi).
+// On the inflow/outflow domain (Section 4.5) the rows of Phi that reach past
+// either end are recomputed after each step from their own coefficients
+// (Fixup); Psi is truncated at both ends (Toeplitz): its taps read zero
+// outside the domain (TR).
 #include <cooperative_groups.h>
 
 #include <cstring>
@@ -147,13 +148,22 @@ __device__ __forceinline__ df64 sparse_coef<df64>(const DevTaps& t, int k) { ret
 template <>
 __device__ __forceinline__ df64 dense_coef<df64>(const DevTaps& t, int k) { return {t.dhi[k], t.dlo[k]}; }
 
+// Element k of a slab for a stencil row: periodic (k wraps at most once), or
+// for a stencil truncated at both ends (TR: Psi on the inflow/outflow domain,
+// Section 4.5) zero outside 0..nx-1.
+template <bool TR, typename T>
+__device__ __forceinline__ T sld(const T* __restrict__ s, int k, int nx) {
+  if constexpr (TR) return (unsigned)k < (unsigned)nx ? s[pidx(k)] : vzero<T>();
+  else return s[pidx(wrapi(k, nx))];
+}
+
 // dst = T src (+ g): one tap at a time, any offsets (padded layout).
-template <typename T, typename G>
+template <typename T, typename G, bool TR = false>
 __device__ __forceinline__ void step_sparse(const DevTaps& t, const T* __restrict__ src, T* __restrict__ dst,
                                            const G* __restrict__ g, int nx) {
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     T acc = g ? gload<T>(g + i) : vzero<T>();
-    for (int k = 0; k < t.n; ++k) acc = vfma<T>(sparse_coef<T>(t, k), src[pidx(wrapi(i + t.off[k], nx))], acc);
+    for (int k = 0; k < t.n; ++k) acc = vfma<T>(sparse_coef<T>(t, k), sld<TR>(src, i + t.off[k], nx), acc);
     dst[pidx(i)] = vfinish<T>(acc);
   }
 }
@@ -162,7 +172,7 @@ __device__ __forceinline__ void step_sparse(const DevTaps& t, const T* __restric
 // outputs from a sliding window of R inputs that advances one offset per tap,
 // so each tap costs one shared load and R FMAs.  Needs the dense form and
 // nx >= 64 (so that every index below wraps at most once).
-template <typename T, int R, typename G>
+template <typename T, int R, typename G, bool TR = false>
 __device__ __forceinline__ void step_tiled(const DevTaps& t, const T* __restrict__ src, T* __restrict__ dst,
                                            const G* __restrict__ g, int nx) {
   const int lo = t.lo, span = t.span;
@@ -171,7 +181,7 @@ __device__ __forceinline__ void step_tiled(const DevTaps& t, const T* __restrict
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       acc[r] = (g && i0 + r < nx) ? gload<T>(g + i0 + r) : vzero<T>();
-      w[r] = src[pidx(wrapi(i0 + lo + r, nx))];
+      w[r] = sld<TR>(src, i0 + lo + r, nx);
     }
     for (int k = 0; k < span; ++k) {
       const T c = dense_coef<T>(t, k);
@@ -181,7 +191,7 @@ __device__ __forceinline__ void step_tiled(const DevTaps& t, const T* __restrict
       }
 #pragma unroll
       for (int r = 0; r < R - 1; ++r) w[r] = w[r + 1];
-      w[R - 1] = src[pidx(wrapi(i0 + lo + k + R, nx))];
+      w[R - 1] = sld<TR>(src, i0 + lo + k + R, nx);
     }
 #pragma unroll
     for (int r = 0; r < R; ++r)
@@ -248,10 +258,13 @@ __device__ __forceinline__ void step_chunked(const DevTaps& t, const T* __restri
 
 // R encodes the path: 0 one tap at a time; 4, 8 sliding window; SPAN > 0
 // selects the fixed-span path with register tile R; SPAN == kChunked the
-// chunked path.
-template <typename T, int R, int SPAN = 0, typename G = double>
+// chunked path.  TR (truncated stencil) exists for the first two.
+template <typename T, int R, int SPAN = 0, bool TR = false, typename G = double>
 __device__ __forceinline__ void slab_step(const DevTaps& t, const T* src, T* dst, const G* g, int nx) {
-  if constexpr (SPAN == kChunked) step_chunked<T, R, 8, G>(t, src, dst, g, nx);
+  static_assert(!TR || SPAN == 0, "truncated stencils use the sliding-window or one-tap path");
+  if constexpr (TR && R > 0) step_tiled<T, R, G, true>(t, src, dst, g, nx);
+  else if constexpr (TR) step_sparse<T, G, true>(t, src, dst, g, nx);
+  else if constexpr (SPAN == kChunked) step_chunked<T, R, 8, G>(t, src, dst, g, nx);
   else if constexpr (SPAN > 0) step_fixed<T, R, SPAN, G>(t, src, dst, g, nx);
   else if constexpr (R > 0) step_tiled<T, R, G>(t, src, dst, g, nx);
   else step_sparse<T, G>(t, src, dst, g, nx);
@@ -303,10 +316,10 @@ __device__ __forceinline__ void fixup_rows(const Fixup& f, const T* __restrict__
 
 // slab_step, then (non-periodic levels) the boundary rows; the caller's
 // barrier after the step covers the fix-up as well.
-template <typename T, int R, int SPAN = 0, typename G = double>
+template <typename T, int R, int SPAN = 0, bool TR = false, typename G = double>
 __device__ __forceinline__ void slab_step_fx(const DevTaps& t, const Fixup& fx, const T* src, T* dst, const G* g,
                                              int nx) {
-  slab_step<T, R, SPAN, G>(t, src, dst, g, nx);
+  slab_step<T, R, SPAN, TR, G>(t, src, dst, g, nx);
   if (fx.nl + fx.nr) {
     __syncthreads();
     fixup_rows<T, G>(fx, src, dst, g, nx, t.one);
@@ -337,7 +350,7 @@ __device__ double block_sum(double v) {
 // PREC 2: both passes in FP32 with FP32 storage (coarse levels of the mixed
 // modes, where every quantity is a correction of the error equation): reads
 // u_old_f and g_f, writes c_new_f and r_f.
-template <int R, int SPAN = 0>
+template <int R, int SPAN = 0, bool TR = false>
 __device__ __forceinline__ void fcf_body_fp32(const FcfArgs& a, const int j, const DevTaps& t, unsigned char* smraw) {
   const int nx = a.nx, m = a.m, plen = padded_len(nx);
   float* b0 = reinterpret_cast<float*>(smraw);
@@ -352,7 +365,7 @@ __device__ __forceinline__ void fcf_body_fp32(const FcfArgs& a, const int j, con
   const bool run1 = __syncthreads_or(nz) || a.g_f;  // zero slab, no rhs: Phi^m 0 = 0
   for (int s = 1; s <= m && run1; ++s) {
     const float* g = a.g_f ? a.g_f + ((long long)(j - 1) * m + s) * nx : nullptr;
-    slab_step_fx<float, R, SPAN>(t, a.fx, b0, b1, g, nx);
+    slab_step_fx<float, R, SPAN, TR>(t, a.fx, b0, b1, g, nx);
     __syncthreads();
     float* tmp = b0; b0 = b1; b1 = tmp;
   }
@@ -371,7 +384,7 @@ __device__ __forceinline__ void fcf_body_fp32(const FcfArgs& a, const int j, con
   float* x0 = b1;
   float* x1 = b0;
   for (int s = 1; s <= m && run2; ++s) {
-    slab_step_fx<float, R, SPAN>(t, a.fx, x0, x1, kNoG, nx);
+    slab_step_fx<float, R, SPAN, TR>(t, a.fx, x0, x1, kNoG, nx);
     __syncthreads();
     float* tmp = x0; x0 = x1; x1 = tmp;
   }
@@ -441,7 +454,7 @@ __device__ __forceinline__ void store_f_relaxation(const FcfArgs& a, int j, cons
 
 // PREC 3: pass 1 (C-point update and residual rho) in float-float, pass 2 in
 // FP32.  A df64 slab occupies as many bytes as an FP64 slab.
-template <int R, int SPAN = 0>
+template <int R, int SPAN = 0, bool TR = false>
 __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const DevTaps& t, unsigned char* smraw) {
   const int nx = a.nx, m = a.m, plen = padded_len(nx);
   df64* b0 = reinterpret_cast<df64*>(smraw);
@@ -456,7 +469,7 @@ __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const
   const bool run1 = __syncthreads_or(nz) || a.g;  // zero slab, no rhs: Phi^m 0 = 0
   for (int s = 1; s <= m && run1; ++s) {
     const double* g = a.g ? a.g + ((long long)(j - 1) * m + s) * nx : nullptr;
-    slab_step_fx<df64, R, SPAN>(t, a.fx, b0, b1, g, nx);
+    slab_step_fx<df64, R, SPAN, TR>(t, a.fx, b0, b1, g, nx);
     __syncthreads();
     df64* tmp = b0; b0 = b1; b1 = tmp;
   }
@@ -479,21 +492,21 @@ __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const
   const bool run2 = __syncthreads_or(nz);
   if (j >= a.N) return;
   for (int s = 1; s <= m && run2; ++s) {
-    slab_step_fx<float, R, SPAN>(t, a.fx, f0, f1, kNoG, nx);
+    slab_step_fx<float, R, SPAN, TR>(t, a.fx, f0, f1, kNoG, nx);
     __syncthreads();
     float* tmp = f0; f0 = f1; f1 = tmp;
   }
   store_residual_f32(a, j, f0);
 }
 
-template <int PREC, int R, int SPAN = 0>
+template <int PREC, int R, int SPAN = 0, bool TR = false>
 __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const DevTaps& t, unsigned char* smraw) {
   if constexpr (PREC == 2) {
-    fcf_body_fp32<R, SPAN>(a, j, t, smraw);
+    fcf_body_fp32<R, SPAN, TR>(a, j, t, smraw);
     return;
   }
   if constexpr (PREC == 3) {
-    fcf_body_df<R, SPAN>(a, j, t, smraw);
+    fcf_body_df<R, SPAN, TR>(a, j, t, smraw);
     return;
   }
   const int nx = a.nx, m = a.m, plen = padded_len(nx);
@@ -511,7 +524,7 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
   const bool run1 = __syncthreads_or(nz) || a.g;
   for (int s = 1; s <= m && run1; ++s) {
     const double* g = a.g ? a.g + ((long long)(j - 1) * m + s) * nx : nullptr;
-    slab_step_fx<double, R, SPAN>(t, a.fx, b0, b1, g, nx);
+    slab_step_fx<double, R, SPAN, TR>(t, a.fx, b0, b1, g, nx);
     __syncthreads();
     double* tmp = b0; b0 = b1; b1 = tmp;
   }
@@ -537,7 +550,7 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
     double* x0 = b1;
     double* x1 = b0;
     for (int s = 1; s <= m && run2; ++s) {
-      slab_step_fx<double, R, SPAN>(t, a.fx, x0, x1, kNoG, nx);
+      slab_step_fx<double, R, SPAN, TR>(t, a.fx, x0, x1, kNoG, nx);
       __syncthreads();
       double* tmp = x0; x0 = x1; x1 = tmp;
     }
@@ -562,7 +575,7 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
     const bool run2 = __syncthreads_or(nz);
     if (!more) return;
     for (int s = 1; s <= m && run2; ++s) {
-      slab_step_fx<float, R, SPAN>(t, a.fx, f0, f1, kNoG, nx);
+      slab_step_fx<float, R, SPAN, TR>(t, a.fx, f0, f1, kNoG, nx);
       __syncthreads();
       float* tmp = f0; f0 = f1; f1 = tmp;
     }
@@ -575,10 +588,10 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
   }
 }
 
-template <int PREC, int R, int SPAN = 0>
+template <int PREC, int R, int SPAN = 0, bool TR = false>
 __global__ void __launch_bounds__(R == 8 ? 512 : 1024) fcf_kernel(const FcfArgs a, const DevTaps t) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  fcf_body<PREC, R, SPAN>(a, blockIdx.x + 1, t, smraw);
+  fcf_body<PREC, R, SPAN, TR>(a, blockIdx.x + 1, t, smraw);
 }
 
 // Batched: one CTA per (solve, interval) item across all admitted solves; the
@@ -618,21 +631,20 @@ __device__ __forceinline__ int modnx(long long v, int nx) {
   return (int)(r < 0 ? r + nx : r);
 }
 
-template <int PPT, bool PAD = false>
+template <int PPT, bool TR = false>
 __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t, unsigned char* smraw,
                                            cg::cluster_group& cl) {
   const int cs = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
-  // np: period of the frame (the zero-padded domain of a non-periodic level)
-  const int nx = a.nx, np = PAD ? a.nxp : nx, w = np / cs, base = rank * w;
+  const int nx = a.nx, w = nx / cs, base = rank * w;
   const int sigma = t.shift;
   const int L = sigma - t.lo, R = t.hi - sigma, W = L + w + R;
   double* B0 = reinterpret_cast<double*>(smraw);
   double* B1 = B0 + W;
   const int tid = threadIdx.x, bs = blockDim.x;
   for (int k = tid; k < W; k += bs) {
-    const int gi = modnx((long long)base - L + k, np);
-    B0[k] = (a.init && (!PAD || gi < nx)) ? a.init[gi] : 0.0;
+    const int gi = modnx((long long)base - L + k, nx);
+    B0[k] = a.init ? a.init[gi] : 0.0;
   }
   __syncthreads();
   // next step's right-hand side and C-points, loaded one step ahead (an FP32
@@ -645,16 +657,15 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
       const int i = tid + p * bs;
-      const int gi = wrapi(base + i + Sn, np);
-      if (i < w && (!PAD || gi < nx)) {
-        const long long o = (long long)n * nx + gi;
+      if (i < w) {
+        const long long o = (long long)n * nx + wrapi(base + i + Sn, nx);
         if (a.g_f) gqf[p] = __ldcg(a.g_f + o);
         else if (a.g) gq[p] = __ldcg(a.g + o);
         if (a.c_add) cq[p] = __ldcg(a.c_add + o);
       }
     }
   };
-  int S = modnx(-(long long)sigma, np);  // S_1
+  int S = modnx(-(long long)sigma, nx);  // S_1
   if (a.P > 1) prefetch(1, S);
   for (int n = 1; n < a.P; ++n) {
     double* cur = (n & 1) ? B0 : B1;
@@ -662,7 +673,7 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
     double gc[PPT], cc[PPT];
 #pragma unroll
     for (int p = 0; p < PPT; ++p) { gc[p] = a.g_f ? (double)gqf[p] : gq[p]; cc[p] = cq[p]; }
-    const int Snext = modnx((long long)S - sigma, np);
+    const int Snext = modnx((long long)S - sigma, nx);
     if (n + 1 < a.P) prefetch(n + 1, Snext);
     const bool store = (a.u_out || a.u_out_f) && (n % a.store_every) == 0;
 #pragma unroll
@@ -671,11 +682,12 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
       if (i < w) {
         double acc = gc[p];
         const double* c = cur + L + i - sigma;
-        for (int k = 0; k < t.n; ++k) acc = fma(t.c64[k], c[t.off[k]], acc);
-        const int gi = wrapi(base + i + S, np);
-        if (PAD && gi >= nx) {  // the zero padding stays zero
-          nxt[L + i] = 0.0;
-          continue;
+        const int gi = wrapi(base + i + S, nx);
+        if constexpr (TR) {  // truncated stencil: the taps whose column gi + off leaves 0..nx-1 drop out
+          for (int k = 0; k < t.n; ++k)
+            if ((unsigned)(gi + t.off[k]) < (unsigned)nx) acc = fma(t.c64[k], c[t.off[k]], acc);
+        } else {
+          for (int k = 0; k < t.n; ++k) acc = fma(t.c64[k], c[t.off[k]], acc);
         }
         nxt[L + i] = acc;
         if (a.c_add) a.c_add[(long long)n * nx + gi] = cc[p] + acc;
@@ -691,7 +703,7 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
       int dst, fi;
       if (k < L) { dst = k; fi = base - L + k; }
       else { dst = w + k; fi = base + w + (k - L); }
-      fi = modnx(fi, np);
+      fi = modnx(fi, nx);
       const int owner = fi / w, loc = fi - owner * w;
       const double* rem = cl.map_shared_rank(nxt, owner);
       nxt[dst] = rem[L + loc];
@@ -702,11 +714,11 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
   cl.sync();  // no CTA leaves while a neighbour may still read its shared memory
 }
 
-template <int PPT, bool PAD>
+template <int PPT, bool TR>
 __global__ void __launch_bounds__(256) march_kernel(const MarchArgs a, const DevTaps t) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cg::cluster_group cl = cg::this_cluster();
-  march_body<PPT, PAD>(a, t, smraw, cl);
+  march_body<PPT, TR>(a, t, smraw, cl);
 }
 
 // Batched two-level coarse solve: cluster c marches solve ids[c] with its
@@ -752,7 +764,7 @@ __device__ __forceinline__ T* pick(double* d, float* f) {
 
 // Storage of the level in T: FP64 fields for T = double, FP32 fields for
 // T = float (FP32 coarse levels).
-template <typename T, int R>
+template <typename T, int R, bool TR = false>
 __global__ void __launch_bounds__(R == 8 ? 512 : 1024) correct_kernel(const CorrectArgs a, const DevTaps t) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nx = a.nx, m = a.m, j = blockIdx.x + 1, plen = padded_len(nx);
@@ -771,7 +783,7 @@ __global__ void __launch_bounds__(R == 8 ? 512 : 1024) correct_kernel(const Corr
   __syncthreads();
   for (int s = 1; s < m; ++s) {
     const T* g = gg ? gg + (p0 + s) * nx : nullptr;
-    slab_step_fx<T, R>(t, a.fx, b0, b1, g, nx);
+    slab_step_fx<T, R, 0, TR>(t, a.fx, b0, b1, g, nx);
     __syncthreads();
     for (int i = threadIdx.x; i < nx; i += blockDim.x) u[(p0 + s) * nx + i] = b1[pidx(i)];
     T* tmp = b0; b0 = b1; b1 = tmp;
@@ -839,7 +851,7 @@ __global__ void add_f_kernel(double* __restrict__ c, const float* __restrict__ e
     c[i] += (double)e[i];
 }
 
-template <int R>
+template <int R, bool TR = false>
 __global__ void __launch_bounds__(R == 8 ? 512 : 1024) propagate_kernel(const double* in, double* out, int nx, int k,
                                                          const DevTaps t, double* partial, const Fixup fx) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -850,7 +862,7 @@ __global__ void __launch_bounds__(R == 8 ? 512 : 1024) propagate_kernel(const do
   for (int i = threadIdx.x; i < nx; i += blockDim.x) b0[pidx(i)] = in[v * nx + i];
   __syncthreads();
   for (int s = 0; s < k; ++s) {
-    slab_step_fx<double, R>(t, fx, b0, b1, kNoG, nx);
+    slab_step_fx<double, R, 0, TR>(t, fx, b0, b1, kNoG, nx);
     __syncthreads();
     double* tmp = b0; b0 = b1; b1 = tmp;
   }
@@ -929,12 +941,12 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaSuccess;
 }
 
-template <int PREC, int R, int SPAN = 0>
+template <int PREC, int R, int SPAN = 0, bool TR = false>
 static cudaError_t launch_fcf_t(const FcfArgs& a, const DevTaps& t, int threads, cudaStream_t s) {
   const size_t smem = 2 * (size_t)padded_len(a.nx) * (PREC == 2 ? sizeof(float) : sizeof(double));
-  cudaError_t e = set_smem(fcf_kernel<PREC, R, SPAN>, smem);
+  cudaError_t e = set_smem(fcf_kernel<PREC, R, SPAN, TR>, smem);
   if (e != cudaSuccess) return e;
-  fcf_kernel<PREC, R, SPAN><<<a.N, threads_for(a.nx, R, threads), smem, s>>>(a, t);
+  fcf_kernel<PREC, R, SPAN, TR><<<a.N, threads_for(a.nx, R, threads), smem, s>>>(a, t);
   return cudaGetLastError();
 }
 
@@ -958,6 +970,18 @@ static cudaError_t launch_fcf_fixed(const FcfArgs& a, const DevTaps& t, int thre
 
 cudaError_t launch_fcf(const FcfArgs& a, const DevTaps& t, int precision, int threads, cudaStream_t s, int tile) {
   if (a.N < 1) return cudaSuccess;
+  if (a.trunc) {  // truncated coarse stencils: FP64 or FP32 levels, sliding window or one tap at a time
+    if (tile == kChunkTile || tile == kFixedTile || (precision != 0 && precision != 2)) return cudaErrorInvalidValue;
+    const int R = (tile >= 0 && (tile == 0 || (t.span > 0 && a.nx >= 64))) ? tile : tile_for(t, a.nx);
+    if (precision == 0) {
+      if (R == 8) return launch_fcf_t<0, 8, 0, true>(a, t, threads, s);
+      if (R == 4) return launch_fcf_t<0, 4, 0, true>(a, t, threads, s);
+      return launch_fcf_t<0, 0, 0, true>(a, t, threads, s);
+    }
+    if (R == 8) return launch_fcf_t<2, 8, 0, true>(a, t, threads, s);
+    if (R == 4) return launch_fcf_t<2, 4, 0, true>(a, t, threads, s);
+    return launch_fcf_t<2, 0, 0, true>(a, t, threads, s);
+  }
   if (tile == kChunkTile) {
     if (!(t.span > 0) || a.nx < 64) return cudaErrorInvalidValue;
     switch (precision) {
@@ -1052,19 +1076,17 @@ static cudaError_t launch_cluster(K kernel, int grid, int cluster, int threads, 
 
 template <int PPT>
 static cudaError_t launch_march_t(const MarchArgs& a, const DevTaps& t, int cluster, int threads, cudaStream_t s) {
-  const bool pad = a.nxp > a.nx;
-  const int w = (pad ? a.nxp : a.nx) / cluster;
+  const int w = a.nx / cluster;
   const size_t smem = 2 * (size_t)(w + t.hi - t.lo) * sizeof(double);
   MarchArgs aa = a;
   DevTaps tt = t;
   void* args[] = {&aa, &tt};
-  if (pad) return launch_cluster(march_kernel<PPT, true>, cluster, cluster, threads, smem, s, args);
+  if (a.trunc) return launch_cluster(march_kernel<PPT, true>, cluster, cluster, threads, smem, s, args);
   return launch_cluster(march_kernel<PPT, false>, cluster, cluster, threads, smem, s, args);
 }
 
 cudaError_t launch_march(const MarchArgs& a, const DevTaps& t, int cluster, int threads, cudaStream_t s) {
-  if (a.nxp > a.nx && (a.nxp < a.nx + (-t.lo > t.hi ? -t.lo : t.hi) || a.nxp % cluster)) return cudaErrorInvalidValue;
-  const int w = (a.nxp > a.nx ? a.nxp : a.nx) / cluster;
+  const int w = a.nx / cluster;
   const int ppt = (w + threads - 1) / threads;
   if (a.P < 2) return cudaSuccess;
   switch (ppt) {
@@ -1108,26 +1130,32 @@ cudaError_t launch_march_batched(const BatchSolve* S, const int* ids, int count,
 
 int march_max_cluster() { return 16; }
 
-template <typename T, int R>
+template <typename T, int R, bool TR>
 static cudaError_t launch_correct_t(const CorrectArgs& a, const DevTaps& t, int threads, cudaStream_t s) {
   const size_t smem = 2 * (size_t)padded_len(a.nx) * sizeof(T);
-  cudaError_t e = set_smem(correct_kernel<T, R>, smem);
+  cudaError_t e = set_smem(correct_kernel<T, R, TR>, smem);
   if (e != cudaSuccess) return e;
-  correct_kernel<T, R><<<a.N, threads_for(a.nx, R, threads), smem, s>>>(a, t);
+  correct_kernel<T, R, TR><<<a.N, threads_for(a.nx, R, threads), smem, s>>>(a, t);
   return cudaGetLastError();
+}
+
+template <bool TR>
+static cudaError_t launch_correct_tr(const CorrectArgs& a, const DevTaps& t, int threads, cudaStream_t s, int fp32) {
+  const int R = tile_for(t, a.nx);
+  if (fp32) {
+    if (R == 8) return launch_correct_t<float, 8, TR>(a, t, threads, s);
+    if (R == 4) return launch_correct_t<float, 4, TR>(a, t, threads, s);
+    return launch_correct_t<float, 0, TR>(a, t, threads, s);
+  }
+  if (R == 8) return launch_correct_t<double, 8, TR>(a, t, threads, s);
+  if (R == 4) return launch_correct_t<double, 4, TR>(a, t, threads, s);
+  return launch_correct_t<double, 0, TR>(a, t, threads, s);
 }
 
 cudaError_t launch_correct(const CorrectArgs& a, const DevTaps& t, int threads, cudaStream_t s, int fp32) {
   if (a.N < 1) return cudaSuccess;
-  const int R = tile_for(t, a.nx);
-  if (fp32) {
-    if (R == 8) return launch_correct_t<float, 8>(a, t, threads, s);
-    if (R == 4) return launch_correct_t<float, 4>(a, t, threads, s);
-    return launch_correct_t<float, 0>(a, t, threads, s);
-  }
-  if (R == 8) return launch_correct_t<double, 8>(a, t, threads, s);
-  if (R == 4) return launch_correct_t<double, 4>(a, t, threads, s);
-  return launch_correct_t<double, 0>(a, t, threads, s);
+  if (a.trunc) return launch_correct_tr<true>(a, t, threads, s, fp32);
+  return launch_correct_tr<false>(a, t, threads, s, fp32);
 }
 
 cudaError_t launch_residual_value(const double* c_new, double* r, double* partial, int nx, int N, cudaStream_t s) {
@@ -1169,24 +1197,29 @@ cudaError_t launch_add_f(double* c, const float* e, long long count, cudaStream_
   return cudaGetLastError();
 }
 
-template <int R>
+template <int R, bool TR>
 static cudaError_t launch_propagate_t(const double* in, double* out, int count, int nx, int k, const DevTaps& t,
                                       double* partial, int threads, cudaStream_t s, const Fixup& fx) {
   const size_t smem = 2 * (size_t)padded_len(nx) * sizeof(double);
-  cudaError_t e = set_smem(propagate_kernel<R>, smem);
+  cudaError_t e = set_smem(propagate_kernel<R, TR>, smem);
   if (e != cudaSuccess) return e;
-  propagate_kernel<R><<<count, threads_for(nx, R, threads), smem, s>>>(in, out, nx, k, t, partial, fx);
+  propagate_kernel<R, TR><<<count, threads_for(nx, R, threads), smem, s>>>(in, out, nx, k, t, partial, fx);
   return cudaGetLastError();
 }
 
 cudaError_t launch_propagate(const double* in, double* out, int count, int nx, int k, const DevTaps& t,
-                             double* partial, int threads, cudaStream_t s, const Fixup* fx) {
+                             double* partial, int threads, cudaStream_t s, const Fixup* fx, int trunc) {
   if (count < 1) return cudaSuccess;
   const Fixup f = fx ? *fx : Fixup{};
   const int R = tile_for(t, nx);
-  if (R == 8) return launch_propagate_t<8>(in, out, count, nx, k, t, partial, threads, s, f);
-  if (R == 4) return launch_propagate_t<4>(in, out, count, nx, k, t, partial, threads, s, f);
-  return launch_propagate_t<0>(in, out, count, nx, k, t, partial, threads, s, f);
+  if (trunc) {
+    if (R == 8) return launch_propagate_t<8, true>(in, out, count, nx, k, t, partial, threads, s, f);
+    if (R == 4) return launch_propagate_t<4, true>(in, out, count, nx, k, t, partial, threads, s, f);
+    return launch_propagate_t<0, true>(in, out, count, nx, k, t, partial, threads, s, f);
+  }
+  if (R == 8) return launch_propagate_t<8, false>(in, out, count, nx, k, t, partial, threads, s, f);
+  if (R == 4) return launch_propagate_t<4, false>(in, out, count, nx, k, t, partial, threads, s, f);
+  return launch_propagate_t<0, false>(in, out, count, nx, k, t, partial, threads, s, f);
 }
 
 template <int R>

@@ -241,7 +241,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     b.fcf.zero_old = 0;
     b.fcf.relax_f = h->opts.relax == MGRIT_RELAX_F;
     b.fcf.value_residual = fine_prec(h) == 0 && !b.fcf.relax_f;
-    b.fcf.fx = h->fx_phi;  // boundary rows (inflow/outflow problems)
+    b.fcf.fx = h->fine_collapse ? h->fx_phim : h->fx_phi;  // boundary rows (inflow/outflow problems)
     b.prec = fine_prec(h);
     b.taps = 2 * k;
     b.psi = 2 * k + 1;

@@ -271,62 +271,59 @@ static std::vector<double> inflow_step(const Tableau& tb, const Taps& L, int q, 
   return r;
 }
 
-BoundaryRows inflow_phi_rows(int rk_order, int upwind_order, double c, int nx) {
+BoundaryRows inflow_phi_rows(int rk_order, int upwind_order, double c, int nx, int m) {
   BoundaryRows B;
   const Tableau tb = erk_tableau(rk_order);
   const Taps L = dtL_taps(upwind_order, c);
-  if (tb.s == 0 || L.size() == 0) return B;
-  const int s = tb.s, lo = L.lo(), hi = L.hi();
-  const int nl = s * -lo, nr = s * hi;  // rows whose stages reach a ghost value
-  // the two ends stay apart: no row of one block reaches the other end
-  const int need = nl + nr + s * (hi - lo) + upwind_order + 2;
-  if (nx < need) return B;
-  // the blocks do not depend on nx beyond `need`: probe a short domain
-  const int np = std::min(nx, std::max(64, 2 * need));
-  std::vector<double> P((size_t)np * np);  // P[row * np + col]
+  if (tb.s == 0 || L.size() == 0 || m < 1) return B;
+  const int s = tb.s, lo = L.lo(), hi = L.hi(), q = upwind_order;
+  // rows of Phi^m whose m steps reach a ghost value: the rows that wrap in
+  // the circulant Phi^m
+  const int nl = m * s * -lo, nr = m * s * hi;
+  // the two ends stay apart (one step's closures)
+  if (nx < 2 * s * (hi - lo) + q + 2 || nl + nr > nx) return B;
+  // The blocks do not depend on nx once the m-step domains of dependence of
+  // the two blocks cannot meet: probe a short domain np (the whole domain
+  // when nx is shorter).
+  const int reach = m * (s * (hi - lo) + q + 1);
+  const int np = std::min(nx, std::max(64, nl + nr + 2 * reach + 64));
+  // Phi on np unknowns by columns, kept as row lists
+  std::vector<std::vector<std::pair<int, double>>> rows(np);
   std::vector<double> e(np, 0.0);
   for (int col = 0; col < np; ++col) {
     e[col] = 1.0;
-    const std::vector<double> v = inflow_step(tb, L, upwind_order, e);
+    const std::vector<double> v = inflow_step(tb, L, q, e);
     e[col] = 0.0;
-    for (int row = 0; row < np; ++row) P[(size_t)row * np + col] = v[row];
+    for (int row = 0; row < np; ++row)
+      if (v[row] != 0.0) rows[row].push_back({col, v[row]});
   }
+  // boundary row i of Phi^m = e_i^T Phi^m, by m row-vector products
+  auto power_row = [&](int i) {
+    std::vector<double> v(np, 0.0), w(np);
+    v[i] = 1.0;
+    for (int k = 0; k < m; ++k) {
+      std::fill(w.begin(), w.end(), 0.0);
+      for (int r = 0; r < np; ++r)
+        if (v[r] != 0.0)
+          for (const auto& cv : rows[r]) w[cv.first] += v[r] * cv.second;
+      v.swap(w);
+    }
+    return v;
+  };
+  std::vector<std::vector<double>> left, right;
+  for (int i = 0; i < nl; ++i) left.push_back(power_row(i));
+  for (int i = np - nr; i < np; ++i) right.push_back(power_row(i));
   int cl = 0, cmin = np;
-  for (int row = 0; row < nl; ++row)
+  for (const auto& v : left)
     for (int col = 0; col < np; ++col)
-      if (P[(size_t)row * np + col] != 0.0) cl = std::max(cl, col + 1);
-  for (int row = np - nr; row < np; ++row)
+      if (v[col] != 0.0) cl = std::max(cl, col + 1);
+  for (const auto& v : right)
     for (int col = 0; col < np; ++col)
-      if (P[(size_t)row * np + col] != 0.0) cmin = std::min(cmin, col);
+      if (v[col] != 0.0) cmin = std::min(cmin, col);
   const int cr = nr ? np - cmin : 0;
   B.nl = nl; B.cl = cl; B.nr = nr; B.cr = cr;
-  for (int row = 0; row < nl; ++row)
-    for (int col = 0; col < cl; ++col) B.w.push_back(P[(size_t)row * np + col]);
-  for (int row = np - nr; row < np; ++row)
-    for (int col = np - cr; col < np; ++col) B.w.push_back(P[(size_t)row * np + col]);
-  return B;
-}
-
-BoundaryRows truncated_rows(const Taps& t, int nx) {
-  BoundaryRows B;
-  const int lo = t.lo(), hi = t.hi();
-  if (nx < (hi - lo) + 1 || nx < -lo + hi) return B;
-  std::vector<double> d(hi - lo + 1, 0.0);
-  for (int k = 0; k < t.size(); ++k) d[t.off[k] - lo] += t.coef[k];
-  B.nl = -lo; B.cl = -lo ? hi - lo : 0;
-  B.nr = hi;  B.cr = hi ? hi - lo : 0;
-  for (int row = 0; row < B.nl; ++row)
-    for (int col = 0; col < B.cl; ++col) {
-      const int o = col - row;
-      B.w.push_back(o >= lo && o <= hi ? d[o - lo] : 0.0);
-    }
-  for (int r = 0; r < B.nr; ++r) {
-    const int row = nx - B.nr + r;
-    for (int cc = 0; cc < B.cr; ++cc) {
-      const int o = (nx - B.cr + cc) - row;
-      B.w.push_back(o >= lo && o <= hi ? d[o - lo] : 0.0);
-    }
-  }
+  for (const auto& v : left) B.w.insert(B.w.end(), v.begin(), v.begin() + cl);
+  for (const auto& v : right) B.w.insert(B.w.end(), v.end() - cr, v.end());
   return B;
 }
 

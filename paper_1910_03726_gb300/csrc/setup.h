@@ -82,15 +82,12 @@ struct BoundaryRows {
 // j: the outflow ghost u_{nx-1+j} = sum_k w_k u_{nx-1-k}.
 std::vector<double> extrapolation_weights(int q, int j);
 
-// Phi of ERKp+Uq with a homogeneous inflow condition at x = -1 (zero ghost
-// values left of the domain in every stage) and degree-q extrapolation to
-// the outflow ghosts in every stage; nx unknowns x_i = -1 + (i+1) dx.
-// Empty (nl = nr = 0) if nx is too small for the two ends to stay apart.
-BoundaryRows inflow_phi_rows(int rk_order, int upwind_order, double c, int nx);
-
-// A stencil truncated at both ends (Toeplitz): (T v)_r sums only the taps
-// whose column r + off lies in 0..nx-1.
-BoundaryRows truncated_rows(const Taps& t, int nx);
+// Phi^m of ERKp+Uq with a homogeneous inflow condition at x = -1 (zero
+// ghost values left of the domain in every stage) and degree-q
+// extrapolation to the outflow ghosts in every stage; nx unknowns
+// x_i = -1 + (i+1) dx.  Empty (nl = nr = 0) if nx is too small for the two
+// ends to stay apart.
+BoundaryRows inflow_phi_rows(int rk_order, int upwind_order, double c, int nx, int m = 1);
 
 // Weighted least-squares fit of Eq. 6 on the given offsets; nt_level sets
 // the Eq. 4 bound's horizon.

@@ -145,13 +145,33 @@ def test_phi_boundary_rows_match_oracle(capi, p):
 def test_inflow_validation(capi):
     prob = capi.problem(96, 64, "SDIRK", 2, 2, 1.0, boundary="inflow")
     ok = capi.problem(96, 64, "ERK", 3, 3, 1.0, boundary="inflow")
-    assert capi._lib.mgrit_phi_boundary(capi.C.byref(prob), 0, None, None) == -10  # ERK only
+    assert capi._lib.mgrit_phi_boundary(capi.C.byref(prob), 1, 0, None, None) == -10  # ERK only
     small = capi.problem(40, 64, "ERK", 5, 5, 1.5, boundary="inflow")
-    assert capi._lib.mgrit_phi_boundary(capi.C.byref(small), 0, None, None) == -10  # ends too close
+    assert capi._lib.mgrit_phi_boundary(capi.C.byref(small), 1, 0, None, None) == -10  # ends too close
     bad = capi.problem(96, 64, "ERK", 3, 3, 1.0)
     bad.boundary = 7
-    assert capi._lib.mgrit_phi_boundary(capi.C.byref(bad), 0, None, None) == -1
+    assert capi._lib.mgrit_phi_boundary(capi.C.byref(bad), 1, 0, None, None) == -1
     opts = capi.mgrit_opts_default(m=4, levels=2, psi_rule=capi.PSI_IDEAL)
     L = 1
     nnz = (capi.C.c_int32 * L)()
     assert capi._lib.mgrit_psi_plan(capi.C.byref(ok), capi.C.byref(opts), 0, nnz, None, None, None) == -10
+
+
+@pytest.mark.parametrize("p,m,nx", [(1, 16, 700), (3, 4, 700), (3, 8, 160), (5, 4, 900)])
+def test_phi_power_boundary_rows_match_oracle(capi, p, m, nx):
+    """Boundary rows of Phi^m (the collapsed path's): the oracle's dense
+    stage-wise Phi to the m-th power on the whole domain, also where the
+    library builds them on a shorter domain (nx = 700, 900)."""
+    from oracle import boundaries as bd
+    from oracle import schemes
+    c = schemes.cfl_number("ERK", p)
+    left, right = capi.mgrit_phi_boundary(capi.problem(nx, 64, "ERK", p, p, c, boundary="inflow"), m)
+    Pm = np.linalg.matrix_power(bd.dense_phi(bd.InflowStep(p, c, nx)), m)
+    nl, cl = left.shape
+    nr, cr = right.shape
+    s = {1: 1, 2: 2, 3: 3, 4: 4, 5: 6}[p]
+    lo, hi = min(schemes.dtL_taps(p, c)), max(schemes.dtL_taps(p, c))
+    assert (nl, nr) == (m * s * -lo, m * s * hi)
+    assert np.max(np.abs(left - Pm[:nl, :cl])) < 1e-13
+    assert np.all(np.abs(right - Pm[nx - nr:, nx - cr:]) < 1e-13)
+    assert np.all(Pm[:nl, cl:] == 0.0) and np.all(Pm[nx - nr:, : nx - cr] == 0.0)

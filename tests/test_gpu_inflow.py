@@ -132,6 +132,7 @@ CASES = [  # p, nx, nt, m, L, cycle, relax
     (3, 256, 1024, 4, 2, "V", "FCF"), (3, 256, 1024, 4, 3, "V", "FCF"), (3, 256, 1024, 4, 4, "F", "FCF"),
     (1, 200, 1600, 16, 2, "V", "FCF"), (5, 160, 512, 4, 3, "V", "FCF"), (2, 128, 512, 8, 2, "V", "F"),
     (4, 192, 768, 4, 3, "V", "F"),
+    (1, 256, 4096, 4, 5, "V", "FCF"),  # level-5 Psi shifted by most of the domain: mostly zero rows
 ]
 
 
@@ -146,6 +147,34 @@ def test_mgrit_parity_fp64(capi, case):
     assert res.converged == 1
     assert res.iterations == it
     assert rel(out, U[::m]) <= TOL
+
+
+@pytest.mark.parametrize("shape", ["98,256,1", "98,512,1", "8,256,1", "99,256,0", "98,256,0", "8,256,0", "0,128,0"])
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_launch_shapes(capi, monkeypatch, shape, precision):
+    """Every level-1 launch shape with the boundary rows: step by step (the
+    rows of Phi after each step) or the collapsed Phi^m (the rows of Phi^m
+    after each pass), in each precision; FP64 gives the oracle's iterations
+    and C-points, the mixed modes FP64 sequential stepping's C-points."""
+    monkeypatch.setenv("MGRIT_FCF_SHAPE", shape)
+    p, nx, nt, m, L = 3, 256, 1024, 8, 3
+    u0 = workloads.fourier_field(nx)
+    st, lev = oracle_levels(p, nx, nt, m, L)
+    U = omg.zero_iterate(u0, nt)
+    it, _ = omg.solve(lev, U, tol=1e-10)
+    res, out = gpu_solve(capi, p, nx, nt, m, L, u0, precision=precision)
+    tile, th, col = (int(v) for v in shape.split(","))
+    assert (res.fine_tile, res.fine_threads, res.fine_collapsed) == (tile, th, col)
+    assert res.converged == 1
+    if precision == 0:
+        assert res.iterations == it
+        assert rel(out, U[::m]) <= TOL
+    else:
+        ref = [u0]
+        for _ in range(nt):
+            ref.append(st(ref[-1]))
+        assert abs(res.iterations - it) <= 1
+        assert rel(out, np.array(ref)[::m]) <= 1e-9
 
 
 def test_full_output_interpolates_with_the_closures(capi):
