@@ -371,6 +371,55 @@ def inflow_variant(capi, stream):
     return out
 
 
+def measured_hbm_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def hbm_variant(capi, stream, steps=3):
+    """The memory-bound instance of the level-1 FCF: ERK1+U1 with m = 4
+    (collapsed Phi^4: 5 taps) on 4096 x 16384, V-cycle L = 4.  In MIXED_DF
+    both passes run on the FP32 pipes, so the kernel is bound by HBM: per
+    launch it must read every C-point slab once (FP64), write every new
+    C-point (FP64) and every residual slab (FP32), 20 B per point and
+    interval.  CUDA events around every level-1 FCF launch; the algorithmic
+    bytes of all launches over their total time, against the measured copy
+    bandwidth.  MIXED (FP64 first pass) alongside: FP64-bound there
+    (0.37 flop/B against a 0.18 flop/B ridge)."""
+    import torch
+    nx, nt, m, L = 4096, 16384, 4, 4
+    peak, src = measured_hbm_gbs()
+    prob = capi.problem(nx, nt, "ERK", 1, 1, 0.85)
+    u0 = torch.tensor(workloads.fourier_field(nx), device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    N1 = nt // m
+    out = {"nx": nx, "nt": nt, "m": m, "levels": L, "peak_gbs": peak, "peak_source": src,
+           "bytes_per_launch": N1 * nx * 20}
+    for name, prec in (("mixed_df", capi.PREC_MIXED_DF), ("mixed", capi.PREC_MIXED)):
+        o = capi.mgrit_opts_default(m=m, levels=L, precision=prec, tol=TOL, output=capi.OUT_FINAL,
+                                    flags=capi.FLAG_TIME_KERNELS)
+        h = capi.mgrit_setup(prob, o, stream=stream)
+        try:
+            capi.mgrit_solve(h, u0, None)
+            ms, n, solve_ms = 0.0, 0, []
+            for _ in range(steps):
+                flush.zero_()
+                r, _ = capi.mgrit_solve(h, u0, None)
+                ms += r.kernel_ms[0]
+                n += r.kernel_count[0]
+                solve_ms.append(1e3 * r.solve_s)
+            gbs = out["bytes_per_launch"] * n / (ms * 1e-3) / 1e9
+            out[name] = {"fcf_launch_ms": ms / n, "achieved_gbs": gbs, "frac_of_hbm_peak": gbs / peak,
+                         "iterations": r.iterations, "shape": [r.fine_tile, r.fine_threads, r.fine_collapsed],
+                         "solve_ms_host_loop": statistics.median(solve_ms)}
+        finally:
+            capi.mgrit_destroy(h)
+    return out
+
+
 def exact_cpoints(nx, nt, m, c, device):
     """Exact solution of Eq. 1 (alpha = 1) at the C-points t_j = j m dt for the
     Fourier-field initial condition: u0(x - t) as a product of the per-time
@@ -463,7 +512,7 @@ def main():
                     help="arithmetic of the headline solve")
     ap.add_argument("--batch", type=int, default=4096, help="solves in the uneven batch (0: skip)")
     ap.add_argument("--serve", type=int, default=400, help="requests per arrival rate (0: skip)")
-    ap.add_argument("--only", choices=["sdirk", "batch", "serve", "inflow"],
+    ap.add_argument("--only", choices=["sdirk", "batch", "serve", "inflow", "hbm"],
                     help="run just this variant and print its JSON (no headline line)")
     ap.add_argument("--host-loop", action="store_true",
                     help="with --only sdirk: drive cycles from the host (kernels visible to ncu)")
@@ -494,7 +543,8 @@ def main():
                                               capi.FLAG_HOST_LOOP if args.host_loop else 0),
                "batch": lambda: batch_variant(capi, args.batch, sp),
                "serve": lambda: serving_variant(capi, (100, 1000, 3000, 10000), args.serve),
-               "inflow": lambda: inflow_variant(capi, sp)}[args.only]
+               "inflow": lambda: inflow_variant(capi, sp),
+               "hbm": lambda: hbm_variant(capi, sp)}[args.only]
         print(json.dumps({args.only: run()}), flush=True)
         return
     u0_np = workloads.fourier_field(NX)
@@ -624,6 +674,7 @@ def main():
         extra["paper_parallel_configs"] = paper_parallel_variant(capi, sp)
         extra["paper_configs_to_discretization_error"] = disc_error_variant(capi, sp)
         extra["inflow_outflow_table5_configs"] = inflow_variant(capi, sp)
+        extra["hbm_bound_erk1_m4"] = hbm_variant(capi, sp)
         if args.batch > 0:
             extra["batch_uneven"] = batch_variant(capi, args.batch, sp)
         if args.serve > 0:

@@ -72,6 +72,9 @@ struct FcfArgs {
   float* r_f;
   Fixup fx;                // boundary rows of T (non-periodic problems)
   int trunc;               // T truncated at both ends: taps outside 0..nx-1 read zero
+  // Precision 3: u_old and c_new hold float-float pairs (hi, lo) instead of
+  // FP64 values (same 8 bytes), so level 1 runs on the FP32 pipes only.
+  int df_store;
 };
 
 // Sequential march u_n = T u_{n-1} + g_n, n = 1..P-1, on one thread-block
@@ -88,6 +91,7 @@ struct MarchArgs {
   // T truncated at both ends (Toeplitz, inflow/outflow Psi): a tap whose
   // column (in the frame that does not move) leaves 0..nx-1 drops out.
   int trunc;
+  int c_add_df;            // c_add holds float-float pairs
 };
 
 // Correction and F-relaxation (ideal interpolation) of one level:
@@ -230,7 +234,9 @@ cudaError_t launch_norm(const double* partial, int n, double* out, cudaStream_t 
 cudaError_t launch_residual_value(const double* c_new, double* r, double* partial, int nx, int N, cudaStream_t s);
 cudaError_t launch_residual_value_batched(const BatchSolve* S, const BatchItem* items, int nitems, cudaStream_t s);
 cudaError_t launch_add(double* c, const double* e, long long count, cudaStream_t s);
-cudaError_t launch_add_f(double* c, const float* e, long long count, cudaStream_t s);
+cudaError_t launch_add_f(double* c, const float* e, long long count, cudaStream_t s, int df_store = 0);
+// FP64 <-> float-float pairs, count values (to_df: in FP64, out pairs).
+cudaError_t launch_convert_df(const double* in, double* out, long long count, int to_df, cudaStream_t s);
 cudaError_t launch_propagate(const double* in, double* out, int count, int nx, int k,
                              const DevTaps& t, double* partial, int threads, cudaStream_t s,
                              const Fixup* fx = nullptr, int trunc = 0);

@@ -642,6 +642,7 @@ void autotune_fine(mgrit_handle* h) {
   f.partial = h->partial;
   f.nx = nx;
   f.fx = h->fx_phi;
+  f.df_store = h->dfc;
   // a sample of the handle's intervals, large enough (12 per SM) that the last
   // wave's share is small for every CTA size
   f.N = std::min(h->Nl[1], 12 * 152);
@@ -765,7 +766,7 @@ size_t handle_bytes(const mgrit_problem* prob, const mgrit_opts* opts) {
   // arrays take half as many in the mixed modes (FP32)
   const bool f32 = opts->precision != MGRIT_PREC_FP64;
   auto arr = [&](size_t count) { return f32 ? (count + 1) / 2 : count; };
-  size_t d = 2 * (N[1] + 1) * nx + arr((N[1] + 1) * nx) + (N[1] + 1) + 2 * nx + 8;
+  size_t d = 2 * (N[1] + 1) * nx + arr((N[1] + 1) * nx) + (N[1] + 1) + 3 * nx + 8;
   for (size_t l = 2; l <= L; ++l) {
     const size_t P = N[l - 1] + 1;
     if (l < L || L > 2) d += arr(P * nx);
@@ -894,7 +895,9 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
     if (s2 == MGRIT_OK) cudaMemsetAsync(h->r[1], 0, count * sizeof(double), h->stream);
     return s2;
   };
+  h->dfc = fine_prec(h) == 3;  // MIXED_DF, ERK: level-1 C-points as float-float pairs
   if ((st = A((N1 + 1) * nx, &h->c[0])) != MGRIT_OK || (st = A((N1 + 1) * nx, &h->c[1])) != MGRIT_OK ||
+      (st = A(nx, &h->u0buf)) != MGRIT_OK ||
       (st = AZ1((N1 + 1) * nx)) != MGRIT_OK || (st = A(N1 + 1, &h->partial)) != MGRIT_OK ||
       (st = A(2 * (size_t)nx + 8, &h->scratch)) != MGRIT_OK) {
     release(h);
@@ -1198,6 +1201,7 @@ mgrit_status coarse_cycle(mgrit_handle* h, double* c_new) {
     a.g = h->r[1];
     a.g_f = h->rf[1];
     a.c_add = c_new;
+    a.c_add_df = h->dfc;
     a.nx = nx;
     a.trunc = h->inflow;
     a.P = h->Nl[1] + 1;
@@ -1207,7 +1211,8 @@ mgrit_status coarse_cycle(mgrit_handle* h, double* c_new) {
   st = h->opts.cycle == MGRIT_CYCLE_F ? fcycle_level(h, 2) : vcycle_level(h, 2, true);
   if (st != MGRIT_OK) return st;
   return klaunch(h, MGRIT_K_ADD, "add", [&] {
-    if (h->f32c) return launch_ok(launch_add_f(c_new + nx, h->uf[2] + nx, (long long)h->Nl[1] * nx, h->stream), "add");
+    if (h->f32c)
+      return launch_ok(launch_add_f(c_new + nx, h->uf[2] + nx, (long long)h->Nl[1] * nx, h->stream, h->dfc), "add");
     return launch_ok(launch_add(c_new + nx, h->u[2] + nx, (long long)h->Nl[1] * nx, h->stream), "add");
   });
 }
@@ -1217,6 +1222,14 @@ mgrit_status write_output(mgrit_handle* h, const double* cres, double* out) {
   const size_t N1 = h->Nl[1];
   const size_t slab = (size_t)nx * sizeof(double);
   mgrit_status st;
+  if (h->dfc) {  // float-float C-points: to FP64 in the other (now free) C-point array
+    double* tmp = cres == h->c[0] ? h->c[1] : h->c[0];
+    if ((st = klaunch(h, MGRIT_K_OTHER, "convert", [&] {
+           return launch_ok(launch_convert_df(cres, tmp, (long long)(N1 + 1) * nx, 0, h->stream), "convert");
+         })) != MGRIT_OK)
+      return st;
+    cres = tmp;
+  }
   if (h->opts.output == MGRIT_OUT_FINAL) {
     CUDA_TRY(cudaMemcpyAsync(out, cres + N1 * nx, slab, kind_from_dev(out), h->stream));
   } else if (h->opts.output == MGRIT_OUT_CPOINTS) {
@@ -1310,6 +1323,7 @@ static mgrit_status graph_cycle(mgrit_handle* h, int cur, cudaGraphConditionalHa
   f.N = h->Nl[1];
   f.relax_f = h->opts.relax == MGRIT_RELAX_F;
   f.value_residual = fine_prec(h) == 0 && !f.relax_f;
+  f.df_store = h->dfc;
   mgrit_status st;
   if ((st = launch_ok(launch_fine_fcf(h, f, fine_prec(h)), "fcf")) != MGRIT_OK) return st;
   if (f.value_residual &&
@@ -1368,15 +1382,22 @@ static mgrit_status build_solve_graph(mgrit_handle* h) {
 // Whole solve: prologue on the stream, one graph launch, one read-back.
 // Initial iterate on the device: C-points from c_init (rows 0..N1) or zero
 // (row 0 = u0).
-static mgrit_status load_iterate(mgrit_handle* h, const double* u0, const double* c_init) {
+// The initial iterate into c[0] (C-point 0 also into c[1]) and u0 in FP64
+// into u0buf; float-float pairs when the handle stores its C-points so.
+mgrit_status load_iterate(mgrit_handle* h, const double* u0, const double* c_init) {
   const int nx = h->nx;
   const size_t N1 = h->Nl[1];
   const size_t slab = (size_t)nx * sizeof(double);
+  double* dst = h->dfc ? h->c[1] : h->c[0];  // float-float: stage the FP64 values in c[1]
   if (c_init) {
-    CUDA_TRY(cudaMemcpyAsync(h->c[0], c_init, (N1 + 1) * slab, kind_to_dev(c_init), h->stream));
+    CUDA_TRY(cudaMemcpyAsync(dst, c_init, (N1 + 1) * slab, kind_to_dev(c_init), h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->u0buf, dst, slab, cudaMemcpyDeviceToDevice, h->stream));
+    if (h->dfc) CUDA_TRY(launch_convert_df(dst, h->c[0], (long long)(N1 + 1) * nx, 1, h->stream));
   } else {
-    CUDA_TRY(cudaMemcpyAsync(h->c[0], u0, slab, kind_to_dev(u0), h->stream));
-    CUDA_TRY(cudaMemsetAsync(h->c[0] + nx, 0, N1 * slab, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->u0buf, u0, slab, kind_to_dev(u0), h->stream));
+    if (h->dfc) CUDA_TRY(launch_convert_df(h->u0buf, h->c[0], nx, 1, h->stream));
+    else CUDA_TRY(cudaMemcpyAsync(h->c[0], h->u0buf, slab, cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_TRY(cudaMemsetAsync(h->c[0] + nx, 0, N1 * slab, h->stream));  // zero bits: 0.0 in both forms
   }
   CUDA_TRY(cudaMemcpyAsync(h->c[1], h->c[0], slab, cudaMemcpyDeviceToDevice, h->stream));
   return MGRIT_OK;
@@ -1395,9 +1416,9 @@ static mgrit_status solve_graph(mgrit_handle* h, const double* u0, const double*
   CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(CheckState), cudaMemcpyHostToDevice, h->stream));
   // otherwise ||Phi u0||^2 straight into the state (zero initial iterate: r^(0) = Phi u0)
   if (!(r0_norm > 0.0) &&
-      (st = launch_ok(h->sdirk ? launch_propagate_sdirk(h->c[0], h->scratch, 1, nx, 1, h->splan, &h->dstate->r0sq,
+      (st = launch_ok(h->sdirk ? launch_propagate_sdirk(h->u0buf, h->scratch, 1, nx, 1, h->splan, &h->dstate->r0sq,
                                                         h->stream)
-                               : launch_propagate(h->c[0], h->scratch, 1, nx, 1, h->dphi, &h->dstate->r0sq,
+                               : launch_propagate(h->u0buf, h->scratch, 1, nx, 1, h->dphi, &h->dstate->r0sq,
                                                   h->fcf_threads, h->stream, &h->fx_phi),
                       "propagate")) != MGRIT_OK)
     return st;
@@ -1473,7 +1494,7 @@ static mgrit_status solve_impl(mgrit_handle* h, const double* u0, const double* 
   mgrit_status st = load_iterate(h, u0, c_init);
   if (st != MGRIT_OK) return st;
   double r0 = r0_norm;
-  if (!(r0_norm > 0.0) && (st = initial_residual(h, h->c[0], &r0)) != MGRIT_OK) return st;
+  if (!(r0_norm > 0.0) && (st = initial_residual(h, h->u0buf, &r0)) != MGRIT_OK) return st;
   R.r0_norm = r0;
   const int prec = fine_prec(h);
   mgrit_status final_status = MGRIT_OK;
@@ -1493,6 +1514,7 @@ static mgrit_status solve_impl(mgrit_handle* h, const double* u0, const double* 
     f.zero_old = 0;
     f.relax_f = h->opts.relax == MGRIT_RELAX_F;
     f.value_residual = prec == 0 && !f.relax_f;
+    f.df_store = h->dfc;
     if ((st = klaunch(h, MGRIT_K_FCF, "fcf", [&] {
            return launch_ok(launch_fine_fcf(h, f, prec), "fcf");
          })) != MGRIT_OK)

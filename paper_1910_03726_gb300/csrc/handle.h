@@ -48,6 +48,10 @@ struct mgrit_handle {
   // (rf, uf, cnewf; the FP64 pointers of those arrays stay null).
   bool f32c = false;
   std::vector<float*> rf, uf, cnewf;
+  // MIXED_DF on an ERK fine level: c[0], c[1] hold float-float pairs
+  // (hi, lo) instead of FP64 values, converted only at load and output
+  bool dfc = false;
+  double* u0buf = nullptr;        // u0 in FP64 (the initial residual reads it)
   double* partial = nullptr;
   double* scratch = nullptr;      // 2*nx + 1 doubles
   double* norm_host = nullptr;    // pinned
@@ -93,6 +97,9 @@ void collect_stats(mgrit_handle* h, mgrit_result* R);
 mgrit_status run_march(mgrit_handle* h, const mg::MarchArgs& a, const mg::DevTaps& t);
 mgrit_status initial_residual(mgrit_handle* h, const double* u0dev, double* r0);
 mgrit_status initial_residual_async(mgrit_handle* h, const double* u0dev);
+// Initial iterate into the handle's C-point arrays (u0 with a zero iterate,
+// or all C-points c_init); u0 in FP64 into u0buf.
+mgrit_status load_iterate(mgrit_handle* h, const double* u0, const double* c_init);
 mgrit_status coarse_cycle(mgrit_handle* h, double* c_new);
 // Build a handle; ops != nullptr supplies an already fitted hierarchy.
 mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cudaStream_t stream,

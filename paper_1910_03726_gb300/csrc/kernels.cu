@@ -96,6 +96,21 @@ __device__ __forceinline__ df64 df_from(double v) {
   return {h, (float)(v - (double)h)};
 }
 __device__ __forceinline__ double df_to(df64 a) { return (double)a.hi + (double)a.lo; }
+// a - b rounded to FP32 (TwoDiff of the high words, exact; low words added
+// to the rounding error), on the FP32 pipes.
+__device__ __forceinline__ float df_sub_f(df64 a, df64 b) {
+  const float s = a.hi - b.hi;
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) - (b.hi + bb);
+  return s + (err + (a.lo - b.lo));
+}
+// a + e (e FP32), normalised: TwoSum of the high words, low words added.
+__device__ __forceinline__ df64 df_add_f(df64 a, float e) {
+  const float s = a.hi + e;
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) + (e - bb);
+  return df_norm({s, err + a.lo});
+}
 
 // Generic arithmetic over double, float and df64 slabs.
 template <typename T>
@@ -326,6 +341,33 @@ __device__ __forceinline__ void slab_step_fx(const DevTaps& t, const Fixup& fx, 
   }
 }
 
+// Element loop i = tid, tid + blockDim.x, ... < nx in groups of K per
+// thread: the K global loads of a group (ld, L2-cached) are issued before any
+// value is used, so K requests per thread are in flight; a plain loop that
+// stores each value to shared memory waits for every load in turn.
+template <int K, typename V, typename L, typename F>
+__device__ __forceinline__ void batched_loads(int nx, L&& ld, F&& use) {
+  const int bs = blockDim.x;
+  for (int i0 = threadIdx.x; i0 < nx; i0 += K * bs) {
+    V v[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+      const int i = i0 + u * bs;
+      if (i < nx) v[u] = ld(i);
+    }
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+      const int i = i0 + u * bs;
+      if (i < nx) use(i, v[u]);
+    }
+  }
+}
+constexpr int kLoadBatch = 8;
+__device__ __forceinline__ df64 ldcg_df(const df64* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return {v.x, v.y};
+}
+
 // Sum over the block in a fixed order (deterministic); result valid in thread 0.
 __device__ double block_sum(double v) {
   __shared__ double ws[32];
@@ -357,11 +399,12 @@ __device__ __forceinline__ void fcf_body_fp32(const FcfArgs& a, const int j, con
   float* b1 = b0 + plen;
   const float* start = a.u_old_f + (long long)(j - 1) * a.cstride;
   int nz = 0;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    const float v = a.zero_old ? 0.0f : start[i];
-    b0[pidx(i)] = v;
-    nz |= v != 0.0f;
-  }
+  batched_loads<kLoadBatch, float>(
+      nx, [&](int i) { return a.zero_old ? 0.0f : __ldcg(start + i); },
+      [&](int i, float v) {
+        b0[pidx(i)] = v;
+        nz |= v != 0.0f;
+      });
   const bool run1 = __syncthreads_or(nz) || a.g_f;  // zero slab, no rhs: Phi^m 0 = 0
   for (int s = 1; s <= m && run1; ++s) {
     const float* g = a.g_f ? a.g_f + ((long long)(j - 1) * m + s) * nx : nullptr;
@@ -372,13 +415,15 @@ __device__ __forceinline__ void fcf_body_fp32(const FcfArgs& a, const int j, con
   const float* oldj = a.u_old_f + (long long)j * a.cstride;
   float* cn = a.c_new_f + (long long)j * nx;
   nz = 0;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    const float v = b0[pidx(i)];
-    cn[i] = v;
-    const float rho = v - (a.zero_old ? 0.0f : oldj[i]);
-    b1[pidx(i)] = rho;
-    nz |= rho != 0.0f;
-  }
+  batched_loads<kLoadBatch, float>(
+      nx, [&](int i) { return a.zero_old ? 0.0f : __ldcg(oldj + i); },
+      [&](int i, float old) {
+        const float v = b0[pidx(i)];
+        cn[i] = v;
+        const float rho = v - old;
+        b1[pidx(i)] = rho;
+        nz |= rho != 0.0f;
+      });
   const bool run2 = __syncthreads_or(nz);
   if (j >= a.N) return;
   float* x0 = b1;
@@ -435,6 +480,26 @@ __device__ __forceinline__ void store_f_relaxation(const FcfArgs& a, int j, cons
   const double* oldj = a.u_old + (long long)j * a.cstride;
   double* cn = a.c_new + (long long)j * nx;
   double ss = 0.0;
+  if constexpr (std::is_same<V, df64>::value) {
+    if (a.df_store) {  // C-points as float-float pairs: the FP32 pipes only, the norm from FP32 values
+      const df64* od = reinterpret_cast<const df64*>(a.u_old) + (long long)j * a.cstride;
+      df64* cd = reinterpret_cast<df64*>(a.c_new) + (long long)j * nx;
+      float sf = 0.0f;
+      for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const df64 old = a.zero_old ? vzero<df64>() : od[i];
+        const float rho = df_sub_f(b0[pidx(i)], old);
+        cd[i] = old;
+        if (a.r_f) a.r_f[(long long)j * nx + i] = rho;
+        else a.r[(long long)j * nx + i] = (double)rho;
+        sf = fmaf(rho, rho, sf);
+      }
+      if (a.partial) {
+        ss = block_sum((double)sf);
+        if (threadIdx.x == 0) a.partial[j] = ss;
+      }
+      return;
+    }
+  }
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     const double old = a.zero_old ? 0.0 : oldj[i];
     double v;
@@ -460,11 +525,22 @@ __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const
   df64* b0 = reinterpret_cast<df64*>(smraw);
   df64* b1 = b0 + plen;
   const double* start = a.u_old + (long long)(j - 1) * a.cstride;
+  const df64* startd = reinterpret_cast<const df64*>(a.u_old) + (long long)(j - 1) * a.cstride;
   int nz = 0;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    const double v = a.zero_old ? 0.0 : start[i];
-    b0[pidx(i)] = df_from(v);
-    nz |= v != 0.0;
+  if (a.df_store) {  // float-float C-points: no conversion on the FP64 pipe
+    batched_loads<kLoadBatch, df64>(
+        nx, [&](int i) { return a.zero_old ? vzero<df64>() : ldcg_df(startd + i); },
+        [&](int i, df64 v) {
+          b0[pidx(i)] = v;
+          nz |= vnonzero<df64>(v);
+        });
+  } else {
+    batched_loads<kLoadBatch, double>(
+        nx, [&](int i) { return a.zero_old ? 0.0 : __ldcg(start + i); },
+        [&](int i, double v) {
+          b0[pidx(i)] = df_from(v);
+          nz |= v != 0.0;
+        });
   }
   const bool run1 = __syncthreads_or(nz) || a.g;  // zero slab, no rhs: Phi^m 0 = 0
   for (int s = 1; s <= m && run1; ++s) {
@@ -482,12 +558,28 @@ __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const
   float* f0 = reinterpret_cast<float*>(b1);
   float* f1 = f0 + plen;
   nz = 0;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    const double v = df_to(b0[pidx(i)]);
-    cn[i] = v;
-    const float rho = (float)(v - (a.zero_old ? 0.0 : oldj[i]));
-    f0[pidx(i)] = rho;
-    nz |= rho != 0.0f;
+  if (a.df_store) {
+    const df64* oldd = reinterpret_cast<const df64*>(a.u_old) + (long long)j * a.cstride;
+    df64* cnd = reinterpret_cast<df64*>(a.c_new) + (long long)j * nx;
+    batched_loads<kLoadBatch, df64>(
+        nx, [&](int i) { return a.zero_old ? vzero<df64>() : ldcg_df(oldd + i); },
+        [&](int i, df64 old) {
+          const df64 v = b0[pidx(i)];
+          cnd[i] = v;
+          const float rho = df_sub_f(v, old);
+          f0[pidx(i)] = rho;
+          nz |= rho != 0.0f;
+        });
+  } else {
+    batched_loads<kLoadBatch, double>(
+        nx, [&](int i) { return a.zero_old ? 0.0 : __ldcg(oldj + i); },
+        [&](int i, double old) {
+          const double v = df_to(b0[pidx(i)]);
+          cn[i] = v;
+          const float rho = (float)(v - old);
+          f0[pidx(i)] = rho;
+          nz |= rho != 0.0f;
+        });
   }
   const bool run2 = __syncthreads_or(nz);
   if (j >= a.N) return;
@@ -514,11 +606,12 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
   double* b1 = b0 + plen;
   const double* start = a.u_old + (long long)(j - 1) * a.cstride;
   int nz = 0;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    const double v = a.zero_old ? 0.0 : start[i];
-    b0[pidx(i)] = v;
-    nz |= v != 0.0;
-  }
+  batched_loads<kLoadBatch, double>(
+      nx, [&](int i) { return a.zero_old ? 0.0 : __ldcg(start + i); },
+      [&](int i, double v) {
+        b0[pidx(i)] = v;
+        nz |= v != 0.0;
+      });
   // Phi^m of an identically zero slab is zero (no right-hand side): the
   // steps are skipped, which leaves the result exactly as computed
   const bool run1 = __syncthreads_or(nz) || a.g;
@@ -538,13 +631,15 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
   }
   if (PREC == 0) {
     nz = 0;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const double v = b0[pidx(i)];
-      cn[i] = v;
-      const double rho = a.value_residual ? v : v - (a.zero_old ? 0.0 : oldj[i]);
-      b1[pidx(i)] = rho;
-      nz |= rho != 0.0;
-    }
+    batched_loads<kLoadBatch, double>(
+        nx, [&](int i) { return (a.value_residual || a.zero_old) ? 0.0 : __ldcg(oldj + i); },
+        [&](int i, double old) {
+          const double v = b0[pidx(i)];
+          cn[i] = v;
+          const double rho = a.value_residual ? v : v - old;
+          b1[pidx(i)] = rho;
+          nz |= rho != 0.0;
+        });
     const bool run2 = __syncthreads_or(nz);
     if (!more) return;
     double* x0 = b1;
@@ -565,13 +660,15 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
     float* f0 = reinterpret_cast<float*>(b1);
     float* f1 = f0 + plen;
     nz = 0;
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const double v = b0[pidx(i)];
-      cn[i] = v;
-      const float rho = (float)(v - (a.zero_old ? 0.0 : oldj[i]));
-      f0[pidx(i)] = rho;
-      nz |= rho != 0.0f;
-    }
+    batched_loads<kLoadBatch, double>(
+        nx, [&](int i) { return a.zero_old ? 0.0 : __ldcg(oldj + i); },
+        [&](int i, double old) {
+          const double v = b0[pidx(i)];
+          cn[i] = v;
+          const float rho = (float)(v - old);
+          f0[pidx(i)] = rho;
+          nz |= rho != 0.0f;
+        });
     const bool run2 = __syncthreads_or(nz);
     if (!more) return;
     for (int s = 1; s <= m && run2; ++s) {
@@ -651,8 +748,9 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
   // right-hand side stays FP32 until it is used, so the load is not waited on)
   double gq[PPT], cq[PPT];
   float gqf[PPT];
+  df64 cqd[PPT];
 #pragma unroll
-  for (int p = 0; p < PPT; ++p) { gq[p] = 0.0; cq[p] = 0.0; gqf[p] = 0.0f; }
+  for (int p = 0; p < PPT; ++p) { gq[p] = 0.0; cq[p] = 0.0; gqf[p] = 0.0f; cqd[p] = {0.0f, 0.0f}; }
   auto prefetch = [&](int n, int Sn) {
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
@@ -661,7 +759,12 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
         const long long o = (long long)n * nx + wrapi(base + i + Sn, nx);
         if (a.g_f) gqf[p] = __ldcg(a.g_f + o);
         else if (a.g) gq[p] = __ldcg(a.g + o);
-        if (a.c_add) cq[p] = __ldcg(a.c_add + o);
+        if (a.c_add && a.c_add_df) {
+          const float2 v = __ldcg(reinterpret_cast<const float2*>(a.c_add) + o);
+          cqd[p] = {v.x, v.y};
+        } else if (a.c_add) {
+          cq[p] = __ldcg(a.c_add + o);
+        }
       }
     }
   };
@@ -671,8 +774,9 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
     double* cur = (n & 1) ? B0 : B1;
     double* nxt = (n & 1) ? B1 : B0;
     double gc[PPT], cc[PPT];
+    df64 ccd[PPT];
 #pragma unroll
-    for (int p = 0; p < PPT; ++p) { gc[p] = a.g_f ? (double)gqf[p] : gq[p]; cc[p] = cq[p]; }
+    for (int p = 0; p < PPT; ++p) { gc[p] = a.g_f ? (double)gqf[p] : gq[p]; cc[p] = cq[p]; ccd[p] = cqd[p]; }
     const int Snext = modnx((long long)S - sigma, nx);
     if (n + 1 < a.P) prefetch(n + 1, Snext);
     const bool store = (a.u_out || a.u_out_f) && (n % a.store_every) == 0;
@@ -690,7 +794,11 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
           for (int k = 0; k < t.n; ++k) acc = fma(t.c64[k], c[t.off[k]], acc);
         }
         nxt[L + i] = acc;
-        if (a.c_add) a.c_add[(long long)n * nx + gi] = cc[p] + acc;
+        if (a.c_add && a.c_add_df) {  // float-float C-points: c + e in FP64, split back
+          reinterpret_cast<df64*>(a.c_add)[(long long)n * nx + gi] = df_from(df_to(ccd[p]) + acc);
+        } else if (a.c_add) {
+          a.c_add[(long long)n * nx + gi] = cc[p] + acc;
+        }
         if (store) {
           const long long o = (long long)(n / a.store_every) * nx + gi;
           if (a.u_out_f) a.u_out_f[o] = (float)acc;
@@ -743,6 +851,7 @@ __global__ void __launch_bounds__(256) march_batched_kernel(const BatchSolve* __
   a.u_out = nullptr;
   a.store_every = 1;
   a.c_add = s->fcf.c_new;
+  a.c_add_df = s->fcf.df_store;
   a.nx = s->fcf.nx;
   a.P = s->fcf.N + 1;
   march_body<PPT>(a, st, smraw, cl);
@@ -849,6 +958,23 @@ __global__ void add_f_kernel(double* __restrict__ c, const float* __restrict__ e
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x)
     c[i] += (double)e[i];
+}
+
+// Float-float C-points: c += e on the FP32 pipes; conversions to and from FP64.
+__global__ void add_df_f_kernel(df64* __restrict__ c, const float* __restrict__ e, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    c[i] = df_add_f(c[i], e[i]);
+}
+__global__ void f64_to_df_kernel(const double* __restrict__ in, df64* __restrict__ out, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = df_from(in[i]);
+}
+__global__ void df_to_f64_kernel(const df64* __restrict__ in, double* __restrict__ out, long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = df_to(in[i]);
 }
 
 template <int R, bool TR = false>
@@ -1189,11 +1315,21 @@ cudaError_t launch_add(double* c, const double* e, long long count, cudaStream_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_add_f(double* c, const float* e, long long count, cudaStream_t s) {
+cudaError_t launch_add_f(double* c, const float* e, long long count, cudaStream_t s, int df_store) {
   if (count <= 0) return cudaSuccess;
   long long blocks = (count + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  add_f_kernel<<<(int)blocks, 256, 0, s>>>(c, e, count);
+  if (df_store) add_df_f_kernel<<<(int)blocks, 256, 0, s>>>(reinterpret_cast<df64*>(c), e, count);
+  else add_f_kernel<<<(int)blocks, 256, 0, s>>>(c, e, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_df(const double* in, double* out, long long count, int to_df, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  long long blocks = (count + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (to_df) f64_to_df_kernel<<<(int)blocks, 256, 0, s>>>(in, reinterpret_cast<df64*>(out), count);
+  else df_to_f64_kernel<<<(int)blocks, 256, 0, s>>>(reinterpret_cast<const df64*>(in), out, count);
   return cudaGetLastError();
 }
 

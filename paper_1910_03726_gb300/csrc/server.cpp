@@ -177,16 +177,13 @@ static std::vector<Request*> admit(mgrit_server* S, std::unique_lock<std::mutex>
     std::string msg = st == MGRIT_OK ? "" : mgrit_last_error();
     if (st == MGRIT_OK) {
       mgrit_handle* h = r->h;
-      const size_t slab = (size_t)h->nx * sizeof(double);
-      cudaMemcpyAsync(h->c[0], r->u0.data(), slab, cudaMemcpyHostToDevice, S->stream);
-      cudaMemcpyAsync(h->c[1], h->c[0], slab, cudaMemcpyDeviceToDevice, S->stream);
-      cudaMemsetAsync(h->c[0] + h->nx, 0, (size_t)h->Nl[1] * slab, S->stream);
+      st = load_iterate(h, r->u0.data(), nullptr);
       reset_stats(h);
       std::memset(&r->res, 0, sizeof(r->res));
       r->res.n_levels = h->L;
       r->res.setup_s = h->setup_s;
       r->res.op_complexity = h->op_complexity;
-      st = initial_residual_async(h, h->c[0]);  // read after the admission batch's one sync
+      if (st == MGRIT_OK) st = initial_residual_async(h, h->u0buf);  // read after the admission batch's one sync
       if (st != MGRIT_OK) msg = mgrit_last_error();
     }
     lk.lock();
@@ -242,6 +239,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     b.fcf.relax_f = h->opts.relax == MGRIT_RELAX_F;
     b.fcf.value_residual = fine_prec(h) == 0 && !b.fcf.relax_f;
     b.fcf.fx = h->fine_collapse ? h->fx_phim : h->fx_phi;  // boundary rows (inflow/outflow problems)
+    b.fcf.df_store = h->dfc;
     b.prec = fine_prec(h);
     b.taps = 2 * k;
     b.psi = 2 * k + 1;
