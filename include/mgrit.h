@@ -264,6 +264,17 @@ mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* out, mgrit_r
 mgrit_status mgrit_solve_from(mgrit_handle* h, const double* c_init, double r0_norm, double* out,
                               mgrit_result* res);
 
+/* Level-1 FCF-relaxation sweeps without coarse-grid correction (Section
+ * 2.2) on the C-points of the handle's last mgrit_solve / mgrit_solve_from
+ * (a relaxation-only smoother).  Each sweep is one launch of the fine FCF
+ * kernel (plus the residual kernel in FP64), queued back to back with no
+ * host synchronisation between sweeps.  rel_residual (may be NULL) receives
+ * the residual after the last sweep relative to that solve's initial
+ * residual norm.  The relaxed C-points become the handle's current iterate:
+ * a later mgrit_relax continues from them; mgrit_solve starts afresh.
+ * MGRIT_ERR_INVALID before the first solve or for sweeps < 0. */
+mgrit_status mgrit_relax(mgrit_handle* h, int32_t sweeps, double* rel_residual);
+
 /* Plain sequential time stepping u^{n+1} = Phi u^n on the GPU (FP64), the
  * baseline of Section 5; out as for mgrit_solve.  seconds may be NULL. */
 mgrit_status mgrit_sequential(mgrit_handle* h, const double* u0, double* out, double* seconds);

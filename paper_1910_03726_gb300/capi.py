@@ -39,7 +39,8 @@ KERNEL_KINDS = ["fcf", "fcf_coarse", "march", "correct", "norm", "add", "propaga
 K_KINDS = len(KERNEL_KINDS)
 
 EXPORTED = ["mgrit_opts_default", "mgrit_set_allocator", "mgrit_phi_taps", "mgrit_phi_boundary", "mgrit_psi_plan",
-            "mgrit_setup", "mgrit_solve", "mgrit_solve_from", "mgrit_sequential", "mgrit_propagate", "mgrit_psi_info",
+            "mgrit_setup", "mgrit_solve", "mgrit_solve_from", "mgrit_relax", "mgrit_sequential", "mgrit_propagate",
+            "mgrit_psi_info",
             "mgrit_device_bytes", "mgrit_destroy", "mgrit_server_create", "mgrit_submit",
             "mgrit_poll", "mgrit_server_stats", "mgrit_server_destroy", "mgrit_fcf_residual_static", "mgrit_last_error",
             "mgrit_abi_version"]
@@ -121,6 +122,7 @@ _sig("mgrit_psi_plan", _i32, _P(MgritProblem), _P(MgritOpts), _i32, _P(_i32), _P
 _sig("mgrit_setup", _i32, _P(MgritProblem), _P(MgritOpts), _vp, _P(_vp))
 _sig("mgrit_solve", _i32, _vp, _vp, _vp, _P(MgritResult))
 _sig("mgrit_solve_from", _i32, _vp, _vp, _f64, _vp, _P(MgritResult))
+_sig("mgrit_relax", _i32, _vp, _i32, _P(_f64))
 _sig("mgrit_sequential", _i32, _vp, _vp, _vp, _P(_f64))
 _sig("mgrit_propagate", _i32, _vp, _i32, _i32, _i32, _vp, _vp)
 _sig("mgrit_psi_info", _i32, _vp, _i32, _i32, _P(_i32), _P(_i32), _P(_f64))
@@ -271,6 +273,13 @@ def mgrit_solve_from(h, c_init, r0_norm=0.0, out=None, allow_not_converged=False
     allow = (MGRIT_OK, -4) if allow_not_converged else (MGRIT_OK,)
     st = _check(_lib.mgrit_solve_from(h, _ptr(c_init), C.c_double(r0_norm), _ptr(out), C.byref(r)), allow)
     return r, st
+
+
+def mgrit_relax(h, sweeps):
+    """Level-1 FCF sweeps on the last solve's C-points; returns the relative residual."""
+    rel = C.c_double()
+    _check(_lib.mgrit_relax(h, int(sweeps), C.byref(rel)))
+    return rel.value
 
 
 def mgrit_sequential(h, u0, out=None):

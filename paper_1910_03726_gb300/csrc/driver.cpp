@@ -606,7 +606,7 @@ void autotune_fine(mgrit_handle* h) {
     if (collapse && !h->have_phim) return false;
     const DevTaps& t = collapse ? h->dphim : h->dphi;
     const bool dense = t.span > 0 && nx >= 64;
-    if (tile == kFixedTile) return !collapse && dense && fixed_span(t.span);
+    if (tile == kFixedTile) return dense && fixed_span(t.span);  // Phi, or Phi^m whose span is compiled
     if (tile == kChunkTile) return dense && t.span >= 8;
     if (tile == 8 || tile == 4) return dense;
     return tile == 0;
@@ -659,8 +659,9 @@ void autotune_fine(mgrit_handle* h) {
   // stencils without a dense form)
   struct Cand { int collapse, tile, threads; };
   std::vector<Cand> cands;
-  for (Cand c : {Cand{1, kChunkTile, 256}, Cand{1, kChunkTile, 512}, Cand{1, 8, 256}, Cand{0, kFixedTile, 256},
-                 Cand{0, kFixedTile, 512}, Cand{0, kChunkTile, 256}, Cand{0, 8, 256}, Cand{0, 0, 128}, Cand{0, 0, 256}})
+  for (Cand c : {Cand{1, kChunkTile, 256}, Cand{1, kChunkTile, 512}, Cand{1, 8, 256}, Cand{1, kFixedTile, 256},
+                 Cand{1, kFixedTile, 512}, Cand{0, kFixedTile, 256}, Cand{0, kFixedTile, 512}, Cand{0, kChunkTile, 256},
+                 Cand{0, 8, 256}, Cand{0, 0, 128}, Cand{0, 0, 256}})
     if (valid(c.collapse, c.tile)) cands.push_back(c);
   bool dense_found = false;
   for (const Cand& c : cands) dense_found |= c.tile != 0;
@@ -1438,6 +1439,8 @@ static mgrit_status solve_graph(mgrit_handle* h, const double* u0, const double*
   h->kcount[MGRIT_K_FCF] = S.it + 1;
   h->kcount[MGRIT_K_NORM] = (fine_prec(h) == 0 && h->opts.relax == MGRIT_RELAX_FCF ? 2 : 1) * (S.it + 1);
   h->kcount[MGRIT_K_OTHER] = S.it + 1;
+  h->last = 1 - S.result_cur;
+  h->r0_last = R->r0_norm;
   if (out && (st = write_output(h, h->c[1 - S.result_cur], out)) != MGRIT_OK) return st;
   const int other_before = h->kcount[MGRIT_K_OTHER];
   (void)other_before;
@@ -1551,6 +1554,8 @@ static mgrit_status solve_impl(mgrit_handle* h, const double* u0, const double* 
   }
   R.iterations = it;
   // result: C-points after the final FCF-relaxation live in c[1-cur]
+  h->last = 1 - cur;
+  h->r0_last = r0;
   if (out && (st = write_output(h, h->c[1 - cur], out)) != MGRIT_OK) return st;
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   R.solve_s = now_s() - t0;
@@ -1572,6 +1577,48 @@ extern "C" mgrit_status mgrit_solve_from(mgrit_handle* h, const double* c_init, 
   if (!c_init) return fail(MGRIT_ERR_INVALID, "c_init is NULL");
   if (!std::isfinite(r0_norm)) return fail(MGRIT_ERR_INVALID, "r0_norm must be finite");
   return solve_impl(h, c_init, c_init, r0_norm, out, res);
+}
+
+extern "C" mgrit_status mgrit_relax(mgrit_handle* h, int32_t sweeps, double* rel_residual) {
+  if (!h) return fail(MGRIT_ERR_INVALID, "handle is NULL");
+  if (h->last < 0) return fail(MGRIT_ERR_INVALID, "no iterate yet: call mgrit_solve first");
+  if (sweeps < 0) return fail(MGRIT_ERR_INVALID, "sweeps must be >= 0");
+  const int nx = h->nx;
+  const int prec = fine_prec(h);
+  reset_stats(h);
+  mgrit_status st;
+  FcfArgs f = {};
+  f.cstride = nx;
+  f.r = h->r[1];
+  f.r_f = h->rf[1];
+  f.partial = h->partial;
+  f.nx = nx;
+  f.m = h->m;
+  f.N = h->Nl[1];
+  f.relax_f = h->opts.relax == MGRIT_RELAX_F;
+  f.value_residual = prec == 0 && !f.relax_f;
+  f.df_store = h->dfc;
+  for (int k = 0; k < sweeps; ++k) {  // back to back on the stream: no host synchronisation between sweeps
+    f.u_old = h->c[h->last];
+    f.c_new = h->c[1 - h->last];
+    if ((st = klaunch(h, MGRIT_K_FCF, "fcf", [&] { return launch_ok(launch_fine_fcf(h, f, prec), "fcf"); })) !=
+        MGRIT_OK)
+      return st;
+    if (f.value_residual && (st = klaunch(h, MGRIT_K_NORM, "residual", [&] {
+                               return launch_ok(launch_residual_value(f.c_new, f.r, f.partial, nx, f.N, h->stream),
+                                                "residual");
+                             })) != MGRIT_OK)
+      return st;
+    h->last = 1 - h->last;
+  }
+  if ((st = klaunch(h, MGRIT_K_NORM, "norm", [&] {
+         return launch_ok(launch_norm(h->partial, f.N + f.relax_f, h->scratch + 2 * nx, h->stream), "norm");
+       })) != MGRIT_OK)
+    return st;
+  CUDA_TRY(cudaMemcpyAsync(h->norm_host, h->scratch + 2 * nx, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (rel_residual) *rel_residual = h->r0_last > 0.0 ? std::sqrt(h->norm_host[0]) / h->r0_last : 0.0;
+  return MGRIT_OK;
 }
 
 extern "C" mgrit_status mgrit_sequential(mgrit_handle* h, const double* u0, double* out, double* seconds) {

@@ -52,6 +52,8 @@ struct mgrit_handle {
   // (hi, lo) instead of FP64 values, converted only at load and output
   bool dfc = false;
   double* u0buf = nullptr;        // u0 in FP64 (the initial residual reads it)
+  int last = -1;                  // c[last]: C-points of the last solve (-1: none yet)
+  double r0_last = 0.0;           // that solve's initial residual norm
   double* partial = nullptr;
   double* scratch = nullptr;      // 2*nx + 1 doubles
   double* norm_host = nullptr;    // pinned

@@ -143,8 +143,14 @@ template <typename T>
 __device__ __forceinline__ T gload(const double* p) { return vfrom<T>(__ldg(p)); }
 template <typename T>
 __device__ __forceinline__ T gload(const float* p) { return (T)__ldg(p); }
+template <>
+__device__ __forceinline__ df64 gload<df64>(const float* p) { return {__ldg(p), 0.0f}; }
 // A typed "no right-hand side".
 constexpr const double* kNoG = nullptr;
+// "No right-hand side" for FP32 and float-float steps: typed float, so that
+// the steps hold no double-to-float conversion (its FP64-pipe instruction
+// would be issued even when the g test is false).
+constexpr const float* kNoGf = nullptr;
 
 template <typename T>
 __device__ __forceinline__ T sparse_coef(const DevTaps& t, int k);
@@ -363,6 +369,56 @@ __device__ __forceinline__ void batched_loads(int nx, L&& ld, F&& use) {
   }
 }
 constexpr int kLoadBatch = 8;
+
+// Fast path of the slab loops when nx is a multiple of 2 * blockDim.x: each
+// thread takes pairs of neighbouring points e = 2 (tid + k blockDim.x), one
+// 16-byte (df64, FP64) or 8-byte (FP32) global access per pair, no bounds
+// tests, and up to 8 pairs' loads in flight before the first use.  Returns
+// false (nothing done) when nx does not fit; the caller then runs the
+// element loop.  Pairs never straddle a padding gap (groups of 8 start at
+// even points), so a pair sits at pidx(e), pidx(e) + 1 in shared memory.
+template <typename V2, typename L, typename F>
+__device__ __forceinline__ bool pair_loop(int nx, bool aligned, L&& ld2, F&& use2) {
+  const int bs = blockDim.x;
+  if (!aligned || nx % (2 * bs) != 0) return false;
+  const int per = nx / (2 * bs);
+  for (int k0 = 0; k0 < per; k0 += 8) {
+    V2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (k0 + u < per) v[u] = ld2(2 * (threadIdx.x + (k0 + u) * bs));
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (k0 + u < per) use2(2 * (threadIdx.x + (k0 + u) * bs), v[u]);
+  }
+  return true;
+}
+// Pair accesses need every row start they touch aligned to the pair's size
+// (caller-supplied arrays may not be).
+__device__ __forceinline__ bool pairs_aligned(const void* p, const void* q, long long stride_elems, int bytes) {
+  const unsigned long long m = 2ull * bytes - 1;
+  return ((reinterpret_cast<unsigned long long>(p) | reinterpret_cast<unsigned long long>(q)) & m) == 0 &&
+         (stride_elems & 1) == 0;
+}
+struct df2 {  // two neighbouring float-float values
+  df64 a, b;
+};
+__device__ __forceinline__ df2 ldcg_df2(const df64* p) {
+  const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+  return {{v.x, v.y}, {v.z, v.w}};
+}
+__device__ __forceinline__ void st_df2(df64* p, df64 a, df64 b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+
+// Ask L2 for `bytes` from p (one request per 128-byte line, spread over the
+// block): the slab a later phase of the CTA reads then arrives while the
+// current phase's loads and steps run.
+__device__ __forceinline__ void prefetch_l2(const void* p, long long bytes) {
+  const char* c = static_cast<const char*>(p);
+  for (long long o = (long long)threadIdx.x * 128; o < bytes; o += (long long)blockDim.x * 128)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(c + o));
+}
 __device__ __forceinline__ df64 ldcg_df(const df64* p) {
   const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
   return {v.x, v.y};
@@ -398,13 +454,23 @@ __device__ __forceinline__ void fcf_body_fp32(const FcfArgs& a, const int j, con
   float* b0 = reinterpret_cast<float*>(smraw);
   float* b1 = b0 + plen;
   const float* start = a.u_old_f + (long long)(j - 1) * a.cstride;
+  if (!a.zero_old) prefetch_l2(a.u_old_f + (long long)j * a.cstride, (long long)nx * sizeof(float));
   int nz = 0;
-  batched_loads<kLoadBatch, float>(
-      nx, [&](int i) { return a.zero_old ? 0.0f : __ldcg(start + i); },
-      [&](int i, float v) {
-        b0[pidx(i)] = v;
-        nz |= v != 0.0f;
-      });
+  const bool al = pairs_aligned(a.u_old_f, a.c_new_f, a.cstride, 4);
+  if (!pair_loop<float2>(
+          nx, al, [&](int e) { return a.zero_old ? make_float2(0.0f, 0.0f) : __ldcg(reinterpret_cast<const float2*>(start + e)); },
+          [&](int e, float2 v) {
+            const int q = pidx(e);
+            b0[q] = v.x;
+            b0[q + 1] = v.y;
+            nz |= (v.x != 0.0f) | (v.y != 0.0f);
+          }))
+    batched_loads<kLoadBatch, float>(
+        nx, [&](int i) { return a.zero_old ? 0.0f : __ldcg(start + i); },
+        [&](int i, float v) {
+          b0[pidx(i)] = v;
+          nz |= v != 0.0f;
+        });
   const bool run1 = __syncthreads_or(nz) || a.g_f;  // zero slab, no rhs: Phi^m 0 = 0
   for (int s = 1; s <= m && run1; ++s) {
     const float* g = a.g_f ? a.g_f + ((long long)(j - 1) * m + s) * nx : nullptr;
@@ -415,21 +481,32 @@ __device__ __forceinline__ void fcf_body_fp32(const FcfArgs& a, const int j, con
   const float* oldj = a.u_old_f + (long long)j * a.cstride;
   float* cn = a.c_new_f + (long long)j * nx;
   nz = 0;
-  batched_loads<kLoadBatch, float>(
-      nx, [&](int i) { return a.zero_old ? 0.0f : __ldcg(oldj + i); },
-      [&](int i, float old) {
-        const float v = b0[pidx(i)];
-        cn[i] = v;
-        const float rho = v - old;
-        b1[pidx(i)] = rho;
-        nz |= rho != 0.0f;
-      });
+  if (!pair_loop<float2>(
+          nx, al, [&](int e) { return a.zero_old ? make_float2(0.0f, 0.0f) : __ldcg(reinterpret_cast<const float2*>(oldj + e)); },
+          [&](int e, float2 old) {
+            const int q = pidx(e);
+            const float v0 = b0[q], v1 = b0[q + 1];
+            *reinterpret_cast<float2*>(cn + e) = make_float2(v0, v1);
+            const float r0 = v0 - old.x, r1 = v1 - old.y;
+            b1[q] = r0;
+            b1[q + 1] = r1;
+            nz |= (r0 != 0.0f) | (r1 != 0.0f);
+          }))
+    batched_loads<kLoadBatch, float>(
+        nx, [&](int i) { return a.zero_old ? 0.0f : __ldcg(oldj + i); },
+        [&](int i, float old) {
+          const float v = b0[pidx(i)];
+          cn[i] = v;
+          const float rho = v - old;
+          b1[pidx(i)] = rho;
+          nz |= rho != 0.0f;
+        });
   const bool run2 = __syncthreads_or(nz);
   if (j >= a.N) return;
   float* x0 = b1;
   float* x1 = b0;
   for (int s = 1; s <= m && run2; ++s) {
-    slab_step_fx<float, R, SPAN, TR>(t, a.fx, x0, x1, kNoG, nx);
+    slab_step_fx<float, R, SPAN, TR>(t, a.fx, x0, x1, kNoGf, nx);
     __syncthreads();
     float* tmp = x0; x0 = x1; x1 = tmp;
   }
@@ -451,7 +528,16 @@ __device__ __forceinline__ void fcf_body_fp32(const FcfArgs& a, const int j, con
 __device__ __forceinline__ void store_residual_f32(const FcfArgs& a, int j, const float* x) {
   const int nx = a.nx;
   float ss = 0.0f;
-  if (a.r_f) {
+  if (a.r_f && nx % (2 * blockDim.x) == 0 && pairs_aligned(a.r_f, a.r_f, nx, 4)) {  // pairs, 8-byte stores
+    float* rr = a.r_f + (long long)(j + 1) * nx;
+    for (int e = 2 * threadIdx.x; e < nx; e += 2 * blockDim.x) {
+      const int q = pidx(e);
+      const float v0 = x[q], v1 = x[q + 1];
+      *reinterpret_cast<float2*>(rr + e) = make_float2(v0, v1);
+      ss = fmaf(v0, v0, ss);
+      ss = fmaf(v1, v1, ss);
+    }
+  } else if (a.r_f) {
     float* rr = a.r_f + (long long)(j + 1) * nx;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       const float v = x[pidx(i)];
@@ -526,14 +612,24 @@ __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const
   df64* b1 = b0 + plen;
   const double* start = a.u_old + (long long)(j - 1) * a.cstride;
   const df64* startd = reinterpret_cast<const df64*>(a.u_old) + (long long)(j - 1) * a.cstride;
+  if (!a.zero_old) prefetch_l2(a.u_old + (long long)j * a.cstride, (long long)nx * 8);
   int nz = 0;
+  const bool al = pairs_aligned(a.u_old, a.c_new, a.cstride, 8);
   if (a.df_store) {  // float-float C-points: no conversion on the FP64 pipe
-    batched_loads<kLoadBatch, df64>(
-        nx, [&](int i) { return a.zero_old ? vzero<df64>() : ldcg_df(startd + i); },
-        [&](int i, df64 v) {
-          b0[pidx(i)] = v;
-          nz |= vnonzero<df64>(v);
-        });
+    if (!pair_loop<df2>(
+            nx, al, [&](int e) { return a.zero_old ? df2{} : ldcg_df2(startd + e); },
+            [&](int e, df2 v) {
+              const int q = pidx(e);
+              b0[q] = v.a;
+              b0[q + 1] = v.b;
+              nz |= vnonzero<df64>(v.a) | vnonzero<df64>(v.b);
+            }))
+      batched_loads<kLoadBatch, df64>(
+          nx, [&](int i) { return a.zero_old ? vzero<df64>() : ldcg_df(startd + i); },
+          [&](int i, df64 v) {
+            b0[pidx(i)] = v;
+            nz |= vnonzero<df64>(v);
+          });
   } else {
     batched_loads<kLoadBatch, double>(
         nx, [&](int i) { return a.zero_old ? 0.0 : __ldcg(start + i); },
@@ -542,10 +638,10 @@ __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const
           nz |= v != 0.0;
         });
   }
-  const bool run1 = __syncthreads_or(nz) || a.g;  // zero slab, no rhs: Phi^m 0 = 0
+  // precision 3 runs only on level 1, which has no right-hand side
+  const bool run1 = __syncthreads_or(nz);  // zero slab: Phi^m 0 = 0
   for (int s = 1; s <= m && run1; ++s) {
-    const double* g = a.g ? a.g + ((long long)(j - 1) * m + s) * nx : nullptr;
-    slab_step_fx<df64, R, SPAN, TR>(t, a.fx, b0, b1, g, nx);
+    slab_step_fx<df64, R, SPAN, TR>(t, a.fx, b0, b1, kNoGf, nx);
     __syncthreads();
     df64* tmp = b0; b0 = b1; b1 = tmp;
   }
@@ -561,15 +657,26 @@ __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const
   if (a.df_store) {
     const df64* oldd = reinterpret_cast<const df64*>(a.u_old) + (long long)j * a.cstride;
     df64* cnd = reinterpret_cast<df64*>(a.c_new) + (long long)j * nx;
-    batched_loads<kLoadBatch, df64>(
-        nx, [&](int i) { return a.zero_old ? vzero<df64>() : ldcg_df(oldd + i); },
-        [&](int i, df64 old) {
-          const df64 v = b0[pidx(i)];
-          cnd[i] = v;
-          const float rho = df_sub_f(v, old);
-          f0[pidx(i)] = rho;
-          nz |= rho != 0.0f;
-        });
+    if (!pair_loop<df2>(
+            nx, al, [&](int e) { return a.zero_old ? df2{} : ldcg_df2(oldd + e); },
+            [&](int e, df2 old) {
+              const int q = pidx(e);
+              const df64 v0 = b0[q], v1 = b0[q + 1];
+              st_df2(cnd + e, v0, v1);
+              const float r0 = df_sub_f(v0, old.a), r1 = df_sub_f(v1, old.b);
+              f0[q] = r0;
+              f0[q + 1] = r1;
+              nz |= (r0 != 0.0f) | (r1 != 0.0f);
+            }))
+      batched_loads<kLoadBatch, df64>(
+          nx, [&](int i) { return a.zero_old ? vzero<df64>() : ldcg_df(oldd + i); },
+          [&](int i, df64 old) {
+            const df64 v = b0[pidx(i)];
+            cnd[i] = v;
+            const float rho = df_sub_f(v, old);
+            f0[pidx(i)] = rho;
+            nz |= rho != 0.0f;
+          });
   } else {
     batched_loads<kLoadBatch, double>(
         nx, [&](int i) { return a.zero_old ? 0.0 : __ldcg(oldj + i); },
@@ -584,7 +691,7 @@ __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const
   const bool run2 = __syncthreads_or(nz);
   if (j >= a.N) return;
   for (int s = 1; s <= m && run2; ++s) {
-    slab_step_fx<float, R, SPAN, TR>(t, a.fx, f0, f1, kNoG, nx);
+    slab_step_fx<float, R, SPAN, TR>(t, a.fx, f0, f1, kNoGf, nx);
     __syncthreads();
     float* tmp = f0; f0 = f1; f1 = tmp;
   }
@@ -605,13 +712,24 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
   double* b0 = reinterpret_cast<double*>(smraw);
   double* b1 = b0 + plen;
   const double* start = a.u_old + (long long)(j - 1) * a.cstride;
+  if (!a.zero_old && !a.value_residual)
+    prefetch_l2(a.u_old + (long long)j * a.cstride, (long long)nx * sizeof(double));
   int nz = 0;
-  batched_loads<kLoadBatch, double>(
-      nx, [&](int i) { return a.zero_old ? 0.0 : __ldcg(start + i); },
-      [&](int i, double v) {
-        b0[pidx(i)] = v;
-        nz |= v != 0.0;
-      });
+  const bool al = pairs_aligned(a.u_old, a.c_new, a.cstride, 8);
+  if (!pair_loop<double2>(
+          nx, al, [&](int e) { return a.zero_old ? make_double2(0.0, 0.0) : __ldcg(reinterpret_cast<const double2*>(start + e)); },
+          [&](int e, double2 v) {
+            const int q = pidx(e);
+            b0[q] = v.x;
+            b0[q + 1] = v.y;
+            nz |= (v.x != 0.0) | (v.y != 0.0);
+          }))
+    batched_loads<kLoadBatch, double>(
+        nx, [&](int i) { return a.zero_old ? 0.0 : __ldcg(start + i); },
+        [&](int i, double v) {
+          b0[pidx(i)] = v;
+          nz |= v != 0.0;
+        });
   // Phi^m of an identically zero slab is zero (no right-hand side): the
   // steps are skipped, which leaves the result exactly as computed
   const bool run1 = __syncthreads_or(nz) || a.g;
@@ -660,19 +778,30 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
     float* f0 = reinterpret_cast<float*>(b1);
     float* f1 = f0 + plen;
     nz = 0;
-    batched_loads<kLoadBatch, double>(
-        nx, [&](int i) { return a.zero_old ? 0.0 : __ldcg(oldj + i); },
-        [&](int i, double old) {
-          const double v = b0[pidx(i)];
-          cn[i] = v;
-          const float rho = (float)(v - old);
-          f0[pidx(i)] = rho;
-          nz |= rho != 0.0f;
-        });
+    if (!pair_loop<double2>(
+            nx, al, [&](int e) { return a.zero_old ? make_double2(0.0, 0.0) : __ldcg(reinterpret_cast<const double2*>(oldj + e)); },
+            [&](int e, double2 old) {
+              const int q = pidx(e);
+              const double v0 = b0[q], v1 = b0[q + 1];
+              *reinterpret_cast<double2*>(cn + e) = make_double2(v0, v1);
+              const float r0 = (float)(v0 - old.x), r1 = (float)(v1 - old.y);
+              f0[q] = r0;
+              f0[q + 1] = r1;
+              nz |= (r0 != 0.0f) | (r1 != 0.0f);
+            }))
+      batched_loads<kLoadBatch, double>(
+          nx, [&](int i) { return a.zero_old ? 0.0 : __ldcg(oldj + i); },
+          [&](int i, double old) {
+            const double v = b0[pidx(i)];
+            cn[i] = v;
+            const float rho = (float)(v - old);
+            f0[pidx(i)] = rho;
+            nz |= rho != 0.0f;
+          });
     const bool run2 = __syncthreads_or(nz);
     if (!more) return;
     for (int s = 1; s <= m && run2; ++s) {
-      slab_step_fx<float, R, SPAN, TR>(t, a.fx, f0, f1, kNoG, nx);
+      slab_step_fx<float, R, SPAN, TR>(t, a.fx, f0, f1, kNoGf, nx);
       __syncthreads();
       float* tmp = f0; f0 = f1; f1 = tmp;
     }

@@ -246,6 +246,66 @@ def test_every_fine_launch_shape_matches_oracle(capi, shape, monkeypatch):
     assert rel(out, U[::m]) <= TOL
 
 
+@pytest.mark.parametrize("precision,relax", [(0, "FCF"), (1, "FCF"), (2, "FCF"), (0, "F")])
+def test_relax_sweeps_match_oracle(capi, precision, relax):
+    """mgrit_relax: FCF- (or F-) relaxation sweeps without coarse correction
+    from the iterate a solve left (here: the paper's random iterate after the
+    one relaxation of a max_iter = 0 solve), against the same sweeps in the
+    oracle: the relative residual after k sweeps agrees (FP64: to 1e-12;
+    mixed modes: to their FP32 second pass).  F-relaxation leaves the
+    C-points alone, so its residual stays put."""
+    fam, p, nx, nt, m = "ERK", 3, 128, 512, 4
+    c = schemes.cfl_number(fam, p)
+    st = stepping.FineStep(fam, p, c, nx)
+    U = workloads.random_iterate(nt, nx, workloads.sin4(nx), 3)
+    r0 = float(np.linalg.norm(omg.spacetime_residual(U, np.zeros_like(U), st)))
+    opts = capi.mgrit_opts_default(m=m, levels=2, max_iter=0, precision=precision,
+                                   relax=0 if relax == "FCF" else 1)
+    h = capi.mgrit_setup(capi.problem(nx, nt, fam, p, p, c), opts)
+    try:
+        res, status = capi.mgrit_solve_from(h, np.ascontiguousarray(U[::m]), r0, allow_not_converged=True)
+        assert status == -4 and res.iterations == 0
+        got = [capi.mgrit_relax(h, 1) for _ in range(3)] + [capi.mgrit_relax(h, 4)]
+    finally:
+        capi.mgrit_destroy(h)
+    G = np.zeros_like(U)
+    want = []
+    for k in range(1 + 3 + 4):
+        omg.f_relax(U, G, st, m)
+        if relax == "FCF":
+            omg.c_relax(U, G, st, m)
+            omg.f_relax(U, G, st, m)
+        if k >= 1 and k <= 3 or k == 7:
+            want.append(float(np.linalg.norm(omg.c_residual(U, G, st, m))) / r0)
+    tol = 1e-12 if precision == 0 else 1e-6
+    np.testing.assert_allclose(got, want, rtol=tol)
+    if relax == "F":
+        assert got[0] == got[-1]
+
+
+@pytest.mark.parametrize("p,m", [(1, 4), (2, 4), (1, 16)])
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_collapsed_fixed_span_shape(capi, monkeypatch, p, m, precision):
+    """The fixed-span path applied to Phi^m when its span is one the kernels
+    are compiled for (ERK1 m = 4: 5; ERK2 m = 4 and ERK1 m = 16: 17): FP64
+    gives the oracle's iterations and C-points, the mixed modes FP64
+    sequential stepping's C-points."""
+    monkeypatch.setenv("MGRIT_FCF_SHAPE", "99,256,1")
+    fam, nx, nt, L = "ERK", 256, 4096, 3
+    c = schemes.cfl_number(fam, p)
+    u0 = workloads.fourier_field(nx)
+    it, r, U, _ = oracle_run(fam, p, c, nx, nt, m, L, "auto", u0)
+    res, out, _ = gpu_run(capi, fam, p, c, nx, nt, m, L, "auto", u0, precision=precision)
+    assert (res.fine_tile, res.fine_threads, res.fine_collapsed) == (99, 256, 1)
+    assert res.converged == 1
+    if precision == 0:
+        assert res.iterations == it
+        assert rel(out, U[::m]) <= TOL
+    else:
+        assert abs(res.iterations - it) <= 1
+        assert rel(out, U[::m]) <= 1e-9
+
+
 @pytest.mark.parametrize("case", [("ERK", 1, 64, 1024, 2, 6), ("ERK", 3, 128, 2048, 4, 4), ("ERK", 5, 128, 1024, 4, 3)])
 @pytest.mark.parametrize("flags", [0, 4])
 def test_fcycle_parity(capi, case, flags):
