@@ -603,10 +603,128 @@ __device__ __forceinline__ void store_f_relaxation(const FcfArgs& a, int j, cons
   }
 }
 
+// The R outputs of chunk i0 (a multiple of 8) of a fixed-span step into
+// registers (no right-hand side).  A window inside 0..nx-1 skips the wrap
+// test, and its padded offsets are those of the stencil shifted by i0.
+template <typename T, int R, int SPAN>
+__device__ __forceinline__ void fixed_chunk(const DevTaps& t, const T* __restrict__ src, int i0, int nx,
+                                            T (&out)[R]) {
+  const int b = i0 + t.lo;
+  T w[R + SPAN - 1];
+  if (b >= 0 && b + R + SPAN - 1 <= nx) {
+    const int p0 = i0 + (i0 >> 3);
+#pragma unroll
+    for (int q = 0; q < R + SPAN - 1; ++q) {
+      const int d = t.lo + q;
+      w[q] = src[p0 + d + (d >> 3)];
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < R + SPAN - 1; ++q) w[q] = src[pidx(wrapi(b + q, nx))];
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    T acc = vzero<T>();
+#pragma unroll
+    for (int k = 0; k < SPAN; ++k) acc = vfma1<T>(dense_coef<T>(t, k), w[r + k], acc, t.one);
+    out[r] = vfinish<T>(acc);
+  }
+}
+
+// PREC 3 with float-float C-points, one application of the collapsed Phi^m
+// per pass, fixed span, FCF, no boundary rows, nx a multiple of 8 blockDim.x
+// (fused_ok): each step's outputs go from registers straight to their uses
+// (pass 1: c_new and rho against the old C-point, loaded before the
+// arithmetic; pass 2: r and its squared norm) instead of through a second
+// slab.  The values are the unfused body's; only the order of the norm's
+// FP32 partial sums differs.
+__device__ __forceinline__ bool fused_ok(const FcfArgs& a) {
+  return a.df_store && a.m == 1 && a.fx.nl + a.fx.nr == 0 && !a.relax_f && a.r_f && !a.g &&
+         a.nx % (8 * blockDim.x) == 0 && pairs_aligned(a.u_old, a.c_new, a.cstride, 8) &&
+         pairs_aligned(a.r_f, a.r_f, 0, 8);
+}
+
+template <int SPAN>
+__device__ __forceinline__ void fcf_body_df_fused(const FcfArgs& a, const int j, const DevTaps& t,
+                                                  unsigned char* smraw) {
+  constexpr int R = 8;
+  const int nx = a.nx, plen = padded_len(nx);
+  df64* b0 = reinterpret_cast<df64*>(smraw);
+  float* f0 = reinterpret_cast<float*>(b0 + plen);
+  const df64* startd = reinterpret_cast<const df64*>(a.u_old) + (long long)(j - 1) * a.cstride;
+  const df64* oldd = reinterpret_cast<const df64*>(a.u_old) + (long long)j * a.cstride;
+  df64* cnd = reinterpret_cast<df64*>(a.c_new) + (long long)j * nx;
+  int nz = 0;
+  pair_loop<df2>(
+      nx, true, [&](int e) { return a.zero_old ? df2{} : ldcg_df2(startd + e); },
+      [&](int e, df2 v) {
+        const int q = pidx(e);
+        b0[q] = v.a;
+        b0[q + 1] = v.b;
+        nz |= vnonzero<df64>(v.a) | vnonzero<df64>(v.b);
+      });
+  const bool run1 = __syncthreads_or(nz);  // zero slab: Phi^m 0 = 0
+  int nzr = 0;
+  for (int i0 = threadIdx.x * R; i0 < nx; i0 += blockDim.x * R) {
+    df64 old[R];
+#pragma unroll
+    for (int r = 0; r < R; r += 2) {
+      const df2 o = a.zero_old ? df2{} : ldcg_df2(oldd + i0 + r);
+      old[r] = o.a;
+      old[r + 1] = o.b;
+    }
+    df64 v[R];
+    if (run1) {
+      fixed_chunk<df64, R, SPAN>(t, b0, i0, nx, v);
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = vzero<df64>();
+    }
+    const int p0 = pidx(i0);
+#pragma unroll
+    for (int r = 0; r < R; r += 2) st_df2(cnd + i0 + r, v[r], v[r + 1]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float rho = df_sub_f(v[r], old[r]);
+      f0[p0 + r] = rho;
+      nzr |= rho != 0.0f;
+    }
+  }
+  const bool run2 = __syncthreads_or(nzr);
+  if (j >= a.N) return;
+  float* rr = a.r_f + (long long)(j + 1) * nx;
+  float ss = 0.0f;
+  for (int i0 = threadIdx.x * R; i0 < nx; i0 += blockDim.x * R) {
+    float v[R];
+    if (run2) {
+      fixed_chunk<float, R, SPAN>(t, f0, i0, nx, v);
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = 0.0f;
+    }
+    *reinterpret_cast<float4*>(rr + i0) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4*>(rr + i0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) ss = fmaf(v[r], v[r], ss);
+  }
+  if (a.partial) {
+    const double tot = block_sum((double)ss);
+    if (threadIdx.x == 0) a.partial[j] = tot;
+  }
+}
+
 // PREC 3: pass 1 (C-point update and residual rho) in float-float, pass 2 in
 // FP32.  A df64 slab occupies as many bytes as an FP64 slab.
-template <int R, int SPAN = 0, bool TR = false>
+template <int R, int SPAN = 0, bool TR = false, bool FUSE = true>
 __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const DevTaps& t, unsigned char* smraw) {
+  // narrow collapsed stencils only: wider windows would raise every path's
+  // register count (and so cut the CTAs per SM)
+  if constexpr (FUSE && SPAN > 0 && SPAN <= 5 && !TR) {
+    if (fused_ok(a)) {  // uniform over the launch
+      fcf_body_df_fused<SPAN>(a, j, t, smraw);
+      return;
+    }
+  }
   const int nx = a.nx, m = a.m, plen = padded_len(nx);
   df64* b0 = reinterpret_cast<df64*>(smraw);
   df64* b1 = b0 + plen;
@@ -698,14 +816,14 @@ __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const
   store_residual_f32(a, j, f0);
 }
 
-template <int PREC, int R, int SPAN = 0, bool TR = false>
+template <int PREC, int R, int SPAN = 0, bool TR = false, bool FUSE = true>
 __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const DevTaps& t, unsigned char* smraw) {
   if constexpr (PREC == 2) {
     fcf_body_fp32<R, SPAN, TR>(a, j, t, smraw);
     return;
   }
   if constexpr (PREC == 3) {
-    fcf_body_df<R, SPAN, TR>(a, j, t, smraw);
+    fcf_body_df<R, SPAN, TR, FUSE>(a, j, t, smraw);
     return;
   }
   const int nx = a.nx, m = a.m, plen = padded_len(nx);
@@ -836,7 +954,7 @@ __global__ void __launch_bounds__(R == 8 ? 512 : 1024) fcf_batched_kernel(const 
   __syncthreads();
   const FcfArgs a = s->fcf;
   if (s->prec == 0) fcf_body<0, R, SPAN>(a, it.j, st, smraw);
-  else if (s->prec == 3) fcf_body<3, R, SPAN>(a, it.j, st, smraw);
+  else if (s->prec == 3) fcf_body<3, R, SPAN, false, false>(a, it.j, st, smraw);  // one register budget for all
   else fcf_body<1, R, SPAN>(a, it.j, st, smraw);
 }
 
