@@ -75,6 +75,7 @@ struct FcfArgs {
   // Precision 3: u_old and c_new hold float-float pairs (hi, lo) instead of
   // FP64 values (same 8 bytes), so level 1 runs on the FP32 pipes only.
   int df_store;
+  int fused;               // set by launch_fcf only: the fused narrow-stencil body runs
 };
 
 // Sequential march u_n = T u_{n-1} + g_n, n = 1..P-1, on one thread-block

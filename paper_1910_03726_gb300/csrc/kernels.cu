@@ -87,6 +87,14 @@ __device__ __forceinline__ df64 df_fma1(df64 c, df64 x, df64 acc, float one) {
   return {s, fmaf(fmaf(err, one, e), one, acc.lo)};
 }
 __device__ __forceinline__ df64 df_fma(df64 c, df64 x, df64 acc) { return df_fma1(c, x, acc, 1.0f); }
+// c * x as an unnormalised pair: the exact product of the high words and
+// the cross terms (the first tap of a sum, which needs no TwoSum).
+__device__ __forceinline__ df64 df_mul(df64 c, df64 x) {
+  const float p = c.hi * x.hi;
+  float e = fmaf(c.hi, x.hi, -p);
+  e = fmaf(c.hi, x.lo, e);
+  return {p, fmaf(c.lo, x.hi, e)};
+}
 __device__ __forceinline__ df64 df_norm(df64 a) {
   const float s = a.hi + a.lo;
   return {s, a.lo - (s - a.hi)};
@@ -624,25 +632,24 @@ __device__ __forceinline__ void fixed_chunk(const DevTaps& t, const T* __restric
   }
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    T acc = vzero<T>();
+    T acc;
+    if constexpr (std::is_same<T, df64>::value) acc = df_mul(dense_coef<T>(t, 0), w[r]);
+    else acc = dense_coef<T>(t, 0) * w[r];
 #pragma unroll
-    for (int k = 0; k < SPAN; ++k) acc = vfma1<T>(dense_coef<T>(t, k), w[r + k], acc, t.one);
+    for (int k = 1; k < SPAN; ++k) acc = vfma1<T>(dense_coef<T>(t, k), w[r + k], acc, t.one);
     out[r] = vfinish<T>(acc);
   }
 }
 
 // PREC 3 with float-float C-points, one application of the collapsed Phi^m
-// per pass, fixed span, FCF, no boundary rows, nx a multiple of 8 blockDim.x
-// (fused_ok): each step's outputs go from registers straight to their uses
-// (pass 1: c_new and rho against the old C-point, loaded before the
-// arithmetic; pass 2: r and its squared norm) instead of through a second
-// slab.  The values are the unfused body's; only the order of the norm's
-// FP32 partial sums differs.
-__device__ __forceinline__ bool fused_ok(const FcfArgs& a) {
-  return a.df_store && a.m == 1 && a.fx.nl + a.fx.nr == 0 && !a.relax_f && a.r_f && !a.g &&
-         a.nx % (8 * blockDim.x) == 0 && pairs_aligned(a.u_old, a.c_new, a.cstride, 8) &&
-         pairs_aligned(a.r_f, a.r_f, 0, 8);
-}
+// per pass, fixed span <= 5, FCF, no boundary rows, nx a multiple of 8
+// blockDim.x, aligned rows (the launcher checks all of it and sets a.fused;
+// the CTA then has one float-float slab and one FP32 slab of shared memory):
+// each step's outputs go from registers straight to their uses (pass 1:
+// c_new and rho against the old C-point, loaded before the arithmetic;
+// pass 2: r and its squared norm) instead of through a second slab.  The
+// values are the unfused body's; only the order of the norm's FP32 partial
+// sums differs.
 
 template <int SPAN>
 __device__ __forceinline__ void fcf_body_df_fused(const FcfArgs& a, const int j, const DevTaps& t,
@@ -720,7 +727,7 @@ __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const
   // narrow collapsed stencils only: wider windows would raise every path's
   // register count (and so cut the CTAs per SM)
   if constexpr (FUSE && SPAN > 0 && SPAN <= 5 && !TR) {
-    if (fused_ok(a)) {  // uniform over the launch
+    if (a.fused) {  // the launcher's decision (it sized shared memory for it)
       fcf_body_df_fused<SPAN>(a, j, t, smraw);
       return;
     }
@@ -1319,7 +1326,9 @@ static cudaError_t launch_fcf_t(const FcfArgs& a, const DevTaps& t, int threads,
   const size_t smem = 2 * (size_t)padded_len(a.nx) * (PREC == 2 ? sizeof(float) : sizeof(double));
   cudaError_t e = set_smem(fcf_kernel<PREC, R, SPAN, TR>, smem);
   if (e != cudaSuccess) return e;
-  fcf_kernel<PREC, R, SPAN, TR><<<a.N, threads_for(a.nx, R, threads), smem, s>>>(a, t);
+  FcfArgs f = a;
+  f.fused = 0;  // two full slabs: the general body
+  fcf_kernel<PREC, R, SPAN, TR><<<a.N, threads_for(a.nx, R, threads), smem, s>>>(f, t);
   return cudaGetLastError();
 }
 
@@ -1329,8 +1338,36 @@ static bool fixed_span_ok(int span) {
   return span == 2 || span == 5 || span == 10 || span == 17 || span == 31;
 }
 
+// The fused narrow-stencil body of precision 3 (see fcf_body_df_fused): the
+// host checks every condition the body assumes, then launches with one
+// float-float and one FP32 slab of shared memory.
+static bool host_fused_ok(const FcfArgs& a, const DevTaps& t, int threads) {
+  auto al = [](const void* p) { return (reinterpret_cast<unsigned long long>(p) & 15ull) == 0; };
+  return t.span > 0 && t.span <= 5 && a.df_store && a.m == 1 && a.fx.nl + a.fx.nr == 0 && !a.relax_f && !a.trunc &&
+         a.r_f && !a.g && threads > 0 && a.nx % (8 * threads) == 0 && al(a.u_old) && al(a.c_new) && al(a.r_f) &&
+         (a.cstride & 1) == 0;
+}
+
+template <int SPAN>
+static cudaError_t launch_fcf_fused(const FcfArgs& a, const DevTaps& t, int threads, cudaStream_t s) {
+  FcfArgs f = a;
+  f.fused = 1;
+  const size_t smem = (size_t)padded_len(a.nx) * (sizeof(double) + sizeof(float));
+  cudaError_t e = set_smem(fcf_kernel<3, 8, SPAN>, smem);
+  if (e != cudaSuccess) return e;
+  fcf_kernel<3, 8, SPAN><<<a.N, threads, smem, s>>>(f, t);
+  return cudaGetLastError();
+}
+
 template <int PREC>
 static cudaError_t launch_fcf_fixed(const FcfArgs& a, const DevTaps& t, int threads, cudaStream_t s) {
+  if constexpr (PREC == 3) {
+    const int th = threads_for(a.nx, kFixedTile, threads);
+    if (host_fused_ok(a, t, th)) {
+      if (t.span == 2) return launch_fcf_fused<2>(a, t, th, s);
+      if (t.span == 5) return launch_fcf_fused<5>(a, t, th, s);
+    }
+  }
   switch (t.span) {
     case 2: return launch_fcf_t<PREC, 8, 2>(a, t, threads, s);
     case 5: return launch_fcf_t<PREC, 8, 5>(a, t, threads, s);
