@@ -27,6 +27,9 @@ MIX = [  # (p, nx, nt, m, levels, precision)
     (1, 64, 512, 8, 2, 0), (3, 128, 1024, 4, 2, 1), (2, 96, 768, 4, 3, 0), (5, 128, 512, 4, 2, 1),
     (3, 256, 2048, 8, 2, 0), (4, 128, 1024, 16, 2, 1), (1, 256, 1024, 4, 3, 1), (3, 64, 256, 4, 2, 0),
     (2, 128, 2048, 8, 2, 1), (5, 256, 1024, 8, 3, 0), (3, 128, 512, 8, 2, 1), (1, 128, 4096, 16, 2, 0),
+    # MIXED_DF (float-float C-points): two-level (batched march adds into the
+    # pairs) and V-cycle (float-float add of the coarse correction)
+    (3, 128, 1024, 4, 2, 2), (1, 256, 1024, 4, 3, 2), (2, 128, 1024, 8, 2, 2),
 ]
 
 
