@@ -95,6 +95,22 @@ struct MarchArgs {
   int c_add_df;            // c_add holds float-float pairs
 };
 
+// Coarse solve of a periodic level in Fourier space (fft.cu): the march
+// e_n = Psi e_{n-1} + g_n becomes, per mode k, E_n = mu_k E_{n-1} + G_n.
+// spec: rows x nx complex FP64 (re, im interleaved) of workspace, rows >=
+// P - 1; tw: nx/2 twiddles exp(-2 pi i k / nx); mu: the nx symbols
+// mu_k = sum_i psi_i exp(+2 pi i i k / nx).  All device memory.
+struct CoarseFft {
+  double* spec;
+  int rows;
+  const double* tw;
+  const double* mu;
+};
+bool fft_coarse_supported(int nx);   // nx = 2^p, 64 <= nx <= 8192
+// Same result as launch_march with a.init == nullptr and periodic T (three
+// launches: forward transforms, recurrences, inverse transforms + epilogue).
+cudaError_t launch_coarse_fft(const MarchArgs& a, const CoarseFft& f, cudaStream_t s);
+
 // Correction and F-relaxation (ideal interpolation) of one level:
 // u[(j-1)m] = c_new[j-1] + e[j-1], then m-1 steps with g; interval N also
 // writes u[Nm] = c_new[N] + e[N].  e == nullptr reads as zero (final

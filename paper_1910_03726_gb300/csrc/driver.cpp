@@ -758,6 +758,54 @@ static mgrit_status upload_boundaries(mgrit_handle* h) {
   return MGRIT_OK;
 }
 
+// Workspace and tables of the Fourier-space coarsest-level solve (periodic
+// stencil Psi, nx = 2^p): twiddles exp(-2 pi i k / nx) and the symbols
+// mu_k = sum_i psi_i exp(+2 pi i i k / nx) of the coarsest Psi, in FP64 from
+// long double.  Used when the coarsest level has at least kFftMinRows steps:
+// the two transforms cost a fixed latency (one CTA per slab, log2(nx)
+// dependent stages) that a short march beats.  MGRIT_COARSE=march or =fft
+// forces either.
+constexpr int kFftMinRows = 64;
+static mgrit_status setup_coarse_fft(mgrit_handle* h) {
+  const char* cm = std::getenv("MGRIT_COARSE");
+  const bool force = cm && std::strcmp(cm, "fft") == 0;
+  if ((cm && std::strcmp(cm, "march") == 0) || h->inflow || h->redisc || !fft_coarse_supported(h->nx)) return MGRIT_OK;
+  const int nx = h->nx, rows = h->Nl[h->L - 1];
+  if (rows < kFftMinRows && !force) return MGRIT_OK;
+  const Taps& psi = h->ops.back().taps;
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  std::vector<long double> cs(nx), sn(nx);  // cos, sin of 2 pi j / nx
+  for (int j = 0; j < nx; ++j) {
+    cs[j] = std::cos(two_pi * j / nx);
+    sn[j] = std::sin(two_pi * j / nx);
+  }
+  std::vector<double> tw(nx), mu(2 * (size_t)nx);
+  for (int k = 0; k < nx / 2; ++k) {
+    tw[2 * k] = (double)cs[k];
+    tw[2 * k + 1] = (double)-sn[k];
+  }
+  for (int k = 0; k < nx; ++k) {
+    long double re = 0.0L, im = 0.0L;
+    for (int t = 0; t < psi.size(); ++t) {
+      long long ik = ((long long)psi.off[t] * k) % nx;
+      if (ik < 0) ik += nx;
+      re += psi.coef[t] * cs[ik];
+      im += psi.coef[t] * sn[ik];
+    }
+    mu[2 * k] = (double)re;
+    mu[2 * k + 1] = (double)im;
+  }
+  double *spec = nullptr, *tab = nullptr;
+  mgrit_status st;
+  if ((st = dalloc(h, 2 * (size_t)rows * nx, &spec)) != MGRIT_OK || (st = dalloc(h, 3 * (size_t)nx, &tab)) != MGRIT_OK)
+    return st;
+  CUDA_TRY(cudaMemcpyAsync(tab, tw.data(), nx * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaMemcpyAsync(tab + nx, mu.data(), 2 * (size_t)nx * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  h->cfft = {spec, rows, tab, tab + nx};
+  h->fft_coarse = true;
+  return MGRIT_OK;
+}
+
 size_t handle_bytes(const mgrit_problem* prob, const mgrit_opts* opts) {
   const size_t nx = prob->nx, m = opts->m, L = opts->levels;
   std::vector<size_t> N(L + 1, 0);
@@ -778,7 +826,7 @@ size_t handle_bytes(const mgrit_problem* prob, const mgrit_opts* opts) {
 }
 
 mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cudaStream_t stream,
-                           const std::vector<CoarseOp>* ops, mgrit_handle** out, bool sync) {
+                           const std::vector<CoarseOp>* ops, mgrit_handle** out, bool sync, bool batched) {
   *out = nullptr;
   const double t0 = now_s();
   mgrit_status st = validate_problem(prob);
@@ -927,6 +975,11 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
     delete h;
     return st;
   }
+  if (!batched && (st = setup_coarse_fft(h)) != MGRIT_OK) {
+    release(h);
+    delete h;
+    return st;
+  }
   if (cudaMallocHost(&h->norm_host, 8 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     release(h);
@@ -1071,6 +1124,15 @@ mgrit_status run_march(mgrit_handle* h, const MarchArgs& a, const DevTaps& t) {
   });
 }
 
+mgrit_status run_coarse_solve(mgrit_handle* h, const MarchArgs& a, const DevTaps& t) {
+  if (!h->fft_coarse) return run_march(h, a, t);
+  mgrit_status st = klaunch(h, MGRIT_K_MARCH, "coarse fft", [&] {
+    return launch_ok(launch_coarse_fft(a, h->cfft, h->stream), "coarse solve (Fourier space)");
+  });
+  if (st == MGRIT_OK) h->kcount[MGRIT_K_MARCH] += 2;  // three kernels
+  return st;
+}
+
 // ||Phi u0||: residual of the zero initial iterate (only time level 1 is nonzero).
 mgrit_status initial_residual(mgrit_handle* h, const double* u0dev, double* r0) {
   mgrit_status st = initial_residual_async(h, u0dev);
@@ -1141,7 +1203,7 @@ mgrit_status solve_coarsest(mgrit_handle* h) {
   a.nx = h->nx;
   a.trunc = h->inflow;
   a.P = h->Nl[L - 1] + 1;
-  return run_march(h, a, h->dpsi[L - 2]);
+  return run_coarse_solve(h, a, h->dpsi[L - 2]);
 }
 
 // u[l] = relaxed C-points + u[l+1], then F-relaxation (ideal interpolation).
@@ -1207,7 +1269,7 @@ mgrit_status coarse_cycle(mgrit_handle* h, double* c_new) {
     a.trunc = h->inflow;
     a.P = h->Nl[1] + 1;
     a.store_every = 1;
-    return run_march(h, a, h->dpsi[0]);
+    return run_coarse_solve(h, a, h->dpsi[0]);
   }
   st = h->opts.cycle == MGRIT_CYCLE_F ? fcycle_level(h, 2) : vcycle_level(h, 2, true);
   if (st != MGRIT_OK) return st;

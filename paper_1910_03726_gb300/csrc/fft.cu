@@ -1,0 +1,156 @@
+// Coarse-level solve of the periodic problem in Fourier space.
+//
+// The coarse system e_0 = 0, e_n = Psi e_{n-1} + g_n (Eq. 5's block
+// bidiagonal system, Psi circulant) is diagonalised by the discrete Fourier
+// transform: with E_n(k) = sum_x e_n(x) w^{xk}, w = exp(-2 pi i / nx),
+//   E_n(k) = mu_k E_{n-1}(k) + G_n(k),   mu_k = sum_i psi_i w^{-ik},
+// one scalar recurrence per mode (mu_k is the symbol of Psi, Lemma 1).  So
+// instead of marching n sequentially over a cluster, the slabs g_1..g_{P-1}
+// are transformed independently (one CTA per slab), the nx recurrences run in
+// parallel (one thread per mode), and the slabs are transformed back, with the
+// march's epilogue (store u_n, or c_n += e_n) fused into the inverse.
+//
+// FFT: complex FP64, nx = 2^p (64 <= nx <= 8192), in place in shared memory:
+// the slab is loaded in bit-reversed order and combined by p radix-2
+// decimation-in-time stages.  A slab that is identically zero transforms to
+// exact zeros, and a zero spectrum back to exact zeros, so coarse corrections
+// of C-points that are already exact stay exactly zero (as in the march).
+#include <cuda_runtime.h>
+
+#include "device.h"
+
+namespace mg {
+
+namespace {
+
+struct cplx64 {
+  double re, im;
+};
+
+__device__ __forceinline__ cplx64 cmul(cplx64 a, cplx64 b) {
+  return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+}
+
+// In-place radix-2 DIT passes over x[0..n) (bit-reversed input, natural
+// output).  tw[k] = exp(-2 pi i k / n), k < n/2; inverse conjugates it.
+template <bool INV>
+__device__ __forceinline__ void fft_passes(cplx64* x, const cplx64* __restrict__ tw, int n) {
+  for (int half = 1; half < n; half <<= 1) {
+    const int stride = n / (2 * half);  // twiddle step of this stage
+    for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
+      const int pos = b & (half - 1);
+      const int i = ((b - pos) << 1) + pos;  // group * 2 * half + pos
+      const int j = i + half;
+      cplx64 w = tw[pos * stride];
+      if (INV) w.im = -w.im;
+      const cplx64 t = cmul(w, x[j]);
+      const cplx64 u = x[i];
+      x[i] = {u.re + t.re, u.im + t.im};
+      x[j] = {u.re - t.re, u.im - t.im};
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int bitrev(int i, int logn) { return (int)(__brev((unsigned)i) >> (32 - logn)); }
+
+// Slab n = blockIdx.x + 1 of g (FP64 or FP32) -> spectrum row n-1 of spec.
+__global__ void __launch_bounds__(512) fft_forward_kernel(const double* __restrict__ g, const float* __restrict__ g_f,
+                                                          cplx64* __restrict__ spec, const cplx64* __restrict__ tw,
+                                                          int nx, int logn) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx64* x = reinterpret_cast<cplx64*>(smraw);
+  const long long n = blockIdx.x + 1;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const double v = g_f ? (double)__ldcg(g_f + n * nx + i) : __ldcg(g + n * nx + i);
+    x[bitrev(i, logn)] = {v, 0.0};
+  }
+  __syncthreads();
+  fft_passes<false>(x, tw, nx);
+  cplx64* out = spec + (n - 1) * nx;
+  for (int k = threadIdx.x; k < nx; k += blockDim.x) out[k] = x[k];
+}
+
+// E_n(k) = mu_k E_{n-1}(k) + G_n(k), n = 1..P-1, in place; one thread per
+// mode, the next row's G loaded one step ahead.
+__global__ void __launch_bounds__(256) fft_recur_kernel(cplx64* __restrict__ spec, const cplx64* __restrict__ mu,
+                                                        int nx, int rows) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nx) return;
+  const cplx64 m = mu[k];
+  cplx64 e = {0.0, 0.0};
+  cplx64 nxt = rows > 0 ? spec[k] : cplx64{0.0, 0.0};
+  for (int r = 0; r < rows; ++r) {
+    const cplx64 gk = nxt;
+    if (r + 1 < rows) nxt = spec[(long long)(r + 1) * nx + k];
+    const cplx64 me = cmul(m, e);
+    e = {me.re + gk.re, me.im + gk.im};
+    spec[(long long)r * nx + k] = e;
+  }
+}
+
+// Spectrum row n-1 -> e_n, then the march's epilogue for point n.
+__global__ void __launch_bounds__(512) fft_inverse_kernel(const cplx64* __restrict__ spec, const cplx64* __restrict__ tw,
+                                                          int nx, int logn, MarchArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplx64* x = reinterpret_cast<cplx64*>(smraw);
+  const long long n = blockIdx.x + 1;
+  const cplx64* in = spec + (n - 1) * nx;
+  for (int k = threadIdx.x; k < nx; k += blockDim.x) x[bitrev(k, logn)] = in[k];
+  __syncthreads();
+  fft_passes<true>(x, tw, nx);
+  const double scale = 1.0 / nx;
+  const bool store = (a.u_out || a.u_out_f) && (n % a.store_every) == 0;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const double e = x[i].re * scale;
+    if (a.c_add && a.c_add_df) {  // float-float C-points
+      float2* c = reinterpret_cast<float2*>(a.c_add) + n * nx + i;
+      const float2 v = *c;
+      const double s = ((double)v.x + (double)v.y) + e;
+      const float hi = (float)s;
+      *c = make_float2(hi, (float)(s - (double)hi));
+    } else if (a.c_add) {
+      a.c_add[n * nx + i] += e;
+    }
+    if (store) {
+      const long long o = (n / a.store_every) * nx + i;
+      if (a.u_out_f) a.u_out_f[o] = (float)e;
+      else a.u_out[o] = e;
+    }
+  }
+}
+
+int fft_threads(int nx) { return nx >= 1024 ? 512 : (nx / 2 < 32 ? 32 : nx / 2); }
+
+}  // namespace
+
+bool fft_coarse_supported(int nx) { return nx >= 64 && nx <= 8192 && (nx & (nx - 1)) == 0; }
+
+cudaError_t launch_coarse_fft(const MarchArgs& a, const CoarseFft& f, cudaStream_t s) {
+  if (a.P < 2) return cudaSuccess;
+  if (!fft_coarse_supported(a.nx) || a.init || a.trunc || !f.spec || a.P - 1 > f.rows || (!a.g && !a.g_f))
+    return cudaErrorInvalidValue;
+  int logn = 0;
+  while ((1 << logn) < a.nx) ++logn;
+  const size_t smem = (size_t)a.nx * sizeof(cplx64);
+  const int th = fft_threads(a.nx);
+  cplx64* spec = reinterpret_cast<cplx64*>(f.spec);
+  const cplx64* tw = reinterpret_cast<const cplx64*>(f.tw);
+  const cplx64* mu = reinterpret_cast<const cplx64*>(f.mu);
+  cudaError_t e = cudaSuccess;
+  if (smem > 48 * 1024) {
+    if ((e = cudaFuncSetAttribute(fft_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(fft_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+      return e;
+  }
+  fft_forward_kernel<<<a.P - 1, th, smem, s>>>(a.g_f ? nullptr : a.g, a.g_f, spec, tw, a.nx, logn);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  fft_recur_kernel<<<(a.nx + 255) / 256, 256, 0, s>>>(spec, mu, a.nx, a.P - 1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  fft_inverse_kernel<<<a.P - 1, th, smem, s>>>(spec, tw, a.nx, logn, a);
+  return cudaGetLastError();
+}
+
+}  // namespace mg

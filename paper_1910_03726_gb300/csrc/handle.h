@@ -39,6 +39,9 @@ struct mgrit_handle {
   // differ from the circulant (device tables); every Psi_l is truncated at
   // both ends by the kernels' loads
   bool inflow = false;
+  // coarsest-level solve in Fourier space (periodic, nx a power of two)
+  bool fft_coarse = false;
+  mg::CoarseFft cfft = {};
   mg::Fixup fx_phi = {};
   mg::Fixup fx_phim = {};             // of Phi^m (the collapsed path)
   std::vector<DevBuf> bufs;       // everything allocated, for release
@@ -97,6 +100,9 @@ void reset_stats(mgrit_handle* h);
 cudaEvent_t next_event(mgrit_handle* h);
 void collect_stats(mgrit_handle* h, mgrit_result* R);
 mgrit_status run_march(mgrit_handle* h, const mg::MarchArgs& a, const mg::DevTaps& t);
+// The coarsest-level solve (a march without initial value): in Fourier space
+// when the handle has the workspace, else the cluster march.
+mgrit_status run_coarse_solve(mgrit_handle* h, const mg::MarchArgs& a, const mg::DevTaps& t);
 mgrit_status initial_residual(mgrit_handle* h, const double* u0dev, double* r0);
 mgrit_status initial_residual_async(mgrit_handle* h, const double* u0dev);
 // Initial iterate into the handle's C-point arrays (u0 with a zero iterate,
@@ -104,9 +110,11 @@ mgrit_status initial_residual_async(mgrit_handle* h, const double* u0dev);
 mgrit_status load_iterate(mgrit_handle* h, const double* u0, const double* c_init);
 mgrit_status coarse_cycle(mgrit_handle* h, double* c_new);
 // Build a handle; ops != nullptr supplies an already fitted hierarchy.
+// batched: a server's handle (its two-level coarse solves run in the
+// batched march, so no Fourier-space workspace is allocated).
 mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cudaStream_t stream,
                            const std::vector<mg::CoarseOp>* ops, mgrit_handle** out,
-                           bool sync = true);
+                           bool sync = true, bool batched = false);
 // Device bytes a handle for this request will allocate (admission control).
 size_t handle_bytes(const mgrit_problem* prob, const mgrit_opts* opts);
 // SDIRK stage-solve plan for the problem (factored stage matrix), checked on

@@ -172,7 +172,7 @@ static std::vector<Request*> admit(mgrit_server* S, std::unique_lock<std::mutex>
     S->resident += r->bytes;
     const std::vector<CoarseOp>* cached = &itp->second.ops;
     lk.unlock();
-    mgrit_status st = handle_create(&r->prob, &r->opts, S->stream, cached, &r->h, false);
+    mgrit_status st = handle_create(&r->prob, &r->opts, S->stream, cached, &r->h, false, true);
     if (st == MGRIT_OK) S->stats.tune_s += r->h->tune_s;
     std::string msg = st == MGRIT_OK ? "" : mgrit_last_error();
     if (st == MGRIT_OK) {

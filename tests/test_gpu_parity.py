@@ -283,6 +283,30 @@ def test_relax_sweeps_match_oracle(capi, precision, relax):
         assert got[0] == got[-1]
 
 
+@pytest.mark.parametrize("case", [("ERK", 3, 256, 2048, 4, 2), ("ERK", 3, 256, 2048, 8, 3), ("ERK", 1, 64, 1024, 2, 6),
+                                  ("ERK", 5, 128, 1024, 4, 3)])
+@pytest.mark.parametrize("coarse", ["fft", "march"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_coarse_solver_parity(capi, monkeypatch, case, coarse, precision):
+    """The coarsest level solved in Fourier space (per-mode recurrences with
+    Psi's symbol between forward and inverse FFTs) and by the cluster march,
+    forced either way for long and short coarsest levels: FP64 gives the
+    oracle's iterations and C-points; MIXED the oracle's C-points to 1e-9."""
+    monkeypatch.setenv("MGRIT_COARSE", coarse)
+    fam, p, nx, nt, m, L = case
+    c = schemes.cfl_number(fam, p)
+    u0 = workloads.fourier_field(nx)
+    it, r, U, _ = oracle_run(fam, p, c, nx, nt, m, L, "auto", u0)
+    res, out, _ = gpu_run(capi, fam, p, c, nx, nt, m, L, "auto", u0, precision=precision)
+    assert res.converged == 1
+    if precision == 0:
+        assert res.iterations == it
+        assert rel(out, U[::m]) <= TOL
+    else:
+        assert abs(res.iterations - it) <= 1
+        assert rel(out, U[::m]) <= 1e-9
+
+
 @pytest.mark.parametrize("p,m", [(1, 4), (2, 4), (1, 16)])
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_collapsed_fixed_span_shape(capi, monkeypatch, p, m, precision):

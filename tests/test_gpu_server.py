@@ -63,9 +63,20 @@ def _wait(capi, srv, ticket, rows, nx, timeout=120.0):
 
 
 @pytest.mark.parametrize("budget_solves", [100, 3])
-def test_batch_results_equal_alone(capi, budget_solves):
+def test_batch_results_equal_alone(capi, budget_solves, monkeypatch):
+    """Each result equals the same solve alone.  The server's two-level
+    coarse solves run in the batched cluster march, so "alone" uses the
+    march too (MGRIT_COARSE=march; equal to 1e-14); single solves by default
+    solve the coarsest level in Fourier space, which agrees to rounding
+    (1e-12, the FP64 parity tolerance) with the same iteration count."""
     specs = [_spec(capi, *s) for s in MIX]
+    fourier = [_alone(capi, *sp) for sp in specs]
+    monkeypatch.setenv("MGRIT_COARSE", "march")
     alone = [_alone(capi, *sp) for sp in specs]
+    monkeypatch.delenv("MGRIT_COARSE")
+    for (fres, fout), (ares, aout) in zip(fourier, alone):
+        assert fres.iterations == ares.iterations
+        assert float(np.max(np.abs(fout - aout)) / np.max(np.abs(aout))) <= 1e-12
     from paper_1910_03726_gb300.capi import _lib  # noqa: F401
     max_bytes = max(sp[0].nx * (sp[0].nt // sp[1].m + 1) * 8 * 6 for sp in specs)
     srv = capi.mgrit_server_create(budget_solves * max_bytes)
