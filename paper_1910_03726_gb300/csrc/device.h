@@ -105,7 +105,9 @@ struct CoarseFft {
   int rows;
   const double* tw;
   const double* mu;
+  double* carry;           // kMaxScanBlocks x nx complex: last value of each block of rows
 };
+constexpr int kMaxScanBlocks = 64;  // blocks of the chunked scan over the coarse steps
 bool fft_coarse_supported(int nx);   // nx = 2^p, 64 <= nx <= 8192
 // Same result as launch_march with a.init == nullptr and periodic T (three
 // launches: forward transforms, recurrences, inverse transforms + epilogue).

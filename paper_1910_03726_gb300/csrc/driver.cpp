@@ -795,13 +795,14 @@ static mgrit_status setup_coarse_fft(mgrit_handle* h) {
     mu[2 * k] = (double)re;
     mu[2 * k + 1] = (double)im;
   }
-  double *spec = nullptr, *tab = nullptr;
+  double *spec = nullptr, *tab = nullptr, *carry = nullptr;
   mgrit_status st;
-  if ((st = dalloc(h, 2 * (size_t)rows * nx, &spec)) != MGRIT_OK || (st = dalloc(h, 3 * (size_t)nx, &tab)) != MGRIT_OK)
+  if ((st = dalloc(h, 2 * (size_t)rows * nx, &spec)) != MGRIT_OK || (st = dalloc(h, 3 * (size_t)nx, &tab)) != MGRIT_OK ||
+      (st = dalloc(h, 2 * (size_t)kMaxScanBlocks * nx, &carry)) != MGRIT_OK)
     return st;
   CUDA_TRY(cudaMemcpyAsync(tab, tw.data(), nx * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(cudaMemcpyAsync(tab + nx, mu.data(), 2 * (size_t)nx * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-  h->cfft = {spec, rows, tab, tab + nx};
+  h->cfft = {spec, rows, tab, tab + nx, carry};
   h->fft_coarse = true;
   return MGRIT_OK;
 }
@@ -1129,7 +1130,7 @@ mgrit_status run_coarse_solve(mgrit_handle* h, const MarchArgs& a, const DevTaps
   mgrit_status st = klaunch(h, MGRIT_K_MARCH, "coarse fft", [&] {
     return launch_ok(launch_coarse_fft(a, h->cfft, h->stream), "coarse solve (Fourier space)");
   });
-  if (st == MGRIT_OK) h->kcount[MGRIT_K_MARCH] += 2;  // three kernels
+  if (st == MGRIT_OK) h->kcount[MGRIT_K_MARCH] += 3;  // four kernels (three with a single scan block)
   return st;
 }
 

@@ -71,21 +71,62 @@ __global__ void __launch_bounds__(512) fft_forward_kernel(const double* __restri
   for (int k = threadIdx.x; k < nx; k += blockDim.x) out[k] = x[k];
 }
 
-// E_n(k) = mu_k E_{n-1}(k) + G_n(k), n = 1..P-1, in place; one thread per
-// mode, the next row's G loaded one step ahead.
-__global__ void __launch_bounds__(256) fft_recur_kernel(cplx64* __restrict__ spec, const cplx64* __restrict__ mu,
-                                                        int nx, int rows) {
+// E_n(k) = mu_k E_{n-1}(k) + G_n(k), n = 1..P-1, in place, as a chunked
+// scan over n so that all SMs work: the rows are split into blocks of L.
+// Pass 1 (one thread per mode and block): the block's recurrence from zero;
+// its last value goes to carry[b][k].  Pass 2: the block's incoming value
+// C_b = sum over earlier blocks of mu^(L (b-1-b')) last_b' (a recurrence over
+// b with mu^L), then E_n += mu^(n - n_b + 1) C_b along the block.  A block
+// whose rows and incoming value are zero stays exactly zero.
+__global__ void __launch_bounds__(256) fft_recur_local_kernel(cplx64* __restrict__ spec, const cplx64* __restrict__ mu,
+                                                              cplx64* __restrict__ carry, int nx, int rows, int L) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nx) return;
+  const int b = blockIdx.y;
+  const int r0 = b * L, r1 = min(rows, r0 + L);
+  if (k >= nx || r0 >= rows) return;
   const cplx64 m = mu[k];
   cplx64 e = {0.0, 0.0};
-  cplx64 nxt = rows > 0 ? spec[k] : cplx64{0.0, 0.0};
-  for (int r = 0; r < rows; ++r) {
+  cplx64 nxt = spec[(long long)r0 * nx + k];
+  for (int r = r0; r < r1; ++r) {
     const cplx64 gk = nxt;
-    if (r + 1 < rows) nxt = spec[(long long)(r + 1) * nx + k];
+    if (r + 1 < r1) nxt = spec[(long long)(r + 1) * nx + k];
     const cplx64 me = cmul(m, e);
     e = {me.re + gk.re, me.im + gk.im};
     spec[(long long)r * nx + k] = e;
+  }
+  carry[(long long)b * nx + k] = e;
+}
+
+__global__ void __launch_bounds__(256) fft_recur_carry_kernel(cplx64* __restrict__ spec, const cplx64* __restrict__ mu,
+                                                              const cplx64* __restrict__ carry, int nx, int rows,
+                                                              int L) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y + 1;  // block 0 has no incoming value
+  const int r0 = b * L, r1 = min(rows, r0 + L);
+  if (k >= nx || r0 >= rows) return;
+  const cplx64 m = mu[k];
+  cplx64 mL = {1.0, 0.0};  // mu^L by squaring
+  {
+    cplx64 base = m;
+    for (int e = L; e; e >>= 1) {
+      if (e & 1) mL = cmul(mL, base);
+      base = cmul(base, base);
+    }
+  }
+  cplx64 c = {0.0, 0.0};  // value entering block b (blocks before b are full)
+  for (int bb = 0; bb < b; ++bb) {
+    const cplx64 t = cmul(mL, c);
+    const cplx64 last = carry[(long long)bb * nx + k];
+    c = {t.re + last.re, t.im + last.im};
+  }
+  if (c.re == 0.0 && c.im == 0.0) return;
+  cplx64 p = m;  // mu^(r - r0 + 1)
+  for (int r = r0; r < r1; ++r) {
+    cplx64* s = spec + (long long)r * nx + k;
+    const cplx64 add = cmul(p, c);
+    const cplx64 v = *s;
+    *s = {v.re + add.re, v.im + add.im};
+    p = cmul(p, m);
   }
 }
 
@@ -128,7 +169,8 @@ bool fft_coarse_supported(int nx) { return nx >= 64 && nx <= 8192 && (nx & (nx -
 
 cudaError_t launch_coarse_fft(const MarchArgs& a, const CoarseFft& f, cudaStream_t s) {
   if (a.P < 2) return cudaSuccess;
-  if (!fft_coarse_supported(a.nx) || a.init || a.trunc || !f.spec || a.P - 1 > f.rows || (!a.g && !a.g_f))
+  if (!fft_coarse_supported(a.nx) || a.init || a.trunc || !f.spec || !f.carry || a.P - 1 > f.rows ||
+      (!a.g && !a.g_f))
     return cudaErrorInvalidValue;
   int logn = 0;
   while ((1 << logn) < a.nx) ++logn;
@@ -147,8 +189,21 @@ cudaError_t launch_coarse_fft(const MarchArgs& a, const CoarseFft& f, cudaStream
   }
   fft_forward_kernel<<<a.P - 1, th, smem, s>>>(a.g_f ? nullptr : a.g, a.g_f, spec, tw, a.nx, logn);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  fft_recur_kernel<<<(a.nx + 255) / 256, 256, 0, s>>>(spec, mu, a.nx, a.P - 1);
+  const int rows = a.P - 1;
+  const int mblocks = (a.nx + 255) / 256;
+  // enough blocks of rows for about four CTAs per SM, at most kMaxScanBlocks
+  int nb = (4 * 152 + mblocks - 1) / mblocks;
+  nb = nb < 1 ? 1 : (nb > kMaxScanBlocks ? kMaxScanBlocks : nb);
+  nb = nb > rows ? rows : nb;
+  const int L = (rows + nb - 1) / nb;
+  nb = (rows + L - 1) / L;
+  cplx64* carry = reinterpret_cast<cplx64*>(f.carry);
+  fft_recur_local_kernel<<<dim3(mblocks, nb), 256, 0, s>>>(spec, mu, carry, a.nx, rows, L);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (nb > 1) {
+    fft_recur_carry_kernel<<<dim3(mblocks, nb - 1), 256, 0, s>>>(spec, mu, carry, a.nx, rows, L);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   fft_inverse_kernel<<<a.P - 1, th, smem, s>>>(spec, tw, a.nx, logn, a);
   return cudaGetLastError();
 }
