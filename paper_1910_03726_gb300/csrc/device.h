@@ -97,15 +97,15 @@ struct MarchArgs {
 
 // Coarse solve of a periodic level in Fourier space (fft.cu): the march
 // e_n = Psi e_{n-1} + g_n becomes, per mode k, E_n = mu_k E_{n-1} + G_n.
-// spec: rows x nx complex FP64 (re, im interleaved) of workspace, rows >=
-// P - 1; tw: nx/2 twiddles exp(-2 pi i k / nx); mu: the nx symbols
-// mu_k = sum_i psi_i exp(+2 pi i i k / nx).  All device memory.
+// spec: rows x (nx/2 + 1) complex FP64 (re, im interleaved) of workspace,
+// rows >= P - 1; tw: nx/2 twiddles exp(-2 pi i k / nx); mu: the symbols
+// mu_k = sum_i psi_i exp(+2 pi i i k / nx), k < nx.  All device memory.
 struct CoarseFft {
   double* spec;
   int rows;
   const double* tw;
   const double* mu;
-  double* carry;           // kMaxScanBlocks x nx complex: last value of each block of rows
+  double* carry;           // kMaxScanBlocks x (nx/2 + 1) complex: last value of each block of rows
 };
 constexpr int kMaxScanBlocks = 64;  // blocks of the chunked scan over the coarse steps
 bool fft_coarse_supported(int nx);   // nx = 2^p, 64 <= nx <= 8192

@@ -797,8 +797,9 @@ static mgrit_status setup_coarse_fft(mgrit_handle* h) {
   }
   double *spec = nullptr, *tab = nullptr, *carry = nullptr;
   mgrit_status st;
-  if ((st = dalloc(h, 2 * (size_t)rows * nx, &spec)) != MGRIT_OK || (st = dalloc(h, 3 * (size_t)nx, &tab)) != MGRIT_OK ||
-      (st = dalloc(h, 2 * (size_t)kMaxScanBlocks * nx, &carry)) != MGRIT_OK)
+  const size_t nh = (size_t)nx / 2 + 1;  // independent modes of a real slab
+  if ((st = dalloc(h, 2 * (size_t)rows * nh, &spec)) != MGRIT_OK || (st = dalloc(h, 3 * (size_t)nx, &tab)) != MGRIT_OK ||
+      (st = dalloc(h, 2 * (size_t)kMaxScanBlocks * nh, &carry)) != MGRIT_OK)
     return st;
   CUDA_TRY(cudaMemcpyAsync(tab, tw.data(), nx * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(cudaMemcpyAsync(tab + nx, mu.data(), 2 * (size_t)nx * sizeof(double), cudaMemcpyHostToDevice, h->stream));

@@ -10,11 +10,17 @@
 // parallel (one thread per mode), and the slabs are transformed back, with the
 // march's epilogue (store u_n, or c_n += e_n) fused into the inverse.
 //
-// FFT: complex FP64, nx = 2^p (64 <= nx <= 8192), in place in shared memory:
-// the slab is loaded in bit-reversed order and combined by p radix-2
-// decimation-in-time stages.  A slab that is identically zero transforms to
-// exact zeros, and a zero spectrum back to exact zeros, so coarse corrections
-// of C-points that are already exact stay exactly zero (as in the march).
+// FFT: the slabs are real, so each is transformed as one complex FFT of
+// half length, z_j = x_{2j} + i x_{2j+1} (FP64, in place in shared memory:
+// loaded in bit-reversed order, p-1 radix-2 decimation-in-time stages), and
+// split into the nx/2 + 1 independent modes with
+//   X_k = E_k + w^k O_k,  E_k = (Z_k + conj Z_{h-k}) / 2,
+//   O_k = (Z_k - conj Z_{h-k}) / 2i,  h = nx/2;
+// the other modes are their conjugates (Psi is real) and are never formed.
+// The inverse recombines Z_k = E_k + i O_k from X_k and X_{h-k}.  A slab that
+// is identically zero transforms to exact zeros, and a zero spectrum back to
+// exact zeros, so coarse corrections of C-points that are already exact stay
+// exactly zero (as in the march).
 #include <cuda_runtime.h>
 
 #include "device.h"
@@ -32,11 +38,12 @@ __device__ __forceinline__ cplx64 cmul(cplx64 a, cplx64 b) {
 }
 
 // In-place radix-2 DIT passes over x[0..n) (bit-reversed input, natural
-// output).  tw[k] = exp(-2 pi i k / n), k < n/2; inverse conjugates it.
+// output).  tw[k] = exp(-2 pi i k / (2n)), k < n: the stages use every second
+// entry (exp(-2 pi i k / n)); inverse conjugates them.
 template <bool INV>
 __device__ __forceinline__ void fft_passes(cplx64* x, const cplx64* __restrict__ tw, int n) {
   for (int half = 1; half < n; half <<= 1) {
-    const int stride = n / (2 * half);  // twiddle step of this stage
+    const int stride = 2 * (n / (2 * half));  // twiddle step of this stage in the 2n-point table
     for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
       const int pos = b & (half - 1);
       const int i = ((b - pos) << 1) + pos;  // group * 2 * half + pos
@@ -54,21 +61,40 @@ __device__ __forceinline__ void fft_passes(cplx64* x, const cplx64* __restrict__
 
 __device__ __forceinline__ int bitrev(int i, int logn) { return (int)(__brev((unsigned)i) >> (32 - logn)); }
 
-// Slab n = blockIdx.x + 1 of g (FP64 or FP32) -> spectrum row n-1 of spec.
+// Slab n = blockIdx.x + 1 of g (FP64 or FP32) -> spectrum row n-1 of spec
+// (nh = nx/2 + 1 modes per row).  logh = log2(nx/2).
 __global__ void __launch_bounds__(512) fft_forward_kernel(const double* __restrict__ g, const float* __restrict__ g_f,
                                                           cplx64* __restrict__ spec, const cplx64* __restrict__ tw,
-                                                          int nx, int logn) {
+                                                          int nx, int logh) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  cplx64* x = reinterpret_cast<cplx64*>(smraw);
+  cplx64* z = reinterpret_cast<cplx64*>(smraw);
+  const int h = nx / 2;
   const long long n = blockIdx.x + 1;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    const double v = g_f ? (double)__ldcg(g_f + n * nx + i) : __ldcg(g + n * nx + i);
-    x[bitrev(i, logn)] = {v, 0.0};
+  for (int j = threadIdx.x; j < h; j += blockDim.x) {
+    double a, b;
+    if (g_f) {
+      const float2 v = __ldcg(reinterpret_cast<const float2*>(g_f + n * nx) + j);
+      a = v.x;
+      b = v.y;
+    } else {
+      const double2 v = __ldcg(reinterpret_cast<const double2*>(g + n * nx) + j);
+      a = v.x;
+      b = v.y;
+    }
+    z[bitrev(j, logh)] = {a, b};
   }
   __syncthreads();
-  fft_passes<false>(x, tw, nx);
-  cplx64* out = spec + (n - 1) * nx;
-  for (int k = threadIdx.x; k < nx; k += blockDim.x) out[k] = x[k];
+  fft_passes<false>(z, tw, h);
+  cplx64* out = spec + (n - 1) * (h + 1);
+  for (int k = threadIdx.x; k <= h; k += blockDim.x) {
+    const cplx64 zk = z[k == h ? 0 : k];
+    const cplx64 zc = z[k == 0 ? 0 : h - k];  // Z_{h-k}, Z_h = Z_0
+    const cplx64 e = {0.5 * (zk.re + zc.re), 0.5 * (zk.im - zc.im)};
+    const cplx64 o = {0.5 * (zk.im + zc.im), -0.5 * (zk.re - zc.re)};  // (Z_k - conj Z_{h-k}) / 2i
+    const cplx64 w = k == h ? cplx64{-1.0, 0.0} : tw[k];
+    const cplx64 wo = cmul(w, o);
+    out[k] = {e.re + wo.re, e.im + wo.im};
+  }
 }
 
 // E_n(k) = mu_k E_{n-1}(k) + G_n(k), n = 1..P-1, in place, as a chunked
@@ -132,36 +158,50 @@ __global__ void __launch_bounds__(256) fft_recur_carry_kernel(cplx64* __restrict
 
 // Spectrum row n-1 -> e_n, then the march's epilogue for point n.
 __global__ void __launch_bounds__(512) fft_inverse_kernel(const cplx64* __restrict__ spec, const cplx64* __restrict__ tw,
-                                                          int nx, int logn, MarchArgs a) {
+                                                          int nx, int logh, MarchArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  cplx64* x = reinterpret_cast<cplx64*>(smraw);
+  cplx64* z = reinterpret_cast<cplx64*>(smraw);
+  const int h = nx / 2;
   const long long n = blockIdx.x + 1;
-  const cplx64* in = spec + (n - 1) * nx;
-  for (int k = threadIdx.x; k < nx; k += blockDim.x) x[bitrev(k, logn)] = in[k];
+  const cplx64* in = spec + (n - 1) * (h + 1);
+  for (int k = threadIdx.x; k < h; k += blockDim.x) {
+    const cplx64 xk = in[k];
+    const cplx64 xc = in[h - k];  // X_{h-k}
+    const cplx64 e = {0.5 * (xk.re + xc.re), 0.5 * (xk.im - xc.im)};
+    const cplx64 d = {0.5 * (xk.re - xc.re), 0.5 * (xk.im + xc.im)};  // (X_k - conj X_{h-k}) / 2
+    const cplx64 w = {tw[k].re, -tw[k].im};
+    const cplx64 o = cmul(w, d);
+    z[bitrev(k, logh)] = {e.re - o.im, e.im + o.re};  // E_k + i O_k
+  }
   __syncthreads();
-  fft_passes<true>(x, tw, nx);
-  const double scale = 1.0 / nx;
+  fft_passes<true>(z, tw, h);
+  const double scale = 1.0 / h;
   const bool store = (a.u_out || a.u_out_f) && (n % a.store_every) == 0;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-    const double e = x[i].re * scale;
-    if (a.c_add && a.c_add_df) {  // float-float C-points
-      float2* c = reinterpret_cast<float2*>(a.c_add) + n * nx + i;
-      const float2 v = *c;
-      const double s = ((double)v.x + (double)v.y) + e;
-      const float hi = (float)s;
-      *c = make_float2(hi, (float)(s - (double)hi));
-    } else if (a.c_add) {
-      a.c_add[n * nx + i] += e;
-    }
-    if (store) {
-      const long long o = (n / a.store_every) * nx + i;
-      if (a.u_out_f) a.u_out_f[o] = (float)e;
-      else a.u_out[o] = e;
+  for (int j = threadIdx.x; j < h; j += blockDim.x) {
+    const double ev[2] = {z[j].re * scale, z[j].im * scale};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int i = 2 * j + q;
+      const double e = ev[q];
+      if (a.c_add && a.c_add_df) {  // float-float C-points
+        float2* c = reinterpret_cast<float2*>(a.c_add) + n * nx + i;
+        const float2 v = *c;
+        const double s = ((double)v.x + (double)v.y) + e;
+        const float hi = (float)s;
+        *c = make_float2(hi, (float)(s - (double)hi));
+      } else if (a.c_add) {
+        a.c_add[n * nx + i] += e;
+      }
+      if (store) {
+        const long long o = (n / a.store_every) * nx + i;
+        if (a.u_out_f) a.u_out_f[o] = (float)e;
+        else a.u_out[o] = e;
+      }
     }
   }
 }
 
-int fft_threads(int nx) { return nx >= 1024 ? 512 : (nx / 2 < 32 ? 32 : nx / 2); }
+int fft_threads(int nx) { return nx >= 2048 ? 512 : (nx / 4 < 32 ? 32 : nx / 4); }
 
 }  // namespace
 
@@ -172,9 +212,10 @@ cudaError_t launch_coarse_fft(const MarchArgs& a, const CoarseFft& f, cudaStream
   if (!fft_coarse_supported(a.nx) || a.init || a.trunc || !f.spec || !f.carry || a.P - 1 > f.rows ||
       (!a.g && !a.g_f))
     return cudaErrorInvalidValue;
-  int logn = 0;
-  while ((1 << logn) < a.nx) ++logn;
-  const size_t smem = (size_t)a.nx * sizeof(cplx64);
+  int logh = 0;
+  while ((2 << logh) < a.nx) ++logh;
+  const int nh = a.nx / 2 + 1;  // independent modes of a real slab
+  const size_t smem = (size_t)(a.nx / 2) * sizeof(cplx64);
   const int th = fft_threads(a.nx);
   cplx64* spec = reinterpret_cast<cplx64*>(f.spec);
   const cplx64* tw = reinterpret_cast<const cplx64*>(f.tw);
@@ -187,10 +228,10 @@ cudaError_t launch_coarse_fft(const MarchArgs& a, const CoarseFft& f, cudaStream
             cudaSuccess)
       return e;
   }
-  fft_forward_kernel<<<a.P - 1, th, smem, s>>>(a.g_f ? nullptr : a.g, a.g_f, spec, tw, a.nx, logn);
+  fft_forward_kernel<<<a.P - 1, th, smem, s>>>(a.g_f ? nullptr : a.g, a.g_f, spec, tw, a.nx, logh);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int rows = a.P - 1;
-  const int mblocks = (a.nx + 255) / 256;
+  const int mblocks = (nh + 255) / 256;
   // enough blocks of rows for about four CTAs per SM, at most kMaxScanBlocks
   int nb = (4 * 152 + mblocks - 1) / mblocks;
   nb = nb < 1 ? 1 : (nb > kMaxScanBlocks ? kMaxScanBlocks : nb);
@@ -198,13 +239,13 @@ cudaError_t launch_coarse_fft(const MarchArgs& a, const CoarseFft& f, cudaStream
   const int L = (rows + nb - 1) / nb;
   nb = (rows + L - 1) / L;
   cplx64* carry = reinterpret_cast<cplx64*>(f.carry);
-  fft_recur_local_kernel<<<dim3(mblocks, nb), 256, 0, s>>>(spec, mu, carry, a.nx, rows, L);
+  fft_recur_local_kernel<<<dim3(mblocks, nb), 256, 0, s>>>(spec, mu, carry, nh, rows, L);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (nb > 1) {
-    fft_recur_carry_kernel<<<dim3(mblocks, nb - 1), 256, 0, s>>>(spec, mu, carry, a.nx, rows, L);
+    fft_recur_carry_kernel<<<dim3(mblocks, nb - 1), 256, 0, s>>>(spec, mu, carry, nh, rows, L);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  fft_inverse_kernel<<<a.P - 1, th, smem, s>>>(spec, tw, a.nx, logn, a);
+  fft_inverse_kernel<<<a.P - 1, th, smem, s>>>(spec, tw, a.nx, logh, a);
   return cudaGetLastError();
 }
 
