@@ -109,6 +109,8 @@ struct CoarseFft {
 };
 constexpr int kMaxScanBlocks = 64;  // blocks of the chunked scan over the coarse steps
 bool fft_coarse_supported(int nx);   // nx = 2^p, 64 <= nx <= 8192
+// Fill tw (nx/2 complex) and mu (nx complex) of CoarseFft from the stencil.
+cudaError_t launch_fft_tables(const DevTaps& psi, int nx, double* tw, double* mu, cudaStream_t s);
 // Same result as launch_march with a.init == nullptr and periodic T (three
 // launches: forward transforms, recurrences, inverse transforms + epilogue).
 cudaError_t launch_coarse_fft(const MarchArgs& a, const CoarseFft& f, cudaStream_t s);

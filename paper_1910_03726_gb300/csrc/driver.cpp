@@ -760,49 +760,32 @@ static mgrit_status upload_boundaries(mgrit_handle* h) {
 
 // Workspace and tables of the Fourier-space coarsest-level solve (periodic
 // stencil Psi, nx = 2^p): twiddles exp(-2 pi i k / nx) and the symbols
-// mu_k = sum_i psi_i exp(+2 pi i i k / nx) of the coarsest Psi, in FP64 from
-// long double.  Used when the coarsest level has at least kFftMinRows steps:
+// mu_k = sum_i psi_i exp(+2 pi i i k / nx) of the coarsest Psi, in FP64 on
+// the device.  Used when the coarsest level has at least kFftMinRows steps:
 // the two transforms cost a fixed latency (one CTA per slab, log2(nx)
 // dependent stages) that a short march beats.  MGRIT_COARSE=march or =fft
 // forces either.
-constexpr int kFftMinRows = 64;
-static mgrit_status setup_coarse_fft(mgrit_handle* h) {
+constexpr int kFftMinRows = 16;
+// Whether a handle for this request solves its coarsest level in Fourier space.
+static bool wants_coarse_fft(const mgrit_problem* p, const mgrit_opts* o, long long rows) {
   const char* cm = std::getenv("MGRIT_COARSE");
   const bool force = cm && std::strcmp(cm, "fft") == 0;
-  if ((cm && std::strcmp(cm, "march") == 0) || h->inflow || h->redisc || !fft_coarse_supported(h->nx)) return MGRIT_OK;
+  if ((cm && std::strcmp(cm, "march") == 0) || p->boundary == MGRIT_BC_INFLOW || o->psi_rule == MGRIT_PSI_REDISC ||
+      !fft_coarse_supported(p->nx))
+    return false;
+  return rows >= kFftMinRows || force;
+}
+static mgrit_status setup_coarse_fft(mgrit_handle* h) {
   const int nx = h->nx, rows = h->Nl[h->L - 1];
-  if (rows < kFftMinRows && !force) return MGRIT_OK;
-  const Taps& psi = h->ops.back().taps;
-  const long double two_pi = 6.283185307179586476925286766559005768L;
-  std::vector<long double> cs(nx), sn(nx);  // cos, sin of 2 pi j / nx
-  for (int j = 0; j < nx; ++j) {
-    cs[j] = std::cos(two_pi * j / nx);
-    sn[j] = std::sin(two_pi * j / nx);
-  }
-  std::vector<double> tw(nx), mu(2 * (size_t)nx);
-  for (int k = 0; k < nx / 2; ++k) {
-    tw[2 * k] = (double)cs[k];
-    tw[2 * k + 1] = (double)-sn[k];
-  }
-  for (int k = 0; k < nx; ++k) {
-    long double re = 0.0L, im = 0.0L;
-    for (int t = 0; t < psi.size(); ++t) {
-      long long ik = ((long long)psi.off[t] * k) % nx;
-      if (ik < 0) ik += nx;
-      re += psi.coef[t] * cs[ik];
-      im += psi.coef[t] * sn[ik];
-    }
-    mu[2 * k] = (double)re;
-    mu[2 * k + 1] = (double)im;
-  }
+  if (!wants_coarse_fft(&h->prob, &h->opts, rows)) return MGRIT_OK;
   double *spec = nullptr, *tab = nullptr, *carry = nullptr;
   mgrit_status st;
   const size_t nh = (size_t)nx / 2 + 1;  // independent modes of a real slab
   if ((st = dalloc(h, 2 * (size_t)rows * nh, &spec)) != MGRIT_OK || (st = dalloc(h, 3 * (size_t)nx, &tab)) != MGRIT_OK ||
       (st = dalloc(h, 2 * (size_t)kMaxScanBlocks * nh, &carry)) != MGRIT_OK)
     return st;
-  CUDA_TRY(cudaMemcpyAsync(tab, tw.data(), nx * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-  CUDA_TRY(cudaMemcpyAsync(tab + nx, mu.data(), 2 * (size_t)nx * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  // tables on the device: no host work and no pageable copy behind the stream
+  CUDA_TRY(launch_fft_tables(h->dpsi.back(), nx, tab, tab + nx, h->stream));
   h->cfft = {spec, rows, tab, tab + nx, carry};
   h->fft_coarse = true;
   return MGRIT_OK;
@@ -824,6 +807,7 @@ size_t handle_bytes(const mgrit_problem* prob, const mgrit_opts* opts) {
     if (l < L) d += 2 * arr((N[l] + 1) * nx);
   }
   if (prob->family == MGRIT_SDIRK) d += 4096;  // recurrence tables and the device plan
+  if (prob->boundary == MGRIT_BC_INFLOW) d += 1 << 16;  // boundary-row tables
   return d * sizeof(double);
 }
 

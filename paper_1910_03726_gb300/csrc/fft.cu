@@ -201,11 +201,41 @@ __global__ void __launch_bounds__(512) fft_inverse_kernel(const cplx64* __restri
   }
 }
 
+// tw[k] = exp(-2 pi i k / nx), k < nx/2, and mu_k = sum_t psi_t
+// exp(2 pi i (off_t k mod nx) / nx), k < nx, in FP64 (sincospi keeps the
+// reduced argument exact).
+__global__ void __launch_bounds__(256) fft_tables_kernel(const DevTaps t, int nx, cplx64* __restrict__ tw,
+                                                         cplx64* __restrict__ mu) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nx) return;
+  double s, c;
+  if (k < nx / 2) {
+    sincospi(-2.0 * k / nx, &s, &c);
+    tw[k] = {c, s};
+  }
+  double re = 0.0, im = 0.0;
+  for (int q = 0; q < t.n; ++q) {
+    long long ik = ((long long)t.off[q] * k) % nx;
+    if (ik < 0) ik += nx;
+    sincospi(2.0 * (double)ik / nx, &s, &c);
+    re = fma(t.c64[q], c, re);
+    im = fma(t.c64[q], s, im);
+  }
+  mu[k] = {re, im};
+}
+
 int fft_threads(int nx) { return nx >= 2048 ? 512 : (nx / 4 < 32 ? 32 : nx / 4); }
 
 }  // namespace
 
 bool fft_coarse_supported(int nx) { return nx >= 64 && nx <= 8192 && (nx & (nx - 1)) == 0; }
+
+cudaError_t launch_fft_tables(const DevTaps& psi, int nx, double* tw, double* mu, cudaStream_t s) {
+  if (!fft_coarse_supported(nx)) return cudaErrorInvalidValue;
+  fft_tables_kernel<<<(nx + 255) / 256, 256, 0, s>>>(psi, nx, reinterpret_cast<cplx64*>(tw),
+                                                     reinterpret_cast<cplx64*>(mu));
+  return cudaGetLastError();
+}
 
 cudaError_t launch_coarse_fft(const MarchArgs& a, const CoarseFft& f, cudaStream_t s) {
   if (a.P < 2) return cudaSuccess;

@@ -110,8 +110,9 @@ mgrit_status initial_residual_async(mgrit_handle* h, const double* u0dev);
 mgrit_status load_iterate(mgrit_handle* h, const double* u0, const double* c_init);
 mgrit_status coarse_cycle(mgrit_handle* h, double* c_new);
 // Build a handle; ops != nullptr supplies an already fitted hierarchy.
-// batched: a server's handle (its two-level coarse solves run in the
-// batched march, so no Fourier-space workspace is allocated).
+// batched: a server's handle.  Its two-level coarse solves run in the
+// server's batched march (with about a thousand solves active, one batched
+// launch beats per-solve transforms), so no Fourier-space workspace.
 mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cudaStream_t stream,
                            const std::vector<mg::CoarseOp>* ops, mgrit_handle** out,
                            bool sync = true, bool batched = false);

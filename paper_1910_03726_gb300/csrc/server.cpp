@@ -340,7 +340,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
       r->status = MGRIT_ERR_NOT_CONVERGED;
       r->error = "max_iter reached";
       (*done)[k] = 1;
-    } else if (r->h->L == 2 && !r->h->redisc && !r->h->inflow) {
+    } else if (r->h->L == 2 && !r->h->redisc && !r->h->inflow && !r->h->fft_coarse) {
       by_cluster[r->h->march_cluster].push_back(k);
     }
   }
@@ -364,7 +364,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
   for (int k = 0; k < n; ++k) {
     Request* r = act[k];
     if ((*done)[k]) continue;
-    if (r->h->L > 2 || r->h->redisc || r->h->inflow) {  // the handle's own coarse solve
+    if (r->h->L > 2 || r->h->redisc || r->h->inflow || r->h->fft_coarse) {  // the handle's own coarse solve
       mgrit_status st = coarse_cycle(r->h, r->h->c[1 - r->cur]);
       if (st != MGRIT_OK) {
         r->status = st;

@@ -211,8 +211,7 @@ def test_mixed_modes_reach_sequential_stepping(capi, precision, L):
 def test_server_inflow_requests_match_single_solves(capi, monkeypatch):
     """Periodic and inflow/outflow requests in one server: each result equals
     its single solve (the batched FCF launch carries each solve's boundary
-    rows; the single solves use the cluster march for their coarsest level,
-    as the server does)."""
+    rows; here every coarsest level marches, in the server and alone)."""
     monkeypatch.setenv("MGRIT_COARSE", "march")
     nx, nt, m = 256, 1024, 4
     reqs = [("inflow", 3, 2), ("periodic", 3, 2), ("inflow", 3, 3), ("inflow", 5, 2)]

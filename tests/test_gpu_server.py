@@ -64,10 +64,10 @@ def _wait(capi, srv, ticket, rows, nx, timeout=120.0):
 
 @pytest.mark.parametrize("budget_solves", [100, 3])
 def test_batch_results_equal_alone(capi, budget_solves, monkeypatch):
-    """Each result equals the same solve alone.  The server's two-level
-    coarse solves run in the batched cluster march, so "alone" uses the
-    march too (MGRIT_COARSE=march; equal to 1e-14); single solves by default
-    solve the coarsest level in Fourier space, which agrees to rounding
+    """Each result equals the same solve alone.  The server's coarsest levels
+    march (two-level ones in its batched march), so "alone" marches too
+    (MGRIT_COARSE=march; equal to 1e-14); single solves by default solve a
+    long periodic coarsest level in Fourier space, which agrees to rounding
     (1e-12, the FP64 parity tolerance) with the same iteration count."""
     specs = [_spec(capi, *s) for s in MIX]
     fourier = [_alone(capi, *sp) for sp in specs]
