@@ -262,8 +262,13 @@ cudaError_t launch_coarse_fft(const MarchArgs& a, const CoarseFft& f, cudaStream
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int rows = a.P - 1;
   const int mblocks = (nh + 255) / 256;
-  // enough blocks of rows for about four CTAs per SM, at most kMaxScanBlocks
+  // enough blocks of rows for about four CTAs per SM, but no more than about
+  // sqrt(rows) (pass 2 walks the earlier blocks' ends one by one), at most
+  // kMaxScanBlocks
   int nb = (4 * 152 + mblocks - 1) / mblocks;
+  int sq = 1;
+  while (sq * sq < rows) ++sq;
+  nb = nb > sq ? sq : nb;
   nb = nb < 1 ? 1 : (nb > kMaxScanBlocks ? kMaxScanBlocks : nb);
   nb = nb > rows ? rows : nb;
   const int L = (rows + nb - 1) / nb;
