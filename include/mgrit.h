@@ -214,6 +214,19 @@ typedef void* (*mgrit_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*mgrit_free_fn)(void* ptr, void* stream, void* ctx);
 void mgrit_set_allocator(mgrit_alloc_fn alloc, mgrit_free_fn release, void* ctx);
 
+/* Environment variables read at mgrit_setup (diagnostics and profiling; the
+ * defaults are the tuned behaviour):
+ *   MGRIT_FCF_SHAPE=tile,threads[,collapse]  pin the level-1 FCF launch shape
+ *                     instead of timing the candidates (tile 99 fixed span,
+ *                     98 chunked, 8/4 sliding window, 0 one tap at a time).
+ *   MGRIT_COARSE=march|fft  solve the coarsest level by the cluster march, or
+ *                     in Fourier space (periodic, nx = 2^p, 64..8192) even when
+ *                     it has fewer than 16 steps.  By default a periodic
+ *                     coarsest level with nx = 2^p and at least 16 steps is
+ *                     solved in Fourier space (per-mode recurrences with Psi's
+ *                     symbol between FFTs); servers always march.
+ *   MGRIT_TILE=8|4|0  register tile of the coarse-level stencil kernels. */
+
 /* ---------------------------------------------------------------- host only */
 
 /* Taps of the fine propagator Phi as one circulant stencil (Corollary 1):
