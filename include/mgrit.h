@@ -225,7 +225,9 @@ void mgrit_set_allocator(mgrit_alloc_fn alloc, mgrit_free_fn release, void* ctx)
  *                     coarsest level with nx = 2^p and at least 16 steps is
  *                     solved in Fourier space (per-mode recurrences with Psi's
  *                     symbol between FFTs); servers always march.
- *   MGRIT_TILE=8|4|0  register tile of the coarse-level stencil kernels. */
+ *   MGRIT_TILE=8|4|0  register tile of the stencil kernels whose shape the
+ *                     autotuner does not pick (coarse levels, correction,
+ *                     propagation, sequential stepping). */
 
 /* ---------------------------------------------------------------- host only */
 
