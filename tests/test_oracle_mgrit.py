@@ -285,3 +285,28 @@ def test_fcycle_needs_fewer_iterations_than_vcycle():
         its[cyc], rel = mgrit.solve(lev, U, cycle=cyc)
         assert rel <= 1e-10
     assert its["F"] < its["V"]
+
+
+def test_coarse_system_diagonalises_in_fourier_space():
+    """The coarse solve e_0 = 0, e_n = Psi e_{n-1} + g_n with a circulant Psi
+    (Eq. 5's system) equals, mode by mode, E_n = mu_k E_{n-1} + G_n with mu_k
+    the symbol of Psi (Lemma 1): the library's Fourier-space coarse solve
+    relies on it, on the n_x/2 + 1 modes of real slabs.  Zero right-hand
+    sides ahead of the first nonzero one give exactly zero corrections on
+    both routes."""
+    rng = np.random.default_rng(7)
+    nx, P = 64, 24
+    diag = {o: float(rng.standard_normal()) * 0.3 for o in (-41, -40, -39, -38, -37, 2)}
+    g = rng.standard_normal((P, nx))
+    g[:6] = 0.0
+    e = np.zeros((P, nx))
+    for n in range(1, P):
+        e[n] = stepping.apply_taps(e[n - 1], diag) + g[n]
+    mu = psi.symbol(diag, nx)[: nx // 2 + 1]
+    G = np.fft.rfft(g, axis=1)
+    E = np.zeros_like(G)
+    for n in range(1, P):
+        E[n] = mu * E[n - 1] + G[n]
+    ef = np.fft.irfft(E, n=nx, axis=1)
+    assert np.max(np.abs(ef - e)) <= 1e-13 * np.max(np.abs(e))
+    assert np.all(ef[:6] == 0.0) and np.all(e[:6] == 0.0)
