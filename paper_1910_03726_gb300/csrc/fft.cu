@@ -6,18 +6,20 @@
 //   E_n(k) = mu_k E_{n-1}(k) + G_n(k),   mu_k = sum_i psi_i w^{-ik},
 // one scalar recurrence per mode (mu_k is the symbol of Psi, Lemma 1).  So
 // instead of marching n sequentially over a cluster, the slabs g_1..g_{P-1}
-// are transformed independently (one CTA per slab), the nx recurrences run in
-// parallel (one thread per mode), and the slabs are transformed back, with the
-// march's epilogue (store u_n, or c_n += e_n) fused into the inverse.
+// are transformed independently (one CTA per slab), the recurrences run in
+// parallel over the modes (and, as a chunked scan, over blocks of n), and
+// the slabs are transformed back, with the march's epilogue (store u_n, or
+// c_n += e_n) fused into the inverse.
 //
 // FFT: the slabs are real, so each is transformed as one complex FFT of
 // half length, z_j = x_{2j} + i x_{2j+1} (FP64, in place in shared memory:
 // loaded in bit-reversed order, p-1 radix-2 decimation-in-time stages), and
 // split into the nx/2 + 1 independent modes with
-//   X_k = E_k + w^k O_k,  E_k = (Z_k + conj Z_{h-k}) / 2,
-//   O_k = (Z_k - conj Z_{h-k}) / 2i,  h = nx/2;
-// the other modes are their conjugates (Psi is real) and are never formed.
-// The inverse recombines Z_k = E_k + i O_k from X_k and X_{h-k}.  A slab that
+//   X_k = A_k + w^k B_k,  A_k = (Z_k + conj Z_{h-k}) / 2,
+//   B_k = (Z_k - conj Z_{h-k}) / 2i,  h = nx/2
+// (A, B: the transforms of the even and odd points); the other modes are
+// their conjugates (Psi is real) and are never formed.  The inverse
+// recombines Z_k = A_k + i B_k from X_k and X_{h-k}.  A slab that
 // is identically zero transforms to exact zeros, and a zero spectrum back to
 // exact zeros, so coarse corrections of C-points that are already exact stay
 // exactly zero (as in the march).
@@ -97,39 +99,40 @@ __global__ void __launch_bounds__(512) fft_forward_kernel(const double* __restri
   }
 }
 
-// E_n(k) = mu_k E_{n-1}(k) + G_n(k), n = 1..P-1, in place, as a chunked
-// scan over n so that all SMs work: the rows are split into blocks of L.
+// E_n(k) = mu_k E_{n-1}(k) + G_n(k), n = 1..P-1, for the nm = nx/2 + 1 modes
+// (rows of nm), in place, as a chunked scan over n so that all SMs work: the
+// rows are split into blocks of L.
 // Pass 1 (one thread per mode and block): the block's recurrence from zero;
 // its last value goes to carry[b][k].  Pass 2: the block's incoming value
 // C_b = sum over earlier blocks of mu^(L (b-1-b')) last_b' (a recurrence over
 // b with mu^L), then E_n += mu^(n - n_b + 1) C_b along the block.  A block
 // whose rows and incoming value are zero stays exactly zero.
 __global__ void __launch_bounds__(256) fft_recur_local_kernel(cplx64* __restrict__ spec, const cplx64* __restrict__ mu,
-                                                              cplx64* __restrict__ carry, int nx, int rows, int L) {
+                                                              cplx64* __restrict__ carry, int nm, int rows, int L) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   const int r0 = b * L, r1 = min(rows, r0 + L);
-  if (k >= nx || r0 >= rows) return;
+  if (k >= nm || r0 >= rows) return;
   const cplx64 m = mu[k];
   cplx64 e = {0.0, 0.0};
-  cplx64 nxt = spec[(long long)r0 * nx + k];
+  cplx64 nxt = spec[(long long)r0 * nm + k];
   for (int r = r0; r < r1; ++r) {
     const cplx64 gk = nxt;
-    if (r + 1 < r1) nxt = spec[(long long)(r + 1) * nx + k];
+    if (r + 1 < r1) nxt = spec[(long long)(r + 1) * nm + k];
     const cplx64 me = cmul(m, e);
     e = {me.re + gk.re, me.im + gk.im};
-    spec[(long long)r * nx + k] = e;
+    spec[(long long)r * nm + k] = e;
   }
-  carry[(long long)b * nx + k] = e;
+  carry[(long long)b * nm + k] = e;
 }
 
 __global__ void __launch_bounds__(256) fft_recur_carry_kernel(cplx64* __restrict__ spec, const cplx64* __restrict__ mu,
-                                                              const cplx64* __restrict__ carry, int nx, int rows,
+                                                              const cplx64* __restrict__ carry, int nm, int rows,
                                                               int L) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y + 1;  // block 0 has no incoming value
   const int r0 = b * L, r1 = min(rows, r0 + L);
-  if (k >= nx || r0 >= rows) return;
+  if (k >= nm || r0 >= rows) return;
   const cplx64 m = mu[k];
   cplx64 mL = {1.0, 0.0};  // mu^L by squaring
   {
@@ -142,13 +145,13 @@ __global__ void __launch_bounds__(256) fft_recur_carry_kernel(cplx64* __restrict
   cplx64 c = {0.0, 0.0};  // value entering block b (blocks before b are full)
   for (int bb = 0; bb < b; ++bb) {
     const cplx64 t = cmul(mL, c);
-    const cplx64 last = carry[(long long)bb * nx + k];
+    const cplx64 last = carry[(long long)bb * nm + k];
     c = {t.re + last.re, t.im + last.im};
   }
   if (c.re == 0.0 && c.im == 0.0) return;
   cplx64 p = m;  // mu^(r - r0 + 1)
   for (int r = r0; r < r1; ++r) {
-    cplx64* s = spec + (long long)r * nx + k;
+    cplx64* s = spec + (long long)r * nm + k;
     const cplx64 add = cmul(p, c);
     const cplx64 v = *s;
     *s = {v.re + add.re, v.im + add.im};
