@@ -427,6 +427,19 @@ def hbm_variant(capi, stream, steps=3):
     return out
 
 
+def hbm_summary(h):
+    """The HBM-roofline fraction of the level-1 FCF on its memory-bound
+    instance (from hbm_variant), or None when that variant did not run."""
+    if not isinstance(h, dict) or "mixed_df" not in h:
+        return None
+    d = h["mixed_df"]
+    return {"instance": f"ERK1+U1 nx={h['nx']} nt={h['nt']} m={h['m']}, MIXED_DF (float-float C-points)",
+            "achieved": d["achieved_gbs"], "peak": h["peak_gbs"], "unit": "GB/s", "frac": d["frac_of_hbm_peak"],
+            "bytes_per_launch": h["bytes_per_launch"], "launch_ms": d["fcf_launch_ms"],
+            "peak_source": h["peak_source"],
+            "mixed_fp64_first_pass_frac": h.get("mixed", {}).get("frac_of_hbm_peak")}
+
+
 def exact_cpoints(nx, nt, m, c, device):
     """Exact solution of Eq. 1 (alpha = 1) at the C-points t_j = j m dt for the
     Fourier-field initial condition: u0(x - t) as a product of the per-time
@@ -723,6 +736,7 @@ def main():
             "precision": args.precision,
             "clocks": clk, "cpu_baseline": cpu, "variants": extra,
         }
+        line["hbm_roofline_fcf"] = hbm_summary(extra.get("hbm_bound_erk1_m4"))
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
