@@ -22,7 +22,13 @@ Pins (tests/test_oracle_psi.py): the first column of Phi^m by stepping equals
 the inverse DFT of lambda^m; unit weights give the truncation of Phi^m (Remark
 1); the fitted psi is real to within the flag and its symbol reproduces
 lambda^m at theta = 0; Psi = Phi^m gives one-iteration convergence; the
-thresholded SDIRK operators reproduce Table 6 iteration counts.
+thresholded SDIRK operators reproduce Table 6 iteration counts.  The
+two-level bound (Eq. 4) is pinned to the error propagator E_k of one oracle
+iteration per Fourier mode: sqrt(m) times the induced l1 norm of its C-point
+block equals the bound exactly (the paper's coarse system counts the initial
+C-point as an unknown, so the oracle's problem with n_t + m steps is compared);
+||E_k||_2 never exceeds it; and with the ideal-interpolation factor
+sqrt(sum_{i<m} |lambda_k|^{2i} / m) it is attained as n_t/m grows (Section 3.1).
 
 Readings (where the paper is silent):
 * ERK pattern ("contiguous subset of the largest entries of Phi^m, widened
