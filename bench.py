@@ -94,9 +94,13 @@ class ClockSampler:
 
 # --------------------------------------------------------- oracle (CPU)
 
-def oracle_sample(nt_sample):
-    """Oracle FCF-MGRIT on the same scheme/CFL/u0/hierarchy shape, first
-    nt_sample steps of the horizon; returns (DOF/s, seconds, iterations)."""
+CPU_NT_SAMPLE = 1024     # the oracle's sample of the horizon (the first 1/16)
+
+
+def oracle_sample(nt_sample=CPU_NT_SAMPLE, repeats=1):
+    """Oracle FCF-MGRIT on the headline's scheme, CFL, u0, tolerance and
+    hierarchy shape over the first nt_sample steps of the horizon (one
+    thread); returns (DOF/s, seconds, iterations).  Psi setup excluded."""
     from oracle import mgrit as omg
     from oracle import psi as opsi
     from oracle import stepping
@@ -104,27 +108,64 @@ def oracle_sample(nt_sample):
     st = stepping.FineStep("ERK", P, CFL, NX)
     ops = opsi.build_hierarchy("ERK", P, CFL, NX, nt_sample, M, LEVELS, rule="auto")
     lev = omg.make_levels(st, M, [o.diag for o in ops])
-    U = omg.zero_iterate(u0, nt_sample)
-    t0 = time.perf_counter()
-    it, rel = omg.solve(lev, U, tol=TOL)
-    dt = time.perf_counter() - t0
-    return NX * nt_sample / dt, dt, it
+    dt, it = 0.0, 0
+    for _ in range(repeats):
+        U = omg.zero_iterate(u0, nt_sample)
+        t0 = time.perf_counter()
+        it, _ = omg.solve(lev, U, tol=TOL)
+        dt += time.perf_counter() - t0
+    return NX * nt_sample * repeats / dt, dt, it
+
+
+def _oracle_worker(args):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    if args[0] == 0:                          # warm-up: imports only
+        from oracle import mgrit  # noqa: F401
+        return None
+    return oracle_sample(*args)
+
+
+def oracle_all_cores(nt_sample=CPU_NT_SAMPLE, repeats=2):
+    """The same oracle solves run concurrently, one process (one thread) per
+    host core (spawned, so no CUDA state is inherited): aggregate DOF/s of
+    the host.  Returns (DOF/s, processes, wall seconds)."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(n) as pool:
+            pool.map(_oracle_worker, [(0, 1)] * n)             # imports outside the timing
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_worker, [(nt_sample, repeats)] * n)
+            wall = time.perf_counter() - t0
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return NX * nt_sample * repeats * len(res) / wall, n, wall
+
+
+def cpu_sample_text(nt_sample=CPU_NT_SAMPLE):
+    return (f"oracle (numpy FP64) V-cycle L=4 m=8 FCF-MGRIT on nx=4096, nt={nt_sample} (the first "
+            f"{nt_sample}/16384 of the horizon), same scheme, CFL, u0 and tol; Psi setup excluded")
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step one single-thread oracle
+    solve of the CPU sample (the sample cpu_baseline's one-thread figure
+    uses)."""
     if rank != 0:
         return
-    nt_sample = 512
     for _ in range(args.warmup):
-        oracle_sample(nt_sample)
-    vals, secs = [], []
-    for _ in range(args.steps):
-        v, s, it = oracle_sample(nt_sample)
-        vals.append(v)
-        secs.append(s)
-    value = NX * nt_sample * len(secs) / sum(secs)
-    sample = (f"oracle (numpy, 1 thread) V-cycle L=4 m=8 FCF-MGRIT on nx=4096, nt={nt_sample} (first "
-              f"{nt_sample}/16384 of the horizon), same scheme, CFL, u0 and tol; Psi setup excluded")
+        oracle_sample()
+    secs = [oracle_sample()[1] for _ in range(args.steps)]
+    value = NX * CPU_NT_SAMPLE * len(secs) / sum(secs)
+    sample = cpu_sample_text() + "; one thread"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -132,6 +173,21 @@ def run_reference(args, rank, world):
             "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def oracle_sequential_cpoints():
+    """The plain definition at full size: the oracle's sequential stepping
+    u^{n+1} = Phi u^n of the headline problem (Eq. 3), at the C-points."""
+    from oracle import stepping
+    st = stepping.FineStep("ERK", P, CFL, NX)
+    u = workloads.fourier_field(NX)
+    out = np.empty((NT // M + 1, NX))
+    out[0] = u
+    for n in range(1, NT + 1):
+        u = st(u)
+        if n % M == 0:
+            out[n // M] = u
+    return out
 
 
 # ------------------------------------------------------------- GPU arm
@@ -520,6 +576,38 @@ def replicas_value(world, dof_per_step, steps, max_total_ms):
     return world * dof_per_step * steps / (max_total_ms * 1e-3)
 
 
+def pct(xs, q):
+    return float(np.percentile(np.asarray(xs), q)) if len(xs) else None
+
+
+def compact_summary(extra):
+    """The variants' headline figures, small enough for the bench line."""
+    out = {}
+    g = extra.get("gpu_sequential_fp64")
+    if g:
+        out["gpu_sequential_dof_per_s"] = g["dof_per_s"]
+        out["speedup_vs_gpu_sequential"] = extra.get("speedup_vs_gpu_sequential")
+    for key, name in (("fp64_vcycle_L4_m8", "plain_fp64_mgrit_dof_per_s"),
+                      ("mixed_df_vcycle_L4_m8", "mixed_df_dof_per_s")):
+        if key in extra:
+            out[name] = extra[key]["dof_per_s"]
+    b = extra.get("batch_uneven")
+    if b:
+        out["batch_4096"] = {"dof_per_s": b["dof_per_s"], "plain_fp64_alone": b["plain_fp64_alone_dof_per_s"],
+                             "gpu_seq_alone": b["gpu_sequential_dof_per_s"], "p50_ms": b["latency_ms"]["p50"],
+                             "p99_ms": b["latency_ms"]["p99"], "converged": b["converged"]}
+    sv = extra.get("serving_poisson")
+    if sv:
+        out["serving"] = {k: [round(v["latency_ms"]["p50"], 1), round(v["latency_ms"]["p99"], 1),
+                              float("%.4g" % v["dof_per_s"])] for k, v in sv.items()}
+        out["serving_fields"] = "rate: [p50 ms, p99 ms, DOF/s]"
+    sd = extra.get("sdirk3_u5_8192")
+    if sd:
+        out["sdirk3_u5_8192_ms"] = {"mixed": sd["mixed"]["ms"], "fp64": sd["fp64"]["ms"],
+                                    "gpu_seq": sd["gpu_sequential_fp64"]["ms"]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -536,6 +624,8 @@ def main():
                     help="run just this variant and print its JSON (no headline line)")
     ap.add_argument("--host-loop", action="store_true",
                     help="with --only sdirk: drive cycles from the host (kernels visible to ncu)")
+    ap.add_argument("--variants-out", default=os.path.join(ROOT, "gpurun_out", "bench_variants.json"),
+                    help="file for the full variant record (written when its folder exists)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = dist_env()
@@ -579,41 +669,51 @@ def main():
                                     flags=flags, max_iter=100, cycle=cycle, relax=relax)
         return capi.mgrit_setup(prob, o, stream=sp)
 
-    def timed_solves(h, K, W, collect=False):
+    def timed_solves(h, K, W, queued=True):
+        """K solves of u0, each bracketed by CUDA events on the solve stream
+        with the L2 flushed before it.  Queued: all K are enqueued
+        (mgrit_solve_async) before the first wait, so host-side delays cannot
+        leave the GPU idle inside a bracket; otherwise one mgrit_solve at a
+        time (the host loop of the kernel-timing pass)."""
         for _ in range(W):
             capi.mgrit_solve(h, u0, out)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        lat, results = [], []
         e0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
         e1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-        for k in range(K):
-            flush.zero_()                       # evict L2 between steps
-            e0[k].record(stream)
-            r, _ = capi.mgrit_solve(h, u0, out)
-            e1[k].record(stream)
-            results.append(r)
+        results = []
+        for k0 in range(0, K, capi.MAX_INFLIGHT):
+            ks = range(k0, min(K, k0 + capi.MAX_INFLIGHT))
+            for k in ks:
+                flush.zero_()                       # evict L2 between steps
+                e0[k].record(stream)
+                if queued:
+                    capi.mgrit_solve_async(h, u0, out)
+                else:
+                    results.append(capi.mgrit_solve(h, u0, out)[0])
+                e1[k].record(stream)
+            if queued:
+                results += [capi.mgrit_solve_wait(h)[0] for _ in ks]
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         lat = [a.elapsed_time(b) for a, b in zip(e0, e1)]
-        total = replica_max(sum(lat), world)
-        return lat, total, results
+        return lat, replica_max(sum(lat), world), results
 
     clocks = ClockSampler(local)
     head_prec = {"fp64": capi.PREC_FP64, "mixed": capi.PREC_MIXED, "mixed_df": capi.PREC_MIXED_DF}[args.precision]
-    # ---- headline: V-cycle L=4, m=8, whole solve as one CUDA-graph launch
+    # ---- headline: V-cycle L=4, m=8, each solve one CUDA-graph launch, queued
     h = make(LEVELS, M, head_prec)
     clocks.start()
     lat, total, results = timed_solves(h, args.steps, args.warmup)
     clk = clocks.stop()
     res0 = results[-1]
-    graph_res = res0
     value = replicas_value(world, NX * NT, args.steps, total)
     launches = sum(r.launches for r in results)
+    head_cpoints = out.cpu().numpy()
     # ---- e2e through the C ABI with host buffers (u0 in, C-points out)
     u0_host = np.ascontiguousarray(u0_np)
     out_host = np.empty((N1 + 1, NX))
@@ -631,7 +731,7 @@ def main():
     # ---- roofline pass: the same solves driven cycle by cycle from the host
     # with CUDA events around every kernel (identical kernels and shapes)
     hp = make(LEVELS, M, head_prec, flags=capi.FLAG_TIME_KERNELS)
-    p_lat, p_total, p_results = timed_solves(hp, args.steps, args.warmup)
+    p_lat, p_total, p_results = timed_solves(hp, args.steps, args.warmup, queued=False)
     capi.mgrit_destroy(hp)
     fcf_ms = sum(r.kernel_ms[0] for r in p_results)
     fcf_n = sum(r.kernel_count[0] for r in p_results)
@@ -650,9 +750,10 @@ def main():
     tot_ms = max(1e-9, sum(sum(r.kernel_ms) for r in p_results))
     kernel_share = {capi.KERNEL_KINDS[i]: round(sum(r.kernel_ms[i] for r in p_results) / tot_ms, 4)
                     for i in range(capi.K_KINDS)}
-    extra = {}
-    extra["host_loop_with_kernel_events"] = {"dof_per_s": world * NX * NT * args.steps / (p_total * 1e-3),
-                                             "ms": p_total / args.steps}
+    extra = {"kernel_time_share": kernel_share,
+             "host_loop_with_kernel_events": {"dof_per_s": world * NX * NT * args.steps / (p_total * 1e-3),
+                                              "ms": p_total / args.steps},
+             "latency_ms_all": [round(x, 4) for x in lat]}
     if not args.no_variants:
         ks = max(3, args.steps // 2)
         for name, (lv, m, prec, cyc, rlx) in {
@@ -685,10 +786,9 @@ def main():
             sl.append(a.elapsed_time(b))
         seq_ms = statistics.median(sl)
         extra["gpu_sequential_fp64"] = {"dof_per_s": NX * NT / (seq_ms * 1e-3), "ms": seq_ms}
-        extra["speedup_vs_gpu_sequential"] = (seq_ms / statistics.median(lat))
-        # accuracy of the headline result against FP64 sequential stepping (C-points)
-        err = float(torch.linalg.norm(out - fin) / torch.linalg.norm(fin))
-        extra["rel_l2_vs_fp64_sequential"] = err
+        extra["speedup_vs_gpu_sequential"] = seq_ms / statistics.median(lat)
+        extra["rel_l2_vs_gpu_fp64_sequential"] = float(np.linalg.norm(head_cpoints - fin.cpu().numpy())
+                                                       / np.linalg.norm(fin.cpu().numpy()))
         capi.mgrit_destroy(hs)
         extra["sdirk3_u5_8192"] = sdirk_variant(capi, sp, 3)
         extra["paper_parallel_configs"] = paper_parallel_variant(capi, sp)
@@ -703,40 +803,50 @@ def main():
     line = None
     if rank == 0:
         cpu = None
+        err_oracle = None
         if not args.no_cpu and world == 1:
-            v, s, it = oracle_sample(4096)
-            cpu = {"value": v, "unit": "DOF/s", "cores": 1, "kind": "oracle",
-                   "sample": f"oracle (numpy, 1 thread) V-cycle L=4 m=8 FCF-MGRIT, nx=4096, nt=4096 (first "
-                             f"1/4 of the horizon), same scheme/CFL/u0/tol, {s:.1f} s, {it} iterations"}
-        lat_sorted = sorted(lat)
+            # the headline result against the plain definition at full size
+            ref = oracle_sequential_cpoints()
+            err_oracle = float(np.linalg.norm(head_cpoints - ref) / np.linalg.norm(ref))
+            v1, s1, it1 = oracle_sample(repeats=3)
+            va, nproc, wall = oracle_all_cores()
+            cpu = {"value": va, "unit": "DOF/s", "cores": nproc, "kind": "oracle",
+                   "sample": cpu_sample_text() + f"; {nproc} concurrent single-thread solves ({nproc} host "
+                             f"cores), {wall:.1f} s", "one_thread_value": v1, "iterations": it1}
+        hb = hbm_summary(extra.get("hbm_bound_erk1_m4"))
         line = {
             "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "fp64+fp32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nx": NX, "nt": NT, "levels": LEVELS, "m": M,
-                       "parallelism": f"replicas x{world}", "l2": "flushed between steps (256 MiB write)"},
-            "latency_ms": {"p50": float(np.percentile(lat_sorted, 50)), "p99": float(np.percentile(lat_sorted, 99))},
-            "iterations": res0.iterations, "rel_residual": res0.rel_residual,
+            "gpu_launches": launches,
+            "config": {"workload": "ERK3+U3 4096x16384 c=0.85*1.62589, Fourier-field u0 (seed 2), zero iterate, "
+                                   "V-cycle L=4 m=8, auto-width LSQ Psi, FP32 F-relax + FP64 residual/coarse/test, "
+                                   "tol 1e-10", "parallelism": f"replicas x{world}",
+                       "l2": "flushed before each step (256 MiB write)",
+                       "timing": "CUDA events per solve; solves queued with mgrit_solve_async"},
             "e2e": {"value": e2e_value, "unit": "DOF/s", "h2d_bytes_per_step": NX * 8,
                     "d2h_bytes_per_step": (N1 + 1) * NX * 8},
-            "gpu_launches": launches,
+            "clocks": clk, "cpu_baseline": cpu,
             "roofline": {"bound": "alu", "kernel": "fcf_kernel (level-1 FCF + fused residual)",
-                         "measured": "CUDA events around every level-1 FCF launch, second timed pass of the "
-                                     "same K solves (host-driven cycles, identical kernels and launch shapes); "
-                                     "FP64 flops of the launches' nonzero intervals / their total time",
                          "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
                          "traffic": fcf_traffic_from_profile(),
-                         "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (FP64 FMA pipe)",
-                         "flops_per_launch_fp64": flops64, "launch_ms": fcf_avg_s * 1e3},
-            "kernel_time_share": kernel_share,
-            "autotuned_fcf": {"tile": res0.fine_tile, "threads": res0.fine_threads,
-                              "collapsed_phi_m": bool(res0.fine_collapsed)},
-            "one_graph_per_solve": bool(graph_res.graph),
-            "precision": args.precision,
-            "clocks": clk, "cpu_baseline": cpu, "variants": extra,
+                         "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+                         "launch_ms": fcf_avg_s * 1e3},
+            "hbm_roofline_fcf": ({"frac": hb["frac"], "achieved": hb["achieved"], "peak": hb["peak"],
+                                  "unit": "GB/s", "instance": "ERK1+U1 4096x16384 m=4 MIXED_DF",
+                                  "mixed_frac": hb["mixed_fp64_first_pass_frac"]} if hb else None),
+            "iterations": res0.iterations, "rel_residual": res0.rel_residual,
+            "err_vs_oracle_sequential": err_oracle,
+            "latency_ms": {"min": min(lat), "p50": pct(lat, 50), "p99": pct(lat, 99), "max": max(lat)},
+            "summary": compact_summary(extra),
         }
-        line["hbm_roofline_fcf"] = hbm_summary(extra.get("hbm_bound_erk1_m4"))
+        try:
+            if os.path.isdir(os.path.dirname(args.variants_out)):
+                with open(args.variants_out, "w") as f:
+                    json.dump({"line": line, "variants": extra}, f, indent=1)
+        except OSError:
+            pass
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

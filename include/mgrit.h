@@ -26,7 +26,8 @@
  *     error, mgrit_last_error() returns a message for the calling thread.
  *   - Every call that touches the GPU runs on the CUDA stream given at
  *     creation (NULL = the legacy default stream) and returns after that
- *     stream has finished the call's work.
+ *     stream has finished the call's work, except mgrit_solve_async and
+ *     mgrit_fcf_residual_static, which only enqueue it.
  */
 #ifndef MGRIT_GB300_H
 #define MGRIT_GB300_H
@@ -38,7 +39,7 @@
 extern "C" {
 #endif
 
-#define MGRIT_ABI_VERSION 4
+#define MGRIT_ABI_VERSION 5
 #define MGRIT_MAX_LEVELS 8
 #define MGRIT_MAX_HISTORY 128
 #define MGRIT_MAX_TAPS 256
@@ -103,6 +104,18 @@ enum {
 
 enum { MGRIT_OUT_FINAL = 0, MGRIT_OUT_CPOINTS = 1, MGRIT_OUT_FULL = 2 };
 
+/* Initial space-time iterate at t > 0 (Section 2.2; u^0 is always the initial
+ * condition):
+ *  ZERO    every point 0 (the relative tolerance then refers to ||Phi u^0||).
+ *  RANDOM  every point, C and F, drawn uniform on [0, 1) as the paper's tests
+ *          do: point i of time level n takes the first two 32-bit words of
+ *          Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with counter
+ *          (i, n, 0, 0) and key (seed mod 2^32, seed / 2^32), joined as
+ *          ((w0 >> 5) 2^26 + (w1 >> 6)) 2^-53.  The relative tolerance
+ *          refers to the full space-time residual of this iterate, F-points
+ *          included, computed on the device. */
+enum { MGRIT_INIT_ZERO = 0, MGRIT_INIT_RANDOM = 1 };
+
 /* Cycle below level 1 (Section 4.4, Section 5): V-cycle, or F-cycle (the
  * coarse error equation of each level is solved by an F-cycle from zero
  * followed by a V-cycle from its result; one exact solve on the level above
@@ -150,6 +163,13 @@ typedef struct mgrit_problem {
   int32_t upwind_order;  /* U1..U5 (Section 2.1)                                   */
   int32_t boundary;      /* MGRIT_BC_* (0 = periodic)                              */
   double cfl;            /* c = alpha dt / dx (> 0)                                */
+  /* Eq. 1's wave speed and domain.  The discrete operators depend on c only
+   * (dt L = c times the U_p stencil), so these fix the physical spacings
+   * dx = (xmax - xmin) / nx and dt = c dx / alpha that mgrit_result reports.
+   * alpha > 0 (a wave moving right, the upwind direction of U_p); 0 selects
+   * 1.  xmin < xmax; xmin = xmax = 0 selects [-1, 1]. */
+  double alpha;
+  double xmin, xmax;
 } mgrit_problem;
 
 typedef struct mgrit_opts {
@@ -164,10 +184,11 @@ typedef struct mgrit_opts {
   int32_t flags;         /* MGRIT_FLAG_* bits                                      */
   int32_t cycle;         /* MGRIT_CYCLE_*                                          */
   int32_t relax;         /* MGRIT_RELAX_*                                          */
-  int32_t reserved;
+  int32_t init_guess;    /* MGRIT_INIT_* (mgrit_solve and mgrit_solve_async)       */
   double tol;            /* stop when ||r|| <= tol ||r^(0)|| (Section 2.2)         */
   double psi_eta;        /* threshold eta_tol; <= 0 = paper's table (Section 4.6)  */
   double psi_rho;        /* bound target of MGRIT_PSI_AUTO (default 0.15)          */
+  uint64_t seed;         /* key of the MGRIT_INIT_RANDOM draws                     */
   /* MGRIT_PSI_USER: coarse level l = 2..levels has psi_user_nnz[l-2] taps; the
    * offsets (diagonal index i: (Psi v)_r = sum_i psi_i v_{r+i}) and
    * coefficients of all levels are concatenated in level order. */
@@ -196,6 +217,7 @@ typedef struct mgrit_result {
   int32_t reserved;
   int32_t kernel_count[MGRIT_K_KINDS];  /* launches per kind                         */
   double kernel_ms[MGRIT_K_KINDS];      /* device time per kind (FLAG_TIME_KERNELS)  */
+  double dx, dt;         /* physical spacings of the problem (alpha, xmin, xmax)    */
 } mgrit_result;
 
 typedef struct mgrit_handle mgrit_handle;
@@ -203,8 +225,7 @@ typedef struct mgrit_server mgrit_server;
 
 /* Fill *o with the defaults: m 8, levels 2, max_iter 100, FP64, PSI_AUTO,
  * halfwidth 3, OUT_CPOINTS, min_coarse 2, flags 0, V-cycle, FCF-relaxation,
- * tol 1e-10, eta <= 0,
- * rho 0.15. */
+ * INIT_ZERO, seed 0, tol 1e-10, eta <= 0, rho 0.15. */
 void mgrit_opts_default(mgrit_opts* o);
 
 /* Optional device allocator used for all later allocations (NULL, NULL
@@ -262,12 +283,35 @@ mgrit_status mgrit_psi_plan(const mgrit_problem* prob, const mgrit_opts* opts, i
 mgrit_status mgrit_setup(const mgrit_problem* prob, const mgrit_opts* opts, void* stream,
                          mgrit_handle** out);
 
-/* Solve from u0 (nx values, host or device) with a zero initial iterate at
- * t > 0.  out (host or device) receives, per opts.output: FINAL the nx
- * values at t = T; CPOINTS (nt/m + 1) * nx C-point values; FULL (nt + 1) * nx
- * values (F-points recomputed by a final F-relaxation, ideal interpolation).
- * out may be NULL.  res may be NULL. */
+/* Solve from u0 (nx values, host or device) with the initial iterate at
+ * t > 0 that opts.init_guess names (Section 2.2).  out (host or device)
+ * receives, per opts.output: FINAL the nx values at t = T; CPOINTS
+ * (nt/m + 1) * nx C-point values; FULL (nt + 1) * nx values (F-points
+ * recomputed by a final F-relaxation, ideal interpolation).  out may be
+ * NULL.  res may be NULL. */
 mgrit_status mgrit_solve(mgrit_handle* h, const double* u0, double* out, mgrit_result* res);
+
+/* The same solve, only enqueued on the handle's stream (Section 2.2's
+ * iteration as one CUDA-graph launch with the stopping test on the device):
+ * the call returns without waiting, so a caller can queue several solves
+ * back to back and the GPU runs them without host round trips in between.
+ * out: device memory or NULL (FINAL or CPOINTS output; FULL is
+ * MGRIT_ERR_UNSUPPORTED, as are MGRIT_FLAG_HOST_LOOP and
+ * MGRIT_FLAG_TIME_KERNELS).  u0 (host or device) and out must stay valid,
+ * and u0 unchanged, until mgrit_solve_wait has returned for this solve.  At
+ * most MGRIT_MAX_INFLIGHT solves may be outstanding on one handle
+ * (MGRIT_ERR_INVALID beyond).  They run in call order on the stream and share
+ * the handle's device state, so each one's output is final only when its
+ * mgrit_solve_wait returns. */
+#define MGRIT_MAX_INFLIGHT 64
+mgrit_status mgrit_solve_async(mgrit_handle* h, const double* u0, double* out);
+
+/* Wait for the oldest outstanding mgrit_solve_async of the handle and return
+ * its status (MGRIT_OK, MGRIT_ERR_NOT_CONVERGED or MGRIT_ERR_DIVERGED, as
+ * mgrit_solve); res (may be NULL) receives its result, with solve_s the time
+ * from the enqueue call to the end of the wait.  MGRIT_ERR_INVALID when none
+ * is outstanding. */
+mgrit_status mgrit_solve_wait(mgrit_handle* h, mgrit_result* res);
 
 /* As mgrit_solve, from a given initial iterate (a warm start, or the
  * paper's random initial iterate of Section 2.2): c_init holds its C-points,

@@ -258,14 +258,16 @@ def auto_width_fit(lam, col_m, m, nt, w0: int, rho_target=DEFAULT_RHO_TARGET, wm
 
 def build_hierarchy(family: str, p: int, c: float, nx: int, nt: int, m: int, levels: int,
                     rule: str = "auto", halfwidth: int = 3, eta=None,
-                    rho_target: float = DEFAULT_RHO_TARGET):
+                    rho_target: float = DEFAULT_RHO_TARGET, q: int | None = None):
     """Coarse operators Phi_2..Phi_L (Section 4.4: each level fits Phi_l^m).
 
     rule: 'halfwidth' | 'auto' | 'threshold' | 'ideal'.  Returns a list of
     CoarseOp (one per coarse level).  For 'ideal' the list holds the dense
-    first-column diagonals of Phi^m (two levels only)."""
-    step = stepping.FineStep(family, p, c, nx)
-    lam = schemes.phi_symbol(family, p, c, nx)
+    first-column diagonals of Phi^m (two levels only).  q: order of the
+    upwind stencil (default p); the threshold rule keeps the eta_tol row of
+    the Runge-Kutta order p."""
+    step = stepping.FineStep(family, p, c, nx, q=q)
+    lam = schemes.phi_symbol(family, p, c, nx, q=q)
     if family == "ERK":
         nnz_fine = len(phi_m_column_nonzeros(step, nx))
     ops = []

@@ -135,11 +135,12 @@ def thetas(nx: int) -> np.ndarray:
     return 2.0 * np.pi * np.arange(nx) / nx
 
 
-def phi_symbol(family: str, p: int, c: float, nx: int) -> np.ndarray:
+def phi_symbol(family: str, p: int, c: float, nx: int, q: int | None = None) -> np.ndarray:
     """Eigenvalues lambda_k of the fine propagator Phi (Lemma 1, Corollary 1):
     lambda_k = R(z_k), z_k the eigenvalue of dt*L on mode theta_k.  Ordered as
-    numpy's DFT of the first column of Phi."""
-    z = stencil_symbol(dtL_taps(p, c), thetas(nx))
+    numpy's DFT of the first column of Phi.  q: order of the upwind stencil
+    (default p, the paper's pairing)."""
+    z = stencil_symbol(dtL_taps(q or p, c), thetas(nx))
     return stability(family, p, z)
 
 

@@ -2,8 +2,10 @@
 
 Every function here has the name of the C entry point it calls.  Arrays may
 be numpy arrays (host) or torch tensors (host or CUDA); the library detects
-device pointers itself.  PyTorch supplies the CUDA stream and, through
-``use_torch_allocator``, the device memory of the library's state.
+device pointers itself.  PyTorch supplies the CUDA stream and, when a CUDA
+device is present, the device memory of the library's state: importing this
+module routes the library's allocations through PyTorch's caching allocator
+(``use_default_allocator`` switches back to the library's cudaMallocAsync).
 
 There is no fallback: if ``libmgrit_gb300.so`` is missing the import fails
 and says how to build it.
@@ -29,6 +31,8 @@ PSI_AUTO, PSI_HALFWIDTH, PSI_THRESHOLD, PSI_USER, PSI_IDEAL, PSI_REDISC = 0, 1, 
 OUT_FINAL, OUT_CPOINTS, OUT_FULL = 0, 1, 2
 CYCLE_V, CYCLE_F = 0, 1
 RELAX_FCF, RELAX_F = 0, 1
+INIT_ZERO, INIT_RANDOM = 0, 1
+MAX_INFLIGHT = 64
 MAX_HISTORY = 128
 MAX_LEVELS = 8
 FLAG_TIME_KERNELS = 1
@@ -39,7 +43,7 @@ KERNEL_KINDS = ["fcf", "fcf_coarse", "march", "correct", "norm", "add", "propaga
 K_KINDS = len(KERNEL_KINDS)
 
 EXPORTED = ["mgrit_opts_default", "mgrit_set_allocator", "mgrit_phi_taps", "mgrit_phi_boundary", "mgrit_psi_plan",
-            "mgrit_setup", "mgrit_solve", "mgrit_solve_from", "mgrit_relax", "mgrit_sequential", "mgrit_propagate",
+            "mgrit_setup", "mgrit_solve", "mgrit_solve_async", "mgrit_solve_wait", "mgrit_solve_from", "mgrit_relax", "mgrit_sequential", "mgrit_propagate",
             "mgrit_psi_info",
             "mgrit_device_bytes", "mgrit_destroy", "mgrit_server_create", "mgrit_submit",
             "mgrit_poll", "mgrit_server_stats", "mgrit_server_destroy", "mgrit_fcf_residual_static", "mgrit_last_error",
@@ -48,15 +52,16 @@ EXPORTED = ["mgrit_opts_default", "mgrit_set_allocator", "mgrit_phi_taps", "mgri
 
 class MgritProblem(C.Structure):
     _fields_ = [("nx", C.c_int32), ("nt", C.c_int32), ("family", C.c_int32), ("rk_order", C.c_int32),
-                ("upwind_order", C.c_int32), ("boundary", C.c_int32), ("cfl", C.c_double)]
+                ("upwind_order", C.c_int32), ("boundary", C.c_int32), ("cfl", C.c_double),
+                ("alpha", C.c_double), ("xmin", C.c_double), ("xmax", C.c_double)]
 
 
 class MgritOpts(C.Structure):
     _fields_ = [("m", C.c_int32), ("levels", C.c_int32), ("max_iter", C.c_int32), ("precision", C.c_int32),
                 ("psi_rule", C.c_int32), ("psi_halfwidth", C.c_int32), ("output", C.c_int32),
                 ("min_coarse", C.c_int32), ("flags", C.c_int32), ("cycle", C.c_int32), ("relax", C.c_int32),
-                ("reserved", C.c_int32), ("tol", C.c_double), ("psi_eta", C.c_double),
-                ("psi_rho", C.c_double), ("psi_user_nnz", C.POINTER(C.c_int32)),
+                ("init_guess", C.c_int32), ("tol", C.c_double), ("psi_eta", C.c_double),
+                ("psi_rho", C.c_double), ("seed", C.c_uint64), ("psi_user_nnz", C.POINTER(C.c_int32)),
                 ("psi_user_offsets", C.POINTER(C.c_int32)), ("psi_user_coeffs", C.POINTER(C.c_double))]
 
 
@@ -68,7 +73,7 @@ class MgritResult(C.Structure):
                 ("launches", C.c_int32), ("fine_tile", C.c_int32), ("fine_threads", C.c_int32),
                 ("graph", C.c_int32), ("fine_collapsed", C.c_int32), ("reserved", C.c_int32),
                 ("kernel_count", C.c_int32 * K_KINDS),
-                ("kernel_ms", C.c_double * K_KINDS)]
+                ("kernel_ms", C.c_double * K_KINDS), ("dx", C.c_double), ("dt", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("history", "kernel_count", "kernel_ms")}
@@ -121,6 +126,8 @@ _sig("mgrit_phi_boundary", _i32, _P(MgritProblem), _i32, _i32, _P(_i32), _P(_f64
 _sig("mgrit_psi_plan", _i32, _P(MgritProblem), _P(MgritOpts), _i32, _P(_i32), _P(_i32), _P(_f64), _P(_f64))
 _sig("mgrit_setup", _i32, _P(MgritProblem), _P(MgritOpts), _vp, _P(_vp))
 _sig("mgrit_solve", _i32, _vp, _vp, _vp, _P(MgritResult))
+_sig("mgrit_solve_async", _i32, _vp, _vp, _vp)
+_sig("mgrit_solve_wait", _i32, _vp, _P(MgritResult))
 _sig("mgrit_solve_from", _i32, _vp, _vp, _f64, _vp, _P(MgritResult))
 _sig("mgrit_relax", _i32, _vp, _i32, _P(_f64))
 _sig("mgrit_sequential", _i32, _vp, _vp, _vp, _P(_f64))
@@ -168,10 +175,12 @@ def _ptr(x):
 
 # ------------------------------------------------------------------ helpers
 
-def problem(nx, nt, family="ERK", rk_order=1, upwind_order=None, cfl=0.85, boundary=BC_PERIODIC):
+def problem(nx, nt, family="ERK", rk_order=1, upwind_order=None, cfl=0.85, boundary=BC_PERIODIC, alpha=1.0,
+            xmin=-1.0, xmax=1.0):
     fam = ERK if family in ("ERK", ERK) else SDIRK
     bc = BC_INFLOW if boundary in ("inflow", BC_INFLOW) else BC_PERIODIC
-    return MgritProblem(nx, nt, fam, rk_order, upwind_order or rk_order, bc, float(cfl))
+    return MgritProblem(nx, nt, fam, rk_order, upwind_order or rk_order, bc, float(cfl), float(alpha),
+                        float(xmin), float(xmax))
 
 
 def mgrit_opts_default(**overrides):
@@ -268,6 +277,19 @@ def mgrit_solve(h, u0, out=None, allow_not_converged=False):
     return r, st
 
 
+def mgrit_solve_async(h, u0, out=None):
+    """Enqueue a solve (out: device tensor or None); finish it with mgrit_solve_wait."""
+    _check(_lib.mgrit_solve_async(h, _ptr(u0), _ptr(out)))
+
+
+def mgrit_solve_wait(h, allow_not_converged=False):
+    """Wait for the oldest queued solve of h; returns (result, status)."""
+    r = MgritResult()
+    allow = (MGRIT_OK, -4) if allow_not_converged else (MGRIT_OK,)
+    st = _check(_lib.mgrit_solve_wait(h, C.byref(r)), allow)
+    return r, st
+
+
 def mgrit_solve_from(h, c_init, r0_norm=0.0, out=None, allow_not_converged=False):
     r = MgritResult()
     allow = (MGRIT_OK, -4) if allow_not_converged else (MGRIT_OK,)
@@ -355,12 +377,16 @@ _KEEP = []
 
 def use_torch_allocator():
     """Route the library's device allocations through PyTorch's caching
-    allocator on the caller's stream."""
+    allocator on the stream of the allocating call (the default once this
+    module is imported on a machine with a CUDA device).  The device is the
+    calling thread's current one, so a server's worker thread allocates on
+    the server's device."""
     import torch
 
     def _alloc(nbytes, stream, ctx):
         try:
-            return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0)))
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), device=torch.cuda.current_device(),
+                                                          stream=int(stream or 0)))
         except Exception:  # noqa: BLE001  (the C side reports OOM)
             return None
 
@@ -375,3 +401,15 @@ def use_torch_allocator():
 def use_default_allocator():
     _lib.mgrit_set_allocator(ALLOC_FN(), FREE_FN(), None)
     _KEEP[:] = []
+
+
+def _torch_memory_by_default():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            use_torch_allocator()
+    except ImportError:
+        pass
+
+
+_torch_memory_by_default()

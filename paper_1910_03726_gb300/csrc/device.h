@@ -114,6 +114,8 @@ cudaError_t launch_fft_tables(const DevTaps& psi, int nx, double* tw, double* mu
 // Same result as launch_march with a.init == nullptr and periodic T (three
 // launches: forward transforms, recurrences, inverse transforms + epilogue).
 cudaError_t launch_coarse_fft(const MarchArgs& a, const CoarseFft& f, cudaStream_t s);
+// Kernels launch_coarse_fft issues for P time levels (three or four).
+int coarse_fft_launches(int nx, int P);
 
 // Correction and F-relaxation (ideal interpolation) of one level:
 // u[(j-1)m] = c_new[j-1] + e[j-1], then m-1 steps with g; interval N also
@@ -146,6 +148,14 @@ cudaError_t launch_fcf(const FcfArgs& a, const DevTaps& t, int precision, int th
 // Shared-memory slab length for nx points in the padded layout (one pad
 // element per 8 so that per-thread chunks of 8 are bank-conflict free).
 __host__ __device__ inline int padded_len(int nx) { return nx + (nx >> 3) + 1; }
+// The FCF and propagation kernels hold two padded FP64 slabs in shared memory
+// (at most 227 KiB per CTA): nx <= kMaxSlabNx.
+constexpr int kMaxSmemBytes = 227 * 1024;
+__host__ __device__ constexpr bool slab_pair_fits(int nx) {
+  return 2LL * (nx + (nx >> 3) + 1) * (long long)sizeof(double) <= kMaxSmemBytes;
+}
+constexpr int kMaxSlabNx = 12913;
+static_assert(slab_pair_fits(kMaxSlabNx) && !slab_pair_fits(kMaxSlabNx + 1), "kMaxSlabNx");
 
 // ------------------------------------------------------- device-side cycle test
 // State of the stopping test when a whole solve runs as one CUDA graph: the
@@ -266,6 +276,27 @@ cudaError_t launch_propagate(const double* in, double* out, int count, int nx, i
 // out + (n/store_every)*nx when n % store_every == 0 (u_0 is not written).
 cudaError_t launch_seq_slab(const double* u0, double* out, int nx, int P, int store_every, const DevTaps& t,
                             const Fixup& fx, int threads, cudaStream_t s);
+// ------------------------------------------------- random initial iterate
+// The paper's tests start from a uniformly random space-time iterate
+// (Section 2.2).  Point i of time level n draws Philox4x32-10 (Salmon,
+// Moraes, Dror, Shaw, SC'11: counter (i, n, 0, 0), key (seed lo, seed hi))
+// and joins its first two words into a double in [0, 1) with 53 random bits.
+// rows slabs: slab k is time level n = first_n + k * stride_n (u0 where n = 0).
+cudaError_t launch_random_rows(double* out, const double* u0, int nx, long long first_n, long long stride_n,
+                               int rows, unsigned long long seed, cudaStream_t s);
+// partial[k] = || phi_u[k] - u_{first_n + k + 1} ||^2 for the random levels u_n
+// (the space-time residual of the random iterate, one slab per CTA).
+cudaError_t launch_random_residual(const double* phi_u, double* partial, int nx, long long first_n, int rows,
+                                   unsigned long long seed, cudaStream_t s);
+// *acc = sum partial[0..n) (first) or *acc += that sum, in a fixed order.
+cudaError_t launch_accumulate(const double* partial, int n, double* acc, int first, cudaStream_t s);
+// CheckState of a solve set on the device (stream-ordered, so several solves
+// may be queued back to back): zero counters, the stopping parameters, r0sq.
+cudaError_t launch_state_init(CheckState* st, double tol, int max_iter, double diverge, double r0sq, cudaStream_t s);
+// out = rows [row0, row0 + rows) of c[1 - st->result_cur] (the C-points of a
+// finished graph solve), converted from float-float pairs when df is set.
+cudaError_t launch_result_rows(const CheckState* st, const double* c0, const double* c1, double* out, int nx,
+                               long long row0, long long rows, int df, cudaStream_t s);
 int march_max_cluster();
 void set_tile(int r);   // register tile of the stencil kernels: 8, 4 or 0
 int get_tile();

@@ -103,6 +103,10 @@ void release(mgrit_handle* h) {
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->hstate) cudaFreeHost(h->hstate);
+  if (h->ring) cudaFreeHost(h->ring);
+  for (auto& ev : h->ring_ev)
+    if (ev) cudaEventDestroy(ev);
+  h->ring = nullptr;
   h->gexec = nullptr;
   h->graph = nullptr;
   h->cap_stream = nullptr;
@@ -171,6 +175,12 @@ mgrit_status validate_problem(const mgrit_problem* p) {
     return fail(MGRIT_ERR_INVALID, "unknown boundary");
   if (p->boundary == MGRIT_BC_INFLOW && p->family != MGRIT_ERK)
     return fail(MGRIT_ERR_UNSUPPORTED, "inflow/outflow boundaries are implemented for ERK only");
+  if (!std::isfinite(p->alpha) || !std::isfinite(p->xmin) || !std::isfinite(p->xmax))
+    return fail(MGRIT_ERR_INVALID, "alpha, xmin and xmax must be finite");
+  if (p->alpha < 0.0)
+    return fail(MGRIT_ERR_UNSUPPORTED, "alpha must be > 0: U_p is upwind for a wave moving to the right");
+  if (!(p->xmin == 0.0 && p->xmax == 0.0) && !(p->xmin < p->xmax))
+    return fail(MGRIT_ERR_INVALID, "xmin must be < xmax (both 0 select [-1, 1])");
   if (p->family == MGRIT_ERK && p->rk_order == p->upwind_order) {
     // Table 1 limits as printed (last digit rounded up)
     static const double cmax[6] = {0, 1.0, 0.5, 1.62590, 1.04450, 1.96584};
@@ -209,7 +219,17 @@ mgrit_status validate_opts(const mgrit_problem* p, const mgrit_opts* o) {
     return fail(MGRIT_ERR_INVALID, "psi_halfwidth must be >= 0");
   if (o->cycle != MGRIT_CYCLE_V && o->cycle != MGRIT_CYCLE_F) return fail(MGRIT_ERR_INVALID, "unknown cycle");
   if (o->relax != MGRIT_RELAX_FCF && o->relax != MGRIT_RELAX_F) return fail(MGRIT_ERR_INVALID, "unknown relax");
+  if (o->init_guess != MGRIT_INIT_ZERO && o->init_guess != MGRIT_INIT_RANDOM)
+    return fail(MGRIT_ERR_INVALID, "unknown init_guess");
   return MGRIT_OK;
+}
+
+// Physical spacings of Eq. 1's grid: dx = (xmax - xmin)/nx, dt = c dx/alpha.
+void grid_spacings(const mgrit_problem* p, double* dx, double* dt) {
+  const double a = p->alpha > 0.0 ? p->alpha : 1.0;
+  const bool dflt = p->xmin == 0.0 && p->xmax == 0.0;
+  *dx = (dflt ? 2.0 : p->xmax - p->xmin) / p->nx;
+  *dt = p->cfl * *dx / a;
 }
 
 static PlanRequest make_request(const mgrit_problem* p, const mgrit_opts* o) {
@@ -818,8 +838,9 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
   mgrit_status st = validate_problem(prob);
   if (st == MGRIT_OK) st = validate_opts(prob, opts);
   if (st != MGRIT_OK) return st;
-  if (2.0 * prob->nx * sizeof(double) > 227.0 * 1024.0)
-    return fail(MGRIT_ERR_UNSUPPORTED, "nx too large for one shared-memory slab (max 14528)");
+  if (!slab_pair_fits(prob->nx))
+    return fail(MGRIT_ERR_UNSUPPORTED, "nx too large for two shared-memory slabs (max " +
+                                           std::to_string(kMaxSlabNx) + ")");
   mgrit_handle* h = new mgrit_handle();
   h->prob = *prob;
   h->opts = *opts;
@@ -1115,7 +1136,7 @@ mgrit_status run_coarse_solve(mgrit_handle* h, const MarchArgs& a, const DevTaps
   mgrit_status st = klaunch(h, MGRIT_K_MARCH, "coarse fft", [&] {
     return launch_ok(launch_coarse_fft(a, h->cfft, h->stream), "coarse solve (Fourier space)");
   });
-  if (st == MGRIT_OK) h->kcount[MGRIT_K_MARCH] += 3;  // four kernels (three with a single scan block)
+  if (st == MGRIT_OK) h->kcount[MGRIT_K_MARCH] += coarse_fft_launches(a.nx, a.P) - 1;  // klaunch counted one
   return st;
 }
 
@@ -1128,11 +1149,20 @@ mgrit_status initial_residual(mgrit_handle* h, const double* u0dev, double* r0) 
   return MGRIT_OK;
 }
 
-// Enqueue ||Phi u0||^2 into h->norm_host[0] (read after a stream sync).
+// Enqueue ||r^(0)||^2 into h->norm_host[0] (read after a stream sync):
+// ||Phi u0||^2 for the zero iterate, the full space-time residual for the
+// random one.
 mgrit_status initial_residual_async(mgrit_handle* h, const double* u0dev) {
   mgrit_status st;
   double* out = h->scratch;
   double* part = h->scratch + h->nx;
+  if (h->iterate_random) {
+    int launches = 0;
+    if ((st = enqueue_r0sq(h, part, &launches)) != MGRIT_OK) return st;
+    h->kcount[MGRIT_K_PROPAGATE] += launches;
+    CUDA_TRY(cudaMemcpyAsync(h->norm_host, part, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return MGRIT_OK;
+  }
   if ((st = klaunch(h, MGRIT_K_PROPAGATE, "propagate", [&] {
          if (h->sdirk) return launch_ok(launch_propagate_sdirk(u0dev, out, 1, h->nx, 1, h->splan, part, h->stream),
                                         "propagate");
@@ -1142,6 +1172,41 @@ mgrit_status initial_residual_async(mgrit_handle* h, const double* u0dev) {
        })) != MGRIT_OK)
     return st;
   CUDA_TRY(cudaMemcpyAsync(h->norm_host, part, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return MGRIT_OK;
+}
+
+mgrit_status enqueue_r0sq(mgrit_handle* h, double* dst, int* launches) {
+  const int nx = h->nx;
+  *launches = 0;
+  if (!h->iterate_random) {
+    *launches = 1;
+    if (h->sdirk)
+      return launch_ok(launch_propagate_sdirk(h->u0buf, h->scratch, 1, nx, 1, h->splan, dst, h->stream), "propagate");
+    return launch_ok(launch_propagate(h->u0buf, h->scratch, 1, nx, 1, h->dphi, dst, h->fcf_threads, h->stream,
+                                      &h->fx_phi),
+                     "propagate");
+  }
+  // r_n = Phi u_{n-1} - u_n for n = 1..nt over chunks of N1 levels: draw
+  // u_{n-1} into rows 1..N1 of c[1] (free until the first FCF writes them),
+  // step them in place, and sum the squared differences to the draws of u_n
+  const int rows = h->Nl[1];
+  double* buf = h->c[1] + nx;
+  const unsigned long long seed = h->opts.seed;
+  int q = 0;
+  for (long long n0 = 0; n0 < h->nt; n0 += rows, ++q) {
+    const int cnt = (int)std::min<long long>(rows, h->nt - n0);
+    cudaError_t e = launch_random_rows(buf, h->u0buf, nx, n0, 1, cnt, seed, h->stream);
+    if (e == cudaSuccess)
+      e = h->sdirk ? launch_propagate_sdirk(buf, buf, cnt, nx, 1, h->splan, nullptr, h->stream)
+                   : launch_propagate(buf, buf, cnt, nx, 1, h->dphi, nullptr, h->fcf_threads, h->stream, &h->fx_phi);
+    if (e == cudaSuccess) e = launch_random_residual(buf, h->partial, nx, n0, cnt, seed, h->stream);
+    if (e == cudaSuccess) e = launch_accumulate(h->partial, cnt, dst, q == 0, h->stream);
+    if (e != cudaSuccess) return launch_ok(e, "random initial residual");
+    *launches += 4;
+  }
+  // the residual norms of the cycles sum partial[0], which no relaxation
+  // writes: leave the partials as zero as the handle was created with them
+  CUDA_TRY(cudaMemsetAsync(h->partial, 0, (size_t)(rows + 1) * sizeof(double), h->stream));
   return MGRIT_OK;
 }
 
@@ -1438,7 +1503,16 @@ mgrit_status load_iterate(mgrit_handle* h, const double* u0, const double* c_ini
   const size_t N1 = h->Nl[1];
   const size_t slab = (size_t)nx * sizeof(double);
   double* dst = h->dfc ? h->c[1] : h->c[0];  // float-float: stage the FP64 values in c[1]
-  if (c_init) {
+  h->iterate_random = false;
+  if (!c_init && h->opts.init_guess == MGRIT_INIT_RANDOM) {
+    // Section 2.2: u0 at t = 0, uniform draws at every later C-point
+    // (row j = time level j m); F-points are drawn where the initial residual
+    // needs them
+    CUDA_TRY(cudaMemcpyAsync(h->u0buf, u0, slab, kind_to_dev(u0), h->stream));
+    CUDA_TRY(launch_random_rows(dst, h->u0buf, nx, 0, h->m, (int)N1 + 1, h->opts.seed, h->stream));
+    if (h->dfc) CUDA_TRY(launch_convert_df(dst, h->c[0], (long long)(N1 + 1) * nx, 1, h->stream));
+    h->iterate_random = true;
+  } else if (c_init) {
     CUDA_TRY(cudaMemcpyAsync(dst, c_init, (N1 + 1) * slab, kind_to_dev(c_init), h->stream));
     CUDA_TRY(cudaMemcpyAsync(h->u0buf, dst, slab, cudaMemcpyDeviceToDevice, h->stream));
     if (h->dfc) CUDA_TRY(launch_convert_df(dst, h->c[0], (long long)(N1 + 1) * nx, 1, h->stream));
@@ -1463,14 +1537,10 @@ static mgrit_status solve_graph(mgrit_handle* h, const double* u0, const double*
   h->hstate->diverge = (h->opts.flags & MGRIT_FLAG_NO_DIVERGENCE_STOP) ? 0.0 : 1e6;
   h->hstate->r0sq = r0_norm > 0.0 ? r0_norm * r0_norm : 0.0;
   CUDA_TRY(cudaMemcpyAsync(h->dstate, h->hstate, sizeof(CheckState), cudaMemcpyHostToDevice, h->stream));
-  // otherwise ||Phi u0||^2 straight into the state (zero initial iterate: r^(0) = Phi u0)
-  if (!(r0_norm > 0.0) &&
-      (st = launch_ok(h->sdirk ? launch_propagate_sdirk(h->u0buf, h->scratch, 1, nx, 1, h->splan, &h->dstate->r0sq,
-                                                        h->stream)
-                               : launch_propagate(h->u0buf, h->scratch, 1, nx, 1, h->dphi, &h->dstate->r0sq,
-                                                  h->fcf_threads, h->stream, &h->fx_phi),
-                      "propagate")) != MGRIT_OK)
-    return st;
+  // otherwise ||r^(0)||^2 straight into the state (zero initial iterate:
+  // r^(0) = Phi u0; random iterate: its full space-time residual)
+  int r0_launches = 0;
+  if (!(r0_norm > 0.0) && (st = enqueue_r0sq(h, &h->dstate->r0sq, &r0_launches)) != MGRIT_OK) return st;
   CUDA_TRY(cudaGraphLaunch(h->gexec, h->stream));
   CUDA_TRY(cudaMemcpyAsync(h->hstate, h->dstate, sizeof(CheckState), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -1483,19 +1553,34 @@ static mgrit_status solve_graph(mgrit_handle* h, const double* u0, const double*
   R->converged = S.status == 0 && S.done ? 1 : 0;
   // launches: initial residual, (it+1) x (fcf, norm, check), it x coarse correction
   reset_stats(h);
-  h->kcount[MGRIT_K_PROPAGATE] = r0_norm > 0.0 ? 0 : 1;
+  h->kcount[MGRIT_K_PROPAGATE] = r0_launches;
   h->kcount[MGRIT_K_FCF] = S.it + 1;
   h->kcount[MGRIT_K_NORM] = (fine_prec(h) == 0 && h->opts.relax == MGRIT_RELAX_FCF ? 2 : 1) * (S.it + 1);
   h->kcount[MGRIT_K_OTHER] = S.it + 1;
   h->last = 1 - S.result_cur;
   h->r0_last = R->r0_norm;
   if (out && (st = write_output(h, h->c[1 - S.result_cur], out)) != MGRIT_OK) return st;
-  const int other_before = h->kcount[MGRIT_K_OTHER];
-  (void)other_before;
   if (!S.done) return fail(MGRIT_ERR_CUDA, "graph ended without a stopping decision");
   if (S.status == -5) return fail(MGRIT_ERR_DIVERGED, "residual not finite or grew above 1e6 x initial");
   if (S.status == -4) return fail(MGRIT_ERR_NOT_CONVERGED, "max_iter reached");
   return MGRIT_OK;
+}
+
+// Build the solve graph at the first graph solve; false (and no half-built
+// graph kept) when the device refuses it: the host-driven loop runs instead.
+static bool ensure_graph(mgrit_handle* h) {
+  if (h->graph_failed) return false;
+  if (h->gexec) return true;
+  const std::string keep = g_err;
+  if (build_solve_graph(h) == MGRIT_OK) return true;
+  h->graph_failed = true;
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->gexec = nullptr;
+  h->graph = nullptr;
+  cudaGetLastError();
+  g_err = keep;
+  return false;
 }
 
 static mgrit_status solve_impl(mgrit_handle* h, const double* u0, const double* c_init, double r0_norm,
@@ -1510,36 +1595,20 @@ static mgrit_status solve_impl(mgrit_handle* h, const double* u0, const double* 
   R.setup_s = h->setup_s;
   R.op_complexity = h->op_complexity;
   reset_stats(h);
+  grid_spacings(&h->prob, &R.dx, &R.dt);
   const bool host_loop = (h->opts.flags & (MGRIT_FLAG_TIME_KERNELS | MGRIT_FLAG_HOST_LOOP)) != 0;
-  if (!host_loop && !h->graph_failed) {
-    if (!h->gexec) {
-      const std::string keep = g_err;
-      mgrit_status gs = build_solve_graph(h);
-      if (gs != MGRIT_OK) {
-        // fall back to the host-driven loop; keep no half-built graph
-        h->graph_failed = true;
-        if (h->gexec) cudaGraphExecDestroy(h->gexec);
-        if (h->graph) cudaGraphDestroy(h->graph);
-        h->gexec = nullptr;
-        h->graph = nullptr;
-        cudaGetLastError();
-        g_err = keep;
-      }
+  if (!host_loop && ensure_graph(h)) {
+    mgrit_status gs = solve_graph(h, u0, c_init, r0_norm, out, &R);
+    if (gs == MGRIT_OK || gs == MGRIT_ERR_NOT_CONVERGED || gs == MGRIT_ERR_DIVERGED) {
+      CUDA_TRY(cudaStreamSynchronize(h->stream));
+      R.solve_s = now_s() - t0;
+      R.dof_per_s = R.solve_s > 0 ? (double)nx * h->nt / R.solve_s : 0.0;
+      collect_stats(h, &R);
+      R.launches += R.iterations * h->graph_coarse_launches;
+      R.graph = 1;
+      if (res) *res = R;
     }
-    if (h->gexec) {
-      mgrit_status gs = solve_graph(h, u0, c_init, r0_norm, out, &R);
-      if (gs == MGRIT_OK || gs == MGRIT_ERR_NOT_CONVERGED || gs == MGRIT_ERR_DIVERGED) {
-        CUDA_TRY(cudaStreamSynchronize(h->stream));
-        R.solve_s = now_s() - t0;
-        R.dof_per_s = R.solve_s > 0 ? (double)nx * h->nt / R.solve_s : 0.0;
-        collect_stats(h, &R);
-        R.launches += R.iterations * h->graph_coarse_launches;
-        R.graph = 1;
-        if (res) *res = R;
-        return gs;
-      }
-      return gs;
-    }
+    return gs;
   }
   int cur = 0;
   mgrit_status st = load_iterate(h, u0, c_init);
@@ -1625,6 +1694,89 @@ extern "C" mgrit_status mgrit_solve_from(mgrit_handle* h, const double* c_init, 
   if (!c_init) return fail(MGRIT_ERR_INVALID, "c_init is NULL");
   if (!std::isfinite(r0_norm)) return fail(MGRIT_ERR_INVALID, "r0_norm must be finite");
   return solve_impl(h, c_init, c_init, r0_norm, out, res);
+}
+
+// ----------------------------------------------------------- queued solves
+
+extern "C" mgrit_status mgrit_solve_async(mgrit_handle* h, const double* u0, double* out) {
+  if (!h) return fail(MGRIT_ERR_INVALID, "handle is NULL");
+  if (!u0) return fail(MGRIT_ERR_INVALID, "u0 is NULL");
+  if (out && !is_device_ptr(out)) return fail(MGRIT_ERR_INVALID, "out must be device memory (or NULL)");
+  if (h->opts.output == MGRIT_OUT_FULL)
+    return fail(MGRIT_ERR_UNSUPPORTED, "mgrit_solve_async writes FINAL or CPOINTS output; use mgrit_solve for FULL");
+  if (h->opts.flags & (MGRIT_FLAG_TIME_KERNELS | MGRIT_FLAG_HOST_LOOP))
+    return fail(MGRIT_ERR_UNSUPPORTED, "mgrit_solve_async runs the graph solve (no host loop or kernel timing)");
+  if (h->ring_count >= MGRIT_MAX_INFLIGHT)
+    return fail(MGRIT_ERR_INVALID, "MGRIT_MAX_INFLIGHT solves outstanding: call mgrit_solve_wait first");
+  if (!ensure_graph(h)) return fail(MGRIT_ERR_UNSUPPORTED, "the device refused the solve graph");
+  if (!h->ring) {
+    if (cudaMallocHost(&h->ring, MGRIT_MAX_INFLIGHT * sizeof(CheckState)) != cudaSuccess) {
+      h->ring = nullptr;
+      return launch_ok(cudaGetLastError(), "pinned result slots");
+    }
+    for (auto& ev : h->ring_ev) CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  }
+  const double t0 = now_s();
+  const int nx = h->nx;
+  const long long N1 = h->Nl[1];
+  mgrit_status st;
+  if ((st = load_iterate(h, u0, nullptr)) != MGRIT_OK) return st;
+  const double diverge = (h->opts.flags & MGRIT_FLAG_NO_DIVERGENCE_STOP) ? 0.0 : 1e6;
+  CUDA_TRY(launch_state_init(h->dstate, h->opts.tol, h->opts.max_iter, diverge, 0.0, h->stream));
+  int r0_launches = 0;
+  if ((st = enqueue_r0sq(h, &h->dstate->r0sq, &r0_launches)) != MGRIT_OK) return st;
+  CUDA_TRY(cudaGraphLaunch(h->gexec, h->stream));
+  const int slot = (h->ring_head + h->ring_count) % MGRIT_MAX_INFLIGHT;
+  CUDA_TRY(cudaMemcpyAsync(&h->ring[slot], h->dstate, sizeof(CheckState), cudaMemcpyDeviceToHost, h->stream));
+  if (out) {
+    const bool fin = h->opts.output == MGRIT_OUT_FINAL;
+    CUDA_TRY(launch_result_rows(h->dstate, h->c[0], h->c[1], out, nx, fin ? N1 : 0, fin ? 1 : N1 + 1, h->dfc,
+                                h->stream));
+  }
+  CUDA_TRY(cudaEventRecord(h->ring_ev[slot], h->stream));
+  h->ring_t0[slot] = t0;
+  h->ring_r0_launches[slot] = r0_launches + 1 + (out ? 1 : 0);  // + state init, result rows
+  h->ring_count++;
+  return MGRIT_OK;
+}
+
+extern "C" mgrit_status mgrit_solve_wait(mgrit_handle* h, mgrit_result* res) {
+  if (!h) return fail(MGRIT_ERR_INVALID, "handle is NULL");
+  if (h->ring_count == 0) return fail(MGRIT_ERR_INVALID, "no mgrit_solve_async outstanding on this handle");
+  const int slot = h->ring_head;
+  CUDA_TRY(cudaEventSynchronize(h->ring_ev[slot]));
+  h->ring_head = (h->ring_head + 1) % MGRIT_MAX_INFLIGHT;
+  h->ring_count--;
+  const CheckState S = h->ring[slot];
+  mgrit_result R;
+  std::memset(&R, 0, sizeof(R));
+  R.n_levels = h->L;
+  R.setup_s = h->setup_s;
+  R.op_complexity = h->op_complexity;
+  grid_spacings(&h->prob, &R.dx, &R.dt);
+  R.r0_norm = std::sqrt(S.r0sq);
+  R.iterations = S.it;
+  R.rel_residual = S.rel;
+  R.n_history = std::min(S.nhist, MGRIT_MAX_HISTORY);
+  for (int k = 0; k < R.n_history; ++k) R.history[k] = S.hist[k];
+  R.converged = S.status == 0 && S.done ? 1 : 0;
+  R.solve_s = now_s() - h->ring_t0[slot];
+  R.dof_per_s = R.solve_s > 0 ? (double)h->nx * h->nt / R.solve_s : 0.0;
+  reset_stats(h);
+  h->kcount[MGRIT_K_FCF] = S.it + 1;
+  h->kcount[MGRIT_K_NORM] = (fine_prec(h) == 0 && h->opts.relax == MGRIT_RELAX_FCF ? 2 : 1) * (S.it + 1);
+  h->kcount[MGRIT_K_OTHER] = S.it + 1;                       // stopping tests
+  h->kcount[MGRIT_K_PROPAGATE] = h->ring_r0_launches[slot];  // initial residual, state, output
+  collect_stats(h, &R);
+  R.launches += R.iterations * h->graph_coarse_launches;
+  R.graph = 1;
+  h->last = 1 - S.result_cur;
+  h->r0_last = R.r0_norm;
+  if (res) *res = R;
+  if (!S.done) return fail(MGRIT_ERR_CUDA, "graph ended without a stopping decision");
+  if (S.status == -5) return fail(MGRIT_ERR_DIVERGED, "residual not finite or grew above 1e6 x initial");
+  if (S.status == -4) return fail(MGRIT_ERR_NOT_CONVERGED, "max_iter reached");
+  return MGRIT_OK;
 }
 
 extern "C" mgrit_status mgrit_relax(mgrit_handle* h, int32_t sweeps, double* rel_residual) {

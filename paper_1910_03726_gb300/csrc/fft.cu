@@ -240,6 +240,25 @@ cudaError_t launch_fft_tables(const DevTaps& psi, int nx, double* tw, double* mu
   return cudaGetLastError();
 }
 
+// Blocks of rows of the chunked scan: enough for about four CTAs per SM, but
+// no more than about sqrt(rows) (pass 2 walks the earlier blocks' ends one by
+// one), at most kMaxScanBlocks, and none empty.
+static int scan_blocks(int rows, int mblocks) {
+  int nb = (4 * 152 + mblocks - 1) / mblocks;
+  int sq = 1;
+  while (sq * sq < rows) ++sq;
+  nb = nb > sq ? sq : nb;
+  nb = nb < 1 ? 1 : (nb > kMaxScanBlocks ? kMaxScanBlocks : nb);
+  nb = nb > rows ? rows : nb;
+  const int L = (rows + nb - 1) / nb;
+  return (rows + L - 1) / L;
+}
+
+int coarse_fft_launches(int nx, int P) {
+  if (P < 2) return 0;
+  return scan_blocks(P - 1, (nx / 2 + 1 + 255) / 256) > 1 ? 4 : 3;
+}
+
 cudaError_t launch_coarse_fft(const MarchArgs& a, const CoarseFft& f, cudaStream_t s) {
   if (a.P < 2) return cudaSuccess;
   if (!fft_coarse_supported(a.nx) || a.init || a.trunc || !f.spec || !f.carry || a.P - 1 > f.rows ||
@@ -265,17 +284,8 @@ cudaError_t launch_coarse_fft(const MarchArgs& a, const CoarseFft& f, cudaStream
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int rows = a.P - 1;
   const int mblocks = (nh + 255) / 256;
-  // enough blocks of rows for about four CTAs per SM, but no more than about
-  // sqrt(rows) (pass 2 walks the earlier blocks' ends one by one), at most
-  // kMaxScanBlocks
-  int nb = (4 * 152 + mblocks - 1) / mblocks;
-  int sq = 1;
-  while (sq * sq < rows) ++sq;
-  nb = nb > sq ? sq : nb;
-  nb = nb < 1 ? 1 : (nb > kMaxScanBlocks ? kMaxScanBlocks : nb);
-  nb = nb > rows ? rows : nb;
+  const int nb = scan_blocks(rows, mblocks);
   const int L = (rows + nb - 1) / nb;
-  nb = (rows + L - 1) / L;
   cplx64* carry = reinterpret_cast<cplx64*>(f.carry);
   fft_recur_local_kernel<<<dim3(mblocks, nb), 256, 0, s>>>(spec, mu, carry, nh, rows, L);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -72,6 +72,14 @@ struct mgrit_handle {
   int graph_coarse_launches = 0;          // kernels of one coarse correction
   mg::CheckState* dstate = nullptr;       // device
   mg::CheckState* hstate = nullptr;       // pinned host
+  // mgrit_solve_async: one pinned CheckState slot, one event and the enqueue
+  // time per outstanding solve, finished in order by mgrit_solve_wait
+  mg::CheckState* ring = nullptr;         // pinned, MGRIT_MAX_INFLIGHT slots
+  cudaEvent_t ring_ev[MGRIT_MAX_INFLIGHT] = {};
+  double ring_t0[MGRIT_MAX_INFLIGHT] = {};
+  int ring_r0_launches[MGRIT_MAX_INFLIGHT] = {};
+  int ring_head = 0, ring_count = 0;
+  bool iterate_random = false;            // load_iterate drew the random iterate
   // per-solve launch accounting (and CUDA-event timing with MGRIT_FLAG_TIME_KERNELS)
   int kcount[MGRIT_K_KINDS] = {0};
   std::vector<cudaEvent_t> evpool;
@@ -93,6 +101,8 @@ cudaMemcpyKind kind_to_dev(const void* src);
 cudaMemcpyKind kind_from_dev(const void* dst);
 mgrit_status validate_problem(const mgrit_problem* p);
 mgrit_status validate_opts(const mgrit_problem* p, const mgrit_opts* o);
+// Physical spacings of Eq. 1's grid: dx = (xmax - xmin)/nx, dt = c dx/alpha.
+void grid_spacings(const mgrit_problem* p, double* dx, double* dt);
 mgrit_status plan(const mgrit_problem* p, const mgrit_opts* o, std::vector<mg::CoarseOp>* ops);
 int pick_cluster(int nx, const mg::Taps& t);
 mgrit_status launch_ok(cudaError_t e, const char* what);
@@ -105,6 +115,10 @@ mgrit_status run_march(mgrit_handle* h, const mg::MarchArgs& a, const mg::DevTap
 mgrit_status run_coarse_solve(mgrit_handle* h, const mg::MarchArgs& a, const mg::DevTaps& t);
 mgrit_status initial_residual(mgrit_handle* h, const double* u0dev, double* r0);
 mgrit_status initial_residual_async(mgrit_handle* h, const double* u0dev);
+// ||r^(0)||^2 of the loaded iterate into the device double dst: the random
+// iterate's space-time residual, or ||Phi u0||^2 for the zero iterate.
+// Returns the number of kernels launched through *launches.
+mgrit_status enqueue_r0sq(mgrit_handle* h, double* dst, int* launches);
 // Initial iterate into the handle's C-point arrays (u0 with a zero iterate,
 // or all C-points c_init); u0 in FP64 into u0buf.
 mgrit_status load_iterate(mgrit_handle* h, const double* u0, const double* c_init);

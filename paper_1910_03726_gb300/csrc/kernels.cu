@@ -1617,6 +1617,120 @@ cudaError_t launch_convert_df(const double* in, double* out, long long count, in
   return cudaGetLastError();
 }
 
+// ------------------------------------------------- random initial iterate
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32 x 32 -> 64-bit
+// products with the key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ double philox_unit(unsigned long long seed, unsigned int i, unsigned int n) {
+  unsigned int c0 = i, c1 = n, c2 = 0u, c3 = 0u;
+  unsigned int k0 = (unsigned int)seed, k1 = (unsigned int)(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned int lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const unsigned int lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const unsigned int n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  const unsigned long long bits = ((unsigned long long)(c0 >> 5) << 26) | (unsigned long long)(c1 >> 6);
+  return (double)bits * 0x1.0p-53;
+}
+
+__global__ void random_rows_kernel(double* __restrict__ out, const double* __restrict__ u0, int nx,
+                                   long long first_n, long long stride_n, unsigned long long seed) {
+  const long long k = blockIdx.y;
+  const long long n = first_n + k * stride_n;
+  double* row = out + k * nx;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx; i += gridDim.x * blockDim.x)
+    row[i] = n == 0 ? u0[i] : philox_unit(seed, (unsigned int)i, (unsigned int)n);
+}
+
+__global__ void __launch_bounds__(256) random_residual_kernel(const double* __restrict__ phi_u,
+                                                              double* __restrict__ partial, int nx,
+                                                              long long first_n, unsigned long long seed) {
+  const long long k = blockIdx.x;
+  const unsigned int n = (unsigned int)(first_n + k + 1);
+  const double* row = phi_u + k * nx;
+  double ss = 0.0;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const double d = row[i] - philox_unit(seed, (unsigned int)i, n);
+    ss = fma(d, d, ss);
+  }
+  ss = block_sum(ss);
+  if (threadIdx.x == 0) partial[k] = ss;
+}
+
+__global__ void __launch_bounds__(1024) accumulate_kernel(const double* __restrict__ partial, int n, double* acc,
+                                                          int first) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += partial[i];
+  v = block_sum(v);
+  if (threadIdx.x == 0) acc[0] = first ? v : acc[0] + v;
+}
+
+__global__ void state_init_kernel(CheckState* st, double tol, int max_iter, double diverge, double r0sq) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  st->r0sq = r0sq;
+  st->tol = tol;
+  st->max_iter = max_iter;
+  st->it = 0;
+  st->done = 0;
+  st->status = 0;
+  st->result_cur = 0;
+  st->nhist = 0;
+  st->rel = 0.0;
+  st->diverge = diverge;
+}
+
+__global__ void result_rows_kernel(const CheckState* __restrict__ st, const double* c0, const double* c1,
+                                   double* __restrict__ out, long long first, long long count, int df) {
+  const double* src = (st->result_cur == 0 ? c1 : c0) + first;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = df ? df_to(reinterpret_cast<const df64*>(src)[i]) : src[i];
+}
+
+cudaError_t launch_random_rows(double* out, const double* u0, int nx, long long first_n, long long stride_n,
+                               int rows, unsigned long long seed, cudaStream_t s) {
+  const int bx = (nx + 255) / 256 < 8 ? (nx + 255) / 256 : 8;
+  for (int k0 = 0; k0 < rows; k0 += 65535) {  // gridDim.y <= 65535
+    const int r = rows - k0 < 65535 ? rows - k0 : 65535;
+    random_rows_kernel<<<dim3(bx, r), 256, 0, s>>>(out + (long long)k0 * nx, u0, nx, first_n + k0 * stride_n,
+                                                   stride_n, seed);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_random_residual(const double* phi_u, double* partial, int nx, long long first_n, int rows,
+                                   unsigned long long seed, cudaStream_t s) {
+  if (rows < 1) return cudaSuccess;
+  random_residual_kernel<<<rows, 256, 0, s>>>(phi_u, partial, nx, first_n, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(const double* partial, int n, double* acc, int first, cudaStream_t s) {
+  accumulate_kernel<<<1, 1024, 0, s>>>(partial, n, acc, first);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_state_init(CheckState* st, double tol, int max_iter, double diverge, double r0sq, cudaStream_t s) {
+  state_init_kernel<<<1, 32, 0, s>>>(st, tol, max_iter, diverge, r0sq);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_result_rows(const CheckState* st, const double* c0, const double* c1, double* out, int nx,
+                               long long row0, long long rows, int df, cudaStream_t s) {
+  const long long count = rows * nx;
+  if (count <= 0) return cudaSuccess;
+  long long blocks = (count + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  result_rows_kernel<<<(int)blocks, 256, 0, s>>>(st, c0, c1, out, row0 * nx, count, df);
+  return cudaGetLastError();
+}
+
 template <int R, bool TR>
 static cudaError_t launch_propagate_t(const double* in, double* out, int count, int nx, int k, const DevTaps& t,
                                       double* partial, int threads, cudaStream_t s, const Fixup& fx) {

@@ -6,6 +6,7 @@
 // caller's inputs and outputs and keeps its one piece of scratch -- the
 // per-interval partial sums of the residual norm -- in a fixed-size array that
 // lives in the library's own device image.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -24,24 +25,63 @@ void set_error(const std::string& msg);  // driver.cpp: thread-local error text
 constexpr int kStaticMaxIntervals = MGRIT_STATIC_MAX_INTERVALS;
 static __device__ __align__(256) double g_fcf_static_partial[kStaticMaxIntervals];
 
-// Device address of the array, looked up once per device with that device
-// current (in host code the symbol itself is only a stand-in, not an address).
-static double* g_partial_addr[128] = {nullptr};
+// Device address of the array, looked up with the device current (in host
+// code the symbol itself is only a stand-in, not an address).  It is kept per
+// device together with the unique ID of the CUDA context it came from, and
+// looked up again when the device's current context is another one (after a
+// cudaDeviceReset the module, and with it the array, is loaded anew).  The
+// context ID comes from the driver's cuCtxGetCurrent and cuCtxGetId, reached
+// through cudaGetDriverEntryPoint (no link against the driver library).
+struct StaticAddr {
+  double* addr = nullptr;
+  unsigned long long ctx_id = 0;
+};
+static StaticAddr g_partial_addr[128];
 static std::mutex g_partial_mu;
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+static cudaError_t current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaError_t e = cudaGetDriverEntryPoint("cuCtxGetCurrent", &f1, cudaEnableDefault, &q1);
+    if (e == cudaSuccess) e = cudaGetDriverEntryPoint("cuCtxGetId", &f2, cudaEnableDefault, &q2);
+    if (e != cudaSuccess) return e;
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return cudaErrorSymbolNotFound;
+    get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    get_id = reinterpret_cast<CtxGetIdFn>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  *id = 0;
+  if (ctx && get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  return cudaSuccess;
+}
 
 static cudaError_t static_partial(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+  unsigned long long id = 0;
+  if ((e = current_context_id(&id)) != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_partial_mu);
-  if (!g_partial_addr[dev]) {
+  StaticAddr& a = g_partial_addr[dev];
+  if (!a.addr || id == 0 || id != a.ctx_id) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_fcf_static_partial);
+    e = cudaGetSymbolAddress(&p, g_fcf_static_partial);  // makes the primary context current
     if (e != cudaSuccess) return e;
-    g_partial_addr[dev] = static_cast<double*>(p);
+    if ((e = current_context_id(&id)) != cudaSuccess) return e;
+    a.addr = static_cast<double*>(p);
+    a.ctx_id = id;
   }
-  *out = g_partial_addr[dev];
+  *out = a.addr;
   return cudaSuccess;
 }
 
@@ -67,8 +107,8 @@ extern "C" mgrit_status mgrit_fcf_residual_static(const double* c_old, double* c
               " (size of the library's static scratch array)");
     return MGRIT_ERR_INVALID;
   }
-  if (nx < 8 || 2.0 * nx * sizeof(double) > 227.0 * 1024.0) {
-    set_error("nx must be in 8..14528");
+  if (nx < 8 || !slab_pair_fits(nx)) {  // two padded FP64 slabs in one CTA's shared memory
+    set_error("nx must be in 8.." + std::to_string(kMaxSlabNx));
     return MGRIT_ERR_INVALID;
   }
   if (m < 1 || ntaps < 1 || ntaps > kMaxDevTaps || !offsets || !coeffs || (precision != 0 && precision != 1)) {
@@ -80,19 +120,16 @@ extern "C" mgrit_status mgrit_fcf_residual_static(const double* c_old, double* c
     set_error("c_old, c_new, r and norm2 must be device pointers");
     return MGRIT_ERR_INVALID;
   }
-  DevTaps t;
-  std::memset(&t, 0, sizeof(t));
-  t.n = ntaps;
   for (int k = 0; k < ntaps; ++k) {
     if (offsets[k] <= -nx || offsets[k] >= nx) {
       set_error("tap offsets must satisfy |offset| < nx");
       return MGRIT_ERR_INVALID;
     }
-    t.off[k] = offsets[k];
-    t.c64[k] = coeffs[k];
-    t.c32[k] = (float)coeffs[k];
-    t.lo = offsets[k] < t.lo ? offsets[k] : t.lo;
-    t.hi = offsets[k] > t.hi ? offsets[k] : t.hi;
+  }
+  DevTaps t;
+  if (!make_dev_taps(offsets, coeffs, ntaps, &t)) {
+    set_error("bad taps");
+    return MGRIT_ERR_INVALID;
   }
   double* partial = nullptr;
   cudaError_t e = static_partial(&partial);

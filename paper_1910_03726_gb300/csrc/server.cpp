@@ -525,6 +525,8 @@ extern "C" mgrit_status mgrit_submit(mgrit_server* S, const mgrit_problem* prob,
   if (st == MGRIT_OK) st = validate_opts(prob, opts);
   if (st != MGRIT_OK) return st;
   if (opts->psi_rule == MGRIT_PSI_USER) return fail(MGRIT_ERR_UNSUPPORTED, "the server fits Psi itself");
+  if (opts->init_guess != MGRIT_INIT_ZERO)
+    return fail(MGRIT_ERR_UNSUPPORTED, "the server starts every request from the zero iterate");
   Request* r = new Request();
   r->prob = *prob;
   r->opts = *opts;
@@ -584,7 +586,10 @@ extern "C" mgrit_status mgrit_poll(mgrit_server* S, uint64_t ticket, double* out
       std::memcpy(out, r->out.data(), r->out.size() * sizeof(double));
     }
   }
-  if (res) *res = r->res;
+  if (res) {
+    *res = r->res;
+    grid_spacings(&r->prob, &res->dx, &res->dt);
+  }
   const mgrit_status st = r->status;
   if (st != MGRIT_OK) fail(st, r->error);
   delete r;

@@ -30,7 +30,33 @@ def test_exports_every_declared_entry_point(capi):
     assert "mgrit_setup" in names and "mgrit_poll" in names
     missing = [n for n in names if not hasattr(capi._lib, n)]
     assert not missing, missing
-    assert capi.mgrit_abi_version() == 4
+    assert capi.mgrit_abi_version() == 5
+
+
+def test_struct_layouts_match_the_header(capi):
+    """mgrit_opts_default writes every field of the C struct: the binding's
+    fields after the ones added in ABI 5 (init_guess, seed) read back the
+    documented defaults only if both sides agree on the layout."""
+    o = capi.mgrit_opts_default()
+    assert (o.m, o.levels, o.max_iter, o.psi_halfwidth, o.min_coarse) == (8, 2, 100, 3, 2)
+    assert (o.init_guess, o.seed, o.tol, o.psi_rho) == (0, 0, 1e-10, 0.15)
+    assert not o.psi_user_nnz and not o.psi_user_offsets and not o.psi_user_coeffs
+    import ctypes as C
+    assert C.sizeof(capi.MgritProblem) == 56 and C.sizeof(capi.MgritOpts) == 104
+
+
+@pytest.mark.parametrize("alpha,xmin,xmax,status", [(-1.0, -1.0, 1.0, -10), (1.0, 1.0, -1.0, -1),
+                                                     (float("nan"), -1.0, 1.0, -1), (0.0, 0.0, 0.0, 0),
+                                                     (2.5, 0.0, 10.0, 0)])
+def test_problem_validation_of_wave_speed_and_domain(capi, alpha, xmin, xmax, status):
+    """Eq. 1's alpha and domain: U_p is upwind for alpha > 0 (a left-moving
+    wave is unsupported), xmin < xmax, and zeros select alpha = 1 on [-1, 1]."""
+    prob = capi.problem(64, 64, "ERK", 1, 1, 0.85, alpha=alpha, xmin=xmin, xmax=xmax)
+    import ctypes as C
+    n = C.c_int32()
+    offs = (C.c_int32 * 16)()
+    cfs = (C.c_double * 16)()
+    assert capi._lib.mgrit_phi_taps(C.byref(prob), 16, C.byref(n), offs, cfs) == status
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
@@ -175,3 +201,17 @@ def test_phi_power_boundary_rows_match_oracle(capi, p, m, nx):
     assert np.max(np.abs(left - Pm[:nl, :cl])) < 1e-13
     assert np.all(np.abs(right - Pm[nx - nr:, nx - cr:]) < 1e-13)
     assert np.all(Pm[:nl, cl:] == 0.0) and np.all(Pm[nx - nr:, : nx - cr] == 0.0)
+
+
+def test_static_entry_point_checks_the_shared_memory_bound(capi):
+    """The FCF keeps two padded FP64 slabs (nx + nx/8 + 1 values each) in one
+    CTA's 227 KiB of shared memory, so nx <= 12913; the check runs before any
+    device call (null buffers are rejected next, still on the host)."""
+    import ctypes as C
+    offs = (C.c_int32 * 2)(0, -1)
+    cfs = (C.c_double * 2)(0.15, 0.85)
+    lib = capi._lib
+    st = lib.mgrit_fcf_residual_static(None, None, None, None, 12914, 4, 8, 2, offs, cfs, 0, None)
+    assert st == -1 and "8..12913" in capi.mgrit_last_error()
+    st = lib.mgrit_fcf_residual_static(None, None, None, None, 12913, 4, 8, 2, offs, cfs, 0, None)
+    assert st == -1 and "device pointers" in capi.mgrit_last_error()

@@ -17,6 +17,19 @@ def test_phi_m_column_stepping_equals_inverse_dft(fam, p, m):
     np.testing.assert_allclose(a, b, atol=1e-13)
 
 
+@pytest.mark.parametrize("fam,p,q,m", [("SDIRK", 3, 5, 16), ("SDIRK", 1, 5, 4), ("ERK", 2, 4, 8)])
+def test_phi_m_column_with_another_upwind_order(fam, p, q, m):
+    """Lemma 1 with U_q in place of U_p: stepping and the inverse DFT of
+    R(z)^m built from U_q's symbol give the same first column of Phi^m."""
+    nx = 256
+    c = 4.0 if fam == "SDIRK" else 0.5 * schemes.cfl_number("ERK", p)
+    st = stepping.FineStep(fam, p, c, nx, q=q)
+    lam = schemes.phi_symbol(fam, p, c, nx, q=q)
+    np.testing.assert_allclose(psi.phi_m_column_by_stepping(st, nx, m), psi.phi_m_column_by_symbol(lam, m),
+                               atol=1e-13)
+    assert not np.allclose(lam, schemes.phi_symbol(fam, p, c, nx))
+
+
 def test_erk_phi_nnz_matches_corollary1():
     """Corollary 1: ERK Phi is one circulant stencil with s(w-1)+1 diagonals."""
     w = {1: 2, 2: 3, 3: 4, 4: 5, 5: 6}
