@@ -283,7 +283,11 @@ mgrit_status mgrit_psi_plan(const mgrit_problem* prob, const mgrit_opts* opts, i
 mgrit_status mgrit_setup(const mgrit_problem* prob, const mgrit_opts* opts, void* stream,
                          mgrit_handle** out);
 
-/* Solve from u0 (nx values, host or device) with the initial iterate at
+/* MGRIT for the block lower-bidiagonal system of Eq. 3 (Section 2.2:
+ * FCF-relaxation, C-point residual, injection, the coarse system of Eq. 5
+ * solved sequentially or by recursion, ideal interpolation; stopping when the
+ * space-time residual falls below tol times the initial one).
+ * Solve from u0 (nx values, host or device) with the initial iterate at
  * t > 0 that opts.init_guess names (Section 2.2).  out (host or device)
  * receives, per opts.output: FINAL the nx values at t = T; CPOINTS
  * (nt/m + 1) * nx C-point values; FULL (nt + 1) * nx values (F-points
@@ -362,13 +366,19 @@ typedef struct mgrit_server_opts {
   int32_t reserved;
 } mgrit_server_opts;
 
-/* Continuous-batching server: a host thread admits submitted solves while
- * their state fits in the budget, advances every admitted solve by one MGRIT
- * cycle per batched launch, retires converged solves and frees their slots. */
+/* Continuous-batching server.  The paper has no counterpart: this is a
+ * serving layer around the solve of Section 2.2, whose per-solve arithmetic
+ * is mgrit_solve's.  A host thread admits submitted solves while their state
+ * fits in the budget, advances every admitted solve by one MGRIT cycle per
+ * batched launch, retires converged solves and frees their slots.  It runs
+ * on the device that is current when the server is created. */
 mgrit_status mgrit_server_create(const mgrit_server_opts* sopts, void* stream, mgrit_server** out);
 
-/* Queue a solve (u0 host or device, copied before return).  *ticket
- * identifies it.  MGRIT_ERR_OVER_BUDGET if it could never fit the budget. */
+/* Queue a solve (u0 host or device, copied before return) of the problem and
+ * options as mgrit_setup takes them (Section 2.2's iteration from the zero
+ * iterate; MGRIT_INIT_RANDOM and MGRIT_PSI_USER are MGRIT_ERR_UNSUPPORTED
+ * here).  *ticket identifies it.  MGRIT_ERR_OVER_BUDGET if it could never fit
+ * the budget. */
 mgrit_status mgrit_submit(mgrit_server* s, const mgrit_problem* prob, const mgrit_opts* opts,
                           const double* u0, uint64_t* ticket);
 
@@ -389,6 +399,11 @@ typedef struct mgrit_server_counters {
   double retire_s;              /* worker time retiring (output copies)        */
   double mean_active;           /* average solves per cycle                    */
   double peak_resident_bytes;   /* largest device state held at once           */
+  double gpu_fcf_ms;            /* device time of the cycles' FCF launches     */
+  double gpu_norm_ms;           /*   residuals and norms                      */
+  double gpu_coarse_ms;         /*   coarse solves                             */
+  double gpu_gap_ms;            /* server stream idle between consecutive cycles */
+  double first_cycle_s;         /* server creation to its first cycle's launch */
 } mgrit_server_counters;
 mgrit_status mgrit_server_stats(mgrit_server* s, mgrit_server_counters* out);
 

@@ -87,7 +87,9 @@ class MgritServerStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
                 ("cycles", C.c_uint64), ("admit_s", C.c_double), ("plan_s", C.c_double), ("tune_s", C.c_double),
                 ("cycle_s", C.c_double),
-                ("retire_s", C.c_double), ("mean_active", C.c_double), ("peak_resident_bytes", C.c_double)]
+                ("retire_s", C.c_double), ("mean_active", C.c_double), ("peak_resident_bytes", C.c_double),
+                ("gpu_fcf_ms", C.c_double), ("gpu_norm_ms", C.c_double), ("gpu_coarse_ms", C.c_double),
+                ("gpu_gap_ms", C.c_double), ("first_cycle_s", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

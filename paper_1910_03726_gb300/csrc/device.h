@@ -299,6 +299,9 @@ cudaError_t launch_result_rows(const CheckState* st, const double* c0, const dou
                                long long row0, long long rows, int df, cudaStream_t s);
 int march_max_cluster();
 void set_tile(int r);   // register tile of the stencil kernels: 8, 4 or 0
+// Form of the fused float-float FCF: 1 register-resident (default, upwind
+// stencils), 0 slab in shared memory, 2 and 3 runs of intervals per CTA.
+void set_stream_fused(int mode);
 int get_tile();
 
 }  // namespace mg

@@ -57,6 +57,34 @@ extern "C" void mgrit_set_allocator(mgrit_alloc_fn a, mgrit_free_fn f, void* ctx
   g_alloc_ctx = ctx;
 }
 
+// Pinned host slots of 8 doubles (a handle's norm read-back), carved from
+// chunks of 4096 so that admitting thousands of server solves costs no
+// pinned allocation (and no release) per solve.
+static std::mutex g_pin_mu;
+static std::vector<double*> g_pin_free;
+
+double* pinned_slot() {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  if (g_pin_free.empty()) {
+    constexpr int kChunk = 4096;
+    double* p = nullptr;
+    if (cudaMallocHost(&p, kChunk * 8 * sizeof(double)) != cudaSuccess) {  // kept until exit
+      cudaGetLastError();
+      return nullptr;
+    }
+    for (int k = kChunk - 1; k >= 0; --k) g_pin_free.push_back(p + 8 * k);
+  }
+  double* s = g_pin_free.back();
+  g_pin_free.pop_back();
+  return s;
+}
+
+void pinned_slot_release(double* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.push_back(p);
+}
+
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -67,7 +95,7 @@ mgrit_status dalloc(mgrit_handle* h, size_t count, double** out) {
   const size_t bytes = std::max<size_t>(count, 1) * sizeof(double);
   void* p = nullptr;
   DevBuf b;
-  if (g_alloc) {
+  if (g_alloc && !h->pool_alloc) {
     p = g_alloc(bytes, (void*)h->stream, g_alloc_ctx);
     if (!p) return fail(MGRIT_ERR_OOM, "allocator callback returned NULL");
     b.freefn = g_free;
@@ -95,7 +123,7 @@ void release(mgrit_handle* h) {
     else cudaFreeAsync(b.p, h->stream);
   }
   h->bufs.clear();
-  if (h->norm_host) cudaFreeHost(h->norm_host);
+  pinned_slot_release(h->norm_host);
   h->norm_host = nullptr;
   for (auto ev : h->evpool) cudaEventDestroy(ev);
   h->evpool.clear();
@@ -111,7 +139,9 @@ void release(mgrit_handle* h) {
   h->graph = nullptr;
   h->cap_stream = nullptr;
   h->hstate = nullptr;
-  cudaStreamSynchronize(h->stream);
+  // a server's handle: its frees are stream-ordered behind the cycles still
+  // running, and its worker does not wait for them
+  if (!h->pool_alloc) cudaStreamSynchronize(h->stream);
 }
 
 DevTaps to_dev(const Taps& t) {
@@ -653,6 +683,12 @@ void autotune_fine(mgrit_handle* h) {
       return;
     }
   }
+  // time the candidates on an otherwise idle device (other streams' work, a
+  // server's running cycle for one, would distort the comparison)
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
   FcfArgs f = {};
   f.u_old = h->c[0];
   f.cstride = nx;
@@ -848,6 +884,7 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
   h->opts.psi_user_offsets = nullptr;
   h->opts.psi_user_coeffs = nullptr;
   h->stream = stream;
+  h->pool_alloc = batched;
   h->nx = prob->nx;
   h->nt = prob->nt;
   h->m = opts->m;
@@ -987,8 +1024,7 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
     delete h;
     return st;
   }
-  if (cudaMallocHost(&h->norm_host, 8 * sizeof(double)) != cudaSuccess) {
-    cudaGetLastError();
+  if (!(h->norm_host = pinned_slot())) {
     release(h);
     delete h;
     return fail(MGRIT_ERR_OOM, "pinned host buffer");
@@ -1026,6 +1062,7 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
   }
   h->fcf_threads = 0;  // chosen per launch from nx and the register tile
   if (const char* tile = std::getenv("MGRIT_TILE")) set_tile(std::atoi(tile));
+  if (const char* sf = std::getenv("MGRIT_FCF_STREAM")) set_stream_fused(std::atoi(sf));
   const Taps& coarsest = h->ops.back().taps;
   h->march_cluster = pick_cluster(nx, coarsest);
   h->march_threads = std::min(256, nx / h->march_cluster);
@@ -1798,6 +1835,11 @@ extern "C" mgrit_status mgrit_relax(mgrit_handle* h, int32_t sweeps, double* rel
   f.relax_f = h->opts.relax == MGRIT_RELAX_F;
   f.value_residual = prec == 0 && !f.relax_f;
   f.df_store = h->dfc;
+  // C-point 0 (the initial condition) of the other buffer: no sweep writes it,
+  // and an output of float-float C-points is converted through that buffer
+  if (sweeps > 0)
+    CUDA_TRY(cudaMemcpyAsync(h->c[1 - h->last], h->c[h->last], (size_t)nx * sizeof(double), cudaMemcpyDeviceToDevice,
+                             h->stream));
   for (int k = 0; k < sweeps; ++k) {  // back to back on the stream: no host synchronisation between sweeps
     f.u_old = h->c[h->last];
     f.c_new = h->c[1 - h->last];

@@ -45,6 +45,11 @@ struct mgrit_handle {
   mg::Fixup fx_phi = {};
   mg::Fixup fx_phim = {};             // of Phi^m (the collapsed path)
   std::vector<DevBuf> bufs;       // everything allocated, for release
+  // A server's handle allocates from the stream-ordered pool of its stream
+  // (cudaMallocAsync) whatever allocator mgrit_set_allocator installed: the
+  // server's worker thread admits thousands of solves, and callbacks into a
+  // host language per buffer stalled it (seconds per 4096-solve batch).
+  bool pool_alloc = false;
   double* c[2] = {nullptr, nullptr};
   std::vector<double*> r, u, cnew;  // indexed by level (size L+1)
   // Mixed modes keep level 1's residual and every coarse-level array in FP32

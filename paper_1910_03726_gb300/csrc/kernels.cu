@@ -104,14 +104,14 @@ __device__ __forceinline__ df64 df_from(double v) {
   return {h, (float)(v - (double)h)};
 }
 __device__ __forceinline__ double df_to(df64 a) { return (double)a.hi + (double)a.lo; }
-// a - b rounded to FP32 (TwoDiff of the high words, exact; low words added
-// to the rounding error), on the FP32 pipes.
-__device__ __forceinline__ float df_sub_f(df64 a, df64 b) {
-  const float s = a.hi - b.hi;
-  const float bb = s - a.hi;
-  const float err = (a.hi - (s - bb)) - (b.hi + bb);
-  return s + (err + (a.lo - b.lo));
-}
+// a - b in FP32 (the C-point residual rho, which only the FP32 second pass
+// reads): (a.hi - b.hi) + (a.lo - b.lo).  Where the high words are within a
+// factor of two of each other -- rho small against the C-points, as it is
+// once the iteration has started converging -- their difference is exact
+// (Sterbenz) and rho carries FP32 rounding once; elsewhere rho is large and
+// two FP32 roundings of it are what the FP32 pass needs.  Three instructions
+// instead of a TwoSum's eight.
+__device__ __forceinline__ float df_sub_f(df64 a, df64 b) { return (a.hi - b.hi) + (a.lo - b.lo); }
 // a + e (e FP32), normalised: TwoSum of the high words, low words added.
 __device__ __forceinline__ df64 df_add_f(df64 a, float e) {
   const float s = a.hi + e;
@@ -720,6 +720,386 @@ __device__ __forceinline__ void fcf_body_df_fused(const FcfArgs& a, const int j,
   }
 }
 
+// Streaming form of the fused body above for the memory-bound instances: CTA
+// b owns the consecutive intervals j0..j1-1 (a balanced split of 1..N) and
+// keeps two float-float slabs A (c_{j-1}, the F+C pass's input) and B (c_j,
+// the old C-point rho is taken against) plus the FP32 rho slab in shared
+// memory.  Once pass 1 has read A, the next interval's B = c_{j+1} is copied
+// into A with cp.async while pass 2 runs, and the two swap roles: every slab
+// crosses HBM once per run instead of twice per interval.  The zero-slab
+// shortcut (Phi^m 0 = 0) reads B's high words as pass 1 loads them, so it
+// costs no extra pass.  Arithmetic per point is the fused body's, in the same
+// order: the results are bitwise those of fcf_body_df_fused.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// One slab (nx float-float values) into padded shared memory, asynchronously.
+__device__ __forceinline__ void slab_async(df64* dst, const df64* src, int nx) {
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) cp_async8(dst + pidx(i), src + i);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+template <int SPAN, bool ASYNC>
+__global__ void __launch_bounds__(512, 2) fcf_df_stream_kernel(const FcfArgs a, const DevTaps t) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int R = 8;
+  const int nx = a.nx, plen = padded_len(nx);
+  df64* const S0 = reinterpret_cast<df64*>(smraw);  // slabs S0 and S0 + plen take turns as A and B
+  float* f0 = reinterpret_cast<float*>(S0 + 2 * plen);
+  const int N = a.N, G = gridDim.x, b = blockIdx.x;
+  const int j0 = 1 + (int)((long long)b * N / G), j1 = 1 + (int)((long long)(b + 1) * N / G);
+  if (j0 >= j1) return;
+  const df64* cold = reinterpret_cast<const df64*>(a.u_old);
+  df64* cnew = reinterpret_cast<df64*>(a.c_new);
+  // run start: A = c_{j0-1} through registers (its zero test); with ASYNC
+  // also B = c_{j0}, copied in asynchronously
+  int nz = 0;
+  if (!a.zero_old) {
+    if constexpr (ASYNC) slab_async(S0 + plen, cold + (long long)j0 * a.cstride, nx);
+    const df64* src = cold + (long long)(j0 - 1) * a.cstride;
+    pair_loop<df2>(nx, true, [&](int e) { return ldcg_df2(src + e); },
+                   [&](int e, df2 v) {
+                     const int q = pidx(e);
+                     S0[q] = v.a;
+                     S0[q + 1] = v.b;
+                     nz |= __float_as_uint(v.a.hi) | __float_as_uint(v.b.hi);
+                   });
+  }
+  bool runA = __syncthreads_or(nz & 0x7fffffff);  // a float-float zero has a zero high word
+  int cur = 0;
+  for (int j = j0; j < j1; ++j) {
+    const df64* A = S0 + cur * plen;
+    df64* B = S0 + (plen - cur * plen);
+    if constexpr (ASYNC) {
+      cp_async_wait_all();
+      __syncthreads();  // B complete and visible
+    }
+    int nzr = 0, nzb = 0;
+    df64* cnd = cnew + (long long)j * nx;
+    const df64* oldd = cold + (long long)j * a.cstride;
+    for (int i0 = threadIdx.x * R; i0 < nx; i0 += blockDim.x * R) {
+      const int p0 = pidx(i0);
+      df64 old[R];
+      if constexpr (ASYNC) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) old[r] = a.zero_old ? vzero<df64>() : B[p0 + r];
+      } else {  // c_j through registers: rho's operand now, the next interval's A after the barrier
+#pragma unroll
+        for (int r = 0; r < R; r += 2) {
+          const df2 o = a.zero_old ? df2{} : ldcg_df2(oldd + i0 + r);
+          old[r] = o.a;
+          old[r + 1] = o.b;
+        }
+      }
+      df64 v[R];
+      if (runA) {
+        fixed_chunk<df64, R, SPAN>(t, A, i0, nx, v);
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = vzero<df64>();
+      }
+#pragma unroll
+      for (int r = 0; r < R; r += 2) st_df2(cnd + i0 + r, v[r], v[r + 1]);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        nzb |= __float_as_uint(old[r].hi);
+        if constexpr (!ASYNC) B[p0 + r] = old[r];
+        const float rho = df_sub_f(v[r], old[r]);
+        f0[p0 + r] = rho;
+        nzr |= __float_as_uint(rho);
+      }
+    }
+    const bool runB = __syncthreads_or(nzb & 0x7fffffff);  // A is free from here on; B holds c_j
+    const bool run2 = __syncthreads_or(nzr & 0x7fffffff);
+    if constexpr (ASYNC)
+      if (j + 1 < j1 && !a.zero_old) slab_async(const_cast<df64*>(A), cold + (long long)(j + 1) * a.cstride, nx);
+    if (j < N) {
+      float* rr = a.r_f + (long long)(j + 1) * nx;
+      float ss = 0.0f;
+      for (int i0 = threadIdx.x * R; i0 < nx; i0 += blockDim.x * R) {
+        float v[R];
+        if (run2) {
+          fixed_chunk<float, R, SPAN>(t, f0, i0, nx, v);
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[r] = 0.0f;
+        }
+        *reinterpret_cast<float4*>(rr + i0) = make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4*>(rr + i0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) ss = fmaf(v[r], v[r], ss);
+      }
+      if (a.partial) {
+        const double tot = block_sum((double)ss);  // its barriers also retire this pass's reads of rho
+        if (threadIdx.x == 0) a.partial[j] = tot;
+      }
+    }
+    __syncthreads();  // rho (f0) is read; the next interval overwrites f0 and reads A/B swapped
+    runA = runB;
+    cur = 1 - cur;
+  }
+  if constexpr (ASYNC) cp_async_wait_all();
+}
+
+// Register-resident form of the fused body for upwind stencils (offsets
+// -(SPAN-1)..0, ERK1+U1's collapsed Phi^m): one CTA per interval, nx/8
+// threads, each holding its 8 points in registers.  The SPAN-1 points left of
+// a thread's chunk come from the lane below by warp shuffle (lane 0 loads its
+// own from the slab, with the periodic wrap); the rho values the residual
+// pass needs across a warp boundary go through shared memory once.  No slab
+// is staged in shared memory, so neither pass waits on shared-memory loads,
+// and the zero-slab shortcut is a warp vote.  Per output the arithmetic is
+// fcf_body_df_fused's, in the same order: bitwise its results.
+template <int SPAN>
+__global__ void __launch_bounds__(1024) fcf_df_reg_kernel(const FcfArgs a, const DevTaps t) {
+  constexpr int R = 8, H = SPAN - 1;
+  __shared__ float xh[32][H > 0 ? H : 1];  // each warp's last H rho values
+  const int nx = a.nx, j = blockIdx.x + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int i0 = threadIdx.x * R;
+  const df64* xs = reinterpret_cast<const df64*>(a.u_old) + (long long)(j - 1) * a.cstride;
+  const df64* os = reinterpret_cast<const df64*>(a.u_old) + (long long)j * a.cstride;
+  df64 w[R + H], old[R];
+#pragma unroll
+  for (int r = 0; r < R; r += 2) {
+    const df2 v = a.zero_old ? df2{} : ldcg_df2(xs + i0 + r);
+    w[H + r] = v.a;
+    w[H + r + 1] = v.b;
+    const df2 o = a.zero_old ? df2{} : ldcg_df2(os + i0 + r);
+    old[r] = o.a;
+    old[r + 1] = o.b;
+  }
+  unsigned nzw = 0;
+#pragma unroll
+  for (int q = 0; q < H; ++q) {
+    float hi = __shfl_up_sync(0xffffffffu, w[R + q].hi, 1);
+    float lo = __shfl_up_sync(0xffffffffu, w[R + q].lo, 1);
+    if (lane == 0) {  // the chunk left of lane 0's: another warp's (or, periodic, the slab's end)
+      float2 g = make_float2(0.0f, 0.0f);
+      if (!a.zero_old) g = __ldcg(reinterpret_cast<const float2*>(xs) + wrapi(i0 - H + q, nx));
+      hi = g.x;
+      lo = g.y;
+    }
+    w[q] = {hi, lo};
+  }
+#pragma unroll
+  for (int q = 0; q < R + H; ++q) nzw |= __float_as_uint(w[q].hi);
+  df64 v[R];
+  if (__any_sync(0xffffffffu, (nzw & 0x7fffffffu) != 0)) {  // Phi^m 0 = 0
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      df64 acc = df_mul(dense_coef<df64>(t, 0), w[r]);
+#pragma unroll
+      for (int k = 1; k < SPAN; ++k) acc = vfma1<df64>(dense_coef<df64>(t, k), w[r + k], acc, t.one);
+      v[r] = vfinish<df64>(acc);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = vzero<df64>();
+  }
+  df64* cnd = reinterpret_cast<df64*>(a.c_new) + (long long)j * nx;
+#pragma unroll
+  for (int r = 0; r < R; r += 2) st_df2(cnd + i0 + r, v[r], v[r + 1]);
+  float rw[R + H];
+  unsigned nzr = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    rw[H + r] = df_sub_f(v[r], old[r]);
+    nzr |= __float_as_uint(rw[H + r]);
+  }
+  if (j >= a.N) return;  // the last interval has no residual (uniform over the CTA)
+  if (lane == 31)
+#pragma unroll
+    for (int q = 0; q < H; ++q) xh[warp][q] = rw[R + q];
+  __syncthreads();
+  const int wl = warp == 0 ? nw - 1 : warp - 1;  // periodic: warp 0's left neighbour is the last warp
+#pragma unroll
+  for (int q = 0; q < H; ++q) {
+    const float u = __shfl_up_sync(0xffffffffu, rw[R + q], 1);
+    rw[q] = lane == 0 ? xh[wl][q] : u;
+    nzr |= __float_as_uint(rw[q]);
+  }
+  float* rr = a.r_f + (long long)(j + 1) * nx;
+  float o[R];
+  if (__any_sync(0xffffffffu, (nzr & 0x7fffffffu) != 0)) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float acc = dense_coef<float>(t, 0) * rw[r];
+#pragma unroll
+      for (int k = 1; k < SPAN; ++k) acc = vfma1<float>(dense_coef<float>(t, k), rw[r + k], acc, t.one);
+      o[r] = vfinish<float>(acc);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) o[r] = 0.0f;
+  }
+  *reinterpret_cast<float4*>(rr + i0) = make_float4(o[0], o[1], o[2], o[3]);
+  *reinterpret_cast<float4*>(rr + i0 + 4) = make_float4(o[4], o[5], o[6], o[7]);
+  float ss = 0.0f;
+#pragma unroll
+  for (int r = 0; r < R; ++r) ss = fmaf(o[r], o[r], ss);
+  if (a.partial) {
+    const double tot = block_sum((double)ss);
+    if (threadIdx.x == 0) a.partial[j] = tot;
+  }
+}
+
+// Persistent form of the register-resident body: CTA b owns the intervals
+// j0..j1-1 (a balanced split of 1..N).  Interval j+1's input c_j is interval
+// j's old C-point, already in registers, so a run reads each slab from HBM
+// once: the next one, c_{j+1}, is copied into shared memory with 16-byte
+// cp.async while interval j computes (three buffers: c_{j-1} for lane 0's
+// halo, c_j being read, c_{j+1} arriving).  Each thread's 8 points are two
+// 16-byte units pairs; unit u of thread t sits at 4t + (u ^ ((t >> 1) & 3)),
+// so a quarter-warp's 16-byte loads hit 8 distinct bank groups.  The norm
+// is one fixed-order block reduction per run, stored at partial[j0] (zeros
+// at the run's other intervals): the sum the norm kernel forms is the same
+// quantity, in another order.  Arithmetic per output: fcf_body_df_fused's.
+__device__ __forceinline__ int swz_unit(int t, int u) { return 4 * t + (u ^ ((t >> 1) & 3)); }
+__device__ __forceinline__ df64 swz_load(const df64* buf, int e) {  // element e of a swizzled slab
+  const int t = e >> 3, r = e & 7;
+  return buf[2 * swz_unit(t, r >> 1) + (r & 1)];
+}
+
+template <int SPAN>
+__global__ void __launch_bounds__(1024) fcf_df_regrun_kernel(const FcfArgs a, const DevTaps t) {
+  constexpr int R = 8, H = SPAN - 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ float xh[32][H > 0 ? H : 1];
+  const int nx = a.nx, N = a.N, G = gridDim.x, b = blockIdx.x;
+  const int j0 = 1 + (int)((long long)b * N / G), j1 = 1 + (int)((long long)(b + 1) * N / G);
+  if (j0 >= j1) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int i0 = tid * R;
+  df64* const B0 = reinterpret_cast<df64*>(smraw);  // buffer (j mod 3) at B0 + (j mod 3) nx
+  const df64* cold = reinterpret_cast<const df64*>(a.u_old);
+  auto prefetch = [&](int jj) {  // c_jj into its buffer: this thread's own 4 units
+    df64* dst = B0 + (long long)(jj % 3) * nx;
+    const df64* src = cold + (long long)jj * a.cstride + i0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const unsigned d = (unsigned)__cvta_generic_to_shared(dst + 2 * swz_unit(tid, u));
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src + 2 * u) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  df64 cur[R];  // c_{j-1} of this thread's chunk
+  if (a.zero_old) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) cur[r] = vzero<df64>();
+  } else {
+    prefetch(j0 - 1);
+    prefetch(j0);
+#pragma unroll
+    for (int r = 0; r < R; r += 2) {
+      const df2 v = ldcg_df2(cold + (long long)(j0 - 1) * a.cstride + i0 + r);
+      cur[r] = v.a;
+      cur[r + 1] = v.b;
+    }
+  }
+  float ss = 0.0f;
+  for (int j = j0; j < j1; ++j) {
+    if (!a.zero_old) asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();  // c_j (and c_{j-1}) complete; last interval's halo reads of the buffer reused below are done
+    if (!a.zero_old && j + 1 < j1) prefetch(j + 1);
+    const df64* Bj = B0 + (long long)(j % 3) * nx;
+    const df64* Bp = B0 + (long long)((j + 2) % 3) * nx;  // c_{j-1}
+    df64 old[R];
+    if (a.zero_old) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) old[r] = vzero<df64>();
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 q = *reinterpret_cast<const float4*>(Bj + 2 * swz_unit(tid, u));
+        old[2 * u] = {q.x, q.y};
+        old[2 * u + 1] = {q.z, q.w};
+      }
+    }
+    df64 w[R + H];
+#pragma unroll
+    for (int r = 0; r < R; ++r) w[H + r] = cur[r];
+    unsigned nzw = 0;
+#pragma unroll
+    for (int q = 0; q < H; ++q) {
+      float hi = __shfl_up_sync(0xffffffffu, cur[R - H + q].hi, 1);
+      float lo = __shfl_up_sync(0xffffffffu, cur[R - H + q].lo, 1);
+      if (lane == 0) {  // the chunk left of lane 0's: another warp's, or (periodic) the slab's end
+        const df64 g = a.zero_old ? vzero<df64>() : swz_load(Bp, wrapi(i0 - H + q, nx));
+        hi = g.hi;
+        lo = g.lo;
+      }
+      w[q] = {hi, lo};
+    }
+#pragma unroll
+    for (int q = 0; q < R + H; ++q) nzw |= __float_as_uint(w[q].hi);
+    df64 v[R];
+    if (__any_sync(0xffffffffu, (nzw & 0x7fffffffu) != 0)) {  // Phi^m 0 = 0
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        df64 acc = df_mul(dense_coef<df64>(t, 0), w[r]);
+#pragma unroll
+        for (int k = 1; k < SPAN; ++k) acc = vfma1<df64>(dense_coef<df64>(t, k), w[r + k], acc, t.one);
+        v[r] = vfinish<df64>(acc);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = vzero<df64>();
+    }
+    df64* cnd = reinterpret_cast<df64*>(a.c_new) + (long long)j * nx;
+#pragma unroll
+    for (int r = 0; r < R; r += 2) st_df2(cnd + i0 + r, v[r], v[r + 1]);
+    float rw[R + H];
+    unsigned nzr = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      rw[H + r] = df_sub_f(v[r], old[r]);
+      nzr |= __float_as_uint(rw[H + r]);
+      cur[r] = old[r];
+    }
+    if (j < N) {  // uniform over the CTA
+      if (lane == 31)
+#pragma unroll
+        for (int q = 0; q < H; ++q) xh[warp][q] = rw[R + q];
+      __syncthreads();
+      const int wl = warp == 0 ? nw - 1 : warp - 1;
+#pragma unroll
+      for (int q = 0; q < H; ++q) {
+        const float u = __shfl_up_sync(0xffffffffu, rw[R + q], 1);
+        rw[q] = lane == 0 ? xh[wl][q] : u;
+        nzr |= __float_as_uint(rw[q]);
+      }
+      float* rr = a.r_f + (long long)(j + 1) * nx;
+      float o[R];
+      if (__any_sync(0xffffffffu, (nzr & 0x7fffffffu) != 0)) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          float acc = dense_coef<float>(t, 0) * rw[r];
+#pragma unroll
+          for (int k = 1; k < SPAN; ++k) acc = vfma1<float>(dense_coef<float>(t, k), rw[r + k], acc, t.one);
+          o[r] = vfinish<float>(acc);
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) o[r] = 0.0f;
+      }
+      *reinterpret_cast<float4*>(rr + i0) = make_float4(o[0], o[1], o[2], o[3]);
+      *reinterpret_cast<float4*>(rr + i0 + 4) = make_float4(o[4], o[5], o[6], o[7]);
+#pragma unroll
+      for (int r = 0; r < R; ++r) ss = fmaf(o[r], o[r], ss);
+      if (a.partial && tid == 0 && j > j0) a.partial[j] = 0.0;
+    }
+  }
+  if (a.partial && j0 < N) {
+    const double tot = block_sum((double)ss);
+    if (tid == 0) a.partial[j0] = tot;
+  }
+  if (!a.zero_old) asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 // PREC 3: pass 1 (C-point update and residual rho) in float-float, pass 2 in
 // FP32.  A df64 slab occupies as many bytes as an FP64 slab.
 template <int R, int SPAN = 0, bool TR = false, bool FUSE = true>
@@ -1295,6 +1675,13 @@ cudaError_t launch_check(const double* norm2, CheckState* st, unsigned long long
 }
 
 static int g_tile = 8;  // register tile of the stencil (0 = one tap at a time)
+// fused float-float FCF (MGRIT_FCF_STREAM): 1 register-resident runs of
+// intervals per CTA with cp.async prefetch (default, upwind stencils); 4
+// register-resident, one interval per CTA; 0 one interval per CTA with the slab
+// in shared memory; 2, 3 runs with the slabs in shared memory (through
+// registers or cp.async)
+static int g_stream_fused = 1;
+void set_stream_fused(int mode) { g_stream_fused = mode >= 0 && mode <= 4 ? mode : 1; }
 
 void set_tile(int r) { g_tile = (r == 4 || r == 8) ? r : 0; }
 int get_tile() { return g_tile; }
@@ -1348,8 +1735,62 @@ static bool host_fused_ok(const FcfArgs& a, const DevTaps& t, int threads) {
          (a.cstride & 1) == 0;
 }
 
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = 152;
+    }
+  }
+  return n;
+}
+
+// Shared memory of the streaming fused body: two float-float slabs and one
+// FP32 slab, padded.
+static size_t stream_smem(int nx) { return (size_t)padded_len(nx) * (2 * sizeof(double) + sizeof(float)); }
+
+// The streaming fused body: two CTAs per SM where their slabs fit (one for
+// nx above about 5000), each a balanced run of intervals, 512 threads (or
+// fewer, so that nx is a multiple of 8 per thread).
+template <int SPAN>
+static cudaError_t launch_fcf_stream(const FcfArgs& a, const DevTaps& t, cudaStream_t s) {
+  int th = 512;
+  while (th > 32 && a.nx % (8 * th) != 0) th >>= 1;
+  if (a.nx % (8 * th) != 0) return cudaErrorInvalidValue;
+  const size_t smem = stream_smem(a.nx);
+  auto kern = g_stream_fused == 3 ? fcf_df_stream_kernel<SPAN, true> : fcf_df_stream_kernel<SPAN, false>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  const int per_sm = 2 * smem <= (size_t)kMaxSmemBytes ? 2 : 1;
+  const int grid = a.N < per_sm * sm_count() ? a.N : per_sm * sm_count();
+  kern<<<grid, th, smem, s>>>(a, t);
+  return cudaGetLastError();
+}
+
 template <int SPAN>
 static cudaError_t launch_fcf_fused(const FcfArgs& a, const DevTaps& t, int threads, cudaStream_t s) {
+  const bool upwind = t.lo == -(SPAN - 1) && t.hi == 0 && a.nx % 256 == 0 && a.nx / 8 <= 1024;
+  if (g_stream_fused == 1 && upwind && 3 * (size_t)a.nx * sizeof(double) <= (size_t)kMaxSmemBytes - 1024) {
+    const size_t smem = 3 * (size_t)a.nx * sizeof(double);
+    cudaError_t e = set_smem(fcf_df_regrun_kernel<SPAN>, smem);
+    if (e != cudaSuccess) return e;
+    const int th = a.nx / 8;
+    int per_sm = (int)(((size_t)kMaxSmemBytes) / (smem + 1024));
+    per_sm = per_sm < 2048 / th ? per_sm : 2048 / th;             // threads per SM
+    per_sm = per_sm < 65536 / (64 * th) ? per_sm : 65536 / (64 * th);  // 64 registers per thread
+    per_sm = per_sm < 1 ? 1 : per_sm;
+    const int grid = a.N < per_sm * sm_count() ? a.N : per_sm * sm_count();
+    fcf_df_regrun_kernel<SPAN><<<grid, th, smem, s>>>(a, t);
+    return cudaGetLastError();
+  }
+  if (g_stream_fused == 4 && upwind) {
+    fcf_df_reg_kernel<SPAN><<<a.N, a.nx / 8, 0, s>>>(a, t);
+    return cudaGetLastError();
+  }
+  if (g_stream_fused >= 2 && stream_smem(a.nx) <= (size_t)kMaxSmemBytes) return launch_fcf_stream<SPAN>(a, t, s);
   FcfArgs f = a;
   f.fused = 1;
   const size_t smem = (size_t)padded_len(a.nx) * (sizeof(double) + sizeof(float));

@@ -1,17 +1,21 @@
 // Continuous-batching MGRIT server (mgrit_server_create / mgrit_submit /
 // mgrit_poll / mgrit_server_destroy).
 //
-// A host worker thread owns one CUDA stream.  Each turn it
-//   1. admits queued requests, first come first served, while their device
-//      state fits in the HBM budget and fewer than max_active are running
-//      (fitted coarse operators are cached per problem/options);
-//   2. advances every admitted solve by one MGRIT cycle: one batched
-//      FCF-relaxation launch per nx over all intervals of all solves, one
-//      batched norm launch, one read-back of all norms, then the coarse solves
-//      (one batched cluster march per cluster size for two-level periodic
-//      solves; the handle's own coarse kernels for multilevel, rediscretised
-//      and inflow/outflow ones);
-//   3. retires converged (or failed) solves: copies their output to host
+// A host worker thread owns one CUDA stream for the cycles and one for
+// set-up copies.  Each turn it
+//   1. queues one MGRIT cycle of every admitted solve: one batched
+//      FCF-relaxation launch per (nx, launch shape) over all intervals of all
+//      those solves, one batched norm launch and one read-back of all norms;
+//   2. while the GPU runs them, admits queued requests, first come first
+//      served, while their device state fits in the HBM budget and fewer than
+//      max_active are running (coarse operators fitted by planner threads as
+//      requests arrive; set-up copies and initial residuals on the upload
+//      stream); they join at the next turn;
+//   3. after the one synchronisation of the turn takes the stopping decisions
+//      and queues the coarse solves (one batched cluster march per cluster
+//      size for two-level periodic solves; the handle's own coarse kernels for
+//      multilevel, rediscretised and inflow/outflow ones);
+//   4. retires converged (or failed) solves: copies their output to host
 //      memory, frees their device state, and wakes pollers.
 // Requests that arrive while others run join at the next turn, so their work
 // overlaps on the device with the solves already in flight.  Per-solve
@@ -53,6 +57,7 @@ struct Request {
   mgrit_result res{};
   std::vector<double> out;
   mgrit_handle* h = nullptr;
+  int slot = -1;  // its two stencils' place in the server's device tap table
   int cur = 0, it = 0;
   double r0 = 0.0, t_submit = 0.0;
   size_t bytes = 0;
@@ -63,6 +68,31 @@ struct PlanKey {
   double cfl, eta, rho;
   bool operator<(const PlanKey& o) const {
     return std::memcmp(this, &o, sizeof(PlanKey)) < 0;
+  }
+};
+
+// Pinned host staging for a descriptor array (an asynchronous copy from
+// pageable memory would first wait for the stream to drain).
+template <typename T>
+struct PinnedArray {
+  T* p = nullptr;
+  size_t cap = 0;
+  bool reserve(size_t n) {
+    if (n <= cap) return true;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = std::max<size_t>(n, 2 * cap);
+    if (cudaMallocHost(&p, cap * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      cap = 0;
+      return false;
+    }
+    return true;
+  }
+  void free() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
   }
 };
 
@@ -126,6 +156,25 @@ struct mgrit_server {
   std::string fatal;
   mgrit_server_counters stats{};
   double active_sum = 0.0;
+  // phase boundaries of a cycle: 0 FCF start, 1 FCF end, 2 norms end, 4 coarse
+  // start, 3 coarse end (read at the next cycle's synchronisation)
+  cudaEvent_t ev[5] = {};
+  int device = 0;          // the creating thread's device; the worker runs on it
+  // Device tap table: slot k holds the fine stencil (2k) and the coarse one
+  // (2k+1) of an active solve, uploaded once at admission
+  DevTaps* taps = nullptr;
+  int slots = 0;
+  std::vector<int> free_slots;
+  // pinned staging: the outputs of the solves retired together, the cycle's
+  // descriptors
+  PinnedArray<double> stage;
+  PinnedArray<BatchSolve> hS;
+  PinnedArray<BatchItem> hItems;
+  PinnedArray<int> hIds;
+  double t_created = 0.0;
+  bool cycled = false;     // ev[3] holds the previous cycle's end
+  cudaStream_t upload = nullptr;    // admissions: set-up copies and initial residuals, beside the cycles
+  cudaStream_t download = nullptr;  // retirements: output copies, beside the cycles
 };
 
 static PlanKey key_of(const mgrit_problem& p, const mgrit_opts& o) {
@@ -145,6 +194,8 @@ static void finish(mgrit_server* S, Request* r, mgrit_status st, const std::stri
     r->h = nullptr;
     S->resident -= std::min(S->resident, r->bytes);
   }
+  if (r->slot >= 0) S->free_slots.push_back(r->slot);
+  r->slot = -1;
   if (st == MGRIT_OK) S->stats.completed++;
   else S->stats.failed++;
   r->res.solve_s = now_s() - r->t_submit;
@@ -172,7 +223,9 @@ static std::vector<Request*> admit(mgrit_server* S, std::unique_lock<std::mutex>
     S->resident += r->bytes;
     const std::vector<CoarseOp>* cached = &itp->second.ops;
     lk.unlock();
-    mgrit_status st = handle_create(&r->prob, &r->opts, S->stream, cached, &r->h, false, true);
+    // set up on the upload stream, so that its copies (some from pageable
+    // memory) and initial residual run beside the cycle the GPU is running
+    mgrit_status st = handle_create(&r->prob, &r->opts, S->upload, cached, &r->h, false, true);
     if (st == MGRIT_OK) S->stats.tune_s += r->h->tune_s;
     std::string msg = st == MGRIT_OK ? "" : mgrit_last_error();
     if (st == MGRIT_OK) {
@@ -194,15 +247,35 @@ static std::vector<Request*> admit(mgrit_server* S, std::unique_lock<std::mutex>
       S->cv.notify_all();
       continue;
     }
+    if (S->free_slots.empty()) {
+      lk.unlock();
+      mgrit_destroy(r->h);
+      r->h = nullptr;
+      lk.lock();
+      S->resident -= std::min(S->resident, r->bytes);
+      r->bytes = 0;
+      finish(S, r, MGRIT_ERR_OOM, "server tap table full");
+      S->cv.notify_all();
+      continue;
+    }
+    r->slot = S->free_slots.back();
+    S->free_slots.pop_back();
+    {
+      mgrit_handle* h = r->h;
+      const DevTaps* fine = h->fine_collapse ? &h->dphim : &h->dphi;
+      cudaMemcpyAsync(S->taps + 2 * r->slot, fine, sizeof(DevTaps), cudaMemcpyHostToDevice, S->upload);
+      cudaMemcpyAsync(S->taps + 2 * r->slot + 1, &h->dpsi.back(), sizeof(DevTaps), cudaMemcpyHostToDevice,
+                      S->upload);
+    }
     S->resident = S->resident - std::min(S->resident, r->bytes) + r->h->bytes;
     S->stats.peak_resident_bytes = std::max(S->stats.peak_resident_bytes, (double)S->resident);
     r->bytes = r->h->bytes;
     r->state = 1;
     fresh.push_back(r);
   }
-  if (!fresh.empty()) {  // one sync for the batch: set-up errors and the initial residuals
+  if (!fresh.empty()) {  // one sync of the upload stream for the batch: set-up errors and initial residuals
     lk.unlock();
-    const cudaError_t e = cudaStreamSynchronize(S->stream);
+    const cudaError_t e = cudaStreamSynchronize(S->upload);
     lk.lock();
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -211,16 +284,20 @@ static std::vector<Request*> admit(mgrit_server* S, std::unique_lock<std::mutex>
     for (Request* r : fresh) {
       r->r0 = std::sqrt(r->h->norm_host[0]);
       r->res.r0_norm = r->r0;
+      r->h->stream = S->stream;  // every later launch of the solve is a cycle's
     }
   }
   return fresh;
 }
 
-// One MGRIT cycle for every active solve.  Called without the lock.
-static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std::vector<char>* done) {
+// One MGRIT cycle for every active solve, in two halves around the one
+// synchronisation of the cycle: cycle_front queues the batched FCF, residual
+// and norm launches and the norms' read-back (the worker admits new requests
+// while they run); cycle_back takes the stopping decisions and queues the
+// coarse solves.  Called without the lock.
+static mgrit_status cycle_front(mgrit_server* S, const std::vector<Request*>& act) {
   const int n = (int)act.size();
   std::vector<BatchSolve> hs(n);
-  std::vector<DevTaps> taps(2 * n);
   for (int k = 0; k < n; ++k) {
     mgrit_handle* h = act[k]->h;
     BatchSolve& b = hs[k];
@@ -241,17 +318,15 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     b.fcf.fx = h->fine_collapse ? h->fx_phim : h->fx_phi;  // boundary rows (inflow/outflow problems)
     b.fcf.df_store = h->dfc;
     b.prec = fine_prec(h);
-    b.taps = 2 * k;
-    b.psi = 2 * k + 1;
+    b.taps = 2 * act[k]->slot;
+    b.psi = 2 * act[k]->slot + 1;
     b.cluster = h->march_cluster;
     b.sd = h->dsplan;
-    taps[2 * k] = h->fine_collapse ? h->dphim : h->dphi;
-    taps[2 * k + 1] = h->dpsi.back();
   }
-  if (!S->dS.reserve(n) || !S->dTaps.reserve(2 * n) || !S->dIds.reserve(n) || !S->dNorm.reserve(n))
+  if (!S->dS.reserve(n) || !S->dIds.reserve(n) || !S->dNorm.reserve(n) || !S->hS.reserve(n) || !S->hIds.reserve(n))
     return fail(MGRIT_ERR_OOM, "server batch descriptors");
-  cudaMemcpyAsync(S->dS.p, hs.data(), n * sizeof(BatchSolve), cudaMemcpyHostToDevice, S->stream);
-  cudaMemcpyAsync(S->dTaps.p, taps.data(), 2 * n * sizeof(DevTaps), cudaMemcpyHostToDevice, S->stream);
+  std::memcpy(S->hS.p, hs.data(), n * sizeof(BatchSolve));
+  cudaMemcpyAsync(S->dS.p, S->hS.p, n * sizeof(BatchSolve), cudaMemcpyHostToDevice, S->stream);
   // ---- batched FCF, one launch per (nx, launch shape): each solve keeps the
   // shape it was tuned to, so its arithmetic is the single-solve path's.
   // SDIRK fine levels: one launch per (nx, recurrence orders, precision).
@@ -261,7 +336,7 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     if (h->sdirk)
       sgroups[{h->nx, h->splan.kf, h->splan.kb, hs[k].prec == 0 ? 0 : 1}].push_back(k);
     else
-      groups[{h->nx, h->fine_tile, h->fine_threads, taps[2 * k].span}].push_back(k);
+      groups[{h->nx, h->fine_tile, h->fine_threads, (h->fine_collapse ? h->dphim : h->dphi).span}].push_back(k);
   }
   std::vector<BatchItem> items;
   std::vector<std::pair<size_t, size_t>> ranges, sranges;
@@ -272,14 +347,19 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
         for (int j = 1; j <= hs[k].fcf.N; ++j) items.push_back({k, j});
       (G == &groups ? ranges : sranges).push_back({b0, items.size()});
     }
-  if (!S->dItems.reserve(items.size())) return fail(MGRIT_ERR_OOM, "server batch items");
-  cudaMemcpyAsync(S->dItems.p, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, S->stream);
+  if (!S->dItems.reserve(items.size()) || !S->hItems.reserve(items.size()))
+    return fail(MGRIT_ERR_OOM, "server batch items");
+  std::memcpy(S->hItems.p, items.data(), items.size() * sizeof(BatchItem));
+  const bool timed = S->ev[0] != nullptr;
+  if (timed) cudaEventRecord(S->ev[0], S->stream);
+  if (S->stats.cycles == 0 && S->stats.first_cycle_s == 0.0) S->stats.first_cycle_s = now_s() - S->t_created;
+  cudaMemcpyAsync(S->dItems.p, S->hItems.p, items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice, S->stream);
   size_t gi = 0;
   for (auto& g : groups) {
     const int nx = std::get<0>(g.first), tile = std::get<1>(g.first), th = std::get<2>(g.first);
     const int span = std::get<3>(g.first);
     const auto rg = ranges[gi++];
-    cudaError_t e = launch_fcf_batched(S->dS.p, S->dItems.p + rg.first, (int)(rg.second - rg.first), S->dTaps.p, nx,
+    cudaError_t e = launch_fcf_batched(S->dS.p, S->dItems.p + rg.first, (int)(rg.second - rg.first), S->taps, nx,
                                        th, tile, span, S->stream);
     if (e != cudaSuccess) return launch_ok(e, "fcf_batched");
     for (int k : g.second) act[k]->h->kcount[MGRIT_K_FCF]++;
@@ -294,15 +374,15 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     if (e != cudaSuccess) return launch_ok(e, "fcf_sdirk_batched");
     for (int k : g.second) act[k]->h->kcount[MGRIT_K_FCF]++;
   }
+  if (timed) cudaEventRecord(S->ev[1], S->stream);
   // ---- value-form residuals of the FP64 solves (no-op for the others)
   {
     cudaError_t e = launch_residual_value_batched(S->dS.p, S->dItems.p, (int)items.size(), S->stream);
     if (e != cudaSuccess) return launch_ok(e, "residual_value_batched");
   }
   // ---- norms of all solves, one read-back
-  std::vector<int> ids(n);
-  for (int k = 0; k < n; ++k) ids[k] = k;
-  cudaMemcpyAsync(S->dIds.p, ids.data(), n * sizeof(int), cudaMemcpyHostToDevice, S->stream);
+  for (int k = 0; k < n; ++k) S->hIds.p[k] = k;
+  cudaMemcpyAsync(S->dIds.p, S->hIds.p, n * sizeof(int), cudaMemcpyHostToDevice, S->stream);
   cudaError_t e = launch_norm_batched(S->dS.p, S->dIds.p, n, S->dNorm.p, S->stream);
   if (e != cudaSuccess) return launch_ok(e, "norm_batched");
   if ((size_t)n > S->hNormCap) {
@@ -315,9 +395,26 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
       return fail(MGRIT_ERR_OOM, "pinned norms");
     }
   }
+  if (timed) cudaEventRecord(S->ev[2], S->stream);
   cudaMemcpyAsync(S->hNorm, S->dNorm.p, n * sizeof(double), cudaMemcpyDeviceToHost, S->stream);
-  e = cudaStreamSynchronize(S->stream);
+  return MGRIT_OK;
+}
+
+static mgrit_status cycle_back(mgrit_server* S, const std::vector<Request*>& act, std::vector<char>* done) {
+  const int n = (int)act.size();
+  const bool timed = S->ev[0] != nullptr;
+  cudaError_t e = cudaStreamSynchronize(S->stream);
   if (e != cudaSuccess) return launch_ok(e, "server cycle");
+  if (timed) {
+    float a = 0.0f, b = 0.0f, g = 0.0f;
+    if (cudaEventElapsedTime(&a, S->ev[0], S->ev[1]) == cudaSuccess) S->stats.gpu_fcf_ms += a;
+    if (cudaEventElapsedTime(&b, S->ev[1], S->ev[2]) == cudaSuccess) S->stats.gpu_norm_ms += b;
+    if (S->cycled && cudaEventElapsedTime(&g, S->ev[3], S->ev[0]) == cudaSuccess) S->stats.gpu_gap_ms += g;
+    float c = 0.0f;
+    if (S->cycled && cudaEventElapsedTime(&c, S->ev[4], S->ev[3]) == cudaSuccess) S->stats.gpu_coarse_ms += c;
+    cudaGetLastError();
+  }
+  if (timed) cudaEventRecord(S->ev[4], S->stream);
   // ---- convergence decisions (Section 2.2 stopping test, per solve)
   std::vector<int> two_level;
   std::map<int, std::vector<int>> by_cluster;
@@ -344,7 +441,14 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
       by_cluster[r->h->march_cluster].push_back(k);
     }
   }
-  // ---- coarse solves: batched cluster marches (two-level), V-cycles (multilevel)
+  // ---- coarse solves: batched cluster marches (two-level), V-cycles (multilevel);
+  // each group's solve ids at their own offset, so no group waits for another
+  {
+    size_t tot = 0;
+    for (auto& g : by_cluster) tot += g.second.size();
+    if (!S->dIds.reserve(std::max<size_t>(tot, (size_t)n))) return fail(MGRIT_ERR_OOM, "server batch ids");
+  }
+  size_t id_off = 0;
   for (auto& g : by_cluster) {
     int max_w = 0, max_halo = 0;
     for (int k : g.second) {
@@ -352,14 +456,12 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
       max_w = std::max(max_w, h->nx / g.first);
       max_halo = std::max(max_halo, h->dpsi.back().hi - h->dpsi.back().lo);
     }
-    cudaMemcpyAsync(S->dIds.p, g.second.data(), g.second.size() * sizeof(int), cudaMemcpyHostToDevice, S->stream);
-    e = launch_march_batched(S->dS.p, S->dIds.p, (int)g.second.size(), S->dTaps.p, g.first, max_w, max_halo,
-                             S->stream);
+    int* ids = S->dIds.p + id_off;
+    id_off += g.second.size();
+    cudaMemcpyAsync(ids, g.second.data(), g.second.size() * sizeof(int), cudaMemcpyHostToDevice, S->stream);
+    e = launch_march_batched(S->dS.p, ids, (int)g.second.size(), S->taps, g.first, max_w, max_halo, S->stream);
     if (e != cudaSuccess) return launch_ok(e, "march_batched");
     for (int k : g.second) act[k]->h->kcount[MGRIT_K_MARCH]++;
-    // the ids buffer is reused by the next group: keep launches ordered
-    e = cudaStreamSynchronize(S->stream);
-    if (e != cudaSuccess) return launch_ok(e, "march_batched");
   }
   for (int k = 0; k < n; ++k) {
     Request* r = act[k];
@@ -376,33 +478,73 @@ static mgrit_status cycle(mgrit_server* S, const std::vector<Request*>& act, std
     r->cur = 1 - r->cur;
     r->it++;
   }
+  if (timed) {
+    cudaEventRecord(S->ev[3], S->stream);  // read at the next cycle's synchronisation (or at exit)
+    S->cycled = true;
+  }
   return MGRIT_OK;
 }
 
-static void retire(mgrit_server* S, Request* r) {
-  mgrit_handle* h = r->h;
-  if (r->status == MGRIT_OK || r->status == MGRIT_ERR_NOT_CONVERGED) {
-    const size_t rows = r->opts.output == MGRIT_OUT_FINAL ? 1
-                        : r->opts.output == MGRIT_OUT_CPOINTS ? (size_t)h->Nl[1] + 1
-                                                              : (size_t)h->nt + 1;
-    r->out.assign(rows * h->nx, 0.0);
-    mgrit_status st = write_output(h, h->c[1 - r->cur], r->out.data());
-    if (st == MGRIT_OK && cudaStreamSynchronize(S->stream) != cudaSuccess) st = MGRIT_ERR_CUDA;
+// Retire solves together, without the lock: their outputs come back through
+// one pinned staging area on the download stream with one synchronisation, while
+// the cycle stream runs the next cycle; then their device state is released
+// (stream-ordered frees behind that cycle).  Nothing of the next cycle touches
+// a retired solve's buffers.
+static void retire_batch(mgrit_server* S, const std::vector<Request*>& done) {
+  auto rows_of = [](const Request* r) {
+    const mgrit_handle* h = r->h;
+    return r->opts.output == MGRIT_OUT_FINAL ? (size_t)1
+           : r->opts.output == MGRIT_OUT_CPOINTS ? (size_t)h->Nl[1] + 1 : (size_t)h->nt + 1;
+  };
+  auto wants = [](const Request* r) { return r->status == MGRIT_OK || r->status == MGRIT_ERR_NOT_CONVERGED; };
+  std::vector<size_t> off(done.size(), 0);
+  size_t total = 0;
+  for (size_t k = 0; k < done.size(); ++k)
+    if (wants(done[k])) {
+      off[k] = total;
+      total += rows_of(done[k]) * done[k]->h->nx;
+    }
+  const bool staged = S->stage.reserve(std::max<size_t>(total, 1));
+  for (size_t k = 0; k < done.size(); ++k) {
+    Request* r = done[k];
+    if (!wants(r)) continue;
+    mgrit_handle* h = r->h;
+    h->stream = S->download;
+    mgrit_status st = staged ? write_output(h, h->c[1 - r->cur], S->stage.p + off[k])
+                             : fail(MGRIT_ERR_OOM, "pinned output staging");
+    h->stream = S->stream;
     if (st != MGRIT_OK) {
       r->status = st;
       r->error = mgrit_last_error();
     }
   }
-  collect_stats(h, &r->res);
-  mgrit_destroy(h);  // device state released here, accounted under the lock by the caller
-  r->h = nullptr;
-  r->res.solve_s = now_s() - r->t_submit;
-  r->res.dof_per_s = r->res.solve_s > 0 ? (double)r->prob.nx * r->prob.nt / r->res.solve_s : 0.0;
+  const cudaError_t e = cudaStreamSynchronize(S->download);
+  for (size_t k = 0; k < done.size(); ++k) {
+    Request* r = done[k];
+    mgrit_handle* h = r->h;
+    if (wants(r)) {
+      if (e != cudaSuccess) {
+        r->status = MGRIT_ERR_CUDA;
+        r->error = cudaGetErrorString(e);
+      } else {
+        const double* src = S->stage.p + off[k];
+        r->out.assign(src, src + rows_of(r) * h->nx);
+      }
+    }
+    collect_stats(h, &r->res);
+    mgrit_destroy(h);  // device state released here, accounted under the lock by publish
+    r->h = nullptr;
+    r->res.solve_s = now_s() - r->t_submit;
+    r->res.dof_per_s = r->res.solve_s > 0 ? (double)r->prob.nx * r->prob.nt / r->res.solve_s : 0.0;
+  }
+  if (e != cudaSuccess) cudaGetLastError();
 }
 
 // Under the lock: a retired request becomes visible to pollers.
 static void publish(mgrit_server* S, Request* r) {
   S->resident -= std::min(S->resident, r->bytes);
+  if (r->slot >= 0) S->free_slots.push_back(r->slot);
+  r->slot = -1;
   if (r->status == MGRIT_OK) S->stats.completed++;
   else S->stats.failed++;
   r->state = 2;
@@ -441,12 +583,52 @@ static void planner_main(mgrit_server* S) {
 
 static void worker_main(mgrit_server* S) {
   std::unique_lock<std::mutex> lk(S->mu);
+  if (cudaSetDevice(S->device) != cudaSuccess) {
+    cudaGetLastError();
+    S->fatal = "cudaSetDevice failed in the server worker";
+  }
   if (!S->stream) {
     if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
       S->fatal = "cudaStreamCreate failed";
     }
   }
+  // the side streams run at the device's highest priority: their small
+  // kernels (initial residuals, float-float output conversions) are scheduled
+  // ahead of the pending CTAs of a running cycle instead of behind all of them
+  int lo_prio = 0, hi_prio = 0;
+  if (cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) != cudaSuccess) {
+    cudaGetLastError();
+    hi_prio = 0;
+  }
+  if (cudaStreamCreateWithPriority(&S->upload, cudaStreamNonBlocking, hi_prio) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&S->download, cudaStreamNonBlocking, hi_prio) != cudaSuccess) {
+    cudaGetLastError();
+    S->fatal = "cudaStreamCreate failed (side streams)";
+  }
+  bool evs = true;
+  for (auto& ev : S->ev)
+    if (cudaEventCreate(&ev) != cudaSuccess) {
+      cudaGetLastError();
+      ev = nullptr;
+      evs = false;
+    }
+  if (!evs)  // phase timing off
+    for (auto& ev : S->ev) {
+      if (ev) cudaEventDestroy(ev);
+      ev = nullptr;
+    }
+  const int slots = S->o.max_active > 0 ? S->o.max_active : 4096;
+  if (cudaMalloc(&S->taps, 2 * (size_t)slots * sizeof(DevTaps)) != cudaSuccess) {
+    cudaGetLastError();
+    S->taps = nullptr;
+    S->fatal = "server tap table: cudaMalloc failed";
+  } else {
+    S->slots = slots;
+    for (int k = slots - 1; k >= 0; --k) S->free_slots.push_back(k);
+  }
+  bool queued = false;  // the active set's next cycle_front is already on the stream
+  mgrit_status queued_status = MGRIT_OK;
   while (!S->stop) {
     if (!S->fatal.empty()) {
       for (Request* r : S->queue) finish(S, r, MGRIT_ERR_CUDA, S->fatal);
@@ -455,21 +637,32 @@ static void worker_main(mgrit_server* S) {
       S->cv.wait(lk, [&] { return S->stop || !S->queue.empty(); });
       continue;
     }
-    const double ta = now_s();
-    std::vector<Request*> fresh = admit(S, lk);
-    S->stats.admit_s += now_s() - ta;
-    for (Request* r : fresh) S->active.push_back(r);
-    if (S->active.empty()) {
-      S->cv.notify_all();
-      S->cv.wait(lk, [&] { return S->stop || head_ready(S); });
+    if (S->active.empty()) {  // nothing running: admit, then cycle
+      queued = false;
+      const double ta = now_s();
+      std::vector<Request*> fresh = admit(S, lk);
+      S->stats.admit_s += now_s() - ta;
+      for (Request* r : fresh) S->active.push_back(r);
+      if (S->active.empty()) {
+        S->cv.notify_all();
+        S->cv.wait(lk, [&] { return S->stop || head_ready(S); });
+      }
       continue;
     }
     std::vector<Request*> act = S->active;
     lk.unlock();
-    std::vector<char> done(act.size(), 0);
     const double tc = now_s();
-    mgrit_status st = cycle(S, act, &done);
-    const double tr = now_s();
+    mgrit_status st = queued ? queued_status : cycle_front(S, act);
+    queued = false;
+    // admit while the GPU runs the cycle's relaxation (set-up on the upload stream)
+    lk.lock();
+    const double ta = now_s();
+    std::vector<Request*> fresh = admit(S, lk);
+    const double admit_dt = now_s() - ta;
+    S->stats.admit_s += admit_dt;
+    lk.unlock();
+    std::vector<char> done(act.size(), 0);
+    if (st == MGRIT_OK) st = cycle_back(S, act, &done);
     std::string msg = st == MGRIT_OK ? "" : mgrit_last_error();
     if (st != MGRIT_OK)
       for (size_t k = 0; k < act.size(); ++k) {
@@ -477,22 +670,33 @@ static void worker_main(mgrit_server* S) {
         act[k]->status = st;
         act[k]->error = msg;
       }
-    for (size_t k = 0; k < act.size(); ++k)
-      if (done[k]) retire(S, act[k]);
+    std::vector<Request*> next, finished;
+    for (size_t k = 0; k < act.size(); ++k) (done[k] ? finished : next).push_back(act[k]);
+    for (Request* r : fresh) next.push_back(r);
+    // queue the next cycle's relaxation behind this cycle's coarse solves before
+    // retiring, so the GPU is not idle while the host copies outputs out
+    if (!next.empty() && st == MGRIT_OK) {
+      queued_status = cycle_front(S, next);
+      queued = true;
+    }
+    const double tr = now_s();
+    retire_batch(S, finished);
     const double te = now_s();
     lk.lock();
-    for (size_t k = 0; k < act.size(); ++k)
-      if (done[k]) publish(S, act[k]);
+    for (Request* r : finished) publish(S, r);
     S->stats.cycles++;
-    S->stats.cycle_s += tr - tc;
+    S->stats.cycle_s += tr - tc - admit_dt;
     S->stats.retire_s += te - tr;
     S->active_sum += (double)act.size();
     S->stats.mean_active = S->active_sum / (double)S->stats.cycles;
-    std::vector<Request*> keep;
-    for (size_t k = 0; k < act.size(); ++k)
-      if (!done[k]) keep.push_back(act[k]);
-    S->active.swap(keep);
+    S->active.swap(next);
     S->cv.notify_all();
+  }
+  if (S->ev[0] && S->cycled) {  // the last cycle's coarse solves
+    float c = 0.0f;
+    if (cudaEventSynchronize(S->ev[3]) == cudaSuccess && cudaEventElapsedTime(&c, S->ev[4], S->ev[3]) == cudaSuccess)
+      S->stats.gpu_coarse_ms += c;
+    cudaGetLastError();
   }
   // drain: everything still queued or active fails with TIMEOUT-free cancellation
   for (Request* r : S->active) finish(S, r, MGRIT_ERR_CUDA, "server destroyed");
@@ -508,7 +712,12 @@ extern "C" mgrit_status mgrit_server_create(const mgrit_server_opts* sopts, void
   if (!sopts || !(sopts->hbm_budget_bytes > 0.0) || sopts->max_active < 0)
     return fail(MGRIT_ERR_INVALID, "server options need hbm_budget_bytes > 0 and max_active >= 0");
   mgrit_server* S = new mgrit_server();
+  if (cudaGetDevice(&S->device) != cudaSuccess) {
+    cudaGetLastError();
+    S->device = 0;
+  }
   S->o = *sopts;
+  S->t_created = now_s();
   S->stream = (cudaStream_t)stream;
   S->worker = std::thread(worker_main, S);
   const unsigned hc = std::thread::hardware_concurrency();
@@ -616,6 +825,16 @@ extern "C" void mgrit_server_destroy(mgrit_server* S) {
     if (t.joinable()) t.join();
   for (auto& kv : S->reqs) delete kv.second;
   S->reqs.clear();
+  for (auto& ev : S->ev)
+    if (ev) cudaEventDestroy(ev);
+  if (S->stream) cudaStreamSynchronize(S->stream);
+  if (S->taps) cudaFree(S->taps);
+  S->stage.free();
+  S->hS.free();
+  S->hItems.free();
+  S->hIds.free();
+  if (S->upload) cudaStreamDestroy(S->upload);
+  if (S->download) cudaStreamDestroy(S->download);
   S->dS.free();
   S->dItems.free();
   S->dTaps.free();

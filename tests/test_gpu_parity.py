@@ -373,3 +373,43 @@ def test_f_relaxation_mixed_reaches_the_fp64_fixed_point(capi):
         res, out, _ = gpu_run(capi, fam, p, c, nx, nt, m, L, "auto", u0, precision=prec, relax="F")
         assert res.converged == 1 and abs(res.iterations - it64) <= 1
         assert rel(out, ref[::m]) <= 1e-9
+
+
+@pytest.mark.parametrize("nx,nt,m,L", [(4096, 16384, 4, 4), (512, 2048, 4, 2), (8192, 1024, 4, 3), (1024, 64, 4, 2),
+                                       (2048, 8192, 4, 3)])
+def test_fused_float_float_fcf_forms_agree(capi, monkeypatch, nx, nt, m, L):
+    """The fused float-float FCF (ERK1+U1, m = 4: collapsed Phi^4 of 5 taps) in
+    its five forms -- the slab in shared memory, one interval per CTA (0);
+    register-resident runs of intervals per CTA with the next slab prefetched
+    (1, the default); runs with the slabs in shared memory, streamed through
+    registers (2) or with cp.async copies (3); register-resident, one interval
+    per CTA (4) -- give the same solve
+    (bitwise C-points, the same iterations) and the same relaxation sweeps,
+    from the zero iterate (zero slabs) and from a converged one; grids from
+    one interval per CTA (nt/m = 16) to runs of about 14."""
+    import torch
+    u0 = torch.tensor(workloads.fourier_field(nx), device="cuda")
+    got = {}
+    for stream in ("0", "1", "2", "3", "4"):
+        monkeypatch.setenv("MGRIT_FCF_STREAM", stream)
+        monkeypatch.setenv("MGRIT_FCF_SHAPE", "99,256,1")
+        o = capi.mgrit_opts_default(m=m, levels=L, precision=capi.PREC_MIXED_DF, output=capi.OUT_CPOINTS,
+                                    tol=1e-10)
+        h = capi.mgrit_setup(capi.problem(nx, nt, "ERK", 1, 1, 0.85), o)
+        try:
+            out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
+            r, _ = capi.mgrit_solve(h, u0, out)
+            rel_sweeps = capi.mgrit_relax(h, 3)
+            out2 = torch.empty_like(out)
+            capi.mgrit_solve(h, u0, out2)
+            got[stream] = (r.iterations, out.cpu().numpy(), rel_sweeps, out2.cpu().numpy())
+        finally:
+            capi.mgrit_destroy(h)
+    b = got["0"]
+    assert np.isfinite(b[2]) and b[2] > 0
+    for mode in ("1", "2", "3", "4"):
+        a = got[mode]
+        assert a[0] == b[0], mode
+        np.testing.assert_array_equal(a[1], b[1])
+        np.testing.assert_array_equal(a[3], b[3])
+        assert abs(a[2] - b[2]) <= 1e-6 * b[2], mode
