@@ -298,9 +298,44 @@ def batch_variant(capi, count, stream):
             "server_stats": stats}
 
 
-def serving_variant(capi, rates, count):
+def fifo_latencies(times, service):
+    """Completion minus arrival of requests served one at a time in arrival
+    order (a queue in front of a single solver)."""
+    done, lat = 0.0, []
+    for a, s in zip(times, service):
+        done = max(done, a) + s
+        lat.append(done - a)
+    return lat
+
+
+def alone_service_times(capi, reqs, stream):
+    """Per request, measured alone on the GPU: plain FP64 MGRIT (set-up -- Psi
+    fit, allocation, autotuning -- plus the solve) and sequential stepping."""
+    import torch
+    fp64, seq = [], []
+    for prob, opts, u0 in reqs:
+        o = capi.MgritOpts.from_buffer_copy(opts)
+        o.precision = capi.PREC_FP64
+        t0 = time.perf_counter()
+        h = capi.mgrit_setup(prob, o, stream=stream)
+        try:
+            capi.mgrit_solve(h, u0, None, allow_not_converged=True)
+            torch.cuda.synchronize()
+            fp64.append(time.perf_counter() - t0)
+            fin = torch.empty(prob.nx, dtype=torch.float64, device="cuda")
+            seq.append(capi.mgrit_sequential(h, u0, fin))
+        finally:
+            capi.mgrit_destroy(h)
+    return fp64, seq
+
+
+def serving_variant(capi, rates, count, stream=None, baselines=True):
     """Poisson arrivals of the batch mix with a 1e-8 or 1e-10 tolerance drawn
-    per request; latency from submission to completion."""
+    per request; latency from submission to completion.  Baselines under the
+    same arrival stream: a FIFO queue in front of one plain-FP64 MGRIT solver
+    (each request set up and solved alone) and in front of GPU sequential
+    stepping, with service times measured per request on the same GPU and the
+    queue replayed on them."""
     out = {}
     for rate in rates:
         times, tols = workloads.arrivals(rate, count)
@@ -309,10 +344,21 @@ def serving_variant(capi, rates, count):
         dof = sum(s["nx"] * s["nt"] for s in specs)
         wall, lat, results, stats = run_server(capi, reqs, times, 150e9)
         ok = sum(1 for st, r in results if st == 0 and r.converged)
-        out[f"{rate:g}/s"] = {"requests": count, "converged": ok, "wall_s": wall, "dof_per_s": dof / wall,
-                              "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
-                                             "p99": 1e3 * float(np.percentile(lat, 99))},
-                              "server_stats": stats}
+        row = {"requests": count, "converged": ok, "wall_s": wall, "dof_per_s": dof / wall,
+               "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)),
+                              "p99": 1e3 * float(np.percentile(lat, 99))},
+               "server_stats": stats}
+        if baselines:
+            fp64, seq = alone_service_times(capi, reqs, stream)
+            for name, svc in (("fifo_plain_fp64", fp64), ("fifo_gpu_sequential", seq)):
+                fl = fifo_latencies(list(times), svc)
+                span = max(max(times) + 0.0, 0.0)
+                end = max(a + l for a, l in zip(times, fl))
+                row[name] = {"latency_ms": {"p50": 1e3 * float(np.percentile(fl, 50)),
+                                            "p99": 1e3 * float(np.percentile(fl, 99))},
+                             "dof_per_s": dof / max(end - float(times[0]), 1e-9), "busy_s": float(sum(svc)),
+                             "arrival_span_s": span}
+        out[f"{rate:g}/s"] = row
     return out
 
 
@@ -603,9 +649,12 @@ def compact_summary(extra):
                              "p99_ms": b["latency_ms"]["p99"], "converged": b["converged"]}
     sv = extra.get("serving_poisson")
     if sv:
-        out["serving"] = {k: [round(v["latency_ms"]["p50"], 1), round(v["latency_ms"]["p99"], 1),
-                              float("%.4g" % v["dof_per_s"])] for k, v in sv.items()}
-        out["serving_fields"] = "rate: [p50 ms, p99 ms, DOF/s]"
+        def trio(v):
+            return [round(v["latency_ms"]["p50"], 1), round(v["latency_ms"]["p99"], 1), float("%.4g" % v["dof_per_s"])]
+        out["serving"] = {k: {"batched": trio(v), **({"fifo_fp64": trio(v["fifo_plain_fp64"]),
+                                                      "fifo_seq": trio(v["fifo_gpu_sequential"])}
+                                                     if "fifo_plain_fp64" in v else {})} for k, v in sv.items()}
+        out["serving_fields"] = "[p50 ms, p99 ms, DOF/s]; fifo_*: one solver in arrival order, service measured alone"
     sd = extra.get("sdirk3_u5_8192")
     if sd:
         out["sdirk3_u5_8192_ms"] = {"mixed": sd["mixed"]["ms"], "fp64": sd["fp64"]["ms"],
@@ -657,7 +706,7 @@ def main():
         run = {"sdirk": lambda: sdirk_variant(capi, sp, args.steps,
                                               capi.FLAG_HOST_LOOP if args.host_loop else 0),
                "batch": lambda: batch_variant(capi, args.batch, sp),
-               "serve": lambda: serving_variant(capi, (100, 1000, 3000, 10000), args.serve),
+               "serve": lambda: serving_variant(capi, (100, 1000, 3000, 10000), args.serve, sp),
                "inflow": lambda: inflow_variant(capi, sp),
                "hbm": lambda: hbm_variant(capi, sp)}[args.only]
         print(json.dumps({args.only: run()}), flush=True)
@@ -803,7 +852,7 @@ def main():
         if args.batch > 0:
             extra["batch_uneven"] = batch_variant(capi, args.batch, sp)
         if args.serve > 0:
-            extra["serving_poisson"] = serving_variant(capi, (100, 1000, 3000, 10000), args.serve)
+            extra["serving_poisson"] = serving_variant(capi, (100, 1000, 3000, 10000), args.serve, sp)
 
     line = None
     if rank == 0:
@@ -816,30 +865,27 @@ def main():
             v1, s1, it1 = oracle_sample(repeats=3)
             va, nproc, wall = oracle_all_cores()
             cpu = {"value": va, "unit": "DOF/s", "cores": nproc, "kind": "oracle",
-                   "sample": cpu_sample_text() + f"; {nproc} concurrent single-thread solves ({nproc} host "
-                             f"cores), {wall:.1f} s", "one_thread_value": v1, "iterations": it1}
+                   "sample": f"oracle V(L=4,m=8) on nx=4096 nt={CPU_NT_SAMPLE}, {nproc} concurrent 1-thread "
+                             f"solves, {wall:.1f} s", "one_thread_value": v1}
         hb = hbm_summary(extra.get("hbm_bound_erk1_m4"))
         line = {
             "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "fp64+fp32", "data": "synthetic",
             "gpu_launches": launches,
-            "config": {"workload": "ERK3+U3 4096x16384 c=0.85*1.62589, Fourier-field u0 (seed 2), zero iterate, "
-                                   "V-cycle L=4 m=8, auto-width LSQ Psi, FP32 F-relax + FP64 residual/coarse/test, "
-                                   "tol 1e-10", "parallelism": f"replicas x{world}",
-                       "l2": "flushed before each step (256 MiB write)",
-                       "timing": "CUDA events per solve; solves queued with mgrit_solve_async"},
+            "config": {"workload": "ERK3+U3 4096x16384 c=.85cmax, V(L=4,m=8), LSQ Psi, FP32 relax/FP64 residual, "
+                                   "tol 1e-10", "parallelism": f"replicas x{world}", "l2": "flushed per step",
+                       "timing": "events per queued solve"},
             "e2e": {"value": e2e_value, "unit": "DOF/s", "h2d_bytes_per_step": NX * 8,
                     "d2h_bytes_per_step": (N1 + 1) * NX * 8},
             "clocks": clk, "cpu_baseline": cpu,
-            "roofline": {"bound": "alu", "kernel": "fcf_kernel (level-1 FCF + fused residual)",
-                         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "roofline": {"bound": "alu", "kernel": "fcf_kernel level 1", "achieved": achieved,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-                         "traffic": fcf_traffic_from_profile(),
-                         "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+                         "traffic": fcf_traffic_from_profile(), "peak_source": "152 SM x 4 FP64 flop/clk x 2.07 GHz",
                          "launch_ms": fcf_avg_s * 1e3},
             "hbm_roofline_fcf": ({"frac": hb["frac"], "achieved": hb["achieved"], "peak": hb["peak"],
-                                  "unit": "GB/s", "instance": "ERK1+U1 4096x16384 m=4 MIXED_DF",
+                                  "unit": "GB/s", "instance": "ERK1 m=4 MIXED_DF",
                                   "mixed_frac": hb["mixed_fp64_first_pass_frac"]} if hb else None),
             "iterations": res0.iterations, "rel_residual": res0.rel_residual,
             "err_vs_oracle_sequential": err_oracle,

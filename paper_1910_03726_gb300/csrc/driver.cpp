@@ -683,9 +683,11 @@ void autotune_fine(mgrit_handle* h) {
       return;
     }
   }
-  // time the candidates on an otherwise idle device (other streams' work, a
-  // server's running cycle for one, would distort the comparison)
-  if (cudaDeviceSynchronize() != cudaSuccess) {
+  // time the candidates on an otherwise idle device (other streams' work would
+  // distort the comparison).  A server's handle is the exception: it tunes on
+  // the server's high-priority set-up stream while a cycle runs, since
+  // waiting for the device would hold every admission behind that cycle.
+  if (!h->pool_alloc && cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     return;
   }

@@ -950,33 +950,36 @@ __global__ void __launch_bounds__(1024) fcf_df_reg_kernel(const FcfArgs a, const
 // Persistent form of the register-resident body: CTA b owns the intervals
 // j0..j1-1 (a balanced split of 1..N).  Interval j+1's input c_j is interval
 // j's old C-point, already in registers, so a run reads each slab from HBM
-// once: the next one, c_{j+1}, is copied into shared memory with 16-byte
-// cp.async while interval j computes (three buffers: c_{j-1} for lane 0's
-// halo, c_j being read, c_{j+1} arriving).  Each thread's 8 points are two
-// 16-byte units pairs; unit u of thread t sits at 4t + (u ^ ((t >> 1) & 3)),
-// so a quarter-warp's 16-byte loads hit 8 distinct bank groups.  The norm
-// is one fixed-order block reduction per run, stored at partial[j0] (zeros
-// at the run's other intervals): the sum the norm kernel forms is the same
-// quantity, in another order.  Arithmetic per output: fcf_body_df_fused's.
+// once: each thread copies its own chunk of the next one, c_{j+1}, into
+// shared memory with 16-byte cp.async while interval j computes (three
+// buffers, slab k in buffer k mod 3).  The SPAN-1 points left of a thread's
+// chunk are the tail of its left neighbour's chunk (periodic across the
+// slab): c_{j-1}'s tail is read from the neighbour's buffer units, published
+// by the previous interval's barrier and not overwritten before the next one;
+// rho's tail goes through a parity-double-buffered per-thread slot at the
+// one barrier of an interval.  Thread t's unit u (16 bytes, two points) sits
+// at 4t + (u ^ ((t >> 1) & 3)), so a quarter-warp's 16-byte loads hit 8
+// distinct bank groups.  The norm is one fixed-order block reduction per
+// run, stored at partial[j0] (zeros at the run's other intervals): the sum
+// the norm kernel forms is the same quantity, in another order.  Arithmetic
+// per output: fcf_body_df_fused's.
 __device__ __forceinline__ int swz_unit(int t, int u) { return 4 * t + (u ^ ((t >> 1) & 3)); }
-__device__ __forceinline__ df64 swz_load(const df64* buf, int e) {  // element e of a swizzled slab
-  const int t = e >> 3, r = e & 7;
-  return buf[2 * swz_unit(t, r >> 1) + (r & 1)];
-}
 
 template <int SPAN>
 __global__ void __launch_bounds__(1024) fcf_df_regrun_kernel(const FcfArgs a, const DevTaps t) {
   constexpr int R = 8, H = SPAN - 1;
+  static_assert(H >= 1 && H <= 4, "the left halo is at most the neighbour's last two units");
   extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ float xh[32][H > 0 ? H : 1];
   const int nx = a.nx, N = a.N, G = gridDim.x, b = blockIdx.x;
   const int j0 = 1 + (int)((long long)b * N / G), j1 = 1 + (int)((long long)(b + 1) * N / G);
   if (j0 >= j1) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, T = blockDim.x;
+  const int tl = tid == 0 ? T - 1 : tid - 1;  // the left neighbour (periodic)
   const int i0 = tid * R;
-  df64* const B0 = reinterpret_cast<df64*>(smraw);  // buffer (j mod 3) at B0 + (j mod 3) nx
+  df64* const B0 = reinterpret_cast<df64*>(smraw);                      // three slabs
+  float4* const RX = reinterpret_cast<float4*>(B0 + 3 * (long long)nx);  // rho tails, two by parity
   const df64* cold = reinterpret_cast<const df64*>(a.u_old);
-  auto prefetch = [&](int jj) {  // c_jj into its buffer: this thread's own 4 units
+  auto prefetch = [&](int jj) {  // this thread's chunk of c_jj into buffer jj mod 3
     df64* dst = B0 + (long long)(jj % 3) * nx;
     const df64* src = cold + (long long)jj * a.cstride + i0;
 #pragma unroll
@@ -986,54 +989,48 @@ __global__ void __launch_bounds__(1024) fcf_df_regrun_kernel(const FcfArgs a, co
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
+  auto load_units = [&](const df64* buf, int th, int u0, int nu, df64* out) {  // units u0.. of thread th
+    for (int u = 0; u < nu; ++u) {
+      const float4 q = *reinterpret_cast<const float4*>(buf + 2 * swz_unit(th, u0 + u));
+      out[2 * u] = {q.x, q.y};
+      out[2 * u + 1] = {q.z, q.w};
+    }
+  };
   df64 cur[R];  // c_{j-1} of this thread's chunk
+  if (!a.zero_old) {
+    prefetch(j0 - 1);
+    prefetch(j0);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+  }
+  __syncthreads();  // c_{j0-1} of every chunk visible (the first interval's halo)
   if (a.zero_old) {
 #pragma unroll
     for (int r = 0; r < R; ++r) cur[r] = vzero<df64>();
   } else {
-    prefetch(j0 - 1);
-    prefetch(j0);
-#pragma unroll
-    for (int r = 0; r < R; r += 2) {
-      const df2 v = ldcg_df2(cold + (long long)(j0 - 1) * a.cstride + i0 + r);
-      cur[r] = v.a;
-      cur[r + 1] = v.b;
-    }
+    load_units(B0 + (long long)((j0 - 1) % 3) * nx, tid, 0, 4, cur);
   }
   float ss = 0.0f;
   for (int j = j0; j < j1; ++j) {
-    if (!a.zero_old) asm volatile("cp.async.wait_all;\n" ::: "memory");
-    __syncthreads();  // c_j (and c_{j-1}) complete; last interval's halo reads of the buffer reused below are done
-    if (!a.zero_old && j + 1 < j1) prefetch(j + 1);
-    const df64* Bj = B0 + (long long)(j % 3) * nx;
-    const df64* Bp = B0 + (long long)((j + 2) % 3) * nx;  // c_{j-1}
+    const int par = j & 1;
     df64 old[R];
+    df64 w[R + H];
     if (a.zero_old) {
 #pragma unroll
       for (int r = 0; r < R; ++r) old[r] = vzero<df64>();
-    } else {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float4 q = *reinterpret_cast<const float4*>(Bj + 2 * swz_unit(tid, u));
-        old[2 * u] = {q.x, q.y};
-        old[2 * u + 1] = {q.z, q.w};
-      }
+      for (int q = 0; q < H; ++q) w[q] = vzero<df64>();
+    } else {
+      asm volatile("cp.async.wait_all;\n" ::: "memory");  // this thread's chunk of c_j
+      if (j + 1 < j1) prefetch(j + 1);  // into the buffer of c_{j-2}, read by its last reader before the last barrier
+      load_units(B0 + (long long)(j % 3) * nx, tid, 0, 4, old);
+      df64 tail[4];
+      load_units(B0 + (long long)((j + 2) % 3) * nx, tl, 2, 2, tail);  // c_{j-1}, points 4..7 of the neighbour
+#pragma unroll
+      for (int q = 0; q < H; ++q) w[q] = tail[4 - H + q];
     }
-    df64 w[R + H];
 #pragma unroll
     for (int r = 0; r < R; ++r) w[H + r] = cur[r];
     unsigned nzw = 0;
-#pragma unroll
-    for (int q = 0; q < H; ++q) {
-      float hi = __shfl_up_sync(0xffffffffu, cur[R - H + q].hi, 1);
-      float lo = __shfl_up_sync(0xffffffffu, cur[R - H + q].lo, 1);
-      if (lane == 0) {  // the chunk left of lane 0's: another warp's, or (periodic) the slab's end
-        const df64 g = a.zero_old ? vzero<df64>() : swz_load(Bp, wrapi(i0 - H + q, nx));
-        hi = g.hi;
-        lo = g.lo;
-      }
-      w[q] = {hi, lo};
-    }
 #pragma unroll
     for (int q = 0; q < R + H; ++q) nzw |= __float_as_uint(w[q].hi);
     df64 v[R];
@@ -1060,17 +1057,15 @@ __global__ void __launch_bounds__(1024) fcf_df_regrun_kernel(const FcfArgs a, co
       nzr |= __float_as_uint(rw[H + r]);
       cur[r] = old[r];
     }
-    if (j < N) {  // uniform over the CTA
-      if (lane == 31)
-#pragma unroll
-        for (int q = 0; q < H; ++q) xh[warp][q] = rw[R + q];
+    if (j < N) {  // uniform over the CTA (only the problem's last interval has no residual)
+      RX[par * T + tid] = make_float4(rw[R + H - 4], rw[R + H - 3], rw[R + H - 2], rw[R + H - 1]);  // last 4 rho
       __syncthreads();
-      const int wl = warp == 0 ? nw - 1 : warp - 1;
+      const float4 q = RX[par * T + tl];
+      const float qa[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-      for (int q = 0; q < H; ++q) {
-        const float u = __shfl_up_sync(0xffffffffu, rw[R + q], 1);
-        rw[q] = lane == 0 ? xh[wl][q] : u;
-        nzr |= __float_as_uint(rw[q]);
+      for (int k = 0; k < H; ++k) {
+        rw[k] = qa[4 - H + k];
+        nzr |= __float_as_uint(rw[k]);
       }
       float* rr = a.r_f + (long long)(j + 1) * nx;
       float o[R];
@@ -1773,17 +1768,17 @@ static cudaError_t launch_fcf_stream(const FcfArgs& a, const DevTaps& t, cudaStr
 template <int SPAN>
 static cudaError_t launch_fcf_fused(const FcfArgs& a, const DevTaps& t, int threads, cudaStream_t s) {
   const bool upwind = t.lo == -(SPAN - 1) && t.hi == 0 && a.nx % 256 == 0 && a.nx / 8 <= 1024;
-  if (g_stream_fused == 1 && upwind && 3 * (size_t)a.nx * sizeof(double) <= (size_t)kMaxSmemBytes - 1024) {
-    const size_t smem = 3 * (size_t)a.nx * sizeof(double);
-    cudaError_t e = set_smem(fcf_df_regrun_kernel<SPAN>, smem);
+  const size_t rsmem = 3 * (size_t)a.nx * sizeof(double) + 2 * (size_t)(a.nx / 8) * sizeof(float4);
+  if (g_stream_fused == 1 && upwind && rsmem <= (size_t)kMaxSmemBytes) {
+    cudaError_t e = set_smem(fcf_df_regrun_kernel<SPAN>, rsmem);
     if (e != cudaSuccess) return e;
     const int th = a.nx / 8;
-    int per_sm = (int)(((size_t)kMaxSmemBytes) / (smem + 1024));
-    per_sm = per_sm < 2048 / th ? per_sm : 2048 / th;             // threads per SM
+    int per_sm = (int)((228 * 1024) / (rsmem + 1024));                // shared memory per SM
+    per_sm = per_sm < 2048 / th ? per_sm : 2048 / th;                  // threads per SM
     per_sm = per_sm < 65536 / (64 * th) ? per_sm : 65536 / (64 * th);  // 64 registers per thread
     per_sm = per_sm < 1 ? 1 : per_sm;
     const int grid = a.N < per_sm * sm_count() ? a.N : per_sm * sm_count();
-    fcf_df_regrun_kernel<SPAN><<<grid, th, smem, s>>>(a, t);
+    fcf_df_regrun_kernel<SPAN><<<grid, th, rsmem, s>>>(a, t);
     return cudaGetLastError();
   }
   if (g_stream_fused == 4 && upwind) {

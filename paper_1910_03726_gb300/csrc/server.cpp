@@ -27,6 +27,7 @@
 #include <atomic>
 #include <cmath>
 #include <condition_variable>
+#include <cstdint>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -62,6 +63,14 @@ struct Request {
   double r0 = 0.0, t_submit = 0.0;
   size_t bytes = 0;
 };
+
+// Requests admitted before the first cycle of a busy period starts; the rest
+// join while cycles run.  Admission during a cycle stops when the cycle's
+// relaxation is done, once at least kMinBatch solves are active: a cycle costs
+// about the time of its longest coarse march whatever the number of solves,
+// so small cycles waste it.
+constexpr size_t kStartBatch = 64;
+constexpr size_t kMinBatch = 512;
 
 struct PlanKey {
   int nx, nt, family, p, q, m, levels, rule, halfwidth;
@@ -160,6 +169,7 @@ struct mgrit_server {
   // start, 3 coarse end (read at the next cycle's synchronisation)
   cudaEvent_t ev[5] = {};
   int device = 0;          // the creating thread's device; the worker runs on it
+  cudaEvent_t ev_front_done = nullptr;  // recorded after a cycle's relaxation and norms (no timing)
   // Device tap table: slot k holds the fine stencil (2k) and the coarse one
   // (2k+1) of an active solve, uploaded once at admission
   DevTaps* taps = nullptr;
@@ -205,10 +215,17 @@ static void finish(mgrit_server* S, Request* r, mgrit_status st, const std::stri
 
 // Admit queued requests that fit (called with the lock held; releases it
 // around the host setup).  Returns the newly admitted requests.
-static std::vector<Request*> admit(mgrit_server* S, std::unique_lock<std::mutex>& lk) {
+// limit: most requests to admit in this call.  until: an event the cycle
+// stream records when its relaxation is done; admission stops once it has
+// completed (after at least one request), so the GPU does not wait for the
+// host to finish admitting before the cycle's coarse solves are queued.
+static std::vector<Request*> admit(mgrit_server* S, std::unique_lock<std::mutex>& lk, size_t limit = SIZE_MAX,
+                                   cudaEvent_t until = nullptr) {
   std::vector<Request*> fresh;
   const size_t max_active = S->o.max_active > 0 ? (size_t)S->o.max_active : 4096;
-  while (!S->queue.empty() && S->active.size() + fresh.size() < max_active) {
+  while (!S->queue.empty() && S->active.size() + fresh.size() < max_active && fresh.size() < limit) {
+    if (until && !fresh.empty() && S->active.size() + fresh.size() >= kMinBatch && cudaEventQuery(until) == cudaSuccess)
+      break;
     Request* r = S->queue.front();
     const auto itp = S->plans.find(key_of(r->prob, r->opts));
     if (itp == S->plans.end() || itp->second.state == 0) break;  // its operators are still being fitted
@@ -397,6 +414,7 @@ static mgrit_status cycle_front(mgrit_server* S, const std::vector<Request*>& ac
   }
   if (timed) cudaEventRecord(S->ev[2], S->stream);
   cudaMemcpyAsync(S->hNorm, S->dNorm.p, n * sizeof(double), cudaMemcpyDeviceToHost, S->stream);
+  if (S->ev_front_done) cudaEventRecord(S->ev_front_done, S->stream);
   return MGRIT_OK;
 }
 
@@ -627,6 +645,10 @@ static void worker_main(mgrit_server* S) {
     S->slots = slots;
     for (int k = slots - 1; k >= 0; --k) S->free_slots.push_back(k);
   }
+  if (cudaEventCreateWithFlags(&S->ev_front_done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    S->ev_front_done = nullptr;
+  }
   bool queued = false;  // the active set's next cycle_front is already on the stream
   mgrit_status queued_status = MGRIT_OK;
   while (!S->stop) {
@@ -637,10 +659,10 @@ static void worker_main(mgrit_server* S) {
       S->cv.wait(lk, [&] { return S->stop || !S->queue.empty(); });
       continue;
     }
-    if (S->active.empty()) {  // nothing running: admit, then cycle
+    if (S->active.empty()) {  // nothing running: admit a few, then cycle (more join during the cycles)
       queued = false;
       const double ta = now_s();
-      std::vector<Request*> fresh = admit(S, lk);
+      std::vector<Request*> fresh = admit(S, lk, kStartBatch);
       S->stats.admit_s += now_s() - ta;
       for (Request* r : fresh) S->active.push_back(r);
       if (S->active.empty()) {
@@ -657,7 +679,7 @@ static void worker_main(mgrit_server* S) {
     // admit while the GPU runs the cycle's relaxation (set-up on the upload stream)
     lk.lock();
     const double ta = now_s();
-    std::vector<Request*> fresh = admit(S, lk);
+    std::vector<Request*> fresh = admit(S, lk, SIZE_MAX, S->ev_front_done);
     const double admit_dt = now_s() - ta;
     S->stats.admit_s += admit_dt;
     lk.unlock();
@@ -828,6 +850,7 @@ extern "C" void mgrit_server_destroy(mgrit_server* S) {
   for (auto& ev : S->ev)
     if (ev) cudaEventDestroy(ev);
   if (S->stream) cudaStreamSynchronize(S->stream);
+  if (S->ev_front_done) cudaEventDestroy(S->ev_front_done);
   if (S->taps) cudaFree(S->taps);
   S->stage.free();
   S->hS.free();
