@@ -679,7 +679,7 @@ def main():
     ap.add_argument("--host-loop", action="store_true",
                     help="with --only sdirk: drive cycles from the host (kernels visible to ncu)")
     ap.add_argument("--variants-out", default=os.path.join(ROOT, "gpurun_out", "bench_variants.json"),
-                    help="file for the full variant record (written when its folder exists)")
+                    help="file for the full variant record (written when its folder exists; '' for none)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = dist_env()
@@ -893,7 +893,7 @@ def main():
             "summary": compact_summary(extra),
         }
         try:
-            if os.path.isdir(os.path.dirname(args.variants_out)):
+            if args.variants_out and os.path.isdir(os.path.dirname(args.variants_out)):
                 with open(args.variants_out, "w") as f:
                     json.dump({"line": line, "variants": extra}, f, indent=1)
         except OSError:
