@@ -150,6 +150,85 @@ def oracle_all_cores(nt_sample=CPU_NT_SAMPLE, repeats=2):
     return NX * nt_sample * repeats * len(res) / wall, n, wall
 
 
+SUBSET_MAX_DOF = 2 ** 20  # the batch subset's solves the oracle leg takes (about 10 s on 16 cores)
+
+
+def _oracle_mix_worker(spec):
+    """One solve of the uneven batch by the oracle: two-level FCF-MGRIT in FP64
+    from the zero iterate to 1e-10 (Section 2.2), its Psi fitted as the server
+    fits it (auto width for ERK, the threshold rule for SDIRK); returns the
+    final time level, the iteration count and the seconds (Psi fit
+    included, as in the batch's timing)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import mgrit as omg
+    from oracle import psi as opsi
+    from oracle import stepping
+    fam, p, nx, nt, m = spec["family"], spec["p"], spec["nx"], spec["nt"], spec["m"]
+    c = 4.0 if fam == "SDIRK" else 0.85 * CMAX_TABLE1[p]
+    t0 = time.perf_counter()
+    st = stepping.FineStep(fam, p, c, nx)
+    ops = opsi.build_hierarchy(fam, p, c, nx, nt, m, 2, rule="threshold" if fam == "SDIRK" else "auto")
+    U = omg.zero_iterate(workloads.fourier_field(nx, seed=spec["field_seed"]), nt)
+    it, _ = omg.solve(omg.make_levels(st, m, [o.diag for o in ops]), U, tol=TOL, max_iter=80)
+    return U[-1].copy(), it, time.perf_counter() - t0
+
+
+def batch_subset_vs_oracle(capi, batch_dof, batch_wall_s, headline_oracle_all_cores):
+    """The solves of the seeded 64-solve subset of the uneven batch (its first
+    64) with nx*nt <= SUBSET_MAX_DOF: timed in the oracle on all host cores
+    at once (spawned processes, one thread each), and through the server in
+    MIXED as the batch runs them; per result, the relative L2 error of the
+    final time level against the oracle's.  The oracle's batch time is
+    extrapolated from the sample's DOF/s; small solves cost the oracle more
+    per DOF (per-step interpreter overhead), so the headline sample's rate
+    (nx = 4096) is given as the other bound."""
+    import multiprocessing as mp
+    specs = [s for s in workloads.batch_specs(64) if s["nx"] * s["nt"] <= SUBSET_MAX_DOF]
+    dof = sum(s["nx"] * s["nt"] for s in specs)
+    n = os.cpu_count() or 1
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(n) as pool:
+            pool.map(_oracle_worker, [(0, 1)] * n)  # imports outside the timing
+            t0 = time.perf_counter()
+            ref = pool.map(_oracle_mix_worker, specs, chunksize=1)
+            wall = time.perf_counter() - t0
+    finally:
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    srv = capi.mgrit_server_create(150e9)
+    errs, dits = [], []
+    try:
+        tickets = [capi.mgrit_submit(srv, *mix_request(capi, s, TOL, capi.PREC_MIXED)) for s in specs]
+        for s, t, (fin_o, it_o, _) in zip(specs, tickets, ref):
+            fin = np.zeros(s["nx"])
+            while True:
+                st, r = capi.mgrit_poll(srv, t, fin)
+                if st != capi.MGRIT_PENDING:
+                    break
+                time.sleep(0.001)
+            errs.append(float(np.linalg.norm(fin - fin_o) / np.linalg.norm(fin_o)) if st == 0 else float("inf"))
+            dits.append(r.iterations - it_o)
+    finally:
+        capi.mgrit_server_destroy(srv)
+    rate_all = dof / wall
+    return {"solves": len(specs), "dof": dof, "cores": n,
+            "sample": f"the {len(specs)} solves with nx*nt <= {SUBSET_MAX_DOF} of the batch's first 64 (seed 4)",
+            "oracle_wall_s": wall, "oracle_dof_per_s_all_cores": rate_all,
+            "oracle_dof_per_s_one_thread": dof / sum(x[2] for x in ref),
+            "extrapolated_oracle_batch_s": {"subset_rate": batch_dof / rate_all,
+                                            "headline_sample_rate": batch_dof / headline_oracle_all_cores},
+            "gpu_batch_s": batch_wall_s,
+            "err_vs_oracle": {"max": max(errs), "median": float(np.median(errs)),
+                              "per_result": [float(f"{e:.3g}") for e in errs]},
+            "iterations_minus_oracle": [min(dits), max(dits)]}
+
+
 def cpu_sample_text(nt_sample=CPU_NT_SAMPLE):
     return (f"oracle (numpy FP64) V-cycle L=4 m=8 FCF-MGRIT on nx=4096, nt={nt_sample} (the first "
             f"{nt_sample}/16384 of the horizon), same scheme, CFL, u0 and tol; Psi setup excluded")
@@ -308,12 +387,20 @@ def fifo_latencies(times, service):
     return lat
 
 
-def alone_service_times(capi, reqs, stream):
+def alone_service_times(capi, reqs, stream, keys=None, cache=None):
     """Per request, measured alone on the GPU: plain FP64 MGRIT (set-up -- Psi
-    fit, allocation, autotuning -- plus the solve) and sequential stepping."""
+    fit, allocation, autotuning -- plus the solve) and sequential stepping.
+    With keys and a cache dict, a request whose key (scheme, order, nx, nt, m,
+    tolerance) was measured before reuses that measurement: such requests
+    differ in u0 only."""
     import torch
     fp64, seq = [], []
-    for prob, opts, u0 in reqs:
+    for i, (prob, opts, u0) in enumerate(reqs):
+        key = keys[i] if keys is not None else None
+        if key is not None and key in cache:
+            fp64.append(cache[key][0])
+            seq.append(cache[key][1])
+            continue
         o = capi.MgritOpts.from_buffer_copy(opts)
         o.precision = capi.PREC_FP64
         t0 = time.perf_counter()
@@ -326,7 +413,12 @@ def alone_service_times(capi, reqs, stream):
             seq.append(capi.mgrit_sequential(h, u0, fin))
         finally:
             capi.mgrit_destroy(h)
+        if key is not None:
+            cache[key] = (fp64[-1], seq[-1])
     return fp64, seq
+
+
+SERVE_MEASURE_EACH = 1024  # above this many requests, service times are measured once per key
 
 
 def serving_variant(capi, rates, count, stream=None, baselines=True):
@@ -335,8 +427,11 @@ def serving_variant(capi, rates, count, stream=None, baselines=True):
     same arrival stream: a FIFO queue in front of one plain-FP64 MGRIT solver
     (each request set up and solved alone) and in front of GPU sequential
     stepping, with service times measured per request on the same GPU and the
-    queue replayed on them."""
+    queue replayed on them.  Above SERVE_MEASURE_EACH requests a service time
+    is measured once per (scheme, order, nx, nt, m, tolerance) and shared by
+    all requests and rates with that key."""
     out = {}
+    cache = {} if count > SERVE_MEASURE_EACH else None
     for rate in rates:
         times, tols = workloads.arrivals(rate, count)
         specs = workloads.batch_specs(count, seed=workloads.SEED_ARRIVALS * 7 + int(rate))
@@ -349,7 +444,11 @@ def serving_variant(capi, rates, count, stream=None, baselines=True):
                               "p99": 1e3 * float(np.percentile(lat, 99))},
                "server_stats": stats}
         if baselines:
-            fp64, seq = alone_service_times(capi, reqs, stream)
+            keys = None if cache is None else [(s["family"], s["p"], s["nx"], s["nt"], s["m"], float(t))
+                                               for s, t in zip(specs, tols)]
+            fp64, seq = alone_service_times(capi, reqs, stream, keys, cache)
+            row["service_times"] = ("measured per request" if cache is None else
+                                    f"measured once per key: {len(cache)} keys so far")
             for name, svc in (("fifo_plain_fp64", fp64), ("fifo_gpu_sequential", seq)):
                 fl = fifo_latencies(list(times), svc)
                 span = max(max(times) + 0.0, 0.0)
@@ -655,6 +754,14 @@ def compact_summary(extra):
                                                       "fifo_seq": trio(v["fifo_gpu_sequential"])}
                                                      if "fifo_plain_fp64" in v else {})} for k, v in sv.items()}
         out["serving_fields"] = "[p50 ms, p99 ms, DOF/s]; fifo_*: one solver in arrival order, service measured alone"
+    bs = extra.get("batch_subset_vs_oracle")
+    if bs:
+        ex = bs["extrapolated_oracle_batch_s"]
+        out["batch_subset_vs_oracle"] = {"solves": bs["solves"], "err_max": float("%.3g" % bs["err_vs_oracle"]["max"]),
+                                         "iterations_minus_oracle": bs["iterations_minus_oracle"],
+                                         "oracle_batch_s_extrapolated": [round(ex["subset_rate"]),
+                                                                         round(ex["headline_sample_rate"])],
+                                         "gpu_batch_s": round(bs["gpu_batch_s"], 2)}
     sd = extra.get("sdirk3_u5_8192")
     if sd:
         out["sdirk3_u5_8192_ms"] = {"mixed": sd["mixed"]["ms"], "fp64": sd["fp64"]["ms"],
@@ -867,6 +974,9 @@ def main():
             cpu = {"value": va, "unit": "DOF/s", "cores": nproc, "kind": "oracle",
                    "sample": f"oracle V(L=4,m=8) on nx=4096 nt={CPU_NT_SAMPLE}, {nproc} concurrent 1-thread "
                              f"solves, {wall:.1f} s", "one_thread_value": v1}
+            bu = extra.get("batch_uneven")
+            if bu is not None:
+                extra["batch_subset_vs_oracle"] = batch_subset_vs_oracle(capi, bu["dof"], bu["wall_s"], va)
         hb = hbm_summary(extra.get("hbm_bound_erk1_m4"))
         line = {
             "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,

@@ -432,6 +432,13 @@ __device__ __forceinline__ df64 ldcg_df(const df64* p) {
   return {v.x, v.y};
 }
 
+// Nonzero bits of v without its sign (0 iff v == +-0): integer instructions,
+// where a double comparison would take an issue slot of the FP64 pipe.
+__device__ __forceinline__ int dnz(double v) {
+  const long long b = __double_as_longlong(v);
+  return (int)(((unsigned)(b >> 32) & 0x7fffffffu) | (unsigned)b);
+}
+
 // Sum over the block in a fixed order (deterministic); result valid in thread 0.
 __device__ double block_sum(double v) {
   __shared__ double ws[32];
@@ -962,11 +969,45 @@ __global__ void __launch_bounds__(1024) fcf_df_reg_kernel(const FcfArgs a, const
 // distinct bank groups.  The norm is one fixed-order block reduction per
 // run, stored at partial[j0] (zeros at the run's other intervals): the sum
 // the norm kernel forms is the same quantity, in another order.  Arithmetic
-// per output: fcf_body_df_fused's.
+// per output: fcf_body_df_fused's (V = df64, MIXED_DF) or the FP64 pass of
+// fcf_body with the FP32 second pass (V = double, MIXED); either C-point type
+// takes 8 bytes per point, so the layout and the copies are the same.
 __device__ __forceinline__ int swz_unit(int t, int u) { return 4 * t + (u ^ ((t >> 1) & 3)); }
 
-template <int SPAN>
-__global__ void __launch_bounds__(1024) fcf_df_regrun_kernel(const FcfArgs a, const DevTaps t) {
+template <typename V>
+struct RunOps;
+template <>
+struct RunOps<df64> {
+  static __device__ __forceinline__ void unit(const df64* p, df64& x, df64& y) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    x = {q.x, q.y};
+    y = {q.z, q.w};
+  }
+  static __device__ __forceinline__ void st2(df64* p, df64 x, df64 y) { st_df2(p, x, y); }
+  static constexpr unsigned kNzMask = 0x7fffffffu;  // nz(v) & kNzMask != 0 iff v != 0
+  static __device__ __forceinline__ unsigned nz(df64 v) { return __float_as_uint(v.hi); }
+  static __device__ __forceinline__ df64 mul(df64 c, df64 w) { return df_mul(c, w); }
+  static __device__ __forceinline__ float sub_f(df64 x, df64 y) { return df_sub_f(x, y); }
+};
+template <>
+struct RunOps<double> {
+  static __device__ __forceinline__ void unit(const double* p, double& x, double& y) {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    x = q.x;
+    y = q.y;
+  }
+  static __device__ __forceinline__ void st2(double* p, double x, double y) {
+    *reinterpret_cast<double2*>(p) = make_double2(x, y);
+  }
+  static constexpr unsigned kNzMask = ~0u;
+  static __device__ __forceinline__ unsigned nz(double v) { return (unsigned)dnz(v); }
+  static __device__ __forceinline__ double mul(double c, double w) { return c * w; }
+  static __device__ __forceinline__ float sub_f(double x, double y) { return (float)(x - y); }
+};
+
+template <int SPAN, typename V>
+__global__ void __launch_bounds__(1024) fcf_regrun_kernel(const FcfArgs a, const DevTaps t) {
+  using Op = RunOps<V>;
   constexpr int R = 8, H = SPAN - 1;
   static_assert(H >= 1 && H <= 4, "the left halo is at most the neighbour's last two units");
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -976,12 +1017,12 @@ __global__ void __launch_bounds__(1024) fcf_df_regrun_kernel(const FcfArgs a, co
   const int tid = threadIdx.x, T = blockDim.x;
   const int tl = tid == 0 ? T - 1 : tid - 1;  // the left neighbour (periodic)
   const int i0 = tid * R;
-  df64* const B0 = reinterpret_cast<df64*>(smraw);                      // three slabs
+  V* const B0 = reinterpret_cast<V*>(smraw);                            // three slabs
   float4* const RX = reinterpret_cast<float4*>(B0 + 3 * (long long)nx);  // rho tails, two by parity
-  const df64* cold = reinterpret_cast<const df64*>(a.u_old);
+  const V* cold = reinterpret_cast<const V*>(a.u_old);
   auto prefetch = [&](int jj) {  // this thread's chunk of c_jj into buffer jj mod 3
-    df64* dst = B0 + (long long)(jj % 3) * nx;
-    const df64* src = cold + (long long)jj * a.cstride + i0;
+    V* dst = B0 + (long long)(jj % 3) * nx;
+    const V* src = cold + (long long)jj * a.cstride + i0;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const unsigned d = (unsigned)__cvta_generic_to_shared(dst + 2 * swz_unit(tid, u));
@@ -989,14 +1030,10 @@ __global__ void __launch_bounds__(1024) fcf_df_regrun_kernel(const FcfArgs a, co
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
-  auto load_units = [&](const df64* buf, int th, int u0, int nu, df64* out) {  // units u0.. of thread th
-    for (int u = 0; u < nu; ++u) {
-      const float4 q = *reinterpret_cast<const float4*>(buf + 2 * swz_unit(th, u0 + u));
-      out[2 * u] = {q.x, q.y};
-      out[2 * u + 1] = {q.z, q.w};
-    }
+  auto load_units = [&](const V* buf, int th, int u0, int nu, V* out) {  // units u0.. of thread th
+    for (int u = 0; u < nu; ++u) Op::unit(buf + 2 * swz_unit(th, u0 + u), out[2 * u], out[2 * u + 1]);
   };
-  df64 cur[R];  // c_{j-1} of this thread's chunk
+  V cur[R];  // c_{j-1} of this thread's chunk
   if (!a.zero_old) {
     prefetch(j0 - 1);
     prefetch(j0);
@@ -1005,25 +1042,25 @@ __global__ void __launch_bounds__(1024) fcf_df_regrun_kernel(const FcfArgs a, co
   __syncthreads();  // c_{j0-1} of every chunk visible (the first interval's halo)
   if (a.zero_old) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) cur[r] = vzero<df64>();
+    for (int r = 0; r < R; ++r) cur[r] = vzero<V>();
   } else {
     load_units(B0 + (long long)((j0 - 1) % 3) * nx, tid, 0, 4, cur);
   }
   float ss = 0.0f;
   for (int j = j0; j < j1; ++j) {
     const int par = j & 1;
-    df64 old[R];
-    df64 w[R + H];
+    V old[R];
+    V w[R + H];
     if (a.zero_old) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) old[r] = vzero<df64>();
+      for (int r = 0; r < R; ++r) old[r] = vzero<V>();
 #pragma unroll
-      for (int q = 0; q < H; ++q) w[q] = vzero<df64>();
+      for (int q = 0; q < H; ++q) w[q] = vzero<V>();
     } else {
       asm volatile("cp.async.wait_all;\n" ::: "memory");  // this thread's chunk of c_j
       if (j + 1 < j1) prefetch(j + 1);  // into the buffer of c_{j-2}, read by its last reader before the last barrier
       load_units(B0 + (long long)(j % 3) * nx, tid, 0, 4, old);
-      df64 tail[4];
+      V tail[4];
       load_units(B0 + (long long)((j + 2) % 3) * nx, tl, 2, 2, tail);  // c_{j-1}, points 4..7 of the neighbour
 #pragma unroll
       for (int q = 0; q < H; ++q) w[q] = tail[4 - H + q];
@@ -1032,28 +1069,28 @@ __global__ void __launch_bounds__(1024) fcf_df_regrun_kernel(const FcfArgs a, co
     for (int r = 0; r < R; ++r) w[H + r] = cur[r];
     unsigned nzw = 0;
 #pragma unroll
-    for (int q = 0; q < R + H; ++q) nzw |= __float_as_uint(w[q].hi);
-    df64 v[R];
-    if (__any_sync(0xffffffffu, (nzw & 0x7fffffffu) != 0)) {  // Phi^m 0 = 0
+    for (int q = 0; q < R + H; ++q) nzw |= Op::nz(w[q]);
+    V v[R];
+    if (__any_sync(0xffffffffu, (nzw & Op::kNzMask) != 0)) {  // Phi^m 0 = 0
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        df64 acc = df_mul(dense_coef<df64>(t, 0), w[r]);
+        V acc = Op::mul(dense_coef<V>(t, 0), w[r]);
 #pragma unroll
-        for (int k = 1; k < SPAN; ++k) acc = vfma1<df64>(dense_coef<df64>(t, k), w[r + k], acc, t.one);
-        v[r] = vfinish<df64>(acc);
+        for (int k = 1; k < SPAN; ++k) acc = vfma1<V>(dense_coef<V>(t, k), w[r + k], acc, t.one);
+        v[r] = vfinish<V>(acc);
       }
     } else {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = vzero<df64>();
+      for (int r = 0; r < R; ++r) v[r] = vzero<V>();
     }
-    df64* cnd = reinterpret_cast<df64*>(a.c_new) + (long long)j * nx;
+    V* cnd = reinterpret_cast<V*>(a.c_new) + (long long)j * nx;
 #pragma unroll
-    for (int r = 0; r < R; r += 2) st_df2(cnd + i0 + r, v[r], v[r + 1]);
+    for (int r = 0; r < R; r += 2) Op::st2(cnd + i0 + r, v[r], v[r + 1]);
     float rw[R + H];
     unsigned nzr = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      rw[H + r] = df_sub_f(v[r], old[r]);
+      rw[H + r] = Op::sub_f(v[r], old[r]);
       nzr |= __float_as_uint(rw[H + r]);
       cur[r] = old[r];
     }
@@ -1135,7 +1172,7 @@ __device__ __forceinline__ void fcf_body_df(const FcfArgs& a, const int j, const
         nx, [&](int i) { return a.zero_old ? 0.0 : __ldcg(start + i); },
         [&](int i, double v) {
           b0[pidx(i)] = df_from(v);
-          nz |= v != 0.0;
+          nz |= dnz(v);
         });
   }
   // precision 3 runs only on level 1, which has no right-hand side
@@ -1222,13 +1259,13 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
             const int q = pidx(e);
             b0[q] = v.x;
             b0[q + 1] = v.y;
-            nz |= (v.x != 0.0) | (v.y != 0.0);
+            nz |= dnz(v.x) | dnz(v.y);
           }))
     batched_loads<kLoadBatch, double>(
         nx, [&](int i) { return a.zero_old ? 0.0 : __ldcg(start + i); },
         [&](int i, double v) {
           b0[pidx(i)] = v;
-          nz |= v != 0.0;
+          nz |= dnz(v);
         });
   // Phi^m of an identically zero slab is zero (no right-hand side): the
   // steps are skipped, which leaves the result exactly as computed
@@ -1256,7 +1293,7 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const int j, const De
           cn[i] = v;
           const double rho = a.value_residual ? v : v - old;
           b1[pidx(i)] = rho;
-          nz |= rho != 0.0;
+          nz |= dnz(rho);
         });
     const bool run2 = __syncthreads_or(nz);
     if (!more) return;
@@ -1765,21 +1802,36 @@ static cudaError_t launch_fcf_stream(const FcfArgs& a, const DevTaps& t, cudaStr
   return cudaGetLastError();
 }
 
+// The register-resident run (fcf_regrun_kernel): an upwind stencil of SPAN
+// taps ending at the output point, nx / 8 threads of eight points each, three
+// slabs and the rho-tail slots in shared memory; persistent grid of as many
+// CTAs as fit on the SMs (at 64 registers per thread), at most one per
+// interval.
+template <int SPAN>
+static bool regrun_shape_ok(const FcfArgs& a, const DevTaps& t) {
+  return t.lo == -(SPAN - 1) && t.hi == 0 && a.nx % 256 == 0 && a.nx / 8 <= 1024;
+}
+static size_t regrun_smem(int nx) { return 3 * (size_t)nx * sizeof(double) + 2 * (size_t)(nx / 8) * sizeof(float4); }
+template <int SPAN, typename V>
+static cudaError_t launch_regrun(const FcfArgs& a, const DevTaps& t, cudaStream_t s) {
+  const size_t rsmem = regrun_smem(a.nx);
+  cudaError_t e = set_smem(fcf_regrun_kernel<SPAN, V>, rsmem);
+  if (e != cudaSuccess) return e;
+  const int th = a.nx / 8;
+  int per_sm = (int)((228 * 1024) / (rsmem + 1024));                // shared memory per SM
+  per_sm = per_sm < 2048 / th ? per_sm : 2048 / th;                  // threads per SM
+  per_sm = per_sm < 65536 / (64 * th) ? per_sm : 65536 / (64 * th);  // 64 registers per thread
+  per_sm = per_sm < 1 ? 1 : per_sm;
+  const int grid = a.N < per_sm * sm_count() ? a.N : per_sm * sm_count();
+  fcf_regrun_kernel<SPAN, V><<<grid, th, rsmem, s>>>(a, t);
+  return cudaGetLastError();
+}
+
 template <int SPAN>
 static cudaError_t launch_fcf_fused(const FcfArgs& a, const DevTaps& t, int threads, cudaStream_t s) {
-  const bool upwind = t.lo == -(SPAN - 1) && t.hi == 0 && a.nx % 256 == 0 && a.nx / 8 <= 1024;
-  const size_t rsmem = 3 * (size_t)a.nx * sizeof(double) + 2 * (size_t)(a.nx / 8) * sizeof(float4);
-  if (g_stream_fused == 1 && upwind && rsmem <= (size_t)kMaxSmemBytes) {
-    cudaError_t e = set_smem(fcf_df_regrun_kernel<SPAN>, rsmem);
-    if (e != cudaSuccess) return e;
-    const int th = a.nx / 8;
-    int per_sm = (int)((228 * 1024) / (rsmem + 1024));                // shared memory per SM
-    per_sm = per_sm < 2048 / th ? per_sm : 2048 / th;                  // threads per SM
-    per_sm = per_sm < 65536 / (64 * th) ? per_sm : 65536 / (64 * th);  // 64 registers per thread
-    per_sm = per_sm < 1 ? 1 : per_sm;
-    const int grid = a.N < per_sm * sm_count() ? a.N : per_sm * sm_count();
-    fcf_df_regrun_kernel<SPAN><<<grid, th, rsmem, s>>>(a, t);
-    return cudaGetLastError();
+  const bool upwind = regrun_shape_ok<SPAN>(a, t);
+  if (g_stream_fused == 1 && upwind && regrun_smem(a.nx) <= (size_t)kMaxSmemBytes) {
+    return launch_regrun<SPAN, df64>(a, t, s);
   }
   if (g_stream_fused == 4 && upwind) {
     fcf_df_reg_kernel<SPAN><<<a.N, a.nx / 8, 0, s>>>(a, t);
@@ -1795,6 +1847,18 @@ static cudaError_t launch_fcf_fused(const FcfArgs& a, const DevTaps& t, int thre
   return cudaGetLastError();
 }
 
+// MIXED (FP64 pass 1, FP32 pass 2 and residual) on the register-resident
+// run: the conditions of host_fused_ok with FP64 C-points, and the run's
+// shape.
+template <int SPAN>
+static bool host_regrun_mixed_ok(const FcfArgs& a, const DevTaps& t) {
+  auto al = [](const void* p) { return (reinterpret_cast<unsigned long long>(p) & 15ull) == 0; };
+  return g_stream_fused == 1 && t.span == SPAN && !a.df_store && a.m == 1 && a.fx.nl + a.fx.nr == 0 &&
+         !a.relax_f && !a.trunc && !a.value_residual && a.r_f && !a.g && regrun_shape_ok<SPAN>(a, t) &&
+         regrun_smem(a.nx) <= (size_t)kMaxSmemBytes && al(a.u_old) && al(a.c_new) && al(a.r_f) &&
+         (a.cstride & 1) == 0;
+}
+
 template <int PREC>
 static cudaError_t launch_fcf_fixed(const FcfArgs& a, const DevTaps& t, int threads, cudaStream_t s) {
   if constexpr (PREC == 3) {
@@ -1803,6 +1867,10 @@ static cudaError_t launch_fcf_fixed(const FcfArgs& a, const DevTaps& t, int thre
       if (t.span == 2) return launch_fcf_fused<2>(a, t, th, s);
       if (t.span == 5) return launch_fcf_fused<5>(a, t, th, s);
     }
+  }
+  if constexpr (PREC == 1) {
+    if (host_regrun_mixed_ok<2>(a, t)) return launch_regrun<2, double>(a, t, s);
+    if (host_regrun_mixed_ok<5>(a, t)) return launch_regrun<5, double>(a, t, s);
   }
   switch (t.span) {
     case 2: return launch_fcf_t<PREC, 8, 2>(a, t, threads, s);

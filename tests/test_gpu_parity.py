@@ -413,3 +413,41 @@ def test_fused_float_float_fcf_forms_agree(capi, monkeypatch, nx, nt, m, L):
         np.testing.assert_array_equal(a[1], b[1])
         np.testing.assert_array_equal(a[3], b[3])
         assert abs(a[2] - b[2]) <= 1e-6 * b[2], mode
+
+
+@pytest.mark.parametrize("nx,nt,m,L", [(4096, 16384, 4, 4), (512, 2048, 4, 2), (8192, 1024, 4, 3), (256, 4096, 4, 3),
+                                       (1024, 64, 4, 2)])
+def test_mixed_fcf_register_run_agrees(capi, monkeypatch, nx, nt, m, L):
+    """MIXED (FP64 C-point update, FP32 second pass) on ERK1+U1, m = 4: the
+    collapsed Phi^4 of 5 taps with one interval per CTA and the slab in shared
+    memory (form 0) and as register-resident runs of intervals with the next
+    slab prefetched (form 1, the default) give bitwise the same C-points and
+    iterations, and the same relaxation sweeps; where the oracle's sequential
+    stepping (Eq. 3) is small enough, the solve reaches its C-points to 1e-9."""
+    import torch
+    u0h = workloads.fourier_field(nx)
+    u0 = torch.tensor(u0h, device="cuda")
+    got = {}
+    for stream in ("0", "1"):
+        monkeypatch.setenv("MGRIT_FCF_STREAM", stream)
+        monkeypatch.setenv("MGRIT_FCF_SHAPE", "99,256,1")
+        o = capi.mgrit_opts_default(m=m, levels=L, precision=capi.PREC_MIXED, output=capi.OUT_CPOINTS, tol=1e-10)
+        h = capi.mgrit_setup(capi.problem(nx, nt, "ERK", 1, 1, 0.85), o)
+        try:
+            out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
+            r, _ = capi.mgrit_solve(h, u0, out)
+            assert r.converged == 1
+            rel_sweeps = capi.mgrit_relax(h, 3)
+            out2 = torch.empty_like(out)
+            capi.mgrit_solve(h, u0, out2)
+            got[stream] = (r.iterations, out.cpu().numpy(), rel_sweeps, out2.cpu().numpy())
+        finally:
+            capi.mgrit_destroy(h)
+    a, b = got["1"], got["0"]
+    assert a[0] == b[0]
+    np.testing.assert_array_equal(a[1], b[1])
+    np.testing.assert_array_equal(a[3], b[3])
+    assert np.isfinite(b[2]) and b[2] > 0 and abs(a[2] - b[2]) <= 1e-6 * b[2]
+    if nx * nt <= 2 ** 21:
+        ref = stepping.sequential(stepping.FineStep("ERK", 1, 0.85, nx), u0h, nt)[::m]
+        assert rel(a[1], ref) <= 1e-9
