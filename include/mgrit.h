@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define MGRIT_ABI_VERSION 5
+#define MGRIT_ABI_VERSION 6
 #define MGRIT_MAX_LEVELS 8
 #define MGRIT_MAX_HISTORY 128
 #define MGRIT_MAX_TAPS 256
@@ -404,6 +404,9 @@ typedef struct mgrit_server_counters {
   double gpu_coarse_ms;         /*   coarse solves                             */
   double gpu_gap_ms;            /* server stream idle between consecutive cycles */
   double first_cycle_s;         /* server creation to its first cycle's launch */
+  uint64_t fft_coarse_solves;   /* solves switched to the Fourier-space coarse
+                                   solve (chosen per cycle when few two-level
+                                   solves need a coarse solve; ABI 6) */
 } mgrit_server_counters;
 mgrit_status mgrit_server_stats(mgrit_server* s, mgrit_server_counters* out);
 

@@ -20,6 +20,7 @@ LIB = os.path.join(HERE, "libmgrit_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 SOURCES = ["kernels.cu", "sdirk.cu", "sdirk_k10.cu", "sdirk_k20.cu", "sdirk_k21.cu", "sdirk_k31.cu", "sdirk_k32.cu",
+           "sdirk_s10.cu", "sdirk_s20.cu", "sdirk_s21.cu", "sdirk_s31.cu", "sdirk_s32.cu",
            "setup.cpp", "driver.cpp", "server.cpp", "noalloc.cu", "fft.cu"]
 HEADERS = ["device.h", "setup.h", "handle.h", "sdirk_impl.cuh"]
 

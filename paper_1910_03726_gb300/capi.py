@@ -89,7 +89,7 @@ class MgritServerStats(C.Structure):
                 ("cycle_s", C.c_double),
                 ("retire_s", C.c_double), ("mean_active", C.c_double), ("peak_resident_bytes", C.c_double),
                 ("gpu_fcf_ms", C.c_double), ("gpu_norm_ms", C.c_double), ("gpu_coarse_ms", C.c_double),
-                ("gpu_gap_ms", C.c_double), ("first_cycle_s", C.c_double)]
+                ("gpu_gap_ms", C.c_double), ("first_cycle_s", C.c_double), ("fft_coarse_solves", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -833,9 +833,33 @@ static bool wants_coarse_fft(const mgrit_problem* p, const mgrit_opts* o, long l
     return false;
   return rows >= kFftMinRows || force;
 }
+static mgrit_status alloc_coarse_fft(mgrit_handle* h);
 static mgrit_status setup_coarse_fft(mgrit_handle* h) {
+  if (!wants_coarse_fft(&h->prob, &h->opts, h->Nl[h->L - 1])) return MGRIT_OK;
+  return alloc_coarse_fft(h);
+}
+// A server's two-level solve switched to the Fourier-space coarse solve on
+// first use (the server picks it per cycle when few solves need a coarse solve;
+// a batched march then costs its longest march).  Returns false, with nothing
+// changed, where the solve does not qualify.
+bool enable_coarse_fft(mgrit_handle* h) {
+  if (h->fft_coarse) return true;
+  const char* cm = std::getenv("MGRIT_COARSE");
+  if ((cm && std::strcmp(cm, "march") == 0) || h->L != 2 || h->redisc || h->inflow ||
+      !fft_coarse_supported(h->nx) || h->Nl[1] < kFftMinRows)
+    return false;
+  if (alloc_coarse_fft(h) != MGRIT_OK) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+size_t coarse_fft_bytes(const mgrit_handle* h) {
+  const size_t nh = (size_t)h->nx / 2 + 1;
+  return (2 * (size_t)h->Nl[h->L - 1] * nh + 3 * (size_t)h->nx + 2 * (size_t)kMaxScanBlocks * nh) * sizeof(double);
+}
+static mgrit_status alloc_coarse_fft(mgrit_handle* h) {
   const int nx = h->nx, rows = h->Nl[h->L - 1];
-  if (!wants_coarse_fft(&h->prob, &h->opts, rows)) return MGRIT_OK;
   double *spec = nullptr, *tab = nullptr, *carry = nullptr;
   mgrit_status st;
   const size_t nh = (size_t)nx / 2 + 1;  // independent modes of a real slab

@@ -128,6 +128,11 @@ mgrit_status enqueue_r0sq(mgrit_handle* h, double* dst, int* launches);
 // or all C-points c_init); u0 in FP64 into u0buf.
 mgrit_status load_iterate(mgrit_handle* h, const double* u0, const double* c_init);
 mgrit_status coarse_cycle(mgrit_handle* h, double* c_new);
+// Two-level periodic solve (nx = 2^p, at least 16 coarse steps): allocate and
+// fill the Fourier-space coarse solve's workspace on the handle's stream and
+// use it from then on; false (nothing changed) where it does not apply.
+bool enable_coarse_fft(mgrit_handle* h);
+size_t coarse_fft_bytes(const mgrit_handle* h);  // device bytes enable_coarse_fft adds
 // Build a handle; ops != nullptr supplies an already fitted hierarchy.
 // batched: a server's handle.  Its two-level coarse solves run in the
 // server's batched march (with about a thousand solves active, one batched

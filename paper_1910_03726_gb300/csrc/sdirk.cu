@@ -1,7 +1,10 @@
 // SDIRK fine steps: host-side launch dispatch over the recurrence orders
 // (KF, KB) of the stage matrix.  The kernels live in sdirk_impl.cuh and are
-// compiled once per (KF, KB) pair in sdirk_k<KF><KB>.cu.
+// compiled once per (KF, KB) pair in sdirk_k<KF><KB>.cu (the split level-1
+// FCF in sdirk_s<KF><KB>.cu).
 #include <cuda_runtime.h>
+
+#include <cstdlib>
 
 #include "device.h"
 
@@ -9,6 +12,8 @@ namespace mg {
 
 template <int KF, int KB>
 cudaError_t sdirk_fcf(const FcfArgs& a, const SdirkPlan& p, int precision, cudaStream_t s);
+template <int KF, int KB>
+cudaError_t sdirk_fcf_split(const FcfArgs& a, const SdirkPlan& p, int precision, cudaStream_t s);
 template <int KF, int KB>
 cudaError_t sdirk_fcf_batched(const BatchSolve* S, const BatchItem* items, int nitems, const SdirkPlan& any,
                               size_t smem, int precision, cudaStream_t s);
@@ -56,8 +61,22 @@ size_t sdirk_smem(const SdirkPlan& p) {
          (size_t)sdirk_slots(p) * padded_len(p.nx) * sizeof(double);
 }
 
+// The level-1 FCF with each interval's slab split over a cluster of two CTAs
+// (fcf_sdirk_cluster_kernel): chosen when one CTA per interval would hold 512
+// threads, which with the slab in registers during the scans leaves one CTA
+// per SM; needs C = 16, ql = 0 and half the threads a whole number of warps.
+// MGRIT_SDIRK_SPLIT = 0 / 1 turns it off / on wherever it applies.
+static bool sdirk_split_ok(const SdirkPlan& p) {
+  if (p.C != kSdirkCMax || p.ql != 0 || (p.threads / 2) % 32 != 0) return false;
+  const char* e = std::getenv("MGRIT_SDIRK_SPLIT");
+  if (e && *e) return std::atoi(e) != 0;
+  return p.threads == 512;
+}
+
 cudaError_t launch_fcf_sdirk(const FcfArgs& a, const SdirkPlan& p, int precision, cudaStream_t s) {
   if (a.N < 1) return cudaSuccess;
+  if (sdirk_split_ok(p))
+    return with_orders(p, [&]<int KF, int KB>() { return sdirk_fcf_split<KF, KB>(a, p, precision, s); });
   return with_orders(p, [&]<int KF, int KB>() { return sdirk_fcf<KF, KB>(a, p, precision, s); });
 }
 

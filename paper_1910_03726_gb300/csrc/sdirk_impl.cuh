@@ -26,12 +26,27 @@
 // for U1..U5, whose stage matrices keep -lo roots inside the unit circle).
 // Each instantiation file compiles one (KF, KB) pair.
 #pragma once
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "device.h"
 
 namespace mg {
 namespace sd {
+
+// CL = 1: one CTA per slab.  CL = 2: the slab split over a cluster of two
+// CTAs (CTA r owns points r*nx/2 ..), which exchange the scans' warp totals
+// through distributed shared memory; a barrier that orders those exchanges
+// spans the cluster.
+template <int CL>
+__device__ __forceinline__ void csync() {
+  if constexpr (CL == 1) __syncthreads();
+  else cooperative_groups::this_cluster().sync();
+}
+// The two halves of a cluster barrier (release / acquire), so that work that
+// needs no other CTA's data runs while the partner arrives.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
 
 __device__ __forceinline__ int wrapn(int k, int nx) {
   k = (k < 0) ? k + nx : k;
@@ -80,16 +95,23 @@ __device__ __forceinline__ void matvec_acc(const T* M, const T (&x)[K], T (&y)[K
 // lies below rounding too, so a chunk only feels the previous warp's total
 // (periodically: warp 0 feels the last warp's) and the closure is the
 // identity.  Both are decided on the host from the norms of the powers.
-template <typename T, int C, int K, bool BWD>
-__device__ __forceinline__ void rec_scan(T (&x)[C], const T* __restrict__ tb, T* smw, int steps, bool trunc) {
+// With CL = 2 the warps of both CTAs form one scan over the slab (global
+// warp rank * warps + w): lane 31 of each warp stores its chunk-end state in
+// its own and in the partner's smw (smw_peer), and after the cluster barrier
+// every CTA reads all warp totals locally.
+template <typename T, int C, int K, bool BWD, int CL = 1>
+__device__ __forceinline__ void rec_scan(T (&x)[C], const T* __restrict__ tb, T* smw, T* smw_peer, int rank,
+                                         int steps, bool trunc) {
   if constexpr (K > 0) {
     const T* lanep = tb + K;
     const T* warpp = lanep + 33 * K * K;
     const T* G = warpp + 17 * K * K;
     const T* Q = G + C * K;
-    const int nw = blockDim.x >> 5;
+    const int nwl = blockDim.x >> 5;
+    const int nw = nwl * CL;
+    const int gw = rank * nwl + (int)(threadIdx.x >> 5);
     const int lane = BWD ? 31 - (int)(threadIdx.x & 31) : (int)(threadIdx.x & 31);
-    const int warp = BWD ? nw - 1 - (int)(threadIdx.x >> 5) : (int)(threadIdx.x >> 5);
+    const int warp = BWD ? nw - 1 - gw : gw;
 #define MG_XM(cc) x[BWD ? C - 1 - (cc) : (cc)]
     T aq[K];
 #pragma unroll
@@ -118,14 +140,19 @@ __device__ __forceinline__ void rec_scan(T (&x)[C], const T* __restrict__ tb, T*
     }
     if (lane == 31)
 #pragma unroll
-      for (int q = 0; q < K; ++q) smw[warp * K + q] = S[q];
-    __syncthreads();
+      for (int q = 0; q < K; ++q) {
+        smw[warp * K + q] = S[q];
+        if constexpr (CL > 1) smw_peer[warp * K + q] = S[q];
+      }
+    if constexpr (CL > 1) cluster_arrive();
+    else __syncthreads();
     T P[K], V[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       const T v = shfl_prev(S[q], 1, BWD);
       P[q] = lane > 0 ? v : (T)0;
     }
+    if constexpr (CL > 1) cluster_wait();
     if (trunc) {
       // 3'. carry from the previous warp's total (the last warp's for warp 0)
       const int wp = warp == 0 ? nw - 1 : warp - 1;
@@ -171,13 +198,15 @@ __device__ __forceinline__ void rec_scan(T (&x)[C], const T* __restrict__ tb, T*
       MG_XM(cc) = acc;
     }
 #undef MG_XM
-    // smw is written again only after the caller's next __syncthreads
+    // smw is written again only after the caller's next barrier (CL = 2: a
+    // cluster barrier, which the partner must pass before its next store)
   }
 }
 
 // u <- Phi u.  u in slot 0; slots 1..s-2 hold A_3..A_s (A_2 replaces u in slot 0).
-template <typename T, int C, int KF, int KB>
-__device__ __forceinline__ void sdirk_step(const SdirkPlan& p, T* slab, int plen, int nx, const T* tab, T* smw) {
+template <typename T, int C, int KF, int KB, int CL = 1>
+__device__ __forceinline__ void sdirk_step(const SdirkPlan& p, T* slab, int plen, int nx, const T* tab, T* smw,
+                                           T* smw_peer = nullptr, int rank = 0) {
   const int s = p.s, base = threadIdx.x * C;
   const T sc = Prec<T>::scale(p), ig = Prec<T>::inv_gamma(p), g = Prec<T>::gamma(p);
   const T* tf = tab;
@@ -187,8 +216,9 @@ __device__ __forceinline__ void sdirk_step(const SdirkPlan& p, T* slab, int plen
     T x[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) x[c] = in[pix(wrapn(base + c + p.ql, nx))];
-    rec_scan<T, C, KF, false>(x, tf, smw, p.steps_f, p.trunc_f);
-    rec_scan<T, C, KB, true>(x, tb, smw + 16 * kMaxRec, p.steps_b, p.trunc_b);
+    rec_scan<T, C, KF, false, CL>(x, tf, smw, smw_peer, rank, p.steps_f, p.trunc_f);
+    rec_scan<T, C, KB, true, CL>(x, tb, smw + 16 * kMaxRec, CL > 1 ? smw_peer + 16 * kMaxRec : nullptr, rank,
+                                 p.steps_b, p.trunc_b);
     if constexpr (KF == 0 && KB == 0) __syncthreads();
 #pragma unroll
     for (int c = 0; c < C; ++c) {
@@ -206,7 +236,12 @@ __device__ __forceinline__ void sdirk_step(const SdirkPlan& p, T* slab, int plen
         if (st == s) slab[e] = fma(g, kv, A);  // u_new = A_s + gamma K_s
       }
     }
-    __syncthreads();
+    // CL = 2: a store into the partner's smw of one direction waits for the
+    // partner's reads of that direction in the stage before.  With both
+    // directions the other direction's cluster barrier lies between them; a
+    // forward recurrence alone needs this barrier to span the cluster.
+    if constexpr (CL > 1 && KB == 0) csync<CL>();
+    else __syncthreads();
   }
 }
 
@@ -246,14 +281,61 @@ __device__ __forceinline__ void load_tables(const SdirkPlan& p, const Smem& m) {
   }
 }
 
+// What a CTA of a 2-CTA cluster shares with its partner beyond the scans: the
+// partner's smw, its own rank, and slots (own and partner's) for the
+// cluster-wide zero-slab votes and the two halves' squared norms.
+struct ClusterLink {
+  double* smw_peer = nullptr;
+  int rank = 0;
+  int* vote = nullptr;
+  int* vote_peer = nullptr;
+  double* ss = nullptr;
+  double* ss_peer = nullptr;
+};
+
+// __syncthreads_or over the slab: with CL = 2 both CTAs take the same branch.
+// Each call site has its own pair of slots.
+template <int CL>
+__device__ __forceinline__ bool slab_or(int v, const ClusterLink& L, int site) {
+  const int mine = __syncthreads_or(v);
+  if constexpr (CL == 1) {
+    return mine != 0;
+  } else {
+    if (threadIdx.x == 0) {
+      L.vote[2 * site + L.rank] = mine;
+      L.vote_peer[2 * site + L.rank] = mine;
+    }
+    csync<CL>();
+    return (L.vote[2 * site] | L.vote[2 * site + 1]) != 0;
+  }
+}
+
+// partial[j] = the slab's squared norm (a block sum per CTA; with CL = 2 rank
+// 0 adds its half and the partner's, in that order).
+template <int CL>
+__device__ __forceinline__ void store_partial(double* partial, int j, double ss, const ClusterLink& L) {
+  ss = block_sum(ss);
+  if constexpr (CL == 1) {
+    if (threadIdx.x == 0) partial[j] = ss;
+  } else {
+    if (threadIdx.x == 0) {
+      L.ss[L.rank] = ss;
+      L.ss_peer[L.rank] = ss;
+    }
+    csync<CL>();
+    if (L.rank == 0 && threadIdx.x == 0) partial[j] = L.ss[0] + L.ss[1];
+  }
+}
+
 // One interval's FCF-relaxation and fused residual (see fcf_kernel): m steps
-// from c_{j-1}, rho_j = v - c_j, then r_{j+1} = Phi^m rho_j.
-template <int PREC, int C, int KF, int KB>
+// from c_{j-1}, rho_j = v - c_j, then r_{j+1} = Phi^m rho_j.  CL = 2: this CTA
+// holds points x0 .. x0 + nx/2 - 1 of the slab (x0 = rank * nx/2).
+template <int PREC, int C, int KF, int KB, int CL = 1>
 __device__ __forceinline__ void fcf_body(const FcfArgs& a, const SdirkPlan& p, int j, const Smem& sm,
-                                         double* smw) {
-  const int nx = a.nx, m = a.m, plen = padded_len(nx);
+                                         double* smw, const ClusterLink& L = ClusterLink()) {
+  const int nxg = a.nx, nx = nxg / CL, x0 = L.rank * nx, m = a.m, plen = padded_len(nx);
   double* slab = sm.slab;
-  const double* start = a.u_old + (long long)(j - 1) * a.cstride;
+  const double* start = a.u_old + (long long)(j - 1) * a.cstride + x0;
   int nz = 0;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     const double v = a.zero_old ? 0.0 : start[i];
@@ -261,10 +343,11 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const SdirkPlan& p, i
     nz |= v != 0.0;
   }
   // Phi^m of an identically zero slab is zero: the steps are skipped
-  const bool run1 = __syncthreads_or(nz);
-  for (int s = 0; s < m && run1; ++s) sdirk_step<double, C, KF, KB>(p, slab, plen, nx, sm.t64, smw);
-  const double* oldj = a.u_old + (long long)j * a.cstride;
-  double* cn = a.c_new + (long long)j * nx;
+  const bool run1 = slab_or<CL>(nz, L, 0);
+  for (int s = 0; s < m && run1; ++s)
+    sdirk_step<double, C, KF, KB, CL>(p, slab, plen, nx, sm.t64, smw, L.smw_peer, L.rank);
+  const double* oldj = a.u_old + (long long)j * a.cstride + x0;
+  double* cn = a.c_new + (long long)j * nxg + x0;
   const bool more = j < a.N;
   double ss = 0.0;
   if (a.relax_f) {  // F-relaxation only: the C-point keeps its value, r_j = v - c_j
@@ -272,14 +355,11 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const SdirkPlan& p, i
       const double old = a.zero_old ? 0.0 : oldj[i];
       const double rho = slab[pix(i)] - old;
       cn[i] = old;
-      if (a.r_f) a.r_f[(long long)j * nx + i] = (float)rho;
-      else a.r[(long long)j * nx + i] = rho;
+      if (a.r_f) a.r_f[(long long)j * nxg + x0 + i] = (float)rho;
+      else a.r[(long long)j * nxg + x0 + i] = rho;
       ss = fma(rho, rho, ss);
     }
-    if (a.partial) {
-      ss = block_sum(ss);
-      if (threadIdx.x == 0) a.partial[j] = ss;
-    }
+    if (a.partial) store_partial<CL>(a.partial, j, ss, L);
     return;
   }
   if (PREC == 0) {
@@ -291,10 +371,11 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const SdirkPlan& p, i
       slab[pix(i)] = rho;
       nz |= rho != 0.0;
     }
-    const bool run2 = __syncthreads_or(nz);
+    const bool run2 = slab_or<CL>(nz, L, 1);
     if (!more) return;
-    for (int s = 0; s < m && run2; ++s) sdirk_step<double, C, KF, KB>(p, slab, plen, nx, sm.t64, smw);
-    double* rr = a.r + (long long)(j + 1) * nx;
+    for (int s = 0; s < m && run2; ++s)
+      sdirk_step<double, C, KF, KB, CL>(p, slab, plen, nx, sm.t64, smw, L.smw_peer, L.rank);
+    double* rr = a.r + (long long)(j + 1) * nxg + x0;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       const double v = slab[pix(i)];
       rr[i] = v;
@@ -318,23 +399,21 @@ __device__ __forceinline__ void fcf_body(const FcfArgs& a, const SdirkPlan& p, i
       fs[pix(i)] = rho;
       nz |= rho != 0.0f;
     }
-    const bool run2 = __syncthreads_or(nz);
+    const bool run2 = slab_or<CL>(nz, L, 1);
     if (!more) return;
     for (int s = 0; s < m && run2; ++s)
-      sdirk_step<float, C, KF, KB>(p, fs, plen, nx, sm.t32, reinterpret_cast<float*>(smw));
+      sdirk_step<float, C, KF, KB, CL>(p, fs, plen, nx, sm.t32, reinterpret_cast<float*>(smw),
+                                       reinterpret_cast<float*>(L.smw_peer), L.rank);
     float ssf = 0.0f;  // FP32 residual (FP32 storage if r_f), per-thread FP32 sums
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       const float v = fs[pix(i)];
-      if (a.r_f) a.r_f[(long long)(j + 1) * nx + i] = v;
-      else a.r[(long long)(j + 1) * nx + i] = (double)v;
+      if (a.r_f) a.r_f[(long long)(j + 1) * nxg + x0 + i] = v;
+      else a.r[(long long)(j + 1) * nxg + x0 + i] = (double)v;
       ssf = fmaf(v, v, ssf);
     }
     ss = (double)ssf;
   }
-  if (a.partial) {
-    ss = block_sum(ss);
-    if (threadIdx.x == 0) a.partial[j] = ss;
-  }
+  if (a.partial) store_partial<CL>(a.partial, j, ss, L);
 }
 
 template <int PREC, int C, int KF, int KB>
@@ -344,6 +423,32 @@ __global__ void __launch_bounds__(512) fcf_sdirk_kernel(const FcfArgs a, const S
   const Smem sm = carve(smraw, p);
   load_tables(p, sm);
   fcf_body<PREC, C, KF, KB>(a, p, blockIdx.x + 1, sm, smw);
+}
+
+// One interval per cluster of two CTAs (blocks 2(j-1), 2(j-1)+1), each with
+// half the slab, half the threads and half the shared memory of
+// fcf_sdirk_kernel, so that two CTAs of different intervals share an SM.
+// Needs ql = 0 (a stage's input is the thread's own points; every U1..U5
+// stage matrix has -lo roots inside the unit circle, so ql = -lo - KF = 0).
+template <int PREC, int C, int KF, int KB>
+__global__ void __launch_bounds__(256, 2) fcf_sdirk_cluster_kernel(const FcfArgs a, const SdirkPlan p) {
+  extern __shared__ __align__(256) unsigned char smraw[];
+  __shared__ __align__(16) double smw[2 * 16 * kMaxRec];
+  __shared__ int vote[4];
+  __shared__ double ssum[2];
+  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+  ClusterLink L;
+  L.rank = (int)cl.block_rank();
+  L.smw_peer = cl.map_shared_rank(smw, L.rank ^ 1);
+  L.vote = vote;
+  L.vote_peer = cl.map_shared_rank(vote, L.rank ^ 1);
+  L.ss = ssum;
+  L.ss_peer = cl.map_shared_rank(ssum, L.rank ^ 1);
+  const Smem sm = carve(smraw, p);
+  load_tables(p, sm);
+  cl.sync();  // both CTAs run before either stores into the other's shared memory
+  fcf_body<PREC, C, KF, KB, 2>(a, p, (int)(blockIdx.x >> 1) + 1, sm, smw, L);
+  cl.sync();  // no CTA leaves while its partner may still store into it
 }
 
 // Batched over solves: one CTA per (solve, interval) item.
@@ -452,6 +557,31 @@ static cudaError_t with_chunk(int C, F&& f) {
   }
 }
 
+// Shared memory of one CTA of the split form: the full tables, half the slabs.
+inline size_t split_smem(const SdirkPlan& p) {
+  return round256((size_t)p.tab_len * 8) + round256((size_t)p.tab_len * 4) +
+         (size_t)sdirk_slots(p) * padded_len(p.nx / 2) * sizeof(double);
+}
+template <typename Kern>
+static cudaError_t launch_split(Kern kernel, const FcfArgs& a, const SdirkPlan& p, cudaStream_t s) {
+  const size_t smem = split_smem(p);
+  cudaError_t e = smem_attr(kernel, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * a.N);
+  cfg.blockDim = dim3(p.threads / 2);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, a, p);
+}
+
 }  // namespace sd
 
 // Launchers for one (KF, KB) pair; instantiated by sdirk_k<KF><KB>.cu.
@@ -512,6 +642,17 @@ cudaError_t sdirk_coarse_march(const double* g, const float* g_f, double* c_add,
     return cudaGetLastError();
   });
 }
+
+// The split form (C = 16 only); instantiated by sdirk_s<KF><KB>.cu.
+template <int KF, int KB>
+cudaError_t sdirk_fcf_split(const FcfArgs& a, const SdirkPlan& p, int precision, cudaStream_t s) {
+  constexpr int C = kSdirkCMax;
+  if (p.C != C) return cudaErrorInvalidValue;
+  return precision == 0 ? sd::launch_split(sd::fcf_sdirk_cluster_kernel<0, C, KF, KB>, a, p, s)
+                        : sd::launch_split(sd::fcf_sdirk_cluster_kernel<1, C, KF, KB>, a, p, s);
+}
+#define MG_SDIRK_SPLIT_INSTANTIATE(KF, KB) \
+  template cudaError_t sdirk_fcf_split<KF, KB>(const FcfArgs&, const SdirkPlan&, int, cudaStream_t);
 
 #define MG_SDIRK_INSTANTIATE(KF, KB)                                                                             \
   template cudaError_t sdirk_fcf<KF, KB>(const FcfArgs&, const SdirkPlan&, int, cudaStream_t);                   \

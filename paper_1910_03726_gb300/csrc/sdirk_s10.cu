@@ -1,0 +1,6 @@
+// SDIRK level-1 FCF split over a cluster of two CTAs, recurrence orders (1, 0).
+#include "sdirk_impl.cuh"
+
+namespace mg {
+MG_SDIRK_SPLIT_INSTANTIATE(1, 0)
+}  // namespace mg

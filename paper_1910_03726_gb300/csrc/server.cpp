@@ -459,6 +459,41 @@ static mgrit_status cycle_back(mgrit_server* S, const std::vector<Request*>& act
       by_cluster[r->h->march_cluster].push_back(k);
     }
   }
+  // ---- few two-level solves: a Fourier-space coarse solve each (workspace set
+  // up on first use, within the budget) when their summed cost is below the
+  // batched march's, which is that of its longest march.  Estimates from the
+  // measured kernels: a march step 0.6 us + 1 ns per point (a Psi step on the
+  // cluster and its barrier); a Fourier-space solve 80 us + 0.04 ns per coarse
+  // point (two transforms of log2 nx dependent stages and two scan passes).
+  {
+    double march_us = 0.0, fft_us = 0.0;
+    for (auto& g : by_cluster)
+      for (int k : g.second) {
+        const mgrit_handle* h = act[k]->h;
+        march_us = std::max(march_us, h->Nl[1] * (0.6 + 1e-3 * h->nx));
+        fft_us += 80.0 + 4e-5 * (double)h->Nl[1] * h->nx;
+      }
+    if (fft_us < march_us) {
+      std::lock_guard<std::mutex> lk(S->mu);
+      for (auto& g : by_cluster) {
+        std::vector<int> keep;
+        for (int k : g.second) {
+          Request* r = act[k];
+          if ((double)(S->resident + coarse_fft_bytes(r->h)) <= S->o.hbm_budget_bytes && enable_coarse_fft(r->h)) {
+            S->resident += r->h->bytes - std::min(r->h->bytes, r->bytes);
+            r->bytes = r->h->bytes;
+            S->stats.peak_resident_bytes = std::max(S->stats.peak_resident_bytes, (double)S->resident);
+            S->stats.fft_coarse_solves++;
+          } else {
+            keep.push_back(k);
+          }
+        }
+        g.second.swap(keep);
+      }
+      for (auto it = by_cluster.begin(); it != by_cluster.end();)
+        it = it->second.empty() ? by_cluster.erase(it) : std::next(it);
+    }
+  }
   // ---- coarse solves: batched cluster marches (two-level), V-cycles (multilevel);
   // each group's solve ids at their own offset, so no group waits for another
   {

@@ -30,7 +30,7 @@ def test_exports_every_declared_entry_point(capi):
     assert "mgrit_setup" in names and "mgrit_poll" in names
     missing = [n for n in names if not hasattr(capi._lib, n)]
     assert not missing, missing
-    assert capi.mgrit_abi_version() == 5
+    assert capi.mgrit_abi_version() == 6
 
 
 def test_struct_layouts_match_the_header(capi):
@@ -43,6 +43,7 @@ def test_struct_layouts_match_the_header(capi):
     assert not o.psi_user_nnz and not o.psi_user_offsets and not o.psi_user_coeffs
     import ctypes as C
     assert C.sizeof(capi.MgritProblem) == 56 and C.sizeof(capi.MgritOpts) == 104
+    assert C.sizeof(capi.MgritServerStats) == 17 * 8   # ABI 6: fft_coarse_solves last
 
 
 @pytest.mark.parametrize("alpha,xmin,xmax,status", [(-1.0, -1.0, 1.0, -10), (1.0, 1.0, -1.0, -1),

@@ -162,3 +162,36 @@ def test_rediscretised_coarse_step_matches_oracle(capi, p, m):
     for _ in range(k):
         ref = st(ref)
     assert rel(yout.cpu().numpy(), ref) <= TOL
+
+
+@pytest.mark.parametrize("p,q,nx,nt,m,L,prec,relax", [
+    (3, 5, 8192, 256, 16, 2, 1, 0), (3, 5, 8192, 256, 16, 2, 0, 0), (1, 1, 2048, 512, 4, 2, 0, 0),
+    (2, 2, 4096, 256, 8, 3, 1, 0), (2, 3, 2048, 512, 8, 2, 0, 1), (4, 4, 4096, 512, 16, 2, 1, 1),
+    (3, 5, 1024, 1024, 4, 3, 0, 0)])
+def test_sdirk_fcf_split_over_a_cluster_agrees(capi, monkeypatch, p, q, nx, nt, m, L, prec, relax):
+    """The level-1 SDIRK FCF with each interval's slab split over a cluster of
+    two CTAs (the scans' warp totals exchanged through distributed shared
+    memory; automatic at nx = 8192) gives bitwise the C-points and the
+    iterations of one CTA per interval, for every recurrence-order pair
+    (U1..U5), FP64 and MIXED, FCF- and F-relaxation.  The norms are the same
+    sums in another order: in FP64 to rounding, in MIXED to the FP32 rounding
+    of the per-thread sums (a thread of the split form sums other points)."""
+    import torch
+    u0 = torch.tensor(workloads.fourier_field(nx), device="cuda")
+    got = {}
+    for split in ("0", "1"):
+        monkeypatch.setenv("MGRIT_SDIRK_SPLIT", split)
+        o = capi.mgrit_opts_default(m=m, levels=L, precision=prec, relax=relax, output=1, tol=1e-10,
+                                    psi_rule=2, max_iter=60)
+        h = capi.mgrit_setup(capi.problem(nx, nt, "SDIRK", p, q, 4.0), o)
+        try:
+            out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
+            r, _ = capi.mgrit_solve(h, u0, out)
+            assert r.converged == 1
+            got[split] = (r.iterations, r.rel_residual, out.cpu().numpy())
+        finally:
+            capi.mgrit_destroy(h)
+    a, b = got["1"], got["0"]
+    assert a[0] == b[0]
+    np.testing.assert_array_equal(a[2], b[2])
+    assert abs(a[1] - b[1]) <= (1e-12 if prec == 0 else 1e-6) * b[1]
