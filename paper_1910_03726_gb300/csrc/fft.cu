@@ -23,13 +23,18 @@
 // is identically zero transforms to exact zeros, and a zero spectrum back to
 // exact zeros, so coarse corrections of C-points that are already exact stay
 // exactly zero (as in the march).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
+
+#include <cstdlib>
 
 #include "device.h"
 
 namespace mg {
 
 namespace {
+
+namespace cg = cooperative_groups;
 
 struct cplx64 {
   double re, im;
@@ -204,6 +209,156 @@ __global__ void __launch_bounds__(512) fft_inverse_kernel(const cplx64* __restri
   }
 }
 
+// The same transforms with a slab split over a cluster of kFftSplit CTAs, for
+// coarse levels with fewer slabs than SMs (one CTA per slab would leave most
+// SMs idle while it runs its log2 h dependent passes).  CTA r holds points
+// r q .. (r+1) q - 1 of the half-length array (q = h / kFftSplit): the first
+// log2 q passes pair points inside a CTA's block (twiddles as in fft_passes:
+// a block starts at a multiple of 2 half); the last log2 kFftSplit pair points
+// of different CTAs, read through distributed shared memory and written to
+// the other of two buffers, one cluster barrier per pass.
+constexpr int kFftSplit = 4;
+
+template <bool INV>
+__device__ __forceinline__ cplx64 tw_at(const cplx64* __restrict__ tw, int k) {
+  cplx64 w = tw[k];
+  if (INV) w.im = -w.im;
+  return w;
+}
+
+// Passes of the split transform; returns the buffer that holds the result.
+template <bool INV>
+__device__ __forceinline__ cplx64* fft_passes_split(cplx64* b0, cplx64* b1, const cplx64* __restrict__ tw, int h,
+                                                    int q, int rank, cg::cluster_group& cl) {
+  for (int half = 1; half < q; half <<= 1) {  // inside the block
+    const int stride = 2 * (h / (2 * half));
+    for (int b = threadIdx.x; b < q / 2; b += blockDim.x) {
+      const int pos = b & (half - 1);
+      const int i = ((b - pos) << 1) + pos;
+      const int j = i + half;
+      const cplx64 t = cmul(tw_at<INV>(tw, pos * stride), b0[j]);
+      const cplx64 u = b0[i];
+      b0[i] = {u.re + t.re, u.im + t.im};
+      b0[j] = {u.re - t.re, u.im - t.im};
+    }
+    __syncthreads();
+  }
+  cl.sync();  // every block's inner passes done before the blocks are read across the cluster
+  cplx64* cur = b0;
+  cplx64* nxt = b1;
+  const int base = rank * q;
+  for (int half = q; half < h; half <<= 1) {  // across blocks
+    const int stride = 2 * (h / (2 * half));
+    for (int p = threadIdx.x; p < q; p += blockDim.x) {
+      const int g = base + p;
+      const int gi = g & ~half, gj = gi | half;
+      const cplx64* su = cl.map_shared_rank(cur, (unsigned)(gi / q));
+      const cplx64* sv = cl.map_shared_rank(cur, (unsigned)(gj / q));
+      const cplx64 u = su[gi % q];
+      const cplx64 t = cmul(tw_at<INV>(tw, (gi & (half - 1)) * stride), sv[gj % q]);
+      nxt[p] = g == gi ? cplx64{u.re + t.re, u.im + t.im} : cplx64{u.re - t.re, u.im - t.im};
+    }
+    cl.sync();  // the pass's reads done everywhere before the next pass writes the buffer they read
+    cplx64* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+  return cur;
+}
+
+__global__ void __launch_bounds__(512) fft_forward_split_kernel(const double* __restrict__ g,
+                                                                const float* __restrict__ g_f,
+                                                                cplx64* __restrict__ spec,
+                                                                const cplx64* __restrict__ tw, int nx, int logh) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int h = nx / 2, q = h / kFftSplit, rank = (int)cl.block_rank(), base = rank * q;
+  cplx64* b0 = reinterpret_cast<cplx64*>(smraw);
+  cplx64* b1 = b0 + q;
+  const long long n = blockIdx.x / kFftSplit + 1;
+  for (int p = threadIdx.x; p < q; p += blockDim.x) {
+    const int j = bitrev(base + p, logh);
+    double a, b;
+    if (g_f) {
+      const float2 v = __ldcg(reinterpret_cast<const float2*>(g_f + n * nx) + j);
+      a = v.x;
+      b = v.y;
+    } else {
+      const double2 v = __ldcg(reinterpret_cast<const double2*>(g + n * nx) + j);
+      a = v.x;
+      b = v.y;
+    }
+    b0[p] = {a, b};
+  }
+  __syncthreads();
+  const cplx64* z = fft_passes_split<false>(b0, b1, tw, h, q, rank, cl);
+  cplx64* out = spec + (n - 1) * (h + 1);
+  for (int p = threadIdx.x; p <= q; p += blockDim.x) {
+    const int k = base + p;
+    if (p == q && k != h) break;  // mode h: the last CTA
+    const int ka = k == h ? 0 : k, kc = k == 0 ? 0 : h - k;
+    const cplx64 zk = cl.map_shared_rank(z, (unsigned)(ka / q))[ka % q];
+    const cplx64 zc = cl.map_shared_rank(z, (unsigned)(kc / q))[kc % q];  // Z_{h-k}, Z_h = Z_0
+    const cplx64 e = {0.5 * (zk.re + zc.re), 0.5 * (zk.im - zc.im)};
+    const cplx64 o = {0.5 * (zk.im + zc.im), -0.5 * (zk.re - zc.re)};
+    const cplx64 w = k == h ? cplx64{-1.0, 0.0} : tw[k];
+    const cplx64 wo = cmul(w, o);
+    out[k] = {e.re + wo.re, e.im + wo.im};
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+__global__ void __launch_bounds__(512) fft_inverse_split_kernel(const cplx64* __restrict__ spec,
+                                                                const cplx64* __restrict__ tw, int nx, int logh,
+                                                                MarchArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int h = nx / 2, q = h / kFftSplit, rank = (int)cl.block_rank(), base = rank * q;
+  cplx64* b0 = reinterpret_cast<cplx64*>(smraw);
+  cplx64* b1 = b0 + q;
+  const long long n = blockIdx.x / kFftSplit + 1;
+  const cplx64* in = spec + (n - 1) * (h + 1);
+  for (int p = threadIdx.x; p < q; p += blockDim.x) {
+    const int k = bitrev(base + p, logh);
+    const cplx64 xk = in[k];
+    const cplx64 xc = in[h - k];
+    const cplx64 e = {0.5 * (xk.re + xc.re), 0.5 * (xk.im - xc.im)};
+    const cplx64 d = {0.5 * (xk.re - xc.re), 0.5 * (xk.im + xc.im)};
+    const cplx64 w = {tw[k].re, -tw[k].im};
+    const cplx64 o = cmul(w, d);
+    b0[p] = {e.re - o.im, e.im + o.re};
+  }
+  __syncthreads();
+  const cplx64* z = fft_passes_split<true>(b0, b1, tw, h, q, rank, cl);
+  const double scale = 1.0 / h;
+  const bool store = (a.u_out || a.u_out_f) && (n % a.store_every) == 0;
+  for (int p = threadIdx.x; p < q; p += blockDim.x) {
+    const int j = base + p;
+    const double ev[2] = {z[p].re * scale, z[p].im * scale};
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int i = 2 * j + r;
+      const double e = ev[r];
+      if (a.c_add && a.c_add_df) {
+        float2* c = reinterpret_cast<float2*>(a.c_add) + n * nx + i;
+        const float2 v = *c;
+        const double s = ((double)v.x + (double)v.y) + e;
+        const float hi = (float)s;
+        *c = make_float2(hi, (float)(s - (double)hi));
+      } else if (a.c_add) {
+        a.c_add[n * nx + i] += e;
+      }
+      if (store) {
+        const long long o = (n / a.store_every) * nx + i;
+        if (a.u_out_f) a.u_out_f[o] = (float)e;
+        else a.u_out[o] = e;
+      }
+    }
+  }
+  // the last cross pass ended with a cluster barrier: no other CTA reads this
+  // one's shared memory any more
+}
+
 // tw[k] = exp(-2 pi i k / nx), k < nx/2, and mu_k = sum_t psi_t
 // exp(2 pi i (off_t k mod nx) / nx), k < nx, in FP64 (sincospi keeps the
 // reduced argument exact).
@@ -254,6 +409,50 @@ static int scan_blocks(int rows, int mblocks) {
   return (rows + L - 1) / L;
 }
 
+// The split transforms where a coarse level has fewer slabs than SMs and a
+// CTA's block keeps at least 256 points (nx >= 2048); MGRIT_FFT_SPLIT = 0 / 1
+// turns them off / on wherever the size allows.
+static int sm_count_fft() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = 152;
+    }
+  }
+  return n;
+}
+static bool use_fft_split(int nx, int rows) {
+  if (nx / 2 / kFftSplit < 256) return false;
+  const char* e = std::getenv("MGRIT_FFT_SPLIT");
+  if (e && *e) return std::atoi(e) != 0;
+  return rows < sm_count_fft();
+}
+template <typename Kern, typename... Args>
+static cudaError_t launch_split(Kern kernel, int nx, int rows, cudaStream_t s, Args... args) {
+  const int q = nx / 2 / kFftSplit;
+  const size_t smem = 2 * (size_t)q * sizeof(cplx64);
+  cudaError_t e = cudaSuccess;
+  if (smem > 48 * 1024 &&
+      (e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(rows * kFftSplit);
+  cfg.blockDim = dim3(q / 2);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kFftSplit;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 int coarse_fft_launches(int nx, int P) {
   if (P < 2) return 0;
   return scan_blocks(P - 1, (nx / 2 + 1 + 255) / 256) > 1 ? 4 : 3;
@@ -280,8 +479,11 @@ cudaError_t launch_coarse_fft(const MarchArgs& a, const CoarseFft& f, cudaStream
             cudaSuccess)
       return e;
   }
-  fft_forward_kernel<<<a.P - 1, th, smem, s>>>(a.g_f ? nullptr : a.g, a.g_f, spec, tw, a.nx, logh);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const bool split = use_fft_split(a.nx, a.P - 1);
+  if (split) e = launch_split(fft_forward_split_kernel, a.nx, a.P - 1, s, a.g_f ? nullptr : a.g, a.g_f, spec, tw,
+                              a.nx, logh);
+  else fft_forward_kernel<<<a.P - 1, th, smem, s>>>(a.g_f ? nullptr : a.g, a.g_f, spec, tw, a.nx, logh);
+  if (e != cudaSuccess || (e = cudaGetLastError()) != cudaSuccess) return e;
   const int rows = a.P - 1;
   const int mblocks = (nh + 255) / 256;
   const int nb = scan_blocks(rows, mblocks);
@@ -293,7 +495,12 @@ cudaError_t launch_coarse_fft(const MarchArgs& a, const CoarseFft& f, cudaStream
     fft_recur_carry_kernel<<<dim3(mblocks, nb - 1), 256, 0, s>>>(spec, mu, carry, nh, rows, L);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  fft_inverse_kernel<<<a.P - 1, th, smem, s>>>(spec, tw, a.nx, logh, a);
+  if (split) {
+    e = launch_split(fft_inverse_split_kernel, a.nx, a.P - 1, s, (const cplx64*)spec, tw, a.nx, logh, a);
+    if (e != cudaSuccess) return e;
+  } else {
+    fft_inverse_kernel<<<a.P - 1, th, smem, s>>>(spec, tw, a.nx, logh, a);
+  }
   return cudaGetLastError();
 }
 

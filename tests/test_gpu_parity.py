@@ -451,3 +451,30 @@ def test_mixed_fcf_register_run_agrees(capi, monkeypatch, nx, nt, m, L):
     if nx * nt <= 2 ** 21:
         ref = stepping.sequential(stepping.FineStep("ERK", 1, 0.85, nx), u0h, nt)[::m]
         assert rel(a[1], ref) <= 1e-9
+
+
+@pytest.mark.parametrize("nx,nt,m,L,prec", [(4096, 16384, 8, 4, 1), (4096, 1024, 8, 2, 0), (2048, 2048, 4, 3, 0),
+                                            (8192, 512, 16, 2, 1), (2048, 1024, 8, 2, 2)])
+def test_coarsest_fourier_solve_split_over_a_cluster_agrees(capi, monkeypatch, nx, nt, m, L, prec):
+    """The coarsest level in Fourier space with each slab's transforms split
+    over a cluster of four CTAs (automatic when the level has fewer slabs
+    than SMs) gives bitwise the C-points and iterations of one CTA per slab:
+    the same butterflies in the same order, the last two passes across the
+    CTAs' blocks."""
+    import torch
+    u0 = torch.tensor(workloads.fourier_field(nx), device="cuda")
+    got = {}
+    for split in ("0", "1"):
+        monkeypatch.setenv("MGRIT_FFT_SPLIT", split)
+        monkeypatch.setenv("MGRIT_COARSE", "fft")
+        o = capi.mgrit_opts_default(m=m, levels=L, precision=prec, output=capi.OUT_CPOINTS, tol=1e-10)
+        h = capi.mgrit_setup(capi.problem(nx, nt, "ERK", 3, 3, 0.85 * 1.62589), o)
+        try:
+            out = torch.empty((nt // m + 1, nx), dtype=torch.float64, device="cuda")
+            r, _ = capi.mgrit_solve(h, u0, out)
+            assert r.converged == 1
+            got[split] = (r.iterations, r.rel_residual, out.cpu().numpy())
+        finally:
+            capi.mgrit_destroy(h)
+    assert got["1"][0] == got["0"][0] and got["1"][1] == got["0"][1]
+    np.testing.assert_array_equal(got["1"][2], got["0"][2])
