@@ -150,7 +150,7 @@ def oracle_all_cores(nt_sample=CPU_NT_SAMPLE, repeats=2):
     return NX * nt_sample * repeats * len(res) / wall, n, wall
 
 
-SUBSET_MAX_DOF = 2 ** 20  # the batch subset's solves the oracle leg takes (about 10 s on 16 cores)
+SUBSET_MAX_DOF = 2 ** 21  # the batch subset's solves the oracle leg takes (24 solves, seconds on 16 cores)
 
 
 def _oracle_mix_worker(spec):
@@ -967,13 +967,18 @@ def main():
         err_oracle = None
         if not args.no_cpu and world == 1:
             # the headline result against the plain definition at full size
+            t_seq = time.perf_counter()
             ref = oracle_sequential_cpoints()
+            t_seq = time.perf_counter() - t_seq
             err_oracle = float(np.linalg.norm(head_cpoints - ref) / np.linalg.norm(ref))
             v1, s1, it1 = oracle_sample(repeats=3)
             va, nproc, wall = oracle_all_cores()
             cpu = {"value": va, "unit": "DOF/s", "cores": nproc, "kind": "oracle",
                    "sample": f"oracle V(L=4,m=8) on nx=4096 nt={CPU_NT_SAMPLE}, {nproc} concurrent 1-thread "
-                             f"solves, {wall:.1f} s", "one_thread_value": v1}
+                             f"solves, {wall:.1f} s", "one_thread_value": v1,
+                   "sequential_one_thread_value": NX * NT / t_seq,
+                   "sequential_sample": f"oracle sequential stepping (Eq. 3), full {NX}x{NT}, one thread, "
+                                        f"{t_seq:.1f} s"}
             bu = extra.get("batch_uneven")
             if bu is not None:
                 extra["batch_subset_vs_oracle"] = batch_subset_vs_oracle(capi, bu["dof"], bu["wall_s"], va)

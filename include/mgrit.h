@@ -235,8 +235,9 @@ typedef void* (*mgrit_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*mgrit_free_fn)(void* ptr, void* stream, void* ctx);
 void mgrit_set_allocator(mgrit_alloc_fn alloc, mgrit_free_fn release, void* ctx);
 
-/* Environment variables read at mgrit_setup (diagnostics and profiling; the
- * defaults are the tuned behaviour):
+/* Environment variables read at mgrit_setup, or where the launches are issued
+ * (when a solve's graph is built, or per launch on the host-driven path);
+ * diagnostics and profiling, the defaults are the tuned behaviour:
  *   MGRIT_FCF_SHAPE=tile,threads[,collapse]  pin the level-1 FCF launch shape
  *                     instead of timing the candidates (tile 99 fixed span,
  *                     98 chunked, 8/4 sliding window, 0 one tap at a time).
@@ -245,7 +246,20 @@ void mgrit_set_allocator(mgrit_alloc_fn alloc, mgrit_free_fn release, void* ctx)
  *                     it has fewer than 16 steps.  By default a periodic
  *                     coarsest level with nx = 2^p and at least 16 steps is
  *                     solved in Fourier space (per-mode recurrences with Psi's
- *                     symbol between FFTs); servers always march.
+ *                     symbol between FFTs).  A server marches its two-level
+ *                     solves in one batched launch, and switches a solve to the
+ *                     Fourier-space solve in cycles where few need a coarse
+ *                     solve (MGRIT_COARSE=march: never).
+ *   MGRIT_FFT_SPLIT=0|1  the Fourier-space solve's transforms with each slab
+ *                     split over a cluster of four CTAs; by default where the
+ *                     level has fewer slabs than SMs and nx >= 2048.
+ *   MGRIT_SDIRK_SPLIT=0|1  the SDIRK level-1 FCF with each interval split over
+ *                     a cluster of two CTAs; by default where one CTA per
+ *                     interval would have 512 threads (nx = 8192).
+ *   MGRIT_FCF_STREAM=0..4  form of the level-1 FCF on upwind collapsed stencils
+ *                     of at most 5 taps (MIXED and MIXED_DF): 1 (default)
+ *                     register-resident runs of intervals, 0 one interval per
+ *                     CTA; 2..4 MIXED_DF test forms.  All give the same C-points.
  *   MGRIT_TILE=8|4|0  register tile of the stencil kernels whose shape the
  *                     autotuner does not pick (coarse levels, correction,
  *                     propagation, sequential stepping). */

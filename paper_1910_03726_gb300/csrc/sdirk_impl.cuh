@@ -116,12 +116,13 @@ __device__ __forceinline__ void rec_scan(T (&x)[C], const T* __restrict__ tb, T*
     T aq[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) aq[q] = tb[q];
-    // 1. chunk from a zero state
+    // 1. chunk from a zero state; the term of the value just computed comes
+    // last, so one FMA per point lies on the recurrence's dependency chain
 #pragma unroll
     for (int cc = 0; cc < C; ++cc) {
       T acc = MG_XM(cc);
 #pragma unroll
-      for (int q = 1; q <= K; ++q)
+      for (int q = K; q >= 1; --q)
         if (cc - q >= 0) acc = fma(aq[q - 1], MG_XM(cc - q), acc);
       MG_XM(cc) = acc;
     }
@@ -431,7 +432,7 @@ __global__ void __launch_bounds__(512) fcf_sdirk_kernel(const FcfArgs a, const S
 // Needs ql = 0 (a stage's input is the thread's own points; every U1..U5
 // stage matrix has -lo roots inside the unit circle, so ql = -lo - KF = 0).
 template <int PREC, int C, int KF, int KB>
-__global__ void __launch_bounds__(256, 2) fcf_sdirk_cluster_kernel(const FcfArgs a, const SdirkPlan p) {
+__global__ void __launch_bounds__(256, 2) fcf_sdirk_cluster_kernel(const FcfArgs a, const SdirkPlan p, int j0) {
   extern __shared__ __align__(256) unsigned char smraw[];
   __shared__ __align__(16) double smw[2 * 16 * kMaxRec];
   __shared__ int vote[4];
@@ -447,7 +448,7 @@ __global__ void __launch_bounds__(256, 2) fcf_sdirk_cluster_kernel(const FcfArgs
   const Smem sm = carve(smraw, p);
   load_tables(p, sm);
   cl.sync();  // both CTAs run before either stores into the other's shared memory
-  fcf_body<PREC, C, KF, KB, 2>(a, p, (int)(blockIdx.x >> 1) + 1, sm, smw, L);
+  fcf_body<PREC, C, KF, KB, 2>(a, p, j0 + (int)(blockIdx.x >> 1), sm, smw, L);
   cl.sync();  // no CTA leaves while its partner may still store into it
 }
 
@@ -563,12 +564,10 @@ inline size_t split_smem(const SdirkPlan& p) {
          (size_t)sdirk_slots(p) * padded_len(p.nx / 2) * sizeof(double);
 }
 template <typename Kern>
-static cudaError_t launch_split(Kern kernel, const FcfArgs& a, const SdirkPlan& p, cudaStream_t s) {
-  const size_t smem = split_smem(p);
-  cudaError_t e = smem_attr(kernel, smem);
-  if (e != cudaSuccess) return e;
+static cudaError_t launch_split_part(Kern kernel, const FcfArgs& a, const SdirkPlan& p, int j0, int count,
+                                     size_t smem, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(2 * a.N);
+  cfg.gridDim = dim3(2 * count);
   cfg.blockDim = dim3(p.threads / 2);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
@@ -579,7 +578,32 @@ static cudaError_t launch_split(Kern kernel, const FcfArgs& a, const SdirkPlan& 
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, a, p);
+  return cudaLaunchKernelEx(&cfg, kernel, a, p, j0);
+}
+// Two CTAs of the split form fit on an SM, so its CTAs run in waves of
+// 2 x SMs, each CTA sharing its SM.  Where the last wave would be at most one
+// CTA per SM, it is launched apart with enough shared memory requested that
+// each of its CTAs has an SM to itself (and runs about twice as fast): the
+// whole waves take intervals 1..N-t, the tail N-t+1..N.
+template <typename Kern>
+static cudaError_t launch_split(Kern kernel, const FcfArgs& a, const SdirkPlan& p, cudaStream_t s) {
+  const size_t smem = split_smem(p);
+  const size_t alone = 116 * 1024;  // more than half of an SM's 228 KB: one CTA per SM
+  cudaError_t e = smem_attr(kernel, smem > alone ? smem : alone);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                cudaSuccess || sms < 2) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  const int wave = sms;                        // intervals per wave at two CTAs per SM
+  const int tail = a.N > wave ? a.N % wave : 0;  // intervals of the last wave
+  if (2 * smem + 16 * 1024 <= 228 * 1024 && tail > 0 && 2 * tail <= sms) {  // two per SM in the whole waves
+    if ((e = launch_split_part(kernel, a, p, 1, a.N - tail, smem, s)) != cudaSuccess) return e;
+    return launch_split_part(kernel, a, p, a.N - tail + 1, tail, alone, s);
+  }
+  return launch_split_part(kernel, a, p, 1, a.N, smem, s);
 }
 
 }  // namespace sd
