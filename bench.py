@@ -875,9 +875,10 @@ def main():
     value = replicas_value(world, NX * NT, args.steps, total)
     launches = sum(r.launches for r in results)
     head_cpoints = out.cpu().numpy()
-    # ---- e2e through the C ABI with host buffers (u0 in, C-points out)
-    u0_host = np.ascontiguousarray(u0_np)
-    out_host = np.empty((N1 + 1, NX))
+    # ---- e2e through the C ABI with host buffers (u0 in, C-points out), in
+    # pinned host memory
+    u0_host = torch.tensor(u0_np).pin_memory()
+    out_host = torch.empty((N1 + 1, NX), dtype=torch.float64).pin_memory()
     capi.mgrit_solve(h, u0_host, out_host)
     torch.cuda.synchronize()
     e2e_t = []
