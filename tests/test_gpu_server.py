@@ -160,7 +160,7 @@ def test_fcycle_and_f_relaxation_requests_equal_alone(capi):
         capi.mgrit_server_destroy(srv)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 3])
+@pytest.mark.parametrize("prec", ["FP64", "MIXED", "MIXED_DF"])
 def test_few_two_level_solves_switch_to_the_fourier_coarse_solve(capi, monkeypatch, prec):
     """One long two-level solve alone in the server (1024 coarse steps): its
     batched march would cost 1024 dependent steps per cycle, so the server
@@ -170,9 +170,10 @@ def test_few_two_level_solves_switch_to_the_fourier_coarse_solve(capi, monkeypat
     (float-float C-points: the inverse transform's epilogue adds e in FP64 and
     splits back).  MGRIT_COARSE=march keeps it on the march."""
     nx, nt, m = 1024, 8192, 8
-    tol = 1e-12 if prec == 0 else 1e-10
+    tol = 1e-12 if prec == "FP64" else 1e-10
     prob = capi.problem(nx, nt, "ERK", 3, 3, 0.85 * 1.62589)
-    opts = capi.mgrit_opts_default(m=m, levels=2, precision=prec, output=capi.OUT_CPOINTS, tol=1e-10)
+    opts = capi.mgrit_opts_default(m=m, levels=2, precision=getattr(capi, "PREC_" + prec), output=capi.OUT_CPOINTS,
+                                   tol=1e-10)
     u0 = workloads.fourier_field(nx, seed=9)
     ares, aout = _alone(capi, prob, opts, u0)
     for env, want in ((None, 1), ("march", 0)):
