@@ -167,12 +167,14 @@ def test_rediscretised_coarse_step_matches_oracle(capi, p, m):
 @pytest.mark.parametrize("p,q,nx,nt,m,L,prec,relax", [
     (3, 5, 8192, 256, 16, 2, 1, 0), (3, 5, 8192, 256, 16, 2, 0, 0), (1, 1, 2048, 512, 4, 2, 0, 0),
     (2, 2, 4096, 256, 8, 3, 1, 0), (2, 3, 2048, 512, 8, 2, 0, 1), (4, 4, 4096, 512, 16, 2, 1, 1),
-    (3, 5, 1024, 1024, 4, 3, 0, 0)])
+    (3, 5, 1024, 1024, 4, 3, 0, 0), (3, 5, 2048, 800, 4, 2, 1, 0), (2, 3, 1024, 1216, 4, 2, 0, 0)])
 def test_sdirk_fcf_split_over_a_cluster_agrees(capi, monkeypatch, p, q, nx, nt, m, L, prec, relax):
     """The level-1 SDIRK FCF with each interval's slab split over a cluster of
     two CTAs (the scans' warp totals exchanged through distributed shared
-    memory; automatic at nx = 8192) gives bitwise the C-points and the
-    iterations of one CTA per interval, for every recurrence-order pair
+    memory; automatic at nx = 8192; with more intervals than SMs the whole
+    waves and the tail go in separate launches, N = 200 and 304 here) gives
+    bitwise the C-points and the iterations of one CTA per interval, for
+    every recurrence-order pair
     (U1..U5), FP64 and MIXED, FCF- and F-relaxation.  The norms are the same
     sums in another order: in FP64 to rounding, in MIXED to the FP32 rounding
     of the per-thread sums (a thread of the split form sums other points)."""
