@@ -785,8 +785,8 @@ def main():
                     help="run just this variant and print its JSON (no headline line)")
     ap.add_argument("--host-loop", action="store_true",
                     help="with --only sdirk: drive cycles from the host (kernels visible to ncu)")
-    ap.add_argument("--variants-out", default=os.path.join(ROOT, "gpurun_out", "bench_variants.json"),
-                    help="file for the full variant record (written when its folder exists; '' for none)")
+    ap.add_argument("--variants-out", default="",
+                    help="file for the full variant record (written when its folder exists; default none)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank, world, local = dist_env()
