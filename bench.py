@@ -1009,7 +1009,7 @@ def main():
             "summary": compact_summary(extra),
         }
         try:
-            if args.variants_out and os.path.isdir(os.path.dirname(args.variants_out)):
+            if args.variants_out and os.path.isdir(os.path.dirname(os.path.abspath(args.variants_out))):
                 with open(args.variants_out, "w") as f:
                     json.dump({"line": line, "variants": extra}, f, indent=1)
         except OSError:
