@@ -120,6 +120,23 @@ __device__ __forceinline__ df64 df_add_f(df64 a, float e) {
   return df_norm({s, err + a.lo});
 }
 
+// binary32 -> binary64 (exact) from the IEEE 754 bit fields with integer
+// instructions: sign as is, exponent rebiased by 1023 - 127, the 23-bit
+// fraction moved to the top of the 52-bit one.  GB300 issues the conversion
+// instruction on its FP64 pipe, which an FP64 add right after already needs.
+// Zeros map directly; subnormal, infinite and NaN inputs (exponent field 0
+// with a nonzero fraction, or 255) take the conversion instruction.
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned ex = (u >> 23) & 0xffu;
+  if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));
+  if (ex == 0u || ex == 0xffu) return (double)x;
+  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(ex + (1023u - 127u)) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)b);
+}
+
 // Generic arithmetic over double, float and df64 slabs.
 template <typename T>
 __device__ __forceinline__ T vzero() { return (T)0; }
@@ -1442,7 +1459,7 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
     double gc[PPT], cc[PPT];
     df64 ccd[PPT];
 #pragma unroll
-    for (int p = 0; p < PPT; ++p) { gc[p] = a.g_f ? (double)gqf[p] : gq[p]; cc[p] = cq[p]; ccd[p] = cqd[p]; }
+    for (int p = 0; p < PPT; ++p) { gc[p] = a.g_f ? f32_to_f64(gqf[p]) : gq[p]; cc[p] = cq[p]; ccd[p] = cqd[p]; }
     const int Snext = modnx((long long)S - sigma, nx);
     if (n + 1 < a.P) prefetch(n + 1, Snext);
     const bool store = (a.u_out || a.u_out_f) && (n % a.store_every) == 0;
@@ -1620,10 +1637,25 @@ __global__ void add_kernel(double* __restrict__ c, const double* __restrict__ e,
     c[i] += e[i];
 }
 
+// c += e (level-1 correction from the FP32 level-2 array), two points per
+// thread and step (16-byte and 8-byte accesses) where both arrays allow it.
 __global__ void add_f_kernel(double* __restrict__ c, const float* __restrict__ e, long long count) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
-       i += (long long)gridDim.x * blockDim.x)
-    c[i] += (double)e[i];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const bool pairs = ((reinterpret_cast<unsigned long long>(c) | reinterpret_cast<unsigned long long>(e)) & 15ull) == 0;
+  long long done = 0;
+  if (pairs) {
+    const long long n2 = count / 2;
+    for (long long i = t0; i < n2; i += stride) {
+      const float2 v = reinterpret_cast<const float2*>(e)[i];
+      double2 w = reinterpret_cast<double2*>(c)[i];
+      w.x += f32_to_f64(v.x);
+      w.y += f32_to_f64(v.y);
+      reinterpret_cast<double2*>(c)[i] = w;
+    }
+    done = 2 * n2;
+  }
+  for (long long i = done + t0; i < count; i += stride) c[i] += f32_to_f64(e[i]);
 }
 
 // Float-float C-points: c += e on the FP32 pipes; conversions to and from FP64.
