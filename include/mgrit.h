@@ -460,6 +460,14 @@ mgrit_status mgrit_fcf_residual_static(const double* c_old, double* c_new, doubl
                                        const int32_t* offsets, const double* coeffs, int32_t precision,
                                        void* stream);
 
+/* Self-check of the format conversion the kernels do with integer
+ * instructions (binary32 -> binary64, exact, from the IEEE 754 bit fields)
+ * against the GPU's conversion instruction, over 2n hashed binary32 bit
+ * patterns (seeded; zeros, subnormals, normals, infinities and NaNs among
+ * them).  *mismatches = patterns whose results differ bitwise: 0 expected.
+ * Runs on the current device and waits for the result. */
+mgrit_status mgrit_check_conversions(uint64_t n, uint64_t seed, uint64_t* mismatches);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* mgrit_last_error(void);
 

@@ -47,7 +47,7 @@ EXPORTED = ["mgrit_opts_default", "mgrit_set_allocator", "mgrit_phi_taps", "mgri
             "mgrit_psi_info",
             "mgrit_device_bytes", "mgrit_destroy", "mgrit_server_create", "mgrit_submit",
             "mgrit_poll", "mgrit_server_stats", "mgrit_server_destroy", "mgrit_fcf_residual_static", "mgrit_last_error",
-            "mgrit_abi_version"]
+            "mgrit_abi_version", "mgrit_check_conversions"]
 
 
 class MgritProblem(C.Structure):
@@ -145,6 +145,7 @@ _sig("mgrit_server_destroy", None, _vp)
 _sig("mgrit_fcf_residual_static", _i32, _vp, _vp, _vp, _vp, _i32, _i32, _i32, _i32, _P(_i32), _P(_f64), _i32, _vp)
 _sig("mgrit_last_error", C.c_char_p)
 _sig("mgrit_abi_version", _i32)
+_sig("mgrit_check_conversions", _i32, C.c_uint64, C.c_uint64, _P(C.c_uint64))
 
 
 class MgritError(RuntimeError):
@@ -217,6 +218,14 @@ def mgrit_last_error():
 
 def mgrit_abi_version():
     return int(_lib.mgrit_abi_version())
+
+
+def mgrit_check_conversions(n, seed=0):
+    """Patterns (of 2n) on which the kernels' integer-pipe binary32 -> binary64
+    conversion differs from the GPU's conversion instruction (0 expected)."""
+    bad = C.c_uint64()
+    _check(_lib.mgrit_check_conversions(int(n), int(seed), C.byref(bad)))
+    return int(bad.value)
 
 
 def mgrit_phi_taps(prob, cap=1024):

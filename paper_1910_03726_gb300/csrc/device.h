@@ -261,6 +261,10 @@ cudaError_t launch_march(const MarchArgs& a, const DevTaps& t, int cluster, int 
                          cudaStream_t s);
 cudaError_t launch_correct(const CorrectArgs& a, const DevTaps& t, int threads, cudaStream_t s, int fp32 = 0);
 cudaError_t launch_norm(const double* partial, int n, double* out, cudaStream_t s);
+// Bitwise comparison of the integer-pipe binary32 -> binary64 conversion with
+// the conversion instruction over 2n hashed patterns; mismatches added to *bad.
+cudaError_t launch_conversion_check(unsigned long long n, unsigned long long seed, unsigned long long* bad,
+                                    cudaStream_t s);
 // r[j+1] -= c_new[j+1] and partial[j] = ||r[j+1]||^2 for j = 1..N-1.
 cudaError_t launch_residual_value(const double* c_new, double* r, double* partial, int nx, int N, cudaStream_t s);
 cudaError_t launch_residual_value_batched(const BatchSolve* S, const BatchItem* items, int nitems, cudaStream_t s);

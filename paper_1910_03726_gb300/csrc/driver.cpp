@@ -188,6 +188,23 @@ extern "C" void mgrit_opts_default(mgrit_opts* o) {
 
 extern "C" int32_t mgrit_abi_version(void) { return MGRIT_ABI_VERSION; }
 
+extern "C" mgrit_status mgrit_check_conversions(uint64_t n, uint64_t seed, uint64_t* mismatches) {
+  if (!mismatches) return fail(MGRIT_ERR_INVALID, "mismatches is NULL");
+  unsigned long long* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(d, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = launch_conversion_check(n, seed, d, nullptr);
+  unsigned long long h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  if (d) cudaFree(d);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MGRIT_ERR_CUDA, std::string("conversion check: ") + cudaGetErrorString(e));
+  }
+  *mismatches = h;
+  return MGRIT_OK;
+}
+
 extern "C" const char* mgrit_last_error(void) { return g_err.c_str(); }
 
 mgrit_status validate_problem(const mgrit_problem* p) {

@@ -1585,6 +1585,38 @@ __global__ void __launch_bounds__(R == 8 ? 512 : 1024) correct_kernel(const Corr
       u[(long long)a.N * m * nx + i] = cnew[(long long)a.N * nx + i] + (e ? e[(long long)a.N * nx + i] : (T)0);
 }
 
+// Self-check of f32_to_f64 against the conversion instruction over n hashed
+// binary32 bit patterns (the SplitMix64 finaliser of Steele, Lea and Flood,
+// OOPSLA 2014, applied to seed and index; every class of value: zeros,
+// subnormals, normals, infinities, NaNs).  Counts the patterns whose results
+// differ bitwise.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+__global__ void __launch_bounds__(256) conversion_check_kernel(unsigned long long n, unsigned long long seed,
+                                                               unsigned long long* bad) {
+  unsigned long long local = 0;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+    const unsigned long long h = mix64(seed ^ mix64(i + 1));
+    for (int q = 0; q < 2; ++q) {
+      unsigned u = (unsigned)(h >> (32 * q));
+      if (((h >> 8) & 7ull) == 0) u &= 0x807fffffu;  // exponent field 0: zeros and subnormals
+      const float f = __uint_as_float(u);
+      if (__double_as_longlong(f32_to_f64(f)) != __double_as_longlong((double)f)) ++local;
+    }
+  }
+  if (local) atomicAdd(bad, local);
+}
+
+cudaError_t launch_conversion_check(unsigned long long n, unsigned long long seed, unsigned long long* bad,
+                                    cudaStream_t s) {
+  conversion_check_kernel<<<152 * 8, 256, 0, s>>>(n, seed, bad);
+  return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(1024) norm_kernel(const double* __restrict__ partial, int n, double* out) {
   double v = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) v += partial[i];
