@@ -218,18 +218,40 @@ __device__ __forceinline__ void step_sparse(const DevTaps& t, const T* __restric
 // outputs from a sliding window of R inputs that advances one offset per tap,
 // so each tap costs one shared load and R FMAs.  Needs the dense form and
 // nx >= 64 (so that every index below wraps at most once).
+// FP32 and FP64 take the taps in groups of R first: the window holds 2R
+// inputs, indexed at compile time, so a group costs R loads, R * R FMAs and R
+// moves (one tap at a time costs R - 1 moves per tap).  The FMAs of every
+// output run in the same order either way.
 template <typename T, int R, typename G, bool TR = false>
 __device__ __forceinline__ void step_tiled(const DevTaps& t, const T* __restrict__ src, T* __restrict__ dst,
                                            const G* __restrict__ g, int nx) {
   const int lo = t.lo, span = t.span;
+  constexpr bool kGroups = !std::is_same_v<T, df64>;
   for (int i0 = threadIdx.x * R; i0 < nx; i0 += blockDim.x * R) {
-    T acc[R], w[R];
+    T acc[R], w[kGroups ? 2 * R : R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       acc[r] = (g && i0 + r < nx) ? gload<T>(g + i0 + r) : vzero<T>();
       w[r] = sld<TR>(src, i0 + lo + r, nx);
     }
-    for (int k = 0; k < span; ++k) {
+    int k = 0;
+    if constexpr (kGroups) {
+      for (; k + R <= span; k += R) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) w[R + q] = sld<TR>(src, i0 + lo + k + R + q, nx);
+#pragma unroll
+        for (int kk = 0; kk < R; ++kk) {
+          const T c = dense_coef<T>(t, k + kk);
+          if (vnonzero<T>(c)) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = vfma<T>(c, w[r + kk], acc[r]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) w[q] = w[R + q];
+      }
+    }
+    for (; k < span; ++k) {
       const T c = dense_coef<T>(t, k);
       if (vnonzero<T>(c)) {
 #pragma unroll
