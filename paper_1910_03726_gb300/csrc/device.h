@@ -148,13 +148,17 @@ cudaError_t launch_fcf(const FcfArgs& a, const DevTaps& t, int precision, int th
 // Shared-memory slab length for nx points in the padded layout (one pad
 // element per 8 so that per-thread chunks of 8 are bank-conflict free).
 __host__ __device__ inline int padded_len(int nx) { return nx + (nx >> 3) + 1; }
-// The FCF and propagation kernels hold two padded FP64 slabs in shared memory
-// (at most 227 KiB per CTA): nx <= kMaxSlabNx.
+// The FCF and propagation kernels hold two padded FP64 slabs in dynamic
+// shared memory, beside their static shared memory: at most 227 KiB per CTA
+// in all.  kSlabStaticReserve covers the largest static part of those kernels
+// (the batched FCF's copy of its stencil, 11.3 KiB; the others' reduction
+// scratch, 256 B): nx <= kMaxSlabNx.
 constexpr int kMaxSmemBytes = 227 * 1024;
+constexpr int kSlabStaticReserve = 12 * 1024;
 __host__ __device__ constexpr bool slab_pair_fits(int nx) {
-  return 2LL * (nx + (nx >> 3) + 1) * (long long)sizeof(double) <= kMaxSmemBytes;
+  return 2LL * (nx + (nx >> 3) + 1) * (long long)sizeof(double) <= kMaxSmemBytes - kSlabStaticReserve;
 }
-constexpr int kMaxSlabNx = 12913;
+constexpr int kMaxSlabNx = 12231;
 static_assert(slab_pair_fits(kMaxSlabNx) && !slab_pair_fits(kMaxSlabNx + 1), "kMaxSlabNx");
 
 // ------------------------------------------------------- device-side cycle test

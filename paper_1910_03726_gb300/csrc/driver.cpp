@@ -372,9 +372,11 @@ extern "C" mgrit_status mgrit_psi_plan(const mgrit_problem* prob, const mgrit_op
 
 // ------------------------------------------------------------------- setup
 
-// Cluster size of the march: the largest power of two <= 16 dividing nx with
-// at least 64 points per CTA and a CTA at least as wide as the stencil (the
-// march runs in the stencil's moving frame, so only the width matters).
+// Cluster size of the march: the largest power of two <= 16 with at least 64
+// points per CTA and a CTA at least as wide as the stencil (the march runs in
+// the stencil's moving frame, so only the width matters).  CTAs own
+// ceil(nx / cs) points each and the last one the rest, so cs need not divide
+// nx (the march kernel holds at most 16 x 256 points per CTA in registers).
 int pick_cluster(int nx, const Taps& t) {
   int lo = t.off.empty() ? 0 : t.off[0], hi = lo;
   for (int o : t.off) {
@@ -383,7 +385,7 @@ int pick_cluster(int nx, const Taps& t) {
   }
   const int width = hi - lo;
   for (int cs = march_max_cluster(); cs > 1; cs >>= 1)
-    if (nx % cs == 0 && nx / cs >= std::max(64, width)) return cs;
+    if (nx / cs >= std::max(64, width) && nx - (cs - 1) * ((nx + cs - 1) / cs) >= 1) return cs;
   return 1;
 }
 
@@ -1108,7 +1110,7 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
   if (const char* sf = std::getenv("MGRIT_FCF_STREAM")) set_stream_fused(std::atoi(sf));
   const Taps& coarsest = h->ops.back().taps;
   h->march_cluster = pick_cluster(nx, coarsest);
-  h->march_threads = std::min(256, nx / h->march_cluster);
+  h->march_threads = std::min(256, (nx + h->march_cluster - 1) / h->march_cluster);
   const double tt = now_s();
   autotune_fine(h);
   h->tune_s = now_s() - tt;
@@ -1201,7 +1203,7 @@ void collect_stats(mgrit_handle* h, mgrit_result* R) {
 mgrit_status run_march(mgrit_handle* h, const MarchArgs& a, const DevTaps& t) {
   return klaunch(h, MGRIT_K_MARCH, "march", [&]() -> mgrit_status {
     for (;;) {
-      int threads = std::min(256, a.nx / h->march_cluster);
+      int threads = std::min(256, (a.nx + h->march_cluster - 1) / h->march_cluster);
       cudaError_t e = launch_march(a, t, h->march_cluster, threads, h->stream);
       if (e == cudaSuccess) return MGRIT_OK;
       cudaGetLastError();

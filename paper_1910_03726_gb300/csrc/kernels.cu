@@ -1422,7 +1422,7 @@ __global__ void __launch_bounds__(R == 8 ? 512 : 1024) fcf_batched_kernel(const 
 // S_n = -n*sigma, sigma the centre of the stencil's offsets, so that
 // B_n[x] = sum_k c_k B_{n-1}[x + off_k - sigma] + g_n[x + S_n] needs halos of
 // the stencil's width only, not of its (characteristic) shift.  CTA `rank`
-// owns frame positions [rank*w, (rank+1)*w); its buffer holds
+// owns frame positions [rank*w, min((rank+1)*w, nx)), w = ceil(nx/cs); its buffer holds
 // [left halo | own | right halo].  Per step: compute, cluster barrier, pull
 // halos from the owners' shared memory (DSMEM), block barrier.  Two buffers
 // alternate so a neighbour's reads of step n never meet its writes of n+1.
@@ -1438,13 +1438,14 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
                                            cg::cluster_group& cl) {
   const int cs = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
-  const int nx = a.nx, w = nx / cs, base = rank * w;
+  // CTAs own w = ceil(nx / cs) positions each, the last one the remainder
+  const int nx = a.nx, w = (nx + cs - 1) / cs, base = rank * w, own = min(w, nx - base);
   const int sigma = t.shift;
   const int L = sigma - t.lo, R = t.hi - sigma, W = L + w + R;
   double* B0 = reinterpret_cast<double*>(smraw);
   double* B1 = B0 + W;
   const int tid = threadIdx.x, bs = blockDim.x;
-  for (int k = tid; k < W; k += bs) {
+  for (int k = tid; k < L + own + R; k += bs) {
     const int gi = modnx((long long)base - L + k, nx);
     B0[k] = a.init ? a.init[gi] : 0.0;
   }
@@ -1460,7 +1461,7 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
       const int i = tid + p * bs;
-      if (i < w) {
+      if (i < own) {
         const long long o = (long long)n * nx + wrapi(base + i + Sn, nx);
         if (a.g_f) gqf[p] = __ldcg(a.g_f + o);
         else if (a.g) gq[p] = __ldcg(a.g + o);
@@ -1488,7 +1489,7 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
 #pragma unroll
     for (int p = 0; p < PPT; ++p) {
       const int i = tid + p * bs;
-      if (i < w) {
+      if (i < own) {
         double acc = gc[p];
         const double* c = cur + L + i - sigma;
         const int gi = wrapi(base + i + S, nx);
@@ -1515,7 +1516,7 @@ __device__ __forceinline__ void march_body(const MarchArgs& a, const DevTaps& t,
     for (int k = tid; k < L + R; k += bs) {
       int dst, fi;
       if (k < L) { dst = k; fi = base - L + k; }
-      else { dst = w + k; fi = base + w + (k - L); }
+      else { dst = own + k; fi = base + own + (k - L); }
       fi = modnx(fi, nx);
       const int owner = fi / w, loc = fi - owner * w;
       const double* rem = cl.map_shared_rank(nxt, owner);
@@ -2076,7 +2077,7 @@ static cudaError_t launch_cluster(K kernel, int grid, int cluster, int threads, 
 
 template <int PPT>
 static cudaError_t launch_march_t(const MarchArgs& a, const DevTaps& t, int cluster, int threads, cudaStream_t s) {
-  const int w = a.nx / cluster;
+  const int w = (a.nx + cluster - 1) / cluster;
   const size_t smem = 2 * (size_t)(w + t.hi - t.lo) * sizeof(double);
   MarchArgs aa = a;
   DevTaps tt = t;
@@ -2086,7 +2087,7 @@ static cudaError_t launch_march_t(const MarchArgs& a, const DevTaps& t, int clus
 }
 
 cudaError_t launch_march(const MarchArgs& a, const DevTaps& t, int cluster, int threads, cudaStream_t s) {
-  const int w = a.nx / cluster;
+  const int w = (a.nx + cluster - 1) / cluster;
   const int ppt = (w + threads - 1) / threads;
   if (a.P < 2) return cudaSuccess;
   switch (ppt) {

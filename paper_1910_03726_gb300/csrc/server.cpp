@@ -506,7 +506,7 @@ static mgrit_status cycle_back(mgrit_server* S, const std::vector<Request*>& act
     int max_w = 0, max_halo = 0;
     for (int k : g.second) {
       const mgrit_handle* h = act[k]->h;
-      max_w = std::max(max_w, h->nx / g.first);
+      max_w = std::max(max_w, (h->nx + g.first - 1) / g.first);
       max_halo = std::max(max_halo, h->dpsi.back().hi - h->dpsi.back().lo);
     }
     int* ids = S->dIds.p + id_off;

@@ -206,13 +206,15 @@ def test_phi_power_boundary_rows_match_oracle(capi, p, m, nx):
 
 def test_static_entry_point_checks_the_shared_memory_bound(capi):
     """The FCF keeps two padded FP64 slabs (nx + nx/8 + 1 values each) in one
-    CTA's 227 KiB of shared memory, so nx <= 12913; the check runs before any
-    device call (null buffers are rejected next, still on the host)."""
+    CTA's 227 KiB of shared memory, beside up to 12 KiB of static shared memory
+    (the server's batched FCF copies its stencil there), so nx <= 12231; the
+    check runs before any device call (null buffers are rejected next, still
+    on the host)."""
     import ctypes as C
     offs = (C.c_int32 * 2)(0, -1)
     cfs = (C.c_double * 2)(0.15, 0.85)
     lib = capi._lib
-    st = lib.mgrit_fcf_residual_static(None, None, None, None, 12914, 4, 8, 2, offs, cfs, 0, None)
-    assert st == -1 and "8..12913" in capi.mgrit_last_error()
-    st = lib.mgrit_fcf_residual_static(None, None, None, None, 12913, 4, 8, 2, offs, cfs, 0, None)
+    st = lib.mgrit_fcf_residual_static(None, None, None, None, 12232, 4, 8, 2, offs, cfs, 0, None)
+    assert st == -1 and "8..12231" in capi.mgrit_last_error()
+    st = lib.mgrit_fcf_residual_static(None, None, None, None, 12231, 4, 8, 2, offs, cfs, 0, None)
     assert st == -1 and "device pointers" in capi.mgrit_last_error()

@@ -488,3 +488,92 @@ def test_integer_pipe_conversion_matches_the_conversion_instruction(capi):
     two seeds."""
     for seed in (1, 2 ** 40 + 7):
         assert capi.mgrit_check_conversions(1 << 24, seed) == 0
+
+
+@pytest.mark.parametrize("nx,p,L", [(12231, 1, 2), (12231, 3, 3), (12224, 2, 2)])
+def test_largest_slab_matches_oracle(capi, nx, p, L):
+    """The largest slab a CTA holds (nx = 12231: two padded FP64 slabs and up
+    to 12 KiB of static shared memory in 227 KiB; odd, so every loop takes
+    its ragged tail): FP64 the oracle's iterations and C-points to 1e-12,
+    MIXED at sequential stepping to 1e-9; and the server (whose batched FCF
+    keeps its stencil in shared memory too) gives the same solve."""
+    nt, m = 256, 4
+    c = schemes.cfl_number("ERK", p)
+    u0 = workloads.fourier_field(nx)
+    it, r, U, _ = oracle_run("ERK", p, c, nx, nt, m, L, "auto", u0)
+    res, out, _ = gpu_run(capi, "ERK", p, c, nx, nt, m, L, "auto", u0)
+    assert res.iterations == it
+    assert rel(out, U[::m]) <= TOL
+    ref = stepping.sequential(stepping.FineStep("ERK", p, c, nx), u0, nt)
+    res, out, _ = gpu_run(capi, "ERK", p, c, nx, nt, m, L, "auto", u0, precision=1)
+    assert res.converged == 1 and rel(out, ref[::m]) <= 1e-9
+    srv = capi.mgrit_server_create(20e9)
+    try:
+        opts = capi.mgrit_opts_default(m=m, levels=L, psi_rule=RULE["auto"], psi_halfwidth=3, precision=0,
+                                       output=1, tol=1e-10)
+        t = capi.mgrit_submit(srv, capi.problem(nx, nt, "ERK", p, p, c), opts, np.ascontiguousarray(u0))
+        sout = np.zeros((nt // m + 1, nx))
+        import time
+        t0 = time.time()
+        while True:
+            st, sres = capi.mgrit_poll(srv, t, sout)
+            if st != capi.MGRIT_PENDING:
+                break
+            assert time.time() - t0 < 120, "request did not finish"
+            time.sleep(0.002)
+        assert st == 0 and sres.iterations == it and rel(sout, U[::m]) <= TOL
+    finally:
+        capi.mgrit_server_destroy(srv)
+
+
+@pytest.mark.parametrize("nx,L", [(131, 2), (1001, 2), (1001, 3), (4099, 2)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ragged_cluster_march_matches_oracle(capi, monkeypatch, nx, L, precision):
+    """The march's cluster need not divide nx: CTAs own ceil(nx / cs) points
+    and the last one the rest (131 on 2 CTAs: 66 + 65; 1001 on 8: 7 x 126 +
+    119; the prime 4099 on 16: 15 x 257 + 244).  The coarsest level forced
+    onto the march gives the oracle's iterations and C-points (FP64, 1e-12),
+    MIXED the oracle's C-points to 1e-9."""
+    monkeypatch.setenv("MGRIT_COARSE", "march")
+    nt, m = 512, 4
+    c = schemes.cfl_number("ERK", 3)
+    u0 = workloads.fourier_field(nx)
+    it, r, U, _ = oracle_run("ERK", 3, c, nx, nt, m, L, "auto", u0)
+    res, out, _ = gpu_run(capi, "ERK", 3, c, nx, nt, m, L, "auto", u0, precision=precision)
+    assert res.converged == 1
+    if precision == 0:
+        assert res.iterations == it
+        assert rel(out, U[::m]) <= TOL
+    else:
+        assert abs(res.iterations - it) <= 1
+        assert rel(out, U[::m]) <= 1e-9
+
+
+def test_ragged_cluster_batched_march_matches_oracle(capi, monkeypatch):
+    """The server's batched march on clusters that do not divide nx (1001 and
+    131 points, two-level solves in one mix): each result is the oracle's."""
+    monkeypatch.setenv("MGRIT_COARSE", "march")
+    nt, m = 512, 4
+    c = schemes.cfl_number("ERK", 3)
+    srv = capi.mgrit_server_create(20e9)
+    try:
+        opts = capi.mgrit_opts_default(m=m, levels=2, psi_rule=RULE["auto"], psi_halfwidth=3, precision=0,
+                                       output=1, tol=1e-10)
+        cases = []
+        for nx in (1001, 131, 1001):
+            u0 = np.ascontiguousarray(workloads.fourier_field(nx))
+            t = capi.mgrit_submit(srv, capi.problem(nx, nt, "ERK", 3, 3, c), opts, u0)
+            cases.append((nx, u0, t, np.zeros((nt // m + 1, nx))))
+        import time
+        for nx, u0, t, sout in cases:
+            t0 = time.time()
+            while True:
+                st, sres = capi.mgrit_poll(srv, t, sout)
+                if st != capi.MGRIT_PENDING:
+                    break
+                assert time.time() - t0 < 120, "request did not finish"
+                time.sleep(0.002)
+            it, r, U, _ = oracle_run("ERK", 3, c, nx, nt, m, 2, "auto", u0)
+            assert st == 0 and sres.iterations == it and rel(sout, U[::m]) <= TOL
+    finally:
+        capi.mgrit_server_destroy(srv)
