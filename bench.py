@@ -42,8 +42,33 @@ TOL = 1e-10
 METRIC = "space-time DOF/s at 1e-10 rel. residual vs GPU seq. stepping; p50/p99 latency"
 # FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.070 GHz
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
-WORKLOAD = ("ERK3+U3 nx=4096 nt=16384 c=0.85*1.62589, Fourier-field u0 (seed 2), zero initial iterate, "
-            "V-cycle L=4 m=8, LSQ Psi (auto width), FP32 F-relax + FP64 residual/coarse/test, tol 1e-10")
+# the FP64 pipe's issue rate: 152 SMs x 2 operations (add, mul, fma, conversion) per clock x 2.070 GHz
+FP64_OPS_PEAK = 152 * 2 * 2.070e9
+
+
+def fourier_fcf_work(nx):
+    """FP64 operations and flops per interval of the level-1 FCF's FP64 pass in
+    Fourier space (Phi^m c_{j-1} by a half-length complex FFT of the slab):
+    forward and inverse radix-4 passes of h/4 butterflies (eight complex
+    additions each, and three complex products, 2 mul + 2 fma = 6 flops each,
+    where the twiddles are not 1), a radix-2 pass of span 1 (two complex
+    additions per butterfly) when log2 h is odd, 32 operations (40 flops) per
+    mode pair of the split / symbol product / recombination, and per point the
+    subtraction rho = c' - c and its rounding to FP32."""
+    h = nx // 2
+    logh = h.bit_length() - 1
+    ops = flops = 0
+    q = h // 4
+    while q >= 1:
+        nontrivial = (h // 4) * (q - 1) // q
+        ops += 2 * (16 * (h // 4) + 12 * nontrivial)
+        flops += 2 * (16 * (h // 4) + 18 * nontrivial)
+        q //= 4
+    if logh % 2:
+        ops += 2 * 4 * (h // 2)
+        flops += 2 * 4 * (h // 2)
+    pairs = h // 2 + 1
+    return ops + 32 * pairs + 2 * nx, flops + 40 * pairs + nx
 
 
 def dist_env():
@@ -271,10 +296,12 @@ def oracle_sequential_cpoints():
 
 # ------------------------------------------------------------- GPU arm
 
-def fcf_traffic_from_profile():
-    """Per-launch DRAM bytes of the level-1 FCF kernel from the committed ncu
-    summary, if it was taken on the current kernels source; else None."""
-    path = os.path.join(ROOT, "profiles", "fcf_kernel_erk3u3_4096.md")
+def fcf_traffic_from_profile(fourier=False):
+    """Per-launch DRAM bytes of the level-1 FCF kernel (stencil or Fourier
+    form) from the committed ncu summary, if it was taken on the current
+    kernels source; else None."""
+    name = "fcf_fourier_kernel_erk3u3_4096.md" if fourier else "fcf_kernel_erk3u3_4096.md"
+    path = os.path.join(ROOT, "profiles", name)
     src = os.path.join(ROOT, "paper_1910_03726_gb300", "csrc", "kernels.cu")
     if not os.path.exists(path):
         return None
@@ -624,7 +651,7 @@ def hbm_variant(capi, stream, steps=3):
             ms = statistics.median(per)
             gbs = out["bytes_per_launch"] / (ms * 1e-3) / 1e9
             out[name] = {"fcf_launch_ms": ms, "achieved_gbs": gbs, "frac_of_hbm_peak": gbs / peak,
-                         "iterations": r.iterations, "shape": [r.fine_tile, r.fine_threads, r.fine_collapsed],
+                         "iterations": r.iterations, "shape": [r.fine_tile, r.fine_threads, r.fine_collapsed, r.fine_fourier],
                          "timing": f"CUDA events around {sweeps} back-to-back sweeps (mgrit_relax) on the "
                                    f"converged iterate, median of {steps}; L2 flushed before each group"}
         finally:
@@ -899,7 +926,18 @@ def main():
     fcf_n = sum(r.kernel_count[0] for r in p_results)
     phi_off = capi.mgrit_phi_taps(prob)[0]
     nnz_phi = len(phi_off)
-    if p_results[-1].fine_collapsed:             # one application of Phi^m per pass
+    fourier = bool(p_results[-1].fine_fourier)
+    peak64 = FP64_PEAK_TFLOPS
+    peak_src = "152 SM x 4 FP64 flop/clk x 2.07 GHz"
+    if fourier:                                  # FP64 pass in Fourier space
+        ops_i, flops_i = fourier_fcf_work(NX)
+        flops64 = N1 * flops_i
+        # the pipe issues one add, mul, fma or conversion per lane-slot: the
+        # peak of this operation mix is the issue rate x its flops per operation
+        peak64 = FP64_OPS_PEAK * flops_i / ops_i / 1e12
+        peak_src = (f"152 SM x 2 FP64 ops/clk x 2.07 GHz x {flops_i / ops_i:.4f} flop/op "
+                    f"(the Fourier form's {ops_i / NX:.2f} ops, {flops_i / NX:.2f} flops per point)")
+    elif p_results[-1].fine_collapsed:           # one application of Phi^m per pass
         flops64 = N1 * NX * 2 * (M * (max(phi_off) - min(phi_off)) + 1)
     else:                                        # m applications of Phi per pass
         flops64 = N1 * M * NX * 2 * nnz_phi
@@ -995,10 +1033,12 @@ def main():
             "e2e": {"value": e2e_value, "unit": "DOF/s", "h2d_bytes_per_step": NX * 8,
                     "d2h_bytes_per_step": (N1 + 1) * NX * 8},
             "clocks": clk, "cpu_baseline": cpu,
-            "roofline": {"bound": "alu", "kernel": "fcf_kernel level 1", "achieved": achieved,
-                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-                         "traffic": fcf_traffic_from_profile(), "peak_source": "152 SM x 4 FP64 flop/clk x 2.07 GHz",
+            "roofline": {"bound": "alu",
+                         "kernel": ("fcf_fourier_kernel level 1 (FP64 pass in Fourier space)" if fourier
+                                    else "fcf_kernel level 1"),
+                         "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
+                         "frac": (achieved / peak64) if achieved else None,
+                         "traffic": fcf_traffic_from_profile(fourier), "peak_source": peak_src,
                          "launch_ms": fcf_avg_s * 1e3},
             "hbm_roofline_fcf": ({"frac": hb["frac"], "achieved": hb["achieved"], "peak": hb["peak"],
                                   "unit": "GB/s", "instance": "ERK1 m=4 MIXED_DF",

@@ -214,7 +214,7 @@ typedef struct mgrit_result {
   int32_t fine_threads;  /*   register tile (99 = fixed-span path) and CTA size     */
   int32_t graph;         /* 1 if the solve ran as one CUDA-graph launch             */
   int32_t fine_collapsed; /* 1 if each FCF pass applies Phi^m as one stencil        */
-  int32_t reserved;
+  int32_t fine_fourier;  /* 1 if the FP64 pass ran in Fourier space (MIXED)         */
   int32_t kernel_count[MGRIT_K_KINDS];  /* launches per kind                         */
   double kernel_ms[MGRIT_K_KINDS];      /* device time per kind (FLAG_TIME_KERNELS)  */
   double dx, dt;         /* physical spacings of the problem (alpha, xmin, xmax)    */
@@ -238,9 +238,17 @@ void mgrit_set_allocator(mgrit_alloc_fn alloc, mgrit_free_fn release, void* ctx)
 /* Environment variables read at mgrit_setup, or where the launches are issued
  * (when a solve's graph is built, or per launch on the host-driven path);
  * diagnostics and profiling, the defaults are the tuned behaviour:
- *   MGRIT_FCF_SHAPE=tile,threads[,collapse]  pin the level-1 FCF launch shape
- *                     instead of timing the candidates (tile 99 fixed span,
- *                     98 chunked, 8/4 sliding window, 0 one tap at a time).
+ *   MGRIT_FCF_SHAPE=tile,threads[,collapse[,fourier]]  pin the level-1 FCF
+ *                     launch shape instead of timing the candidates (tile 99
+ *                     fixed span, 98 chunked, 8/4 sliding window, 0 one tap
+ *                     at a time; fourier 128 or 256: the Fourier-space form
+ *                     below with that CTA size, 0: not).
+ *   MGRIT_FCF_FOURIER=0|1  the MIXED level-1 FCF of a periodic problem with
+ *                     nx = 2^p (256..8192) takes its FP64 pass, Phi^m applied
+ *                     to each old C-point, in Fourier space: a real FFT of the
+ *                     slab, the product with Phi^m's symbol (Lemma 1), the
+ *                     inverse FFT.  0 never, 1 always (256 threads); by
+ *                     default it is one of the autotuner's candidates.
  *   MGRIT_COARSE=march|fft  solve the coarsest level by the cluster march, or
  *                     in Fourier space (periodic, nx = 2^p, 64..8192) even when
  *                     it has fewer than 16 steps.  By default a periodic

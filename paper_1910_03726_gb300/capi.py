@@ -71,7 +71,7 @@ class MgritResult(C.Structure):
                 ("setup_s", C.c_double), ("solve_s", C.c_double), ("dof_per_s", C.c_double),
                 ("op_complexity", C.c_double), ("history", C.c_double * MAX_HISTORY),
                 ("launches", C.c_int32), ("fine_tile", C.c_int32), ("fine_threads", C.c_int32),
-                ("graph", C.c_int32), ("fine_collapsed", C.c_int32), ("reserved", C.c_int32),
+                ("graph", C.c_int32), ("fine_collapsed", C.c_int32), ("fine_fourier", C.c_int32),
                 ("kernel_count", C.c_int32 * K_KINDS),
                 ("kernel_ms", C.c_double * K_KINDS), ("dx", C.c_double), ("dt", C.c_double)]
 

@@ -145,6 +145,18 @@ constexpr int kChunkTile = 98;
 cudaError_t launch_fcf(const FcfArgs& a, const DevTaps& t, int precision, int threads,
                        cudaStream_t s, int tile = -1);
 
+// Level-1 FCF (MIXED, periodic) with the FP64 pass Phi^m c_{j-1} taken in
+// Fourier space: forward FFT of the slab, product with the collapsed
+// stencil's symbol, inverse FFT; the residual's pass is the MIXED body's with
+// the collapsed stencil t (a.m = 1).  tab (fourier_table_doubles(nx) doubles,
+// 16-byte aligned) is filled by launch_fourier_tables(t, ...): twiddles and
+// the symbol.  threads: 128 or 256.
+bool fourier_fcf_supported(int nx);  // nx = 2^p, 256 <= nx <= 8192
+bool fourier_fcf_args_ok(const FcfArgs& a);
+size_t fourier_table_doubles(int nx);
+cudaError_t launch_fourier_tables(const DevTaps& t, int nx, double* tab, cudaStream_t s);
+cudaError_t launch_fcf_fourier(const FcfArgs& a, const DevTaps& t, const double* tab, int threads, cudaStream_t s);
+
 // Shared-memory slab length for nx points in the padded layout (one pad
 // element per 8 so that per-thread chunks of 8 are bank-conflict free).
 __host__ __device__ inline int padded_len(int nx) { return nx + (nx >> 3) + 1; }

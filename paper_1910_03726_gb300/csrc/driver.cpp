@@ -652,7 +652,7 @@ struct TuneKey {
   }
 };
 struct TunePick {
-  int collapse, tile, threads;
+  int collapse, tile, threads, fourier;
 };
 std::map<TuneKey, TunePick> g_tune;
 std::mutex g_tune_mu;
@@ -664,11 +664,22 @@ bool fixed_span(int span) { return span == 2 || span == 5 || span == 10 || span 
 // application of the collapsed Phi^m per pass; register tile (fixed-span,
 // sliding window 8 or 4, one tap at a time) and CTA size.  Timed on the
 // handle's own interval count at set-up and cached per problem shape.
+// MGRIT_FCF_FOURIER=0 / 1 keeps the Fourier-space FP64 pass off / takes it
+// (256 threads) wherever the handle has its tables; unset, it is a candidate.
+static int fourier_env() {
+  const char* e = std::getenv("MGRIT_FCF_FOURIER");
+  if (!e) return -1;
+  return std::atoi(e) != 0 ? 1 : 0;
+}
+
 void autotune_fine(mgrit_handle* h) {
   const int prec = fine_prec(h);
   h->fine_collapse = 0;
   h->fine_tile = default_tile(h->dphi, h->nx);
   h->fine_threads = default_threads(h->nx, h->fine_tile);
+  h->fine_fourier = 0;
+  const int fenv = h->ftab ? fourier_env() : 0;
+  if (fenv == 1) h->fine_fourier = 256;
   if (h->sdirk || (h->opts.flags & MGRIT_FLAG_NO_AUTOTUNE)) return;
   const int nx = h->nx;
   auto valid = [&](int collapse, int tile) {
@@ -680,14 +691,16 @@ void autotune_fine(mgrit_handle* h) {
     if (tile == 8 || tile == 4) return dense;
     return tile == 0;
   };
-  // MGRIT_FCF_SHAPE="tile,threads[,collapse]" pins the shape (reproducible profiling)
+  // MGRIT_FCF_SHAPE="tile,threads[,collapse[,fourier threads]]" pins the
+  // shape (reproducible profiling)
   if (const char* shape = std::getenv("MGRIT_FCF_SHAPE")) {
-    int tile = 0, th = 0, col = 0;
-    const int n = std::sscanf(shape, "%d,%d,%d", &tile, &th, &col);
+    int tile = 0, th = 0, col = 0, fo = 0;
+    const int n = std::sscanf(shape, "%d,%d,%d,%d", &tile, &th, &col, &fo);
     if (n >= 2 && (th == 128 || th == 256 || th == 512) && (col == 0 || col == 1) && valid(col, tile)) {
       h->fine_collapse = col;
       h->fine_tile = tile;
       h->fine_threads = th;
+      if (n >= 4 && h->ftab && fenv != 0) h->fine_fourier = (fo == 128 || fo == 256) ? fo : 0;
       return;
     }
   }
@@ -699,6 +712,7 @@ void autotune_fine(mgrit_handle* h) {
       h->fine_collapse = it->second.collapse;
       h->fine_tile = it->second.tile;
       h->fine_threads = it->second.threads;
+      if (fenv == -1 && h->ftab) h->fine_fourier = it->second.fourier;
       return;
     }
   }
@@ -743,7 +757,7 @@ void autotune_fine(mgrit_handle* h) {
   bool dense_found = false;
   for (const Cand& c : cands) dense_found |= c.tile != 0;
   float best = 1e30f;
-  TunePick pick{0, h->fine_tile, h->fine_threads};
+  TunePick pick{0, h->fine_tile, h->fine_threads, 0};
   bool warmed = false;
   for (const Cand& c : cands) {
     if (c.tile == 0 && dense_found) continue;
@@ -775,7 +789,34 @@ void autotune_fine(mgrit_handle* h) {
     }
     if (tm < best) {
       best = tm;
-      pick = {c.collapse, c.tile, c.threads};
+      pick = {c.collapse, c.tile, c.threads, 0};
+    }
+  }
+  // the Fourier-space FP64 pass (collapsed residual pass), where it applies
+  if (fenv == -1 && h->ftab) {
+    f.m = 1;
+    f.fx = h->fx_phim;
+    for (int th : {256, 128}) {
+      if (!fourier_fcf_args_ok(f)) break;
+      float tm = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {  // the first launch sets the shared-memory limit
+        cudaEventRecord(e0, h->stream);
+        if (launch_fcf_fourier(f, h->dphim, h->ftab, th, h->stream) != cudaSuccess) {
+          cudaGetLastError();
+          break;
+        }
+        cudaEventRecord(e1, h->stream);
+        float ms = 0.0f;
+        if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+          if (rep > 0) tm = std::min(tm, ms);
+        } else {
+          cudaGetLastError();
+        }
+      }
+      if (tm < best) {
+        best = tm;
+        pick.fourier = th;
+      }
     }
   }
   cudaEventDestroy(e0);
@@ -783,12 +824,19 @@ void autotune_fine(mgrit_handle* h) {
   h->fine_collapse = pick.collapse;
   h->fine_tile = pick.tile;
   h->fine_threads = pick.threads;
+  if (fenv == -1) h->fine_fourier = pick.fourier;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = pick;
 }
 
 cudaError_t launch_fine_fcf(mgrit_handle* h, const FcfArgs& f, int prec) {
   if (h->sdirk) return launch_fcf_sdirk(f, h->splan, prec == 0 ? 0 : 1, h->stream);
+  if (h->fine_fourier && prec == 1) {  // FP64 pass in Fourier space, collapsed residual pass
+    FcfArgs g = f;
+    g.m = 1;
+    g.fx = h->fx_phim;
+    if (fourier_fcf_args_ok(g)) return launch_fcf_fourier(g, h->dphim, h->ftab, h->fine_fourier, h->stream);
+  }
   FcfArgs g = f;
   g.fx = h->fx_phi;  // boundary rows (inflow/outflow)
   if (h->fine_collapse) {  // each pass is one application of Phi^m
@@ -1111,6 +1159,18 @@ mgrit_status handle_create(const mgrit_problem* prob, const mgrit_opts* opts, cu
   const Taps& coarsest = h->ops.back().taps;
   h->march_cluster = pick_cluster(nx, coarsest);
   h->march_threads = std::min(256, (nx + h->march_cluster - 1) / h->march_cluster);
+  // tables of the Fourier-space FP64 pass (MIXED periodic level 1; not for a
+  // server's handles, whose level-1 FCF is the batched launch)
+  if (fine_prec(h) == 1 && !h->sdirk && !h->inflow && !h->pool_alloc && h->have_phim && fourier_fcf_supported(nx) &&
+      fourier_env() != 0) {
+    double* tab = nullptr;
+    if (dalloc(h, fourier_table_doubles(nx), &tab) == MGRIT_OK &&
+        launch_fourier_tables(h->dphim, nx, tab, h->stream) == cudaSuccess) {
+      h->ftab = tab;
+    } else {
+      cudaGetLastError();
+    }
+  }
   const double tt = now_s();
   autotune_fine(h);
   h->tune_s = now_s() - tt;
@@ -1190,6 +1250,7 @@ void collect_stats(mgrit_handle* h, mgrit_result* R) {
   R->fine_tile = h->fine_tile;
   R->fine_threads = h->fine_threads;
   R->fine_collapsed = h->fine_collapse;
+  R->fine_fourier = h->fine_fourier ? 1 : 0;
   for (size_t p = 0; p < h->evkind.size(); ++p) {
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, h->evpool[2 * p], h->evpool[2 * p + 1]) == cudaSuccess)

@@ -68,6 +68,11 @@ struct mgrit_handle {
   int fcf_threads = 512, march_cluster = 1, march_threads = 256;
   int fine_tile = -1, fine_threads = 0;   // level-1 FCF launch shape (autotuned)
   int fine_collapse = 0;                  // 1: each pass applies Phi^m once
+  // MIXED, periodic, nx = 2^p: the level-1 FCF may take its FP64 pass in
+  // Fourier space (twiddles and the symbol of Phi^m / (2 nx) in ftab on the
+  // device); fine_fourier = its CTA size when the autotuner picked it, else 0
+  double* ftab = nullptr;
+  int fine_fourier = 0;
   // a whole solve as one CUDA graph (WHILE over cycles, IF around each
   // coarse correction), built at the first solve
   cudaGraph_t graph = nullptr;

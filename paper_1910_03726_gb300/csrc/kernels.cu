@@ -1417,6 +1417,274 @@ __global__ void __launch_bounds__(R == 8 ? 512 : 1024) fcf_batched_kernel(const 
 }
 
 // ----------------------------------------------------------------------------
+// Level-1 FCF-relaxation of a periodic problem with its FP64 pass in Fourier
+// space (MIXED).  The collapsed Phi^m is circulant, so the discrete Fourier
+// transform diagonalises it (Lemma 1): with X_k = sum_x x[x] w^{xk},
+// w = exp(-2 pi i / nx), the new C-point c'_j = Phi^m c_{j-1} has the
+// spectrum S_k X_k, S_k = sum_q c_q exp(+2 pi i o_q k / nx) the symbol of the
+// collapsed stencil (offsets o_q, coefficients c_q).  Per interval the slab
+// is transformed as one complex FFT of half length h = nx/2 (z_q = x_{2q} +
+// i x_{2q+1}; radix-4 decimation in frequency, natural order in, bit-reversed
+// out), its modes are split into X_0..X_h, multiplied by S and recombined
+// (one thread per mode pair k, h-k, in the bit-reversed positions), and a
+// radix-4 decimation-in-time inverse (bit-reversed in, natural out) returns
+// c'_j.  That takes about 45 FP64 instructions per point where the collapsed
+// stencil takes one FMA per tap (73 for ERK3+U3 at m = 8).  The residual's
+// pass (rho = c'_j - c_j in FP32, r_{j+1} = Phi^m rho) is the MIXED body's.
+// The factors 1/2 of the split and recombination and the inverse's 1/h are
+// one exact power of two folded into S (the table holds S_k / (2 nx)).  An
+// identically zero slab skips the transforms and stays exactly zero.
+// ----------------------------------------------------------------------------
+struct zc64 {
+  double re, im;
+};
+__device__ __forceinline__ zc64 zmul(zc64 a, zc64 b) {
+  return {fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
+}
+__device__ __forceinline__ zc64 ldz(const zc64* p) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  return {v.x, v.y};
+}
+
+// Sign flip on the integer pipe (an FP64 negation would take an FP64 issue).
+__device__ __forceinline__ double dneg(double x) {
+  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+// a * conj(w)
+__device__ __forceinline__ zc64 zmulc(zc64 a, zc64 w) {
+  return {fma(a.re, w.re, a.im * w.im), fma(a.im, w.re, -a.re * w.im)};
+}
+// w^k, w = exp(-2 pi i / nx), 0 <= k < 3h/2 (nx = 2h), from the quarter
+// table tw[0..h/4]: w^(h/2 - k) = -i conj(w^k) folds (h/4, h/2) onto
+// [0, h/4), w^(h/2) = -i and w^h = -1 the rest; sign flips and swaps only.
+__device__ __forceinline__ zc64 twq(const zc64* __restrict__ tw, int k, int h) {
+  const int hh = h >> 1;
+  const int sector = k >= h ? 2 : (k >= hh ? 1 : 0);
+  const int kk = k - sector * hh;
+  zc64 r;
+  if (kk <= (h >> 2)) {
+    r = ldz(tw + kk);
+  } else {
+    const zc64 c = ldz(tw + (hh - kk));
+    r = {dneg(c.im), dneg(c.re)};
+  }
+  if (sector == 1) r = {r.im, dneg(r.re)};
+  else if (sector == 2) r = {dneg(r.re), dneg(r.im)};
+  return r;
+}
+
+// The radix-2 pass of span 1 (twiddle 1): the last forward pass, the first
+// inverse one, when log2 h is odd.
+__device__ __forceinline__ void radix2_unit_pass(zc64* x, int h) {
+  for (int b = threadIdx.x; b < (h >> 1); b += blockDim.x) {
+    const zc64 u = x[2 * b], v = x[2 * b + 1];
+    x[2 * b] = {u.re + v.re, u.im + v.im};
+    x[2 * b + 1] = {u.re - v.re, u.im - v.im};
+  }
+  __syncthreads();
+}
+
+// One radix-4 pass of span q over x[0..h): butterfly (g, pos) takes
+// x[4qg + pos + {0, q, 2q, 3q}], pos < q, g < h/4q.  A thread keeps one
+// position while it can (q <= CTA size: every group of its position), so
+// its three twiddles are looked up once per position, not per butterfly.
+// Forward (DIF, the work of the radix-2 passes of spans 2q and q; twiddles
+// W^pos, W^2pos, W^3pos of W = exp(-2 pi i / 4q) on the outputs), or inverse
+// (DIT, conjugate twiddles on the inputs, the two passes in reverse order).
+template <bool INV>
+__device__ __forceinline__ void radix4_pass(zc64* x, const zc64* __restrict__ tw, int h, int q) {
+  const int bs = blockDim.x, tid = threadIdx.x;
+  const int s = h / (2 * q), groups = h / (4 * q);  // W^pos = w^(pos s)
+  const bool wide = q >= bs;
+  const int gstep = wide ? 1 : bs / q;
+  for (int pos = wide ? tid : (tid & (q - 1)); pos < q; pos += wide ? bs : q) {
+    zc64 w1 = {1.0, 0.0}, w2 = {1.0, 0.0}, w3 = {1.0, 0.0};
+    if (pos) {
+      w1 = twq(tw, pos * s, h);
+      w2 = twq(tw, 2 * pos * s, h);
+      w3 = twq(tw, 3 * pos * s, h);
+    }
+    for (int g = wide ? 0 : tid / q; g < groups; g += gstep) {
+      const int i0 = 4 * q * g + pos;
+      if constexpr (!INV) {
+        const zc64 x0 = x[i0], x1 = x[i0 + q], x2 = x[i0 + 2 * q], x3 = x[i0 + 3 * q];
+        const zc64 a0 = {x0.re + x2.re, x0.im + x2.im}, a1 = {x0.re - x2.re, x0.im - x2.im};
+        const zc64 a2 = {x1.re + x3.re, x1.im + x3.im};
+        const zc64 a3 = {x1.im - x3.im, x3.re - x1.re};  // -i (x1 - x3)
+        zc64 y1 = {a0.re - a2.re, a0.im - a2.im};
+        zc64 y2 = {a1.re + a3.re, a1.im + a3.im};
+        zc64 y3 = {a1.re - a3.re, a1.im - a3.im};
+        x[i0] = {a0.re + a2.re, a0.im + a2.im};
+        if (pos) {
+          y1 = zmul(y1, w2);
+          y2 = zmul(y2, w1);
+          y3 = zmul(y3, w3);
+        }
+        x[i0 + q] = y1;
+        x[i0 + 2 * q] = y2;
+        x[i0 + 3 * q] = y3;
+      } else {
+        zc64 v0 = x[i0], v1 = x[i0 + q], v2 = x[i0 + 2 * q], v3 = x[i0 + 3 * q];
+        if (pos) {
+          v1 = zmulc(v1, w2);
+          v2 = zmulc(v2, w1);
+          v3 = zmulc(v3, w3);
+        }
+        const zc64 p0 = {v0.re + v1.re, v0.im + v1.im}, m0 = {v0.re - v1.re, v0.im - v1.im};
+        const zc64 p1 = {v2.re + v3.re, v2.im + v3.im};
+        const zc64 m1 = {v3.im - v2.im, v2.re - v3.re};  // i (v2 - v3)
+        x[i0] = {p0.re + p1.re, p0.im + p1.im};
+        x[i0 + 2 * q] = {p0.re - p1.re, p0.im - p1.im};
+        x[i0 + q] = {m0.re + m1.re, m0.im + m1.im};
+        x[i0 + 3 * q] = {m0.re - m1.re, m0.im - m1.im};
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Forward transform of x[0..h) in place, natural order in, bit-reversed out:
+// radix-4 passes of spans h/4, h/16, ..., then a radix-2 pass of span 1 if
+// log2 h is odd.
+__device__ __forceinline__ void dif_forward(zc64* x, const zc64* __restrict__ tw, int h, int logh) {
+  for (int q = h >> 2; q >= 1; q >>= 2) radix4_pass<false>(x, tw, h, q);
+  if (logh & 1) radix2_unit_pass(x, h);
+}
+
+// Inverse transform (conjugate twiddles, no 1/h), bit-reversed order in,
+// natural out: the forward passes' inverses in reverse order.
+__device__ __forceinline__ void dit_inverse(zc64* x, const zc64* __restrict__ tw, int h, int logh) {
+  int q = 1;
+  if (logh & 1) {
+    radix2_unit_pass(x, h);
+    q = 2;
+  }
+  for (; q <= (h >> 2); q <<= 2) radix4_pass<true>(x, tw, h, q);
+}
+
+__device__ __forceinline__ int bitrev_n(int i, int logn) { return (int)(__brev((unsigned)i) >> (32 - logn)); }
+
+// Multiply the spectrum of the slab by S, in place on the half-length
+// transform Z (bit-reversed order).  Mode pair (k, h-k), k = 0..h/2, with
+// A = Z_k + conj Z_{h-k}, B = -i (Z_k - conj Z_{h-k}) (twice the transforms
+// of the even and odd points), T = w^k B:
+//   X_k = A + T,  X_{h-k} = conj(A - T)      (twice the slab's modes; k = 0
+//                                             gives X_0 and X_h)
+//   Y = S X;  A' = Y_k + conj Y_{h-k},  B' = (Y_k - conj Y_{h-k}) conj(w^k)
+//   Z'_k = A' + i B',  Z'_{h-k} = conj(A') + i conj(B')
+// Pair t < h/2 is the mode k = bitrev(2t) < h/2 held at the even position 2t
+// (its partner's positions then run contiguously too, so neither access
+// meets more than two-way bank conflicts); pair h/2 is the mode h/2 itself.
+// spec[3t..3t+2] = w^k, S_k, S_{h-k} of pair t.
+__device__ __forceinline__ void spectral_multiply(zc64* z, const zc64* __restrict__ spec, int h, int logh) {
+  for (int t = threadIdx.x; t <= (h >> 1); t += blockDim.x) {
+    const int pk = t < (h >> 1) ? 2 * t : 1;
+    const int k = bitrev_n(pk, logh);
+    const int hk = (h - k) & (h - 1);
+    const int ph = bitrev_n(hk, logh);
+    const zc64 a = z[pk], b = z[ph];
+    const zc64 w = ldz(spec + 3 * t), Sk = ldz(spec + 3 * t + 1), Sh = ldz(spec + 3 * t + 2);
+    const zc64 A = {a.re + b.re, a.im - b.im};
+    const zc64 B = {a.im + b.im, b.re - a.re};
+    const zc64 T = zmul(w, B);
+    const zc64 Yk = zmul(Sk, zc64{A.re + T.re, A.im + T.im});
+    const zc64 Yh = zmul(Sh, zc64{A.re - T.re, T.im - A.im});
+    const zc64 Ap = {Yk.re + Yh.re, Yk.im - Yh.im};
+    const zc64 Bp = zmulc(zc64{Yk.re - Yh.re, Yk.im + Yh.im}, w);
+    z[pk] = {Ap.re - Bp.im, Ap.im + Bp.re};
+    if (k != 0 && hk != k) z[ph] = {Ap.re + Bp.im, Bp.re - Ap.im};
+  }
+}
+
+// One CTA per interval j = blockIdx.x + 1.  Shared memory: the slab as h
+// complex values (nx doubles), then the FP32 residual slab (padded); the
+// second FP32 slab of the residual pass reuses the complex buffer.  The host
+// checks the conditions (periodic, no right-hand side, FCF, MIXED with FP32
+// residual storage, nx = 2^p, 16-byte aligned rows).
+template <int R, int SPAN>
+__global__ void __launch_bounds__(256) fcf_fourier_kernel(const FcfArgs a, const DevTaps t,
+                                                          const zc64* __restrict__ tw,
+                                                          const zc64* __restrict__ spec, int logh) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int nx = a.nx, h = nx >> 1, j = blockIdx.x + 1;
+  zc64* z = reinterpret_cast<zc64*>(smraw);
+  float* f0 = reinterpret_cast<float*>(smraw + (size_t)nx * sizeof(double));
+  float* f1 = reinterpret_cast<float*>(smraw);
+  const double2* start = reinterpret_cast<const double2*>(a.u_old + (long long)(j - 1) * a.cstride);
+  const double* oldj = a.u_old + (long long)j * a.cstride;
+  prefetch_l2(oldj, (long long)nx * sizeof(double));
+  int nz = 0;
+  for (int q = threadIdx.x; q < h; q += blockDim.x) {
+    const double2 v = __ldcg(start + q);
+    z[q] = {v.x, v.y};
+    nz |= dnz(v.x) | dnz(v.y);
+  }
+  // a zero slab maps to zero: the transforms are skipped
+  if (__syncthreads_or(nz)) {
+    dif_forward(z, tw, h, logh);
+    spectral_multiply(z, spec, h, logh);
+    __syncthreads();
+    dit_inverse(z, tw, h, logh);
+  }
+  const double* v = reinterpret_cast<const double*>(z);
+  double* cn = a.c_new + (long long)j * nx;
+  nz = 0;
+  for (int e = 2 * threadIdx.x; e < nx; e += 2 * blockDim.x) {
+    const double2 old = __ldcg(reinterpret_cast<const double2*>(oldj + e));
+    const double v0 = v[e], v1 = v[e + 1];
+    *reinterpret_cast<double2*>(cn + e) = make_double2(v0, v1);
+    const float r0 = (float)(v0 - old.x), r1 = (float)(v1 - old.y);
+    const int q = pidx(e);
+    f0[q] = r0;
+    f0[q + 1] = r1;
+    nz |= (r0 != 0.0f) | (r1 != 0.0f);
+  }
+  const bool run2 = __syncthreads_or(nz);
+  if (j >= a.N) return;
+  float* x0 = f0;
+  float* x1 = f1;
+  if (run2) {
+    slab_step_fx<float, R, SPAN, false>(t, a.fx, x0, x1, kNoGf, nx);
+    __syncthreads();
+    x0 = f1;
+  }
+  store_residual_f32(a, j, x0);
+}
+
+// Fourier FCF tables (FP64): tw[k] = w^k, k = 0..nx/8 (the quarter table of
+// w = exp(-2 pi i / nx)), and spec[3t..3t+2] = w^k, scale S_k, scale S_{h-k}
+// for pair t = 0..nx/4 of spectral_multiply (k = bitrev(2t), or nx/4 for the
+// last), S_k = sum_q c_q exp(+2 pi i o_q k / nx).
+__device__ __forceinline__ zc64 stencil_symbol(const DevTaps& t, int k, int nx, double scale) {
+  double re = 0.0, im = 0.0, s, c;
+  for (int q = 0; q < t.n; ++q) {
+    long long ik = ((long long)t.off[q] * k) % nx;
+    if (ik < 0) ik += nx;
+    sincospi(2.0 * (double)ik / nx, &s, &c);
+    re = fma(t.c64[q], c, re);
+    im = fma(t.c64[q], s, im);
+  }
+  return {re * scale, im * scale};
+}
+__global__ void __launch_bounds__(256) fourier_tables_kernel(const DevTaps t, int nx, int logh, double scale,
+                                                             zc64* __restrict__ tw, zc64* __restrict__ spec) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int h = nx / 2;
+  double s, c;
+  if (i <= h / 4) {
+    sincospi(-2.0 * i / nx, &s, &c);
+    tw[i] = {c, s};
+  }
+  if (i <= h / 2) {
+    const int k = i < h / 2 ? bitrev_n(2 * i, logh) : h / 2;
+    sincospi(-2.0 * k / nx, &s, &c);
+    spec[3 * i] = {c, s};
+    spec[3 * i + 1] = stencil_symbol(t, k, nx, scale);
+    spec[3 * i + 2] = stencil_symbol(t, h - k, nx, scale);
+  }
+}
+
+// ----------------------------------------------------------------------------
 // Sequential march on one thread-block cluster, in a frame that moves with the
 // stencil: the shared buffers hold B_n[x] = u_n[(x + S_n) mod nx] with
 // S_n = -n*sigma, sigma the centre of the stencil's offsets, so that
@@ -2020,6 +2288,57 @@ cudaError_t launch_fcf(const FcfArgs& a, const DevTaps& t, int precision, int th
   if (R == 8) return launch_fcf_t<1, 8>(a, t, threads, s);
   if (R == 4) return launch_fcf_t<1, 4>(a, t, threads, s);
   return launch_fcf_t<1, 0>(a, t, threads, s);
+}
+
+// ------------------------------------------------- FCF with the FP64 pass in Fourier space
+bool fourier_fcf_supported(int nx) {
+  return nx >= 256 && nx <= 8192 && (nx & (nx - 1)) == 0 &&
+         (size_t)nx * sizeof(double) + (size_t)padded_len(nx) * sizeof(float) <= (size_t)(kMaxSmemBytes - 1024);
+}
+
+static int log2_half(int nx) {
+  int logh = 0;
+  while ((2 << logh) < nx) ++logh;
+  return logh;
+}
+size_t fourier_table_doubles(int nx) { return 2 * (size_t)(nx / 8 + 1) + 6 * (size_t)(nx / 4 + 1); }
+
+cudaError_t launch_fourier_tables(const DevTaps& t, int nx, double* tab, cudaStream_t s) {
+  if (!fourier_fcf_supported(nx)) return cudaErrorInvalidValue;
+  const int n = nx / 4 + 1;
+  fourier_tables_kernel<<<(n + 255) / 256, 256, 0, s>>>(t, nx, log2_half(nx), 1.0 / (2.0 * nx),
+                                                        reinterpret_cast<zc64*>(tab),
+                                                        reinterpret_cast<zc64*>(tab + 2 * (nx / 8 + 1)));
+  return cudaGetLastError();
+}
+
+bool fourier_fcf_args_ok(const FcfArgs& a) {
+  auto al = [](const void* p) { return (reinterpret_cast<unsigned long long>(p) & 15ull) == 0; };
+  return fourier_fcf_supported(a.nx) && a.m == 1 && !a.g && !a.relax_f && !a.value_residual && !a.zero_old &&
+         !a.df_store && !a.trunc && a.fx.nl + a.fx.nr == 0 && a.r_f && a.u_old && a.c_new && al(a.u_old) &&
+         al(a.c_new) && (a.cstride & 1) == 0;
+}
+
+template <int R, int SPAN>
+static cudaError_t launch_fourier_t(const FcfArgs& a, const DevTaps& t, const double* tab, int threads,
+                                    cudaStream_t s) {
+  const size_t smem = (size_t)a.nx * sizeof(double) + (size_t)padded_len(a.nx) * sizeof(float);
+  cudaError_t e = set_smem(fcf_fourier_kernel<R, SPAN>, smem);
+  if (e != cudaSuccess) return e;
+  fcf_fourier_kernel<R, SPAN><<<a.N, threads, smem, s>>>(
+      a, t, reinterpret_cast<const zc64*>(tab), reinterpret_cast<const zc64*>(tab + 2 * (a.nx / 8 + 1)),
+      log2_half(a.nx));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fcf_fourier(const FcfArgs& a, const DevTaps& t, const double* tab, int threads, cudaStream_t s) {
+  if (a.N < 1) return cudaSuccess;
+  if (!fourier_fcf_args_ok(a) || !tab || (threads != 128 && threads != 256)) return cudaErrorInvalidValue;
+  FcfArgs f = a;
+  f.fused = 0;
+  if (t.span >= 8 && a.nx >= 64) return launch_fourier_t<8, kChunked>(f, t, tab, threads, s);
+  if (t.span > 0 && a.nx >= 64) return launch_fourier_t<8, 0>(f, t, tab, threads, s);
+  return launch_fourier_t<0, 0>(f, t, tab, threads, s);
 }
 
 template <int R, int SPAN = 0>

@@ -92,3 +92,32 @@ def test_compact_summary_is_small_and_carries_the_headline_figures():
     assert out["batch_subset_vs_oracle"]["oracle_batch_s_extrapolated"] == [3175, 1682]
     assert out["sdirk3_u5_8192_ms"]["mixed"] == 24.9
     assert len(json.dumps(out)) < 1500
+
+
+def test_fourier_fcf_work_counts_every_butterfly():
+    """bench.fourier_fcf_work (the roofline's FP64 work of the level-1 FCF's
+    Fourier-space pass) against an enumeration of the passes' butterflies,
+    for odd and even log2(nx/2)."""
+    for nx in (8, 16, 256, 512, 4096, 8192):
+        h = nx // 2
+        ops = flops = 0
+        spans = []
+        q = h // 4
+        while q >= 1:
+            spans.append(q)
+            q //= 4
+        for _direction in range(2):
+            for q in spans:
+                for b in range(h // 4):
+                    pos = b % q
+                    ops += 16 + (12 if pos else 0)
+                    flops += 16 + (18 if pos else 0)
+            if (h.bit_length() - 1) % 2:
+                ops += 4 * (h // 2)
+                flops += 4 * (h // 2)
+        for _k in range(h // 2 + 1):
+            ops += 32
+            flops += 40
+        ops += 2 * nx
+        flops += nx
+        assert bench.fourier_fcf_work(nx) == (ops, flops), nx

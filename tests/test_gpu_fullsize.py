@@ -169,6 +169,33 @@ def test_level1_shapes_at_4096_match_oracle(capi, monkeypatch, shape, levels):
     assert rel(out, ref) <= 1e-12
 
 
+@pytest.mark.parametrize("fourier", ["0", "1"])
+def test_headline_full_size_fourier_fcf_forms(capi, monkeypatch, sequential_cpoints, fourier):
+    """The headline in MIXED with the level-1 FCF's FP64 pass in Fourier space
+    (forced on) and as the collapsed stencil (forced off): both reach the
+    oracle's sequential stepping to the stopping tolerance, with FP64's
+    iterations within one."""
+    monkeypatch.setenv("MGRIT_FCF_FOURIER", fourier)
+    res, cp = headline_solve(capi, 1)
+    assert res.fine_fourier == int(fourier)
+    assert res.converged == 1 and res.rel_residual <= 1e-10
+    assert rel(cp, sequential_cpoints) <= 1e-10
+    assert abs(res.iterations - read_golden()["iterations"]) <= 1
+
+
+@pytest.mark.parametrize("threads", ["256", "128"])
+@pytest.mark.parametrize("levels", [3, 4])
+def test_fourier_fcf_at_4096_matches_oracle(capi, monkeypatch, threads, levels):
+    """nx = 4096: the MIXED level-1 FCF with its FP64 pass in Fourier space
+    (2048-point half-length FFTs) against the oracle's MGRIT at nt = 1024."""
+    monkeypatch.setenv("MGRIT_FCF_SHAPE", "98,256,1," + threads)
+    it, ref = oracle_erk3(1024, levels)
+    res, out = gpu_erk3(capi, 1024, levels, precision=1)
+    assert res.fine_fourier == 1
+    assert abs(res.iterations - it) <= 1
+    assert rel(out, ref) <= 1e-9
+
+
 @pytest.mark.parametrize("coarse", ["fft", "march"])
 @pytest.mark.parametrize("levels", [2, 3])
 def test_coarsest_level_at_4096_matches_oracle(capi, monkeypatch, coarse, levels):

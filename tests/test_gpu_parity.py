@@ -577,3 +577,75 @@ def test_ragged_cluster_batched_march_matches_oracle(capi, monkeypatch):
             assert st == 0 and sres.iterations == it and rel(sout, U[::m]) <= TOL
     finally:
         capi.mgrit_server_destroy(srv)
+
+
+@pytest.mark.parametrize("p,nx,m,L", [(1, 256, 4, 3), (2, 512, 8, 2), (3, 1024, 8, 3), (4, 256, 4, 2), (5, 512, 4, 3),
+                                      (3, 8192, 8, 2)])
+@pytest.mark.parametrize("shape", ["1", "8,256,1,128"])
+def test_fourier_fcf_matches_oracle(capi, monkeypatch, p, nx, m, L, shape):
+    """MIXED level-1 FCF with the FP64 pass Phi^m c_{j-1} taken in Fourier
+    space (half-length complex FFT of the slab, product with the collapsed
+    stencil's symbol, inverse FFT; Lemma 1's diagonalisation of a circulant),
+    forced on (256 threads, or pinned at 128): the oracle's C-points to 1e-9
+    and its iterations within one, from nx = 256 (fewer butterflies per pass
+    than threads) to 8192."""
+    if shape == "1":
+        monkeypatch.setenv("MGRIT_FCF_FOURIER", "1")
+    else:
+        monkeypatch.setenv("MGRIT_FCF_SHAPE", shape)
+    nt = 512 if nx <= 1024 else 256
+    c = schemes.cfl_number("ERK", p)
+    u0 = workloads.fourier_field(nx)
+    it, r, U, _ = oracle_run("ERK", p, c, nx, nt, m, L, "auto", u0)
+    res, out, _ = gpu_run(capi, "ERK", p, c, nx, nt, m, L, "auto", u0, precision=1)
+    assert res.fine_fourier == 1
+    assert res.converged == 1 and abs(res.iterations - it) <= 1
+    assert rel(out, U[::m]) <= 1e-9
+
+
+def test_fourier_fcf_off_and_other_precisions(capi, monkeypatch):
+    """MGRIT_FCF_FOURIER=0 keeps the stencil form; FP64 and MIXED_DF never
+    take the Fourier form (their FP64 pass is the exact-cancellation value
+    form, or float-float)."""
+    nx, nt, m, L = 512, 512, 8, 2
+    c = schemes.cfl_number("ERK", 3)
+    u0 = workloads.fourier_field(nx)
+    monkeypatch.setenv("MGRIT_FCF_FOURIER", "0")
+    res, _, _ = gpu_run(capi, "ERK", 3, c, nx, nt, m, L, "auto", u0, precision=1)
+    assert res.fine_fourier == 0
+    monkeypatch.setenv("MGRIT_FCF_FOURIER", "1")
+    for prec in (0, 2):
+        res, _, _ = gpu_run(capi, "ERK", 3, c, nx, nt, m, L, "auto", u0, precision=prec)
+        assert res.fine_fourier == 0
+
+
+def test_fourier_fcf_relax_sweeps_match_stencil_form(capi, monkeypatch):
+    """FCF sweeps without coarse correction from the paper's random iterate:
+    the Fourier form's relative residuals after 1, 2, 3 and 7 sweeps equal
+    the oracle's to the FP32 second pass (1e-6), as the stencil form's do."""
+    fam, p, nx, nt, m = "ERK", 3, 256, 512, 4
+    c = schemes.cfl_number(fam, p)
+    st = stepping.FineStep(fam, p, c, nx)
+    U = workloads.random_iterate(nt, nx, workloads.sin4(nx), 3)
+    r0 = float(np.linalg.norm(omg.spacetime_residual(U, np.zeros_like(U), st)))
+    got = {}
+    for fourier in ("0", "1"):
+        monkeypatch.setenv("MGRIT_FCF_FOURIER", fourier)
+        opts = capi.mgrit_opts_default(m=m, levels=2, max_iter=0, precision=1)
+        h = capi.mgrit_setup(capi.problem(nx, nt, fam, p, p, c), opts)
+        try:
+            res, status = capi.mgrit_solve_from(h, np.ascontiguousarray(U[::m]), r0, allow_not_converged=True)
+            assert status == -4 and res.fine_fourier == int(fourier)
+            got[fourier] = [capi.mgrit_relax(h, 1) for _ in range(3)] + [capi.mgrit_relax(h, 4)]
+        finally:
+            capi.mgrit_destroy(h)
+    G = np.zeros_like(U)
+    want = []
+    for k in range(1 + 3 + 4):
+        omg.f_relax(U, G, st, m)
+        omg.c_relax(U, G, st, m)
+        omg.f_relax(U, G, st, m)
+        if 1 <= k <= 3 or k == 7:
+            want.append(float(np.linalg.norm(omg.c_residual(U, G, st, m))) / r0)
+    np.testing.assert_allclose(got["1"], want, rtol=1e-6)
+    np.testing.assert_allclose(got["0"], want, rtol=1e-6)
