@@ -390,7 +390,8 @@ typedef struct mgrit_server_opts {
 
 /* Continuous-batching server.  The paper has no counterpart: this is a
  * serving layer around the solve of Section 2.2, whose per-solve arithmetic
- * is mgrit_solve's.  A host thread admits submitted solves while their state
+ * is mgrit_solve's (its batched level-1 FCF applies Phi^m as a stencil, as
+ * mgrit_solve does with MGRIT_FCF_FOURIER=0).  A host thread admits submitted solves while their state
  * fits in the budget, advances every admitted solve by one MGRIT cycle per
  * batched launch, retires converged solves and frees their slots.  It runs
  * on the device that is current when the server is created. */

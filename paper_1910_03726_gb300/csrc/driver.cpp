@@ -646,9 +646,10 @@ int fine_prec(const mgrit_handle* h) {
 
 namespace {
 struct TuneKey {
-  int prec, nx, span, ntaps, m, inflow;
+  int prec, nx, span, ntaps, m, inflow, fourier;  // fourier: the Fourier form was a candidate
   bool operator<(const TuneKey& o) const {
-    return std::tie(prec, nx, span, ntaps, m, inflow) < std::tie(o.prec, o.nx, o.span, o.ntaps, o.m, o.inflow);
+    return std::tie(prec, nx, span, ntaps, m, inflow, fourier) <
+           std::tie(o.prec, o.nx, o.span, o.ntaps, o.m, o.inflow, o.fourier);
   }
 };
 struct TunePick {
@@ -704,7 +705,7 @@ void autotune_fine(mgrit_handle* h) {
       return;
     }
   }
-  const TuneKey key{prec, nx, h->dphi.span, h->dphi.n, h->m, h->inflow ? 1 : 0};
+  const TuneKey key{prec, nx, h->dphi.span, h->dphi.n, h->m, h->inflow ? 1 : 0, h->ftab ? 1 : 0};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);

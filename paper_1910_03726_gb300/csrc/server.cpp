@@ -20,7 +20,9 @@
 // Requests that arrive while others run join at the next turn, so their work
 // overlaps on the device with the solves already in flight.  Per-solve
 // arithmetic is the single-solve path's (same kernels, same block shapes),
-// so a result is the same alone and in the mix.
+// so a result is the same alone and in the mix.  (The batched FCF applies
+// Phi^m as a stencil: a MIXED solve alone matches it with the Fourier-space
+// FP64 pass off, MGRIT_FCF_FOURIER=0; with it on, to that pass's rounding.)
 #include <cuda_runtime.h>
 
 #include <algorithm>
