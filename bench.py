@@ -13,7 +13,10 @@ sequential time stepping.
 
 Prints one JSON line (rank 0).  Multi-GPU runs are independent replicas
 (the solve has no data-parallel exchange on one box): value = total DOF of all
-ranks / max-over-ranks time.
+ranks / max-over-ranks time.  Its roofline object is for the level-1 FCF in
+the form the autotuner picked: the stencil form against the FP64 FMA peak, the
+Fourier-space form against the FP64 pipe's issue rate times that form's flops
+per operation (fourier_fcf_work).
 """
 from __future__ import annotations
 
